@@ -1,0 +1,276 @@
+/*
+ * kbc_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, double-precision CPU statement of the entropic
+ * multi-relaxation-time lattice Boltzmann (KBC) step that the CUDA library
+ * computes.  It exists to check the CUDA path: only the tests, the smoke
+ * check and the CPU-baseline leg of the benchmark may load it.  It shares no
+ * code, header or table with the CUDA library.
+ *
+ * Paper: Dorschner, Chikatamarla, Karlin, "Fluid-structure interaction with
+ * the entropic lattice Boltzmann method" (arXiv 1710.02375).
+ *   - evolution / over-relaxation ............ Eq. (f_equations)
+ *   - kinematic / shear / higher split ........ Eq. (popSplit)
+ *   - mirror state ............................ Eq. (f_mirr)
+ *   - entropic equilibrium .................... Eqs. (feq_min), (conservationLaws)
+ *   - stabiliser gamma ........................ Eq. (gamma_min_approx)
+ *   - viscosity ............................... Eq. (visc)
+ *
+ * Readings of points the paper leaves open (each is pinned by a test):
+ *   - Lattices D2Q9 / D3Q27 are tensor products of D1Q3 with weights 2/3
+ *     (c = 0) and 1/6 (c = +-1).
+ *   - The minimiser of Eq. (feq_min) under Eq. (conservationLaws) is taken in
+ *     its closed product form (Ansumali, Karlin, Oettinger 2003):
+ *       feq_i = rho prod_a w(c_ia) (2 - S_a) ((2 u_a + S_a)/(1 - u_a))^c_ia,
+ *       S_a = sqrt(1 + 3 u_a^2).
+ *   - k = {rho, j}; s = trace-free (deviatoric) part of the second moments;
+ *     h = everything else (trace, third and fourth order moments).
+ *   - gamma = 2 (plain BGK with omega = 2 beta) when <dh|dh> <= 1e-30.
+ *
+ * Population layout (the library's interface layout as well): structure of
+ * arrays f[i][z][y][x], direction index i = (cz+1)*9 + (cy+1)*3 + (cx+1) for
+ * D3Q27 and i = (cy+1)*3 + (cx+1) for D2Q9; the opposite of i is Q-1-i.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_MAXQ 27
+
+typedef struct {
+  int Q, D;
+  int c[OR_MAXQ][3];
+  double w[OR_MAXQ];
+} or_lattice;
+
+static int make_lattice(int lat, or_lattice *L) {
+  const double w1[3] = {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0}; /* index c+1 */
+  if (lat == 9) {
+    L->Q = 9; L->D = 2;
+    for (int cy = -1; cy <= 1; ++cy)
+      for (int cx = -1; cx <= 1; ++cx) {
+        int i = (cy + 1) * 3 + (cx + 1);
+        L->c[i][0] = cx; L->c[i][1] = cy; L->c[i][2] = 0;
+        L->w[i] = w1[cx + 1] * w1[cy + 1];
+      }
+    return 0;
+  }
+  if (lat == 27) {
+    L->Q = 27; L->D = 3;
+    for (int cz = -1; cz <= 1; ++cz)
+      for (int cy = -1; cy <= 1; ++cy)
+        for (int cx = -1; cx <= 1; ++cx) {
+          int i = (cz + 1) * 9 + (cy + 1) * 3 + (cx + 1);
+          L->c[i][0] = cx; L->c[i][1] = cy; L->c[i][2] = cz;
+          L->w[i] = w1[cx + 1] * w1[cy + 1] * w1[cz + 1];
+        }
+    return 0;
+  }
+  return -1;
+}
+
+/* ---- exported lattice tables (for tests) ---- */
+int or_lattice_tables(int lat, int *c /*[Q][3]*/, double *w /*[Q]*/) {
+  or_lattice L;
+  if (make_lattice(lat, &L)) return -1;
+  for (int i = 0; i < L.Q; ++i) {
+    for (int a = 0; a < 3; ++a) c[3 * i + a] = L.c[i][a];
+    w[i] = L.w[i];
+  }
+  return L.Q;
+}
+
+/* Entropic equilibrium, Eq. (feq_min) under Eq. (conservationLaws), in the
+ * closed product form.  u has 3 components; for D2Q9 u[2] is ignored. */
+static void equilibrium(const or_lattice *L, double rho, const double *u, double *feq) {
+  for (int i = 0; i < L->Q; ++i) {
+    double p = rho;
+    for (int a = 0; a < L->D; ++a) {
+      double S = sqrt(1.0 + 3.0 * u[a] * u[a]);
+      int ci = L->c[i][a];
+      double w1 = (ci == 0) ? 2.0 / 3.0 : 1.0 / 6.0;
+      double f = w1 * (2.0 - S);
+      if (ci == 1) f *= (2.0 * u[a] + S) / (1.0 - u[a]);
+      if (ci == -1) f *= (1.0 - u[a]) / (2.0 * u[a] + S);
+      p *= f;
+    }
+    feq[i] = p;
+  }
+}
+
+int or_equilibrium(int lat, double rho, const double *u, double *feq) {
+  or_lattice L;
+  if (make_lattice(lat, &L)) return -1;
+  equilibrium(&L, rho, u, feq);
+  return 0;
+}
+
+/* Zeroth, first and second moments of a population vector. */
+static void moments(const or_lattice *L, const double *f, double *rho, double *j, double P[3][3]) {
+  *rho = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    j[a] = 0.0;
+    for (int b = 0; b < 3; ++b) P[a][b] = 0.0;
+  }
+  for (int i = 0; i < L->Q; ++i) {
+    *rho += f[i];
+    for (int a = 0; a < 3; ++a) {
+      j[a] += L->c[i][a] * f[i];
+      for (int b = 0; b < 3; ++b) P[a][b] += L->c[i][a] * L->c[i][b] * f[i];
+    }
+  }
+}
+
+/* Shear part of a population vector with second-moment tensor dP: the
+ * population carrying exactly the trace-free part of dP and no other natural
+ * moment (Eq. popSplit, s-part). */
+static void shear_part(const or_lattice *L, const double dP[3][3], double *s) {
+  for (int i = 0; i < L->Q; ++i) {
+    const int *c = L->c[i];
+    int nnz = (c[0] != 0) + (c[1] != 0) + (c[2] != 0);
+    double v = 0.0;
+    if (L->D == 2) {
+      double N = dP[0][0] - dP[1][1];
+      if (nnz == 1) v = (c[0] != 0) ? N / 4.0 : -N / 4.0;
+      else if (nnz == 2) v = c[0] * c[1] * dP[0][1] / 4.0;
+    } else {
+      double Nxz = dP[0][0] - dP[2][2], Nyz = dP[1][1] - dP[2][2];
+      if (nnz == 1) {
+        if (c[0] != 0) v = (2.0 * Nxz - Nyz) / 6.0;
+        else if (c[1] != 0) v = (2.0 * Nyz - Nxz) / 6.0;
+        else v = -(Nxz + Nyz) / 6.0;
+      } else if (nnz == 2) {
+        if (c[2] == 0) v = c[0] * c[1] * dP[0][1] / 4.0;
+        else if (c[1] == 0) v = c[0] * c[2] * dP[0][2] / 4.0;
+        else v = c[1] * c[2] * dP[1][2] / 4.0;
+      }
+    }
+    s[i] = v;
+  }
+}
+
+/* One KBC collision at one node, Eqs. (f_equations), (f_mirr),
+ * (gamma_min_approx).  mode 0: KBC; mode 1: gamma fixed to 2 (BGK).
+ * Outputs (optional, may be NULL): gamma, ds[Q], dh[Q], feq[Q]. */
+static void collide(const or_lattice *L, double beta, int mode, const double *f, double *fout,
+                    double *gamma_out, double *ds_out, double *dh_out, double *feq_out) {
+  const int Q = L->Q;
+  double rho, j[3], P[3][3], u[3], feq[OR_MAXQ];
+  moments(L, f, &rho, j, P);
+  for (int a = 0; a < 3; ++a) u[a] = j[a] / rho;
+  equilibrium(L, rho, u, feq);
+
+  double rho_e, j_e[3], Peq[3][3], dP[3][3];
+  moments(L, feq, &rho_e, j_e, Peq);
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) dP[a][b] = P[a][b] - Peq[a][b];
+
+  double ds[OR_MAXQ], dh[OR_MAXQ];
+  shear_part(L, dP, ds);
+  for (int i = 0; i < Q; ++i) dh[i] = (f[i] - feq[i]) - ds[i]; /* dk = 0 */
+
+  double sh = 0.0, hh = 0.0;
+  for (int i = 0; i < Q; ++i) {
+    sh += ds[i] * dh[i] / feq[i];
+    hh += dh[i] * dh[i] / feq[i];
+  }
+  double gamma = 2.0;
+  if (mode == 0 && hh > 1e-30) gamma = 1.0 / beta - (2.0 - 1.0 / beta) * sh / hh;
+
+  for (int i = 0; i < Q; ++i) {
+    /* f_mirr = k + (2 s_eq - s) + ((1 - gamma) h + gamma h_eq) = f - 2 ds - gamma dh */
+    double fmirr = f[i] - 2.0 * ds[i] - gamma * dh[i];
+    fout[i] = (1.0 - beta) * f[i] + beta * fmirr;
+  }
+  if (gamma_out) *gamma_out = gamma;
+  if (ds_out) memcpy(ds_out, ds, sizeof(double) * Q);
+  if (dh_out) memcpy(dh_out, dh, sizeof(double) * Q);
+  if (feq_out) memcpy(feq_out, feq, sizeof(double) * Q);
+}
+
+int or_collide(int lat, double beta, int mode, const double *f, double *fout, double *gamma,
+               double *ds, double *dh, double *feq) {
+  or_lattice L;
+  if (make_lattice(lat, &L)) return -1;
+  collide(&L, beta, mode, f, fout, gamma, ds, dh, feq);
+  return 0;
+}
+
+static inline long idx3(int x, int y, int z, int nx, int ny) {
+  return ((long)z * ny + y) * nx + x;
+}
+static inline int wrap(int a, int n) { return ((a % n) + n) % n; }
+
+/* Initialise a state to the equilibrium of given macroscopic fields.
+ * rho[n], u[3][n] (n = nx*ny*nz, x fastest). */
+int or_init_equilibrium(int lat, int nx, int ny, int nz, const double *rho, const double *u,
+                        double *f) {
+  or_lattice L;
+  if (make_lattice(lat, &L)) return -1;
+  long n = (long)nx * ny * nz;
+  double feq[OR_MAXQ];
+  for (long k = 0; k < n; ++k) {
+    double uk[3] = {u[k], u[n + k], (L.D == 3) ? u[2 * n + k] : 0.0};
+    equilibrium(&L, rho[k], uk, feq);
+    for (int i = 0; i < L.Q; ++i) f[i * n + k] = feq[i];
+  }
+  return 0;
+}
+
+/* Density and velocity of a state: rho[n], u[3][n]. */
+int or_macros(int lat, int nx, int ny, int nz, const double *f, double *rho, double *u) {
+  or_lattice L;
+  if (make_lattice(lat, &L)) return -1;
+  long n = (long)nx * ny * nz;
+  for (long k = 0; k < n; ++k) {
+    double r = 0, j[3] = {0, 0, 0};
+    for (int i = 0; i < L.Q; ++i) {
+      double v = f[i * n + k];
+      r += v;
+      for (int a = 0; a < 3; ++a) j[a] += L.c[i][a] * v;
+    }
+    rho[k] = r;
+    for (int a = 0; a < 3; ++a) u[a * n + k] = j[a] / r;
+  }
+  return 0;
+}
+
+/* Fully periodic time step: pull-stream f_i(x) = f'_i(x - c_i), then the KBC
+ * collision, Eq. (f_equations).  fin and fout hold post-collision states. */
+int or_step_periodic(int lat, int nx, int ny, int nz, double beta, int mode, const double *fin,
+                     double *fout, double *gamma_field) {
+  or_lattice L;
+  if (make_lattice(lat, &L)) return -1;
+  if (L.D == 2 && nz != 1) return -1;
+  long n = (long)nx * ny * nz;
+  double f[OR_MAXQ], fo[OR_MAXQ], g;
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        long k = idx3(x, y, z, nx, ny);
+        for (int i = 0; i < L.Q; ++i) {
+          int xs = wrap(x - L.c[i][0], nx), ys = wrap(y - L.c[i][1], ny),
+              zs = wrap(z - L.c[i][2], nz);
+          f[i] = fin[i * n + idx3(xs, ys, zs, nx, ny)];
+        }
+        collide(&L, beta, mode, f, fo, &g, NULL, NULL, NULL);
+        for (int i = 0; i < L.Q; ++i) fout[i * n + k] = fo[i];
+        if (gamma_field) gamma_field[k] = g;
+      }
+  return 0;
+}
+
+/* nsteps periodic steps; the state is advanced in place (f has Q*n doubles,
+ * work is scratch of the same size). */
+int or_run_periodic(int lat, int nx, int ny, int nz, double beta, int mode, int nsteps, double *f,
+                    double *work) {
+  for (int t = 0; t < nsteps; ++t) {
+    int rc = or_step_periodic(lat, nx, ny, nz, beta, mode, f, work, NULL);
+    if (rc) return rc;
+    or_lattice L;
+    make_lattice(lat, &L);
+    memcpy(f, work, sizeof(double) * (size_t)L.Q * nx * ny * nz);
+  }
+  return 0;
+}

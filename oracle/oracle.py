@@ -1,0 +1,146 @@
+"""ctypes binding of the FP64 CPU oracle -- TEST INFRASTRUCTURE ONLY.
+
+The oracle (``kbc_oracle.c`` and friends in this folder) is a plain, slow,
+double-precision statement of the entropic lattice Boltzmann (KBC) method of
+Dorschner, Chikatamarla & Karlin (arXiv 1710.02375).  Only the tests, the
+smoke check and the CPU-baseline leg of ``bench.py`` may import this module;
+the CUDA library never does, and this module never touches the CUDA library.
+
+Each wrapper names the equation of the paper it follows; the C source states
+the readings of points the paper leaves open.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SOURCES = ["kbc_oracle.c"]
+_LIB_PATH = os.path.join(_HERE, "libkbc_oracle.so")
+_lib = None
+
+D = ctypes.POINTER(ctypes.c_double)
+I32 = ctypes.POINTER(ctypes.c_int32)
+U8 = ctypes.POINTER(ctypes.c_uint8)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle's C sources into a shared library with gcc."""
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES]
+    if not force and os.path.exists(_LIB_PATH):
+        lib_mtime = os.path.getmtime(_LIB_PATH)
+        if all(os.path.getmtime(s) <= lib_mtime for s in srcs):
+            return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
+           "-o", tmp] + srcs + ["-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        _declare(_lib)
+    return _lib
+
+
+def _declare(L):
+    c_int, c_double = ctypes.c_int, ctypes.c_double
+    L.or_lattice_tables.argtypes = [c_int, I32, D]
+    L.or_equilibrium.argtypes = [c_int, c_double, D, D]
+    L.or_collide.argtypes = [c_int, c_double, c_int, D, D, D, D, D, D]
+    L.or_init_equilibrium.argtypes = [c_int, c_int, c_int, c_int, D, D, D]
+    L.or_macros.argtypes = [c_int, c_int, c_int, c_int, D, D, D]
+    L.or_step_periodic.argtypes = [c_int, c_int, c_int, c_int, c_double, c_int, D, D, D]
+    L.or_run_periodic.argtypes = [c_int, c_int, c_int, c_int, c_double, c_int, c_int, D, D]
+
+
+def _p(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(D)
+
+
+def _check(rc):
+    if rc < 0:
+        raise RuntimeError(f"oracle call failed with status {rc}")
+    return rc
+
+
+def lattice(lat: int):
+    """Velocities c[Q,3] and weights W[Q] (tensor product of D1Q3)."""
+    Q = lat
+    c = np.zeros((Q, 3), dtype=np.int32)
+    w = np.zeros(Q, dtype=np.float64)
+    _check(lib().or_lattice_tables(lat, c.ctypes.data_as(I32), _p(w)))
+    return c, w
+
+
+def equilibrium(lat: int, rho: float, u) -> np.ndarray:
+    """Minimiser of H(f) = sum f ln(f/W) at given rho, u (Eqs. feq_min, conservationLaws)."""
+    uu = np.zeros(3)
+    uu[: len(u)] = u
+    feq = np.zeros(lat)
+    _check(lib().or_equilibrium(lat, float(rho), _p(uu), _p(feq)))
+    return feq
+
+
+def collide(lat: int, beta: float, f: np.ndarray, mode: int = 0):
+    """One KBC collision (Eqs. f_equations, f_mirr, gamma_min_approx) at one node.
+
+    mode 0 is KBC, mode 1 fixes gamma = 2 (LBGK with omega = 2 beta).
+    Returns (f_post, gamma, ds, dh, feq)."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    fo = np.zeros(lat)
+    g = np.zeros(1)
+    ds = np.zeros(lat)
+    dh = np.zeros(lat)
+    feq = np.zeros(lat)
+    _check(lib().or_collide(lat, float(beta), int(mode), _p(f), _p(fo), _p(g), _p(ds), _p(dh), _p(feq)))
+    return fo, float(g[0]), ds, dh, feq
+
+
+def init_equilibrium(lat: int, rho: np.ndarray, u: np.ndarray) -> np.ndarray:
+    """State f[Q, nz, ny, nx] = feq(rho, u) per node; rho[nz,ny,nx], u[dim,nz,ny,nx]."""
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    nz, ny, nx = rho.shape
+    u3 = np.zeros((3,) + rho.shape)
+    u3[: u.shape[0]] = u
+    f = np.zeros((lat,) + rho.shape)
+    _check(lib().or_init_equilibrium(lat, nx, ny, nz, _p(rho), _p(u3), _p(f)))
+    return f
+
+
+def macros(lat: int, f: np.ndarray):
+    """Density rho[nz,ny,nx] and velocity u[3,nz,ny,nx] of a state."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    _, nz, ny, nx = f.shape
+    rho = np.zeros((nz, ny, nx))
+    u = np.zeros((3, nz, ny, nx))
+    _check(lib().or_macros(lat, nx, ny, nz, _p(f), _p(rho), _p(u)))
+    return rho, u
+
+
+def step_periodic(lat: int, beta: float, f: np.ndarray, mode: int = 0, want_gamma: bool = False):
+    """One fully periodic pull-stream + collide step (Eq. f_equations)."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    _, nz, ny, nx = f.shape
+    fo = np.zeros_like(f)
+    g = np.zeros((nz, ny, nx)) if want_gamma else None
+    _check(lib().or_step_periodic(lat, nx, ny, nz, float(beta), int(mode), _p(f), _p(fo),
+                                  _p(g) if want_gamma else None))
+    return (fo, g) if want_gamma else fo
+
+
+def run_periodic(lat: int, beta: float, f: np.ndarray, nsteps: int, mode: int = 0) -> np.ndarray:
+    """nsteps periodic steps starting from the post-collision state f."""
+    f = np.array(f, dtype=np.float64, order="C", copy=True)
+    work = np.zeros_like(f)
+    _, nz, ny, nx = f.shape
+    _check(lib().or_run_periodic(lat, nx, ny, nz, float(beta), int(mode), int(nsteps), _p(f), _p(work)))
+    return f
