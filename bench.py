@@ -1,0 +1,298 @@
+"""Benchmark of the fused D3Q27 KBC sweep (MLUPS and fraction of the HBM roofline).
+
+Workload: periodic D3Q27 Taylor-Green vortex, 128^3 nodes, u0 = 0.05,
+Re = 1600, FP32 storage of f - W (226 MB per population buffer, larger than
+the 129 MB L2, so no L2 flush is needed between steps).  A step is one pass of
+the hot path over the whole lattice: pull-stream + KBC collision, one kernel.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  With N > 1 (torchrun) every rank advances its own
+independent replica of the workload ("replicas only": the path has no
+exchange step in this build) and value sums the nodes of all ranks over the
+slowest rank's time.  --impl reference times the FP64 CPU oracle on the host
+cores (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "D3Q27 KBC MLUPS & % HBM roofline; mixed/batched/surrogate vs FP32 at stated err"
+UNIT = "MLUPS"
+N_LATTICE = 128
+U0, RE = 0.05, 1600.0
+Q = 27
+SWEEP_SOURCES = ["paper_1710_02375_gb300/csrc/kbc_collide.cuh", "paper_1710_02375_gb300/csrc/kbc_sweep.cu",
+                 "paper_1710_02375_gb300/csrc/kbc_common.cuh"]
+PROFILE_MD = os.path.join(ROOT, "profiles", "kbc_sweep_d3q27_f32_tgv128.md")
+
+
+def sweep_source_hash() -> str:
+    h = hashlib.sha256()
+    for p in SWEEP_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per sweep launch from the committed ncu summary, if it was taken
+    on the current sweep source (else None)."""
+    if not os.path.exists(PROFILE_MD):
+        return None
+    txt = open(PROFILE_MD).read()
+    m_h = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
+    m_t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not (m_h and m_t) or m_h.group(1) != sweep_source_hash():
+        return None
+    return float(m_t.group(1))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, fl in rows for k, v in enumerate(fl) if v.lower() == "active"})
+        sm_max = max(r[1] for r in rows)
+        loaded = [r[0] for r in rows if r[0] > 0.5 * sm_max] or [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": sm_max, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def tgv_problem(n=N_LATTICE):
+    from paper_1710_02375_gb300 import synth
+    nu = U0 * (n / (2 * 3.141592653589793)) / RE
+    beta = 1.0 / (6.0 * nu + 1.0)
+    rho, u = synth.tgv_fields(n, n, n, U0)
+    return beta, rho, u
+
+
+def cpu_baseline_oracle(steps=2):
+    """The FP64 oracle, as it stands, on the host cores: `steps` time steps of the
+    full 128^3 workload (single-threaded plain C)."""
+    from oracle import oracle as orc
+    beta, rho, u = tgv_problem()
+    f = orc.init_equilibrium(Q, rho, u)
+    t0 = time.perf_counter()
+    orc.run_periodic(Q, beta, f, steps)
+    dt = time.perf_counter() - t0
+    nodes = N_LATTICE ** 3
+    return {"value": nodes * steps / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} steps of the 128^3 D3Q27 TGV workload ({nodes} nodes), FP64, "
+                      f"single-threaded, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle, timed as it stands on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle import oracle as orc
+    beta, rho, u = tgv_problem()
+    # bounded per-step sample: a periodic 128 x R x 1 slab of the 128^3 fields,
+    # R chosen so the whole run stays near 90 s at ~0.4 MLUPS
+    budget_nodes = 0.4e6 * 90.0 / max(1, args.steps + args.warmup)
+    R = int(max(1, min(N_LATTICE, budget_nodes // N_LATTICE)))
+    rs = np.ascontiguousarray(rho[:1, :R, :])
+    us = np.ascontiguousarray(u[:, :1, :R, :])
+    f = orc.init_equilibrium(Q, rs, us)
+    for _ in range(args.warmup):
+        f = orc.run_periodic(Q, beta, f, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = orc.run_periodic(Q, beta, f, 1)
+    dt = time.perf_counter() - t0
+    nodes = N_LATTICE * R
+    value = nodes * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "D3Q27 KBC periodic Taylor-Green vortex 128^3, u0=0.05, Re=1600",
+                   "sample": f"periodic 128x{R}x1 slab of the 128^3 fields per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{nodes} nodes per step, FP64 plain C, single-threaded"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1710_02375_gb300.lbm import Lattice
+
+    beta, rho, u = tgv_problem()
+    stream = torch.cuda.Stream()
+    L = Lattice(Q, N_LATTICE, N_LATTICE, N_LATTICE, beta, stream=stream)
+    L.init_equilibrium(rho, u)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    L.step(args.warmup)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    L.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    L.check()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    nodes = N_LATTICE ** 3
+    value = world * nodes * args.steps / (ms * 1e-3) / 1e6
+    per_launch_s = ms * 1e-3 / args.steps
+    alg_bytes = 2 * Q * 4 * nodes
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / per_launch_s / 1e9
+
+    # ---- end to end through the C ABI with pinned host buffers: upload the
+    # initial fields, then per step lbm_step + lbm_get_macros to the host
+    e2e_steps = max(3, min(args.steps, 20))
+    rho_h = torch.from_numpy(rho).pin_memory()
+    u_h = torch.from_numpy(np.ascontiguousarray(u)).pin_memory()
+    rho_o = torch.empty(rho.shape, dtype=torch.float64).pin_memory()
+    u_o = torch.empty(u.shape, dtype=torch.float64).pin_memory()
+    from paper_1710_02375_gb300 import lbm as abi
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    abi.lbm_init_equilibrium(L.ctx, rho_h, u_h)
+    for _ in range(e2e_steps):
+        abi.lbm_step(L.ctx, 1)
+        abi.lbm_get_macros(L.ctx, rho_o, u_o)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    h2d = (rho.nbytes + u.nbytes) / e2e_steps
+    d2h = rho.nbytes + u.nbytes
+    e2e_val = world * nodes * e2e_steps / e2e_s / 1e6
+    L.close()
+
+    if rank != 0:
+        return
+    cpu = None if args.no_cpu_baseline else cpu_baseline_oracle()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "D3Q27 KBC periodic Taylor-Green vortex 128^3, u0=0.05, Re=1600, "
+                               "FP32 storage of f-W",
+                   "nodes": nodes, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (226 MB per population buffer, no flush)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": recorded_traffic(),
+                     "peak_kind": peak_kind, "algorithmic_bytes_per_launch": alg_bytes},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": e2e_steps},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40000)
+    ap.add_argument("--warmup", type=int, default=500)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

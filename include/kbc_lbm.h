@@ -1,0 +1,133 @@
+/*
+ * kbc_lbm.h -- C ABI of the GB300 (sm_103a) entropic lattice Boltzmann
+ * library for fluid-structure interaction.
+ *
+ * Method: Dorschner, Chikatamarla & Karlin, "Fluid-structure interaction with
+ * the entropic lattice Boltzmann method" (arXiv 1710.02375):
+ *   - fluid step: KBC collide-and-stream, Eqs. (f_equations), (popSplit),
+ *     (f_mirr), (feq_min), (conservationLaws), (gamma_min_approx); viscosity
+ *     nu = c_s^2 (1/(2 beta) - 1/2), Eq. (visc);
+ *   - moving walls: Grad's approximation for missing populations, Eq. (grad),
+ *     with target values (section "Fluid boundary conditions");
+ *   - force on the structure (section "Solid boundary conditions").
+ *
+ * General rules for every call:
+ *   - All arguments are plain pointers and sizes.  A pointer argument may be
+ *     host memory or device memory of the context's device; the library tells
+ *     them apart with cudaPointerGetAttributes.  Caller-owned arrays are only
+ *     read (inputs) or written (outputs) during the call; the library keeps
+ *     no reference to them.
+ *   - Work runs in order on one CUDA stream (the caller's, given in
+ *     lbm_config.stream, or one the library creates).  lbm_step returns
+ *     without waiting for the GPU; every lbm_get_* call waits for the stream.
+ *   - Every call returns an lbm_status.  On failure lbm_last_error() gives a
+ *     one-line message.  A CUDA error poisons the context: every later call
+ *     except lbm_last_error/lbm_destroy returns LBM_ESTATE.
+ *   - Units are lattice units (dx = dt = 1).
+ *
+ * Population layout (the interface layout of every populations array):
+ *   structure of arrays f[i][z][y][x] with x fastest, interior nodes only,
+ *   direction index i = (cz+1)*9 + (cy+1)*3 + (cx+1) for D3Q27 and
+ *   i = (cy+1)*3 + (cx+1) for D2Q9 (nz = 1); the opposite direction of i is
+ *   Q-1-i.  Weights are tensor products of (1/6, 2/3, 1/6).
+ */
+#ifndef KBC_LBM_H
+#define KBC_LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_EINVAL = -1,    /* bad argument */
+  LBM_ENOMEM = -2,    /* workspace too small or allocation failed */
+  LBM_ECUDA = -3,     /* CUDA runtime error (context poisoned) */
+  LBM_EUNSTABLE = -4, /* non-finite or non-positive density met */
+  LBM_ETIMEOUT = -5,  /* a bounded device wait gave up */
+  LBM_ECAPACITY = -6, /* a fixed-capacity buffer overflowed */
+  LBM_ESTATE = -7     /* context poisoned by an earlier error, or wrong call order */
+} lbm_status;
+
+enum { LBM_D2Q9 = 9, LBM_D3Q27 = 27 };
+
+/* Storage of populations in device memory (computation is always FP32):
+ *   F32  stores f_i - W_i        (deviation from the lattice weight)
+ *   F16  stores f_i / W_i - 1    (scaled deviation, IEEE half, round to nearest even)
+ *   BF16 stores f_i / W_i - 1    (scaled deviation, bfloat16, round to nearest even) */
+enum { LBM_STORE_F32 = 0, LBM_STORE_F16 = 1, LBM_STORE_BF16 = 2 };
+
+/* Collision: KBC (entropic multi-relaxation time, gamma from
+ * Eq. gamma_min_approx) or BGK (gamma fixed to 2, i.e. LBGK with omega = 2 beta). */
+enum { LBM_COLLIDE_KBC = 0, LBM_COLLIDE_BGK = 1 };
+
+/* Face boundary kinds, faces ordered -x, +x, -y, +y, -z, +z. */
+enum {
+  LBM_BC_PERIODIC = 0,   /* both faces of the axis must be periodic */
+  LBM_BC_WALL = 1,       /* planar no-slip wall half a cell outside the face (Grad, q = 1/2),
+                            moving with face_velocity */
+  LBM_BC_INLET = 2,      /* prescribed velocity (face_velocity, or the per-node profile) */
+  LBM_BC_OUTLET = 3,     /* rho = 1, velocity extrapolated from the interior */
+  LBM_BC_FREESTREAM = 4  /* rho = 1, u = face_velocity, no velocity gradient */
+};
+
+typedef struct {
+  int lattice;            /* LBM_D2Q9 or LBM_D3Q27 */
+  int nx, ny, nz;         /* interior nodes; nz = 1 for D2Q9 */
+  double beta;            /* relaxation parameter in (0,1); nu = (1/(2 beta) - 1/2)/3, Eq. (visc) */
+  int storage;            /* LBM_STORE_* */
+  int collision;          /* LBM_COLLIDE_* */
+  int bc[6];              /* LBM_BC_* per face */
+  double face_velocity[6][3]; /* wall / inlet / free-stream velocity per face */
+  int max_links;          /* capacity of the cut-link list (0: no immersed bodies) */
+  int max_vertices;       /* capacity of surface-mesh vertices over all bodies */
+  int max_elements;       /* capacity of surface-mesh elements over all bodies */
+  void *stream;           /* cudaStream_t to run on; NULL: the library creates one */
+} lbm_config;
+
+/* Bytes of device workspace lbm_create needs for this configuration. */
+lbm_status lbm_workspace_size(const lbm_config *cfg, size_t *bytes);
+
+/* Create a context.  workspace: device memory of at least
+ * lbm_workspace_size() bytes, 256-byte aligned, owned by the caller and kept
+ * alive until lbm_destroy; NULL makes the library allocate (and free) it with
+ * cudaMalloc.  The populations start at rest: f_i = W_i. */
+lbm_status lbm_create(const lbm_config *cfg, void *workspace, size_t workspace_bytes,
+                      lbm_ctx **out);
+
+/* Set every interior node to the entropic equilibrium of the given density
+ * rho[nz][ny][nx] and velocity u[dim][nz][ny][nx] (FP64), Eq. (feq_min). */
+lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const double *rho, const double *u);
+
+/* Set / get the populations of all interior nodes as FP64 absolute values in
+ * the interface layout f[Q][nz][ny][nx] (post-collision state). */
+lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f);
+lbm_status lbm_get_populations(lbm_ctx *ctx, double *f);
+
+/* Advance n time steps: per step, the Grad fill at boundary nodes and the
+ * fused pull-stream + KBC collision sweep, Eq. (f_equations).  Asynchronous. */
+lbm_status lbm_step(lbm_ctx *ctx, int n);
+
+/* Density rho[nz][ny][nx] and velocity u[dim][nz][ny][nx] of the current
+ * state (FP64 outputs; solid nodes give rho = 0, u = 0).  Synchronises. */
+lbm_status lbm_get_macros(lbm_ctx *ctx, double *rho, double *u);
+
+/* Wait for the stream and report LBM_EUNSTABLE if any sweep since the last
+ * check met a non-finite or non-positive density. */
+lbm_status lbm_check(lbm_ctx *ctx);
+
+/* The cudaStream_t the context runs on (for CUDA-event timing by the caller). */
+void *lbm_stream(const lbm_ctx *ctx);
+
+const char *lbm_last_error(const lbm_ctx *ctx);
+void lbm_destroy(lbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KBC_LBM_H */

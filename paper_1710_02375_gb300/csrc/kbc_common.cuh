@@ -1,0 +1,118 @@
+// kbc_common.cuh -- lattice and storage traits shared by the CUDA kernels.
+//
+// Lattices D2Q9 / D3Q27 are tensor products of D1Q3 (weights 2/3 for c = 0,
+// 1/6 for c = +-1).  Direction index i = (cz+1)*9 + (cy+1)*3 + (cx+1)
+// (D2Q9: i = (cy+1)*3 + (cx+1)); the opposite direction is Q-1-i.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace kbc {
+
+template <int Q>
+struct Lat;
+
+template <>
+struct Lat<9> {
+  static constexpr int Q = 9, D = 2;
+  __host__ __device__ static constexpr int cx(int i) { return i % 3 - 1; }
+  __host__ __device__ static constexpr int cy(int i) { return i / 3 - 1; }
+  __host__ __device__ static constexpr int cz(int) { return 0; }
+};
+
+template <>
+struct Lat<27> {
+  static constexpr int Q = 27, D = 3;
+  __host__ __device__ static constexpr int cx(int i) { return i % 3 - 1; }
+  __host__ __device__ static constexpr int cy(int i) { return (i / 3) % 3 - 1; }
+  __host__ __device__ static constexpr int cz(int i) { return i / 9 - 1; }
+};
+
+__host__ __device__ constexpr double w1d(int c) { return c == 0 ? 2.0 / 3.0 : 1.0 / 6.0; }
+
+template <class L>
+__host__ __device__ constexpr double weight(int i) {
+  return L::D == 2 ? w1d(L::cx(i)) * w1d(L::cy(i))
+                   : w1d(L::cx(i)) * w1d(L::cy(i)) * w1d(L::cz(i));
+}
+
+// ---- storage of one population ------------------------------------------
+// F32 keeps g = f - W; F16 / BF16 keep h = f/W - 1 so that every direction
+// uses the full mantissa around O(u) deviations.
+enum { STORE_F32 = 0, STORE_F16 = 1, STORE_BF16 = 2 };
+
+template <int S>
+struct Store;
+
+template <>
+struct Store<STORE_F32> {
+  using T = float;
+  static constexpr int bytes = 4;
+  __device__ __forceinline__ static float load(const T *p, float /*w*/) { return __ldg(p); }
+  __device__ __forceinline__ static void store(T *p, float g, float /*invw*/) { *p = g; }
+  __device__ __forceinline__ static T encode(double g, double /*w*/) { return (float)g; }
+  __device__ __forceinline__ static double decode(T v, double /*w*/) { return (double)v; }
+};
+
+template <>
+struct Store<STORE_F16> {
+  using T = __half;
+  static constexpr int bytes = 2;
+  __device__ __forceinline__ static float load(const T *p, float w) {
+    return w * __half2float(__ldg(p));
+  }
+  __device__ __forceinline__ static void store(T *p, float g, float invw) {
+    *p = __float2half_rn(g * invw);
+  }
+  __device__ __forceinline__ static T encode(double g, double w) { return __double2half(g / w); }
+  __device__ __forceinline__ static double decode(T v, double w) {
+    return w * (double)__half2float(v);
+  }
+};
+
+template <>
+struct Store<STORE_BF16> {
+  using T = __nv_bfloat16;
+  static constexpr int bytes = 2;
+  __device__ __forceinline__ static float load(const T *p, float w) {
+    return w * __bfloat162float(__ldg(p));
+  }
+  __device__ __forceinline__ static void store(T *p, float g, float invw) {
+    *p = __float2bfloat16_rn(g * invw);
+  }
+  __device__ __forceinline__ static T encode(double g, double w) {
+    return __float2bfloat16_rn((float)(g / w));
+  }
+  __device__ __forceinline__ static double decode(T v, double w) {
+    return w * (double)__bfloat162float(v);
+  }
+};
+
+// Node flags (one byte per stored node, ghosts included).
+enum : uint8_t { NODE_FLUID = 0, NODE_SOLID = 1, NODE_GHOST = 3 };
+
+// Geometry of the stored lattice: interior nx*ny*nz, padded by one ghost
+// layer on every non-periodic axis.
+struct Grid {
+  int nx, ny, nz;     // interior
+  int NX, NY, NZ;     // stored (interior + ghosts)
+  int px, py, pz;     // ghost padding per axis (0 periodic, 1 otherwise)
+  long long N;        // NX*NY*NZ, the population plane stride
+};
+
+__device__ __forceinline__ long long sidx(const Grid &g, int X, int Y, int Z) {
+  return ((long long)Z * g.NY + Y) * g.NX + X;
+}
+
+// Neighbour coordinate in stored space: wraps only on periodic axes (a padded
+// axis keeps X-1 >= 0 and X+1 < NX for every interior node).
+__device__ __forceinline__ int nbr(int X, int c, int NX) {
+  int s = X + c;
+  if (s < 0) s += NX;
+  if (s >= NX) s -= NX;
+  return s;
+}
+
+}  // namespace kbc

@@ -1,0 +1,237 @@
+"""Python binding of the C ABI in include/kbc_lbm.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and passes
+plain pointers and sizes; all lattice Boltzmann work runs in the CUDA library
+libkbcfsi.so.  PyTorch provides device memory (the context workspace) and the
+CUDA stream.  There is no CPU fallback: if the library is missing or does not
+load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkbcfsi.so")
+_lib = None
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ECAPACITY, LBM_ESTATE = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+STATUS_NAMES = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA", -4: "LBM_EUNSTABLE",
+                -5: "LBM_ETIMEOUT", -6: "LBM_ECAPACITY", -7: "LBM_ESTATE"}
+LBM_D2Q9, LBM_D3Q27 = 9, 27
+LBM_STORE_F32, LBM_STORE_F16, LBM_STORE_BF16 = 0, 1, 2
+LBM_COLLIDE_KBC, LBM_COLLIDE_BGK = 0, 1
+LBM_BC_PERIODIC, LBM_BC_WALL, LBM_BC_INLET, LBM_BC_OUTLET, LBM_BC_FREESTREAM = 0, 1, 2, 3, 4
+
+
+class lbm_config(ctypes.Structure):
+    _fields_ = [
+        ("lattice", ctypes.c_int),
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("beta", ctypes.c_double),
+        ("storage", ctypes.c_int),
+        ("collision", ctypes.c_int),
+        ("bc", ctypes.c_int * 6),
+        ("face_velocity", (ctypes.c_double * 3) * 6),
+        ("max_links", ctypes.c_int),
+        ("max_vertices", ctypes.c_int),
+        ("max_elements", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def load():
+    """Load libkbcfsi.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                           "(there is no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    L.lbm_workspace_size.argtypes = [ctypes.POINTER(lbm_config), ctypes.POINTER(sz)]
+    L.lbm_create.argtypes = [ctypes.POINTER(lbm_config), vp, sz, ctypes.POINTER(vp)]
+    L.lbm_init_equilibrium.argtypes = [vp, vp, vp]
+    L.lbm_set_populations.argtypes = [vp, vp]
+    L.lbm_get_populations.argtypes = [vp, vp]
+    L.lbm_step.argtypes = [vp, i32]
+    L.lbm_get_macros.argtypes = [vp, vp, vp]
+    L.lbm_check.argtypes = [vp]
+    L.lbm_stream.argtypes = [vp]
+    L.lbm_stream.restype = vp
+    L.lbm_last_error.argtypes = [vp]
+    L.lbm_last_error.restype = ctypes.c_char_p
+    L.lbm_destroy.argtypes = [vp]
+    L.lbm_destroy.restype = None
+    for name in ("lbm_workspace_size", "lbm_create", "lbm_init_equilibrium", "lbm_set_populations",
+                 "lbm_get_populations", "lbm_step", "lbm_get_macros", "lbm_check"):
+        getattr(L, name).restype = ctypes.c_int
+    _extend(L)
+    _lib = L
+    return L
+
+
+def _extend(L):
+    """Declarations of the entry points added by later subsystems (if exported)."""
+    from . import _abi_ext
+    _abi_ext.declare(L)
+
+
+def _ptr(a):
+    """Raw pointer of a numpy array or torch tensor (host or device)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _chk(ctx, st):
+    if st != LBM_OK:
+        msg = load().lbm_last_error(ctx).decode(errors="replace") if True else ""
+        raise LbmError(st, msg)
+
+
+def make_config(lattice, nx, ny, nz, beta, storage=LBM_STORE_F32, collision=LBM_COLLIDE_KBC,
+                bc=(0, 0, 0, 0, 0, 0), face_velocity=None, max_links=0, max_vertices=0,
+                max_elements=0, stream=None) -> lbm_config:
+    c = lbm_config()
+    c.lattice, c.nx, c.ny, c.nz = lattice, nx, ny, nz
+    c.beta, c.storage, c.collision = beta, storage, collision
+    for k in range(6):
+        c.bc[k] = bc[k]
+        if face_velocity is not None:
+            for a in range(3):
+                c.face_velocity[k][a] = face_velocity[k][a]
+    c.max_links, c.max_vertices, c.max_elements = max_links, max_vertices, max_elements
+    c.stream = stream
+    return c
+
+
+def lbm_workspace_size(cfg: lbm_config) -> int:
+    n = ctypes.c_size_t()
+    st = load().lbm_workspace_size(ctypes.byref(cfg), ctypes.byref(n))
+    if st != LBM_OK:
+        raise LbmError(st, load().lbm_last_error(None).decode())
+    return n.value
+
+
+def lbm_create(cfg: lbm_config, workspace_ptr: int | None, workspace_bytes: int):
+    out = ctypes.c_void_p()
+    st = load().lbm_create(ctypes.byref(cfg), workspace_ptr, workspace_bytes, ctypes.byref(out))
+    if st != LBM_OK:
+        raise LbmError(st, load().lbm_last_error(None).decode())
+    return out.value
+
+
+def lbm_init_equilibrium(ctx, rho, u):
+    _chk(ctx, load().lbm_init_equilibrium(ctx, _ptr(rho), _ptr(u)))
+
+
+def lbm_set_populations(ctx, f):
+    _chk(ctx, load().lbm_set_populations(ctx, _ptr(f)))
+
+
+def lbm_get_populations(ctx, f):
+    _chk(ctx, load().lbm_get_populations(ctx, _ptr(f)))
+
+
+def lbm_step(ctx, n: int):
+    _chk(ctx, load().lbm_step(ctx, int(n)))
+
+
+def lbm_get_macros(ctx, rho, u):
+    _chk(ctx, load().lbm_get_macros(ctx, _ptr(rho), _ptr(u)))
+
+
+def lbm_check(ctx):
+    _chk(ctx, load().lbm_check(ctx))
+
+
+def lbm_stream(ctx) -> int:
+    return load().lbm_stream(ctx)
+
+
+def lbm_last_error(ctx) -> str:
+    return load().lbm_last_error(ctx).decode(errors="replace")
+
+
+def lbm_destroy(ctx):
+    if ctx:
+        load().lbm_destroy(ctx)
+
+
+class Lattice:
+    """Owner of one context: torch allocates the workspace, the library does the work.
+
+    Arrays passed in or out may be numpy arrays (host) or torch tensors on the
+    context's device; layouts follow include/kbc_lbm.h."""
+
+    def __init__(self, lattice, nx, ny, nz, beta, storage=LBM_STORE_F32, collision=LBM_COLLIDE_KBC,
+                 bc=(0, 0, 0, 0, 0, 0), face_velocity=None, max_links=0, max_vertices=0,
+                 max_elements=0, stream=None, device="cuda"):
+        import torch
+
+        self.torch = torch
+        self.Q = lattice
+        self.dim = 2 if lattice == 9 else 3
+        self.shape = (nz, ny, nx)
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        self.cfg = make_config(lattice, nx, ny, nz, beta, storage, collision, bc, face_velocity,
+                               max_links, max_vertices, max_elements,
+                               stream=self.stream.cuda_stream)
+        nbytes = lbm_workspace_size(self.cfg)
+        # 256-byte alignment: torch's caching allocator returns 512-byte aligned blocks
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.ctx = lbm_create(self.cfg, self.workspace.data_ptr(), nbytes)
+
+    @property
+    def n(self):
+        nz, ny, nx = self.shape
+        return nx * ny * nz
+
+    def init_equilibrium(self, rho, u):
+        lbm_init_equilibrium(self.ctx, rho, u)
+
+    def set_populations(self, f):
+        lbm_set_populations(self.ctx, f)
+
+    def get_populations(self, out=None):
+        if out is None:
+            out = np.zeros((self.Q,) + self.shape)
+        lbm_get_populations(self.ctx, out)
+        return out
+
+    def step(self, n=1):
+        lbm_step(self.ctx, n)
+
+    def macros(self):
+        rho = np.zeros(self.shape)
+        u = np.zeros((self.dim,) + self.shape)
+        lbm_get_macros(self.ctx, rho, u)
+        return rho, u
+
+    def check(self):
+        lbm_check(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

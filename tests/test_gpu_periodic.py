@@ -1,0 +1,124 @@
+"""GPU-vs-oracle parity of the fused periodic KBC sweep, through the C ABI.
+
+Tolerances (FP32 storage of f - W, FP32 arithmetic):
+  * one step from a random state: |f_gpu - f_oracle| <= 2e-6 W_i per population;
+  * laminar runs of 1000 steps: max |u_gpu - u_oracle| / max |u_oracle| <= 1e-5
+    (the FP32 bound of the benchmark spec).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1710_02375_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def make(lat, shape, beta, **kw):
+    from paper_1710_02375_gb300.lbm import Lattice
+    nz, ny, nx = shape
+    return Lattice(lat, nx, ny, nz, beta, **kw)
+
+
+def rel_u_err(u_gpu, u_ref):
+    return np.max(np.abs(u_gpu - u_ref)) / np.max(np.abs(u_ref))
+
+
+@pytest.mark.parametrize("lat,shape", [(27, (6, 5, 37)), (27, (3, 9, 130)), (9, (1, 13, 70)),
+                                       (9, (1, 300, 33)), (27, (1, 1, 1)), (9, (1, 1, 1))])
+@pytest.mark.parametrize("bgk", [0, 1])
+def test_one_step_random_state(lat, shape, bgk):
+    f0 = synth.random_state(lat, shape, 0.03, 42)
+    beta = 0.91
+    L = make(lat, shape, beta, collision=bgk)
+    L.set_populations(f0)
+    L.step(1)
+    got = L.get_populations()
+    ref = orc.step_periodic(lat, beta, f0, mode=bgk)
+    w = synth.lattice_weights(lat).reshape((lat, 1, 1, 1))
+    err = np.max(np.abs(got - ref) / w)
+    assert err <= 2e-6, err
+    L.check()
+
+
+def test_set_get_roundtrip_f32():
+    lat, shape = 27, (4, 5, 6)
+    f0 = synth.random_state(lat, shape, 0.05, 1)
+    L = make(lat, shape, 0.9)
+    L.set_populations(f0)
+    got = L.get_populations()
+    w = synth.lattice_weights(lat).reshape((lat, 1, 1, 1))
+    # FP32 rounding of the deviation f - W
+    assert np.max(np.abs(got - f0) / w) <= 0.05 * 2 ** -23 * 1.01
+
+
+@pytest.mark.parametrize("lat,shape,u0,nu", [(27, (16, 20, 24), 0.05, 0.01), (9, (1, 48, 64), 0.05, 0.005)])
+def test_taylor_green_1000_steps_laminar(lat, shape, u0, nu):
+    nz, ny, nx = shape
+    rho, u = synth.tgv_fields(nx, ny, nz, u0, three_d=(lat == 27))
+    dim = 2 if lat == 9 else 3
+    beta = 1.0 / (6.0 * nu + 1.0)
+    L = make(lat, shape, beta)
+    L.init_equilibrium(rho, np.ascontiguousarray(u[:dim]))
+    L.step(1000)
+    L.check()
+    _, u_gpu = L.macros()
+    f_or = orc.run_periodic(lat, beta, orc.init_equilibrium(lat, rho, u[:dim]), 1000)
+    _, u_or = orc.macros(lat, f_or)
+    err = rel_u_err(u_gpu, u_or[:dim])
+    assert err <= 1e-5, err
+
+
+def test_taylor_green_re1600_32cube_300_steps():
+    """The C2 flow (u0 = 0.05, Re = 1600) on a 32^3 box, 300 steps."""
+    N, u0, Re = 32, 0.05, 1600.0
+    nu = u0 * (N / (2 * np.pi)) / Re
+    beta = 1.0 / (6.0 * nu + 1.0)
+    rho, u = synth.tgv_fields(N, N, N, u0)
+    L = make(27, (N, N, N), beta)
+    L.init_equilibrium(rho, u)
+    L.step(300)
+    _, u_gpu = L.macros()
+    f_or = orc.run_periodic(27, beta, orc.init_equilibrium(27, rho, u), 300)
+    _, u_or = orc.macros(27, f_or)
+    err = rel_u_err(u_gpu, u_or)
+    assert err <= 1e-5, err
+
+
+def gather_pull(lat, f, nodes):
+    """Populations streamed into each sampled node (pull from x - c_i, periodic)."""
+    c, _ = orc.lattice(lat)
+    _, nz, ny, nx = f.shape
+    out = np.empty((len(nodes), lat))
+    for k, (z, y, x) in enumerate(nodes):
+        for i in range(lat):
+            out[k, i] = f[i, (z - c[i, 2]) % nz, (y - c[i, 1]) % ny, (x - c[i, 0]) % nx]
+    return out
+
+
+def test_full_size_128cube_sampled_nodes():
+    """C2 at its full size (128^3, the benchmark's launch configuration): one
+    GPU step from a developed state, 2000 sampled nodes updated one by one by
+    the oracle from the same pre-step populations, plus global conservation."""
+    N, u0, Re = 128, 0.05, 1600.0
+    nu = u0 * (N / (2 * np.pi)) / Re
+    beta = 1.0 / (6.0 * nu + 1.0)
+    rho, u = synth.tgv_fields(N, N, N, u0)
+    L = make(27, (N, N, N), beta)
+    L.init_equilibrium(rho, u)
+    L.step(20)
+    pre = L.get_populations()
+    L.step(1)
+    post = L.get_populations()
+    rng = np.random.default_rng(0)
+    nodes = rng.integers(0, N, size=(2000, 3))
+    fin = gather_pull(27, pre, nodes)
+    w = synth.lattice_weights(27)
+    worst = 0.0
+    for k, (z, y, x) in enumerate(nodes):
+        ref, _, _, _, _ = orc.collide(27, beta, fin[k])
+        worst = max(worst, np.max(np.abs(post[:, z, y, x] - ref) / w))
+    assert worst <= 2e-6, worst
+    # mass and momentum of the whole box are conserved by the sweep
+    m_pre, m_post = pre.sum(), post.sum()
+    assert abs(m_post - m_pre) / m_pre < 1e-6
