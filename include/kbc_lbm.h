@@ -117,8 +117,17 @@ lbm_status lbm_step(lbm_ctx *ctx, int n);
  * state (FP64 outputs; solid nodes give rho = 0, u = 0).  Synchronises. */
 lbm_status lbm_get_macros(lbm_ctx *ctx, double *rho, double *u);
 
+/* Kernel form of the fused sweep.  AUTO (default) and ROWS use the persistent
+ * row-staged kernel (bulk asynchronous copies of the Q source rows of every
+ * output row into shared memory, mbarrier pipeline) when its shared-memory
+ * plan fits the device, else the direct kernel (one thread per node, Q
+ * global loads).  Results are identical.  LBM_EINVAL for an unknown value. */
+enum { LBM_SWEEP_AUTO = 0, LBM_SWEEP_DIRECT = 1, LBM_SWEEP_ROWS = 2 };
+lbm_status lbm_set_sweep_variant(lbm_ctx *ctx, int variant);
+
 /* Wait for the stream and report LBM_EUNSTABLE if any sweep since the last
- * check met a non-finite or non-positive density. */
+ * check met a non-finite or non-positive density, LBM_ETIMEOUT if a bounded
+ * device wait of the row-staged sweep gave up (the affected step is void). */
 lbm_status lbm_check(lbm_ctx *ctx);
 
 /* The cudaStream_t the context runs on (for CUDA-event timing by the caller). */

@@ -18,7 +18,7 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SOURCES = ["kbc_oracle.c"]
+_SOURCES = ["kbc_oracle.c", "kbc_oracle_bc.c"]
 _LIB_PATH = os.path.join(_HERE, "libkbc_oracle.so")
 _lib = None
 
@@ -59,6 +59,10 @@ def _declare(L):
     L.or_macros.argtypes = [c_int, c_int, c_int, c_int, D, D, D]
     L.or_step_periodic.argtypes = [c_int, c_int, c_int, c_int, c_double, c_int, D, D, D]
     L.or_run_periodic.argtypes = [c_int, c_int, c_int, c_int, c_double, c_int, c_int, D, D]
+    L.or_solid_mask.argtypes = [c_int, c_int, c_int, c_int, c_int, c_int, c_int, D, I32, I32, U8]
+    L.or_step_bc.argtypes = [c_int, c_int, c_int, c_int, c_double, c_int, I32, D,
+                             ctypes.POINTER(D), c_double, U8, c_int, c_int, c_int, D, D, I32, I32,
+                             D, D, D, D]
 
 
 def _p(a: np.ndarray):
@@ -144,3 +148,73 @@ def run_periodic(lat: int, beta: float, f: np.ndarray, nsteps: int, mode: int = 
     _, nz, ny, nx = f.shape
     _check(lib().or_run_periodic(lat, nx, ny, nz, float(beta), int(mode), int(nsteps), _p(f), _p(work)))
     return f
+
+
+# ---------------------------------------------------------------- boundaries
+class Surface:
+    """Closed surface mesh in lattice units: vertices x[nv,dim], vertex
+    velocities v[nv,dim], elements e[ne,dim] (segments / triangles) and a body
+    id per element."""
+
+    def __init__(self, x, v, e, body, nbodies=None):
+        self.x = np.ascontiguousarray(x, dtype=np.float64)
+        self.v = np.ascontiguousarray(v, dtype=np.float64)
+        self.e = np.ascontiguousarray(e, dtype=np.int32)
+        self.body = np.ascontiguousarray(body, dtype=np.int32)
+        self.dim = self.x.shape[1]
+        self.nb = int(nbodies if nbodies is not None else (self.body.max() + 1 if len(self.body) else 0))
+
+    @staticmethod
+    def empty(dim):
+        return Surface(np.zeros((0, dim)), np.zeros((0, dim)), np.zeros((0, dim), np.int32),
+                       np.zeros(0, np.int32), 0)
+
+
+def solid_mask(shape, surf: "Surface") -> np.ndarray:
+    """Interior nodes inside any closed body (crossing-number test)."""
+    nz, ny, nx = shape
+    m = np.zeros(shape, dtype=np.uint8)
+    if surf.e.shape[0]:
+        _check(lib().or_solid_mask(surf.dim, nx, ny, nz, surf.x.shape[0], surf.e.shape[0], surf.nb,
+                                   _p(surf.x), surf.e.ctypes.data_as(I32), surf.body.ctypes.data_as(I32),
+                                   m.ctypes.data_as(U8)))
+    return m
+
+
+def step_bc(lat, beta, f, bc, face_u=None, inlet=None, inlet_scale=1.0, surf=None, solid=None,
+            mode=0):
+    """One step with Grad boundaries (walls, open faces, immersed surfaces).
+
+    bc: 6 face kinds; face_u[6,3]; inlet: dict face -> profile [3, face nodes];
+    returns (f_new, vertex_force[nv,3], body_force[nb,3], n_links)."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    Q, nz, ny, nx = f.shape
+    dim = 2 if lat == 9 else 3
+    surf = surf if surf is not None else Surface.empty(dim)
+    if solid is None:
+        solid = solid_mask((nz, ny, nx), surf)
+    solid = np.ascontiguousarray(solid, dtype=np.uint8)
+    bcv = np.ascontiguousarray(bc, dtype=np.int32)
+    fu = np.zeros((6, 3)) if face_u is None else np.ascontiguousarray(face_u, dtype=np.float64)
+    keep = []
+    arr = (D * 6)()
+    for fc in range(6):
+        if inlet is not None and fc in inlet:
+            prof = np.ascontiguousarray(inlet[fc], dtype=np.float64)
+            keep.append(prof)
+            arr[fc] = _p(prof)
+        else:
+            arr[fc] = None
+    fo = np.zeros_like(f)
+    nv, ne, nb = surf.x.shape[0], surf.e.shape[0], max(surf.nb, 1)
+    vf = np.zeros((max(nv, 1), 3))
+    bf = np.zeros((nb, 3))
+    x = surf.x if nv else np.zeros((1, dim))
+    v = surf.v if nv else np.zeros((1, dim))
+    e = surf.e if ne else np.zeros((1, dim), np.int32)
+    b = surf.body if ne else np.zeros(1, np.int32)
+    n = lib().or_step_bc(lat, nx, ny, nz, float(beta), int(mode), bcv.ctypes.data_as(I32), _p(fu), arr,
+                         float(inlet_scale), solid.ctypes.data_as(U8), nv, ne, surf.nb, _p(x), _p(v),
+                         e.ctypes.data_as(I32), b.ctypes.data_as(I32), _p(f), _p(fo), _p(vf), _p(bf))
+    _check(n)
+    return fo, vf[:nv], bf[: surf.nb], n

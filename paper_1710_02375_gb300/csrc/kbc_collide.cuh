@@ -27,17 +27,18 @@ struct AxisEq {
 __device__ __forceinline__ AxisEq axis_eq(float u) {
   AxisEq a;
   const float u2 = u * u;
-  const float S = sqrtf(1.0f + 3.0f * u2);
-  const float d = 3.0f * u2 / (1.0f + S);  // S - 1 without cancellation
-  const float om = 1.0f - d;               // 2 - S
-  const float ip = __frcp_rn(1.0f - u);
-  const float im = __frcp_rn(1.0f + u);
+  const float x = fmaf(3.0f, u2, 1.0f);
+  const float S = x * rsqrtf(x);                       // sqrt(1 + 3u^2)
+  const float d = __fdividef(3.0f * u2, 1.0f + S);     // S - 1 without cancellation
+  const float om = 1.0f - d;                           // 2 - S
+  const float ip = __fdividef(1.0f, 1.0f - u);
+  const float im = __fdividef(1.0f, 1.0f + u);
   a.e[1] = -d;
   a.e[2] = fmaf(om, (d + 3.0f * u) * ip, -d);
   a.e[0] = fmaf(om, (d - 3.0f * u) * im, -d);
-  a.r[0] = __frcp_rn(1.0f + a.e[0]);
-  a.r[1] = __frcp_rn(om);
-  a.r[2] = __frcp_rn(1.0f + a.e[2]);
+  a.r[0] = __fdividef(1.0f, 1.0f + a.e[0]);
+  a.r[1] = __fdividef(1.0f, om);
+  a.r[2] = __fdividef(1.0f, 1.0f + a.e[2]);
   a.d = d;
   return a;
 }
@@ -62,7 +63,7 @@ __device__ __forceinline__ float collide(float (&g)[L::Q], float beta, bool bgk)
     if (cy && cz) pyz += cy * cz * v;
   }
   const float rho = 1.0f + drho;
-  const float irho = __frcp_rn(rho);
+  const float irho = __fdividef(1.0f, rho);
   const float ux = jx * irho, uy = jy * irho, uz = jz * irho;
 
   const AxisEq ax = axis_eq(ux), ay = axis_eq(uy);
@@ -129,9 +130,9 @@ __device__ __forceinline__ float collide(float (&g)[L::Q], float beta, bool bgk)
     sh = fmaf(ds * dh, invfeq, sh);
     hh = fmaf(dh * dh, invfeq, hh);
   }
-  const float ib = __frcp_rn(beta);
+  const float ib = __fdividef(1.0f, beta);
   float gamma = 2.f;
-  if (!bgk && hh > 1e-30f) gamma = ib - (2.f - ib) * __fdiv_rn(sh, hh);
+  if (!bgk && hh > 1e-30f) gamma = ib - (2.f - ib) * __fdividef(sh, hh);
 
   // ---- relaxation f' = f - beta (2 ds + gamma dh) = f - beta ((2 - gamma) ds + gamma df)
   const float bg = beta * gamma, b2g = beta * (2.f - gamma);

@@ -51,6 +51,7 @@ struct Store<STORE_F32> {
   using T = float;
   static constexpr int bytes = 4;
   __device__ __forceinline__ static float load(const T *p, float /*w*/) { return __ldg(p); }
+  __device__ __forceinline__ static float load_smem(const T *p, float /*w*/) { return *p; }
   __device__ __forceinline__ static void store(T *p, float g, float /*invw*/) { *p = g; }
   __device__ __forceinline__ static T encode(double g, double /*w*/) { return (float)g; }
   __device__ __forceinline__ static double decode(T v, double /*w*/) { return (double)v; }
@@ -62,6 +63,9 @@ struct Store<STORE_F16> {
   static constexpr int bytes = 2;
   __device__ __forceinline__ static float load(const T *p, float w) {
     return w * __half2float(__ldg(p));
+  }
+  __device__ __forceinline__ static float load_smem(const T *p, float w) {
+    return w * __half2float(*p);
   }
   __device__ __forceinline__ static void store(T *p, float g, float invw) {
     *p = __float2half_rn(g * invw);
@@ -78,6 +82,9 @@ struct Store<STORE_BF16> {
   static constexpr int bytes = 2;
   __device__ __forceinline__ static float load(const T *p, float w) {
     return w * __bfloat162float(__ldg(p));
+  }
+  __device__ __forceinline__ static float load_smem(const T *p, float w) {
+    return w * __bfloat162float(*p);
   }
   __device__ __forceinline__ static void store(T *p, float g, float invw) {
     *p = __float2bfloat16_rn(g * invw);
@@ -99,11 +106,13 @@ struct Grid {
   int nx, ny, nz;     // interior
   int NX, NY, NZ;     // stored (interior + ghosts)
   int px, py, pz;     // ghost padding per axis (0 periodic, 1 otherwise)
-  long long N;        // NX*NY*NZ, the population plane stride
+  int pitch;          // row stride in elements: NX rounded up to a multiple of 8
+                      // (every row starts on a 16-byte boundary for bulk copies)
+  long long N;        // pitch*NY*NZ, the population plane stride
 };
 
-__device__ __forceinline__ long long sidx(const Grid &g, int X, int Y, int Z) {
-  return ((long long)Z * g.NY + Y) * g.NX + X;
+__host__ __device__ __forceinline__ long long sidx(const Grid &g, int X, int Y, int Z) {
+  return ((long long)Z * g.NY + Y) * g.pitch + X;
 }
 
 // Neighbour coordinate in stored space: wraps only on periodic axes (a padded

@@ -7,8 +7,11 @@
 // writes Q populations per node: 2 Q bytes_per_population of algorithmic HBM
 // traffic, Eq. (f_equations); the collision (kbc_collide.cuh) stays in
 // registers.  No tensor cores: there is no contraction on this path.
+#include "bulk.cuh"
 #include "kbc_collide.cuh"
 #include "lbm_internal.h"
+
+#include <string.h>
 
 namespace kbc {
 
@@ -37,7 +40,7 @@ __global__ void __launch_bounds__(256, 2)
   float v[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const long long src = ((long long)zs[L::cz(i) + 1] * g.NY + ys[L::cy(i) + 1]) * g.NX +
+    const long long src = ((long long)zs[L::cz(i) + 1] * g.NY + ys[L::cy(i) + 1]) * g.pitch +
                           xs[L::cx(i) + 1];
     v[i] = St::load(fin + (long long)i * g.N + src, (float)weight<L>(i));
   }
@@ -48,6 +51,172 @@ __global__ void __launch_bounds__(256, 2)
     St::store(fout + (long long)i * g.N + k, v[i], (float)(1.0 / weight<L>(i)));
 }
 
+
+// ---------------------------------------------------------------- row-staged sweep
+// Persistent form of the same sweep.  A CTA walks output rows (y, z) of the
+// interior; for each it fetches, with the bulk-copy engine, the Q source rows
+// (direction i, row (y - cy_i, z - cz_i)) into a shared-memory stage, so each
+// input row crosses HBM exactly once and the memory pipeline runs ahead of the
+// collision by `stages - 1` rows without holding registers.  Threads read
+// their node's Q populations from the stage (x shift and periodic wrap
+// resolved in shared memory), collide in registers and store coalesced.
+constexpr uint32_t kMaxSpins = 1u << 22;  // bounded mbarrier waits
+
+template <int Q, int S, bool FLAGS>
+__global__ void __launch_bounds__(128, 4)
+    k_sweep_rows(Grid g, const typename Store<S>::T *__restrict__ fin,
+                 typename Store<S>::T *__restrict__ fout, const uint8_t *__restrict__ flags,
+                 float beta, int bgk, int *__restrict__ err, int row_bytes, int stages) {
+  using L = Lat<Q>;
+  using St = Store<S>;
+  using T = typename St::T;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)stages * Q * row_bytes);
+  const int tid = threadIdx.x;
+  const int nrows = g.ny * g.nz;
+  if ((int)blockIdx.x >= nrows) return;
+  const int my_rows = (nrows - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int row_elems = row_bytes / (int)sizeof(T);
+
+  if (tid == 0) {
+    for (int s = 0; s < stages; ++s) mbar_init(&bars[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  auto issue = [&](int j, int s) {
+    const int r = (int)blockIdx.x + j * (int)gridDim.x;
+    const int Y = r % g.ny + g.py, Z = r / g.ny + g.pz;
+    mbar_arrive_expect_tx(&bars[s], (uint32_t)(Q * row_bytes));
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int Ys = nbr(Y, -L::cy(i), g.NY);
+      const int Zs = (L::D == 3) ? nbr(Z, -L::cz(i), g.NZ) : Z;
+      const T *src = fin + (long long)i * g.N + ((long long)Zs * g.NY + Ys) * g.pitch;
+      bulk_g2s(smem + ((size_t)s * Q + i) * row_bytes, src, (uint32_t)row_bytes, &bars[s]);
+    }
+  };
+
+  if (tid == 0) {
+    const int pre = my_rows < stages ? my_rows : stages;
+    for (int j = 0; j < pre; ++j) issue(j, j);
+  }
+  const int groups = (g.nx + (int)blockDim.x - 1) / (int)blockDim.x;
+
+  for (int j = 0; j < my_rows; ++j) {
+    const int s = j % stages;
+    const uint32_t parity = (uint32_t)((j / stages) & 1);
+    const bool timed_out = !mbar_wait_bounded(&bars[s], parity, kMaxSpins);
+    if (__syncthreads_or(timed_out)) {
+      // give up: flag it, let the copies already issued land, leave
+      if (tid == 0) {
+        atomicOr(err, 2);
+        for (int jj = j; jj < my_rows && jj < j + stages; ++jj)
+          mbar_wait_bounded(&bars[jj % stages], (uint32_t)((jj / stages) & 1), kMaxSpins);
+      }
+      __syncthreads();
+      return;
+    }
+    const int r = (int)blockIdx.x + j * (int)gridDim.x;
+    const int Y = r % g.ny + g.py, Z = r / g.ny + g.pz;
+    const long long k0 = sidx(g, 0, Y, Z);
+    const T *stage = reinterpret_cast<const T *>(smem + (size_t)s * Q * row_bytes);
+
+    for (int grp = 0; grp < groups; ++grp) {
+      const int x = grp * (int)blockDim.x + tid;
+      const bool active = x < g.nx;
+      const int X = (active ? x : 0) + g.px;
+      const int xs[3] = {nbr(X, 1, g.NX), X, nbr(X, -1, g.NX)};
+      float v[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i)
+        v[i] = St::load_smem(stage + i * row_elems + xs[L::cx(i) + 1], (float)weight<L>(i));
+      if (grp == groups - 1) {
+        __syncthreads();  // every read of stage s is done
+        if (tid == 0 && j + stages < my_rows) {
+          fence_proxy_async_smem();
+          issue(j + stages, s);
+        }
+      }
+      if (active && (!FLAGS || flags[k0 + X] == NODE_FLUID)) {
+        const float rho = collide<L>(v, beta, bgk != 0);
+        if (!(rho > 0.f && rho < 1e30f)) atomicOr(err, 1);
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+          St::store(fout + (long long)i * g.N + k0 + X, v[i], (float)(1.0 / weight<L>(i)));
+      }
+    }
+  }
+}
+
+struct RowPlan {
+  int ok = 0, stages = 0, blocks = 0, row_bytes = 0;
+  size_t smem = 0;
+};
+
+template <int Q, int S, bool FLAGS>
+static RowPlan plan_rows(const Grid &g) {
+  RowPlan p;
+  using T = typename Store<S>::T;
+  p.row_bytes = (int)(((size_t)g.NX * sizeof(T) + 15) / 16 * 16);
+  int dev = 0, sms = 0, smem_optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  auto kern = k_sweep_rows<Q, S, FLAGS>;
+  int best_score = 0;
+  for (int st = 4; st >= 2; --st) {
+    const size_t smem = (size_t)st * Q * p.row_bytes + (size_t)st * sizeof(uint64_t);
+    if (smem > (size_t)smem_optin) continue;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, 128, smem) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    const int score = nb * (st - 1) * 4 + nb;  // rows in flight, then resident warps
+    if (nb >= 2 && score > best_score) {
+      best_score = score;
+      p.ok = 1;
+      p.stages = st;
+      p.blocks = nb * sms;
+      p.smem = smem;
+    }
+  }
+  if (p.ok) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+  return p;
+}
+
+template <int Q, int S>
+static cudaError_t sweep_rows_t(const Grid &g, const void *fin, void *fout, const uint8_t *flags,
+                                float beta, int bgk, int *err, cudaStream_t s, bool *used) {
+  using T = typename Store<S>::T;
+  // plans are cached per (template, lattice shape)
+  static thread_local Grid last_g[2] = {};
+  static thread_local RowPlan last_p[2] = {};
+  const int fi = flags ? 1 : 0;
+  if (memcmp(&last_g[fi], &g, sizeof(Grid)) != 0 || !last_p[fi].ok) {
+    last_p[fi] = flags ? plan_rows<Q, S, true>(g) : plan_rows<Q, S, false>(g);
+    last_g[fi] = g;
+  }
+  const RowPlan &p = last_p[fi];
+  *used = p.ok != 0;
+  if (!p.ok) return cudaSuccess;
+  const int nrows = g.ny * g.nz;
+  const int grid = p.blocks < nrows ? p.blocks : nrows;
+  if (flags)
+    k_sweep_rows<Q, S, true><<<grid, 128, p.smem, s>>>(g, (const T *)fin, (T *)fout, flags, beta,
+                                                       bgk, err, p.row_bytes, p.stages);
+  else
+    k_sweep_rows<Q, S, false><<<grid, 128, p.smem, s>>>(g, (const T *)fin, (T *)fout, flags, beta,
+                                                        bgk, err, p.row_bytes, p.stages);
+  return cudaGetLastError();
+}
+
 static dim3 sweep_block(const Grid &g) {
   if (g.nx >= 128) return dim3(128, 2, 1);
   if (g.nx >= 64) return dim3(64, 4, 1);
@@ -56,8 +225,13 @@ static dim3 sweep_block(const Grid &g) {
 
 template <int Q, int S>
 static cudaError_t sweep_t(const Grid &g, const void *fin, void *fout, const uint8_t *flags,
-                           float beta, int bgk, int *err, cudaStream_t s) {
+                           float beta, int bgk, int *err, cudaStream_t s, int variant) {
   using T = typename Store<S>::T;
+  if (variant != SWEEP_DIRECT) {
+    bool used = false;
+    cudaError_t e = sweep_rows_t<Q, S>(g, fin, fout, flags, beta, bgk, err, s, &used);
+    if (e != cudaSuccess || used) return e;
+  }
   dim3 b = sweep_block(g);
   dim3 grid((g.nx + b.x - 1) / b.x, (g.ny + b.y - 1) / b.y, g.nz);
   if (flags)
@@ -82,8 +256,10 @@ static cudaError_t sweep_t(const Grid &g, const void *fin, void *fout, const uin
   } while (0)
 
 cudaError_t launch_sweep(int Q, int storage, const Grid &g, const void *fin, void *fout,
-                         const uint8_t *flags, float beta, int bgk, int *err, cudaStream_t s) {
-  KBC_DISPATCH(Q, storage, return (sweep_t<QQ, SS>(g, fin, fout, flags, beta, bgk, err, s)));
+                         const uint8_t *flags, float beta, int bgk, int *err, cudaStream_t s,
+                         int variant) {
+  KBC_DISPATCH(Q, storage,
+               return (sweep_t<QQ, SS>(g, fin, fout, flags, beta, bgk, err, s, variant)));
 }
 
 // ---------------------------------------------------------------- conversions
@@ -166,23 +342,28 @@ __global__ void k_macros(Grid g, const typename Store<S>::T *__restrict__ f,
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= count) return;
   const long long k = interior_to_stored(g, begin + t);
-  double r = 0, jx = 0, jy = 0, jz = 0;
+  double r = 0, ux = 0, uy = 0, uz = 0;
   if (!flags || flags[k] == NODE_FLUID) {
+    // sums of the stored deviations in FP32 (exact to the storage precision),
+    // rho = 1 + sum and u = j / rho in FP64
+    float dr = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const double w = weight<L>(i);
-      const double v = w + Store<S>::decode(f[(long long)i * g.N + k], w);
-      r += v;
+      const float v = Store<S>::load(f + (long long)i * g.N + k, (float)weight<L>(i));
+      dr += v;
       jx += L::cx(i) * v;
       jy += L::cy(i) * v;
       jz += L::cz(i) * v;
     }
-    jx /= r; jy /= r; jz /= r;
+    r = 1.0 + (double)dr;
+    ux = (double)jx / r;
+    uy = (double)jy / r;
+    uz = (double)jz / r;
   }
   rho[t] = r;
-  u[t] = jx;
-  u[ustride + t] = jy;
-  if (L::D == 3) u[2 * ustride + t] = jz;
+  u[t] = ux;
+  u[ustride + t] = uy;
+  if (L::D == 3) u[2 * ustride + t] = uz;
 }
 
 static inline unsigned nblk(long long n, int b) { return (unsigned)((n + b - 1) / b); }

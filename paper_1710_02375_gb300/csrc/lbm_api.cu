@@ -33,7 +33,8 @@ Grid make_grid(const lbm_config &c) {
   g.NX = c.nx + 2 * g.px;
   g.NY = c.ny + 2 * g.py;
   g.NZ = c.nz + 2 * g.pz;
-  g.N = (long long)g.NX * g.NY * g.NZ;
+  g.pitch = (g.NX + 7) / 8 * 8;
+  g.N = (long long)g.pitch * g.NY * g.NZ;
   return g;
 }
 
@@ -94,6 +95,7 @@ struct lbm_ctx {
   bool has_solid = false;
   int *err = nullptr;
   char *stage = nullptr;
+  int sweep_variant = SWEEP_AUTO;
   bool poisoned = false;
   char msg[512] = {0};
 };
@@ -298,9 +300,17 @@ lbm_status lbm_step(lbm_ctx *ctx, int n) {
   for (int t = 0; t < n; ++t) {
     CK(launch_sweep(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur], ctx->f[1 - ctx->cur],
                     ctx->has_solid || ctx->g.px || ctx->g.py || ctx->g.pz ? ctx->flags : nullptr,
-                    beta, bgk, ctx->err, ctx->stream));
+                    beta, bgk, ctx->err, ctx->stream, ctx->sweep_variant));
     ctx->cur = 1 - ctx->cur;
   }
+  return LBM_OK;
+}
+
+lbm_status lbm_set_sweep_variant(lbm_ctx *ctx, int variant) {
+  GUARD();
+  if (variant < LBM_SWEEP_AUTO || variant > LBM_SWEEP_ROWS)
+    return fail(ctx, LBM_EINVAL, "lbm_set_sweep_variant: unknown variant %d", variant);
+  ctx->sweep_variant = variant;
   return LBM_OK;
 }
 
@@ -311,6 +321,7 @@ lbm_status lbm_check(lbm_ctx *ctx) {
   CK(cudaStreamSynchronize(ctx->stream));
   if (h) {
     CK(cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream));
+    if (h & 2) return fail(ctx, LBM_ETIMEOUT, "a bounded device wait gave up (flags 0x%x)", h);
     return fail(ctx, LBM_EUNSTABLE, "non-finite or non-positive density met (flags 0x%x)", h);
   }
   return LBM_OK;

@@ -10,8 +10,12 @@ namespace kbc {
 // Fused pull-stream + KBC collision over all interior nodes (solid nodes are
 // skipped when flags != nullptr).  fin / fout: population buffers in storage
 // layout [Q][NZ][NY][NX].  err: device word, bit 0 set on a bad density.
+enum { SWEEP_AUTO = 0, SWEEP_DIRECT = 1, SWEEP_ROWS = 2 };
+// variant: SWEEP_AUTO / SWEEP_ROWS use the row-staged bulk-copy kernel when its
+// shared-memory plan fits, else the direct kernel; SWEEP_DIRECT forces the latter.
 cudaError_t launch_sweep(int Q, int storage, const Grid &g, const void *fin, void *fout,
-                         const uint8_t *flags, float beta, int bgk, int *err, cudaStream_t s);
+                         const uint8_t *flags, float beta, int bgk, int *err, cudaStream_t s,
+                         int variant = SWEEP_AUTO);
 
 // f = feq(rho, u) for interior nodes [begin, begin+count) of the linear
 // interior index; rho[count], u[dim][ustride] (FP64, device).

@@ -67,6 +67,8 @@ def load():
     L.lbm_step.argtypes = [vp, i32]
     L.lbm_get_macros.argtypes = [vp, vp, vp]
     L.lbm_check.argtypes = [vp]
+    L.lbm_set_sweep_variant.argtypes = [vp, i32]
+    L.lbm_set_sweep_variant.restype = ctypes.c_int
     L.lbm_stream.argtypes = [vp]
     L.lbm_stream.restype = vp
     L.lbm_last_error.argtypes = [vp]
@@ -154,6 +156,13 @@ def lbm_get_macros(ctx, rho, u):
     _chk(ctx, load().lbm_get_macros(ctx, _ptr(rho), _ptr(u)))
 
 
+LBM_SWEEP_AUTO, LBM_SWEEP_DIRECT, LBM_SWEEP_ROWS = 0, 1, 2
+
+
+def lbm_set_sweep_variant(ctx, variant: int):
+    _chk(ctx, load().lbm_set_sweep_variant(ctx, int(variant)))
+
+
 def lbm_check(ctx):
     _chk(ctx, load().lbm_check(ctx))
 
@@ -221,6 +230,9 @@ class Lattice:
         u = np.zeros((self.dim,) + self.shape)
         lbm_get_macros(self.ctx, rho, u)
         return rho, u
+
+    def set_sweep_variant(self, variant):
+        lbm_set_sweep_variant(self.ctx, variant)
 
     def check(self):
         lbm_check(self.ctx)
