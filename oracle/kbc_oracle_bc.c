@@ -19,17 +19,21 @@
  *     the face velocity.
  *   Open node (a missing link crosses an inlet, outlet or free-stream face;
  *     first such face in the order -x,+x,-y,+y,-z,+z):
- *       inlet:       u_t = prescribed velocity, rho_t = rho(x_b, t-1)
- *       outlet:      u_t = u(x_b, t-1),         rho_t = 1
+ *       inlet:       u_t = prescribed velocity, rho_t = rho(x_n, t-1)
+ *       outlet:      u_t = u(x_n, t-1),         rho_t = 1
+ *       (x_n: the next node inward across that face, x_b itself if x_n is
+ *       not fluid)
  *       free stream: u_t = face velocity,        rho_t = 1, grad u = 0
  *   Wall node (all missing links are walls or immersed):
  *       u_i = (u_w,i + q_i u(x_b + c_i, t-1)) / (1 + q_i) if x_b + c_i is
  *             fluid, else u_w,i;  u_t = mean of u_i over M
  *       rho_t = sum_{i not in M} f_i + sum_{i in M} [f'_opp(i)(x_b, t-1)
  *               + 6 W_i c_i . u_w,i]      (moving-wall bounce-back density)
- *   grad u: per axis, central difference of u(t-1) when both neighbours are
- *     fluid, else the one-sided second-order difference with u(x_b) = u_t
- *     (first order if only one fluid node on that side), else 0.
+ *   grad u: finite differences of the previous-step velocity u(t-1): per
+ *     axis the central difference when both neighbours are fluid, else the
+ *     one-sided second-order difference through x_b itself (first order if
+ *     only one fluid node lies on that side), else 0.  (Taking the target u_t
+ *     at x_b in the one-sided stencil instead is unstable at beta = 1/2.)
  *   Pi = rho c_s^2 I + rho u u - rho c_s^2/(2 beta) (grad u + grad u^T);
  *   f*_i = W_i [rho + rho c_i.u / c_s^2 + (Pi - rho c_s^2 I):(c_i c_i - c_s^2 I)/(2 c_s^4)]
  *     replaces every missing population of the node (and only those).
@@ -255,7 +259,9 @@ static void node_moments(const field_t *F, const int *p0, double *rho, double *u
   for (int a = 0; a < 3; ++a) u[a] = j[a] / r;
 }
 
-static void grad_u(const field_t *F, const int *x, const double *ut, double G[3][3] /* G[a][b] = d u_a / d x_b */) {
+static void grad_u(const field_t *F, const int *x, double G[3][3] /* G[a][b] = d u_a / d x_b */) {
+  double r, u0[3];
+  node_moments(F, x, &r, u0);
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 3; ++b) G[a][b] = 0.0;
   for (int b = 0; b < F->L->D; ++b) {
@@ -263,7 +269,7 @@ static void grad_u(const field_t *F, const int *x, const double *ut, double G[3]
     int p2[3] = {x[0], x[1], x[2]}, m2[3] = {x[0], x[1], x[2]};
     p1[b] += 1; m1[b] -= 1; p2[b] += 2; m2[b] -= 2;
     int fp = is_fluid(F, p1), fm = is_fluid(F, m1);
-    double r, up1[3], um1[3], up2[3], um2[3];
+    double up1[3], um1[3], up2[3], um2[3];
     if (fp && fm) {
       node_moments(F, p1, &r, up1);
       node_moments(F, m1, &r, um1);
@@ -272,17 +278,17 @@ static void grad_u(const field_t *F, const int *x, const double *ut, double G[3]
       node_moments(F, p1, &r, up1);
       if (is_fluid(F, p2)) {
         node_moments(F, p2, &r, up2);
-        for (int a = 0; a < 3; ++a) G[a][b] = 0.5 * (-3.0 * ut[a] + 4.0 * up1[a] - up2[a]);
+        for (int a = 0; a < 3; ++a) G[a][b] = 0.5 * (-3.0 * u0[a] + 4.0 * up1[a] - up2[a]);
       } else {
-        for (int a = 0; a < 3; ++a) G[a][b] = up1[a] - ut[a];
+        for (int a = 0; a < 3; ++a) G[a][b] = up1[a] - u0[a];
       }
     } else if (fm) {
       node_moments(F, m1, &r, um1);
       if (is_fluid(F, m2)) {
         node_moments(F, m2, &r, um2);
-        for (int a = 0; a < 3; ++a) G[a][b] = 0.5 * (3.0 * ut[a] - 4.0 * um1[a] + um2[a]);
+        for (int a = 0; a < 3; ++a) G[a][b] = 0.5 * (3.0 * u0[a] - 4.0 * um1[a] + um2[a]);
       } else {
-        for (int a = 0; a < 3; ++a) G[a][b] = ut[a] - um1[a];
+        for (int a = 0; a < 3; ++a) G[a][b] = u0[a] - um1[a];
       }
     }
   }
@@ -395,10 +401,14 @@ int or_step_bc(int lat, int nx, int ny, int nz, double beta, int mode, const int
           double rho_t, ut[3] = {0, 0, 0};
           int zero_grad = 0;
           if (open_face >= 0) {
-            double r0, u0[3];
-            node_moments(&F, xb, &r0, u0);
+            /* the interior neighbour across the open face */
+            const int ax = open_face / 2;
+            int xin[3] = {x, y, z};
+            xin[ax] += (open_face % 2 == 0) ? 1 : -1;
+            double r0 = 1.0, u0[3] = {0, 0, 0};
+            if (is_fluid(&F, xin)) node_moments(&F, xin, &r0, u0);
+            else node_moments(&F, xb, &r0, u0);
             if (bc[open_face] == BC_INLET) {
-              const int ax = open_face / 2;
               const double *prof = inlet_u ? inlet_u[open_face] : NULL;
               if (prof) {
                 long fidx, fn;
@@ -438,7 +448,7 @@ int or_step_bc(int lat, int nx, int ny, int nz, double beta, int mode, const int
             }
           }
           double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-          if (!zero_grad) grad_u(&F, xb, ut, G);
+          if (!zero_grad) grad_u(&F, xb, G);
           double Pi[3][3];
           const double cs2 = 1.0 / 3.0;
           for (int a = 0; a < 3; ++a)
@@ -467,4 +477,52 @@ int or_step_bc(int lat, int nx, int ny, int nz, double beta, int mode, const int
         for (int i = 0; i < Q; ++i) fout[i * F.N + k] = fo[i];
       }
   return nlinks;
+}
+
+/* Immersed cut links of a static configuration: for every fluid node x_b and
+ * direction i whose source x_b - c_i is solid, the crossing found by
+ * link_hit.  Writes up to cap entries: node (linear interior index), i, q,
+ * element, and the wall velocity; returns the number of links (may exceed
+ * cap).  Periodic wrap is applied to the source node only (the link itself is
+ * taken in unwrapped coordinates, as in or_step_bc). */
+int or_links(int lat, int nx, int ny, int nz, const int *periodic, const uint8_t *solid, int nv,
+             int ne, int nb, const double *vx, const double *vv, const int32_t *el,
+             const int32_t *eb, int cap, int32_t *node, int32_t *dir, double *q, int32_t *elem,
+             double *uw) {
+  lat_t L;
+  if (lat_make(lat, &L)) return -1;
+  surf_t S = {L.D, nv, ne, nb, vx, vv, el, eb};
+  int n[3] = {nx, ny, nz};
+  int cnt = 0;
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        long k = ((long)z * ny + y) * nx + x;
+        if (solid[k]) continue;
+        for (int i = 0; i < L.Q; ++i) {
+          int p[3] = {x - L.c[i][0], y - L.c[i][1], z - L.c[i][2]};
+          int out = 0;
+          for (int a = 0; a < 3; ++a) {
+            if (p[a] < 0 || p[a] >= n[a]) {
+              if (!periodic[a]) out = 1;
+              else p[a] = ((p[a] % n[a]) + n[a]) % n[a];
+            }
+          }
+          if (out) continue;
+          if (!solid[((long)p[2] * ny + p[1]) * nx + p[0]]) continue;
+          double xb[3] = {(double)x, (double)y, (double)z}, qq, u[3];
+          int vid[3];
+          double vw[3];
+          int e = link_hit(&S, xb, L.c[i], &qq, u, vid, vw);
+          if (cnt < cap) {
+            node[cnt] = (int32_t)k;
+            dir[cnt] = i;
+            q[cnt] = e >= 0 ? qq : -1.0;
+            elem[cnt] = e;
+            for (int a = 0; a < 3; ++a) uw[3 * cnt + a] = e >= 0 ? u[a] : 0.0;
+          }
+          cnt++;
+        }
+      }
+  return cnt;
 }

@@ -63,6 +63,8 @@ def _declare(L):
     L.or_step_bc.argtypes = [c_int, c_int, c_int, c_int, c_double, c_int, I32, D,
                              ctypes.POINTER(D), c_double, U8, c_int, c_int, c_int, D, D, I32, I32,
                              D, D, D, D]
+    L.or_links.argtypes = [c_int, c_int, c_int, c_int, I32, U8, c_int, c_int, c_int, D, D, I32, I32,
+                           c_int, I32, I32, D, I32, D]
 
 
 def _p(a: np.ndarray):
@@ -218,3 +220,27 @@ def step_bc(lat, beta, f, bc, face_u=None, inlet=None, inlet_scale=1.0, surf=Non
                          e.ctypes.data_as(I32), b.ctypes.data_as(I32), _p(f), _p(fo), _p(vf), _p(bf))
     _check(n)
     return fo, vf[:nv], bf[: surf.nb], n
+
+
+def links(lat, shape, surf: "Surface", periodic=(1, 1, 1), solid=None):
+    """Immersed cut links of a static configuration: dict of arrays node, dir,
+    q, elem, uw (q = -1 and elem = -1 where no crossing was found)."""
+    nz, ny, nx = shape
+    if solid is None:
+        solid = solid_mask(shape, surf)
+    solid = np.ascontiguousarray(solid, dtype=np.uint8)
+    per = np.ascontiguousarray(periodic, dtype=np.int32)
+    args = lambda cap, a: (lat, nx, ny, nz, per.ctypes.data_as(I32), solid.ctypes.data_as(U8),
+                           surf.x.shape[0], surf.e.shape[0], surf.nb, _p(surf.x), _p(surf.v),
+                           surf.e.ctypes.data_as(I32), surf.body.ctypes.data_as(I32), cap,
+                           a["node"].ctypes.data_as(I32), a["dir"].ctypes.data_as(I32), _p(a["q"]),
+                           a["elem"].ctypes.data_as(I32), _p(a["uw"]))
+
+    def alloc(cap):
+        return {"node": np.zeros(cap, np.int32), "dir": np.zeros(cap, np.int32), "q": np.zeros(cap),
+                "elem": np.zeros(cap, np.int32), "uw": np.zeros((cap, 3))}
+    a = alloc(1)
+    n = _check(lib().or_links(*args(0, a)))
+    a = alloc(max(n, 1))
+    _check(lib().or_links(*args(n, a)))
+    return {k: v[:n] for k, v in a.items()}

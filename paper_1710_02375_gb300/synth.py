@@ -63,3 +63,57 @@ def random_macros(shape, u_amp: float, rho_amp: float, seed: int, dim: int = 3):
     u = np.zeros((3,) + tuple(shape))
     u[:dim] = u_amp * rng.uniform(-1, 1, size=(dim,) + tuple(shape))
     return rho, u
+
+
+# ---------------------------------------------------------------- surface meshes
+def circle_polygon(cx: float, cy: float, r: float, n: int, phase: float = 0.5):
+    """Closed polygon of n segments approximating a circle; vertices at angles
+    2 pi (k + phase) / n.  Returns (x[n,2], e[n,2])."""
+    t = 2 * np.pi * (np.arange(n) + phase) / n
+    x = np.stack([cx + r * np.cos(t), cy + r * np.sin(t)], axis=1)
+    e = np.stack([np.arange(n), (np.arange(n) + 1) % n], axis=1).astype(np.int32)
+    return x, e
+
+
+def rect_polygon(x0: float, y0: float, x1: float, y1: float):
+    """Closed counter-clockwise rectangle (x[4,2], e[4,2])."""
+    x = np.array([[x0, y0], [x1, y0], [x1, y1], [x0, y1]], dtype=np.float64)
+    e = np.array([[0, 1], [1, 2], [2, 3], [3, 0]], dtype=np.int32)
+    return x, e
+
+
+def icosphere(center, r: float, level: int = 2, rotate: float = 0.3):
+    """Closed triangulated sphere (subdivided icosahedron, rotated by `rotate`
+    radians about a generic axis so no vertex sits on a lattice line).
+    Returns (x[nv,3], e[ne,3])."""
+    p = (1 + 5 ** 0.5) / 2
+    v = [(-1, p, 0), (1, p, 0), (-1, -p, 0), (1, -p, 0), (0, -1, p), (0, 1, p), (0, -1, -p), (0, 1, -p),
+         (p, 0, -1), (p, 0, 1), (-p, 0, -1), (-p, 0, 1)]
+    f = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4), (11, 10, 2),
+         (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9), (4, 9, 5),
+         (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    verts = [np.array(a, dtype=np.float64) / np.linalg.norm(a) for a in v]
+    faces = list(f)
+    for _ in range(level):
+        cache = {}
+
+        def mid(a, b):
+            key = (min(a, b), max(a, b))
+            if key not in cache:
+                m = verts[a] + verts[b]
+                verts.append(m / np.linalg.norm(m))
+                cache[key] = len(verts) - 1
+            return cache[key]
+
+        nf = []
+        for a, b, c in faces:
+            ab, bc, ca = mid(a, b), mid(b, c), mid(c, a)
+            nf += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        faces = nf
+    X = np.array(verts)
+    ax = np.array([0.48, 0.6, 0.64])
+    ax /= np.linalg.norm(ax)
+    K = np.array([[0, -ax[2], ax[1]], [ax[2], 0, -ax[0]], [-ax[1], ax[0], 0]])
+    R = np.eye(3) + np.sin(rotate) * K + (1 - np.cos(rotate)) * K @ K
+    X = X @ R.T
+    return np.asarray(center, dtype=np.float64) + r * X, np.array(faces, dtype=np.int32)
