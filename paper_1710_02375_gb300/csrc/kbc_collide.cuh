@@ -13,6 +13,8 @@
 //                                                   -- Eq. (gamma_min_approx)
 //   f' = f - beta (2 ds + gamma dh)                 -- Eqs. (f_equations), (f_mirr)
 // gamma = 2 (LBGK, omega = 2 beta) when <dh|dh> <= 1e-30 or BGK is requested.
+// The metric weights are evaluated up to the common factor 1/rho, so the
+// degenerate-case threshold applies to rho <dh|dh>.
 #pragma once
 #include "kbc_common.cuh"
 
@@ -20,7 +22,7 @@ namespace kbc {
 
 struct AxisEq {
   float e[3];   // phi(c) - 1 for c = -1, 0, +1
-  float r[3];   // 1 / phi(c)
+  float r[3];   // 1 / (w(c) phi(c)): per-axis factor of the entropic metric 1/feq
   float d;      // S - 1
 };
 
@@ -36,32 +38,53 @@ __device__ __forceinline__ AxisEq axis_eq(float u) {
   a.e[1] = -d;
   a.e[2] = fmaf(om, (d + 3.0f * u) * ip, -d);
   a.e[0] = fmaf(om, (d - 3.0f * u) * im, -d);
-  a.r[0] = __fdividef(1.0f, 1.0f + a.e[0]);
-  a.r[1] = __fdividef(1.0f, om);
-  a.r[2] = __fdividef(1.0f, 1.0f + a.e[2]);
+  a.r[0] = __fdividef(6.0f, 1.0f + a.e[0]);
+  a.r[1] = __fdividef(1.5f, om);
+  a.r[2] = __fdividef(6.0f, 1.0f + a.e[2]);
   a.d = d;
   return a;
 }
 
-// In-place collision of g[Q] (deviations).  Returns rho (for stability checks).
+// In-place collision of g[Q] (deviations g_i = f_i - W_i).  Returns rho.
+//
+// Sums are taken in the tensor-product structure of the lattice (rows of
+// three x-neighbours, then planes), the equilibrium factors and the metric
+// weights 1/feq_i (up to the common factor 1/rho, which cancels in gamma) as
+// products of per-axis factors, and <ds|dh> grouped by the six distinct
+// values of ds.
 template <class L>
 __device__ __forceinline__ float collide(float (&g)[L::Q], float beta, bool bgk) {
   constexpr int Q = L::Q;
-  // ---- moments of the deviations
-  float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-  float pxx = 0.f, pyy = 0.f, pzz = 0.f, pxy = 0.f, pxz = 0.f, pyz = 0.f;
+  constexpr int NR = Q / 3;  // rows of three x-neighbours (cy, cz)
+  // ---- moments of the deviations (Eq. conservationLaws and second moments)
+  float rs[NR], rd[NR], rm[NR];  // per row: g+ + g-, g+ - g-, g- + g0 + g+
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-    const float v = g[i];
-    drho += v;
-    if (cx) { jx += cx * v; pxx += v; }
-    if (cy) { jy += cy * v; pyy += v; }
-    if (cz) { jz += cz * v; pzz += v; }
-    if (cx && cy) pxy += cx * cy * v;
-    if (cx && cz) pxz += cx * cz * v;
-    if (cy && cz) pyz += cy * cz * v;
+  for (int r = 0; r < NR; ++r) {
+    rs[r] = g[3 * r + 2] + g[3 * r];
+    rd[r] = g[3 * r + 2] - g[3 * r];
+    rm[r] = rs[r] + g[3 * r + 1];
   }
+  // row r has cy = r % 3 - 1, cz = r / 3 - 1
+  float drho = 0.f, jx = 0.f, pxx = 0.f;
+  float yp = 0.f, ym = 0.f, zp = 0.f, zm = 0.f;      // sums of rm over cy = +-1, cz = +-1
+  float pxy = 0.f, pxz = 0.f, pyz = 0.f;
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    const int cy = r % 3 - 1, cz = (L::D == 3) ? r / 3 - 1 : 0;
+    drho += rm[r];
+    jx += rd[r];
+    pxx += rs[r];
+    if (cy > 0) yp += rm[r];
+    if (cy < 0) ym += rm[r];
+    if (cz > 0) zp += rm[r];
+    if (cz < 0) zm += rm[r];
+    if (cy) pxy += cy * rd[r];
+    if (cz) pxz += cz * rd[r];
+    if (cy && cz) pyz += cy * cz * rm[r];
+  }
+  const float jy = yp - ym, pyy = yp + ym;
+  const float jz = zp - zm, pzz = zp + zm;
+
   const float rho = 1.0f + drho;
   const float irho = __fdividef(1.0f, rho);
   const float ux = jx * irho, uy = jy * irho, uz = jz * irho;
@@ -70,84 +93,93 @@ __device__ __forceinline__ float collide(float (&g)[L::Q], float beta, bool bgk)
   AxisEq az;
   if (L::D == 3) az = axis_eq(uz);
 
-  // ---- deviatoric non-equilibrium stress -> shear part (Eq. popSplit)
+  // ---- shear part of f - feq from the deviatoric non-equilibrium stress
   // dPi_aa = P_aa - (drho + 2 rho d_a)/3, dPi_ab = P_ab - rho u_a u_b
   const float dxx = pxx - (drho + 2.f * rho * ax.d) * (1.f / 3.f);
   const float dyy = pyy - (drho + 2.f * rho * ay.d) * (1.f / 3.f);
-  const float dxy = pxy - rho * ux * uy;
-  float s_x, s_y, s_z = 0.f, s_xy, s_xz = 0.f, s_yz = 0.f;
+  float sv[6];  // ds of the x, y, z faces and of the xy, xz, yz edges (sign +)
   if (L::D == 2) {
     const float N = dxx - dyy;
-    s_x = 0.25f * N;
-    s_y = -0.25f * N;
-    s_xy = 0.25f * dxy;
+    sv[0] = 0.25f * N;
+    sv[1] = -0.25f * N;
+    sv[2] = 0.f;
+    sv[3] = 0.25f * (pxy - rho * ux * uy);
+    sv[4] = sv[5] = 0.f;
   } else {
     const float dzz = pzz - (drho + 2.f * rho * az.d) * (1.f / 3.f);
     const float Nxz = dxx - dzz, Nyz = dyy - dzz;
-    s_x = (2.f * Nxz - Nyz) * (1.f / 6.f);
-    s_y = (2.f * Nyz - Nxz) * (1.f / 6.f);
-    s_z = -(Nxz + Nyz) * (1.f / 6.f);
-    s_xy = 0.25f * dxy;
-    s_xz = 0.25f * (pxz - rho * ux * uz);
-    s_yz = 0.25f * (pyz - rho * uy * uz);
+    sv[0] = (2.f * Nxz - Nyz) * (1.f / 6.f);
+    sv[1] = (2.f * Nyz - Nxz) * (1.f / 6.f);
+    sv[2] = -(Nxz + Nyz) * (1.f / 6.f);
+    sv[3] = 0.25f * (pxy - rho * ux * uy);
+    sv[4] = 0.25f * (pxz - rho * ux * uz);
+    sv[5] = 0.25f * (pyz - rho * uy * uz);
   }
 
-  // ---- entropic products <ds|dh>, <dh|dh>
+  // ---- per-direction non-equilibrium part and the entropic products
+  float exy[9], mxy[9];
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      exy[3 * b + a] = fmaf(ax.e[a], ay.e[b], ax.e[a] + ay.e[b]);
+      mxy[3 * b + a] = ax.r[a] * ay.r[b];
+    }
   float df[Q];
-  float sh = 0.f, hh = 0.f;
-  const float irho_w = irho;
+  float grp[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // signed sums of m_i dh_i per ds group
+  float hh = 0.f;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-    const float W = (float)weight<L>(i);
-    const float iW = (float)(1.0 / weight<L>(i));
-    // feq_i - W_i = W_i (drho + rho e_i), e_i = prod(1 + eps_a) - 1
-    float e = ax.e[cx + 1];
-    float r = ax.r[cx + 1];
-    {
-      const float ey = ay.e[cy + 1];
-      e = e + ey + e * ey;
-      r *= ay.r[cy + 1];
-    }
+    const int k2 = 3 * (cy + 1) + (cx + 1);
+    float e = exy[k2], m = mxy[k2];
     if (L::D == 3) {
       const float ez = az.e[cz + 1];
-      e = e + ez + e * ez;
-      r *= az.r[cz + 1];
+      e = fmaf(e, ez, e + ez);
+      m *= az.r[cz + 1];
     }
-    const float feqdev = W * fmaf(rho, e, drho);
-    const float invfeq = iW * irho_w * r;
-    float ds = 0.f;
-    const int nnz = (cx != 0) + (cy != 0) + (cz != 0);
-    if (nnz == 1) ds = cx ? s_x : (cy ? s_y : s_z);
-    if (nnz == 2) {
-      if (cx && cy) ds = cx * cy * s_xy;
-      else if (cx && cz) ds = cx * cz * s_xz;
-      else ds = cy * cz * s_yz;
-    }
-    const float d = g[i] - feqdev;
+    // feq_i - W_i = W_i (drho + rho e_i);  df_i = g_i - (feq_i - W_i)
+    const float d = fmaf(-(float)weight<L>(i), fmaf(rho, e, drho), g[i]);
     df[i] = d;
-    const float dh = d - ds;
-    sh = fmaf(ds * dh, invfeq, sh);
-    hh = fmaf(dh * dh, invfeq, hh);
+    const int nnz = (cx != 0) + (cy != 0) + (cz != 0);
+    int gi = -1, sg = 1;
+    if (nnz == 1) gi = cx ? 0 : (cy ? 1 : 2);
+    if (nnz == 2) {
+      if (cx && cy) { gi = 3; sg = cx * cy; }
+      else if (cx && cz) { gi = 4; sg = cx * cz; }
+      else { gi = 5; sg = cy * cz; }
+    }
+    const float dh = (gi >= 0) ? d - sg * sv[gi < 0 ? 0 : gi] : d;
+    const float t = m * dh;
+    hh = fmaf(t, dh, hh);
+    if (gi >= 0) grp[gi] += sg * t;
   }
+  float sh = 0.f;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) sh = fmaf(sv[k], grp[k], sh);
+
   const float ib = __fdividef(1.0f, beta);
   float gamma = 2.f;
+  // <.|.> carries a common factor rho that cancels in the ratio
   if (!bgk && hh > 1e-30f) gamma = ib - (2.f - ib) * __fdividef(sh, hh);
 
-  // ---- relaxation f' = f - beta (2 ds + gamma dh) = f - beta ((2 - gamma) ds + gamma df)
+  // ---- relaxation f' = f - beta (2 ds + gamma dh) = f - beta (gamma df + (2 - gamma) ds)
   const float bg = beta * gamma, b2g = beta * (2.f - gamma);
+  float bs[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) bs[k] = b2g * sv[k];
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-    float ds = 0.f;
     const int nnz = (cx != 0) + (cy != 0) + (cz != 0);
-    if (nnz == 1) ds = cx ? s_x : (cy ? s_y : s_z);
+    float sds = 0.f;
+    if (nnz == 1) sds = cx ? bs[0] : (cy ? bs[1] : bs[2]);
     if (nnz == 2) {
-      if (cx && cy) ds = cx * cy * s_xy;
-      else if (cx && cz) ds = cx * cz * s_xz;
-      else ds = cy * cz * s_yz;
+      if (cx && cy) sds = cx * cy * bs[3];
+      else if (cx && cz) sds = cx * cz * bs[4];
+      else sds = cy * cz * bs[5];
     }
-    g[i] = g[i] - fmaf(bg, df[i], b2g * ds);
+    g[i] = g[i] - fmaf(bg, df[i], sds);
   }
   return rho;
 }
