@@ -87,6 +87,7 @@ typedef struct {
   int max_links;          /* capacity of the cut-link list (0: no immersed bodies) */
   int max_vertices;       /* capacity of surface-mesh vertices over all bodies */
   int max_elements;       /* capacity of surface-mesh elements over all bodies */
+  int inlet_ramp_steps;   /* inlet velocity ramp (1 - cos(pi t/T))/2 over T steps, 0: none */
   void *stream;           /* cudaStream_t to run on; NULL: the library creates one */
 } lbm_config;
 
@@ -112,6 +113,60 @@ lbm_status lbm_get_populations(lbm_ctx *ctx, double *f);
 /* Advance n time steps: per step, the Grad fill at boundary nodes and the
  * fused pull-stream + KBC collision sweep, Eq. (f_equations).  Asynchronous. */
 lbm_status lbm_step(lbm_ctx *ctx, int n);
+
+/* ---------------------------------------------------------------------------
+ * Boundaries (section "Fluid boundary conditions"): every fluid node with a
+ * missing population (its source x - c_i is solid or beyond a non-periodic
+ * face) gets Grad's approximation, Eq. (grad), with Pi = Pi_eq + Pi_neq as
+ * stated after it, from target values:
+ *   wall node: u_t = mean over missing links of (u_w + q u(x_b + c_i))/(1 + q),
+ *     rho_t = moving-wall bounce-back density, grad u by finite differences of
+ *     the previous-step velocity;
+ *   open face (first inlet/outlet/free-stream face crossed): prescribed u and
+ *     rho of the next inward node (inlet), rho = 1 and u of the next inward
+ *     node (outlet), rho = 1 and the face velocity with grad u = 0 (free stream).
+ * ------------------------------------------------------------------------- */
+
+/* Prescribed inlet velocity of face `face` (must be LBM_BC_INLET): u[3][m]
+ * FP64, m = the face's node count, indexed by the two other interior
+ * coordinates in (z, y, x) order with the face axis removed (face -x: z*ny+y;
+ * face -y: z*nx+x; face -z: y*nx+x).  Copied.  Without it the inlet uses
+ * face_velocity.  LBM_EINVAL if the face is not an inlet. */
+lbm_status lbm_set_inlet_profile(lbm_ctx *ctx, int face, const double *u);
+
+/* Immersed bodies (section "Fluid boundary conditions": the structure's
+ * surface mesh passed to the fluid solver).  verts[nv][dim] positions in
+ * lattice units (interior node (x,y,z) sits at (x,y,z)), elems[ne][dim]
+ * closed polygons (2-D, segments) or closed triangle meshes (3-D),
+ * elem_body[ne] in [0, nbodies), vert_vel[nv][dim] wall velocities (NULL:
+ * at rest).  Nodes inside a body become solid; cut links (nearest crossing
+ * along each lattice link) are built on the device.  band_margin: how far
+ * (lattice units) the surface may later move from this position; bodies plus
+ * margin must stay 2 nodes inside non-periodic faces (LBM_EINVAL), and at
+ * most 16 bodies.  LBM_ECAPACITY if the mesh exceeds max_vertices /
+ * max_elements or the links exceed max_links.  Arrays are copied; synchronises. */
+lbm_status lbm_set_geometry(lbm_ctx *ctx, int nbodies, const double *verts, int nv,
+                            const int32_t *elems, int ne, const int32_t *elem_body,
+                            const double *vert_vel, double band_margin);
+
+/* New vertex positions / velocities of the same mesh (moving surface, the
+ * coupling step of the conventional serial staggered scheme).  Solid flags
+ * and cut links of the band are rebuilt on the device; nodes that leave the
+ * solid are set to the entropic equilibrium of the mean density of their
+ * fluid neighbours and the velocity of the nearest vertex.  Asynchronous; a
+ * link-list overflow is reported by lbm_check as LBM_ECAPACITY. */
+lbm_status lbm_update_surface(lbm_ctx *ctx, const double *verts, const double *vert_vel);
+
+/* Momentum-exchange force of the last step on the immersed surface,
+ * accumulated in FP64: vert_force[nv][3] (each link's force split over the
+ * hit element's vertices by its interpolation weights) and
+ * body_force[nbodies][3] totals.  Either may be NULL.  Per link i of fluid
+ * node x_b: -c_i (f'_opp(i)(x_b, t-1) + f*_i(x_b, t)).  Synchronises. */
+lbm_status lbm_get_interface_force(lbm_ctx *ctx, double *vert_force, double *body_force);
+
+/* info[4] = {face boundary nodes, immersed boundary nodes, cut links,
+ * inlet-ramp step counter}.  Synchronises. */
+lbm_status lbm_get_boundary_info(lbm_ctx *ctx, int *info);
 
 /* Density rho[nz][ny][nx] and velocity u[dim][nz][ny][nx] of the current
  * state (FP64 outputs; solid nodes give rho = 0, u = 0).  Synchronises. */

@@ -526,3 +526,74 @@ int or_links(int lat, int nx, int ny, int nz, const int *periodic, const uint8_t
       }
   return cnt;
 }
+
+/* Nodes that leave the solid when the surface moves ("fresh" nodes; the
+ * paper accounts for the mass swept by the object through the target
+ * density, the state of uncovered nodes is left open).  Reading: a node with
+ * old_solid = 1 and new_solid = 0 is set to the entropic equilibrium of
+ * rho_bar = mean density of its neighbours x + c_i (i not the rest
+ * direction) that are fluid in the new mask and not fresh themselves (1 if
+ * none), and of the velocity of the nearest surface vertex (lowest index on
+ * ties).  f is the post-collision state [Q][n], updated in place.  Returns
+ * the number of fresh nodes. */
+int or_fresh_init(int lat, int nx, int ny, int nz, const int *periodic, const uint8_t *old_solid,
+                  const uint8_t *new_solid, int nv, const double *vx, const double *vv, double *f) {
+  lat_t L;
+  if (lat_make(lat, &L)) return -1;
+  field_t F;
+  F.L = &L;
+  F.n[0] = nx; F.n[1] = ny; F.n[2] = nz;
+  for (int a = 0; a < 3; ++a) F.periodic[a] = periodic[a];
+  F.solid = new_solid;
+  F.fin = f;
+  F.N = (long)nx * ny * nz;
+  int nfresh = 0;
+  for (long k = 0; k < F.N; ++k)
+    if (old_solid[k] && !new_solid[k]) nfresh++;
+  if (!nfresh) return 0;
+  double *rho_bar = (double *)malloc(sizeof(double) * nfresh);
+  long *idx = (long *)malloc(sizeof(long) * nfresh);
+  int m = 0;
+  for (long k = 0; k < F.N; ++k) {
+    if (!(old_solid[k] && !new_solid[k])) continue;
+    int p0[3] = {(int)(k % nx), (int)((k / nx) % ny), (int)(k / ((long)nx * ny))};
+    double rs = 0.0;
+    int rn = 0;
+    for (int i = 0; i < L.Q; ++i) {
+      if (!L.c[i][0] && !L.c[i][1] && !L.c[i][2]) continue;
+      int p[3] = {p0[0] + L.c[i][0], p0[1] + L.c[i][1], p0[2] + L.c[i][2]};
+      if (!in_domain(&F, p)) continue;
+      long kn = nid(&F, p);
+      if (new_solid[kn]) continue;
+      if (old_solid[kn]) continue; /* fresh itself */
+      double r, u[3];
+      node_moments(&F, p, &r, u);
+      rs += r;
+      rn++;
+    }
+    rho_bar[m] = rn ? rs / rn : 1.0;
+    idx[m] = k;
+    m++;
+  }
+  for (int q = 0; q < nfresh; ++q) {
+    long k = idx[q];
+    double p[3] = {(double)(k % nx), (double)((k / nx) % ny), (double)(k / ((long)nx * ny))};
+    int best = 0;
+    double bd = 1e300;
+    for (int v = 0; v < nv; ++v) {
+      double d2 = 0.0;
+      for (int a = 0; a < L.D; ++a) {
+        double dd = vx[L.D * v + a] - p[a];
+        d2 += dd * dd;
+      }
+      if (d2 < bd) { bd = d2; best = v; }
+    }
+    double u[3] = {0, 0, 0}, feq[MAXQ];
+    for (int a = 0; a < L.D; ++a) u[a] = vv[L.D * best + a];
+    or_equilibrium(lat, rho_bar[q], u, feq);
+    for (int i = 0; i < L.Q; ++i) f[i * F.N + k] = feq[i];
+  }
+  free(rho_bar);
+  free(idx);
+  return nfresh;
+}

@@ -63,6 +63,7 @@ def _declare(L):
     L.or_step_bc.argtypes = [c_int, c_int, c_int, c_int, c_double, c_int, I32, D,
                              ctypes.POINTER(D), c_double, U8, c_int, c_int, c_int, D, D, I32, I32,
                              D, D, D, D]
+    L.or_fresh_init.argtypes = [c_int, c_int, c_int, c_int, I32, U8, U8, c_int, D, D, D]
     L.or_links.argtypes = [c_int, c_int, c_int, c_int, I32, U8, c_int, c_int, c_int, D, D, I32, I32,
                            c_int, I32, I32, D, I32, D]
 
@@ -244,3 +245,15 @@ def links(lat, shape, surf: "Surface", periodic=(1, 1, 1), solid=None):
     a = alloc(max(n, 1))
     _check(lib().or_links(*args(n, a)))
     return {k: v[:n] for k, v in a.items()}
+
+
+def fresh_init(lat, f, old_solid, new_solid, surf: "Surface", periodic=(0, 0, 1)):
+    """Initialise nodes uncovered by a moving surface (in place); returns their count."""
+    Q, nz, ny, nx = f.shape
+    assert f.dtype == np.float64 and f.flags["C_CONTIGUOUS"]
+    per = np.ascontiguousarray(periodic, dtype=np.int32)
+    a = np.ascontiguousarray(old_solid, dtype=np.uint8)
+    b = np.ascontiguousarray(new_solid, dtype=np.uint8)
+    return _check(lib().or_fresh_init(lat, nx, ny, nz, per.ctypes.data_as(I32), a.ctypes.data_as(U8),
+                                      b.ctypes.data_as(U8), surf.x.shape[0], _p(surf.x), _p(surf.v),
+                                      _p(f)))

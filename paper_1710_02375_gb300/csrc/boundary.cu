@@ -1,0 +1,626 @@
+// boundary.cu -- Grad's-approximation boundary fill, cut-link geometry and
+// the momentum-exchange force gather (arXiv 1710.02375, section "Fluid
+// boundary conditions", Eq. (grad); section "Solid boundary conditions").
+//
+// Readings of the target values (the paper defers them to earlier work):
+//   missing set M(x_b): directions i whose source x_b - c_i is solid or a
+//     ghost beyond a non-periodic face;
+//   immersed link i: crossing at x_b - q_i c_i (nearest, q in (0,1]) with the
+//     wall velocity interpolated on the hit element; a wall face: q = 1/2 and
+//     the face velocity;
+//   open node (a missing link crosses an inlet/outlet/free-stream face, first
+//     such face in the order -x,+x,-y,+y,-z,+z): inlet u_t = prescribed,
+//     rho_t = rho(x_n); outlet u_t = u(x_n), rho_t = 1; free stream
+//     u_t = face velocity, rho_t = 1, grad u = 0 (x_n: next node inward);
+//   wall node: u_t = mean over M of (u_w + q u(x_b + c_i)) / (1 + q) (u_w
+//     alone if x_b + c_i is not fluid); rho_t = moving-wall bounce-back density
+//     sum_known f_i + sum_M [f'_opp(i)(x_b) + 6 W_i c_i.u_w];
+//   grad u: central differences of the previous-step velocity, one-sided
+//     second order through x_b at walls (first order with one fluid node);
+//   f*_i = W_i [rho + 3 rho c_i.u + 9/2 (rho u u + Pi_neq):(c_i c_i - I/3)],
+//     Pi_neq = -rho/(6 beta) (grad u + grad u^T), for every missing i;
+//   force on the surface per immersed link: -c_i (f'_opp(i)(x_b) + f*_i),
+//     accumulated in FP64 per vertex (interpolation weights) and per body.
+// The previous-step velocity of a node is the first moment of its stored
+// post-collision populations (collisions conserve it).
+//
+// Layout: the fill writes f*_i straight into the solid (or ghost) slot
+// A[i][x_b - c_i] of the source buffer, which the fused sweep then pulls
+// unchanged; no boundary branch is needed in the sweep itself.
+#include "boundary.cuh"
+#include "lbm_internal.h"
+
+namespace kbc {
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ void decompose(const Grid &g, long long k, int &X, int &Y, int &Z) {
+  X = (int)(k % g.pitch);
+  const long long r = k / g.pitch;
+  Y = (int)(r % g.NY);
+  Z = (int)(r / g.NY);
+}
+
+// Stored coordinate S + c on one axis; -1 if it leaves the interior of a
+// padded (non-periodic) axis.
+__device__ __forceinline__ int step_axis(int S, int c, int NS, int pad) {
+  int s = S + c;
+  if (pad) return (s < pad || s >= NS - pad) ? -1 : s;
+  while (s < 0) s += NS;
+  while (s >= NS) s -= NS;
+  return s;
+}
+
+template <int Q, int S>
+__device__ void dev_moments(const Grid &g, const typename Store<S>::T *f, long long k, float &drho,
+                            float (&j)[3]) {
+  using L = Lat<Q>;
+  drho = 0.f;
+  j[0] = j[1] = j[2] = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const float v = Store<S>::load(f + (long long)i * g.N + k, (float)weight<L>(i));
+    drho += v;
+    j[0] += L::cx(i) * v;
+    j[1] += L::cy(i) * v;
+    j[2] += L::cz(i) * v;
+  }
+}
+
+template <int Q, int S>
+__device__ void dev_velocity(const Grid &g, const typename Store<S>::T *f, long long k, float (&u)[3],
+                             float *rho = nullptr) {
+  float dr, j[3];
+  dev_moments<Q, S>(g, f, k, dr, j);
+  const float r = 1.f + dr;
+  for (int a = 0; a < 3; ++a) u[a] = j[a] / r;
+  if (rho) *rho = r;
+}
+
+// ---------------------------------------------------------------- ghosts / faces
+__global__ void k_mark_ghosts(Grid g, uint8_t *flags) {
+  const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k >= g.N) return;
+  int X, Y, Z;
+  decompose(g, k, X, Y, Z);
+  const bool ghost = X >= g.NX || (g.px && (X == 0 || X == g.NX - 1)) ||
+                     (g.py && (Y == 0 || Y == g.NY - 1)) || (g.pz && (Z == 0 || Z == g.NZ - 1));
+  flags[k] = ghost ? NODE_GHOST : NODE_FLUID;
+}
+
+// Interior nodes that touch a non-periodic face.
+__global__ void k_face_nodes(Grid g, BNode *out, int *count, int cap) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long n = (long long)g.nx * g.ny * g.nz;
+  if (t >= n) return;
+  const int x = (int)(t % g.nx), y = (int)((t / g.nx) % g.ny), z = (int)(t / ((long long)g.nx * g.ny));
+  const bool face = (g.px && (x == 0 || x == g.nx - 1)) || (g.py && (y == 0 || y == g.ny - 1)) ||
+                    (g.pz && (z == 0 || z == g.nz - 1));
+  if (!face) return;
+  const int slot = atomicAdd(count, 1);
+  if (slot < cap) out[slot] = BNode{sidx(g, x + g.px, y + g.py, z + g.pz), -1, 0};
+}
+
+// ---------------------------------------------------------------- geometry (FP64)
+__constant__ double c_ray2[2] = {0.8191520442889918, 0.5735764363510461};
+__constant__ double c_ray3[3] = {0.6245004513516506, 0.4806291366599437, 0.6155950585117604};
+
+__device__ bool seg_ray_cross(const double *p, const double *d, const double *a, const double *b) {
+  const double ex = b[0] - a[0], ey = b[1] - a[1];
+  const double den = d[0] * (-ey) - d[1] * (-ex);
+  if (fabs(den) < 1e-300) return false;
+  const double rx = a[0] - p[0], ry = a[1] - p[1];
+  const double t = (rx * (-ey) - ry * (-ex)) / den;
+  const double s = (d[0] * ry - d[1] * rx) / den;
+  return t > 0.0 && s >= 0.0 && s < 1.0;
+}
+
+// Moller-Trumbore; barycentrics (1-u-v, u, v) at distance t along d.
+__device__ bool tri_ray(const double *p, const double *d, const double *a, const double *b,
+                        const double *c, double &t, double &u, double &v) {
+  const double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+  const double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+  const double pv[3] = {d[1] * e2[2] - d[2] * e2[1], d[2] * e2[0] - d[0] * e2[2],
+                        d[0] * e2[1] - d[1] * e2[0]};
+  const double det = e1[0] * pv[0] + e1[1] * pv[1] + e1[2] * pv[2];
+  if (fabs(det) < 1e-300) return false;
+  const double inv = 1.0 / det;
+  const double tv[3] = {p[0] - a[0], p[1] - a[1], p[2] - a[2]};
+  u = (tv[0] * pv[0] + tv[1] * pv[1] + tv[2] * pv[2]) * inv;
+  const double qv[3] = {tv[1] * e1[2] - tv[2] * e1[1], tv[2] * e1[0] - tv[0] * e1[2],
+                        tv[0] * e1[1] - tv[1] * e1[0]};
+  v = (d[0] * qv[0] + d[1] * qv[1] + d[2] * qv[2]) * inv;
+  t = (e2[0] * qv[0] + e2[1] * qv[1] + e2[2] * qv[2]) * inv;
+  return true;
+}
+
+__device__ bool inside_any(const SurfaceDev &s, const double *p) {
+  // crossing parity per body; a node is solid inside any body
+  for (int b = 0; b < s.nb; ++b) {
+    int cnt = 0;
+    for (int k = 0; k < s.ne; ++k) {
+      if (s.eb[k] != b) continue;
+      if (s.dim == 2) {
+        cnt += seg_ray_cross(p, c_ray2, s.x + 2 * s.e[2 * k], s.x + 2 * s.e[2 * k + 1]);
+      } else {
+        double t, u, v;
+        if (tri_ray(p, c_ray3, s.x + 3 * s.e[3 * k], s.x + 3 * s.e[3 * k + 1],
+                    s.x + 3 * s.e[3 * k + 2], t, u, v) &&
+            t > 0.0 && u >= 0.0 && v >= 0.0 && u + v < 1.0)
+          cnt++;
+      }
+    }
+    if (cnt & 1) return true;
+  }
+  return false;
+}
+
+// Nearest crossing of x_b -> x_b - c over all elements; fills the link.
+__device__ void link_hit(const SurfaceDev &s, const double *xb, int cx, int cy, int cz, Link &L) {
+  const double eps = 1e-9;
+  const double d[3] = {-(double)cx, -(double)cy, -(double)cz};
+  int best = -1;
+  double bs = 2.0, bw[3] = {0, 0, 0};
+  for (int k = 0; k < s.ne; ++k) {
+    if (s.dim == 2) {
+      const double *a = s.x + 2 * s.e[2 * k], *b = s.x + 2 * s.e[2 * k + 1];
+      const double ex = b[0] - a[0], ey = b[1] - a[1];
+      const double den = d[0] * (-ey) - d[1] * (-ex);
+      if (fabs(den) < 1e-300) continue;
+      const double rx = a[0] - xb[0], ry = a[1] - xb[1];
+      const double sp = (rx * (-ey) - ry * (-ex)) / den;
+      const double t = (d[0] * ry - d[1] * rx) / den;
+      if (sp > eps && sp <= 1.0 + eps && t >= -eps && t <= 1.0 + eps && sp < bs) {
+        bs = sp;
+        best = k;
+        const double tt = t < 0 ? 0 : (t > 1 ? 1 : t);
+        bw[0] = 1.0 - tt; bw[1] = tt; bw[2] = 0.0;
+      }
+    } else {
+      double sp, u, v;
+      if (!tri_ray(xb, d, s.x + 3 * s.e[3 * k], s.x + 3 * s.e[3 * k + 1], s.x + 3 * s.e[3 * k + 2],
+                   sp, u, v))
+        continue;
+      if (sp > eps && sp <= 1.0 + eps && u >= -eps && v >= -eps && u + v <= 1.0 + eps && sp < bs) {
+        bs = sp;
+        best = k;
+        bw[0] = 1.0 - u - v; bw[1] = u; bw[2] = v;
+      }
+    }
+  }
+  L.uw[0] = L.uw[1] = L.uw[2] = 0.f;
+  L.v[0] = L.v[1] = L.v[2] = 0;
+  L.vw[0] = L.vw[1] = L.vw[2] = 0.f;
+  if (best < 0) {  // no crossing found: a wall half-way at rest, no force
+    L.q = 0.5f;
+    L.body = -1;
+    return;
+  }
+  L.q = (float)(bs > 1.0 ? 1.0 : bs);
+  L.body = s.eb[best];
+  double uw[3] = {0, 0, 0};
+  for (int m = 0; m < s.dim; ++m) {
+    const int vid = s.e[s.dim * best + m];
+    L.v[m] = vid;
+    L.vw[m] = (float)bw[m];
+    for (int a = 0; a < s.dim; ++a) uw[a] += bw[m] * s.v[s.dim * vid + a];
+  }
+  for (int a = 0; a < 3; ++a) L.uw[a] = (float)uw[a];
+}
+
+// New solid flags inside the band; nodes that turn fluid are listed as fresh.
+__global__ void k_solid_flags(Grid g, Band bd, SurfaceDev s, uint8_t *flags, int64_t *fresh,
+                              int *nfresh, int cap, int track_fresh) {
+  const int bx = bd.x1 - bd.x0, by = bd.y1 - bd.y0, bz = bd.z1 - bd.z0;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)bx * by * bz) return;
+  const int x = bd.x0 + (int)(t % bx), y = bd.y0 + (int)((t / bx) % by),
+            z = bd.z0 + (int)(t / ((long long)bx * by));
+  const double p[3] = {(double)x, (double)y, (double)z};
+  const long long k = sidx(g, x + g.px, y + g.py, z + g.pz);
+  const uint8_t now = inside_any(s, p) ? NODE_SOLID : NODE_FLUID;
+  const uint8_t before = flags[k];
+  if (before == NODE_GHOST) return;
+  if (track_fresh && before == NODE_SOLID && now == NODE_FLUID) {
+    const int slot = atomicAdd(nfresh, 1);
+    if (slot < cap) fresh[slot] = k;
+  }
+  flags[k] = now;
+}
+
+// Immersed boundary nodes of the band and their cut links.
+template <int Q>
+__global__ void k_build_links(Grid g, Band bd, SurfaceDev s, const uint8_t *flags, BNode *bnodes,
+                              int *nbn, int bcap, Link *links, int *nl, int lcap, int *err) {
+  using L = Lat<Q>;
+  const int bx = bd.x1 - bd.x0, by = bd.y1 - bd.y0, bz = bd.z1 - bd.z0;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)bx * by * bz) return;
+  const int x = bd.x0 + (int)(t % bx), y = bd.y0 + (int)((t / bx) % by),
+            z = bd.z0 + (int)(t / ((long long)bx * by));
+  const int X = x + g.px, Y = y + g.py, Z = z + g.pz;
+  const long long k = sidx(g, X, Y, Z);
+  if (flags[k] != NODE_FLUID) return;
+  uint32_t mask = 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int Xs = nbr(X, -L::cx(i), g.NX), Ys = nbr(Y, -L::cy(i), g.NY),
+              Zs = (L::D == 3) ? nbr(Z, -L::cz(i), g.NZ) : Z;
+    if (flags[sidx(g, Xs, Ys, Zs)] == NODE_SOLID) mask |= 1u << i;
+  }
+  if (!mask) return;
+  const int n = __popc(mask);
+  const int l0 = atomicAdd(nl, n);
+  const int slot = atomicAdd(nbn, 1);
+  if (l0 + n > lcap || slot >= bcap) {
+    atomicOr(err, 4);  // capacity overflow
+    return;
+  }
+  bnodes[slot] = BNode{k, l0, n};
+  const double xb[3] = {(double)x, (double)y, (double)z};
+  int m = 0;
+  for (int i = 0; i < Q; ++i) {
+    if (!(mask & (1u << i))) continue;
+    Link lk;
+    lk.i = i;
+    link_hit(s, xb, L::cx(i), L::cy(i), L::cz(i), lk);
+    links[l0 + m++] = lk;
+  }
+}
+
+// Fresh nodes (solid -> fluid): f = feq(mean rho of fluid non-fresh neighbours,
+// velocity of the nearest surface vertex).
+template <int Q, int S>
+__global__ void k_fresh_init(Grid g, typename Store<S>::T *f, const uint8_t *flags,
+                             const int64_t *fresh, const int *nfresh, int cap, SurfaceDev s) {
+  using L = Lat<Q>;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nf = *nfresh < cap ? *nfresh : cap;
+  if (t >= nf) return;
+  const long long k = fresh[t];
+  int X, Y, Z;
+  decompose(g, k, X, Y, Z);
+  double rsum = 0.0;
+  int rn = 0;
+  for (int i = 0; i < Q; ++i) {
+    if (L::cx(i) == 0 && L::cy(i) == 0 && L::cz(i) == 0) continue;
+    const int Xn = step_axis(X, L::cx(i), g.NX, g.px), Yn = step_axis(Y, L::cy(i), g.NY, g.py);
+    const int Zn = (L::D == 3) ? step_axis(Z, L::cz(i), g.NZ, g.pz) : Z;
+    if (Xn < 0 || Yn < 0 || Zn < 0) continue;
+    const long long kn = sidx(g, Xn, Yn, Zn);
+    if (flags[kn] != NODE_FLUID) continue;
+    bool is_fresh = false;
+    for (int m = 0; m < nf; ++m)
+      if (fresh[m] == kn) { is_fresh = true; break; }
+    if (is_fresh) continue;
+    float dr, j[3];
+    dev_moments<Q, S>(g, f, kn, dr, j);
+    rsum += 1.0 + (double)dr;
+    rn++;
+  }
+  const double rho = rn ? rsum / rn : 1.0;
+  const double p[3] = {(double)(X - g.px), (double)(Y - g.py), (double)(Z - g.pz)};
+  int best = 0;
+  double bd = 1e300;
+  for (int v = 0; v < s.nv; ++v) {
+    double d2 = 0;
+    for (int a = 0; a < s.dim; ++a) {
+      const double dd = s.x[s.dim * v + a] - p[a];
+      d2 += dd * dd;
+    }
+    if (d2 < bd) { bd = d2; best = v; }
+  }
+  double u[3] = {0, 0, 0};
+  for (int a = 0; a < s.dim; ++a) u[a] = s.v[s.dim * best + a];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    double p_eq = rho;
+    const int c[3] = {L::cx(i), L::cy(i), L::cz(i)};
+    for (int a = 0; a < L::D; ++a) {
+      const double Sa = sqrt(1.0 + 3.0 * u[a] * u[a]);
+      double fa = w1d(c[a]) * (2.0 - Sa);
+      if (c[a] == 1) fa *= (2.0 * u[a] + Sa) / (1.0 - u[a]);
+      if (c[a] == -1) fa *= (Sa - 2.0 * u[a]) / (1.0 + u[a]);
+      p_eq *= fa;
+    }
+    const double w = weight<L>(i);
+    f[(long long)i * g.N + k] = Store<S>::encode(p_eq - w, w);
+  }
+}
+
+// ---------------------------------------------------------------- Grad fill + force
+template <int Q, int S>
+__global__ void __launch_bounds__(128)
+    k_grad(Grid g, typename Store<S>::T *f, const uint8_t *__restrict__ flags,
+           const BNode *__restrict__ bnodes, const int *__restrict__ nbn, int nfixed, int cap,
+           const Link *__restrict__ links, BoundaryParams bp, double *vforce, double *bforce,
+           int nbodies) {
+  using L = Lat<Q>;
+  using St = Store<S>;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int dyn = nbn ? *nbn : 0;
+  if (dyn > cap - nfixed) dyn = cap - nfixed;
+  const int count = nfixed + dyn;
+  const bool active = t < count;
+  int my_body = -1;
+  double Fd[3] = {0, 0, 0};
+  if (active) {
+    const BNode bn = bnodes[t];
+    const long long k = bn.k;
+    int X, Y, Z;
+    decompose(g, k, X, Y, Z);
+    long long src[Q];
+    int face_of[Q];
+    uint32_t miss = 0;
+    float gk[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int Xs = nbr(X, -L::cx(i), g.NX), Ys = nbr(Y, -L::cy(i), g.NY),
+                Zs = (L::D == 3) ? nbr(Z, -L::cz(i), g.NZ) : Z;
+      src[i] = sidx(g, Xs, Ys, Zs);
+      const uint8_t fl = flags[src[i]];
+      face_of[i] = -1;
+      gk[i] = 0.f;
+      if (fl == NODE_FLUID) {
+        gk[i] = St::load(f + (long long)i * g.N + src[i], (float)weight<L>(i));
+      } else {
+        miss |= 1u << i;
+        if (fl == NODE_GHOST) {
+          if (g.px && (Xs == 0 || Xs == g.NX - 1)) face_of[i] = Xs == 0 ? 0 : 1;
+          else if (g.py && (Ys == 0 || Ys == g.NY - 1)) face_of[i] = Ys == 0 ? 2 : 3;
+          else face_of[i] = Zs == 0 ? 4 : 5;
+        }
+      }
+    }
+    if (miss) {
+      const int nmiss = __popc(miss);
+      int open_face = -1;
+      for (int fc = 0; fc < 6 && open_face < 0; ++fc)
+        for (int i = 0; i < Q; ++i)
+          if (((miss >> i) & 1u) && face_of[i] == fc &&
+              (bp.bc[fc] == BCK_INLET || bp.bc[fc] == BCK_OUTLET ||
+               bp.bc[fc] == BCK_FREESTREAM)) {
+            open_face = fc;
+            break;
+          }
+      float rho_t, ut[3] = {0.f, 0.f, 0.f};
+      bool zero_grad = false;
+      if (open_face >= 0) {
+        const int ax = open_face / 2;
+        int Xn = X, Yn = Y, Zn = Z;
+        const int dir = (open_face % 2 == 0) ? 1 : -1;
+        if (ax == 0) Xn = step_axis(X, dir, g.NX, g.px);
+        if (ax == 1) Yn = step_axis(Y, dir, g.NY, g.py);
+        if (ax == 2) Zn = step_axis(Z, dir, g.NZ, g.pz);
+        long long kn = k;
+        if (Xn >= 0 && Yn >= 0 && Zn >= 0 && flags[sidx(g, Xn, Yn, Zn)] == NODE_FLUID)
+          kn = sidx(g, Xn, Yn, Zn);
+        float u0[3], r0;
+        dev_velocity<Q, S>(g, f, kn, u0, &r0);
+        if (bp.bc[open_face] == BCK_INLET) {
+          float scale = 1.f;
+          if (bp.ramp_steps > 0 && bp.step) {
+            const int st = *bp.step;
+            if (st < bp.ramp_steps) scale = 0.5f * (1.f - cospif((float)st / bp.ramp_steps));
+          }
+          const float *prof = bp.inlet[open_face];
+          const int x = X - g.px, y = Y - g.py, z = Z - g.pz;
+          long long fidx, fn;
+          if (ax == 0) { fidx = (long long)z * g.ny + y; fn = (long long)g.ny * g.nz; }
+          else if (ax == 1) { fidx = (long long)z * g.nx + x; fn = (long long)g.nx * g.nz; }
+          else { fidx = (long long)y * g.nx + x; fn = (long long)g.nx * g.ny; }
+          for (int a = 0; a < L::D; ++a)
+            ut[a] = scale * (prof ? prof[a * fn + fidx] : bp.face_u[open_face][a]);
+          rho_t = r0;
+        } else if (bp.bc[open_face] == BCK_OUTLET) {
+          for (int a = 0; a < 3; ++a) ut[a] = u0[a];
+          rho_t = 1.f;
+        } else {
+          for (int a = 0; a < L::D; ++a) ut[a] = bp.face_u[open_face][a];
+          rho_t = 1.f;
+          zero_grad = true;
+        }
+      } else {
+        float drt = 0.f;
+        int m = 0;
+        for (int i = 0; i < Q; ++i) {
+          if (!((miss >> i) & 1u)) { drt += gk[i]; continue; }
+          float q = 0.5f, uw[3] = {0.f, 0.f, 0.f};
+          if (face_of[i] >= 0) {
+            for (int a = 0; a < 3; ++a) uw[a] = bp.face_u[face_of[i]][a];
+          } else {
+            // immersed links of the node are stored in ascending direction order
+            for (int l = 0; l < bn.nlink; ++l) {
+              const Link &lk = links[bn.link0 + l];
+              if (lk.i == i) {
+                q = lk.q;
+                for (int a = 0; a < 3; ++a) uw[a] = lk.uw[a];
+                break;
+              }
+            }
+          }
+          const float cuw = L::cx(i) * uw[0] + L::cy(i) * uw[1] + L::cz(i) * uw[2];
+          drt += St::load(f + (long long)(Q - 1 - i) * g.N + k, (float)weight<L>(i)) +
+                 6.f * (float)weight<L>(i) * cuw;
+          const int Xn = step_axis(X, L::cx(i), g.NX, g.px), Yn = step_axis(Y, L::cy(i), g.NY, g.py);
+          const int Zn = (L::D == 3) ? step_axis(Z, L::cz(i), g.NZ, g.pz) : Z;
+          float ui[3] = {uw[0], uw[1], uw[2]};
+          if (Xn >= 0 && Yn >= 0 && Zn >= 0 && flags[sidx(g, Xn, Yn, Zn)] == NODE_FLUID) {
+            float un[3];
+            dev_velocity<Q, S>(g, f, sidx(g, Xn, Yn, Zn), un);
+            for (int a = 0; a < 3; ++a) ui[a] = (uw[a] + q * un[a]) / (1.f + q);
+          }
+          for (int a = 0; a < 3; ++a) ut[a] += ui[a];
+          ++m;
+        }
+        for (int a = 0; a < 3; ++a) ut[a] /= (float)nmiss;
+        rho_t = 1.f + drt;
+      }
+      // ---- velocity gradient G[a][b] = d u_a / d x_b (previous step)
+      float G[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+      if (!zero_grad) {
+        float u0[3];
+        dev_velocity<Q, S>(g, f, k, u0);
+        for (int b = 0; b < L::D; ++b) {
+          int P1[3] = {X, Y, Z}, M1[3] = {X, Y, Z}, P2[3] = {X, Y, Z}, M2[3] = {X, Y, Z};
+          const int NS = b == 0 ? g.NX : (b == 1 ? g.NY : g.NZ);
+          const int pad = b == 0 ? g.px : (b == 1 ? g.py : g.pz);
+          const int Sb = b == 0 ? X : (b == 1 ? Y : Z);
+          P1[b] = step_axis(Sb, 1, NS, pad);
+          M1[b] = step_axis(Sb, -1, NS, pad);
+          P2[b] = step_axis(Sb, 2, NS, pad);
+          M2[b] = step_axis(Sb, -2, NS, pad);
+          auto fluid = [&](const int *P) {
+            return P[b] >= 0 && flags[sidx(g, P[0], P[1], P[2])] == NODE_FLUID;
+          };
+          auto vel = [&](const int *P, float (&u)[3]) {
+            dev_velocity<Q, S>(g, f, sidx(g, P[0], P[1], P[2]), u);
+          };
+          const bool fp = fluid(P1), fm = fluid(M1);
+          float a1[3], a2[3];
+          if (fp && fm) {
+            vel(P1, a1);
+            vel(M1, a2);
+            for (int a = 0; a < 3; ++a) G[a][b] = 0.5f * (a1[a] - a2[a]);
+          } else if (fp) {
+            vel(P1, a1);
+            if (fluid(P2)) {
+              vel(P2, a2);
+              for (int a = 0; a < 3; ++a) G[a][b] = 0.5f * (-3.f * u0[a] + 4.f * a1[a] - a2[a]);
+            } else {
+              for (int a = 0; a < 3; ++a) G[a][b] = a1[a] - u0[a];
+            }
+          } else if (fm) {
+            vel(M1, a1);
+            if (fluid(M2)) {
+              vel(M2, a2);
+              for (int a = 0; a < 3; ++a) G[a][b] = 0.5f * (3.f * u0[a] - 4.f * a1[a] + a2[a]);
+            } else {
+              for (int a = 0; a < 3; ++a) G[a][b] = u0[a] - a1[a];
+            }
+          }
+        }
+      }
+      // ---- Grad's approximation, Eq. (grad)
+      float A[3][3];
+      const float cneq = -rho_t / (6.f * bp.beta);
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) A[a][b] = rho_t * ut[a] * ut[b] + cneq * (G[a][b] + G[b][a]);
+      const float trA = A[0][0] + A[1][1] + A[2][2];
+      int l = 0;
+      for (int i = 0; i < Q; ++i) {
+        if (!((miss >> i) & 1u)) continue;
+        const int c[3] = {L::cx(i), L::cy(i), L::cz(i)};
+        float cAc = 0.f;
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) cAc += c[a] * c[b] * A[a][b];
+        const float cu = c[0] * ut[0] + c[1] * ut[1] + c[2] * ut[2];
+        const float W = (float)weight<L>(i);
+        const float gstar = W * ((rho_t - 1.f) + 3.f * rho_t * cu + 4.5f * (cAc - trA / 3.f));
+        St::store(f + (long long)i * g.N + src[i], gstar, (float)(1.0 / weight<L>(i)));
+        if (face_of[i] < 0) {
+          // momentum exchange on the immersed surface, FP64 accumulation
+          while (l < bn.nlink && links[bn.link0 + l].i != i) ++l;
+          if (l < bn.nlink) {
+            const Link &lk = links[bn.link0 + l];
+            if (lk.body >= 0) {
+              const double gop = (double)St::load(f + (long long)(Q - 1 - i) * g.N + k, W);
+              const double fsum = 2.0 * weight<L>(i) + gop + (double)gstar;
+              for (int a = 0; a < L::D; ++a) {
+                const double Fa = -(double)c[a] * fsum;
+                for (int m = 0; m < L::D; ++m)
+                  atomicAdd(&vforce[3 * lk.v[m] + a], (double)lk.vw[m] * Fa);
+                if (lk.body == my_body || my_body < 0) {
+                  my_body = lk.body;
+                  Fd[a] += Fa;
+                } else {
+                  atomicAdd(&bforce[3 * lk.body + a], Fa);
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+  // per-body totals: warp reduction per body id, one atomic per warp and body
+  for (int b = 0; b < nbodies; ++b) {
+    double v[3];
+    for (int a = 0; a < 3; ++a) v[a] = (my_body == b) ? Fd[a] : 0.0;
+    const unsigned any = __ballot_sync(0xffffffffu, my_body == b);
+    if (!any) continue;
+    for (int off = 16; off > 0; off >>= 1)
+      for (int a = 0; a < 3; ++a) v[a] += __shfl_down_sync(0xffffffffu, v[a], off);
+    if ((threadIdx.x & 31) == 0)
+      for (int a = 0; a < 3; ++a) atomicAdd(&bforce[3 * b + a], v[a]);
+  }
+}
+
+__global__ void k_step_counter(int *step) { *step += 1; }
+
+// ---------------------------------------------------------------- launchers
+static inline unsigned nb_(long long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+cudaError_t launch_mark_ghosts(const Grid &g, uint8_t *flags, cudaStream_t s) {
+  k_mark_ghosts<<<nb_(g.N, 256), 256, 0, s>>>(g, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_face_nodes(const Grid &g, BNode *out, int *count, int cap, cudaStream_t s) {
+  const long long n = (long long)g.nx * g.ny * g.nz;
+  k_face_nodes<<<nb_(n, 256), 256, 0, s>>>(g, out, count, cap);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_fresh(int Q, int storage, const Grid &g, void *f, const uint8_t *flags,
+                                const int64_t *fresh, const int *nfresh, int cap,
+                                const SurfaceDev &sd, cudaStream_t s) {
+  KBC_DISPATCH(Q, storage, {
+    k_fresh_init<QQ, SS><<<nb_(cap, 128), 128, 0, s>>>(g, (typename Store<SS>::T *)f, flags, fresh,
+                                                       nfresh, cap, sd);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_geometry(int Q, int storage, const Grid &g, const Band &bd, const SurfaceDev &sd,
+                            uint8_t *flags, void *f, int64_t *fresh, int *nfresh, int fresh_cap,
+                            int track_fresh, BNode *bnodes, int *nbn, int bcap, Link *links,
+                            int *nl, int lcap, int *err, cudaStream_t s) {
+  const long long nb = (long long)(bd.x1 - bd.x0) * (bd.y1 - bd.y0) * (bd.z1 - bd.z0);
+  if (nb <= 0) return cudaSuccess;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(nfresh, 0, sizeof(int), s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(nbn, 0, sizeof(int), s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(nl, 0, sizeof(int), s)) != cudaSuccess) return e;
+  k_solid_flags<<<nb_(nb, 128), 128, 0, s>>>(g, bd, sd, flags, fresh, nfresh, fresh_cap,
+                                              track_fresh);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (track_fresh && (e = launch_fresh(Q, storage, g, f, flags, fresh, nfresh, fresh_cap, sd, s)) !=
+                         cudaSuccess)
+    return e;
+  if (Q == 9)
+    k_build_links<9><<<nb_(nb, 128), 128, 0, s>>>(g, bd, sd, flags, bnodes, nbn, bcap, links, nl,
+                                                   lcap, err);
+  else
+    k_build_links<27><<<nb_(nb, 128), 128, 0, s>>>(g, bd, sd, flags, bnodes, nbn, bcap, links,
+                                                    nl, lcap, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad(int Q, int storage, const Grid &g, void *f, const uint8_t *flags,
+                        const BNode *bnodes, const int *nbn, int nfixed, int cap,
+                        const Link *links, const BoundaryParams &bp, double *vforce,
+                        double *bforce, int nbodies, cudaStream_t s) {
+  if (cap <= 0) return cudaSuccess;
+  KBC_DISPATCH(Q, storage, {
+    k_grad<QQ, SS><<<nb_(cap, 128), 128, 0, s>>>(g, (typename Store<SS>::T *)f, flags, bnodes, nbn,
+                                                 nfixed, cap, links, bp, vforce, bforce, nbodies);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_step_counter(int *step, cudaStream_t s) {
+  k_step_counter<<<1, 1, 0, s>>>(step);
+  return cudaGetLastError();
+}
+
+}  // namespace kbc

@@ -163,8 +163,26 @@ __device__ __forceinline__ float collide(float (&g)[L::Q], float beta, bool bgk)
   // <.|.> carries a common factor rho that cancels in the ratio
   if (!bgk && hh > 1e-30f) gamma = ib - (2.f - ib) * __fdividef(sh, hh);
 
+  // ---- conservation of the FP32 update: df carries no mass or momentum in
+  // exact arithmetic; its rounding residue (dm, dj) would otherwise leak into
+  // the conserved moments every step, so it is removed along W_i (1, 3 c_i).
+  float qm = 0.f, qx = 0.f, qyp = 0.f, qym = 0.f, qzp = 0.f, qzm = 0.f;
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    const int cy = r % 3 - 1, cz = (L::D == 3) ? r / 3 - 1 : 0;
+    const float m = df[3 * r] + df[3 * r + 1] + df[3 * r + 2];
+    qm += m;
+    qx += df[3 * r + 2] - df[3 * r];
+    if (cy > 0) qyp += m;
+    if (cy < 0) qym += m;
+    if (cz > 0) qzp += m;
+    if (cz < 0) qzm += m;
+  }
+
   // ---- relaxation f' = f - beta (2 ds + gamma dh) = f - beta (gamma df + (2 - gamma) ds)
   const float bg = beta * gamma, b2g = beta * (2.f - gamma);
+  const float A = bg * qm, Bx = 3.f * bg * qx, By = 3.f * bg * (qyp - qym),
+              Bz = 3.f * bg * (qzp - qzm);
   float bs[6];
 #pragma unroll
   for (int k = 0; k < 6; ++k) bs[k] = b2g * sv[k];
@@ -179,7 +197,11 @@ __device__ __forceinline__ float collide(float (&g)[L::Q], float beta, bool bgk)
       else if (cx && cz) sds = cx * cz * bs[4];
       else sds = cy * cz * bs[5];
     }
-    g[i] = g[i] - fmaf(bg, df[i], sds);
+    float t = A;
+    if (cy) t += cy * By;
+    if (cz) t += cz * Bz;
+    if (cx) t += cx * Bx;
+    g[i] = g[i] - fmaf(bg, df[i], fmaf(-(float)weight<L>(i), t, sds));
   }
   return rho;
 }

@@ -241,19 +241,7 @@ static cudaError_t sweep_t(const Grid &g, const void *fin, void *fout, const uin
   return cudaGetLastError();
 }
 
-#define KBC_DISPATCH(Q, storage, ...)                                               \
-  do {                                                                              \
-    if (Q == 9) {                                                                   \
-      if (storage == STORE_F32) { constexpr int QQ = 9, SS = STORE_F32; __VA_ARGS__; }     \
-      if (storage == STORE_F16) { constexpr int QQ = 9, SS = STORE_F16; __VA_ARGS__; }     \
-      if (storage == STORE_BF16) { constexpr int QQ = 9, SS = STORE_BF16; __VA_ARGS__; }   \
-    } else if (Q == 27) {                                                           \
-      if (storage == STORE_F32) { constexpr int QQ = 27, SS = STORE_F32; __VA_ARGS__; }    \
-      if (storage == STORE_F16) { constexpr int QQ = 27, SS = STORE_F16; __VA_ARGS__; }    \
-      if (storage == STORE_BF16) { constexpr int QQ = 27, SS = STORE_BF16; __VA_ARGS__; }  \
-    }                                                                               \
-    return cudaErrorInvalidValue;                                                   \
-  } while (0)
+
 
 cudaError_t launch_sweep(int Q, int storage, const Grid &g, const void *fin, void *fout,
                          const uint8_t *flags, float beta, int bgk, int *err, cudaStream_t s,

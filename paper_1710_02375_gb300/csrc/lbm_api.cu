@@ -4,7 +4,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+#include <cmath>
 #include <new>
+#include <vector>
 
 #include "../../include/kbc_lbm.h"
 #include "lbm_internal.h"
@@ -18,8 +21,13 @@ constexpr size_t kStageBytes = 16u << 20;  // host<->device staging chunk
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
+constexpr int kMaxBodies = 16;
+
 struct Layout {
-  size_t f[2], flags, err, stage, total;
+  size_t f[2], flags, err, stage;
+  size_t sx, sv, se, seb, links, bnodes, fresh, counters, vforce, bforce, inlet[6];
+  int nface, bcap, inlet_n[6];
+  size_t total;
 };
 
 int pop_bytes(int storage) { return storage == LBM_STORE_F32 ? 4 : 2; }
@@ -48,6 +56,35 @@ Layout make_layout(const lbm_config &c) {
   L.flags = off; off += align_up((size_t)g.N);
   L.err = off; off += kAlign;
   L.stage = off; off += kStageBytes;
+  // immersed surface and boundary lists
+  const int nv = c.max_vertices, ne = c.max_elements, nl = c.max_links;
+  L.sx = off; off += align_up(sizeof(double) * 3 * (size_t)std::max(nv, 1));
+  L.sv = off; off += align_up(sizeof(double) * 3 * (size_t)std::max(nv, 1));
+  L.se = off; off += align_up(sizeof(int32_t) * 3 * (size_t)std::max(ne, 1));
+  L.seb = off; off += align_up(sizeof(int32_t) * (size_t)std::max(ne, 1));
+  L.links = off; off += align_up(sizeof(Link) * (size_t)std::max(nl, 1));
+  long long nface = 0;
+  const long long n[3] = {c.nx, c.ny, c.nz};
+  const int pads[3] = {g.px, g.py, g.pz};
+  for (int a = 0; a < 3; ++a)
+    if (pads[a]) nface += 2 * (n[0] * n[1] * n[2] / n[a]);
+  L.nface = (int)nface;
+  L.bcap = L.nface + nl;
+  L.bnodes = off; off += align_up(sizeof(BNode) * (size_t)std::max(L.bcap, 1));
+  L.fresh = off; off += align_up(sizeof(int64_t) * (size_t)std::max(nl, 1));
+  L.counters = off; off += kAlign;  // nbn, nl, nfresh, step, nface
+  L.vforce = off; off += align_up(sizeof(double) * 3 * (size_t)std::max(nv, 1));
+  L.bforce = off; off += align_up(sizeof(double) * 3 * kMaxBodies);
+  for (int fc = 0; fc < 6; ++fc) {
+    L.inlet_n[fc] = 0;
+    L.inlet[fc] = 0;
+    if (c.bc[fc] == LBM_BC_INLET) {
+      const int a = fc / 2;
+      L.inlet_n[fc] = (int)(n[0] * n[1] * n[2] / n[a]);
+      L.inlet[fc] = off;
+      off += align_up(sizeof(float) * 3 * (size_t)L.inlet_n[fc]);
+    }
+  }
   L.total = off;
   return L;
 }
@@ -75,6 +112,11 @@ const char *validate(const lbm_config *c) {
   long long n = (long long)c->nx * c->ny * c->nz;
   if (n > (1LL << 31)) return "lattice too large";
   if (c->max_links < 0 || c->max_vertices < 0 || c->max_elements < 0) return "negative capacity";
+  if (c->inlet_ramp_steps < 0) return "negative inlet ramp";
+  const int nz_ax = c->lattice == LBM_D2Q9 ? 2 : 3;
+  const int nn[3] = {c->nx, c->ny, c->nz};
+  for (int a = 0; a < nz_ax; ++a)
+    if (c->bc[2 * a] != LBM_BC_PERIODIC && nn[a] < 3) return "non-periodic axes need >= 3 nodes";
   return nullptr;
 }
 
@@ -96,6 +138,12 @@ struct lbm_ctx {
   int *err = nullptr;
   char *stage = nullptr;
   int sweep_variant = SWEEP_AUTO;
+  // boundary state
+  int nface = 0;             // face boundary nodes (fixed list head)
+  int nbodies = 0, nv = 0, ne = 0;
+  Band band{0, 0, 0, 0, 0, 0};
+  int *counters = nullptr;   // [0] immersed nodes, [1] links, [2] fresh, [3] step
+  BoundaryParams bp;
   bool poisoned = false;
   char msg[512] = {0};
 };
@@ -195,6 +243,29 @@ lbm_status lbm_create(const lbm_config *cfg, void *workspace, size_t workspace_b
   CK(cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream));
   CK(cudaMemsetAsync(ctx->flags, NODE_FLUID, (size_t)ctx->g.N, ctx->stream));
   ctx->has_solid = false;
+  ctx->counters = (int *)(ctx->ws + ctx->lay.counters);
+  CK(cudaMemsetAsync(ctx->counters, 0, kAlign, ctx->stream));
+  // boundary parameters
+  for (int fc = 0; fc < 6; ++fc) {
+    ctx->bp.bc[fc] = cfg->bc[fc];
+    for (int a = 0; a < 3; ++a) ctx->bp.face_u[fc][a] = (float)cfg->face_velocity[fc][a];
+    ctx->bp.inlet[fc] = nullptr;
+  }
+  ctx->bp.beta = (float)cfg->beta;
+  ctx->bp.ramp_steps = cfg->inlet_ramp_steps;
+  ctx->bp.step = ctx->counters + 3;
+  if (ctx->g.px || ctx->g.py || ctx->g.pz) {
+    // ghost layer and the fixed list of face boundary nodes
+    CK(launch_mark_ghosts(ctx->g, ctx->flags, ctx->stream));
+    int *cnt = ctx->counters + 4;
+    CK(launch_face_nodes(ctx->g, (BNode *)(ctx->ws + ctx->lay.bnodes), cnt, ctx->lay.nface,
+                         ctx->stream));
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, cnt, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->nface = std::min(h, ctx->lay.nface);
+    ctx->has_solid = true;  // ghosts are skipped by the sweep
+  }
   *out = ctx;
   return LBM_OK;
 }
@@ -297,12 +368,180 @@ lbm_status lbm_step(lbm_ctx *ctx, int n) {
   if (n < 0) return fail(ctx, LBM_EINVAL, "lbm_step: n < 0");
   const float beta = (float)ctx->cfg.beta;
   const int bgk = ctx->cfg.collision == LBM_COLLIDE_BGK;
+  const bool bnd = ctx->nface > 0 || ctx->nbodies > 0;
+  const int cap = ctx->nface + (ctx->nbodies > 0 ? ctx->cfg.max_links : 0);
   for (int t = 0; t < n; ++t) {
+    if (bnd) {
+      if (ctx->nbodies > 0) {
+        CK(cudaMemsetAsync(ctx->ws + ctx->lay.vforce, 0, sizeof(double) * 3 * (size_t)ctx->nv,
+                           ctx->stream));
+        CK(cudaMemsetAsync(ctx->ws + ctx->lay.bforce, 0, sizeof(double) * 3 * kMaxBodies,
+                           ctx->stream));
+      }
+      CK(launch_grad(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur], ctx->flags,
+                     (const BNode *)(ctx->ws + ctx->lay.bnodes),
+                     ctx->nbodies > 0 ? ctx->counters : nullptr, ctx->nface, cap,
+                     (const Link *)(ctx->ws + ctx->lay.links), ctx->bp,
+                     (double *)(ctx->ws + ctx->lay.vforce), (double *)(ctx->ws + ctx->lay.bforce),
+                     ctx->nbodies, ctx->stream));
+      if (ctx->bp.ramp_steps > 0) CK(launch_step_counter(ctx->counters + 3, ctx->stream));
+    }
     CK(launch_sweep(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur], ctx->f[1 - ctx->cur],
-                    ctx->has_solid || ctx->g.px || ctx->g.py || ctx->g.pz ? ctx->flags : nullptr,
-                    beta, bgk, ctx->err, ctx->stream, ctx->sweep_variant));
+                    ctx->has_solid ? ctx->flags : nullptr, beta, bgk, ctx->err, ctx->stream,
+                    ctx->sweep_variant));
     ctx->cur = 1 - ctx->cur;
   }
+  return LBM_OK;
+}
+
+static lbm_status copy_in(lbm_ctx *ctx, void *dst, const void *src, size_t bytes) {
+  // cudaMemcpyDefault infers host or device from the unified address space
+  CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, ctx->stream));
+  return LBM_OK;
+}
+
+static SurfaceDev surface_dev(lbm_ctx *ctx) {
+  SurfaceDev s;
+  s.dim = ctx->Q == 9 ? 2 : 3;
+  s.nv = ctx->nv;
+  s.ne = ctx->ne;
+  s.nb = ctx->nbodies;
+  s.x = (const double *)(ctx->ws + ctx->lay.sx);
+  s.v = (const double *)(ctx->ws + ctx->lay.sv);
+  s.e = (const int32_t *)(ctx->ws + ctx->lay.se);
+  s.eb = (const int32_t *)(ctx->ws + ctx->lay.seb);
+  return s;
+}
+
+static lbm_status run_geometry(lbm_ctx *ctx, int track_fresh) {
+  CK(launch_geometry(ctx->Q, ctx->cfg.storage, ctx->g, ctx->band, surface_dev(ctx), ctx->flags,
+                     ctx->f[ctx->cur], (int64_t *)(ctx->ws + ctx->lay.fresh), ctx->counters + 2,
+                     ctx->cfg.max_links, track_fresh,
+                     (BNode *)(ctx->ws + ctx->lay.bnodes) + ctx->nface, ctx->counters,
+                     ctx->cfg.max_links, (Link *)(ctx->ws + ctx->lay.links), ctx->counters + 1,
+                     ctx->cfg.max_links, ctx->err, ctx->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_set_geometry(lbm_ctx *ctx, int nbodies, const double *verts, int nv,
+                            const int32_t *elems, int ne, const int32_t *elem_body,
+                            const double *vert_vel, double band_margin) {
+  GUARD();
+  const int dim = ctx->Q == 9 ? 2 : 3;
+  if (nbodies < 1 || nbodies > kMaxBodies || nv < dim || ne < 1 || !verts || !elems ||
+      !elem_body || !(band_margin >= 0.0))
+    return fail(ctx, LBM_EINVAL, "lbm_set_geometry: bad arguments");
+  if (nv > ctx->cfg.max_vertices || ne > ctx->cfg.max_elements)
+    return fail(ctx, LBM_ECAPACITY, "lbm_set_geometry: %d vertices / %d elements exceed capacity",
+                nv, ne);
+  // host copies for validation and the band
+  std::vector<double> hx((size_t)nv * dim);
+  std::vector<int32_t> he((size_t)ne * dim), hb((size_t)ne);
+  CK(cudaMemcpy(hx.data(), verts, hx.size() * sizeof(double), cudaMemcpyDefault));
+  CK(cudaMemcpy(he.data(), elems, he.size() * sizeof(int32_t), cudaMemcpyDefault));
+  CK(cudaMemcpy(hb.data(), elem_body, hb.size() * sizeof(int32_t), cudaMemcpyDefault));
+  for (int32_t v : he)
+    if (v < 0 || v >= nv) return fail(ctx, LBM_EINVAL, "lbm_set_geometry: element vertex id out of range");
+  for (int32_t b : hb)
+    if (b < 0 || b >= nbodies) return fail(ctx, LBM_EINVAL, "lbm_set_geometry: body id out of range");
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int v = 0; v < nv; ++v)
+    for (int a = 0; a < dim; ++a) {
+      const double x = hx[(size_t)v * dim + a];
+      if (!std::isfinite(x)) return fail(ctx, LBM_EINVAL, "lbm_set_geometry: non-finite vertex");
+      lo[a] = std::min(lo[a], x);
+      hi[a] = std::max(hi[a], x);
+    }
+  const int n[3] = {ctx->g.nx, ctx->g.ny, ctx->g.nz};
+  const int pads[3] = {ctx->g.px, ctx->g.py, ctx->g.pz};
+  int b0[3] = {0, 0, 0}, b1[3] = {1, 1, 1};
+  for (int a = 0; a < dim; ++a) {
+    b0[a] = (int)std::floor(lo[a] - band_margin) - 2;
+    b1[a] = (int)std::ceil(hi[a] + band_margin) + 3;
+    if (pads[a] && (b0[a] < 2 || b1[a] > n[a] - 2))
+      return fail(ctx, LBM_EINVAL,
+                  "lbm_set_geometry: bodies (plus margin) must stay 2 nodes inside non-periodic faces");
+    b0[a] = std::max(b0[a], 0);
+    b1[a] = std::min(b1[a], n[a]);
+  }
+  if (dim == 2) { b0[2] = 0; b1[2] = 1; }
+  ctx->band = Band{b0[0], b1[0], b0[1], b1[1], b0[2], b1[2]};
+  ctx->nbodies = nbodies;
+  ctx->nv = nv;
+  ctx->ne = ne;
+  lbm_status st;
+  if ((st = copy_in(ctx, ctx->ws + ctx->lay.sx, verts, sizeof(double) * dim * nv)) != LBM_OK) return st;
+  if (vert_vel) {
+    if ((st = copy_in(ctx, ctx->ws + ctx->lay.sv, vert_vel, sizeof(double) * dim * nv)) != LBM_OK) return st;
+  } else {
+    CK(cudaMemsetAsync(ctx->ws + ctx->lay.sv, 0, sizeof(double) * dim * nv, ctx->stream));
+  }
+  if ((st = copy_in(ctx, ctx->ws + ctx->lay.se, elems, sizeof(int32_t) * dim * ne)) != LBM_OK) return st;
+  if ((st = copy_in(ctx, ctx->ws + ctx->lay.seb, elem_body, sizeof(int32_t) * ne)) != LBM_OK) return st;
+  // every previously solid node of the band is reset to fluid, then re-marked
+  if ((st = run_geometry(ctx, 0)) != LBM_OK) return st;
+  ctx->has_solid = true;
+  int h[3];
+  CK(cudaMemcpyAsync(h, ctx->counters, 3 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (h[0] > ctx->cfg.max_links || h[1] > ctx->cfg.max_links)
+    return fail(ctx, LBM_ECAPACITY, "lbm_set_geometry: %d boundary nodes / %d links exceed max_links %d",
+                h[0], h[1], ctx->cfg.max_links);
+  return LBM_OK;
+}
+
+lbm_status lbm_update_surface(lbm_ctx *ctx, const double *verts, const double *vert_vel) {
+  GUARD();
+  if (ctx->nbodies == 0) return fail(ctx, LBM_ESTATE, "lbm_update_surface: no geometry set");
+  if (!verts) return fail(ctx, LBM_EINVAL, "lbm_update_surface: NULL vertices");
+  const int dim = ctx->Q == 9 ? 2 : 3;
+  lbm_status st;
+  if ((st = copy_in(ctx, ctx->ws + ctx->lay.sx, verts, sizeof(double) * dim * ctx->nv)) != LBM_OK) return st;
+  if (vert_vel &&
+      (st = copy_in(ctx, ctx->ws + ctx->lay.sv, vert_vel, sizeof(double) * dim * ctx->nv)) != LBM_OK)
+    return st;
+  return run_geometry(ctx, 1);
+}
+
+lbm_status lbm_get_interface_force(lbm_ctx *ctx, double *vert_force, double *body_force) {
+  GUARD();
+  if (ctx->nbodies == 0) return fail(ctx, LBM_ESTATE, "lbm_get_interface_force: no geometry set");
+  if (vert_force)
+    CK(cudaMemcpyAsync(vert_force, ctx->ws + ctx->lay.vforce, sizeof(double) * 3 * ctx->nv,
+                       cudaMemcpyDefault, ctx->stream));
+  if (body_force)
+    CK(cudaMemcpyAsync(body_force, ctx->ws + ctx->lay.bforce, sizeof(double) * 3 * ctx->nbodies,
+                       cudaMemcpyDefault, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_set_inlet_profile(lbm_ctx *ctx, int face, const double *u) {
+  GUARD();
+  if (face < 0 || face > 5 || ctx->cfg.bc[face] != LBM_BC_INLET || !u)
+    return fail(ctx, LBM_EINVAL, "lbm_set_inlet_profile: face %d is not an inlet", face);
+  const size_t n = (size_t)ctx->lay.inlet_n[face];
+  std::vector<double> h(3 * n);
+  CK(cudaMemcpy(h.data(), u, sizeof(double) * 3 * n, cudaMemcpyDefault));
+  std::vector<float> hf(3 * n);
+  for (size_t k = 0; k < 3 * n; ++k) hf[k] = (float)h[k];
+  float *dst = (float *)(ctx->ws + ctx->lay.inlet[face]);
+  CK(cudaMemcpyAsync(dst, hf.data(), sizeof(float) * 3 * n, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->bp.inlet[face] = dst;
+  return LBM_OK;
+}
+
+lbm_status lbm_get_boundary_info(lbm_ctx *ctx, int *info) {
+  GUARD();
+  if (!info) return fail(ctx, LBM_EINVAL, "lbm_get_boundary_info: NULL");
+  int h[4] = {0, 0, 0, 0};
+  CK(cudaMemcpyAsync(h, ctx->counters, 4 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  info[0] = ctx->nface;
+  info[1] = ctx->nbodies ? h[0] : 0;
+  info[2] = ctx->nbodies ? h[1] : 0;
+  info[3] = h[3];
   return LBM_OK;
 }
 
@@ -322,6 +561,7 @@ lbm_status lbm_check(lbm_ctx *ctx) {
   if (h) {
     CK(cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream));
     if (h & 2) return fail(ctx, LBM_ETIMEOUT, "a bounded device wait gave up (flags 0x%x)", h);
+    if (h & 4) return fail(ctx, LBM_ECAPACITY, "cut-link list overflowed max_links (flags 0x%x)", h);
     return fail(ctx, LBM_EUNSTABLE, "non-finite or non-positive density met (flags 0x%x)", h);
   }
   return LBM_OK;

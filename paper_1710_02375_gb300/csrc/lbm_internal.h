@@ -3,9 +3,26 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "boundary.cuh"
 #include "kbc_common.cuh"
 
 namespace kbc {
+
+// Dispatch a runtime (lattice, storage) pair to compile-time constants QQ, SS;
+// every branch must return.
+#define KBC_DISPATCH(Q, storage, ...)                                               \
+  do {                                                                              \
+    if (Q == 9) {                                                                   \
+      if (storage == STORE_F32) { constexpr int QQ = 9, SS = STORE_F32; __VA_ARGS__; }     \
+      if (storage == STORE_F16) { constexpr int QQ = 9, SS = STORE_F16; __VA_ARGS__; }     \
+      if (storage == STORE_BF16) { constexpr int QQ = 9, SS = STORE_BF16; __VA_ARGS__; }   \
+    } else if (Q == 27) {                                                           \
+      if (storage == STORE_F32) { constexpr int QQ = 27, SS = STORE_F32; __VA_ARGS__; }    \
+      if (storage == STORE_F16) { constexpr int QQ = 27, SS = STORE_F16; __VA_ARGS__; }    \
+      if (storage == STORE_BF16) { constexpr int QQ = 27, SS = STORE_BF16; __VA_ARGS__; }  \
+    }                                                                               \
+    return cudaErrorInvalidValue;                                                   \
+  } while (0)
 
 // Fused pull-stream + KBC collision over all interior nodes (solid nodes are
 // skipped when flags != nullptr).  fin / fout: population buffers in storage
@@ -35,5 +52,25 @@ cudaError_t launch_get_pop(int Q, int storage, const Grid &g, int i, double *dst
 cudaError_t launch_macros(int Q, int storage, const Grid &g, const void *f, const uint8_t *flags,
                           double *rho, double *u, long long ustride, long long begin,
                           long long count, cudaStream_t s);
+
+}  // namespace kbc
+
+namespace kbc {
+
+cudaError_t launch_mark_ghosts(const Grid &g, uint8_t *flags, cudaStream_t s);
+cudaError_t launch_face_nodes(const Grid &g, BNode *out, int *count, int cap, cudaStream_t s);
+// Solid flags, fresh-node initialisation (track_fresh) and the immersed
+// boundary-node / cut-link lists of the band.
+cudaError_t launch_geometry(int Q, int storage, const Grid &g, const Band &bd, const SurfaceDev &sd,
+                            uint8_t *flags, void *f, int64_t *fresh, int *nfresh, int fresh_cap,
+                            int track_fresh, BNode *bnodes, int *nbn, int bcap, Link *links,
+                            int *nl, int lcap, int *err, cudaStream_t s);
+// Grad fill of the missing populations of nfixed face nodes followed by
+// min(*nbn, cap - nfixed) immersed boundary nodes, and the force gather.
+cudaError_t launch_grad(int Q, int storage, const Grid &g, void *f, const uint8_t *flags,
+                        const BNode *bnodes, const int *nbn, int nfixed, int cap,
+                        const Link *links, const BoundaryParams &bp, double *vforce,
+                        double *bforce, int nbodies, cudaStream_t s);
+cudaError_t launch_step_counter(int *step, cudaStream_t s);
 
 }  // namespace kbc

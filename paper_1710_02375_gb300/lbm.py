@@ -39,6 +39,7 @@ class lbm_config(ctypes.Structure):
         ("max_links", ctypes.c_int),
         ("max_vertices", ctypes.c_int),
         ("max_elements", ctypes.c_int),
+        ("inlet_ramp_steps", ctypes.c_int),
         ("stream", ctypes.c_void_p),
     ]
 
@@ -67,6 +68,14 @@ def load():
     L.lbm_step.argtypes = [vp, i32]
     L.lbm_get_macros.argtypes = [vp, vp, vp]
     L.lbm_check.argtypes = [vp]
+    L.lbm_set_inlet_profile.argtypes = [vp, i32, vp]
+    L.lbm_set_geometry.argtypes = [vp, i32, vp, i32, vp, i32, vp, vp, ctypes.c_double]
+    L.lbm_update_surface.argtypes = [vp, vp, vp]
+    L.lbm_get_interface_force.argtypes = [vp, vp, vp]
+    L.lbm_get_boundary_info.argtypes = [vp, vp]
+    for name in ("lbm_set_inlet_profile", "lbm_set_geometry", "lbm_update_surface",
+                 "lbm_get_interface_force", "lbm_get_boundary_info"):
+        getattr(L, name).restype = ctypes.c_int
     L.lbm_set_sweep_variant.argtypes = [vp, i32]
     L.lbm_set_sweep_variant.restype = ctypes.c_int
     L.lbm_stream.argtypes = [vp]
@@ -106,7 +115,7 @@ def _chk(ctx, st):
 
 def make_config(lattice, nx, ny, nz, beta, storage=LBM_STORE_F32, collision=LBM_COLLIDE_KBC,
                 bc=(0, 0, 0, 0, 0, 0), face_velocity=None, max_links=0, max_vertices=0,
-                max_elements=0, stream=None) -> lbm_config:
+                max_elements=0, stream=None, inlet_ramp_steps=0) -> lbm_config:
     c = lbm_config()
     c.lattice, c.nx, c.ny, c.nz = lattice, nx, ny, nz
     c.beta, c.storage, c.collision = beta, storage, collision
@@ -116,6 +125,7 @@ def make_config(lattice, nx, ny, nz, beta, storage=LBM_STORE_F32, collision=LBM_
             for a in range(3):
                 c.face_velocity[k][a] = face_velocity[k][a]
     c.max_links, c.max_vertices, c.max_elements = max_links, max_vertices, max_elements
+    c.inlet_ramp_steps = inlet_ramp_steps
     c.stream = stream
     return c
 
@@ -163,6 +173,27 @@ def lbm_set_sweep_variant(ctx, variant: int):
     _chk(ctx, load().lbm_set_sweep_variant(ctx, int(variant)))
 
 
+def lbm_set_inlet_profile(ctx, face, u):
+    _chk(ctx, load().lbm_set_inlet_profile(ctx, int(face), _ptr(u)))
+
+
+def lbm_set_geometry(ctx, nbodies, verts, nv, elems, ne, elem_body, vert_vel, band_margin):
+    _chk(ctx, load().lbm_set_geometry(ctx, int(nbodies), _ptr(verts), int(nv), _ptr(elems), int(ne),
+                                      _ptr(elem_body), _ptr(vert_vel), float(band_margin)))
+
+
+def lbm_update_surface(ctx, verts, vert_vel):
+    _chk(ctx, load().lbm_update_surface(ctx, _ptr(verts), _ptr(vert_vel)))
+
+
+def lbm_get_interface_force(ctx, vert_force, body_force):
+    _chk(ctx, load().lbm_get_interface_force(ctx, _ptr(vert_force), _ptr(body_force)))
+
+
+def lbm_get_boundary_info(ctx, info):
+    _chk(ctx, load().lbm_get_boundary_info(ctx, _ptr(info)))
+
+
 def lbm_check(ctx):
     _chk(ctx, load().lbm_check(ctx))
 
@@ -188,7 +219,7 @@ class Lattice:
 
     def __init__(self, lattice, nx, ny, nz, beta, storage=LBM_STORE_F32, collision=LBM_COLLIDE_KBC,
                  bc=(0, 0, 0, 0, 0, 0), face_velocity=None, max_links=0, max_vertices=0,
-                 max_elements=0, stream=None, device="cuda"):
+                 max_elements=0, stream=None, device="cuda", inlet_ramp_steps=0):
         import torch
 
         self.torch = torch
@@ -199,7 +230,7 @@ class Lattice:
         self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
         self.cfg = make_config(lattice, nx, ny, nz, beta, storage, collision, bc, face_velocity,
                                max_links, max_vertices, max_elements,
-                               stream=self.stream.cuda_stream)
+                               stream=self.stream.cuda_stream, inlet_ramp_steps=inlet_ramp_steps)
         nbytes = lbm_workspace_size(self.cfg)
         # 256-byte alignment: torch's caching allocator returns 512-byte aligned blocks
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
@@ -236,6 +267,34 @@ class Lattice:
 
     def check(self):
         lbm_check(self.ctx)
+
+    def set_inlet_profile(self, face, u):
+        lbm_set_inlet_profile(self.ctx, face, np.ascontiguousarray(u, dtype=np.float64))
+
+    def set_geometry(self, verts, elems, elem_body, nbodies=None, vel=None, band_margin=0.0):
+        verts = np.ascontiguousarray(verts, dtype=np.float64)
+        elems = np.ascontiguousarray(elems, dtype=np.int32)
+        elem_body = np.ascontiguousarray(elem_body, dtype=np.int32)
+        vel = None if vel is None else np.ascontiguousarray(vel, dtype=np.float64)
+        nb = int(nbodies if nbodies is not None else elem_body.max() + 1)
+        self._nv, self._nb = verts.shape[0], nb
+        lbm_set_geometry(self.ctx, nb, verts, verts.shape[0], elems, elems.shape[0], elem_body, vel,
+                         band_margin)
+
+    def update_surface(self, verts, vel=None):
+        lbm_update_surface(self.ctx, np.ascontiguousarray(verts, dtype=np.float64),
+                           None if vel is None else np.ascontiguousarray(vel, dtype=np.float64))
+
+    def interface_force(self):
+        vf = np.zeros((self._nv, 3))
+        bf = np.zeros((self._nb, 3))
+        lbm_get_interface_force(self.ctx, vf, bf)
+        return vf, bf
+
+    def boundary_info(self):
+        info = np.zeros(4, dtype=np.int32)
+        lbm_get_boundary_info(self.ctx, info)
+        return info
 
     def close(self):
         if getattr(self, "ctx", None):

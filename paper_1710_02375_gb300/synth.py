@@ -117,3 +117,44 @@ def icosphere(center, r: float, level: int = 2, rotate: float = 0.3):
     R = np.eye(3) + np.sin(rotate) * K + (1 - np.cos(rotate)) * K @ K
     X = X @ R.T
     return np.asarray(center, dtype=np.float64) + r * X, np.array(faces, dtype=np.int32)
+
+
+def parabolic_profile(ny: int, u_max: float, noise: float = 0.0, seed: int = 0):
+    """Inlet profile u[3, ny] (one x-face column, nz = 1) between walls half a
+    cell outside the faces: u_x = 4 u_max (y + 1/2)(H - y - 1/2)/H^2, H = ny,
+    times a static multiplicative noise (1 + noise * N(0,1)) drawn once."""
+    y = np.arange(ny)
+    H = float(ny)
+    u = np.zeros((3, ny))
+    u[0] = 4 * u_max * (y + 0.5) * (H - y - 0.5) / H ** 2
+    if noise:
+        rng = np.random.default_rng(seed)
+        u[0] *= 1.0 + noise * rng.standard_normal(ny)
+    return u
+
+
+def cylinder_flag_2d(cx=20.0, cy=20.0, d=10.0, flag_len=35.0, flag_h=2.0, n_cyl=64,
+                     n_beam=20, with_flag=True):
+    """Turek-type rigid cylinder plus an attached flag as closed polygons.
+
+    Body 0: cylinder of diameter d (n_cyl segments).  Body 1: the flag, a
+    rectangle of length flag_len and thickness flag_h whose centre line runs
+    from the cylinder's downstream side x0 = cx + sqrt(r^2 - (h/2)^2) to
+    cx + r + flag_len at y = cy, with n_beam + 1 vertices on each long edge
+    (one per beam node).  Returns (x[nv,2], e[ne,2], body[ne], beam_x[n_beam+1])."""
+    r = d / 2
+    xc, ec = circle_polygon(cx, cy, r, n_cyl)
+    if not with_flag:
+        return xc, ec, np.zeros(len(ec), np.int32), None
+    x0 = cx + np.sqrt(r * r - (flag_h / 2) ** 2)
+    x1 = cx + r + flag_len
+    bx = np.linspace(x0, x1, n_beam + 1)
+    bot = np.stack([bx, np.full_like(bx, cy - flag_h / 2)], axis=1)
+    top = np.stack([bx[::-1], np.full_like(bx, cy + flag_h / 2)], axis=1)
+    xf = np.concatenate([bot, top])
+    nf = len(xf)
+    ef = np.stack([np.arange(nf), (np.arange(nf) + 1) % nf], axis=1).astype(np.int32)
+    x = np.concatenate([xc, xf])
+    e = np.concatenate([ec, ef + len(xc)])
+    body = np.array([0] * len(ec) + [1] * len(ef), dtype=np.int32)
+    return x, e, body, bx
