@@ -251,8 +251,14 @@ __global__ void k_build_links(Grid g, Band bd, SurfaceDev s, const uint8_t *flag
   const int n = __popc(mask);
   const int l0 = atomicAdd(nl, n);
   const int slot = atomicAdd(nbn, 1);
-  if (l0 + n > lcap || slot >= bcap) {
-    atomicOr(err, 4);  // capacity overflow
+  if (slot >= bcap) {
+    atomicOr(err, 4);  // capacity overflow: the node is left out
+    return;
+  }
+  if (l0 + n > lcap) {
+    // no room for its links: keep the node (walls half-way at rest, no force)
+    atomicOr(err, 4);
+    bnodes[slot] = BNode{k, -1, 0};
     return;
   }
   bnodes[slot] = BNode{k, l0, n};
