@@ -18,7 +18,7 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SOURCES = ["kbc_oracle.c", "kbc_oracle_bc.c"]
+_SOURCES = ["kbc_oracle.c", "kbc_oracle_bc.c", "fem_oracle.c"]
 _LIB_PATH = os.path.join(_HERE, "libkbc_oracle.so")
 _lib = None
 
@@ -63,6 +63,12 @@ def _declare(L):
     L.or_step_bc.argtypes = [c_int, c_int, c_int, c_int, c_double, c_int, I32, D,
                              ctypes.POINTER(D), c_double, U8, c_int, c_int, c_int, D, D, I32, I32,
                              D, D, D, D]
+    L.or_beam_step.argtypes = [c_int, D, c_double, c_double, c_double, I32, c_double, c_double,
+                               c_double, c_double, c_double, c_int, D, D, D, D]
+    L.or_beam_static.argtypes = [c_int, D, c_double, c_double, I32, D, c_double, c_double, c_double,
+                                 c_int, D]
+    L.or_beam_internal.argtypes = [c_int, D, c_double, c_double, D, D, D]
+    L.or_beam_mass.argtypes = [c_int, D, c_double, D]
     L.or_fresh_init.argtypes = [c_int, c_int, c_int, c_int, I32, U8, U8, c_int, D, D, D]
     L.or_links.argtypes = [c_int, c_int, c_int, c_int, I32, U8, c_int, c_int, c_int, D, D, I32, I32,
                            c_int, I32, I32, D, I32, D]
@@ -257,3 +263,50 @@ def fresh_init(lat, f, old_solid, new_solid, surf: "Surface", periodic=(0, 0, 1)
     return _check(lib().or_fresh_init(lat, nx, ny, nz, per.ctypes.data_as(I32), a.ctypes.data_as(U8),
                                       b.ctypes.data_as(U8), surf.x.shape[0], _p(surf.x), _p(surf.v),
                                       _p(f)))
+
+
+# ---------------------------------------------------------------- structure
+class Beam:
+    """2-D co-rotational Euler-Bernoulli beam (FP64 oracle): reference nodes
+    X[nn,2], axial stiffness EA, bending stiffness EI, mass per length rhoA,
+    fixed[3 nn] Dirichlet mask (DOFs ux, uy, theta per node)."""
+
+    def __init__(self, X, EA, EI, rhoA, fixed):
+        self.X = np.ascontiguousarray(X, dtype=np.float64)
+        self.nn = self.X.shape[0]
+        self.EA, self.EI, self.rhoA = float(EA), float(EI), float(rhoA)
+        self.fixed = np.ascontiguousarray(fixed, dtype=np.int32)
+
+    def internal(self, u, want_K=True):
+        n = 3 * self.nn
+        f = np.zeros(n)
+        K = np.zeros((n, n)) if want_K else None
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        lib().or_beam_internal(self.nn, _p(self.X), self.EA, self.EI, _p(u), _p(f),
+                               _p(K) if want_K else None)
+        return f, K
+
+    def mass(self):
+        n = 3 * self.nn
+        M = np.zeros((n, n))
+        lib().or_beam_mass(self.nn, _p(self.X), self.rhoA, _p(M))
+        return M
+
+    def step(self, u, v, F0, F1, dt=1.0, theta=0.5, lam=0.7, rtol=1e-10, atol=1e-13, max_it=200):
+        """One theta-scheme step (Eq. timeInt) with Newton + line search lambda;
+        returns (u1, v1, iterations)."""
+        u = np.array(u, dtype=np.float64)
+        v = np.array(v, dtype=np.float64)
+        F0 = np.ascontiguousarray(F0, dtype=np.float64)
+        F1 = np.ascontiguousarray(F1, dtype=np.float64)
+        it = lib().or_beam_step(self.nn, _p(self.X), self.EA, self.EI, self.rhoA,
+                                self.fixed.ctypes.data_as(I32), dt, theta, lam, rtol, atol, max_it,
+                                _p(F0), _p(F1), _p(u), _p(v))
+        return u, v, it
+
+    def static(self, F, lam=1.0, rtol=1e-12, atol=1e-13, max_it=200, u0=None):
+        u = np.zeros(3 * self.nn) if u0 is None else np.array(u0, dtype=np.float64)
+        F = np.ascontiguousarray(F, dtype=np.float64)
+        it = lib().or_beam_static(self.nn, _p(self.X), self.EA, self.EI, self.fixed.ctypes.data_as(I32),
+                                  _p(F), lam, rtol, atol, max_it, _p(u))
+        return u, it

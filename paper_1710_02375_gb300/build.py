@@ -40,6 +40,12 @@ def _deps_mtime():
     return max(os.path.getmtime(f) for f in files if os.path.exists(f))
 
 
+# Per-file flags: the geometry and boundary code keeps IEEE operation-by-operation
+# FP64 arithmetic (no fused multiply-add contraction), so that solid/fluid and
+# cut-link decisions on degenerate geometry are reproducible.
+FILE_FLAGS = {"boundary.cu": ["-fmad=false"]}
+
+
 def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
         return LIB
@@ -49,7 +55,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD_DIR, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc, "-c", src, "-o", obj] + flags
+        cmd = [nvcc, "-c", src, "-o", obj] + flags + FILE_FLAGS.get(os.path.basename(src), [])
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")

@@ -50,15 +50,15 @@ __device__ __forceinline__ int step_axis(int S, int c, int NS, int pad) {
   return s;
 }
 
-template <int Q, int S>
-__device__ void dev_moments(const Grid &g, const typename Store<S>::T *f, long long k, float &drho,
-                            float (&j)[3]) {
+template <int Q, int S, typename R = float>
+__device__ void dev_moments(const Grid &g, const typename Store<S>::T *f, long long k, R &drho,
+                            R (&j)[3]) {
   using L = Lat<Q>;
-  drho = 0.f;
-  j[0] = j[1] = j[2] = 0.f;
+  drho = 0;
+  j[0] = j[1] = j[2] = 0;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const float v = Store<S>::load(f + (long long)i * g.N + k, (float)weight<L>(i));
+    const R v = (R)Store<S>::load(f + (long long)i * g.N + k, (float)weight<L>(i));
     drho += v;
     j[0] += L::cx(i) * v;
     j[1] += L::cy(i) * v;
@@ -66,12 +66,12 @@ __device__ void dev_moments(const Grid &g, const typename Store<S>::T *f, long l
   }
 }
 
-template <int Q, int S>
-__device__ void dev_velocity(const Grid &g, const typename Store<S>::T *f, long long k, float (&u)[3],
-                             float *rho = nullptr) {
-  float dr, j[3];
-  dev_moments<Q, S>(g, f, k, dr, j);
-  const float r = 1.f + dr;
+template <int Q, int S, typename R = float>
+__device__ void dev_velocity(const Grid &g, const typename Store<S>::T *f, long long k, R (&u)[3],
+                             R *rho = nullptr) {
+  R dr, j[3];
+  dev_moments<Q, S, R>(g, f, k, dr, j);
+  const R r = (R)1 + dr;
   for (int a = 0; a < 3; ++a) u[a] = j[a] / r;
   if (rho) *rho = r;
 }
@@ -334,18 +334,19 @@ __global__ void k_fresh_init(Grid g, typename Store<S>::T *f, const uint8_t *fla
 }
 
 // ---------------------------------------------------------------- Grad fill + force
-template <int Q, int S>
+template <int Q, int S, typename R>
 __global__ void __launch_bounds__(128)
     k_grad(Grid g, typename Store<S>::T *f, const uint8_t *__restrict__ flags,
            const BNode *__restrict__ bnodes, const int *__restrict__ nbn, int nfixed, int cap,
-           const Link *__restrict__ links, BoundaryParams bp, double *vforce, double *bforce,
-           int nbodies) {
+           int first, int last, const Link *__restrict__ links, BoundaryParams bp, double *vforce,
+           double *bforce, int nbodies) {
   using L = Lat<Q>;
   using St = Store<S>;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  // threads [0, nfixed) take the face nodes, the rest the immersed nodes
+  const int t = blockIdx.x * blockDim.x + threadIdx.x + first;
   int dyn = nbn ? *nbn : 0;
   if (dyn > cap - nfixed) dyn = cap - nfixed;
-  const int count = nfixed + dyn;
+  const int count = last < 0 ? nfixed + dyn : last;
   const bool active = t < count;
   int my_body = -1;
   double Fd[3] = {0, 0, 0};
@@ -357,7 +358,7 @@ __global__ void __launch_bounds__(128)
     long long src[Q];
     int face_of[Q];
     uint32_t miss = 0;
-    float gk[Q];
+    R gk[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const int Xs = nbr(X, -L::cx(i), g.NX), Ys = nbr(Y, -L::cy(i), g.NY),
@@ -365,9 +366,9 @@ __global__ void __launch_bounds__(128)
       src[i] = sidx(g, Xs, Ys, Zs);
       const uint8_t fl = flags[src[i]];
       face_of[i] = -1;
-      gk[i] = 0.f;
+      gk[i] = 0;
       if (fl == NODE_FLUID) {
-        gk[i] = St::load(f + (long long)i * g.N + src[i], (float)weight<L>(i));
+        gk[i] = (R)St::load(f + (long long)i * g.N + src[i], (float)weight<L>(i));
       } else {
         miss |= 1u << i;
         if (fl == NODE_GHOST) {
@@ -388,7 +389,7 @@ __global__ void __launch_bounds__(128)
             open_face = fc;
             break;
           }
-      float rho_t, ut[3] = {0.f, 0.f, 0.f};
+      R rho_t, ut[3] = {0, 0, 0};
       bool zero_grad = false;
       if (open_face >= 0) {
         const int ax = open_face / 2;
@@ -400,13 +401,13 @@ __global__ void __launch_bounds__(128)
         long long kn = k;
         if (Xn >= 0 && Yn >= 0 && Zn >= 0 && flags[sidx(g, Xn, Yn, Zn)] == NODE_FLUID)
           kn = sidx(g, Xn, Yn, Zn);
-        float u0[3], r0;
-        dev_velocity<Q, S>(g, f, kn, u0, &r0);
+        R u0[3], r0;
+        dev_velocity<Q, S, R>(g, f, kn, u0, &r0);
         if (bp.bc[open_face] == BCK_INLET) {
-          float scale = 1.f;
+          R scale = 1;
           if (bp.ramp_steps > 0 && bp.step) {
             const int st = *bp.step;
-            if (st < bp.ramp_steps) scale = 0.5f * (1.f - cospif((float)st / bp.ramp_steps));
+            if (st < bp.ramp_steps) scale = (R)0.5 * ((R)1 - cospi((double)st / bp.ramp_steps));
           }
           const float *prof = bp.inlet[open_face];
           const int x = X - g.px, y = Y - g.py, z = Z - g.pz;
@@ -415,22 +416,22 @@ __global__ void __launch_bounds__(128)
           else if (ax == 1) { fidx = (long long)z * g.nx + x; fn = (long long)g.nx * g.nz; }
           else { fidx = (long long)y * g.nx + x; fn = (long long)g.nx * g.ny; }
           for (int a = 0; a < L::D; ++a)
-            ut[a] = scale * (prof ? prof[a * fn + fidx] : bp.face_u[open_face][a]);
+            ut[a] = scale * (R)(prof ? prof[a * fn + fidx] : bp.face_u[open_face][a]);
           rho_t = r0;
         } else if (bp.bc[open_face] == BCK_OUTLET) {
           for (int a = 0; a < 3; ++a) ut[a] = u0[a];
-          rho_t = 1.f;
+          rho_t = 1;
         } else {
           for (int a = 0; a < L::D; ++a) ut[a] = bp.face_u[open_face][a];
-          rho_t = 1.f;
+          rho_t = 1;
           zero_grad = true;
         }
       } else {
-        float drt = 0.f;
+        R drt = 0;
         int m = 0;
         for (int i = 0; i < Q; ++i) {
           if (!((miss >> i) & 1u)) { drt += gk[i]; continue; }
-          float q = 0.5f, uw[3] = {0.f, 0.f, 0.f};
+          R q = 0.5, uw[3] = {0, 0, 0};
           if (face_of[i] >= 0) {
             for (int a = 0; a < 3; ++a) uw[a] = bp.face_u[face_of[i]][a];
           } else {
@@ -444,28 +445,28 @@ __global__ void __launch_bounds__(128)
               }
             }
           }
-          const float cuw = L::cx(i) * uw[0] + L::cy(i) * uw[1] + L::cz(i) * uw[2];
-          drt += St::load(f + (long long)(Q - 1 - i) * g.N + k, (float)weight<L>(i)) +
-                 6.f * (float)weight<L>(i) * cuw;
+          const R cuw = L::cx(i) * uw[0] + L::cy(i) * uw[1] + L::cz(i) * uw[2];
+          drt += (R)St::load(f + (long long)(Q - 1 - i) * g.N + k, (float)weight<L>(i)) +
+                 (R)6 * (R)weight<L>(i) * cuw;
           const int Xn = step_axis(X, L::cx(i), g.NX, g.px), Yn = step_axis(Y, L::cy(i), g.NY, g.py);
           const int Zn = (L::D == 3) ? step_axis(Z, L::cz(i), g.NZ, g.pz) : Z;
-          float ui[3] = {uw[0], uw[1], uw[2]};
+          R ui[3] = {uw[0], uw[1], uw[2]};
           if (Xn >= 0 && Yn >= 0 && Zn >= 0 && flags[sidx(g, Xn, Yn, Zn)] == NODE_FLUID) {
-            float un[3];
-            dev_velocity<Q, S>(g, f, sidx(g, Xn, Yn, Zn), un);
-            for (int a = 0; a < 3; ++a) ui[a] = (uw[a] + q * un[a]) / (1.f + q);
+            R un[3];
+            dev_velocity<Q, S, R>(g, f, sidx(g, Xn, Yn, Zn), un);
+            for (int a = 0; a < 3; ++a) ui[a] = (uw[a] + q * un[a]) / ((R)1 + q);
           }
           for (int a = 0; a < 3; ++a) ut[a] += ui[a];
           ++m;
         }
-        for (int a = 0; a < 3; ++a) ut[a] /= (float)nmiss;
-        rho_t = 1.f + drt;
+        for (int a = 0; a < 3; ++a) ut[a] /= (R)nmiss;
+        rho_t = (R)1 + drt;
       }
       // ---- velocity gradient G[a][b] = d u_a / d x_b (previous step)
-      float G[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+      R G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
       if (!zero_grad) {
-        float u0[3];
-        dev_velocity<Q, S>(g, f, k, u0);
+        R u0[3];
+        dev_velocity<Q, S, R>(g, f, k, u0);
         for (int b = 0; b < L::D; ++b) {
           int P1[3] = {X, Y, Z}, M1[3] = {X, Y, Z}, P2[3] = {X, Y, Z}, M2[3] = {X, Y, Z};
           const int NS = b == 0 ? g.NX : (b == 1 ? g.NY : g.NZ);
@@ -478,20 +479,20 @@ __global__ void __launch_bounds__(128)
           auto fluid = [&](const int *P) {
             return P[b] >= 0 && flags[sidx(g, P[0], P[1], P[2])] == NODE_FLUID;
           };
-          auto vel = [&](const int *P, float (&u)[3]) {
-            dev_velocity<Q, S>(g, f, sidx(g, P[0], P[1], P[2]), u);
+          auto vel = [&](const int *P, R (&u)[3]) {
+            dev_velocity<Q, S, R>(g, f, sidx(g, P[0], P[1], P[2]), u);
           };
           const bool fp = fluid(P1), fm = fluid(M1);
-          float a1[3], a2[3];
+          R a1[3], a2[3];
           if (fp && fm) {
             vel(P1, a1);
             vel(M1, a2);
-            for (int a = 0; a < 3; ++a) G[a][b] = 0.5f * (a1[a] - a2[a]);
+            for (int a = 0; a < 3; ++a) G[a][b] = (R)0.5 * (a1[a] - a2[a]);
           } else if (fp) {
             vel(P1, a1);
             if (fluid(P2)) {
               vel(P2, a2);
-              for (int a = 0; a < 3; ++a) G[a][b] = 0.5f * (-3.f * u0[a] + 4.f * a1[a] - a2[a]);
+              for (int a = 0; a < 3; ++a) G[a][b] = (R)0.5 * ((R)-3 * u0[a] + (R)4 * a1[a] - a2[a]);
             } else {
               for (int a = 0; a < 3; ++a) G[a][b] = a1[a] - u0[a];
             }
@@ -499,7 +500,7 @@ __global__ void __launch_bounds__(128)
             vel(M1, a1);
             if (fluid(M2)) {
               vel(M2, a2);
-              for (int a = 0; a < 3; ++a) G[a][b] = 0.5f * (3.f * u0[a] - 4.f * a1[a] + a2[a]);
+              for (int a = 0; a < 3; ++a) G[a][b] = (R)0.5 * ((R)3 * u0[a] - (R)4 * a1[a] + a2[a]);
             } else {
               for (int a = 0; a < 3; ++a) G[a][b] = u0[a] - a1[a];
             }
@@ -507,22 +508,23 @@ __global__ void __launch_bounds__(128)
         }
       }
       // ---- Grad's approximation, Eq. (grad)
-      float A[3][3];
-      const float cneq = -rho_t / (6.f * bp.beta);
+      R A[3][3];
+      const R cneq = -rho_t / ((R)6 * (R)bp.beta);
       for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) A[a][b] = rho_t * ut[a] * ut[b] + cneq * (G[a][b] + G[b][a]);
-      const float trA = A[0][0] + A[1][1] + A[2][2];
+      const R trA = A[0][0] + A[1][1] + A[2][2];
       int l = 0;
       for (int i = 0; i < Q; ++i) {
         if (!((miss >> i) & 1u)) continue;
         const int c[3] = {L::cx(i), L::cy(i), L::cz(i)};
-        float cAc = 0.f;
+        R cAc = 0;
         for (int a = 0; a < 3; ++a)
           for (int b = 0; b < 3; ++b) cAc += c[a] * c[b] * A[a][b];
-        const float cu = c[0] * ut[0] + c[1] * ut[1] + c[2] * ut[2];
+        const R cu = c[0] * ut[0] + c[1] * ut[1] + c[2] * ut[2];
         const float W = (float)weight<L>(i);
-        const float gstar = W * ((rho_t - 1.f) + 3.f * rho_t * cu + 4.5f * (cAc - trA / 3.f));
-        St::store(f + (long long)i * g.N + src[i], gstar, (float)(1.0 / weight<L>(i)));
+        const R gstar =
+            (R)weight<L>(i) * ((rho_t - (R)1) + (R)3 * rho_t * cu + (R)4.5 * (cAc - trA / (R)3));
+        St::store(f + (long long)i * g.N + src[i], (float)gstar, (float)(1.0 / weight<L>(i)));
         if (face_of[i] < 0) {
           // momentum exchange on the immersed surface, FP64 accumulation
           while (l < bn.nlink && links[bn.link0 + l].i != i) ++l;
@@ -530,7 +532,7 @@ __global__ void __launch_bounds__(128)
             const Link &lk = links[bn.link0 + l];
             if (lk.body >= 0) {
               const double gop = (double)St::load(f + (long long)(Q - 1 - i) * g.N + k, W);
-              const double fsum = 2.0 * weight<L>(i) + gop + (double)gstar;
+              const double fsum = 2.0 * weight<L>(i) + gop + (double)(float)gstar;
               for (int a = 0; a < L::D; ++a) {
                 const double Fa = -(double)c[a] * fsum;
                 for (int m = 0; m < L::D; ++m)
@@ -618,8 +620,20 @@ cudaError_t launch_grad(int Q, int storage, const Grid &g, void *f, const uint8_
                         double *bforce, int nbodies, cudaStream_t s) {
   if (cap <= 0) return cudaSuccess;
   KBC_DISPATCH(Q, storage, {
-    k_grad<QQ, SS><<<nb_(cap, 128), 128, 0, s>>>(g, (typename Store<SS>::T *)f, flags, bnodes, nbn,
-                                                 nfixed, cap, links, bp, vforce, bforce, nbodies);
+    using T = typename Store<SS>::T;
+    // face nodes in FP32 arithmetic (their count scales with the lattice faces)
+    if (nfixed > 0) {
+      k_grad<QQ, SS, float><<<nb_(nfixed, 128), 128, 0, s>>>(
+          g, (T *)f, flags, bnodes, nullptr, nfixed, cap, 0, nfixed, links, bp, vforce, bforce, 0);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    // immersed boundary nodes in FP64 arithmetic, with the force gather
+    if (cap > nfixed) {
+      k_grad<QQ, SS, double><<<nb_(cap - nfixed, 128), 128, 0, s>>>(
+          g, (T *)f, flags, bnodes, nbn, nfixed, cap, nfixed, -1, links, bp, vforce, bforce,
+          nbodies);
+    }
     return cudaGetLastError();
   });
 }

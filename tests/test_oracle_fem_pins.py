@@ -1,0 +1,152 @@
+"""Pins of the oracle's co-rotational beam and theta-scheme (section
+"Structural modeling": Eqs. timeInt, timeDiscrete_*, Newton with lambda = 0.7)
+against closed forms, an independent elastica shooting solution, finite
+differences and the exact cantilever eigenvalue."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+
+
+def cantilever(ne=20, L=35.0, E=1.5, h=2.0, rho=10.0):
+    X = np.stack([np.linspace(0, L, ne + 1), np.zeros(ne + 1)], axis=1)
+    fixed = np.zeros(3 * (ne + 1), np.int32)
+    fixed[:3] = 1
+    A, I = h, h ** 3 / 12.0
+    return orc.Beam(X, E * A, E * I, rho * A, fixed), L, E * I
+
+
+def test_tangent_is_derivative_of_internal_force():
+    beam, L, EI = cantilever(ne=6)
+    rng = np.random.default_rng(0)
+    u = rng.normal(scale=[2.0, 3.0, 0.4] * beam.nn)
+    u[:3] = 0
+    f, K = beam.internal(u)
+    h = 1e-6
+    Kfd = np.zeros_like(K)
+    for j in range(len(u)):
+        up, um = u.copy(), u.copy()
+        up[j] += h
+        um[j] -= h
+        Kfd[:, j] = (beam.internal(up, False)[0] - beam.internal(um, False)[0]) / (2 * h)
+    assert np.max(np.abs(K - Kfd)) < 1e-6 * np.max(np.abs(K))
+    # rigid-body motion of the free beam costs no force
+    free, _, _ = cantilever(ne=6)
+    th = 0.9
+    c, s = np.cos(th), np.sin(th)
+    ur = np.zeros(3 * free.nn)
+    for j, (x, y) in enumerate(free.X):
+        ur[3 * j] = c * x - s * y - x + 3.0
+        ur[3 * j + 1] = s * x + c * y - y - 1.0
+        ur[3 * j + 2] = th
+    assert np.max(np.abs(free.internal(ur, False)[0])) < 1e-10
+
+
+def test_linear_cantilever_tip_load():
+    """Small tip load: Hermite elements give PL^3/(3EI) and PL^2/(2EI) exactly."""
+    beam, L, EI = cantilever()
+    P = 1e-8
+    F = np.zeros(3 * beam.nn)
+    F[-2] = P
+    u, it = beam.static(F)
+    assert it > 0
+    assert abs(u[-2] - P * L ** 3 / (3 * EI)) < 1e-6 * P * L ** 3 / (3 * EI)
+    assert abs(u[-1] - P * L ** 2 / (2 * EI)) < 1e-6 * P * L ** 2 / (2 * EI)
+
+
+def elastica_tip(P, EI, L, n=4000):
+    """Cantilever under a fixed-direction tip load P (along +y): EI th'' = -P cos th,
+    th(0) = 0, th'(L) = 0, solved by RK4 shooting on th'(0) (bisection)."""
+    def shoot(k0):
+        h = L / n
+        th, k, x, y = 0.0, k0, 0.0, 0.0
+
+        def rhs(state):
+            th_, k_, _, _ = state
+            return np.array([k_, -P / EI * np.cos(th_), np.cos(th_), np.sin(th_)])
+        st = np.array([th, k, x, y])
+        for _ in range(n):
+            a = rhs(st)
+            b = rhs(st + 0.5 * h * a)
+            c = rhs(st + 0.5 * h * b)
+            d = rhs(st + h * c)
+            st = st + h / 6 * (a + 2 * b + 2 * c + d)
+        return st
+    lo, hi = 0.0, P * L / EI * 1.5
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        if shoot(mid)[1] > 0:
+            hi = mid
+        else:
+            lo = mid
+    st = shoot(0.5 * (lo + hi))
+    return st[2], st[3], st[0]
+
+
+def test_large_deflection_matches_elastica():
+    """Inextensible limit (EA large): the discrete tip deflection approaches the
+    elastica at second order in the element size."""
+    errs = []
+    for ne in (10, 20):
+        beam, L, EI = cantilever(ne=ne)
+        beam.EA *= 1e5
+        P = 2.0 * EI / L ** 2
+        F = np.zeros(3 * beam.nn)
+        F[-2] = P
+        u, it = beam.static(F, lam=0.7, max_it=400, atol=1e-9)
+        assert it > 0
+        xe, ye, the = elastica_tip(P, EI, L)
+        errs.append(abs(u[-2] - ye) / ye)
+        assert abs(L + u[-3] - xe) < 5e-3 * L
+    assert errs[1] < 2e-3
+    assert errs[0] / errs[1] > 3.0
+
+
+def test_first_natural_frequency():
+    """Lowest eigenvalue of K(0) phi = w^2 M phi against (1.8751)^2 sqrt(EI/(rhoA L^4))."""
+    from scipy.linalg import eigh
+    beam, L, EI = cantilever()
+    _, K = beam.internal(np.zeros(3 * beam.nn))
+    M = beam.mass()
+    free = beam.fixed == 0
+    w2 = eigh(K[np.ix_(free, free)], M[np.ix_(free, free)], eigvals_only=True)
+    w1 = np.sqrt(w2.min())
+    exact = 1.8751040687119611 ** 2 * np.sqrt(EI / (beam.rhoA * L ** 4))
+    assert abs(w1 - exact) / exact < 1e-4
+
+
+def test_crank_nicolson_free_vibration_period_and_energy():
+    beam, L, EI = cantilever(ne=10)
+    _, K0 = beam.internal(np.zeros(3 * beam.nn))
+    M = beam.mass()
+    # start from the static tip-load shape, tiny amplitude (linear regime)
+    F = np.zeros(3 * beam.nn)
+    F[-2] = 1e-9
+    u, _ = beam.static(F)
+    v = np.zeros_like(u)
+    Z = np.zeros_like(u)
+    E0 = 0.5 * u @ K0 @ u
+    tip = []
+    for _ in range(4000):
+        u, v, it = beam.step(u, v, Z, Z, dt=20.0, theta=0.5, lam=1.0)
+        assert it >= 0
+        tip.append(u[-2])
+        E = 0.5 * v @ M @ v + 0.5 * u @ K0 @ u
+        assert abs(E - E0) < 1e-6 * E0
+    tip = np.array(tip)
+    cross = np.where((tip[:-1] > 0) & (tip[1:] <= 0))[0]
+    period = np.mean(np.diff(cross)) * 20.0
+    w = 1.8751040687119611 ** 2 * np.sqrt(EI / (beam.rhoA * L ** 4))
+    assert abs(period - 2 * np.pi / w) / (2 * np.pi / w) < 2e-3
+
+
+def test_newton_with_line_search_converges():
+    beam, L, EI = cantilever()
+    n = 3 * beam.nn
+    F1 = np.zeros(n)
+    F1[1::3] = 0.002
+    u, v, it = beam.step(np.zeros(n), np.zeros(n), np.zeros(n), F1, lam=0.7)
+    assert 5 < it < 200
+    u2, v2, it2 = beam.step(np.zeros(n), np.zeros(n), np.zeros(n), F1, lam=1.0)
+    assert 0 < it2 < it
+    assert np.max(np.abs(u - u2)) < 1e-9 * np.max(np.abs(u2))
