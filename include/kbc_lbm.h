@@ -136,7 +136,8 @@ lbm_status lbm_set_inlet_profile(lbm_ctx *ctx, int face, const double *u);
 
 /* Immersed bodies (section "Fluid boundary conditions": the structure's
  * surface mesh passed to the fluid solver).  verts[nv][dim] positions in
- * lattice units (interior node (x,y,z) sits at (x,y,z)), elems[ne][dim]
+ * lattice units (interior node (x,y,z) is the centre of its cell, at
+ * (x + 1/2, y + 1/2, z + 1/2); a node on the surface counts as solid), elems[ne][dim]
  * closed polygons (2-D, segments) or closed triangle meshes (3-D),
  * elem_body[ne] in [0, nbodies), vert_vel[nv][dim] wall velocities (NULL:
  * at rest).  Nodes inside a body become solid; cut links (nearest crossing
@@ -161,12 +162,65 @@ lbm_status lbm_update_surface(lbm_ctx *ctx, const double *verts, const double *v
  * accumulated in FP64: vert_force[nv][3] (each link's force split over the
  * hit element's vertices by its interpolation weights) and
  * body_force[nbodies][3] totals.  Either may be NULL.  Per link i of fluid
- * node x_b: -c_i (f'_opp(i)(x_b, t-1) + f*_i(x_b, t)).  Synchronises. */
+ * node x_b: -c_i (f'_opp(i)(x_b, t-1) + f*_i(x_b, t) - 2 W_i), the momentum
+ * exchange relative to the rest state (gauge pressure).  Synchronises. */
 lbm_status lbm_get_interface_force(lbm_ctx *ctx, double *vert_force, double *body_force);
 
 /* info[4] = {face boundary nodes, immersed boundary nodes, cut links,
  * inlet-ramp step counter}.  Synchronises. */
 lbm_status lbm_get_boundary_info(lbm_ctx *ctx, int *info);
+
+/* ---------------------------------------------------------------------------
+ * Structure (section "Structural modeling"): 2-D geometrically nonlinear
+ * co-rotational Euler-Bernoulli beam in FP64 on the GPU, one-step-theta
+ * scheme Eq. (timeInt) in the two-field (v, u) form, Newton-Raphson with the
+ * constant line-search relaxation lambda (the paper uses 0.7).
+ * Element a-b: N = EA (L - L0)/L0, M1 = 2EI/L0 (2 t1 + t2),
+ * M2 = 2EI/L0 (t1 + 2 t2), t = nodal rotation minus chord rotation;
+ * consistent Hermite mass.  DOFs per node: (ux, uy, theta).
+ * ------------------------------------------------------------------------- */
+typedef struct fem_ctx fem_ctx;
+
+typedef struct {
+  int nn;                 /* beam nodes, 2..64 */
+  const double *X;        /* [nn][2] reference node positions (lattice units), copied */
+  double EA, EI, rhoA;    /* axial / bending stiffness, mass per length */
+  double thickness;       /* flag thickness h (surface offset h/2 each side) */
+  const int32_t *fixed;   /* [3 nn] 1 = DOF held at zero, copied */
+  double theta;           /* theta of Eq. (timeInt), (0, 1] */
+  double lambda;          /* Newton relaxation, (0, 1] */
+  double rtol, atol;      /* stop when |R| <= rtol |R_0| + atol */
+  int max_it;             /* Newton iteration limit */
+  double dt;              /* structural time step (lattice steps) */
+  void *stream;           /* cudaStream_t, NULL: library-owned */
+} fem_beam_config;
+
+lbm_status fem_beam_workspace_size(const fem_beam_config *cfg, size_t *bytes);
+/* workspace: device memory of fem_beam_workspace_size() bytes (256-byte
+ * aligned, caller-owned) or NULL (cudaMalloc).  State starts at rest. */
+lbm_status fem_beam_create(const fem_beam_config *cfg, void *workspace, size_t bytes,
+                           fem_ctx **out);
+/* One theta-scheme step with nodal loads F1[3 nn] at the new time (the
+ * previous call's loads serve as F0).  Asynchronous. */
+lbm_status fem_beam_step(fem_ctx *f, const double *F1);
+/* u[3nn], v[3nn] (either may be NULL) and the last step's Newton iteration
+ * count (negative: not converged within max_it).  Synchronises. */
+lbm_status fem_beam_get_state(fem_ctx *f, double *u, double *v, int *iterations);
+lbm_status fem_beam_set_state(fem_ctx *f, const double *u, const double *v, const double *F0);
+const char *fem_last_error(const fem_ctx *f);
+void fem_destroy(fem_ctx *f);
+
+/* Couple a beam to the lattice (conventional serial staggered scheme,
+ * section "Fluid-structure coupling"): the beam's flag surface occupies
+ * surface vertices [first_vertex, first_vertex + 2 nn) of the geometry given
+ * to lbm_set_geometry (bottom edge in node order, then the top edge in
+ * reverse node order).  Every lbm_step then runs, on the lattice stream:
+ * fluid step with Grad boundaries -> momentum-exchange forces -> nodal loads
+ * (sum of the node's two vertex forces; moments about the centre line are
+ * not transferred) -> structural step ->
+ * new flag vertices and velocities -> solid flags, fresh nodes and cut links.
+ * The fem context must stay alive while coupled.  LBM_EINVAL on a bad range. */
+lbm_status fsi_couple(lbm_ctx *ctx, fem_ctx *f, int first_vertex);
 
 /* Density rho[nz][ny][nx] and velocity u[dim][nz][ny][nx] of the current
  * state (FP64 outputs; solid nodes give rho = 0, u = 0).  Synchronises. */

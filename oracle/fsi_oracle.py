@@ -1,0 +1,108 @@
+"""Conventional serial staggered (CSS) coupling of the KBC fluid and the beam
+-- TEST INFRASTRUCTURE ONLY (section "Fluid-structure coupling": fluid step
+with boundary conditions, traction on the solid, structural step, transfer of
+velocity and displacement, geometry update).
+
+Readings shared with the CUDA library:
+  * the flag is a closed polygon around the beam centre line: bottom edge
+    vertex j = x_j + (h/2)(sin th_j, -cos th_j), top edge (stored in reverse
+    node order) x_j + (h/2)(-sin th_j, cos th_j); vertex velocities follow by
+    differentiation, v_j -+ (h/2) dth_j (cos th_j, sin th_j) for top / bottom
+    (x_j = X_j + u_j and th_j the nodal rotation);
+  * nodal loads on beam node j: the sum of the momentum-exchange forces of its
+    two surface vertices; the moments of these forces about the centre line
+    are not transferred (the flag-tip rotation is a stiff mode, omega dt ~ 1.5
+    at h = 2, that the one-step lag of the staggered scheme drives unstable
+    when they are);
+  * one structural step per fluid step (dt = 1), theta-scheme loads F^n (the
+    previous step's) and F^{n+1} (this step's).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import oracle as orc
+
+
+def flag_vertices(X, u, v, h):
+    """Surface vertices x[2nn,2] and velocities [2nn,2] of the flag polygon."""
+    nn = X.shape[0]
+    U = u.reshape(nn, 3)
+    V = v.reshape(nn, 3)
+    xc = X + U[:, :2]
+    th, om = U[:, 2], V[:, 2]
+    nrm = np.stack([-np.sin(th), np.cos(th)], axis=1)          # unit normal (top side)
+    dn = np.stack([-np.cos(th), -np.sin(th)], axis=1) * om[:, None]
+    bot = xc - 0.5 * h * nrm
+    top = xc + 0.5 * h * nrm
+    vbot = V[:, :2] - 0.5 * h * dn
+    vtop = V[:, :2] + 0.5 * h * dn
+    x = np.concatenate([bot, top[::-1]])
+    vel = np.concatenate([vbot, vtop[::-1]])
+    return x, vel
+
+
+def nodal_loads(X, u, xs, fs):
+    """Beam nodal loads [3nn] from the forces fs[2nn,3] on the flag vertices
+    (forces only, no moments)."""
+    nn = X.shape[0]
+    F = np.zeros((nn, 3))
+    for j in range(nn):
+        for vtx in (j, 2 * nn - 1 - j):
+            F[j, 0] += fs[vtx, 0]
+            F[j, 1] += fs[vtx, 1]
+    return F.reshape(-1)
+
+
+class CSSFlag:
+    """Rigid bodies plus one flag body (the last body) whose surface vertices
+    are the last 2 nn vertices of the surface mesh."""
+
+    def __init__(self, lat, shape, beta, bc, face_u, inlet, ramp, x_rigid, e_all, body,
+                 beam: "orc.Beam", h, rho0=None, u0=None):
+        self.lat, self.shape, self.beta, self.bc = lat, shape, beta, bc
+        self.face_u, self.inlet, self.ramp = face_u, inlet, ramp
+        self.x_rigid = np.asarray(x_rigid, dtype=np.float64)
+        self.e, self.body = e_all, body
+        self.beam, self.h = beam, h
+        n = 3 * beam.nn
+        self.u = np.zeros(n)
+        self.v = np.zeros(n)
+        self.F0 = np.zeros(n)
+        self.t = 0
+        nz, ny, nx = shape
+        dim = 2
+        rho0 = np.ones(shape) if rho0 is None else rho0
+        u0 = np.zeros((dim,) + shape) if u0 is None else u0
+        self.f = orc.init_equilibrium(lat, rho0, u0)
+        self.surf = self._surface()
+        self.solid = orc.solid_mask(shape, self.surf)
+        self.iterations = []
+
+    def _surface(self):
+        xf, vf = flag_vertices(self.beam.X, self.u, self.v, self.h)
+        x = np.concatenate([self.x_rigid, xf])
+        vel = np.concatenate([np.zeros_like(self.x_rigid), vf])
+        return orc.Surface(x, vel, self.e, self.body)
+
+    def step(self):
+        s = 1.0
+        if self.ramp and self.t < self.ramp:
+            s = 0.5 * (1 - np.cos(np.pi * self.t / self.ramp))
+        # 1. fluid step with the current geometry and wall velocities
+        self.f, vf, bf, _ = orc.step_bc(self.lat, self.beta, self.f, bc=self.bc, face_u=self.face_u,
+                                        inlet=self.inlet, inlet_scale=s, surf=self.surf,
+                                        solid=self.solid)
+        self.vforce, self.bforce = vf, bf
+        # 2. traction on the structure, structural step
+        nr = self.x_rigid.shape[0]
+        F1 = nodal_loads(self.beam.X, self.u, self.surf.x[nr:], vf[nr:])
+        self.u, self.v, it = self.beam.step(self.u, self.v, self.F0, F1)
+        self.iterations.append(it)
+        self.F0 = F1
+        # 3. transfer displacement and velocity, update the geometry
+        self.surf = self._surface()
+        new_solid = orc.solid_mask(self.shape, self.surf)
+        orc.fresh_init(self.lat, self.f, self.solid, new_solid, self.surf, periodic=(0, 0, 1))
+        self.solid = new_solid
+        self.t += 1

@@ -37,16 +37,20 @@
  *   Pi = rho c_s^2 I + rho u u - rho c_s^2/(2 beta) (grad u + grad u^T);
  *   f*_i = W_i [rho + rho c_i.u / c_s^2 + (Pi - rho c_s^2 I):(c_i c_i - c_s^2 I)/(2 c_s^4)]
  *     replaces every missing population of the node (and only those).
- *   Force on the surface per immersed link: -c_i (f'_opp(i)(x_b,t-1) + f*_i),
- *     split over the hit element's vertices by the same interpolation weights.
+ *   Force on the surface per immersed link: -c_i (f'_opp(i)(x_b,t-1) + f*_i - 2 W_i)
+ *     (momentum exchange relative to the rest state f = W, i.e. with the
+ *     uniform ambient pressure rho0 c_s^2 taken out; it cancels on a closed
+ *     body but not on one attached to another), split over the hit element's
+ *     vertices by the same interpolation weights.
  *   u(x, t-1) and rho(x, t-1) are the moments of the stored post-collision
  *   populations (collisions conserve them).
  *
  * Surface meshes: closed polygons (2-D: segments, element = 2 vertex ids) or
  * closed triangle meshes (3-D: element = 3 vertex ids), one body id per
- * element; node (x,y,z) of the interior sits at position (x,y,z).  A node is
- * solid when it lies inside any body (crossing-number test per body along a
- * fixed generic ray).
+ * element; node (x,y,z) of the interior is the centre of its cell, at
+ * position (x + 1/2, y + 1/2, z + 1/2) in lattice units.  A node is
+ * solid when it lies on the surface (within 1e-12) or inside any body
+ * (crossing-number test per body along a fixed generic ray).
  */
 #include <math.h>
 #include <stdint.h>
@@ -152,15 +156,49 @@ static int point_inside_body(const surf_t *S, int body, const double *p) {
   return cnt & 1;
 }
 
-/* solid[n] (interior nodes) = 1 inside any body, else 0. */
+/* A point lying on the surface (within 1e-12 lattice units of an element) is
+ * solid: the parity test alone would split nodes sitting exactly on a face
+ * between solid and fluid depending on the ray direction. */
+static int point_on_surface(const surf_t *S, const double *p) {
+  const double tol = 1e-12;
+  for (int k = 0; k < S->ne; ++k) {
+    if (S->dim == 2) {
+      const double *a = S->x + 2 * S->e[2 * k], *b = S->x + 2 * S->e[2 * k + 1];
+      const double ex = b[0] - a[0], ey = b[1] - a[1];
+      const double px = p[0] - a[0], py = p[1] - a[1];
+      const double len2 = ex * ex + ey * ey;
+      const double cr = ex * py - ey * px, dt = ex * px + ey * py;
+      if (fabs(cr) <= tol * sqrt(len2) && dt >= 0.0 && dt <= len2) return 1;
+    } else {
+      const double *a = S->x + 3 * S->e[3 * k], *b = S->x + 3 * S->e[3 * k + 1],
+                   *c = S->x + 3 * S->e[3 * k + 2];
+      const double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+      const double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+      const double w[3] = {p[0] - a[0], p[1] - a[1], p[2] - a[2]};
+      double nrm[3];
+      cross3(e1, e2, nrm);
+      const double nn = sqrt(dot3(nrm, nrm));
+      if (nn == 0.0 || fabs(dot3(nrm, w)) > tol * nn) continue;
+      /* barycentric coordinates in the plane */
+      const double d11 = dot3(e1, e1), d12 = dot3(e1, e2), d22 = dot3(e2, e2);
+      const double dw1 = dot3(w, e1), dw2 = dot3(w, e2);
+      const double den = d11 * d22 - d12 * d12;
+      const double u = (d22 * dw1 - d12 * dw2) / den, v = (d11 * dw2 - d12 * dw1) / den;
+      if (u >= 0.0 && v >= 0.0 && u + v <= 1.0) return 1;
+    }
+  }
+  return 0;
+}
+
+/* solid[n] (interior nodes) = 1 inside (or on) any body, else 0. */
 int or_solid_mask(int dim, int nx, int ny, int nz, int nv, int ne, int nb, const double *x,
                   const int32_t *e, const int32_t *eb, uint8_t *solid) {
   surf_t S = {dim, nv, ne, nb, x, NULL, e, eb};
   for (int z = 0; z < nz; ++z)
     for (int y = 0; y < ny; ++y)
       for (int xx = 0; xx < nx; ++xx) {
-        double p[3] = {(double)xx, (double)y, (double)z};
-        int in = 0;
+        double p[3] = {xx + 0.5, y + 0.5, z + 0.5};
+        int in = point_on_surface(&S, p);
         for (int b = 0; b < nb && !in; ++b) in = point_inside_body(&S, b, p);
         solid[((long)z * ny + y) * nx + xx] = (uint8_t)in;
       }
@@ -388,7 +426,7 @@ int or_step_bc(int lat, int nx, int ny, int nz, double beta, int mode, const int
               q[i] = 0.5;
               for (int a = 0; a < 3; ++a) uw[i][a] = face_u[3 * face_of[i] + a];
             } else {
-              double xbd[3] = {(double)x, (double)y, (double)z};
+              double xbd[3] = {x + 0.5, y + 0.5, z + 0.5};
               hit[i] = link_hit(&S, xbd, L.c[i], &q[i], uw[i], vid[i], vwt[i]);
               if (hit[i] < 0) { /* no crossing found: treat as a wall half-way, at rest */
                 q[i] = 0.5;
@@ -461,10 +499,12 @@ int or_step_bc(int lat, int nx, int ny, int nz, double beta, int mode, const int
             if (!miss[i]) continue;
             f[i] = grad_pop(&L, i, rho_t, ut, Pi);
             if (hit[i] >= 0) {
-              double fo = fin[(Q - 1 - i) * F.N + k];
+              /* gauge form: the reference state f = W (uniform ambient
+               * pressure rho0 c_s^2) is taken out of both populations */
+              double fo = fin[(Q - 1 - i) * F.N + k] - L.w[i];
               int body = eb[hit[i]];
               for (int a = 0; a < L.D; ++a) {
-                double Fa = -L.c[i][a] * (fo + f[i]);
+                double Fa = -L.c[i][a] * (fo + (f[i] - L.w[i]));
                 if (bforce) bforce[3 * body + a] += Fa;
                 if (vforce)
                   for (int m = 0; m < L.D; ++m) vforce[3 * vid[i][m] + a] += vwt[i][m] * Fa;
@@ -510,7 +550,7 @@ int or_links(int lat, int nx, int ny, int nz, const int *periodic, const uint8_t
           }
           if (out) continue;
           if (!solid[((long)p[2] * ny + p[1]) * nx + p[0]]) continue;
-          double xb[3] = {(double)x, (double)y, (double)z}, qq, u[3];
+          double xb[3] = {x + 0.5, y + 0.5, z + 0.5}, qq, u[3];
           int vid[3];
           double vw[3];
           int e = link_hit(&S, xb, L.c[i], &qq, u, vid, vw);
@@ -577,7 +617,7 @@ int or_fresh_init(int lat, int nx, int ny, int nz, const int *periodic, const ui
   }
   for (int q = 0; q < nfresh; ++q) {
     long k = idx[q];
-    double p[3] = {(double)(k % nx), (double)((k / nx) % ny), (double)(k / ((long)nx * ny))};
+    double p[3] = {(k % nx) + 0.5, ((k / nx) % ny) + 0.5, (k / ((long)nx * ny)) + 0.5};
     int best = 0;
     double bd = 1e300;
     for (int v = 0; v < nv; ++v) {

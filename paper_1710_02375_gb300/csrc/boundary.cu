@@ -19,7 +19,9 @@
 //     second order through x_b at walls (first order with one fluid node);
 //   f*_i = W_i [rho + 3 rho c_i.u + 9/2 (rho u u + Pi_neq):(c_i c_i - I/3)],
 //     Pi_neq = -rho/(6 beta) (grad u + grad u^T), for every missing i;
-//   force on the surface per immersed link: -c_i (f'_opp(i)(x_b) + f*_i),
+//   force on the surface per immersed link: -c_i (f'_opp(i)(x_b) + f*_i - 2 W_i)
+//     (relative to the rest state, i.e. without the uniform ambient pressure,
+//     which cancels on a closed body but loads one attached to another),
 //     accumulated in FP64 per vertex (interpolation weights) and per body.
 // The previous-step velocity of a node is the first moment of its stored
 // post-collision populations (collisions conserve it).
@@ -133,7 +135,43 @@ __device__ bool tri_ray(const double *p, const double *d, const double *a, const
   return true;
 }
 
+// Within 1e-12 of an element: a node exactly on a face is solid (the parity
+// test alone would depend on the ray direction there).
+__device__ bool on_surface(const SurfaceDev &s, const double *p) {
+  const double tol = 1e-12;
+  for (int k = 0; k < s.ne; ++k) {
+    if (s.dim == 2) {
+      const double *a = s.x + 2 * s.e[2 * k], *b = s.x + 2 * s.e[2 * k + 1];
+      const double ex = b[0] - a[0], ey = b[1] - a[1];
+      const double px = p[0] - a[0], py = p[1] - a[1];
+      const double len2 = ex * ex + ey * ey;
+      const double cr = ex * py - ey * px, dt = ex * px + ey * py;
+      if (fabs(cr) <= tol * sqrt(len2) && dt >= 0.0 && dt <= len2) return true;
+    } else {
+      const double *a = s.x + 3 * s.e[3 * k], *b = s.x + 3 * s.e[3 * k + 1],
+                   *c = s.x + 3 * s.e[3 * k + 2];
+      const double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+      const double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+      const double w[3] = {p[0] - a[0], p[1] - a[1], p[2] - a[2]};
+      const double nr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                            e1[0] * e2[1] - e1[1] * e2[0]};
+      const double nn = sqrt(nr[0] * nr[0] + nr[1] * nr[1] + nr[2] * nr[2]);
+      if (nn == 0.0 || fabs(nr[0] * w[0] + nr[1] * w[1] + nr[2] * w[2]) > tol * nn) continue;
+      const double d11 = e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2];
+      const double d12 = e1[0] * e2[0] + e1[1] * e2[1] + e1[2] * e2[2];
+      const double d22 = e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2];
+      const double dw1 = w[0] * e1[0] + w[1] * e1[1] + w[2] * e1[2];
+      const double dw2 = w[0] * e2[0] + w[1] * e2[1] + w[2] * e2[2];
+      const double den = d11 * d22 - d12 * d12;
+      const double u = (d22 * dw1 - d12 * dw2) / den, v = (d11 * dw2 - d12 * dw1) / den;
+      if (u >= 0.0 && v >= 0.0 && u + v <= 1.0) return true;
+    }
+  }
+  return false;
+}
+
 __device__ bool inside_any(const SurfaceDev &s, const double *p) {
+  if (on_surface(s, p)) return true;
   // crossing parity per body; a node is solid inside any body
   for (int b = 0; b < s.nb; ++b) {
     int cnt = 0;
@@ -215,7 +253,7 @@ __global__ void k_solid_flags(Grid g, Band bd, SurfaceDev s, uint8_t *flags, int
   if (t >= (long long)bx * by * bz) return;
   const int x = bd.x0 + (int)(t % bx), y = bd.y0 + (int)((t / bx) % by),
             z = bd.z0 + (int)(t / ((long long)bx * by));
-  const double p[3] = {(double)x, (double)y, (double)z};
+  const double p[3] = {x + 0.5, y + 0.5, z + 0.5};  // cell-centred node position
   const long long k = sidx(g, x + g.px, y + g.py, z + g.pz);
   const uint8_t now = inside_any(s, p) ? NODE_SOLID : NODE_FLUID;
   const uint8_t before = flags[k];
@@ -262,7 +300,7 @@ __global__ void k_build_links(Grid g, Band bd, SurfaceDev s, const uint8_t *flag
     return;
   }
   bnodes[slot] = BNode{k, l0, n};
-  const double xb[3] = {(double)x, (double)y, (double)z};
+  const double xb[3] = {x + 0.5, y + 0.5, z + 0.5};
   int m = 0;
   for (int i = 0; i < Q; ++i) {
     if (!(mask & (1u << i))) continue;
@@ -304,7 +342,7 @@ __global__ void k_fresh_init(Grid g, typename Store<S>::T *f, const uint8_t *fla
     rn++;
   }
   const double rho = rn ? rsum / rn : 1.0;
-  const double p[3] = {(double)(X - g.px), (double)(Y - g.py), (double)(Z - g.pz)};
+  const double p[3] = {X - g.px + 0.5, Y - g.py + 0.5, Z - g.pz + 0.5};
   int best = 0;
   double bd = 1e300;
   for (int v = 0; v < s.nv; ++v) {
@@ -532,7 +570,8 @@ __global__ void __launch_bounds__(128)
             const Link &lk = links[bn.link0 + l];
             if (lk.body >= 0) {
               const double gop = (double)St::load(f + (long long)(Q - 1 - i) * g.N + k, W);
-              const double fsum = 2.0 * weight<L>(i) + gop + (double)(float)gstar;
+              // gauge form: the rest state f = W (ambient pressure) is taken out
+              const double fsum = gop + (double)(float)gstar;
               for (int a = 0; a < L::D; ++a) {
                 const double Fa = -(double)c[a] * fsum;
                 for (int m = 0; m < L::D; ++m)

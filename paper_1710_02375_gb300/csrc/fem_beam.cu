@@ -1,0 +1,487 @@
+// fem_beam.cu -- FP64 structural step on the GPU: 2-D co-rotational
+// Euler-Bernoulli beam, one-step-theta time integration in the two-field
+// (v, u) form and Newton-Raphson with a constant line-search relaxation
+// (arXiv 1710.02375, section "Structural modeling": Eqs. (timeInt),
+// (timeDiscrete_solid_velocity), (timeDiscrete_solid_displacement), Newton
+// update with lambda; section "Fluid-structure coupling" for the loads).
+//
+// Element a-b (reference length L0, chord angle b0; current length L, angle
+// b): ul = L - L0, t1 = th_a - (b - b0), t2 = th_b - (b - b0);
+// N = EA ul/L0, M1 = 2EI/L0 (2 t1 + t2), M2 = 2EI/L0 (t1 + 2 t2);
+// f = B^T (N, M1, M2); K = B^T D B + N/L z z^T + (M1 + M2)/L^2 (r z^T + z r^T).
+// Mass: consistent Hermite mass of the linear element (constant).
+// Step: R(u1) = M (v1 - v0)/dt - th (F1 - f(u1)) - (1 - th)(F0 - f(u0)),
+// v1 = ((u1 - u0)/dt - (1 - th) v0)/th, J = M/(th dt^2) + th K(u1),
+// u1 += lambda du until |R| <= rtol |R0| + atol.
+//
+// One CTA per beam.  Matrices are banded (node-major DOFs: half bandwidth 5)
+// in shared memory; element loops run in two colour passes (even, odd
+// elements) so no two threads add into the same entries; the banded LU
+// (no pivoting: the mass term keeps J diagonally dominant at these steps)
+// runs on one thread.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "../../include/kbc_lbm.h"
+#include "lbm_internal.h"
+
+namespace kbc {
+
+constexpr int KB = 5;            // half bandwidth
+constexpr int BW = 2 * KB + 1;   // band width
+constexpr int kMaxBeamNodes = 64;
+
+struct BeamParams {
+  int nn;
+  double EA, EI, rhoA, h;
+  double theta, lambda, rtol, atol, dt;
+  int max_it;
+};
+
+struct BeamDev {
+  const double *X;     // [nn][2]
+  const int32_t *fixed;
+  double *u, *v, *F0;  // [3nn] state and previous loads
+  int *iters;          // last step's Newton iteration count (negative: not converged)
+};
+
+__device__ __forceinline__ double &band(double *A, int i, int j) { return A[i * BW + (j - i + KB)]; }
+
+__device__ void element_geom(const BeamParams &p, const double *X, const double *u, int a,
+                             double &L0, double &L, double &c, double &s, double &rot) {
+  const int b = a + 1;
+  const double X0x = X[2 * b] - X[2 * a], X0y = X[2 * b + 1] - X[2 * a + 1];
+  L0 = sqrt(X0x * X0x + X0y * X0y);
+  const double b0 = atan2(X0y, X0x);
+  const double dx = X0x + u[3 * b] - u[3 * a], dy = X0y + u[3 * b + 1] - u[3 * a + 1];
+  L = sqrt(dx * dx + dy * dy);
+  const double bb = atan2(dy, dx);
+  c = dx / L;
+  s = dy / L;
+  rot = bb - b0;
+  const double PI = 3.14159265358979323846;
+  while (rot > PI) rot -= 2 * PI;
+  while (rot <= -PI) rot += 2 * PI;
+}
+
+// Add element e's internal force (and tangent if K != nullptr) at state u.
+__device__ void element_internal(const BeamParams &p, const double *X, const double *u, int e,
+                                 double *f, double *K) {
+  double L0, L, c, s, rot;
+  element_geom(p, X, u, e, L0, L, c, s, rot);
+  const int a = e, b = e + 1;
+  const double ul = L - L0, t1 = u[3 * a + 2] - rot, t2 = u[3 * b + 2] - rot;
+  const double N = p.EA * ul / L0;
+  const double k2 = 2.0 * p.EI / L0;
+  const double M1 = k2 * (2 * t1 + t2), M2 = k2 * (t1 + 2 * t2);
+  const double r[6] = {-c, -s, 0, c, s, 0};
+  const double z[6] = {s, -c, 0, -s, c, 0};
+  double Bm[3][6];
+  for (int k = 0; k < 6; ++k) {
+    Bm[0][k] = r[k];
+    Bm[1][k] = -z[k] / L;
+    Bm[2][k] = -z[k] / L;
+  }
+  Bm[1][2] += 1.0;
+  Bm[2][5] += 1.0;
+  const double q[3] = {N, M1, M2};
+  const int d0 = 3 * a;
+  for (int k = 0; k < 6; ++k) f[d0 + k] += Bm[0][k] * q[0] + Bm[1][k] * q[1] + Bm[2][k] * q[2];
+  if (K) {
+    const double D[3][3] = {{p.EA / L0, 0, 0}, {0, 2 * k2, k2}, {0, k2, 2 * k2}};
+    for (int k = 0; k < 6; ++k)
+      for (int l = 0; l < 6; ++l) {
+        double v = 0.0;
+        for (int m = 0; m < 3; ++m)
+          for (int q2 = 0; q2 < 3; ++q2) v += Bm[m][k] * D[m][q2] * Bm[q2][l];
+        v += N / L * z[k] * z[l] + (M1 + M2) / (L * L) * (r[k] * z[l] + z[k] * r[l]);
+        band(K, d0 + k, d0 + l) += v;
+      }
+  }
+}
+
+__device__ void element_mass(const BeamParams &p, const double *X, int e, double *M) {
+  const int a = e, b = e + 1;
+  const double X0x = X[2 * b] - X[2 * a], X0y = X[2 * b + 1] - X[2 * a + 1];
+  const double L = sqrt(X0x * X0x + X0y * X0y);
+  const double c = X0x / L, s = X0y / L;
+  double Ml[6][6];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) Ml[i][j] = 0.0;
+  const double ma = p.rhoA * L / 6.0, mb = p.rhoA * L / 420.0;
+  Ml[0][0] = 2 * ma; Ml[0][3] = ma; Ml[3][0] = ma; Ml[3][3] = 2 * ma;
+  const int bi[4] = {1, 2, 4, 5};
+  const double Mb[4][4] = {{156, 22 * L, 54, -13 * L},
+                           {22 * L, 4 * L * L, 13 * L, -3 * L * L},
+                           {54, 13 * L, 156, -22 * L},
+                           {-13 * L, -3 * L * L, -22 * L, 4 * L * L}};
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) Ml[bi[i]][bi[j]] = mb * Mb[i][j];
+  double T[6][6];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) T[i][j] = 0.0;
+  for (int k = 0; k < 2; ++k) {
+    T[3 * k][3 * k] = c; T[3 * k][3 * k + 1] = s;
+    T[3 * k + 1][3 * k] = -s; T[3 * k + 1][3 * k + 1] = c;
+    T[3 * k + 2][3 * k + 2] = 1;
+  }
+  const int d0 = 3 * a;
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) {
+      double v = 0.0;
+      for (int k = 0; k < 6; ++k)
+        for (int l = 0; l < 6; ++l) v += T[k][i] * Ml[k][l] * T[l][j];
+      band(M, d0 + i, d0 + j) += v;
+    }
+}
+
+// Surface of the flag around the beam: bottom vertices 0..nn-1 (node order),
+// top vertices nn..2nn-1 (reverse node order), offset h/2 along the normal of
+// each cross-section.
+__device__ void flag_vertex(const BeamParams &p, const double *X, const double *u, const double *v,
+                            int j, double *xb, double *vb, double *xt, double *vt) {
+  const double th = u[3 * j + 2], om = v[3 * j + 2];
+  const double nx = -sin(th), ny = cos(th);
+  const double dnx = -cos(th) * om, dny = -sin(th) * om;
+  const double cx = X[2 * j] + u[3 * j], cy = X[2 * j + 1] + u[3 * j + 1];
+  xb[0] = cx - 0.5 * p.h * nx; xb[1] = cy - 0.5 * p.h * ny;
+  xt[0] = cx + 0.5 * p.h * nx; xt[1] = cy + 0.5 * p.h * ny;
+  vb[0] = v[3 * j] - 0.5 * p.h * dnx; vb[1] = v[3 * j + 1] - 0.5 * p.h * dny;
+  vt[0] = v[3 * j] + 0.5 * p.h * dnx; vt[1] = v[3 * j + 1] + 0.5 * p.h * dny;
+}
+
+// One structural step.  Loads F1 come from F1_in (standalone) or from the
+// momentum-exchange forces of the flag's surface vertices (coupled: vforce,
+// surf_x / surf_v of the whole surface, the flag's vertices start at v0).
+template <bool COUPLED>
+__global__ void __launch_bounds__(128)
+    k_beam_step(BeamParams p, BeamDev d, const double *__restrict__ F1_in,
+                const double *__restrict__ vforce, double *surf_x, double *surf_v, int v0) {
+  __shared__ double sJ[3 * kMaxBeamNodes * BW], sM[3 * kMaxBeamNodes * BW];
+  __shared__ double su[3 * kMaxBeamNodes], su0[3 * kMaxBeamNodes], sv0[3 * kMaxBeamNodes];
+  __shared__ double sf0[3 * kMaxBeamNodes], sf1[3 * kMaxBeamNodes], sF1[3 * kMaxBeamNodes];
+  __shared__ double sR[3 * kMaxBeamNodes], sX[2 * kMaxBeamNodes];
+  __shared__ double red[128];
+  __shared__ int s_done;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int nn = p.nn, n = 3 * nn, ne = nn - 1;
+  for (int i = tid; i < n; i += nt) {
+    su0[i] = d.u[i];
+    su[i] = d.u[i];
+    sv0[i] = d.v[i];
+    sf0[i] = 0.0;
+    sf1[i] = 0.0;
+  }
+  for (int i = tid; i < 2 * nn; i += nt) sX[i] = d.X[i];
+  for (int i = tid; i < n * BW; i += nt) sM[i] = 0.0;
+  __syncthreads();
+  // ---- mass matrix and f(u0), two colour passes
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int e = 2 * tid + pass; e < ne; e += 2 * nt) {
+      element_mass(p, sX, e, sM);
+      element_internal(p, sX, su0, e, sf0, nullptr);
+    }
+    __syncthreads();
+  }
+  // ---- loads F1
+  if (COUPLED) {
+    // nodal loads: the forces of the node's two surface vertices (their
+    // moments about the centre line are not transferred: the flag-tip
+    // rotation is a stiff mode that the staggered one-step lag destabilises)
+    for (int j = tid; j < nn; j += nt) {
+      const int vb = v0 + j, vt = v0 + 2 * nn - 1 - j;
+      sF1[3 * j] = vforce[3 * vb] + vforce[3 * vt];
+      sF1[3 * j + 1] = vforce[3 * vb + 1] + vforce[3 * vt + 1];
+      sF1[3 * j + 2] = 0.0;
+    }
+  } else {
+    for (int i = tid; i < n; i += nt) sF1[i] = F1_in[i];
+  }
+  __syncthreads();
+  // ---- Newton iterations with the constant relaxation lambda
+  double r0 = -1.0;
+  int it = 0, conv = 0;
+  for (it = 0; it < p.max_it; ++it) {
+    for (int i = tid; i < n; i += nt) sf1[i] = 0.0;
+    for (int i = tid; i < n * BW; i += nt) sJ[i] = 0.0;
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int e = 2 * tid + pass; e < ne; e += 2 * nt) element_internal(p, sX, su, e, sf1, sJ);
+      __syncthreads();
+    }
+    // residual
+    double part = 0.0;
+    for (int i = tid; i < n; i += nt) {
+      double mv = 0.0;
+      for (int j = (i - KB > 0 ? i - KB : 0); j <= (i + KB < n - 1 ? i + KB : n - 1); ++j) {
+        const double v1 = ((su[j] - su0[j]) / p.dt - (1.0 - p.theta) * sv0[j]) / p.theta;
+        mv += band(sM, i, j) * (v1 - sv0[j]);
+      }
+      double R = mv / p.dt - p.theta * (sF1[i] - sf1[i]) - (1.0 - p.theta) * (d.F0[i] - sf0[i]);
+      if (d.fixed[i]) R = 0.0;
+      sR[i] = R;
+      part += R * R;
+    }
+    red[tid] = part;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int k = 0; k < nt; ++k) t += red[k];
+      red[0] = sqrt(t);
+    }
+    __syncthreads();
+    const double rn = red[0];
+    if (r0 < 0) r0 = rn;
+    if (rn <= p.rtol * r0 + p.atol) {
+      conv = 1;
+      break;
+    }
+    // Jacobian M/(th dt^2) + th K with Dirichlet rows/columns
+    for (int idx = tid; idx < n * BW; idx += nt) {
+      const int i = idx / BW, j = i + idx % BW - KB;
+      double v = 0.0;
+      if (j >= 0 && j < n) v = sM[idx] / (p.theta * p.dt * p.dt) + p.theta * sJ[idx];
+      if (j >= 0 && j < n && (d.fixed[i] || d.fixed[j])) v = (i == j) ? 1.0 : 0.0;
+      sJ[idx] = v;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      // banded LU (Doolittle, no pivoting) on -R, in place
+      for (int i = 0; i < n; ++i) sR[i] = -sR[i];
+      for (int k = 0; k < n; ++k) {
+        const double piv = band(sJ, k, k);
+        const int iend = (k + KB < n - 1) ? k + KB : n - 1;
+        for (int i = k + 1; i <= iend; ++i) {
+          const double m = band(sJ, i, k) / piv;
+          if (m == 0.0) continue;
+          for (int j = k + 1; j <= iend; ++j) band(sJ, i, j) -= m * band(sJ, k, j);
+          sR[i] -= m * sR[k];
+        }
+      }
+      for (int k = n - 1; k >= 0; --k) {
+        double sum = sR[k];
+        const int jend = (k + KB < n - 1) ? k + KB : n - 1;
+        for (int j = k + 1; j <= jend; ++j) sum -= band(sJ, k, j) * sR[j];
+        sR[k] = sum / band(sJ, k, k);
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += nt) su[i] += p.lambda * sR[i];
+    __syncthreads();
+  }
+  // ---- final velocities, state, loads
+  for (int i = tid; i < n; i += nt) {
+    double ui = su[i], vi = ((su[i] - su0[i]) / p.dt - (1.0 - p.theta) * sv0[i]) / p.theta;
+    if (d.fixed[i]) { ui = 0.0; vi = 0.0; }
+    d.u[i] = ui;
+    d.v[i] = vi;
+    d.F0[i] = sF1[i];
+    su[i] = ui;
+    sR[i] = vi;
+  }
+  if (tid == 0) *d.iters = conv ? it : -it - 1;
+  __syncthreads();
+  if (COUPLED) {
+    // transfer displacement and velocity to the surface mesh
+    for (int j = tid; j < nn; j += nt) {
+      double xb[2], vb[2], xt[2], vt[2];
+      flag_vertex(p, sX, su, sR, j, xb, vb, xt, vt);
+      const int ib = v0 + j, it2 = v0 + 2 * nn - 1 - j;
+      surf_x[2 * ib] = xb[0]; surf_x[2 * ib + 1] = xb[1];
+      surf_v[2 * ib] = vb[0]; surf_v[2 * ib + 1] = vb[1];
+      surf_x[2 * it2] = xt[0]; surf_x[2 * it2 + 1] = xt[1];
+      surf_v[2 * it2] = vt[0]; surf_v[2 * it2 + 1] = vt[1];
+    }
+  }
+  (void)s_done;
+}
+
+}  // namespace kbc
+
+using namespace kbc;
+
+struct fem_ctx {
+  BeamParams p;
+  BeamDev d;
+  char *ws = nullptr;
+  bool own_ws = false;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  double *F1 = nullptr;   // staging of standalone loads
+  bool poisoned = false;
+  char msg[256] = {0};
+};
+
+static size_t fem_bytes(int nn) {
+  const size_t n = 3 * (size_t)nn;
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  return al(sizeof(double) * 2 * nn) + al(sizeof(int32_t) * n) + 4 * al(sizeof(double) * n) +
+         al(sizeof(int));
+}
+
+static thread_local char g_fem_msg[256];
+
+extern "C" {
+
+lbm_status fem_beam_workspace_size(const fem_beam_config *c, size_t *bytes) {
+  if (!c || !bytes || c->nn < 2 || c->nn > kMaxBeamNodes) return LBM_EINVAL;
+  *bytes = fem_bytes(c->nn);
+  return LBM_OK;
+}
+
+lbm_status fem_beam_create(const fem_beam_config *c, void *workspace, size_t bytes, fem_ctx **out) {
+  if (!out) return LBM_EINVAL;
+  *out = nullptr;
+  if (!c || c->nn < 2 || c->nn > kMaxBeamNodes || !c->X || !c->fixed ||
+      !(c->EA > 0 && c->EI > 0 && c->rhoA > 0 && c->thickness >= 0) ||
+      !(c->theta > 0 && c->theta <= 1) || !(c->lambda > 0 && c->lambda <= 1) || c->max_it < 1 ||
+      !(c->dt > 0)) {
+    snprintf(g_fem_msg, sizeof(g_fem_msg), "fem_beam_create: bad configuration (nn in [2, %d])",
+             kMaxBeamNodes);
+    return LBM_EINVAL;
+  }
+  fem_ctx *f = new (std::nothrow) fem_ctx();
+  if (!f) return LBM_ENOMEM;
+  const size_t need = fem_bytes(c->nn);
+  if (workspace) {
+    if (bytes < need || ((uintptr_t)workspace % 256) != 0) {
+      delete f;
+      snprintf(g_fem_msg, sizeof(g_fem_msg), "fem_beam_create: workspace needs %zu bytes", need);
+      return LBM_ENOMEM;
+    }
+    f->ws = (char *)workspace;
+  } else {
+    if (cudaMalloc((void **)&f->ws, need) != cudaSuccess) {
+      delete f;
+      return LBM_ENOMEM;
+    }
+    f->own_ws = true;
+  }
+  if (c->stream) {
+    f->stream = (cudaStream_t)c->stream;
+  } else {
+    cudaStreamCreateWithFlags(&f->stream, cudaStreamNonBlocking);
+    f->own_stream = true;
+  }
+  const int nn = c->nn;
+  const size_t n = 3 * (size_t)nn;
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  char *p = f->ws;
+  double *X = (double *)p; p += al(sizeof(double) * 2 * nn);
+  int32_t *fx = (int32_t *)p; p += al(sizeof(int32_t) * n);
+  double *u = (double *)p; p += al(sizeof(double) * n);
+  double *v = (double *)p; p += al(sizeof(double) * n);
+  double *F0 = (double *)p; p += al(sizeof(double) * n);
+  double *F1 = (double *)p; p += al(sizeof(double) * n);
+  int *iters = (int *)p;
+  f->p = BeamParams{nn, c->EA, c->EI, c->rhoA, c->thickness, c->theta, c->lambda, c->rtol,
+                    c->atol, c->dt, c->max_it};
+  f->d = BeamDev{X, fx, u, v, F0, iters};
+  f->F1 = F1;
+  cudaError_t e = cudaMemcpyAsync(X, c->X, sizeof(double) * 2 * nn, cudaMemcpyDefault, f->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(fx, c->fixed, sizeof(int32_t) * n, cudaMemcpyDefault, f->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(u, 0, sizeof(double) * n, f->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(v, 0, sizeof(double) * n, f->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(F0, 0, sizeof(double) * n, f->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(iters, 0, sizeof(int), f->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
+  if (e != cudaSuccess) {
+    snprintf(g_fem_msg, sizeof(g_fem_msg), "fem_beam_create: %s", cudaGetErrorString(e));
+    if (f->own_ws) cudaFree(f->ws);
+    delete f;
+    return LBM_ECUDA;
+  }
+  *out = f;
+  return LBM_OK;
+}
+
+#define FEM_CK(call)                                                             \
+  do {                                                                           \
+    cudaError_t e_ = (call);                                                     \
+    if (e_ != cudaSuccess) {                                                     \
+      f->poisoned = true;                                                        \
+      snprintf(f->msg, sizeof(f->msg), "%s: %s", #call, cudaGetErrorString(e_)); \
+      return LBM_ECUDA;                                                          \
+    }                                                                            \
+  } while (0)
+
+lbm_status fem_beam_step(fem_ctx *f, const double *F1) {
+  if (!f || !F1) return LBM_EINVAL;
+  if (f->poisoned) return LBM_ESTATE;
+  FEM_CK(cudaMemcpyAsync(f->F1, F1, sizeof(double) * 3 * f->p.nn, cudaMemcpyDefault, f->stream));
+  k_beam_step<false><<<1, 128, 0, f->stream>>>(f->p, f->d, f->F1, nullptr, nullptr, nullptr, 0);
+  FEM_CK(cudaGetLastError());
+  return LBM_OK;
+}
+
+lbm_status fem_beam_get_state(fem_ctx *f, double *u, double *v, int *iterations) {
+  if (!f) return LBM_EINVAL;
+  if (f->poisoned) return LBM_ESTATE;
+  const size_t n = 3 * (size_t)f->p.nn;
+  if (u) FEM_CK(cudaMemcpyAsync(u, f->d.u, sizeof(double) * n, cudaMemcpyDefault, f->stream));
+  if (v) FEM_CK(cudaMemcpyAsync(v, f->d.v, sizeof(double) * n, cudaMemcpyDefault, f->stream));
+  if (iterations)
+    FEM_CK(cudaMemcpyAsync(iterations, f->d.iters, sizeof(int), cudaMemcpyDefault, f->stream));
+  FEM_CK(cudaStreamSynchronize(f->stream));
+  return LBM_OK;
+}
+
+lbm_status fem_beam_set_state(fem_ctx *f, const double *u, const double *v, const double *F0) {
+  if (!f) return LBM_EINVAL;
+  if (f->poisoned) return LBM_ESTATE;
+  const size_t n = 3 * (size_t)f->p.nn;
+  if (u) FEM_CK(cudaMemcpyAsync(f->d.u, u, sizeof(double) * n, cudaMemcpyDefault, f->stream));
+  if (v) FEM_CK(cudaMemcpyAsync(f->d.v, v, sizeof(double) * n, cudaMemcpyDefault, f->stream));
+  if (F0) FEM_CK(cudaMemcpyAsync(f->d.F0, F0, sizeof(double) * n, cudaMemcpyDefault, f->stream));
+  FEM_CK(cudaStreamSynchronize(f->stream));
+  return LBM_OK;
+}
+
+const char *fem_last_error(const fem_ctx *f) { return f ? f->msg : g_fem_msg; }
+
+void fem_destroy(fem_ctx *f) {
+  if (!f) return;
+  if (f->stream) cudaStreamSynchronize(f->stream);
+  if (f->own_stream) cudaStreamDestroy(f->stream);
+  if (f->own_ws) cudaFree(f->ws);
+  delete f;
+}
+
+}  // extern "C"
+
+namespace kbc {
+
+int fem_nodes(const fem_ctx *f) { return f->p.nn; }
+
+// Coupled structural step on the lattice stream: loads from the surface
+// forces of vertices [v0, v0 + 2 nn), then the new flag surface.
+cudaError_t launch_beam_coupled(fem_ctx *f, const double *vforce, double *surf_x, double *surf_v,
+                                int v0, cudaStream_t s) {
+  k_beam_step<true><<<1, 128, 0, s>>>(f->p, f->d, nullptr, vforce, surf_x, surf_v, v0);
+  return cudaGetLastError();
+}
+
+// Flag surface of the current beam state (used when coupling starts).
+__global__ void k_flag_surface(BeamParams p, BeamDev d, double *surf_x, double *surf_v, int v0) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= p.nn) return;
+  double xb[2], vb[2], xt[2], vt[2];
+  flag_vertex(p, d.X, d.u, d.v, j, xb, vb, xt, vt);
+  const int ib = v0 + j, it = v0 + 2 * p.nn - 1 - j;
+  surf_x[2 * ib] = xb[0]; surf_x[2 * ib + 1] = xb[1];
+  surf_v[2 * ib] = vb[0]; surf_v[2 * ib + 1] = vb[1];
+  surf_x[2 * it] = xt[0]; surf_x[2 * it + 1] = xt[1];
+  surf_v[2 * it] = vt[0]; surf_v[2 * it + 1] = vt[1];
+}
+
+cudaError_t launch_flag_surface(fem_ctx *f, double *surf_x, double *surf_v, int v0,
+                                cudaStream_t s) {
+  k_flag_surface<<<1, 64, 0, s>>>(f->p, f->d, surf_x, surf_v, v0);
+  return cudaGetLastError();
+}
+
+}  // namespace kbc

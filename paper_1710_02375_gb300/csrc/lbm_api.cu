@@ -144,6 +144,8 @@ struct lbm_ctx {
   Band band{0, 0, 0, 0, 0, 0};
   int *counters = nullptr;   // [0] immersed nodes, [1] links, [2] fresh, [3] step
   BoundaryParams bp;
+  fem_ctx *fem = nullptr;    // coupled beam (conventional serial staggered loop)
+  int fem_v0 = 0;
   bool poisoned = false;
   char msg[512] = {0};
 };
@@ -363,6 +365,8 @@ lbm_status lbm_get_populations(lbm_ctx *ctx, double *f) {
   return LBM_OK;
 }
 
+static lbm_status run_geometry(lbm_ctx *ctx, int track_fresh);
+
 lbm_status lbm_step(lbm_ctx *ctx, int n) {
   GUARD();
   if (n < 0) return fail(ctx, LBM_EINVAL, "lbm_step: n < 0");
@@ -390,6 +394,14 @@ lbm_status lbm_step(lbm_ctx *ctx, int n) {
                     ctx->has_solid ? ctx->flags : nullptr, beta, bgk, ctx->err, ctx->stream,
                     ctx->sweep_variant));
     ctx->cur = 1 - ctx->cur;
+    if (ctx->fem) {
+      // structural step from this step's forces, transfer to the surface, new geometry
+      CK(launch_beam_coupled(ctx->fem, (const double *)(ctx->ws + ctx->lay.vforce),
+                             (double *)(ctx->ws + ctx->lay.sx), (double *)(ctx->ws + ctx->lay.sv),
+                             ctx->fem_v0, ctx->stream));
+      lbm_status st = run_geometry(ctx, 1);
+      if (st != LBM_OK) return st;
+    }
   }
   return LBM_OK;
 }
@@ -530,6 +542,25 @@ lbm_status lbm_set_inlet_profile(lbm_ctx *ctx, int face, const double *u) {
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->bp.inlet[face] = dst;
   return LBM_OK;
+}
+
+lbm_status fsi_couple(lbm_ctx *ctx, fem_ctx *f, int first_vertex) {
+  GUARD();
+  if (!f) {
+    ctx->fem = nullptr;
+    return LBM_OK;
+  }
+  if (ctx->Q != 9) return fail(ctx, LBM_EINVAL, "fsi_couple: the beam couples to D2Q9 lattices");
+  if (ctx->nbodies == 0) return fail(ctx, LBM_ESTATE, "fsi_couple: set the geometry first");
+  const int nn = fem_nodes(f);
+  if (first_vertex < 0 || first_vertex + 2 * nn > ctx->nv)
+    return fail(ctx, LBM_EINVAL, "fsi_couple: vertices [%d, %d) outside the surface (%d)",
+                first_vertex, first_vertex + 2 * nn, ctx->nv);
+  ctx->fem = f;
+  ctx->fem_v0 = first_vertex;
+  CK(launch_flag_surface(f, (double *)(ctx->ws + ctx->lay.sx), (double *)(ctx->ws + ctx->lay.sv),
+                         first_vertex, ctx->stream));
+  return run_geometry(ctx, 1);
 }
 
 lbm_status lbm_get_boundary_info(lbm_ctx *ctx, int *info) {

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/kbc_lbm.h"
 #include "boundary.cuh"
 #include "kbc_common.cuh"
 
@@ -72,5 +73,11 @@ cudaError_t launch_grad(int Q, int storage, const Grid &g, void *f, const uint8_
                         const Link *links, const BoundaryParams &bp, double *vforce,
                         double *bforce, int nbodies, cudaStream_t s);
 cudaError_t launch_step_counter(int *step, cudaStream_t s);
+
+int fem_nodes(const fem_ctx *f);
+cudaError_t launch_beam_coupled(fem_ctx *f, const double *vforce, double *surf_x, double *surf_v,
+                                int v0, cudaStream_t s);
+cudaError_t launch_flag_surface(fem_ctx *f, double *surf_x, double *surf_v, int v0,
+                                cudaStream_t s);
 
 }  // namespace kbc

@@ -306,3 +306,90 @@ class Lattice:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- structure
+def _fem_chk(f, st):
+    if st != LBM_OK:
+        raise LbmError(st, load().fem_last_error(f).decode(errors="replace"))
+
+
+def fem_beam_create(cfg, workspace_ptr, nbytes):
+    out = ctypes.c_void_p()
+    st = load().fem_beam_create(ctypes.byref(cfg), workspace_ptr, nbytes, ctypes.byref(out))
+    if st != LBM_OK:
+        raise LbmError(st, load().fem_last_error(None).decode())
+    return out.value
+
+
+def fem_beam_step(f, F1):
+    _fem_chk(f, load().fem_beam_step(f, _ptr(F1)))
+
+
+def fem_beam_get_state(f, u, v, iterations):
+    _fem_chk(f, load().fem_beam_get_state(f, _ptr(u), _ptr(v), _ptr(iterations)))
+
+
+def fem_beam_set_state(f, u, v, F0):
+    _fem_chk(f, load().fem_beam_set_state(f, _ptr(u), _ptr(v), _ptr(F0)))
+
+
+def fem_destroy(f):
+    if f:
+        load().fem_destroy(f)
+
+
+def fsi_couple(ctx, f, first_vertex):
+    _chk(ctx, load().fsi_couple(ctx, f, int(first_vertex)))
+
+
+class Beam:
+    """Owner of one GPU beam context (FP64 co-rotational beam, theta-scheme,
+    Newton with relaxation lambda); torch allocates the workspace."""
+
+    def __init__(self, X, EA, EI, rhoA, fixed, thickness=0.0, theta=0.5, lam=0.7, rtol=1e-10,
+                 atol=1e-13, max_it=200, dt=1.0, stream=None, device="cuda"):
+        import torch
+        from ._abi_ext import fem_beam_config
+        load()
+        self.X = np.ascontiguousarray(X, dtype=np.float64)
+        self.fixed = np.ascontiguousarray(fixed, dtype=np.int32)
+        self.nn = self.X.shape[0]
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=torch.device(device))
+        c = fem_beam_config()
+        c.nn = self.nn
+        c.X = self.X.ctypes.data
+        c.EA, c.EI, c.rhoA, c.thickness = EA, EI, rhoA, thickness
+        c.fixed = self.fixed.ctypes.data
+        c.theta, c.lambda_, c.rtol, c.atol, c.max_it, c.dt = theta, lam, rtol, atol, max_it, dt
+        c.stream = self.stream.cuda_stream
+        n = ctypes.c_size_t()
+        st = load().fem_beam_workspace_size(ctypes.byref(c), ctypes.byref(n))
+        if st != LBM_OK:
+            raise LbmError(st, "fem_beam_workspace_size")
+        self.workspace = torch.empty(n.value, dtype=torch.uint8, device=torch.device(device))
+        self.ctx = fem_beam_create(c, self.workspace.data_ptr(), n.value)
+
+    def step(self, F1):
+        fem_beam_step(self.ctx, np.ascontiguousarray(F1, dtype=np.float64))
+
+    def state(self):
+        u = np.zeros(3 * self.nn)
+        v = np.zeros(3 * self.nn)
+        it = np.zeros(1, dtype=np.int32)
+        fem_beam_get_state(self.ctx, u, v, it)
+        return u, v, int(it[0])
+
+    def set_state(self, u, v, F0):
+        fem_beam_set_state(self.ctx, *(np.ascontiguousarray(a, dtype=np.float64) for a in (u, v, F0)))
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            fem_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -158,3 +158,21 @@ def cylinder_flag_2d(cx=20.0, cy=20.0, d=10.0, flag_len=35.0, flag_h=2.0, n_cyl=
     e = np.concatenate([ec, ef + len(xc)])
     body = np.array([0] * len(ec) + [1] * len(ef), dtype=np.int32)
     return x, e, body, bx
+
+
+def c1_flag_beam(cx=20.0, cy=20.0, d=10.0, flag_len=35.0, flag_h=2.0, n_beam=20, u_max=0.05,
+                 Ae=1.4e3, density_ratio=10.0):
+    """Beam data of the C1 flag: reference nodes X[n_beam+1, 2] on the centre
+    line, EA, EI, rhoA per unit depth (E from the aeroelastic number
+    Ae = E / (rho_f U_mean^2), U_mean = 2/3 u_max, rho_f = 1) and the clamped
+    root mask."""
+    r = d / 2
+    x0 = cx + np.sqrt(r * r - (flag_h / 2) ** 2)
+    x1 = cx + r + flag_len
+    X = np.stack([np.linspace(x0, x1, n_beam + 1), np.full(n_beam + 1, cy)], axis=1)
+    U = 2.0 / 3.0 * u_max
+    E = Ae * U * U
+    A, I = flag_h, flag_h ** 3 / 12.0
+    fixed = np.zeros(3 * (n_beam + 1), np.int32)
+    fixed[:3] = 1
+    return X, E * A, E * I, density_ratio * A, fixed

@@ -45,8 +45,8 @@ def test_couette_face_walls():
 
 
 def slabs(nx, ny, y_lo, y_hi, U):
-    xa, ea = synth.rect_polygon(-3.0, -0.5, nx + 2.0, y_lo)
-    xb, eb = synth.rect_polygon(-3.0, y_hi, nx + 2.0, ny - 0.5)
+    xa, ea = synth.rect_polygon(-3.0, 0.0, nx + 2.0, y_lo)
+    xb, eb = synth.rect_polygon(-3.0, y_hi, nx + 2.0, float(ny))
     x = np.concatenate([xa, xb])
     e = np.concatenate([ea, eb + len(xa)])
     v = np.zeros_like(x)

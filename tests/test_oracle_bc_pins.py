@@ -33,10 +33,10 @@ def test_couette_face_walls_linear_profile():
 
 
 def slab_surface(nx, y_lo, y_hi, ny, U):
-    """Two x-invariant slabs: y in [-0.5, y_lo] at rest and y in [y_hi, ny - 0.5]
-    moving with U along x (periodic box)."""
-    xa, ea = synth.rect_polygon(-3.0, -0.5, nx + 2.0, y_lo)
-    xb, eb = synth.rect_polygon(-3.0, y_hi, nx + 2.0, ny - 0.5)
+    """Two x-invariant slabs: y in [0, y_lo] at rest and y in [y_hi, ny] moving
+    with U along x (periodic box; node y sits at y + 1/2)."""
+    xa, ea = synth.rect_polygon(-3.0, 0.0, nx + 2.0, y_lo)
+    xb, eb = synth.rect_polygon(-3.0, y_hi, nx + 2.0, float(ny))
     x = np.concatenate([xa, xb])
     e = np.concatenate([ea, eb + len(xa)])
     v = np.zeros_like(x)
@@ -58,7 +58,7 @@ def test_couette_immersed_walls_off_lattice(y_lo, y_hi):
     rho, u = orc.macros(9, f)
     H = y_hi - y_lo
     solid = orc.solid_mask((1, ny, nx), surf)[0, :, 1].astype(bool)
-    y = np.arange(ny)
+    y = np.arange(ny) + 0.5  # cell-centred node positions
     exact = U * (y - y_lo) / H
     err = np.max(np.abs(u[0, 0, :, 1] - exact)[~solid])
     assert err < 1e-3 * U, err
@@ -102,7 +102,7 @@ def test_circle_links_match_analytic_intersection():
     surf = orc.Surface(x, np.zeros_like(x), e, np.zeros(len(e), np.int32))
     shape = (1, 20, 21)
     solid = orc.solid_mask(shape, surf)[0]
-    Y, X = np.mgrid[0:20, 0:21]
+    Y, X = np.mgrid[0:20, 0:21] + 0.5
     d = np.hypot(X - cx, Y - cy)
     sag = R * (1 - np.cos(np.pi / n))
     far = np.abs(d - R) > 2 * sag
@@ -112,7 +112,7 @@ def test_circle_links_match_analytic_intersection():
     assert len(L["q"]) > 0 and np.all(L["elem"] >= 0)
     for k in range(len(L["q"])):
         node, i = L["node"][k], L["dir"][k]
-        p = np.array([node % 21, node // 21], dtype=float)
+        p = np.array([node % 21, node // 21], dtype=float) + 0.5
         dvec = -c[i, :2].astype(float)
         # |p + s d - c|^2 = R^2, smallest root in (0, 1]
         a = dvec @ dvec
@@ -128,7 +128,7 @@ def test_sphere_links_and_mask_3d():
     surf = orc.Surface(x, np.zeros_like(x), e, np.zeros(len(e), np.int32))
     shape = (12, 13, 13)
     solid = orc.solid_mask(shape, surf)
-    Z, Y, X = np.mgrid[0:12, 0:13, 0:13]
+    Z, Y, X = np.mgrid[0:12, 0:13, 0:13] + 0.5
     d = np.sqrt((X - cen[0]) ** 2 + (Y - cen[1]) ** 2 + (Z - cen[2]) ** 2)
     tol = 0.08  # mesh deviation from the sphere at level 3
     far = np.abs(d - R) > tol
@@ -138,7 +138,7 @@ def test_sphere_links_and_mask_3d():
     assert np.all(L["elem"] >= 0)
     for k in range(0, len(L["q"]), 7):
         node, i = L["node"][k], L["dir"][k]
-        p = np.array([node % 13, (node // 13) % 13, node // 169], dtype=float)
+        p = np.array([node % 13, (node // 13) % 13, node // 169], dtype=float) + 0.5
         dvec = -c[i].astype(float)
         a = dvec @ dvec
         b = 2 * dvec @ (p - cen)
