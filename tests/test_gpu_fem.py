@@ -47,7 +47,7 @@ def test_coupled_flag_c1_matches_oracle():
     h = 2.0
     ncyl = int(np.sum(body == 0))
     bc = (2, 3, 1, 1, 0, 0)
-    ramp, steps = 100, 400
+    ramp, steps = 1000, 600
     L = Lattice(9, nx, ny, 1, beta, bc=bc, max_links=4000, max_vertices=len(x),
                 max_elements=len(e), inlet_ramp_steps=ramp)
     L.set_inlet_profile(0, prof)
