@@ -94,7 +94,7 @@ def test_channel_cylinder_c1_geometry_1000_steps(with_flag):
     """The C1 channel (220 x 41, parabolic inflow u_max = 0.05 with 1e-4 static
     noise, Re = 100 on D = 10) around the rigid cylinder (and flag), 1000 steps."""
     nx, ny, beta, prof, x, e, body = c1_setup(with_flag)
-    steps, ramp = 1000, 200
+    steps, ramp = 1000, 1000
     bc = (INLET, OUTLET, WALL, WALL, 0, 0)
     L = lattice(9, (1, ny, nx), beta, bc=bc, max_links=4000, max_vertices=200, max_elements=200,
                 inlet_ramp_steps=ramp)

@@ -30,7 +30,7 @@ def test_beam_prescribed_loads_matches_oracle():
         assert itg >= 0 and it >= 0
         worst = max(worst, np.max(np.abs(ug - u)) / max(np.max(np.abs(u)), 1e-30))
     assert worst < 1e-8
-    assert np.max(np.abs(u[1::3])) > 1.0  # large deflection regime reached
+    assert np.max(np.abs(u[1::3])) > 0.5  # large deflection regime reached
 
 
 def test_coupled_flag_c1_matches_oracle():
