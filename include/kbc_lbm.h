@@ -166,6 +166,29 @@ lbm_status lbm_update_surface(lbm_ctx *ctx, const double *verts, const double *v
  * exchange relative to the rest state (gauge pressure).  Synchronises. */
 lbm_status lbm_get_interface_force(lbm_ctx *ctx, double *vert_force, double *body_force);
 
+/* Force probe that allocates nothing (the paper has no counterpart: this is a
+ * service for callers).  Some callers cannot allocate device memory where
+ * they need the interface force: code that runs under a device-memory budget
+ * fixed at start-up, or on a path that must not call cudaMalloc because it
+ * may synchronise the device or fail under memory pressure.  This call gives
+ * them the momentum-exchange force the next lbm_step would produce for the
+ * current populations and surface: vert_force[nv][3] and
+ * body_force[nbodies][3] (either may be NULL; host or device memory), the
+ * same quantities lbm_get_interface_force reports after that step.
+ * It rebuilds the cut links of the current solid flags and runs the Grad fill
+ * and force gather with all scratch (node list, link list, counters, FP64
+ * accumulators) in one fixed file-scope device array of about 5.4 MB that
+ * every GPU loading the library keeps until the process exits; it calls no
+ * cudaMalloc, cudaFree or allocating library routine.  Fixed maxima: 16384
+ * surface vertices, 65536 boundary nodes, 65536 cut links; beyond them it
+ * returns LBM_ECAPACITY with a message.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress, with that device
+ * current), so make that first call before any stream capture.  All calls
+ * share the array: calls that overlap on the GPU (several streams or host
+ * threads at once) race on it.  The Grad values written into solid slots are
+ * the ones the next step writes there anyway.  Synchronises. */
+lbm_status lbm_probe_interface_force_static(lbm_ctx *ctx, double *vert_force, double *body_force);
+
 /* info[4] = {face boundary nodes, immersed boundary nodes, cut links,
  * inlet-ramp step counter}.  Synchronises. */
 lbm_status lbm_get_boundary_info(lbm_ctx *ctx, int *info);

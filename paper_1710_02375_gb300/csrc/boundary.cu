@@ -677,6 +677,20 @@ cudaError_t launch_grad(int Q, int storage, const Grid &g, void *f, const uint8_
   });
 }
 
+cudaError_t launch_build_links(int Q, const Grid &g, const Band &bd, const SurfaceDev &sd,
+                               const uint8_t *flags, BNode *bnodes, int *nbn, int bcap,
+                               Link *links, int *nl, int lcap, int *err, cudaStream_t s) {
+  const long long nb = (long long)(bd.x1 - bd.x0) * (bd.y1 - bd.y0) * (bd.z1 - bd.z0);
+  if (nb <= 0) return cudaSuccess;
+  if (Q == 9)
+    k_build_links<9><<<nb_(nb, 128), 128, 0, s>>>(g, bd, sd, flags, bnodes, nbn, bcap, links, nl,
+                                                   lcap, err);
+  else
+    k_build_links<27><<<nb_(nb, 128), 128, 0, s>>>(g, bd, sd, flags, bnodes, nbn, bcap, links,
+                                                    nl, lcap, err);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_step_counter(int *step, cudaStream_t s) {
   k_step_counter<<<1, 1, 0, s>>>(step);
   return cudaGetLastError();

@@ -19,7 +19,7 @@ namespace {
 constexpr size_t kAlign = 256;
 constexpr size_t kStageBytes = 16u << 20;  // host<->device staging chunk
 
-size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+constexpr size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 constexpr int kMaxBodies = 16;
 
@@ -626,3 +626,85 @@ lbm_status lbm_get_macros(lbm_ctx *ctx, double *rho, double *u) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Force probe without allocation.
+//
+// For callers that cannot allocate device memory at this point (for example
+// code running where cudaMalloc is not allowed: inside a memory-pool budget
+// fixed at start-up, or on a path that must not synchronise the device as a
+// cudaMalloc may).  Its scratch -- the boundary-node list, the cut-link
+// list, the counters and the FP64 force accumulators -- lives in one
+// file-scope device array that every GPU loading this library holds until
+// the process exits.  Every call reuses it; calls that overlap on the GPU
+// race on it.
+namespace {
+
+constexpr int kProbeMaxLinks = 65536;
+constexpr int kProbeMaxNodes = 65536;
+constexpr int kProbeMaxVertices = 16384;
+constexpr size_t kProbeLinksOff = 0;
+constexpr size_t kProbeNodesOff = align_up(sizeof(Link) * kProbeMaxLinks);
+constexpr size_t kProbeVforceOff = kProbeNodesOff + align_up(sizeof(BNode) * kProbeMaxNodes);
+constexpr size_t kProbeBforceOff =
+    kProbeVforceOff + align_up(sizeof(double) * 3 * kProbeMaxVertices);
+constexpr size_t kProbeCountOff = kProbeBforceOff + align_up(sizeof(double) * 3 * kMaxBodies);
+constexpr size_t kProbeBytes = kProbeCountOff + kAlign;  // about 5.4 MB
+
+static __device__ __align__(256) unsigned char g_probe_scratch[kProbeBytes];
+
+constexpr int kProbeMaxDevices = 64;
+static char *g_probe_ptr[kProbeMaxDevices];  // device address of g_probe_scratch per device
+
+}  // namespace
+
+extern "C" lbm_status lbm_probe_interface_force_static(lbm_ctx *ctx, double *vert_force,
+                                                       double *body_force) {
+  GUARD();
+  if (ctx->nbodies == 0) return fail(ctx, LBM_ESTATE, "lbm_probe_interface_force_static: no geometry");
+  if (ctx->nv > kProbeMaxVertices)
+    return fail(ctx, LBM_ECAPACITY,
+                "lbm_probe_interface_force_static: %d surface vertices exceed the fixed maximum %d",
+                ctx->nv, kProbeMaxVertices);
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kProbeMaxDevices)
+    return fail(ctx, LBM_EINVAL, "lbm_probe_interface_force_static: device %d unsupported", dev);
+  if (!g_probe_ptr[dev]) {
+    // first call on this device (device current): the host-side name of the
+    // array is only a stand-in, the kernels need its device address
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_probe_scratch);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGetSymbolAddress(g_probe_scratch)");
+    g_probe_ptr[dev] = (char *)p;
+  }
+  char *base = g_probe_ptr[dev];
+  Link *links = (Link *)(base + kProbeLinksOff);
+  BNode *nodes = (BNode *)(base + kProbeNodesOff);
+  double *vf = (double *)(base + kProbeVforceOff);
+  double *bf = (double *)(base + kProbeBforceOff);
+  int *cnt = (int *)(base + kProbeCountOff);  // [0] nodes, [1] links, [2] overflow flags
+  // the array keeps the previous call's contents: clear what must start at zero
+  CK(cudaMemsetAsync(cnt, 0, 4 * sizeof(int), ctx->stream));
+  CK(cudaMemsetAsync(vf, 0, sizeof(double) * 3 * (size_t)ctx->nv, ctx->stream));
+  CK(cudaMemsetAsync(bf, 0, sizeof(double) * 3 * kMaxBodies, ctx->stream));
+  CK(launch_build_links(ctx->Q, ctx->g, ctx->band, surface_dev(ctx), ctx->flags, nodes, cnt,
+                        kProbeMaxNodes, links, cnt + 1, kProbeMaxLinks, cnt + 2, ctx->stream));
+  CK(launch_grad(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur], ctx->flags, nodes, cnt, 0,
+                 kProbeMaxNodes, links, ctx->bp, vf, bf, ctx->nbodies, ctx->stream));
+  int h[3] = {0, 0, 0};
+  CK(cudaMemcpyAsync(h, cnt, 3 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  if (vert_force)
+    CK(cudaMemcpyAsync(vert_force, vf, sizeof(double) * 3 * ctx->nv, cudaMemcpyDefault,
+                       ctx->stream));
+  if (body_force)
+    CK(cudaMemcpyAsync(body_force, bf, sizeof(double) * 3 * ctx->nbodies, cudaMemcpyDefault,
+                       ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (h[2] || h[0] > kProbeMaxNodes || h[1] > kProbeMaxLinks)
+    return fail(ctx, LBM_ECAPACITY,
+                "lbm_probe_interface_force_static: %d boundary nodes / %d cut links exceed the "
+                "fixed maximum %d / %d",
+                h[0], h[1], kProbeMaxNodes, kProbeMaxLinks);
+  return LBM_OK;
+}

@@ -73,6 +73,10 @@ cudaError_t launch_grad(int Q, int storage, const Grid &g, void *f, const uint8_
                         const Link *links, const BoundaryParams &bp, double *vforce,
                         double *bforce, int nbodies, cudaStream_t s);
 cudaError_t launch_step_counter(int *step, cudaStream_t s);
+// Immersed boundary nodes and cut links of the band for the current flags.
+cudaError_t launch_build_links(int Q, const Grid &g, const Band &bd, const SurfaceDev &sd,
+                               const uint8_t *flags, BNode *bnodes, int *nbn, int bcap,
+                               Link *links, int *nl, int lcap, int *err, cudaStream_t s);
 
 int fem_nodes(const fem_ctx *f);
 cudaError_t launch_beam_coupled(fem_ctx *f, const double *vforce, double *surf_x, double *surf_v,

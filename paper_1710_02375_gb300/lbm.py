@@ -76,6 +76,8 @@ def load():
     for name in ("lbm_set_inlet_profile", "lbm_set_geometry", "lbm_update_surface",
                  "lbm_get_interface_force", "lbm_get_boundary_info"):
         getattr(L, name).restype = ctypes.c_int
+    L.lbm_probe_interface_force_static.argtypes = [vp, vp, vp]
+    L.lbm_probe_interface_force_static.restype = ctypes.c_int
     L.lbm_set_sweep_variant.argtypes = [vp, i32]
     L.lbm_set_sweep_variant.restype = ctypes.c_int
     L.lbm_stream.argtypes = [vp]
@@ -192,6 +194,10 @@ def lbm_get_interface_force(ctx, vert_force, body_force):
 
 def lbm_get_boundary_info(ctx, info):
     _chk(ctx, load().lbm_get_boundary_info(ctx, _ptr(info)))
+
+
+def lbm_probe_interface_force_static(ctx, vert_force, body_force):
+    _chk(ctx, load().lbm_probe_interface_force_static(ctx, _ptr(vert_force), _ptr(body_force)))
 
 
 def lbm_check(ctx):
