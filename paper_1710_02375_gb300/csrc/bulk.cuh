@@ -28,6 +28,11 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t tx
                : "memory");
 }
 
+// Plain arrive (count 1) on the current phase.
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // Bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16),
 // completion signalled on bar as transaction bytes.
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,

@@ -52,7 +52,10 @@ __device__ __forceinline__ AxisEq axis_eq(float u) {
 // weights 1/feq_i (up to the common factor 1/rho, which cancels in gamma) as
 // products of per-axis factors, and <ds|dh> grouped by the six distinct
 // values of ds.
-template <class L>
+// CONSERVE: remove the FP32 rounding residue of mass and momentum from the
+// non-equilibrium part (used with FP32 storage, where it would otherwise be
+// the dominant error; with 16-bit storage the storage rounding dominates).
+template <class L, bool CONSERVE = true>
 __device__ __forceinline__ float collide(float (&g)[L::Q], float beta, bool bgk) {
   constexpr int Q = L::Q;
   constexpr int NR = Q / 3;  // rows of three x-neighbours (cy, cz)
@@ -168,7 +171,7 @@ __device__ __forceinline__ float collide(float (&g)[L::Q], float beta, bool bgk)
   // the conserved moments every step, so it is removed along W_i (1, 3 c_i).
   float qm = 0.f, qx = 0.f, qyp = 0.f, qym = 0.f, qzp = 0.f, qzm = 0.f;
 #pragma unroll
-  for (int r = 0; r < NR; ++r) {
+  for (int r = 0; r < (CONSERVE ? NR : 0); ++r) {
     const int cy = r % 3 - 1, cz = (L::D == 3) ? r / 3 - 1 : 0;
     const float m = df[3 * r] + df[3 * r + 1] + df[3 * r + 2];
     qm += m;

@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(256, 2)
                           xs[L::cx(i) + 1];
     v[i] = St::load(fin + (long long)i * g.N + src, (float)weight<L>(i));
   }
-  const float rho = collide<L>(v, beta, bgk != 0);
+  const float rho = collide<L, S == STORE_F32>(v, beta, bgk != 0);
   if (!(rho > 0.f && rho < 1e30f)) atomicOr(err, 1);
 #pragma unroll
   for (int i = 0; i < Q; ++i)
@@ -71,15 +71,22 @@ __global__ void __launch_bounds__(128, 4)
   using St = Store<S>;
   using T = typename St::T;
   extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)stages * Q * row_bytes);
-  const int tid = threadIdx.x;
+  // per stage: a "full" barrier (bulk copies landed) and an "empty" barrier
+  // (every warp has read the stage); no CTA-wide barrier inside the loop
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)stages * Q * row_bytes);
+  uint64_t *empty = full + stages;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int nwarps = (int)blockDim.x >> 5;
   const int nrows = g.ny * g.nz;
   if ((int)blockIdx.x >= nrows) return;
   const int my_rows = (nrows - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
   const int row_elems = row_bytes / (int)sizeof(T);
 
   if (tid == 0) {
-    for (int s = 0; s < stages; ++s) mbar_init(&bars[s], 1);
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], nwarps);
+    }
     fence_mbar_init();
   }
   __syncthreads();
@@ -87,13 +94,13 @@ __global__ void __launch_bounds__(128, 4)
   auto issue = [&](int j, int s) {
     const int r = (int)blockIdx.x + j * (int)gridDim.x;
     const int Y = r % g.ny + g.py, Z = r / g.ny + g.pz;
-    mbar_arrive_expect_tx(&bars[s], (uint32_t)(Q * row_bytes));
+    mbar_arrive_expect_tx(&full[s], (uint32_t)(Q * row_bytes));
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const int Ys = nbr(Y, -L::cy(i), g.NY);
       const int Zs = (L::D == 3) ? nbr(Z, -L::cz(i), g.NZ) : Z;
       const T *src = fin + (long long)i * g.N + ((long long)Zs * g.NY + Ys) * g.pitch;
-      bulk_g2s(smem + ((size_t)s * Q + i) * row_bytes, src, (uint32_t)row_bytes, &bars[s]);
+      bulk_g2s(smem + ((size_t)s * Q + i) * row_bytes, src, (uint32_t)row_bytes, &full[s]);
     }
   };
 
@@ -102,20 +109,18 @@ __global__ void __launch_bounds__(128, 4)
     for (int j = 0; j < pre; ++j) issue(j, j);
   }
   const int groups = (g.nx + (int)blockDim.x - 1) / (int)blockDim.x;
+  bool timed_out = false;
 
   for (int j = 0; j < my_rows; ++j) {
     const int s = j % stages;
-    const uint32_t parity = (uint32_t)((j / stages) & 1);
-    const bool timed_out = !mbar_wait_bounded(&bars[s], parity, kMaxSpins);
-    if (__syncthreads_or(timed_out)) {
-      // give up: flag it, let the copies already issued land, leave
-      if (tid == 0) {
-        atomicOr(err, 2);
-        for (int jj = j; jj < my_rows && jj < j + stages; ++jj)
-          mbar_wait_bounded(&bars[jj % stages], (uint32_t)((jj / stages) & 1), kMaxSpins);
-      }
-      __syncthreads();
-      return;
+    if (!mbar_wait_bounded(&full[s], (uint32_t)((j / stages) & 1), kMaxSpins)) timed_out = true;
+    // refill the stage released one row earlier (its readers are past it)
+    if (tid == 0 && j >= 1 && j - 1 + stages < my_rows) {
+      const int sp = (j - 1) % stages;
+      if (!mbar_wait_bounded(&empty[sp], (uint32_t)(((j - 1) / stages) & 1), kMaxSpins))
+        timed_out = true;
+      fence_proxy_async_smem();
+      issue(j - 1 + stages, sp);
     }
     const int r = (int)blockIdx.x + j * (int)gridDim.x;
     const int Y = r % g.ny + g.py, Z = r / g.ny + g.pz;
@@ -132,14 +137,11 @@ __global__ void __launch_bounds__(128, 4)
       for (int i = 0; i < Q; ++i)
         v[i] = St::load_smem(stage + i * row_elems + xs[L::cx(i) + 1], (float)weight<L>(i));
       if (grp == groups - 1) {
-        __syncthreads();  // every read of stage s is done
-        if (tid == 0 && j + stages < my_rows) {
-          fence_proxy_async_smem();
-          issue(j + stages, s);
-        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);  // this warp is done with the stage
       }
       if (active && (!FLAGS || flags[k0 + X] == NODE_FLUID)) {
-        const float rho = collide<L>(v, beta, bgk != 0);
+        const float rho = collide<L, S == STORE_F32>(v, beta, bgk != 0);
         if (!(rho > 0.f && rho < 1e30f)) atomicOr(err, 1);
 #pragma unroll
         for (int i = 0; i < Q; ++i)
@@ -147,6 +149,14 @@ __global__ void __launch_bounds__(128, 4)
       }
     }
   }
+  if (timed_out) atomicOr(err, 2);
+  // a copy can only still be in flight after a timed-out wait: let it land
+  // (bounded) before the CTA's shared memory is released
+  if (tid == 0 && timed_out)
+    for (int s = 0; s < stages; ++s) {
+      const int jl = my_rows - 1 - ((my_rows - 1 - s) % stages + stages) % stages;
+      if (jl >= 0) mbar_wait_bounded(&full[s], (uint32_t)((jl / stages) & 1), kMaxSpins);
+    }
 }
 
 struct RowPlan {
@@ -166,7 +176,7 @@ static RowPlan plan_rows(const Grid &g) {
   auto kern = k_sweep_rows<Q, S, FLAGS>;
   int best_score = 0;
   for (int st = 4; st >= 2; --st) {
-    const size_t smem = (size_t)st * Q * p.row_bytes + (size_t)st * sizeof(uint64_t);
+    const size_t smem = (size_t)st * Q * p.row_bytes + 2 * (size_t)st * sizeof(uint64_t);
     if (smem > (size_t)smem_optin) continue;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess) {

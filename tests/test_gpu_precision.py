@@ -1,0 +1,50 @@
+"""Reduced-precision storage (populations kept as f/W - 1 in FP16 or BF16,
+arithmetic in FP32) against the FP64 oracle; the stated bound for
+reduced-precision storage is a relative velocity error <= 1e-3."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1710_02375_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+F16, BF16 = 1, 2
+
+
+def make(lat, shape, beta, **kw):
+    from paper_1710_02375_gb300.lbm import Lattice
+    nz, ny, nx = shape
+    return Lattice(lat, nx, ny, nz, beta, **kw)
+
+
+@pytest.mark.parametrize("storage,bits", [(F16, 11), (BF16, 8)])
+def test_encoding_roundtrip(storage, bits):
+    """Stored value h = f/W - 1 rounds to nearest: |f_back - f| <= W |h| 2^-bits."""
+    lat, shape = 27, (3, 4, 5)
+    f0 = synth.random_state(lat, shape, 0.05, 9)
+    L = make(lat, shape, 0.9, storage=storage)
+    L.set_populations(f0)
+    got = L.get_populations()
+    w = synth.lattice_weights(lat).reshape((lat, 1, 1, 1))
+    h = f0 / w - 1
+    assert np.all(np.abs(got - f0) <= w * np.abs(h) * 2.0 ** -bits * 1.0001 + 1e-300)
+
+
+@pytest.mark.parametrize("lat,shape,nu", [(27, (16, 20, 24), 0.002), (9, (1, 48, 64), 0.005)])
+@pytest.mark.parametrize("storage", [F16, BF16])
+def test_taylor_green_1000_steps_reduced_storage(lat, shape, nu, storage):
+    nz, ny, nx = shape
+    rho, u = synth.tgv_fields(nx, ny, nz, 0.05, three_d=(lat == 27))
+    dim = 2 if lat == 9 else 3
+    beta = 1.0 / (6.0 * nu + 1.0)
+    L = make(lat, shape, beta, storage=storage)
+    L.init_equilibrium(rho, np.ascontiguousarray(u[:dim]))
+    L.step(1000)
+    L.check()
+    _, ug = L.macros()
+    f = orc.run_periodic(lat, beta, orc.init_equilibrium(lat, rho, u[:dim]), 1000)
+    _, uo = orc.macros(lat, f)
+    err = np.max(np.abs(ug - uo[:dim])) / np.max(np.abs(uo))
+    bound = 1e-3 if storage == F16 else 2e-2
+    print(f"storage {storage} lattice {lat}: relative velocity error {err:.3e}")
+    assert err <= bound, err
