@@ -120,12 +120,17 @@ __device__ __forceinline__ float collide(float (&g)[L::Q], float beta, bool bgk)
   }
 
   // ---- per-direction non-equilibrium part and the entropic products
-  float exy[9], mxy[9];
+  // (1 + e_x)(1 + e_y) - 1 = e_x + e_y (1 + e_x), and likewise with e_z
+  float exy[9], qxy[9], mxy[9];
+  float px1[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) px1[a] = 1.0f + ax.e[a];
 #pragma unroll
   for (int b = 0; b < 3; ++b)
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      exy[3 * b + a] = fmaf(ax.e[a], ay.e[b], ax.e[a] + ay.e[b]);
+      exy[3 * b + a] = fmaf(ay.e[b], px1[a], ax.e[a]);
+      if (L::D == 3) qxy[3 * b + a] = 1.0f + exy[3 * b + a];
       mxy[3 * b + a] = ax.r[a] * ay.r[b];
     }
   float df[Q];
@@ -137,8 +142,7 @@ __device__ __forceinline__ float collide(float (&g)[L::Q], float beta, bool bgk)
     const int k2 = 3 * (cy + 1) + (cx + 1);
     float e = exy[k2], m = mxy[k2];
     if (L::D == 3) {
-      const float ez = az.e[cz + 1];
-      e = fmaf(e, ez, e + ez);
+      e = fmaf(az.e[cz + 1], qxy[k2], e);
       m *= az.r[cz + 1];
     }
     // feq_i - W_i = W_i (drho + rho e_i);  df_i = g_i - (feq_i - W_i)
@@ -189,6 +193,16 @@ __device__ __forceinline__ float collide(float (&g)[L::Q], float beta, bool bgk)
   float bs[6];
 #pragma unroll
   for (int k = 0; k < 6; ++k) bs[k] = b2g * sv[k];
+  // projection term A + c_i.B built row by row: (cy, cz) part once per row
+  float tyz[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    const int cy = r % 3 - 1, cz = (L::D == 3) ? r / 3 - 1 : 0;
+    float t = A;
+    if (cy) t += cy * By;
+    if (cz) t += cz * Bz;
+    tyz[r] = t;
+  }
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
@@ -200,11 +214,12 @@ __device__ __forceinline__ float collide(float (&g)[L::Q], float beta, bool bgk)
       else if (cx && cz) sds = cx * cz * bs[4];
       else sds = cy * cz * bs[5];
     }
-    float t = A;
-    if (cy) t += cy * By;
-    if (cz) t += cz * Bz;
-    if (cx) t += cx * Bx;
-    g[i] = g[i] - fmaf(bg, df[i], fmaf(-(float)weight<L>(i), t, sds));
+    if (CONSERVE) {
+      float t = tyz[i / 3];
+      if (cx) t += cx * Bx;
+      sds = fmaf(-(float)weight<L>(i), t, sds);
+    }
+    g[i] = g[i] - fmaf(bg, df[i], sds);
   }
   return rho;
 }

@@ -13,10 +13,16 @@
 
 #include <string.h>
 
+// Resident CTAs per SM the register allocation is sized for (128 threads
+// each): five keep the D3Q27 kernels at <= 96 registers without spills.
+#ifndef KBC_MIN_CTAS
+#define KBC_MIN_CTAS 5
+#endif
+
 namespace kbc {
 
 template <int Q, int S, bool FLAGS>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(128, KBC_MIN_CTAS)
     k_sweep(Grid g, const typename Store<S>::T *__restrict__ fin,
             typename Store<S>::T *__restrict__ fout, const uint8_t *__restrict__ flags,
             float beta, int bgk, int *__restrict__ err) {
@@ -46,9 +52,9 @@ __global__ void __launch_bounds__(256, 2)
   }
   const float rho = collide<L, S == STORE_F32>(v, beta, bgk != 0);
   if (!(rho > 0.f && rho < 1e30f)) atomicOr(err, 1);
+  typename St::T *po = fout + k;
 #pragma unroll
-  for (int i = 0; i < Q; ++i)
-    St::store(fout + (long long)i * g.N + k, v[i], (float)(1.0 / weight<L>(i)));
+  for (int i = 0; i < Q; ++i, po += g.N) St::store(po, v[i], (float)(1.0 / weight<L>(i)));
 }
 
 
@@ -63,7 +69,7 @@ __global__ void __launch_bounds__(256, 2)
 constexpr uint32_t kMaxSpins = 1u << 22;  // bounded mbarrier waits
 
 template <int Q, int S, bool FLAGS>
-__global__ void __launch_bounds__(128, 4)
+__global__ void __launch_bounds__(128, KBC_MIN_CTAS)
     k_sweep_rows(Grid g, const typename Store<S>::T *__restrict__ fin,
                  typename Store<S>::T *__restrict__ fout, const uint8_t *__restrict__ flags,
                  float beta, int bgk, int *__restrict__ err, int row_bytes, int stages) {
@@ -143,9 +149,9 @@ __global__ void __launch_bounds__(128, 4)
       if (active && (!FLAGS || flags[k0 + X] == NODE_FLUID)) {
         const float rho = collide<L, S == STORE_F32>(v, beta, bgk != 0);
         if (!(rho > 0.f && rho < 1e30f)) atomicOr(err, 1);
+        T *po = fout + k0 + X;
 #pragma unroll
-        for (int i = 0; i < Q; ++i)
-          St::store(fout + (long long)i * g.N + k0 + X, v[i], (float)(1.0 / weight<L>(i)));
+        for (int i = 0; i < Q; ++i, po += g.N) St::store(po, v[i], (float)(1.0 / weight<L>(i)));
       }
     }
   }
@@ -228,9 +234,9 @@ static cudaError_t sweep_rows_t(const Grid &g, const void *fin, void *fout, cons
 }
 
 static dim3 sweep_block(const Grid &g) {
-  if (g.nx >= 128) return dim3(128, 2, 1);
-  if (g.nx >= 64) return dim3(64, 4, 1);
-  return dim3(32, 8, 1);
+  if (g.nx >= 128) return dim3(128, 1, 1);
+  if (g.nx >= 64) return dim3(64, 2, 1);
+  return dim3(32, 4, 1);
 }
 
 template <int Q, int S>
