@@ -249,11 +249,11 @@ lbm_status fsi_couple(lbm_ctx *ctx, fem_ctx *f, int first_vertex);
  * state (FP64 outputs; solid nodes give rho = 0, u = 0).  Synchronises. */
 lbm_status lbm_get_macros(lbm_ctx *ctx, double *rho, double *u);
 
-/* Kernel form of the fused sweep.  AUTO (default) and ROWS use the persistent
- * row-staged kernel (bulk asynchronous copies of the Q source rows of every
- * output row into shared memory, mbarrier pipeline) when its shared-memory
- * plan fits the device, else the direct kernel (one thread per node, Q
- * global loads).  Results are identical.  LBM_EINVAL for an unknown value. */
+/* Kernel form of the fused sweep.  AUTO (default) and DIRECT: one thread per
+ * node, Q coalesced global loads and stores.  ROWS: a persistent kernel that
+ * fetches the Q source rows of every output row into shared memory with bulk
+ * asynchronous copies (mbarrier pipeline), when its shared-memory plan fits
+ * the device.  Results are identical.  LBM_EINVAL for an unknown value. */
 enum { LBM_SWEEP_AUTO = 0, LBM_SWEEP_DIRECT = 1, LBM_SWEEP_ROWS = 2 };
 lbm_status lbm_set_sweep_variant(lbm_ctx *ctx, int variant);
 

@@ -243,7 +243,7 @@ template <int Q, int S>
 static cudaError_t sweep_t(const Grid &g, const void *fin, void *fout, const uint8_t *flags,
                            float beta, int bgk, int *err, cudaStream_t s, int variant) {
   using T = typename Store<S>::T;
-  if (variant != SWEEP_DIRECT) {
+  if (variant == SWEEP_ROWS) {
     bool used = false;
     cudaError_t e = sweep_rows_t<Q, S>(g, fin, fout, flags, beta, bgk, err, s, &used);
     if (e != cudaSuccess || used) return e;

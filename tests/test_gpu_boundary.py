@@ -140,10 +140,10 @@ def test_channel_cylinder_c1_1000_steps_within_oracle_spread():
     outlet amplifies perturbations (a 1e-8 relative perturbation of the oracle's
     own initial state grows to ~6e-4 by step 1000), so the GPU is held to the
     oracle's own sensitivity there: error <= max(1e-5, 3 x the spread between
-    the oracle and its perturbed copy)."""
+    the oracle and a copy perturbed at the FP32 level, 1e-7 relative)."""
     ug, _, _, _ = gpu_c1(False, 1000)
     uo, _, _, _ = run_c1(False, 1000)
-    up, _, _, _ = run_c1(False, 1000, perturb=1e-8)
+    up, _, _, _ = run_c1(False, 1000, perturb=1e-7)
     spread = rel(up, uo)
     assert rel(ug, uo) <= max(1e-5, 3 * spread), (rel(ug, uo), spread)
 
