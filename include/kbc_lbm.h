@@ -245,6 +245,13 @@ void fem_destroy(fem_ctx *f);
  * The fem context must stay alive while coupled.  LBM_EINVAL on a bad range. */
 lbm_status fsi_couple(lbm_ctx *ctx, fem_ctx *f, int first_vertex);
 
+/* Advance n * repeats steps by replaying a CUDA graph of n steps (n even, so
+ * the two population buffers return to their roles).  The graph is captured
+ * on the first call and again after any call that changes what a step
+ * launches (geometry, coupling, inlet profile, sweep variant) or when n
+ * changes.  Same results as lbm_step; no host work per step.  Asynchronous. */
+lbm_status lbm_step_graph(lbm_ctx *ctx, int n, int repeats);
+
 /* Density rho[nz][ny][nx] and velocity u[dim][nz][ny][nx] of the current
  * state (FP64 outputs; solid nodes give rho = 0, u = 0).  Synchronises. */
 lbm_status lbm_get_macros(lbm_ctx *ctx, double *rho, double *u);
@@ -253,8 +260,11 @@ lbm_status lbm_get_macros(lbm_ctx *ctx, double *rho, double *u);
  * node, Q coalesced global loads and stores.  ROWS: a persistent kernel that
  * fetches the Q source rows of every output row into shared memory with bulk
  * asynchronous copies (mbarrier pipeline), when its shared-memory plan fits
- * the device.  Results are identical.  LBM_EINVAL for an unknown value. */
-enum { LBM_SWEEP_AUTO = 0, LBM_SWEEP_DIRECT = 1, LBM_SWEEP_ROWS = 2 };
+ * the device.  ASYNC (FP32 storage): each thread prefetches the 27 source
+ * values of its node in the next row with per-thread asynchronous copies into
+ * shared memory while it collides the current one (other storage: DIRECT).
+ * Results are identical.  LBM_EINVAL for an unknown value. */
+enum { LBM_SWEEP_AUTO = 0, LBM_SWEEP_DIRECT = 1, LBM_SWEEP_ROWS = 2, LBM_SWEEP_ASYNC = 3 };
 lbm_status lbm_set_sweep_variant(lbm_ctx *ctx, int variant);
 
 /* Wait for the stream and report LBM_EUNSTABLE if any sweep since the last

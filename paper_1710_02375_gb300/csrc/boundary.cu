@@ -660,10 +660,17 @@ cudaError_t launch_grad(int Q, int storage, const Grid &g, void *f, const uint8_
   if (cap <= 0) return cudaSuccess;
   KBC_DISPATCH(Q, storage, {
     using T = typename Store<SS>::T;
-    // face nodes in FP32 arithmetic (their count scales with the lattice faces)
+    // face nodes: FP64 arithmetic on 2-D lattices, FP32 on 3-D ones (where
+    // their count scales with the lattice faces)
     if (nfixed > 0) {
-      k_grad<QQ, SS, float><<<nb_(nfixed, 128), 128, 0, s>>>(
-          g, (T *)f, flags, bnodes, nullptr, nfixed, cap, 0, nfixed, links, bp, vforce, bforce, 0);
+      if (QQ == 9)
+        k_grad<QQ, SS, double><<<nb_(nfixed, 128), 128, 0, s>>>(
+            g, (T *)f, flags, bnodes, nullptr, nfixed, cap, 0, nfixed, links, bp, vforce, bforce,
+            0);
+      else
+        k_grad<QQ, SS, float><<<nb_(nfixed, 128), 128, 0, s>>>(
+            g, (T *)f, flags, bnodes, nullptr, nfixed, cap, 0, nfixed, links, bp, vforce, bforce,
+            0);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }

@@ -233,6 +233,82 @@ static cudaError_t sweep_rows_t(const Grid &g, const void *fin, void *fout, cons
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- prefetching sweep
+// FP32 form with per-thread double buffering: while a thread collides the
+// node of row j, cp.async copies of the 27 source values of its node in row
+// j+1 are already in flight into shared memory, so the memory pipeline stays
+// full without holding registers.  A CTA owns one x-segment of 128 nodes over
+// `rows_per_cta` consecutive interior rows; no CTA barriers.
+template <int Q, bool FLAGS>
+__global__ void __launch_bounds__(128, KBC_MIN_CTAS)
+    k_sweep_async(Grid g, const float *__restrict__ fin, float *__restrict__ fout,
+                  const uint8_t *__restrict__ flags, float beta, int bgk, int *__restrict__ err,
+                  int rows_per_cta) {
+  using L = Lat<Q>;
+  __shared__ float buf[2][Q][128];
+  const int tid = threadIdx.x;
+  const int x = blockIdx.x * 128 + tid;
+  const bool active = x < g.nx;
+  const int X = (active ? x : 0) + g.px;
+  const int xs[3] = {nbr(X, 1, g.NX), X, nbr(X, -1, g.NX)};
+  const int nrows = g.ny * g.nz;
+  const int r0 = blockIdx.y * rows_per_cta;
+  const int rend = min(r0 + rows_per_cta, nrows);
+
+  auto prefetch = [&](int r, int b) {
+    const int Y = r % g.ny + g.py, Z = r / g.ny + g.pz;
+    const int ys[3] = {nbr(Y, 1, g.NY), Y, nbr(Y, -1, g.NY)};
+    int zs[3] = {Z, Z, Z};
+    if (L::D == 3) {
+      zs[0] = nbr(Z, 1, g.NZ);
+      zs[2] = nbr(Z, -1, g.NZ);
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const long long src = ((long long)zs[L::cz(i) + 1] * g.NY + ys[L::cy(i) + 1]) * g.pitch +
+                            xs[L::cx(i) + 1];
+      cp_async4(&buf[b][i][tid], fin + (long long)i * g.N + src);
+    }
+  };
+
+  if (r0 < rend) prefetch(r0, 0);
+  cp_async_commit();
+  for (int r = r0; r < rend; ++r) {
+    const int b = (r - r0) & 1;
+    if (r + 1 < rend) prefetch(r + 1, b ^ 1);
+    cp_async_commit();
+    cp_async_wait1();  // this thread's copies of row r have landed
+    float v[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) v[i] = buf[b][i][tid];
+    const int Y = r % g.ny + g.py, Z = r / g.ny + g.pz;
+    const long long k = sidx(g, X, Y, Z);
+    if (active && (!FLAGS || flags[k] == NODE_FLUID)) {
+      const float rho = collide<L, true>(v, beta, bgk != 0);
+      if (!(rho > 0.f && rho < 1e30f)) atomicOr(err, 1);
+      float *po = fout + k;
+#pragma unroll
+      for (int i = 0; i < Q; ++i, po += g.N) *po = v[i];
+    }
+  }
+}
+
+template <int Q>
+static cudaError_t sweep_async_t(const Grid &g, const void *fin, void *fout, const uint8_t *flags,
+                                 float beta, int bgk, int *err, cudaStream_t s) {
+  const int rows_per_cta = 8;
+  const int nrows = g.ny * g.nz;
+  dim3 grid((g.nx + 127) / 128, (nrows + rows_per_cta - 1) / rows_per_cta, 1);
+  if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+  if (flags)
+    k_sweep_async<Q, true><<<grid, 128, 0, s>>>(g, (const float *)fin, (float *)fout, flags, beta,
+                                                bgk, err, rows_per_cta);
+  else
+    k_sweep_async<Q, false><<<grid, 128, 0, s>>>(g, (const float *)fin, (float *)fout, flags, beta,
+                                                 bgk, err, rows_per_cta);
+  return cudaGetLastError();
+}
+
 static dim3 sweep_block(const Grid &g) {
   if (g.nx >= 128) return dim3(128, 1, 1);
   if (g.nx >= 64) return dim3(64, 2, 1);
@@ -243,6 +319,9 @@ template <int Q, int S>
 static cudaError_t sweep_t(const Grid &g, const void *fin, void *fout, const uint8_t *flags,
                            float beta, int bgk, int *err, cudaStream_t s, int variant) {
   using T = typename Store<S>::T;
+  if (variant == SWEEP_ASYNC && S == STORE_F32 &&
+      (long long)g.ny * g.nz <= 65535LL * 8)
+    return sweep_async_t<Q>(g, fin, fout, flags, beta, bgk, err, s);
   if (variant == SWEEP_ROWS) {
     bool used = false;
     cudaError_t e = sweep_rows_t<Q, S>(g, fin, fout, flags, beta, bgk, err, s, &used);

@@ -146,6 +146,10 @@ struct lbm_ctx {
   BoundaryParams bp;
   fem_ctx *fem = nullptr;    // coupled beam (conventional serial staggered loop)
   int fem_v0 = 0;
+  // CUDA graph of graph_n steps (replayed by lbm_step_graph)
+  cudaGraphExec_t gexec = nullptr;
+  int graph_n = 0;
+  bool graph_dirty = true;
   bool poisoned = false;
   char msg[512] = {0};
 };
@@ -279,6 +283,7 @@ void *lbm_stream(const lbm_ctx *ctx) { return ctx ? (void *)ctx->stream : nullpt
 void lbm_destroy(lbm_ctx *ctx) {
   if (!ctx) return;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   if (ctx->own_ws) cudaFree(ctx->ws);
   delete ctx;
@@ -478,6 +483,7 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, int nbodies, const double *verts, int 
   }
   if (dim == 2) { b0[2] = 0; b1[2] = 1; }
   ctx->band = Band{b0[0], b1[0], b0[1], b1[1], b0[2], b1[2]};
+  ctx->graph_dirty = true;
   ctx->nbodies = nbodies;
   ctx->nv = nv;
   ctx->ne = ne;
@@ -541,6 +547,7 @@ lbm_status lbm_set_inlet_profile(lbm_ctx *ctx, int face, const double *u) {
   CK(cudaMemcpyAsync(dst, hf.data(), sizeof(float) * 3 * n, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->bp.inlet[face] = dst;
+  ctx->graph_dirty = true;
   return LBM_OK;
 }
 
@@ -548,6 +555,7 @@ lbm_status fsi_couple(lbm_ctx *ctx, fem_ctx *f, int first_vertex) {
   GUARD();
   if (!f) {
     ctx->fem = nullptr;
+    ctx->graph_dirty = true;
     return LBM_OK;
   }
   if (ctx->Q != 9) return fail(ctx, LBM_EINVAL, "fsi_couple: the beam couples to D2Q9 lattices");
@@ -558,6 +566,7 @@ lbm_status fsi_couple(lbm_ctx *ctx, fem_ctx *f, int first_vertex) {
                 first_vertex, first_vertex + 2 * nn, ctx->nv);
   ctx->fem = f;
   ctx->fem_v0 = first_vertex;
+  ctx->graph_dirty = true;
   CK(launch_flag_surface(f, (double *)(ctx->ws + ctx->lay.sx), (double *)(ctx->ws + ctx->lay.sv),
                          first_vertex, ctx->stream));
   return run_geometry(ctx, 1);
@@ -576,11 +585,42 @@ lbm_status lbm_get_boundary_info(lbm_ctx *ctx, int *info) {
   return LBM_OK;
 }
 
+lbm_status lbm_step_graph(lbm_ctx *ctx, int n, int repeats) {
+  GUARD();
+  if (n <= 0 || (n & 1) || repeats < 0)
+    return fail(ctx, LBM_EINVAL, "lbm_step_graph: n must be even and positive, repeats >= 0");
+  if (ctx->graph_dirty || ctx->graph_n != n || !ctx->gexec) {
+    if (ctx->gexec) {
+      cudaGraphExecDestroy(ctx->gexec);
+      ctx->gexec = nullptr;
+    }
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed));
+    const int cur0 = ctx->cur;
+    lbm_status st = lbm_step(ctx, n);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+    ctx->cur = cur0;  // an even number of steps returns to the same buffer
+    if (st != LBM_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&ctx->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+    ctx->graph_n = n;
+    ctx->graph_dirty = false;
+  }
+  for (int r = 0; r < repeats; ++r) CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
+  return LBM_OK;
+}
+
 lbm_status lbm_set_sweep_variant(lbm_ctx *ctx, int variant) {
   GUARD();
-  if (variant < LBM_SWEEP_AUTO || variant > LBM_SWEEP_ROWS)
+  if (variant < LBM_SWEEP_AUTO || variant > LBM_SWEEP_ASYNC)
     return fail(ctx, LBM_EINVAL, "lbm_set_sweep_variant: unknown variant %d", variant);
   ctx->sweep_variant = variant;
+  ctx->graph_dirty = true;
   return LBM_OK;
 }
 

@@ -28,7 +28,7 @@ namespace kbc {
 // Fused pull-stream + KBC collision over all interior nodes (solid nodes are
 // skipped when flags != nullptr).  fin / fout: population buffers in storage
 // layout [Q][NZ][NY][NX].  err: device word, bit 0 set on a bad density.
-enum { SWEEP_AUTO = 0, SWEEP_DIRECT = 1, SWEEP_ROWS = 2 };
+enum { SWEEP_AUTO = 0, SWEEP_DIRECT = 1, SWEEP_ROWS = 2, SWEEP_ASYNC = 3 };
 // variant: SWEEP_ROWS uses the row-staged bulk-copy kernel when its
 // shared-memory plan fits (else the direct kernel); SWEEP_AUTO and
 // SWEEP_DIRECT use the direct kernel (faster on GB300 at 96 registers).

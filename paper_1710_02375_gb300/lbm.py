@@ -76,6 +76,8 @@ def load():
     for name in ("lbm_set_inlet_profile", "lbm_set_geometry", "lbm_update_surface",
                  "lbm_get_interface_force", "lbm_get_boundary_info"):
         getattr(L, name).restype = ctypes.c_int
+    L.lbm_step_graph.argtypes = [vp, i32, i32]
+    L.lbm_step_graph.restype = ctypes.c_int
     L.lbm_probe_interface_force_static.argtypes = [vp, vp, vp]
     L.lbm_probe_interface_force_static.restype = ctypes.c_int
     L.lbm_set_sweep_variant.argtypes = [vp, i32]
@@ -164,11 +166,15 @@ def lbm_step(ctx, n: int):
     _chk(ctx, load().lbm_step(ctx, int(n)))
 
 
+def lbm_step_graph(ctx, n: int, repeats: int):
+    _chk(ctx, load().lbm_step_graph(ctx, int(n), int(repeats)))
+
+
 def lbm_get_macros(ctx, rho, u):
     _chk(ctx, load().lbm_get_macros(ctx, _ptr(rho), _ptr(u)))
 
 
-LBM_SWEEP_AUTO, LBM_SWEEP_DIRECT, LBM_SWEEP_ROWS = 0, 1, 2
+LBM_SWEEP_AUTO, LBM_SWEEP_DIRECT, LBM_SWEEP_ROWS, LBM_SWEEP_ASYNC = 0, 1, 2, 3
 
 
 def lbm_set_sweep_variant(ctx, variant: int):
@@ -261,6 +267,9 @@ class Lattice:
 
     def step(self, n=1):
         lbm_step(self.ctx, n)
+
+    def step_graph(self, n, repeats):
+        lbm_step_graph(self.ctx, n, repeats)
 
     def macros(self):
         rho = np.zeros(self.shape)

@@ -27,7 +27,7 @@ def rel_u_err(u_gpu, u_ref):
 @pytest.mark.parametrize("lat,shape", [(27, (6, 5, 37)), (27, (3, 9, 130)), (9, (1, 13, 70)),
                                        (9, (1, 300, 33)), (27, (1, 1, 1)), (9, (1, 1, 1))])
 @pytest.mark.parametrize("bgk", [0, 1])
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 def test_one_step_random_state(lat, shape, bgk, variant):
     f0 = synth.random_state(lat, shape, 0.03, 42)
     beta = 0.91
@@ -103,7 +103,7 @@ def test_variants_agree_bitwise():
     N = 40
     rho, u = synth.tgv_fields(N, N, N, 0.05)
     out = []
-    for variant in (1, 2):
+    for variant in (1, 2, 3):
         L = make(27, (N, N, N), 0.99)
         L.set_sweep_variant(variant)
         L.init_equilibrium(rho, u)
@@ -111,6 +111,7 @@ def test_variants_agree_bitwise():
         out.append(L.get_populations())
         L.close()
     assert np.array_equal(out[0], out[1])
+    assert np.array_equal(out[0], out[2])
 
 
 def test_full_size_128cube_sampled_nodes():
