@@ -252,6 +252,34 @@ lbm_status fsi_couple(lbm_ctx *ctx, fem_ctx *f, int first_vertex);
  * changes.  Same results as lbm_step; no host work per step.  Asynchronous. */
 lbm_status lbm_step_graph(lbm_ctx *ctx, int n, int repeats);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many independent lattices (same lattice type, storage and stream;
+ * any sizes, geometries and couplings) advanced together with one launch per
+ * phase: boundary fill + force for all lattices, a persistent sweep whose
+ * CTAs take tiles (lattice, rows, 128-node x segment) from an atomic ticket,
+ * one CTA per coupled beam, and the geometry rebuild of all moving surfaces.
+ * Results equal stepping each lattice on its own (up to the order of FP64
+ * force additions).  While batched, step the member contexts only through the
+ * batch; the contexts must outlive it.  The paper has no counterpart (its
+ * cases are single runs); this serves ensembles.
+ * ------------------------------------------------------------------------- */
+typedef struct lbm_batch lbm_batch;
+lbm_status lbm_batch_workspace_size(lbm_ctx *const *ctxs, int n, size_t *bytes);
+/* workspace: device memory (256-byte aligned, caller-owned) or NULL (cudaMalloc). */
+lbm_status lbm_batch_create(lbm_ctx *const *ctxs, int n, void *workspace, size_t bytes,
+                            lbm_batch **out);
+lbm_status lbm_batch_step(lbm_batch *b, int n);
+/* n * repeats steps by replaying a CUDA graph of n batched steps (n even). */
+lbm_status lbm_batch_step_graph(lbm_batch *b, int n, int repeats);
+/* Tile height (rows per tile, 1..64) and resident CTAs per SM of the sweep. */
+lbm_status lbm_batch_set_tuning(lbm_batch *b, int rows_per_tile, int ctas_per_sm);
+/* Times every (rows per tile, CTAs per SM) candidate over `steps` batched
+ * steps and keeps the fastest; the trial steps advance the simulation. */
+lbm_status lbm_batch_autotune(lbm_batch *b, int steps, int *best_rows, int *best_ctas,
+                              float *best_us_per_step);
+const char *lbm_batch_last_error(const lbm_batch *b);
+void lbm_batch_destroy(lbm_batch *b);
+
 /* Density rho[nz][ny][nx] and velocity u[dim][nz][ny][nx] of the current
  * state (FP64 outputs; solid nodes give rho = 0, u = 0).  Synchronises. */
 lbm_status lbm_get_macros(lbm_ctx *ctx, double *rho, double *u);

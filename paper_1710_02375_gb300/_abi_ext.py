@@ -31,6 +31,20 @@ def declare(L):
     L.fem_destroy.argtypes = [vp]
     L.fem_destroy.restype = None
     L.fsi_couple.argtypes = [vp, vp, i32]
+    L.lbm_batch_workspace_size.argtypes = [vp, i32, ctypes.POINTER(sz)]
+    L.lbm_batch_create.argtypes = [vp, i32, vp, sz, ctypes.POINTER(vp)]
+    L.lbm_batch_step.argtypes = [vp, i32]
+    L.lbm_batch_step_graph.argtypes = [vp, i32, i32]
+    L.lbm_batch_set_tuning.argtypes = [vp, i32, i32]
+    L.lbm_batch_autotune.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                     ctypes.POINTER(ctypes.c_float)]
+    L.lbm_batch_last_error.argtypes = [vp]
+    L.lbm_batch_last_error.restype = ctypes.c_char_p
+    L.lbm_batch_destroy.argtypes = [vp]
+    L.lbm_batch_destroy.restype = None
+    for name in ("lbm_batch_workspace_size", "lbm_batch_create", "lbm_batch_step",
+                 "lbm_batch_step_graph", "lbm_batch_set_tuning", "lbm_batch_autotune"):
+        getattr(L, name).restype = ctypes.c_int
     for name in ("fem_beam_workspace_size", "fem_beam_create", "fem_beam_step", "fem_beam_get_state",
                  "fem_beam_set_state", "fsi_couple"):
         getattr(L, name).restype = ctypes.c_int

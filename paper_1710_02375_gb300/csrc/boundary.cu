@@ -246,10 +246,11 @@ __device__ void link_hit(const SurfaceDev &s, const double *xb, int cx, int cy, 
 }
 
 // New solid flags inside the band; nodes that turn fluid are listed as fresh.
-__global__ void k_solid_flags(Grid g, Band bd, SurfaceDev s, uint8_t *flags, int64_t *fresh,
-                              int *nfresh, int cap, int track_fresh) {
+__device__ __forceinline__ void solid_flags_body(long long t, const Grid &g, const Band &bd,
+                                                 const SurfaceDev &s, uint8_t *flags,
+                                                 int64_t *fresh, int *nfresh, int cap,
+                                                 int track_fresh) {
   const int bx = bd.x1 - bd.x0, by = bd.y1 - bd.y0, bz = bd.z1 - bd.z0;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (long long)bx * by * bz) return;
   const int x = bd.x0 + (int)(t % bx), y = bd.y0 + (int)((t / bx) % by),
             z = bd.z0 + (int)(t / ((long long)bx * by));
@@ -265,13 +266,20 @@ __global__ void k_solid_flags(Grid g, Band bd, SurfaceDev s, uint8_t *flags, int
   flags[k] = now;
 }
 
+__global__ void k_solid_flags(Grid g, Band bd, SurfaceDev s, uint8_t *flags, int64_t *fresh,
+                              int *nfresh, int cap, int track_fresh) {
+  solid_flags_body(blockIdx.x * (long long)blockDim.x + threadIdx.x, g, bd, s, flags, fresh,
+                   nfresh, cap, track_fresh);
+}
+
 // Immersed boundary nodes of the band and their cut links.
 template <int Q>
-__global__ void k_build_links(Grid g, Band bd, SurfaceDev s, const uint8_t *flags, BNode *bnodes,
-                              int *nbn, int bcap, Link *links, int *nl, int lcap, int *err) {
+__device__ __forceinline__ void build_links_body(long long t, const Grid &g, const Band &bd,
+                                                 const SurfaceDev &s, const uint8_t *flags,
+                                                 BNode *bnodes, int *nbn, int bcap, Link *links,
+                                                 int *nl, int lcap, int *err) {
   using L = Lat<Q>;
   const int bx = bd.x1 - bd.x0, by = bd.y1 - bd.y0, bz = bd.z1 - bd.z0;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (long long)bx * by * bz) return;
   const int x = bd.x0 + (int)(t % bx), y = bd.y0 + (int)((t / bx) % by),
             z = bd.z0 + (int)(t / ((long long)bx * by));
@@ -311,13 +319,20 @@ __global__ void k_build_links(Grid g, Band bd, SurfaceDev s, const uint8_t *flag
   }
 }
 
+template <int Q>
+__global__ void k_build_links(Grid g, Band bd, SurfaceDev s, const uint8_t *flags, BNode *bnodes,
+                              int *nbn, int bcap, Link *links, int *nl, int lcap, int *err) {
+  build_links_body<Q>(blockIdx.x * (long long)blockDim.x + threadIdx.x, g, bd, s, flags, bnodes,
+                      nbn, bcap, links, nl, lcap, err);
+}
+
 // Fresh nodes (solid -> fluid): f = feq(mean rho of fluid non-fresh neighbours,
 // velocity of the nearest surface vertex).
 template <int Q, int S>
-__global__ void k_fresh_init(Grid g, typename Store<S>::T *f, const uint8_t *flags,
-                             const int64_t *fresh, const int *nfresh, int cap, SurfaceDev s) {
+__device__ __forceinline__ void fresh_init_body(int t, const Grid &g, typename Store<S>::T *f,
+                                                const uint8_t *flags, const int64_t *fresh,
+                                                const int *nfresh, int cap, const SurfaceDev &s) {
   using L = Lat<Q>;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int nf = *nfresh < cap ? *nfresh : cap;
   if (t >= nf) return;
   const long long k = fresh[t];
@@ -371,17 +386,25 @@ __global__ void k_fresh_init(Grid g, typename Store<S>::T *f, const uint8_t *fla
   }
 }
 
+template <int Q, int S>
+__global__ void k_fresh_init(Grid g, typename Store<S>::T *f, const uint8_t *flags,
+                             const int64_t *fresh, const int *nfresh, int cap, SurfaceDev s) {
+  fresh_init_body<Q, S>(blockIdx.x * blockDim.x + threadIdx.x, g, f, flags, fresh, nfresh, cap, s);
+}
+
 // ---------------------------------------------------------------- Grad fill + force
 template <int Q, int S, typename R>
-__global__ void __launch_bounds__(128)
-    k_grad(Grid g, typename Store<S>::T *f, const uint8_t *__restrict__ flags,
-           const BNode *__restrict__ bnodes, const int *__restrict__ nbn, int nfixed, int cap,
-           int first, int last, const Link *__restrict__ links, BoundaryParams bp, double *vforce,
-           double *bforce, int nbodies) {
+__device__ __forceinline__ void grad_body(int tb, const Grid &g, typename Store<S>::T *f,
+                                          const uint8_t *__restrict__ flags,
+                                          const BNode *__restrict__ bnodes,
+                                          const int *__restrict__ nbn, int nfixed, int cap,
+                                          int first, int last, const Link *__restrict__ links,
+                                          const BoundaryParams &bp, double *vforce,
+                                          double *bforce, int nbodies) {
   using L = Lat<Q>;
   using St = Store<S>;
   // threads [0, nfixed) take the face nodes, the rest the immersed nodes
-  const int t = blockIdx.x * blockDim.x + threadIdx.x + first;
+  const int t = tb + first;
   int dyn = nbn ? *nbn : 0;
   if (dyn > cap - nfixed) dyn = cap - nfixed;
   const int count = last < 0 ? nfixed + dyn : last;
@@ -602,6 +625,16 @@ __global__ void __launch_bounds__(128)
   }
 }
 
+template <int Q, int S, typename R>
+__global__ void __launch_bounds__(128)
+    k_grad(Grid g, typename Store<S>::T *f, const uint8_t *__restrict__ flags,
+           const BNode *__restrict__ bnodes, const int *__restrict__ nbn, int nfixed, int cap,
+           int first, int last, const Link *__restrict__ links, BoundaryParams bp, double *vforce,
+           double *bforce, int nbodies) {
+  grad_body<Q, S, R>(blockIdx.x * blockDim.x + threadIdx.x, g, f, flags, bnodes, nbn, nfixed, cap,
+                     first, last, links, bp, vforce, bforce, nbodies);
+}
+
 __global__ void k_step_counter(int *step) { *step += 1; }
 
 // ---------------------------------------------------------------- launchers
@@ -696,6 +729,92 @@ cudaError_t launch_build_links(int Q, const Grid &g, const Band &bd, const Surfa
     k_build_links<27><<<nb_(nb, 128), 128, 0, s>>>(g, bd, sd, flags, bnodes, nbn, bcap, links,
                                                     nl, lcap, err);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- batched phases
+// Zero the force accumulators of every lattice and reset the sweep's tile ticket.
+__global__ void k_batch_pre(const InstDesc *__restrict__ d, int *ticket) {
+  const InstDesc &b = d[blockIdx.y];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *ticket = 0;
+  if (b.nbodies == 0) return;
+  if (t < 3 * b.nv) b.vforce[t] = 0.0;
+  if (t < 3 * b.nbodies) b.bforce[t] = 0.0;
+}
+
+template <int Q, int S>
+__global__ void __launch_bounds__(128) k_grad_batch(const InstDesc *__restrict__ d, int parity) {
+  const InstDesc &b = d[blockIdx.y];
+  if ((int)(blockIdx.x * blockDim.x) >= b.cap) return;  // whole block idle
+  typename Store<S>::T *f = (typename Store<S>::T *)b.f[(b.cur0 + parity) & 1];
+  grad_body<Q, S, double>(blockIdx.x * blockDim.x + threadIdx.x, b.g, f, b.flags, b.bnodes, b.nbn,
+                          b.nfixed, b.cap, 0, -1, b.links, b.bp, b.vforce, b.bforce, b.nbodies);
+}
+
+__global__ void k_geom_reset_batch(const InstDesc *__restrict__ d, const int *__restrict__ idx,
+                                   int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const InstDesc &b = d[idx[t]];
+  *b.nbn = 0;
+  *b.nl = 0;
+  *b.nfresh = 0;
+}
+
+__global__ void k_solid_flags_batch(const InstDesc *__restrict__ d, const int *__restrict__ idx) {
+  const InstDesc &b = d[idx[blockIdx.y]];
+  solid_flags_body(blockIdx.x * (long long)blockDim.x + threadIdx.x, b.g, b.band, b.sd, b.flags,
+                   b.fresh, b.nfresh, b.lcap, 1);
+}
+
+template <int Q, int S>
+__global__ void k_fresh_batch(const InstDesc *__restrict__ d, const int *__restrict__ idx,
+                              int parity) {
+  const InstDesc &b = d[idx[blockIdx.y]];
+  typename Store<S>::T *f = (typename Store<S>::T *)b.f[(b.cur0 + parity) & 1];
+  fresh_init_body<Q, S>(blockIdx.x * blockDim.x + threadIdx.x, b.g, f, b.flags, b.fresh, b.nfresh,
+                        b.lcap, b.sd);
+}
+
+template <int Q>
+__global__ void k_links_batch(const InstDesc *__restrict__ d, const int *__restrict__ idx) {
+  const InstDesc &b = d[idx[blockIdx.y]];
+  build_links_body<Q>(blockIdx.x * (long long)blockDim.x + threadIdx.x, b.g, b.band, b.sd, b.flags,
+                      b.bnodes + b.nfixed, b.nbn, b.lcap, b.links, b.nl, b.lcap, b.err);
+}
+
+cudaError_t launch_batch_pre(const InstDesc *d, int n, int max_nv3, int *ticket, cudaStream_t s) {
+  dim3 grid(nb_(max_nv3 > 0 ? max_nv3 : 1, 128), n);
+  k_batch_pre<<<grid, 128, 0, s>>>(d, ticket);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_batch(int Q, int storage, const InstDesc *d, int n, int max_cap, int parity,
+                              cudaStream_t s) {
+  if (max_cap <= 0) return cudaSuccess;
+  dim3 grid(nb_(max_cap, 128), n);
+  KBC_DISPATCH(Q, storage, {
+    k_grad_batch<QQ, SS><<<grid, 128, 0, s>>>(d, parity);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_geometry_batch(int Q, int storage, const InstDesc *d, const int *idx, int n,
+                                  long long max_band, int max_fresh, int parity, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_geom_reset_batch<<<nb_(n, 128), 128, 0, s>>>(d, idx, n);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  dim3 gb(nb_(max_band, 128), n), gf(nb_(max_fresh, 128), n);
+  k_solid_flags_batch<<<gb, 128, 0, s>>>(d, idx);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  KBC_DISPATCH(Q, storage, {
+    k_fresh_batch<QQ, SS><<<gf, 128, 0, s>>>(d, idx, parity);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (QQ == 9) k_links_batch<9><<<gb, 128, 0, s>>>(d, idx);
+    else k_links_batch<27><<<gb, 128, 0, s>>>(d, idx);
+    return cudaGetLastError();
+  });
 }
 
 cudaError_t launch_step_counter(int *step, cudaStream_t s) {

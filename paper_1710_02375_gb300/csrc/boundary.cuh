@@ -49,4 +49,31 @@ struct BoundaryParams {
   const int *step;        // device step counter (ramp clock)
 };
 
+// One lattice of a batch (all device pointers point into its own workspace).
+struct InstDesc {
+  Grid g;
+  void *f[2];             // population buffers; step parity p reads f[(cur0 + p) & 1]
+  int cur0;
+  uint8_t *flags;
+  float beta;
+  int bgk;
+  int *err;
+  // boundary fill and force
+  BNode *bnodes;          // face nodes, then immersed nodes
+  int *nbn;               // immersed node counter (nullptr: no bodies)
+  int nfixed, cap;
+  Link *links;
+  BoundaryParams bp;
+  double *vforce, *bforce;
+  int nbodies, nv;
+  // geometry rebuild (moving surface)
+  int coupled;
+  Band band;
+  SurfaceDev sd;
+  int64_t *fresh;
+  int *nfresh;
+  int *nl;
+  int lcap;
+};
+
 }  // namespace kbc

@@ -26,27 +26,14 @@
 #include <new>
 
 #include "../../include/kbc_lbm.h"
+#include "fem_beam.cuh"
 #include "lbm_internal.h"
 
 namespace kbc {
 
 constexpr int KB = 5;            // half bandwidth
 constexpr int BW = 2 * KB + 1;   // band width
-constexpr int kMaxBeamNodes = 64;
 
-struct BeamParams {
-  int nn;
-  double EA, EI, rhoA, h;
-  double theta, lambda, rtol, atol, dt;
-  int max_it;
-};
-
-struct BeamDev {
-  const double *X;     // [nn][2]
-  const int32_t *fixed;
-  double *u, *v, *F0;  // [3nn] state and previous loads
-  int *iters;          // last step's Newton iteration count (negative: not converged)
-};
 
 __device__ __forceinline__ double &band(double *A, int i, int j) { return A[i * BW + (j - i + KB)]; }
 
@@ -157,9 +144,10 @@ __device__ void flag_vertex(const BeamParams &p, const double *X, const double *
 // momentum-exchange forces of the flag's surface vertices (coupled: vforce,
 // surf_x / surf_v of the whole surface, the flag's vertices start at v0).
 template <bool COUPLED>
-__global__ void __launch_bounds__(128)
-    k_beam_step(BeamParams p, BeamDev d, const double *__restrict__ F1_in,
-                const double *__restrict__ vforce, double *surf_x, double *surf_v, int v0) {
+__device__ __forceinline__ void beam_step_body(const BeamParams &p, const BeamDev &d,
+                                               const double *__restrict__ F1_in,
+                                               const double *__restrict__ vforce, double *surf_x,
+                                               double *surf_v, int v0) {
   __shared__ double sJ[3 * kMaxBeamNodes * BW], sM[3 * kMaxBeamNodes * BW];
   __shared__ double su[3 * kMaxBeamNodes], su0[3 * kMaxBeamNodes], sv0[3 * kMaxBeamNodes];
   __shared__ double sf0[3 * kMaxBeamNodes], sf1[3 * kMaxBeamNodes], sF1[3 * kMaxBeamNodes];
@@ -297,6 +285,25 @@ __global__ void __launch_bounds__(128)
     }
   }
   (void)s_done;
+}
+
+template <bool COUPLED>
+__global__ void __launch_bounds__(128)
+    k_beam_step(BeamParams p, BeamDev d, const double *__restrict__ F1_in,
+                const double *__restrict__ vforce, double *surf_x, double *surf_v, int v0) {
+  beam_step_body<COUPLED>(p, d, F1_in, vforce, surf_x, surf_v, v0);
+}
+
+// One CTA per coupled beam of a batch.
+__global__ void __launch_bounds__(128) k_beam_step_batch(const BeamBatchDesc *__restrict__ d) {
+  const BeamBatchDesc &b = d[blockIdx.x];
+  beam_step_body<true>(b.p, b.d, nullptr, b.vforce, b.surf_x, b.surf_v, b.v0);
+}
+
+cudaError_t launch_beam_batch(const BeamBatchDesc *d, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_beam_step_batch<<<n, 128, 0, s>>>(d);
+  return cudaGetLastError();
 }
 
 }  // namespace kbc
@@ -456,6 +463,11 @@ void fem_destroy(fem_ctx *f) {
 namespace kbc {
 
 int fem_nodes(const fem_ctx *f) { return f->p.nn; }
+
+void fem_describe(const fem_ctx *f, BeamParams *p, BeamDev *d) {
+  *p = f->p;
+  *d = f->d;
+}
 
 // Coupled structural step on the lattice stream: loads from the surface
 // forces of vertices [v0, v0 + 2 nn), then the new flag surface.

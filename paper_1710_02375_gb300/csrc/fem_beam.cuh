@@ -1,0 +1,33 @@
+// fem_beam.cuh -- device data of the GPU beam (shared with the batched launch).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace kbc {
+
+constexpr int kMaxBeamNodes = 64;
+
+struct BeamParams {
+  int nn;
+  double EA, EI, rhoA, h;
+  double theta, lambda, rtol, atol, dt;
+  int max_it;
+};
+
+struct BeamDev {
+  const double *X;     // [nn][2]
+  const int32_t *fixed;
+  double *u, *v, *F0;  // [3nn] state and previous loads
+  int *iters;          // last step's Newton iteration count (negative: not converged)
+};
+
+// A coupled beam of a batch: its state and the surface arrays of its lattice.
+struct BeamBatchDesc {
+  BeamParams p;
+  BeamDev d;
+  const double *vforce;
+  double *surf_x, *surf_v;
+  int v0;
+};
+
+}  // namespace kbc

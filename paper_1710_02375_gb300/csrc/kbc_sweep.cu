@@ -21,17 +21,15 @@
 
 namespace kbc {
 
+// One node (interior coordinates x, y, z) of the fused sweep.
 template <int Q, int S, bool FLAGS>
-__global__ void __launch_bounds__(128, KBC_MIN_CTAS)
-    k_sweep(Grid g, const typename Store<S>::T *__restrict__ fin,
-            typename Store<S>::T *__restrict__ fout, const uint8_t *__restrict__ flags,
-            float beta, int bgk, int *__restrict__ err) {
+__device__ __forceinline__ void sweep_node(const Grid &g,
+                                           const typename Store<S>::T *__restrict__ fin,
+                                           typename Store<S>::T *__restrict__ fout,
+                                           const uint8_t *__restrict__ flags, float beta, int bgk,
+                                           int *__restrict__ err, int x, int y, int z) {
   using L = Lat<Q>;
   using St = Store<S>;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
-  if (x >= g.nx || y >= g.ny) return;
   const int X = x + g.px, Y = y + g.py, Z = z + g.pz;
   const long long k = sidx(g, X, Y, Z);
   if (FLAGS && flags[k] != NODE_FLUID) return;
@@ -55,6 +53,18 @@ __global__ void __launch_bounds__(128, KBC_MIN_CTAS)
   typename St::T *po = fout + k;
 #pragma unroll
   for (int i = 0; i < Q; ++i, po += g.N) St::store(po, v[i], (float)(1.0 / weight<L>(i)));
+}
+
+template <int Q, int S, bool FLAGS>
+__global__ void __launch_bounds__(128, KBC_MIN_CTAS)
+    k_sweep(Grid g, const typename Store<S>::T *__restrict__ fin,
+            typename Store<S>::T *__restrict__ fout, const uint8_t *__restrict__ flags,
+            float beta, int bgk, int *__restrict__ err) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= g.nx || y >= g.ny) return;
+  sweep_node<Q, S, FLAGS>(g, fin, fout, flags, beta, bgk, err, x, y, z);
 }
 
 
@@ -307,6 +317,55 @@ static cudaError_t sweep_async_t(const Grid &g, const void *fin, void *fout, con
     k_sweep_async<Q, false><<<grid, 128, 0, s>>>(g, (const float *)fin, (float *)fout, flags, beta,
                                                  bgk, err, rows_per_cta);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- batched sweep
+// Persistent CTAs take tiles (lattice, first row, x segment of 128 nodes)
+// from an atomic ticket until the list is exhausted; lattices of any shape
+// share one launch.  Block 0 also advances every lattice's inlet-ramp clock
+// (this kernel runs after the boundary fill of the step).
+template <int Q, int S>
+__global__ void __launch_bounds__(128, KBC_MIN_CTAS)
+    k_sweep_batch(const InstDesc *__restrict__ d, int n, const int4 *__restrict__ tiles,
+                  int ntiles, int *ticket, int parity, int rows_per_tile) {
+  using T = typename Store<S>::T;
+  __shared__ int s_tile;
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      if (d[i].bp.ramp_steps > 0 && d[i].bp.step) atomicAdd((int *)d[i].bp.step, 1);
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1);
+    __syncthreads();
+    const int tile = s_tile;
+    __syncthreads();
+    if (tile >= ntiles) break;
+    const int4 tl = tiles[tile];
+    const InstDesc &b = d[tl.x];
+    const T *fin = (const T *)b.f[(b.cur0 + parity) & 1];
+    T *fout = (T *)b.f[(b.cur0 + parity + 1) & 1];
+    const int x = tl.z * 128 + threadIdx.x;
+    const int nrows = b.g.ny * b.g.nz;
+    const int rend = min(tl.y + rows_per_tile, nrows);
+    if (x < b.g.nx)
+      for (int r = tl.y; r < rend; ++r)
+        sweep_node<Q, S, true>(b.g, fin, fout, b.flags, b.beta, b.bgk, b.err, x, r % b.g.ny,
+                               r / b.g.ny);
+  }
+}
+
+cudaError_t launch_sweep_batch(int Q, int storage, const InstDesc *d, int n, const int4 *tiles,
+                               int ntiles, int *ticket, int parity, int rows_per_tile,
+                               int ctas_per_sm, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int grid = sms * ctas_per_sm;
+  if (grid > ntiles) grid = ntiles > 0 ? ntiles : 1;
+  KBC_DISPATCH(Q, storage, {
+    k_sweep_batch<QQ, SS><<<grid, 128, 0, s>>>(d, n, tiles, ntiles, ticket, parity,
+                                                rows_per_tile);
+    return cudaGetLastError();
+  });
 }
 
 static dim3 sweep_block(const Grid &g) {

@@ -22,6 +22,9 @@ constexpr size_t kStageBytes = 16u << 20;  // host<->device staging chunk
 constexpr size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 constexpr int kMaxBodies = 16;
+#ifndef KBC_BATCH_CTAS
+#define KBC_BATCH_CTAS 5
+#endif
 
 struct Layout {
   size_t f[2], flags, err, stage;
@@ -748,3 +751,328 @@ extern "C" lbm_status lbm_probe_interface_force_static(lbm_ctx *ctx, double *ver
                 h[0], h[1], kProbeMaxNodes, kProbeMaxLinks);
   return LBM_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Batches: many lattices advanced by one launch per phase.
+struct lbm_batch {
+  int n = 0;
+  std::vector<lbm_ctx *> ctx;
+  int Q = 0, storage = 0;
+  cudaStream_t stream = nullptr;
+  char *ws = nullptr;
+  bool own_ws = false;
+  InstDesc *d_desc = nullptr;
+  int4 *d_tiles = nullptr;
+  int *d_ticket = nullptr;
+  int *d_coupled = nullptr;
+  BeamBatchDesc *d_beam = nullptr;
+  int ncoupled = 0;
+  int max_cap = 0, max_nv3 = 0, max_fresh = 0;
+  long long max_band = 0;
+  int ntiles = 0, max_tiles = 0;
+  int rows_per_tile = 1, ctas_per_sm = KBC_BATCH_CTAS;
+  int parity = 0;
+  std::vector<int> cur0;
+  cudaGraphExec_t gexec = nullptr;
+  int graph_n = 0;
+  bool graph_dirty = true;
+  char msg[256] = {0};
+};
+
+namespace {
+
+size_t batch_tiles_capacity(lbm_ctx *const *ctxs, int n) {
+  size_t t = 0;
+  for (int i = 0; i < n; ++i)
+    t += (size_t)ctxs[i]->g.ny * ctxs[i]->g.nz * ((ctxs[i]->g.nx + 127) / 128);
+  return t;
+}
+
+struct BatchLayout {
+  size_t desc, tiles, ticket, coupled, beam, total;
+};
+
+BatchLayout batch_layout(lbm_ctx *const *ctxs, int n) {
+  BatchLayout L;
+  size_t off = 0;
+  L.desc = off; off += align_up(sizeof(InstDesc) * (size_t)n);
+  L.tiles = off; off += align_up(sizeof(int4) * std::max<size_t>(1, batch_tiles_capacity(ctxs, n)));
+  L.ticket = off; off += kAlign;
+  L.coupled = off; off += align_up(sizeof(int) * (size_t)n);
+  L.beam = off; off += align_up(sizeof(BeamBatchDesc) * (size_t)n);
+  L.total = off;
+  return L;
+}
+
+// Tiles (lattice, first row, x segment), largest lattices first.
+std::vector<int4> batch_tiles(lbm_batch *b) {
+  std::vector<int> order(b->n);
+  for (int i = 0; i < b->n; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int a, int c) {
+    return (long long)b->ctx[a]->g.nx * b->ctx[a]->g.ny * b->ctx[a]->g.nz >
+           (long long)b->ctx[c]->g.nx * b->ctx[c]->g.ny * b->ctx[c]->g.nz;
+  });
+  std::vector<int4> t;
+  for (int i : order) {
+    const Grid &g = b->ctx[i]->g;
+    const int rows = g.ny * g.nz, xs = (g.nx + 127) / 128;
+    for (int r = 0; r < rows; r += b->rows_per_tile)
+      for (int x = 0; x < xs; ++x) t.push_back(make_int4(i, r, x, 0));
+  }
+  return t;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_batch_workspace_size(lbm_ctx *const *ctxs, int n, size_t *bytes) {
+  if (!ctxs || n < 1 || !bytes) return LBM_EINVAL;
+  for (int i = 0; i < n; ++i)
+    if (!ctxs[i]) return LBM_EINVAL;
+  *bytes = batch_layout(ctxs, n).total;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_create(lbm_ctx *const *ctxs, int n, void *workspace, size_t bytes,
+                            lbm_batch **out) {
+  if (!out) return LBM_EINVAL;
+  *out = nullptr;
+  if (!ctxs || n < 1) return LBM_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i] || ctxs[i]->poisoned) return LBM_EINVAL;
+    if (ctxs[i]->Q != ctxs[0]->Q || ctxs[i]->cfg.storage != ctxs[0]->cfg.storage ||
+        ctxs[i]->stream != ctxs[0]->stream) {
+      snprintf(g_create_msg, sizeof(g_create_msg),
+               "lbm_batch_create: lattices must share lattice type, storage and stream");
+      return LBM_EINVAL;
+    }
+    if (ctxs[i]->sweep_variant == SWEEP_ROWS) return LBM_EINVAL;
+  }
+  lbm_batch *b = new (std::nothrow) lbm_batch();
+  if (!b) return LBM_ENOMEM;
+  b->n = n;
+  b->ctx.assign(ctxs, ctxs + n);
+  b->Q = ctxs[0]->Q;
+  b->storage = ctxs[0]->cfg.storage;
+  b->stream = ctxs[0]->stream;
+  const BatchLayout L = batch_layout(ctxs, n);
+  if (workspace) {
+    if (bytes < L.total || ((uintptr_t)workspace % kAlign)) {
+      delete b;
+      return LBM_ENOMEM;
+    }
+    b->ws = (char *)workspace;
+  } else {
+    if (cudaMalloc((void **)&b->ws, L.total) != cudaSuccess) {
+      delete b;
+      return LBM_ENOMEM;
+    }
+    b->own_ws = true;
+  }
+  b->d_desc = (InstDesc *)(b->ws + L.desc);
+  b->d_tiles = (int4 *)(b->ws + L.tiles);
+  b->d_ticket = (int *)(b->ws + L.ticket);
+  b->d_coupled = (int *)(b->ws + L.coupled);
+  b->d_beam = (BeamBatchDesc *)(b->ws + L.beam);
+  b->max_tiles = (int)batch_tiles_capacity(ctxs, n);
+  std::vector<InstDesc> hd(n);
+  std::vector<int> coupled;
+  std::vector<BeamBatchDesc> beams;
+  b->cur0.resize(n);
+  for (int i = 0; i < n; ++i) {
+    lbm_ctx *c = ctxs[i];
+    InstDesc &d = hd[i];
+    memset(&d, 0, sizeof(d));
+    d.g = c->g;
+    d.f[0] = c->f[0];
+    d.f[1] = c->f[1];
+    d.cur0 = c->cur;
+    b->cur0[i] = c->cur;
+    d.flags = c->flags;
+    d.beta = (float)c->cfg.beta;
+    d.bgk = c->cfg.collision == LBM_COLLIDE_BGK;
+    d.err = c->err;
+    d.bnodes = (BNode *)(c->ws + c->lay.bnodes);
+    d.nbn = c->nbodies > 0 ? c->counters : nullptr;
+    d.nfixed = c->nface;
+    d.cap = c->nface + (c->nbodies > 0 ? c->cfg.max_links : 0);
+    d.links = (Link *)(c->ws + c->lay.links);
+    d.bp = c->bp;
+    d.vforce = (double *)(c->ws + c->lay.vforce);
+    d.bforce = (double *)(c->ws + c->lay.bforce);
+    d.nbodies = c->nbodies;
+    d.nv = c->nv;
+    d.coupled = c->fem != nullptr;
+    d.band = c->band;
+    d.sd = surface_dev(c);
+    d.fresh = (int64_t *)(c->ws + c->lay.fresh);
+    d.nfresh = c->counters + 2;
+    d.nl = c->counters + 1;
+    d.lcap = c->cfg.max_links;
+    b->max_cap = std::max(b->max_cap, d.cap);
+    b->max_nv3 = std::max(b->max_nv3, 3 * std::max(d.nv, kMaxBodies));
+    if (c->fem) {
+      coupled.push_back(i);
+      BeamBatchDesc bd;
+      fem_describe(c->fem, &bd.p, &bd.d);
+      bd.vforce = d.vforce;
+      bd.surf_x = (double *)(c->ws + c->lay.sx);
+      bd.surf_v = (double *)(c->ws + c->lay.sv);
+      bd.v0 = c->fem_v0;
+      beams.push_back(bd);
+      const Band &B = c->band;
+      b->max_band = std::max(b->max_band, (long long)(B.x1 - B.x0) * (B.y1 - B.y0) * (B.z1 - B.z0));
+      b->max_fresh = std::max(b->max_fresh, c->cfg.max_links);
+    }
+  }
+  b->ncoupled = (int)coupled.size();
+  cudaError_t e = cudaMemcpyAsync(b->d_desc, hd.data(), sizeof(InstDesc) * n,
+                                  cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess && b->ncoupled)
+    e = cudaMemcpyAsync(b->d_coupled, coupled.data(), sizeof(int) * b->ncoupled,
+                        cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess && b->ncoupled)
+    e = cudaMemcpyAsync(b->d_beam, beams.data(), sizeof(BeamBatchDesc) * b->ncoupled,
+                        cudaMemcpyHostToDevice, b->stream);
+  std::vector<int4> t = batch_tiles(b);
+  b->ntiles = (int)t.size();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_tiles, t.data(), sizeof(int4) * t.size(), cudaMemcpyHostToDevice,
+                        b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) {
+    if (b->own_ws) cudaFree(b->ws);
+    delete b;
+    return LBM_ECUDA;
+  }
+  *out = b;
+  return LBM_OK;
+}
+
+const char *lbm_batch_last_error(const lbm_batch *b) { return b ? b->msg : g_create_msg; }
+
+#define BCK(call)                                                                  \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      snprintf(b->msg, sizeof(b->msg), "%s: %s", #call, cudaGetErrorString(e_));   \
+      return LBM_ECUDA;                                                            \
+    }                                                                              \
+  } while (0)
+
+static lbm_status batch_steps(lbm_batch *b, int nsteps) {
+  for (int t = 0; t < nsteps; ++t) {
+    BCK(launch_batch_pre(b->d_desc, b->n, b->max_nv3, b->d_ticket, b->stream));
+    BCK(launch_grad_batch(b->Q, b->storage, b->d_desc, b->n, b->max_cap, b->parity, b->stream));
+    BCK(launch_sweep_batch(b->Q, b->storage, b->d_desc, b->n, b->d_tiles, b->ntiles, b->d_ticket,
+                           b->parity, b->rows_per_tile, b->ctas_per_sm, b->stream));
+    b->parity ^= 1;
+    if (b->ncoupled) {
+      BCK(launch_beam_batch(b->d_beam, b->ncoupled, b->stream));
+      BCK(launch_geometry_batch(b->Q, b->storage, b->d_desc, b->d_coupled, b->ncoupled,
+                                b->max_band, b->max_fresh, b->parity, b->stream));
+    }
+  }
+  for (int i = 0; i < b->n; ++i) b->ctx[i]->cur = (b->cur0[i] + b->parity) & 1;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch *b, int nsteps) {
+  if (!b || nsteps < 0) return LBM_EINVAL;
+  return batch_steps(b, nsteps);
+}
+
+lbm_status lbm_batch_step_graph(lbm_batch *b, int n, int repeats) {
+  if (!b || n <= 0 || (n & 1) || repeats < 0) return LBM_EINVAL;
+  if (b->graph_dirty || b->graph_n != n || !b->gexec) {
+    if (b->gexec) {
+      cudaGraphExecDestroy(b->gexec);
+      b->gexec = nullptr;
+    }
+    const int p0 = b->parity;
+    BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed));
+    lbm_status st = batch_steps(b, n);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+    b->parity = p0;  // capture does not advance the state
+    for (int i = 0; i < b->n; ++i) b->ctx[i]->cur = (b->cur0[i] + b->parity) & 1;
+    if (st != LBM_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    BCK(e);
+    e = cudaGraphInstantiate(&b->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    BCK(e);
+    b->graph_n = n;
+    b->graph_dirty = false;
+  }
+  for (int r = 0; r < repeats; ++r) BCK(cudaGraphLaunch(b->gexec, b->stream));
+  // an even n leaves every lattice's buffer roles unchanged
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_set_tuning(lbm_batch *b, int rows_per_tile, int ctas_per_sm) {
+  if (!b || rows_per_tile < 1 || rows_per_tile > 64 || ctas_per_sm < 1 || ctas_per_sm > 32)
+    return LBM_EINVAL;
+  b->ctas_per_sm = ctas_per_sm;
+  if (rows_per_tile != b->rows_per_tile) {
+    b->rows_per_tile = rows_per_tile;
+    std::vector<int4> t = batch_tiles(b);
+    b->ntiles = (int)t.size();
+    BCK(cudaMemcpyAsync(b->d_tiles, t.data(), sizeof(int4) * t.size(), cudaMemcpyHostToDevice,
+                        b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+  }
+  b->graph_dirty = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_autotune(lbm_batch *b, int steps, int *best_rows, int *best_ctas,
+                              float *best_us) {
+  if (!b || steps < 2) return LBM_EINVAL;
+  const int rows_c[] = {1, 2, 4, 8};
+  const int ctas_c[] = {3, 4, 5, 6, 8};
+  float best = 1e30f;
+  int br = b->rows_per_tile, bc = b->ctas_per_sm;
+  cudaEvent_t e0, e1;
+  BCK(cudaEventCreate(&e0));
+  BCK(cudaEventCreate(&e1));
+  for (int r : rows_c)
+    for (int c : ctas_c) {
+      lbm_status st = lbm_batch_set_tuning(b, r, c);
+      if (st != LBM_OK) return st;
+      if ((st = batch_steps(b, 2)) != LBM_OK) return st;  // warm-up
+      BCK(cudaEventRecord(e0, b->stream));
+      if ((st = batch_steps(b, steps)) != LBM_OK) return st;
+      BCK(cudaEventRecord(e1, b->stream));
+      BCK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      BCK(cudaEventElapsedTime(&ms, e0, e1));
+      const float us = ms * 1e3f / steps;
+      if (us < best) {
+        best = us;
+        br = r;
+        bc = c;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  lbm_status st = lbm_batch_set_tuning(b, br, bc);
+  if (st != LBM_OK) return st;
+  if (best_rows) *best_rows = br;
+  if (best_ctas) *best_ctas = bc;
+  if (best_us) *best_us = best;
+  return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch *b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->own_ws) cudaFree(b->ws);
+  delete b;
+}
+
+}  // extern "C"

@@ -5,6 +5,7 @@
 
 #include "../../include/kbc_lbm.h"
 #include "boundary.cuh"
+#include "fem_beam.cuh"
 #include "kbc_common.cuh"
 
 namespace kbc {
@@ -79,7 +80,19 @@ cudaError_t launch_build_links(int Q, const Grid &g, const Band &bd, const Surfa
                                const uint8_t *flags, BNode *bnodes, int *nbn, int bcap,
                                Link *links, int *nl, int lcap, int *err, cudaStream_t s);
 
+// batched phases (one launch each for all lattices of a batch)
+cudaError_t launch_batch_pre(const InstDesc *d, int n, int max_nv3, int *ticket, cudaStream_t s);
+cudaError_t launch_grad_batch(int Q, int storage, const InstDesc *d, int n, int max_cap, int parity,
+                              cudaStream_t s);
+cudaError_t launch_sweep_batch(int Q, int storage, const InstDesc *d, int n, const int4 *tiles,
+                               int ntiles, int *ticket, int parity, int rows_per_tile,
+                               int ctas_per_sm, cudaStream_t s);
+cudaError_t launch_geometry_batch(int Q, int storage, const InstDesc *d, const int *idx, int n,
+                                  long long max_band, int max_fresh, int parity, cudaStream_t s);
+
 int fem_nodes(const fem_ctx *f);
+void fem_describe(const fem_ctx *f, BeamParams *p, BeamDev *d);
+cudaError_t launch_beam_batch(const BeamBatchDesc *d, int n, cudaStream_t s);
 cudaError_t launch_beam_coupled(fem_ctx *f, const double *vforce, double *surf_x, double *surf_v,
                                 int v0, cudaStream_t s);
 cudaError_t launch_flag_surface(fem_ctx *f, double *surf_x, double *surf_v, int v0,

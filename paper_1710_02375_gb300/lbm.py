@@ -408,3 +408,57 @@ class Beam:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- batches
+def _batch_chk(b, st):
+    if st != LBM_OK:
+        raise LbmError(st, load().lbm_batch_last_error(b).decode(errors="replace"))
+
+
+class Batch:
+    """Many Lattice objects advanced with one launch per phase (lbm_batch_*).
+
+    The member lattices must share lattice type, storage and stream; torch
+    allocates the batch workspace."""
+
+    def __init__(self, lattices):
+        import torch
+        self.lattices = list(lattices)
+        n = len(self.lattices)
+        self._arr = (ctypes.c_void_p * n)(*[L.ctx for L in self.lattices])
+        nb = ctypes.c_size_t()
+        _batch_chk(None, load().lbm_batch_workspace_size(self._arr, n, ctypes.byref(nb)))
+        self.workspace = torch.empty(nb.value, dtype=torch.uint8, device=self.lattices[0].device)
+        out = ctypes.c_void_p()
+        st = load().lbm_batch_create(self._arr, n, self.workspace.data_ptr(), nb.value, ctypes.byref(out))
+        if st != LBM_OK:
+            raise LbmError(st, load().lbm_batch_last_error(None).decode())
+        self.b = out.value
+        self.stream = self.lattices[0].stream
+
+    def step(self, n=1):
+        _batch_chk(self.b, load().lbm_batch_step(self.b, int(n)))
+
+    def step_graph(self, n, repeats):
+        _batch_chk(self.b, load().lbm_batch_step_graph(self.b, int(n), int(repeats)))
+
+    def set_tuning(self, rows_per_tile, ctas_per_sm):
+        _batch_chk(self.b, load().lbm_batch_set_tuning(self.b, int(rows_per_tile), int(ctas_per_sm)))
+
+    def autotune(self, steps=4):
+        r, c, us = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        _batch_chk(self.b, load().lbm_batch_autotune(self.b, int(steps), ctypes.byref(r), ctypes.byref(c),
+                                                      ctypes.byref(us)))
+        return r.value, c.value, us.value
+
+    def close(self):
+        if getattr(self, "b", None):
+            load().lbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -176,3 +176,34 @@ def c1_flag_beam(cx=20.0, cy=20.0, d=10.0, flag_len=35.0, flag_h=2.0, n_beam=20,
     fixed = np.zeros(3 * (n_beam + 1), np.int32)
     fixed[:3] = 1
     return X, E * A, E * I, density_ratio * A, fixed
+
+
+
+def c4_instances(n=64, seed=0, n_cyl=48, n_beam=20, u_max=0.05, Ae0=1.4e3):
+    """The batched ensemble: n flag-in-channel instances.  Instance k draws
+    (seed + k) a scale s ~ U[1, 4] (nx = round(200 s), ny = round(40 s), so
+    domains span 200x40 .. 800x160), Re ~ U[50, 200] on the cylinder diameter
+    D = ny / 4.1 with the cylinder at (2D, 2D), a flag of length 3.5 D and
+    thickness 0.2 D, and an aeroelastic number Ae log-uniform on
+    [Ae0 / sqrt(10), Ae0 sqrt(10)] (stiffness over one decade).  Returns a
+    list of dicts with the lattice size, beta, inflow profile, surface mesh
+    (cylinder then flag) and beam data."""
+    out = []
+    for k in range(n):
+        rng = np.random.default_rng(seed + k)
+        s = rng.uniform(1.0, 4.0)
+        nx, ny = int(round(200 * s)), int(round(40 * s))
+        D = ny / 4.1
+        Re = rng.uniform(50.0, 200.0)
+        Ae = Ae0 * 10 ** rng.uniform(-0.5, 0.5)
+        U = 2.0 / 3.0 * u_max
+        nu = U * D / Re
+        beta = 1.0 / (6 * nu + 1)
+        prof = parabolic_profile(ny, u_max, noise=1e-4, seed=seed + k)
+        x, e, body, _ = cylinder_flag_2d(cx=2 * D, cy=2 * D, d=D, flag_len=3.5 * D, flag_h=0.2 * D,
+                                         n_cyl=n_cyl, n_beam=n_beam)
+        X, EA, EI, rhoA, fixed = c1_flag_beam(cx=2 * D, cy=2 * D, d=D, flag_len=3.5 * D,
+                                              flag_h=0.2 * D, n_beam=n_beam, u_max=u_max, Ae=Ae)
+        out.append(dict(nx=nx, ny=ny, beta=beta, Re=Re, Ae=Ae, D=D, inlet=prof, x=x, e=e, body=body,
+                        ncyl=n_cyl, beam=(X, EA, EI, rhoA, fixed), h=0.2 * D))
+    return out
