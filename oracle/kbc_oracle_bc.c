@@ -100,15 +100,17 @@ typedef struct {
 static const double RAY2[2] = {0.8191520442889918, 0.5735764363510461};       /* 35 deg */
 static const double RAY3[3] = {0.6245004513516506, 0.4806291366599437, 0.6155950585117604};
 
-/* crossing of the ray p + t d (t > 0) with segment a-b */
+/* crossing of the ray p + t d (t > 0) with segment a-b at s in [0, 1):
+ * t = tn/den, s = sn/den, compared without dividing */
 static int ray_hits_segment(const double *p, const double *d, const double *a, const double *b) {
   double ex = b[0] - a[0], ey = b[1] - a[1];
   double den = d[0] * (-ey) - d[1] * (-ex);
   if (fabs(den) < 1e-300) return 0;
   double rx = a[0] - p[0], ry = a[1] - p[1];
-  double t = (rx * (-ey) - ry * (-ex)) / den;
-  double s = (d[0] * ry - d[1] * rx) / den;
-  return t > 0.0 && s >= 0.0 && s < 1.0;
+  double tn = rx * (-ey) - ry * (-ex);
+  double sn = d[0] * ry - d[1] * rx;
+  if (den > 0.0) return tn > 0.0 && sn >= 0.0 && sn < den;
+  return tn < 0.0 && sn <= 0.0 && sn > den;
 }
 
 static void cross3(const double *a, const double *b, double *o) {

@@ -52,20 +52,25 @@ __device__ __forceinline__ int step_axis(int S, int c, int NS, int pad) {
   return s;
 }
 
+// Deviation moments of a node: sums of the stored FP32 values in FP32 (exact
+// to the storage precision), returned in the caller's arithmetic type.
 template <int Q, int S, typename R = float>
 __device__ void dev_moments(const Grid &g, const typename Store<S>::T *f, long long k, R &drho,
                             R (&j)[3]) {
   using L = Lat<Q>;
-  drho = 0;
-  j[0] = j[1] = j[2] = 0;
+  float dr = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const R v = (R)Store<S>::load(f + (long long)i * g.N + k, (float)weight<L>(i));
-    drho += v;
-    j[0] += L::cx(i) * v;
-    j[1] += L::cy(i) * v;
-    j[2] += L::cz(i) * v;
+    const float v = Store<S>::load(f + (long long)i * g.N + k, (float)weight<L>(i));
+    dr += v;
+    jx += L::cx(i) * v;
+    jy += L::cy(i) * v;
+    jz += L::cz(i) * v;
   }
+  drho = (R)dr;
+  j[0] = (R)jx;
+  j[1] = (R)jy;
+  j[2] = (R)jz;
 }
 
 template <int Q, int S, typename R = float>
@@ -106,14 +111,17 @@ __global__ void k_face_nodes(Grid g, BNode *out, int *count, int cap) {
 __constant__ double c_ray2[2] = {0.8191520442889918, 0.5735764363510461};
 __constant__ double c_ray3[3] = {0.6245004513516506, 0.4806291366599437, 0.6155950585117604};
 
+// Crossing of the ray p + t d (t > 0) with segment a-b at parameter s in
+// [0, 1), decided without division: t = tn/den > 0 and s = sn/den in [0, 1).
 __device__ bool seg_ray_cross(const double *p, const double *d, const double *a, const double *b) {
   const double ex = b[0] - a[0], ey = b[1] - a[1];
   const double den = d[0] * (-ey) - d[1] * (-ex);
   if (fabs(den) < 1e-300) return false;
   const double rx = a[0] - p[0], ry = a[1] - p[1];
-  const double t = (rx * (-ey) - ry * (-ex)) / den;
-  const double s = (d[0] * ry - d[1] * rx) / den;
-  return t > 0.0 && s >= 0.0 && s < 1.0;
+  const double tn = rx * (-ey) - ry * (-ex);
+  const double sn = d[0] * ry - d[1] * rx;
+  if (den > 0.0) return tn > 0.0 && sn >= 0.0 && sn < den;
+  return tn < 0.0 && sn <= 0.0 && sn > den;
 }
 
 // Moller-Trumbore; barycentrics (1-u-v, u, v) at distance t along d.
@@ -178,8 +186,18 @@ __device__ bool inside_any(const SurfaceDev &s, const double *p) {
     for (int k = 0; k < s.ne; ++k) {
       if (s.eb[k] != b) continue;
       if (s.dim == 2) {
-        cnt += seg_ray_cross(p, c_ray2, s.x + 2 * s.e[2 * k], s.x + 2 * s.e[2 * k + 1]);
+        const double *a = s.x + 2 * s.e[2 * k], *c = s.x + 2 * s.e[2 * k + 1];
+        // the ray runs towards +x and +y: an element entirely behind the node
+        // in either coordinate cannot cross it (exact test, no rounding)
+        if ((a[0] < p[0] && c[0] < p[0]) || (a[1] < p[1] && c[1] < p[1])) continue;
+        cnt += seg_ray_cross(p, c_ray2, a, c);
       } else {
+        const double *a = s.x + 3 * s.e[3 * k], *c = s.x + 3 * s.e[3 * k + 1],
+                     *e = s.x + 3 * s.e[3 * k + 2];
+        if ((a[0] < p[0] && c[0] < p[0] && e[0] < p[0]) ||
+            (a[1] < p[1] && c[1] < p[1] && e[1] < p[1]) ||
+            (a[2] < p[2] && c[2] < p[2] && e[2] < p[2]))
+          continue;
         double t, u, v;
         if (tri_ray(p, c_ray3, s.x + 3 * s.e[3 * k], s.x + 3 * s.e[3 * k + 1],
                     s.x + 3 * s.e[3 * k + 2], t, u, v) &&
@@ -198,9 +216,19 @@ __device__ void link_hit(const SurfaceDev &s, const double *xb, int cx, int cy, 
   const double d[3] = {-(double)cx, -(double)cy, -(double)cz};
   int best = -1;
   double bs = 2.0, bw[3] = {0, 0, 0};
+  // bounding box of the link (with the crossing tolerance): elements outside
+  // it cannot be hit
+  double lo[3], hi[3];
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = fmin(xb[a], xb[a] + d[a]) - 1e-6;
+    hi[a] = fmax(xb[a], xb[a] + d[a]) + 1e-6;
+  }
   for (int k = 0; k < s.ne; ++k) {
     if (s.dim == 2) {
       const double *a = s.x + 2 * s.e[2 * k], *b = s.x + 2 * s.e[2 * k + 1];
+      if (fmax(a[0], b[0]) < lo[0] || fmin(a[0], b[0]) > hi[0] || fmax(a[1], b[1]) < lo[1] ||
+          fmin(a[1], b[1]) > hi[1])
+        continue;
       const double ex = b[0] - a[0], ey = b[1] - a[1];
       const double den = d[0] * (-ey) - d[1] * (-ex);
       if (fabs(den) < 1e-300) continue;
@@ -214,10 +242,14 @@ __device__ void link_hit(const SurfaceDev &s, const double *xb, int cx, int cy, 
         bw[0] = 1.0 - tt; bw[1] = tt; bw[2] = 0.0;
       }
     } else {
+      const double *a = s.x + 3 * s.e[3 * k], *b = s.x + 3 * s.e[3 * k + 1],
+                   *c = s.x + 3 * s.e[3 * k + 2];
+      bool out = false;
+      for (int q = 0; q < 3; ++q)
+        out |= fmax(fmax(a[q], b[q]), c[q]) < lo[q] || fmin(fmin(a[q], b[q]), c[q]) > hi[q];
+      if (out) continue;
       double sp, u, v;
-      if (!tri_ray(xb, d, s.x + 3 * s.e[3 * k], s.x + 3 * s.e[3 * k + 1], s.x + 3 * s.e[3 * k + 2],
-                   sp, u, v))
-        continue;
+      if (!tri_ray(xb, d, a, b, c, sp, u, v)) continue;
       if (sp > eps && sp <= 1.0 + eps && u >= -eps && v >= -eps && u + v <= 1.0 + eps && sp < bs) {
         bs = sp;
         best = k;
