@@ -280,6 +280,41 @@ lbm_status lbm_batch_autotune(lbm_batch *b, int steps, int *best_rows, int *best
 const char *lbm_batch_last_error(const lbm_batch *b);
 void lbm_batch_destroy(lbm_batch *b);
 
+/* ---------------------------------------------------------------------------
+ * MLP for the structural-step surrogate (the paper has no counterpart; it
+ * solves every structural step with Newton, section "Structural modeling").
+ * Fully connected layers dims[0] -> ... -> dims[n_layers], exact-erf GELU on
+ * hidden layers, linear output; BF16 tensor-core GEMMs (mma.sync m16n8k16)
+ * with FP32 accumulation, FP32 master parameters, Adam, mean-squared error.
+ * Parameter vector layout (FP32): for each layer W[dims[l+1]][dims[l]] then
+ * b[dims[l+1]].  Batches are row-major [B][width] FP32, host or device.
+ * ------------------------------------------------------------------------- */
+typedef struct mlp_ctx mlp_ctx;
+typedef struct {
+  int n_layers;           /* 1..8 weight layers */
+  int dims[9];            /* layer widths, 1..4096 */
+  int max_batch;          /* largest batch passed to any call */
+  double lr, beta1, beta2, eps;  /* Adam */
+  void *stream;           /* cudaStream_t, NULL: library-owned */
+} mlp_config;
+lbm_status mlp_workspace_size(const mlp_config *cfg, size_t *bytes);
+lbm_status mlp_create(const mlp_config *cfg, void *workspace, size_t bytes, mlp_ctx **out);
+/* Copy the FP32 parameters in (resets the Adam state) / out.  Synchronise. */
+lbm_status mlp_set_params(mlp_ctx *x, const float *params);
+lbm_status mlp_get_params(mlp_ctx *x, float *params);
+long long mlp_param_count(const mlp_ctx *x);
+/* Y[B][dims[n]] = MLP(X[B][dims[0]]).  Synchronises. */
+lbm_status mlp_forward(mlp_ctx *x, const float *X, int B, float *Y);
+/* Gradients of mean((MLP(X) - Y)^2) w.r.t. the parameters (same layout as
+ * the parameter vector) and the loss; no update.  Synchronises. */
+lbm_status mlp_gradients(mlp_ctx *x, const float *X, const float *Y, int B, float *grads,
+                         float *loss);
+/* One Adam step on the batch; loss (may be NULL) of the batch before the
+ * step.  Asynchronous when loss is NULL. */
+lbm_status mlp_train_step(mlp_ctx *x, const float *X, const float *Y, int B, float *loss);
+const char *mlp_last_error(const mlp_ctx *x);
+void mlp_destroy(mlp_ctx *x);
+
 /* Density rho[nz][ny][nx] and velocity u[dim][nz][ny][nx] of the current
  * state (FP64 outputs; solid nodes give rho = 0, u = 0).  Synchronises. */
 lbm_status lbm_get_macros(lbm_ctx *ctx, double *rho, double *u);

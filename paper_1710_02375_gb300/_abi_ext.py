@@ -19,6 +19,17 @@ class fem_beam_config(ctypes.Structure):
     ]
 
 
+class mlp_config(ctypes.Structure):
+    _fields_ = [
+        ("n_layers", ctypes.c_int),
+        ("dims", ctypes.c_int * 9),
+        ("max_batch", ctypes.c_int),
+        ("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+        ("eps", ctypes.c_double),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
 def declare(L):
     vp, i32, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
     L.fem_beam_workspace_size.argtypes = [ctypes.POINTER(fem_beam_config), ctypes.POINTER(sz)]
@@ -42,6 +53,22 @@ def declare(L):
     L.lbm_batch_last_error.restype = ctypes.c_char_p
     L.lbm_batch_destroy.argtypes = [vp]
     L.lbm_batch_destroy.restype = None
+    L.mlp_workspace_size.argtypes = [ctypes.POINTER(mlp_config), ctypes.POINTER(sz)]
+    L.mlp_create.argtypes = [ctypes.POINTER(mlp_config), vp, sz, ctypes.POINTER(vp)]
+    L.mlp_set_params.argtypes = [vp, vp]
+    L.mlp_get_params.argtypes = [vp, vp]
+    L.mlp_param_count.argtypes = [vp]
+    L.mlp_param_count.restype = ctypes.c_longlong
+    L.mlp_forward.argtypes = [vp, vp, i32, vp]
+    L.mlp_gradients.argtypes = [vp, vp, vp, i32, vp, vp]
+    L.mlp_train_step.argtypes = [vp, vp, vp, i32, vp]
+    L.mlp_last_error.argtypes = [vp]
+    L.mlp_last_error.restype = ctypes.c_char_p
+    L.mlp_destroy.argtypes = [vp]
+    L.mlp_destroy.restype = None
+    for name in ("mlp_workspace_size", "mlp_create", "mlp_set_params", "mlp_get_params", "mlp_forward",
+                 "mlp_gradients", "mlp_train_step"):
+        getattr(L, name).restype = ctypes.c_int
     for name in ("lbm_batch_workspace_size", "lbm_batch_create", "lbm_batch_step",
                  "lbm_batch_step_graph", "lbm_batch_set_tuning", "lbm_batch_autotune"):
         getattr(L, name).restype = ctypes.c_int

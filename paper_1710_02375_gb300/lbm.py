@@ -462,3 +462,77 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- MLP surrogate
+class Mlp:
+    """GPU MLP (BF16 tensor-core GEMMs, FP32 accumulation, Adam); torch
+    allocates the workspace."""
+
+    def __init__(self, dims, max_batch=256, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None,
+                 device="cuda"):
+        import torch
+        from ._abi_ext import mlp_config
+        L = load()
+        self.dims = list(dims)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=torch.device(device))
+        c = mlp_config()
+        c.n_layers = len(dims) - 1
+        for k, d in enumerate(dims):
+            c.dims[k] = d
+        c.max_batch, c.lr, c.beta1, c.beta2, c.eps = max_batch, lr, beta1, beta2, eps
+        c.stream = self.stream.cuda_stream
+        n = ctypes.c_size_t()
+        st = L.mlp_workspace_size(ctypes.byref(c), ctypes.byref(n))
+        if st != LBM_OK:
+            raise LbmError(st, "mlp_workspace_size")
+        self.workspace = torch.empty(n.value, dtype=torch.uint8, device=torch.device(device))
+        out = ctypes.c_void_p()
+        st = L.mlp_create(ctypes.byref(c), self.workspace.data_ptr(), n.value, ctypes.byref(out))
+        if st != LBM_OK:
+            raise LbmError(st, L.mlp_last_error(None).decode())
+        self.ctx = out.value
+        self.nparam = L.mlp_param_count(self.ctx)
+
+    def _chk(self, st):
+        if st != LBM_OK:
+            raise LbmError(st, load().mlp_last_error(self.ctx).decode(errors="replace"))
+
+    def set_params(self, p):
+        self._chk(load().mlp_set_params(self.ctx, _ptr(np.ascontiguousarray(p, dtype=np.float32))))
+
+    def params(self):
+        p = np.zeros(self.nparam, dtype=np.float32)
+        self._chk(load().mlp_get_params(self.ctx, _ptr(p)))
+        return p
+
+    def forward(self, X):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.zeros((X.shape[0], self.dims[-1]), dtype=np.float32)
+        self._chk(load().mlp_forward(self.ctx, _ptr(X), X.shape[0], _ptr(Y)))
+        return Y
+
+    def gradients(self, X, Y):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.ascontiguousarray(Y, dtype=np.float32)
+        g = np.zeros(self.nparam, dtype=np.float32)
+        loss = np.zeros(1, dtype=np.float32)
+        self._chk(load().mlp_gradients(self.ctx, _ptr(X), _ptr(Y), X.shape[0], _ptr(g), _ptr(loss)))
+        return g, float(loss[0])
+
+    def train_step(self, X, Y, want_loss=False):
+        """X, Y: numpy arrays or device tensors (FP32, row-major)."""
+        loss = np.zeros(1, dtype=np.float32) if want_loss else None
+        self._chk(load().mlp_train_step(self.ctx, _ptr(X), _ptr(Y), X.shape[0], _ptr(loss)))
+        return float(loss[0]) if want_loss else None
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            load().mlp_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
