@@ -312,8 +312,34 @@ lbm_status mlp_gradients(mlp_ctx *x, const float *X, const float *Y, int B, floa
 /* One Adam step on the batch; loss (may be NULL) of the batch before the
  * step.  Asynchronous when loss is NULL. */
 lbm_status mlp_train_step(mlp_ctx *x, const float *X, const float *Y, int B, float *loss);
+/* Adam learning rate of the following steps (> 0); keeps the Adam state. */
+lbm_status mlp_set_learning_rate(mlp_ctx *x, double lr);
 const char *mlp_last_error(const mlp_ctx *x);
 void mlp_destroy(mlp_ctx *x);
+
+/* Surrogate for the coupled beam's structural step (no counterpart in the
+ * paper).  Each coupled step then builds the network input on the GPU --
+ * the out-of-balance loads F(t) - f(u), F(t-1) - f(u), F(t-2) - f(u) (F: the
+ * nodal loads, each node's two surface-vertex forces summed, zero moment;
+ * f: the internal force at the state u before the step; zero loads before
+ * the surrogate was set), then u and v; each block on the 3 nn - 3 free DOFs
+ * of nodes 1..nn-1 in (ux, uy, theta) order -- normalises it with in_mean /
+ * in_std, runs the network (batch 1) and takes u + dt v + (output * out_std
+ * + out_mean) as the Newton initial guess of the structural step.  The guess
+ * is accepted when the theta-scheme residual satisfies
+ * |R| <= accept_tol |theta F1 + (1 - theta) F0| (free DOFs); otherwise Newton
+ * continues from it (FEM fallback) to the usual stopping test, which stays
+ * relative to the residual at the start u.  Network: 15 nn - 15 inputs,
+ * 3 nn - 3 outputs (LBM_EINVAL otherwise).  mlp NULL removes the surrogate.
+ * The network context must outlive its use by the lattice. */
+lbm_status fsi_set_surrogate(lbm_ctx *ctx, mlp_ctx *mlp, const float *in_mean, const float *in_std,
+                             const float *out_mean, const float *out_std, double accept_tol);
+/* Structural-step counters of the coupled beam since fsi_couple,
+ * fsi_set_surrogate or the last reset: stats[0] guesses accepted, stats[1]
+ * guesses rejected, stats[2] Newton solves (linearised systems solved),
+ * stats[3] structural steps.  reset != 0 zeroes them after reading.
+ * Synchronises. */
+lbm_status fsi_get_structure_stats(lbm_ctx *ctx, int stats[4], int reset);
 
 /* Density rho[nz][ny][nx] and velocity u[dim][nz][ny][nx] of the current
  * state (FP64 outputs; solid nodes give rho = 0, u = 0).  Synchronises. */

@@ -62,6 +62,8 @@ def declare(L):
     L.mlp_forward.argtypes = [vp, vp, i32, vp]
     L.mlp_gradients.argtypes = [vp, vp, vp, i32, vp, vp]
     L.mlp_train_step.argtypes = [vp, vp, vp, i32, vp]
+    L.mlp_set_learning_rate.argtypes = [vp, ctypes.c_double]
+    L.mlp_set_learning_rate.restype = ctypes.c_int
     L.mlp_last_error.argtypes = [vp]
     L.mlp_last_error.restype = ctypes.c_char_p
     L.mlp_destroy.argtypes = [vp]

@@ -29,6 +29,8 @@
 // Layout: the fill writes f*_i straight into the solid (or ghost) slot
 // A[i][x_b - c_i] of the source buffer, which the fused sweep then pulls
 // unchanged; no boundary branch is needed in the sweep itself.
+#include <type_traits>
+
 #include "boundary.cuh"
 #include "lbm_internal.h"
 
@@ -52,16 +54,19 @@ __device__ __forceinline__ int step_axis(int S, int c, int NS, int pad) {
   return s;
 }
 
-// Deviation moments of a node: sums of the stored FP32 values in FP32 (exact
-// to the storage precision), returned in the caller's arithmetic type.
+// Deviation moments of a node.  D3Q27: sums of the stored values in FP32,
+// returned in the caller's type (FP64 adds are scarce on this part and 27 of
+// them per neighbour dominate the boundary pass).  D2Q9: sums in the caller's
+// type, so that the FP64 boundary path adds the stored values exactly.
 template <int Q, int S, typename R = float>
 __device__ void dev_moments(const Grid &g, const typename Store<S>::T *f, long long k, R &drho,
                             R (&j)[3]) {
   using L = Lat<Q>;
-  float dr = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+  using A = typename std::conditional<Q == 9, R, float>::type;
+  A dr = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const float v = Store<S>::load(f + (long long)i * g.N + k, (float)weight<L>(i));
+    const A v = (A)Store<S>::load(f + (long long)i * g.N + k, (float)weight<L>(i));
     dr += v;
     jx += L::cx(i) * v;
     jy += L::cy(i) * v;

@@ -158,7 +158,7 @@ __device__ __forceinline__ void beam_step_body(const BeamParams &p, const BeamDe
   const int nn = p.nn, n = 3 * nn, ne = nn - 1;
   for (int i = tid; i < n; i += nt) {
     su0[i] = d.u[i];
-    su[i] = d.u[i];
+    su[i] = (d.u_guess && !d.fixed[i]) ? d.u_guess[i] : d.u[i];
     sv0[i] = d.v[i];
     sf0[i] = 0.0;
     sf1[i] = 0.0;
@@ -189,8 +189,31 @@ __device__ __forceinline__ void beam_step_body(const BeamParams &p, const BeamDe
     for (int i = tid; i < n; i += nt) sF1[i] = F1_in[i];
   }
   __syncthreads();
-  // ---- Newton iterations with the constant relaxation lambda
+  // ---- Newton iterations with the constant relaxation lambda.  The
+  // convergence test is relative to the residual at the start u0 (f(u0) is
+  // sf0), also when the iteration starts from a surrogate guess, so that a
+  // guess changes where Newton starts but not where it stops.
   double r0 = -1.0;
+  if (d.u_guess) {
+    double part = 0.0;
+    for (int i = tid; i < n; i += nt) {
+      double mv = 0.0;
+      for (int j = (i - KB > 0 ? i - KB : 0); j <= (i + KB < n - 1 ? i + KB : n - 1); ++j)
+        mv += band(sM, i, j) * (-(1.0 - p.theta) / p.theta * sv0[j] - sv0[j]);
+      double R = mv / p.dt - p.theta * (sF1[i] - sf0[i]) - (1.0 - p.theta) * (d.F0[i] - sf0[i]);
+      if (!d.fixed[i]) part += R * R;
+    }
+    red[tid] = part;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int k = 0; k < nt; ++k) t += red[k];
+      red[0] = sqrt(t);
+    }
+    __syncthreads();
+    r0 = red[0];
+    __syncthreads();
+  }
   int it = 0, conv = 0;
   for (it = 0; it < p.max_it; ++it) {
     for (int i = tid; i < n; i += nt) sf1[i] = 0.0;
@@ -222,6 +245,30 @@ __device__ __forceinline__ void beam_step_body(const BeamParams &p, const BeamDe
     }
     __syncthreads();
     const double rn = red[0];
+    if (it == 0 && d.u_guess && p.accept_tol > 0.0) {
+      // surrogate guess: accept it when the residual is small against the loads
+      double fp = 0.0;
+      for (int i = tid; i < n; i += nt) {
+        const double fe = d.fixed[i] ? 0.0 : p.theta * sF1[i] + (1.0 - p.theta) * d.F0[i];
+        fp += fe * fe;
+      }
+      __syncthreads();
+      red[tid] = fp;
+      __syncthreads();
+      if (tid == 0) {
+        double tsum = 0.0;
+        for (int k = 0; k < nt; ++k) tsum += red[k];
+        red[0] = sqrt(tsum);
+      }
+      __syncthreads();
+      const bool accept = rn <= p.accept_tol * red[0];
+      __syncthreads();
+      if (tid == 0 && d.stats) atomicAdd(&d.stats[accept ? 0 : 1], 1);
+      if (accept) {
+        conv = 1;
+        break;
+      }
+    }
     if (r0 < 0) r0 = rn;
     if (rn <= p.rtol * r0 + p.atol) {
       conv = 1;
@@ -270,7 +317,13 @@ __device__ __forceinline__ void beam_step_body(const BeamParams &p, const BeamDe
     su[i] = ui;
     sR[i] = vi;
   }
-  if (tid == 0) *d.iters = conv ? it : -it - 1;
+  if (tid == 0) {
+    *d.iters = conv ? it : -it - 1;
+    if (d.stats) {
+      atomicAdd(&d.stats[2], it);  // Newton solves of this step
+      atomicAdd(&d.stats[3], 1);
+    }
+  }
   __syncthreads();
   if (COUPLED) {
     // transfer displacement and velocity to the surface mesh
@@ -313,6 +366,13 @@ using namespace kbc;
 struct fem_ctx {
   BeamParams p;
   BeamDev d;
+  // surrogate coupling: nodal load history ring [3][nn][2] (FP64), guess,
+  // statistics (accepted, rejected, Newton solves, steps), normalisation of
+  // the network input / output
+  double *hist = nullptr;
+  double *u_guess = nullptr;
+  int *stats = nullptr;
+  float *in_mean = nullptr, *in_std = nullptr, *out_mean = nullptr, *out_std = nullptr;
   char *ws = nullptr;
   bool own_ws = false;
   cudaStream_t stream = nullptr;
@@ -325,8 +385,10 @@ struct fem_ctx {
 static size_t fem_bytes(int nn) {
   const size_t n = 3 * (size_t)nn;
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t nin = surrogate_inputs(nn), nout = 3 * (size_t)nn - 3;
   return al(sizeof(double) * 2 * nn) + al(sizeof(int32_t) * n) + 4 * al(sizeof(double) * n) +
-         al(sizeof(int));
+         al(sizeof(int)) + al(sizeof(double) * 6 * nn) + al(sizeof(double) * n) +
+         al(kFemStats * sizeof(int)) + 2 * al(sizeof(float) * nin) + 2 * al(sizeof(float) * nout);
 }
 
 static thread_local char g_fem_msg[256];
@@ -383,10 +445,18 @@ lbm_status fem_beam_create(const fem_beam_config *c, void *workspace, size_t byt
   double *v = (double *)p; p += al(sizeof(double) * n);
   double *F0 = (double *)p; p += al(sizeof(double) * n);
   double *F1 = (double *)p; p += al(sizeof(double) * n);
-  int *iters = (int *)p;
+  int *iters = (int *)p; p += al(sizeof(int));
+  const size_t nin = surrogate_inputs(nn), nout = 3 * (size_t)nn - 3;
+  f->hist = (double *)p; p += al(sizeof(double) * 6 * nn);
+  f->u_guess = (double *)p; p += al(sizeof(double) * n);
+  f->stats = (int *)p; p += al(kFemStats * sizeof(int));
+  f->in_mean = (float *)p; p += al(sizeof(float) * nin);
+  f->in_std = (float *)p; p += al(sizeof(float) * nin);
+  f->out_mean = (float *)p; p += al(sizeof(float) * nout);
+  f->out_std = (float *)p;
   f->p = BeamParams{nn, c->EA, c->EI, c->rhoA, c->thickness, c->theta, c->lambda, c->rtol,
-                    c->atol, c->dt, c->max_it};
-  f->d = BeamDev{X, fx, u, v, F0, iters};
+                    c->atol, c->dt, c->max_it, 0.0};
+  f->d = BeamDev{X, fx, u, v, F0, iters, nullptr, f->stats};
   f->F1 = F1;
   cudaError_t e = cudaMemcpyAsync(X, c->X, sizeof(double) * 2 * nn, cudaMemcpyDefault, f->stream);
   if (e == cudaSuccess)
@@ -395,6 +465,8 @@ lbm_status fem_beam_create(const fem_beam_config *c, void *workspace, size_t byt
   if (e == cudaSuccess) e = cudaMemsetAsync(v, 0, sizeof(double) * n, f->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(F0, 0, sizeof(double) * n, f->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(iters, 0, sizeof(int), f->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(f->hist, 0, sizeof(double) * 6 * nn, f->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(f->stats, 0, kFemStats * sizeof(int), f->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
   if (e != cudaSuccess) {
     snprintf(g_fem_msg, sizeof(g_fem_msg), "fem_beam_create: %s", cudaGetErrorString(e));
@@ -488,6 +560,112 @@ __global__ void k_flag_surface(BeamParams p, BeamDev d, double *surf_x, double *
   surf_v[2 * ib] = vb[0]; surf_v[2 * ib + 1] = vb[1];
   surf_x[2 * it] = xt[0]; surf_x[2 * it + 1] = xt[1];
   surf_v[2 * it] = vt[0]; surf_v[2 * it + 1] = vt[1];
+}
+
+// Network input of the surrogate for step t: the out-of-balance loads
+// F(t-k) - f(u) for k = 0, 1, 2 (F: nodal loads, the sums of each node's two
+// surface-vertex forces; f: internal force at the state u before the step),
+// then u and v, all on the free DOFs (the root node's three excluded);
+// normalised with the training statistics.  One CTA.
+__global__ void __launch_bounds__(128)
+    k_surrogate_input(BeamParams p, BeamDev d, double *hist, const double *vforce, int v0,
+                      const float *mean, const float *stdv, float *xin) {
+  __shared__ double sX[2 * kMaxBeamNodes], su[3 * kMaxBeamNodes], sf[3 * kMaxBeamNodes];
+  const int nn = p.nn, n = 3 * nn, ne = nn - 1, tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < n; i += nt) {
+    su[i] = d.u[i];
+    sf[i] = 0.0;
+  }
+  for (int i = tid; i < 2 * nn; i += nt) sX[i] = d.X[i];
+  // ring slots 0 (t), 1 (t-1), 2 (t-2), each [nn][2]: shift, then store step t
+  for (int k = tid; k < 2 * nn; k += nt) {
+    const double h1 = hist[2 * nn + k], h0 = hist[k];
+    hist[4 * nn + k] = h1;
+    hist[2 * nn + k] = h0;
+  }
+  __syncthreads();
+  for (int j = tid; j < nn; j += nt) {
+    const int vb = v0 + j, vt = v0 + 2 * nn - 1 - j;
+    hist[2 * j] = vforce[3 * vb] + vforce[3 * vt];
+    hist[2 * j + 1] = vforce[3 * vb + 1] + vforce[3 * vt + 1];
+  }
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int e = 2 * tid + pass; e < ne; e += 2 * nt) element_internal(p, sX, su, e, sf, nullptr);
+    __syncthreads();
+  }
+  const int nf = n - 3, nin = 5 * nf;
+  for (int k = tid; k < nin; k += nt) {
+    const int blk = k / nf, i = 3 + k % nf;  // DOF index
+    double val;
+    if (blk < 3) {
+      const int comp = i % 3;
+      const double F = comp < 2 ? hist[2 * nn * blk + 2 * (i / 3) + comp] : 0.0;
+      val = F - sf[i];
+    } else if (blk == 3) {
+      val = su[i];
+    } else {
+      val = d.v[i];
+    }
+    xin[k] = (float)((val - (double)mean[k]) / (double)stdv[k]);
+  }
+}
+
+// Newton initial guess: the constant-velocity predictor u + dt v plus the
+// network's correction to it (de-normalised), root node held.
+__global__ void k_surrogate_guess(BeamParams p, BeamDev d, const float *yhat, const float *mean,
+                                  const float *stdv, double *u_guess) {
+  const int n = 3 * p.nn;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double g = d.u[i] + p.dt * d.v[i];
+    if (i >= 3) g += (double)(yhat[i - 3] * stdv[i - 3] + mean[i - 3]);
+    u_guess[i] = d.fixed[i] ? 0.0 : g;
+  }
+}
+
+cudaError_t launch_surrogate_input(fem_ctx *f, const double *vforce, int v0, float *xin,
+                                   cudaStream_t s) {
+  k_surrogate_input<<<1, 128, 0, s>>>(f->p, f->d, f->hist, vforce, v0, f->in_mean, f->in_std, xin);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_surrogate_guess(fem_ctx *f, const float *yhat, cudaStream_t s) {
+  k_surrogate_guess<<<1, 128, 0, s>>>(f->p, f->d, yhat, f->out_mean, f->out_std, f->u_guess);
+  return cudaGetLastError();
+}
+
+// Coupled step with the surrogate guess: the beam kernel first checks it.
+cudaError_t launch_beam_coupled_guess(fem_ctx *f, const double *vforce, double *surf_x,
+                                      double *surf_v, int v0, double accept_tol, cudaStream_t s) {
+  BeamParams p = f->p;
+  p.accept_tol = accept_tol;
+  BeamDev d = f->d;
+  d.u_guess = f->u_guess;
+  k_beam_step<true><<<1, 128, 0, s>>>(p, d, nullptr, vforce, surf_x, surf_v, v0);
+  return cudaGetLastError();
+}
+
+lbm_status fem_set_normalisation(fem_ctx *f, const float *in_mean, const float *in_std,
+                                 const float *out_mean, const float *out_std) {
+  const size_t nin = surrogate_inputs(f->p.nn), nout = 3 * (size_t)f->p.nn - 3;
+  cudaError_t e = cudaMemcpyAsync(f->in_mean, in_mean, sizeof(float) * nin, cudaMemcpyDefault, f->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(f->in_std, in_std, sizeof(float) * nin, cudaMemcpyDefault, f->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(f->out_mean, out_mean, sizeof(float) * nout, cudaMemcpyDefault, f->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(f->out_std, out_std, sizeof(float) * nout, cudaMemcpyDefault, f->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(f->stats, 0, kFemStats * sizeof(int), f->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(f->hist, 0, sizeof(double) * 6 * f->p.nn, f->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
+  return e == cudaSuccess ? LBM_OK : LBM_ECUDA;
+}
+
+lbm_status fem_reset_stats(fem_ctx *f) {
+  cudaError_t e = cudaMemsetAsync(f->stats, 0, kFemStats * sizeof(int), f->stream);
+  return e == cudaSuccess ? LBM_OK : LBM_ECUDA;
+}
+
+lbm_status fem_get_stats(fem_ctx *f, int *stats) {
+  cudaError_t e = cudaMemcpyAsync(stats, f->stats, kFemStats * sizeof(int), cudaMemcpyDefault, f->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
+  return e == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }
 
 cudaError_t launch_flag_surface(fem_ctx *f, double *surf_x, double *surf_v, int v0,

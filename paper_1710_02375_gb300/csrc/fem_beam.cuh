@@ -12,6 +12,7 @@ struct BeamParams {
   double EA, EI, rhoA, h;
   double theta, lambda, rtol, atol, dt;
   int max_it;
+  double accept_tol;   // > 0: accept the initial guess when |R| <= accept_tol |F_ext|
 };
 
 struct BeamDev {
@@ -19,6 +20,8 @@ struct BeamDev {
   const int32_t *fixed;
   double *u, *v, *F0;  // [3nn] state and previous loads
   int *iters;          // last step's Newton iteration count (negative: not converged)
+  const double *u_guess;  // [3nn] Newton initial guess (nullptr: the current state)
+  int *stats;          // [2]: guesses accepted, guesses rejected (FEM fallback)
 };
 
 // A coupled beam of a batch: its state and the surface arrays of its lattice.

@@ -149,6 +149,8 @@ struct lbm_ctx {
   BoundaryParams bp;
   fem_ctx *fem = nullptr;    // coupled beam (conventional serial staggered loop)
   int fem_v0 = 0;
+  mlp_ctx *mlp = nullptr;    // structural-step surrogate (Newton initial guess)
+  double accept_tol = 0.0;
   // CUDA graph of graph_n steps (replayed by lbm_step_graph)
   cudaGraphExec_t gexec = nullptr;
   int graph_n = 0;
@@ -402,7 +404,21 @@ lbm_status lbm_step(lbm_ctx *ctx, int n) {
                     ctx->has_solid ? ctx->flags : nullptr, beta, bgk, ctx->err, ctx->stream,
                     ctx->sweep_variant));
     ctx->cur = 1 - ctx->cur;
-    if (ctx->fem) {
+    if (ctx->fem && ctx->mlp) {
+      // surrogate: network guess of the increment, accepted by the FEM
+      // residual or refined by Newton from there
+      const double *vf = (const double *)(ctx->ws + ctx->lay.vforce);
+      CK(launch_surrogate_input(ctx->fem, vf, ctx->fem_v0, mlp_input_buffer(ctx->mlp), ctx->stream));
+      float *yhat = nullptr, *xin = nullptr;
+      lbm_status st = mlp_forward_device(ctx->mlp, 1, ctx->stream, &yhat, &xin);
+      if (st != LBM_OK) return fail(ctx, st, "surrogate forward failed");
+      CK(launch_surrogate_guess(ctx->fem, yhat, ctx->stream));
+      CK(launch_beam_coupled_guess(ctx->fem, vf, (double *)(ctx->ws + ctx->lay.sx),
+                                   (double *)(ctx->ws + ctx->lay.sv), ctx->fem_v0, ctx->accept_tol,
+                                   ctx->stream));
+      st = run_geometry(ctx, 1);
+      if (st != LBM_OK) return st;
+    } else if (ctx->fem) {
       // structural step from this step's forces, transfer to the surface, new geometry
       CK(launch_beam_coupled(ctx->fem, (const double *)(ctx->ws + ctx->lay.vforce),
                              (double *)(ctx->ws + ctx->lay.sx), (double *)(ctx->ws + ctx->lay.sv),
@@ -570,9 +586,46 @@ lbm_status fsi_couple(lbm_ctx *ctx, fem_ctx *f, int first_vertex) {
   ctx->fem = f;
   ctx->fem_v0 = first_vertex;
   ctx->graph_dirty = true;
+  if (fem_reset_stats(f) != LBM_OK) return fail(ctx, LBM_ECUDA, "fsi_couple: counter reset failed");
   CK(launch_flag_surface(f, (double *)(ctx->ws + ctx->lay.sx), (double *)(ctx->ws + ctx->lay.sv),
                          first_vertex, ctx->stream));
   return run_geometry(ctx, 1);
+}
+
+lbm_status fsi_set_surrogate(lbm_ctx *ctx, mlp_ctx *mlp, const float *in_mean, const float *in_std,
+                             const float *out_mean, const float *out_std, double accept_tol) {
+  GUARD();
+  if (!mlp) {
+    ctx->mlp = nullptr;
+    ctx->graph_dirty = true;
+    return LBM_OK;
+  }
+  if (!ctx->fem) return fail(ctx, LBM_ESTATE, "fsi_set_surrogate: couple a beam first");
+  const int nn = fem_nodes(ctx->fem);
+  if (mlp_dim(mlp, 0) != surrogate_inputs(nn) || mlp_dim(mlp, mlp_layers(mlp)) != 3 * nn - 3)
+    return fail(ctx, LBM_EINVAL,
+                "fsi_set_surrogate: the network must map %d inputs to %d outputs for a %d-node beam",
+                surrogate_inputs(nn), 3 * nn - 3, nn);
+  if (!in_mean || !in_std || !out_mean || !out_std || !(accept_tol > 0.0))
+    return fail(ctx, LBM_EINVAL, "fsi_set_surrogate: bad normalisation or tolerance");
+  lbm_status st = fem_set_normalisation(ctx->fem, in_mean, in_std, out_mean, out_std);
+  if (st != LBM_OK) return fail(ctx, st, "fsi_set_surrogate: copy failed");
+  ctx->mlp = mlp;
+  ctx->accept_tol = accept_tol;
+  ctx->graph_dirty = true;
+  return LBM_OK;
+}
+
+lbm_status fsi_get_structure_stats(lbm_ctx *ctx, int stats[4], int reset) {
+  GUARD();
+  if (!stats) return fail(ctx, LBM_EINVAL, "fsi_get_structure_stats: NULL");
+  if (!ctx->fem) return fail(ctx, LBM_ESTATE, "fsi_get_structure_stats: no beam coupled");
+  CK(cudaStreamSynchronize(ctx->stream));
+  lbm_status st = fem_get_stats(ctx->fem, stats);
+  if (st == LBM_OK && reset) st = fem_reset_stats(ctx->fem);
+  if (st != LBM_OK) return fail(ctx, st, "fsi_get_structure_stats: copy failed");
+  CK(cudaStreamSynchronize(ctx->stream));
+  return LBM_OK;
 }
 
 lbm_status lbm_get_boundary_info(lbm_ctx *ctx, int *info) {

@@ -91,6 +91,25 @@ cudaError_t launch_geometry_batch(int Q, int storage, const InstDesc *d, const i
                                   long long max_band, int max_fresh, int parity, cudaStream_t s);
 
 int fem_nodes(const fem_ctx *f);
+cudaError_t launch_surrogate_input(fem_ctx *f, const double *vforce, int v0, float *xin,
+                                   cudaStream_t s);
+cudaError_t launch_surrogate_guess(fem_ctx *f, const float *yhat, cudaStream_t s);
+cudaError_t launch_beam_coupled_guess(fem_ctx *f, const double *vforce, double *surf_x,
+                                      double *surf_v, int v0, double accept_tol, cudaStream_t s);
+lbm_status fem_set_normalisation(fem_ctx *f, const float *in_mean, const float *in_std,
+                                 const float *out_mean, const float *out_std);
+// Structural-step counters: surrogate guesses accepted, rejected, Newton
+// solves, structural steps (since coupling or the last reset).
+constexpr int kFemStats = 4;
+lbm_status fem_get_stats(fem_ctx *f, int *stats);
+lbm_status fem_reset_stats(fem_ctx *f);
+// Surrogate network input width for an nn-node beam: three out-of-balance
+// load vectors, u and v, each on the 3 nn - 3 free DOFs.
+constexpr int surrogate_inputs(int nn) { return 15 * nn - 15; }
+lbm_status mlp_forward_device(mlp_ctx *x, int B, cudaStream_t s, float **yhat, float **xin);
+float *mlp_input_buffer(mlp_ctx *x);
+int mlp_dim(const mlp_ctx *x, int l);
+int mlp_layers(const mlp_ctx *x);
 void fem_describe(const fem_ctx *f, BeamParams *p, BeamDev *d);
 cudaError_t launch_beam_batch(const BeamBatchDesc *d, int n, cudaStream_t s);
 cudaError_t launch_beam_coupled(fem_ctx *f, const double *vforce, double *surf_x, double *surf_v,

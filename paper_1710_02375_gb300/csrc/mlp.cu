@@ -464,6 +464,12 @@ lbm_status mlp_train_step(mlp_ctx *x, const float *X, const float *Y, int B, flo
   return LBM_OK;
 }
 
+lbm_status mlp_set_learning_rate(mlp_ctx *x, double lr) {
+  if (!x || !(lr > 0.0)) return LBM_EINVAL;
+  x->lr = lr;
+  return LBM_OK;
+}
+
 const char *mlp_last_error(const mlp_ctx *x) { return x ? x->msg : g_mlp_msg; }
 
 void mlp_destroy(mlp_ctx *x) {

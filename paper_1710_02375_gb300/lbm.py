@@ -76,6 +76,10 @@ def load():
     for name in ("lbm_set_inlet_profile", "lbm_set_geometry", "lbm_update_surface",
                  "lbm_get_interface_force", "lbm_get_boundary_info"):
         getattr(L, name).restype = ctypes.c_int
+    L.fsi_set_surrogate.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.c_double]
+    L.fsi_set_surrogate.restype = ctypes.c_int
+    L.fsi_get_structure_stats.argtypes = [vp, ctypes.POINTER(i32), i32]
+    L.fsi_get_structure_stats.restype = ctypes.c_int
     L.lbm_step_graph.argtypes = [vp, i32, i32]
     L.lbm_step_graph.restype = ctypes.c_int
     L.lbm_probe_interface_force_static.argtypes = [vp, vp, vp]
@@ -204,6 +208,22 @@ def lbm_get_boundary_info(ctx, info):
 
 def lbm_probe_interface_force_static(ctx, vert_force, body_force):
     _chk(ctx, load().lbm_probe_interface_force_static(ctx, _ptr(vert_force), _ptr(body_force)))
+
+
+def fsi_set_surrogate(ctx, mlp_ctx, in_mean, in_std, out_mean, out_std, accept_tol):
+    """Attach (mlp_ctx not None) or remove the structural-step surrogate."""
+    if mlp_ctx is None:
+        _chk(ctx, load().fsi_set_surrogate(ctx, None, None, None, None, None, 1.0))
+        return
+    arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (in_mean, in_std, out_mean, out_std)]
+    _chk(ctx, load().fsi_set_surrogate(ctx, mlp_ctx, *[_ptr(a) for a in arrs], float(accept_tol)))
+
+
+def fsi_get_structure_stats(ctx, reset=False):
+    """(accepted, rejected, newton_solves, steps) of the coupled beam."""
+    st = (ctypes.c_int * 4)()
+    _chk(ctx, load().fsi_get_structure_stats(ctx, st, int(bool(reset))))
+    return tuple(st)
 
 
 def lbm_check(ctx):
@@ -499,7 +519,8 @@ class Mlp:
             raise LbmError(st, load().mlp_last_error(self.ctx).decode(errors="replace"))
 
     def set_params(self, p):
-        self._chk(load().mlp_set_params(self.ctx, _ptr(np.ascontiguousarray(p, dtype=np.float32))))
+        p32 = np.ascontiguousarray(p, dtype=np.float32)  # held until the copy returns
+        self._chk(load().mlp_set_params(self.ctx, _ptr(p32)))
 
     def params(self):
         p = np.zeros(self.nparam, dtype=np.float32)
@@ -520,8 +541,18 @@ class Mlp:
         self._chk(load().mlp_gradients(self.ctx, _ptr(X), _ptr(Y), X.shape[0], _ptr(g), _ptr(loss)))
         return g, float(loss[0])
 
+    def set_learning_rate(self, lr):
+        self._chk(load().mlp_set_learning_rate(self.ctx, float(lr)))
+
     def train_step(self, X, Y, want_loss=False):
         """X, Y: numpy arrays or device tensors (FP32, row-major)."""
+        if isinstance(X, np.ndarray):
+            X = np.ascontiguousarray(X, dtype=np.float32)
+        if isinstance(Y, np.ndarray):
+            Y = np.ascontiguousarray(Y, dtype=np.float32)
+        for a in (X, Y):
+            if not isinstance(a, np.ndarray) and (str(a.dtype) != "torch.float32" or not a.is_contiguous()):
+                raise ValueError("device inputs must be contiguous float32 tensors")
         loss = np.zeros(1, dtype=np.float32) if want_loss else None
         self._chk(load().mlp_train_step(self.ctx, _ptr(X), _ptr(Y), X.shape[0], _ptr(loss)))
         return float(loss[0]) if want_loss else None

@@ -1,0 +1,55 @@
+"""The C1 flag case (Turek-type channel, cylinder D = 10, elastic flag,
+rho_s / rho_f = 10, Ae = 1.4e3, 1000-step inflow ramp) at a chosen Reynolds
+number, for the oracle and for the CUDA library; and the worker that turns an
+oracle run into surrogate training pairs (importable by spawned processes)."""
+from __future__ import annotations
+
+import numpy as np
+
+from paper_1710_02375_gb300 import synth
+
+NX, NY, D, U_MAX, H, RAMP = 220, 41, 10.0, 0.05, 2.0, 1000
+BC = (2, 3, 1, 1, 0, 0)
+
+
+def case(Re, seed=0):
+    nu = (2.0 / 3.0) * U_MAX * D / Re
+    beta = 1.0 / (6 * nu + 1)
+    prof = synth.parabolic_profile(NY, U_MAX, noise=1e-4, seed=seed)
+    x, e, body, _ = synth.cylinder_flag_2d()
+    beam = synth.c1_flag_beam()
+    return dict(beta=beta, prof=prof, x=x, e=e, body=body, ncyl=int(np.sum(body == 0)), beam=beam)
+
+
+def oracle_run(Re, seed=0):
+    from oracle import fsi_oracle
+    from oracle import oracle as orc
+    c = case(Re, seed)
+    X, EA, EI, rhoA, fixed = c["beam"]
+    ob = orc.Beam(X, EA, EI, rhoA, fixed)
+    return fsi_oracle.CSSFlag(9, (1, NY, NX), c["beta"], BC, None, {0: c["prof"]}, RAMP,
+                              c["x"][:c["ncyl"]], c["e"], c["body"], ob, H)
+
+
+def oracle_pairs(args):
+    """(X, Y) surrogate pairs of `steps` steps of the oracle run at (Re, seed)."""
+    from oracle import surrogate_data
+    Re, seed, steps = args
+    X, Y, _ = surrogate_data.pairs_from_run(oracle_run(Re, seed), steps)
+    return X, Y
+
+
+def gpu_run(Re, seed=0):
+    """(Lattice, Beam) of the CUDA library, coupled, at step 0."""
+    from paper_1710_02375_gb300 import lbm as abi
+    from paper_1710_02375_gb300.lbm import Beam, Lattice
+    c = case(Re, seed)
+    X, EA, EI, rhoA, fixed = c["beam"]
+    L = Lattice(9, NX, NY, 1, c["beta"], bc=BC, max_links=4000, max_vertices=len(c["x"]),
+                max_elements=len(c["e"]), inlet_ramp_steps=RAMP)
+    L.set_inlet_profile(0, c["prof"])
+    L.set_geometry(c["x"], c["e"], c["body"], band_margin=8.0)
+    L.init_equilibrium(np.ones((1, NY, NX)), np.zeros((2, 1, NY, NX)))
+    gb = Beam(X, EA, EI, rhoA, fixed, thickness=H, stream=L.stream)
+    abi.fsi_couple(L.ctx, gb.ctx, c["ncyl"])
+    return L, gb
