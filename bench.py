@@ -6,6 +6,11 @@ the 129 MB L2, so no L2 flush is needed between steps).  A step is one pass of
 the hot path over the whole lattice: pull-stream + KBC collision, one kernel.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload tgv128|c4|c4-coupled]
+
+The default line also carries "patterns": the same workload with FP16 and
+BF16 storage, as speedups over FP32.  --workload c4 / c4-coupled time the
+batched ensemble (one extra JSON line per call, not the headline).
 
 Prints one JSON line.  With N > 1 (torchrun) every rank advances its own
 independent replica of the workload ("replicas only": the path has no
@@ -255,6 +260,27 @@ def run_ours(args):
     e2e_val = world * nodes * e2e_steps / e2e_s / 1e6
     L.close()
 
+    # ---- reduced-precision storage (FP16 / BF16 of f/W - 1) on the same
+    # workload, as speedups over the FP32 form above
+    patterns = {}
+    for name, storage in (("f16", 1), ("bf16", 2)):
+        Lp = Lattice(Q, N_LATTICE, N_LATTICE, N_LATTICE, beta, storage=storage, stream=stream)
+        Lp.init_equilibrium(rho, u)
+        Lp.step(args.warmup)
+        ksteps = max(1, min(args.steps, 4000))
+        torch.cuda.synchronize()
+        e0.record(stream)
+        Lp.step(ksteps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        Lp.check()
+        ms_p = e0.elapsed_time(e1) / ksteps
+        Lp.close()
+        v = world * nodes / (ms_p * 1e-3) / 1e6
+        patterns[name] = {"value": v, "unit": UNIT, "ms_per_step": ms_p, "steps": ksteps,
+                          "speedup_vs_f32": v / value,
+                          "achieved_gbs": 2 * Q * 2 * nodes / (ms_p * 1e-3) / 1e9}
+
     if rank != 0:
         return
     cpu = None if args.no_cpu_baseline else cpu_baseline_oracle()
@@ -274,6 +300,70 @@ def run_ours(args):
                 "steps": e2e_steps},
         "gpu_launches": args.steps,
         "clocks": clocks,
+        "patterns": patterns,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_c4(args):
+    """Batched pattern: the 64-member flag ensemble (synth.c4_instances, D2Q9,
+    200x40 .. 800x160 lattices, 3.78M nodes in all) stepped as one batch under
+    CUDA-graph replay, against stepping each lattice on its own (the plain
+    FP32 form).  --workload c4-coupled makes every flag an elastic beam."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1710_02375_gb300 import synth
+    from paper_1710_02375_gb300.cases import c4_lattice
+    from paper_1710_02375_gb300.lbm import Batch
+    coupled = args.workload == "c4-coupled"
+    insts = synth.c4_instances(n=64, seed=0)
+    stream = torch.cuda.Stream()
+    nodes = sum(i["nx"] * i["ny"] for i in insts)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, steps):
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    solo = [c4_lattice(i, coupled, stream) for i in insts]
+    for L, _ in solo:
+        L.step(args.warmup)
+    k_solo = max(2, min(args.steps, 200))
+    ms_solo = timed(lambda k: [L.step(k) for L, _ in solo], k_solo)
+    for L, b in solo:
+        L.check()
+        L.close()
+    group = [c4_lattice(i, coupled, stream) for i in insts]
+    B = Batch([L for L, _ in group])
+    B.step(args.warmup)
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    chunk = 10
+    reps = max(1, args.steps // chunk)
+    B.step_graph(chunk, 1)
+    ms = timed(lambda k: B.step_graph(chunk, k), reps) / chunk
+    clocks = sampler.stop()
+    for L, _ in group:
+        L.check()
+    B.close()
+    value = nodes / (ms * 1e-3) / 1e6
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": reps * chunk,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batched ensemble of 64 D2Q9 cylinder+flag channels, 200x40..800x160, "
+                               + ("elastic flags (CSS-coupled beams)" if coupled else "rigid flags"),
+                   "nodes": nodes, "l2": "working set 545 MB, larger than L2 (no flush)"},
+        "individual": {"ms_per_step": ms_solo, "value": nodes / (ms_solo * 1e-3) / 1e6,
+                       "steps": k_solo},
+        "speedup_vs_individual": ms_solo / ms,
+        "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
 
@@ -285,11 +375,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=500)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["tgv128", "c4", "c4-coupled"], default="tgv128")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload in ("c4", "c4-coupled"):
+        run_c4(args)
     else:
         run_ours(args)
 
