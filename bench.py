@@ -6,11 +6,12 @@ the 129 MB L2, so no L2 flush is needed between steps).  A step is one pass of
 the hot path over the whole lattice: pull-stream + KBC collision, one kernel.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload tgv128|c4|c4-coupled]
+                  [--workload tgv128|c4|c4-coupled|c1-fsi]
 
 The default line also carries "patterns": the same workload with FP16 and
 BF16 storage, as speedups over FP32.  --workload c4 / c4-coupled time the
-batched ensemble (one extra JSON line per call, not the headline).
+batched ensemble and --workload c1-fsi the coupled C1 flag (one extra JSON
+line per call, not the headline).
 
 Prints one JSON line.  With N > 1 (torchrun) every rank advances its own
 independent replica of the workload ("replicas only": the path has no
@@ -368,6 +369,46 @@ def run_c4(args):
     print(json.dumps(line), flush=True)
 
 
+def run_c1_fsi(args):
+    """The coupled C1 flag (CSS: fluid, Grad boundaries, forces, beam Newton
+    step, surface transfer, geometry), Re = 100, from rest through the inflow
+    ramp: steps per second and Newton solves per structural step."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1710_02375_gb300 import lbm as abi
+    from paper_1710_02375_gb300.cases import c1_coupled
+    stream = torch.cuda.Stream()
+    L, beam, _ = c1_coupled(100.0, stream=stream)
+    L.step(args.warmup)
+    abi.fsi_get_structure_stats(L.ctx, reset=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    L.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    L.check()
+    acc, rej, solves, steps = abi.fsi_get_structure_stats(L.ctx)
+    nodes = 220 * 41
+    line = {
+        "metric": "coupled FSI steps/s (C1 flag)", "value": 1e3 / ms, "unit": "steps/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "C1 cylinder+elastic flag, D2Q9 220x41, Re=100, CSS-coupled beam "
+                               "(21 nodes, Newton lambda=0.7, rtol 1e-10)",
+                   "nodes": nodes, "first_step": args.warmup},
+        "newton_solves_per_step": solves / max(1, steps), "mlups": nodes / (ms * 1e-3) / 1e6,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -375,7 +416,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=500)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["tgv128", "c4", "c4-coupled"], default="tgv128")
+    ap.add_argument("--workload", choices=["tgv128", "c4", "c4-coupled", "c1-fsi"], default="tgv128")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -383,6 +424,8 @@ def main():
         run_reference(args)
     elif args.workload in ("c4", "c4-coupled"):
         run_c4(args)
+    elif args.workload == "c1-fsi":
+        run_c1_fsi(args)
     else:
         run_ours(args)
 

@@ -205,7 +205,7 @@ lbm_status lbm_get_boundary_info(lbm_ctx *ctx, int *info);
 typedef struct fem_ctx fem_ctx;
 
 typedef struct {
-  int nn;                 /* beam nodes, 2..64 */
+  int nn;                 /* beam nodes, 2..48 */
   const double *X;        /* [nn][2] reference node positions (lattice units), copied */
   double EA, EI, rhoA;    /* axial / bending stiffness, mass per length */
   double thickness;       /* flag thickness h (surface offset h/2 each side) */

@@ -170,7 +170,8 @@ static int point_on_surface(const surf_t *S, const double *p) {
       const double px = p[0] - a[0], py = p[1] - a[1];
       const double len2 = ex * ex + ey * ey;
       const double cr = ex * py - ey * px, dt = ex * px + ey * py;
-      if (fabs(cr) <= tol * sqrt(len2) && dt >= 0.0 && dt <= len2) return 1;
+      /* a zero-length element has no surface */
+      if (len2 > 0.0 && fabs(cr) <= tol * sqrt(len2) && dt >= 0.0 && dt <= len2) return 1;
     } else {
       const double *a = S->x + 3 * S->e[3 * k], *b = S->x + 3 * S->e[3 * k + 1],
                    *c = S->x + 3 * S->e[3 * k + 2];

@@ -23,3 +23,31 @@ def c4_lattice(inst, coupled, stream, storage=0):
         beam = Beam(X, EA, EI, rhoA, fixed, thickness=inst["h"], stream=stream)
         lbm.fsi_couple(L.ctx, beam.ctx, inst["ncyl"])
     return L, beam
+
+
+C1 = dict(nx=220, ny=41, D=10.0, u_max=0.05, h=2.0, ramp=1000, bc=(2, 3, 1, 1, 0, 0))
+
+
+def c1_coupled(Re, seed=0, stream=None):
+    """The C1 flag case (channel 220 x 41, cylinder D = 10 with an elastic flag
+    of length 3.5 D and thickness 0.2 D, rho_s / rho_f = 10, Ae = 1.4e3,
+    parabolic inflow u_max = 0.05 with a 1000-step ramp) at Reynolds number
+    Re on the mean inflow speed and D, CSS-coupled.  Returns (Lattice, Beam,
+    first flag vertex)."""
+    from . import lbm, synth
+    from .lbm import Beam, Lattice
+    c = C1
+    nu = (2.0 / 3.0) * c["u_max"] * c["D"] / Re
+    beta = 1.0 / (6 * nu + 1)
+    prof = synth.parabolic_profile(c["ny"], c["u_max"], noise=1e-4, seed=seed)
+    x, e, body, _ = synth.cylinder_flag_2d()
+    X, EA, EI, rhoA, fixed = synth.c1_flag_beam()
+    ncyl = int(np.sum(body == 0))
+    L = Lattice(9, c["nx"], c["ny"], 1, beta, bc=c["bc"], max_links=4000, max_vertices=len(x),
+                max_elements=len(e), inlet_ramp_steps=c["ramp"], stream=stream)
+    L.set_inlet_profile(0, prof)
+    L.set_geometry(x, e, body, band_margin=8.0)
+    L.init_equilibrium(np.ones((1, c["ny"], c["nx"])), np.zeros((2, 1, c["ny"], c["nx"])))
+    beam = Beam(X, EA, EI, rhoA, fixed, thickness=c["h"], stream=L.stream)
+    lbm.fsi_couple(L.ctx, beam.ctx, ncyl)
+    return L, beam, ncyl

@@ -159,7 +159,8 @@ __device__ bool on_surface(const SurfaceDev &s, const double *p) {
       const double px = p[0] - a[0], py = p[1] - a[1];
       const double len2 = ex * ex + ey * ey;
       const double cr = ex * py - ey * px, dt = ex * px + ey * py;
-      if (fabs(cr) <= tol * sqrt(len2) && dt >= 0.0 && dt <= len2) return true;
+      // a zero-length element has no surface
+      if (len2 > 0.0 && fabs(cr) <= tol * sqrt(len2) && dt >= 0.0 && dt <= len2) return true;
     } else {
       const double *a = s.x + 3 * s.e[3 * k], *b = s.x + 3 * s.e[3 * k + 1],
                    *c = s.x + 3 * s.e[3 * k + 2];
@@ -215,8 +216,68 @@ __device__ bool inside_any(const SurfaceDev &s, const double *p) {
   return false;
 }
 
+// ---- FP32 filters over staged 2-D elements.  Every decision above is taken
+// in FP64; these filters only skip elements whose FP64 test cannot pass,
+// judged in FP32 with a margin T far above the FP32 rounding of the
+// endpoints and of the products (about 4e-7 of the coordinates), so the
+// filtered and unfiltered paths give identical flags and links.
+constexpr int kStageSeg = 1024;
+
+struct SegStage {
+  float4 seg[kStageSeg];          // (ax, ay, bx, by) rounded to FP32
+  unsigned char body[kStageSeg];
+};
+
+// Stage the elements of a 2-D surface (all threads of the CTA; the caller
+// synchronises).  Returns false when the surface is 3-D or too large.
+__device__ bool stage_segments(const SurfaceDev &s, SegStage &st) {
+  if (s.dim != 2 || s.ne > kStageSeg) return false;
+  for (int k = threadIdx.x; k < s.ne; k += blockDim.x) {
+    const double *a = s.x + 2 * s.e[2 * k], *b = s.x + 2 * s.e[2 * k + 1];
+    st.seg[k] = make_float4((float)a[0], (float)a[1], (float)b[0], (float)b[1]);
+    st.body[k] = (unsigned char)s.eb[k];
+  }
+  return true;
+}
+
+__device__ __forceinline__ float seg_margin(const float4 &q, float px, float py) {
+  return 4e-6f * (1.f + fabsf(px) + fabsf(py) + fabsf(q.x) + fabsf(q.y) + fabsf(q.z) + fabsf(q.w));
+}
+
+// inside_any for a 2-D surface through the staged filters.
+__device__ bool inside_any_staged(const SurfaceDev &s, const SegStage &st, const double *p) {
+  const float px = (float)p[0], py = (float)p[1];
+  const float dx = (float)c_ray2[0], dy = (float)c_ray2[1];
+  const double tol = 1e-12;
+  unsigned par = 0;
+  for (int k = 0; k < s.ne; ++k) {
+    const float4 q = st.seg[k];
+    const float T = seg_margin(q, px, py);
+    const float xlo = fminf(q.x, q.z), xhi = fmaxf(q.x, q.z);
+    const float ylo = fminf(q.y, q.w), yhi = fmaxf(q.y, q.w);
+    const bool near = px >= xlo - T && px <= xhi + T && py >= ylo - T && py <= yhi + T;
+    if (near) {  // on-surface test (as in on_surface)
+      const double *a = s.x + 2 * s.e[2 * k], *b = s.x + 2 * s.e[2 * k + 1];
+      const double ex = b[0] - a[0], ey = b[1] - a[1];
+      const double qx = p[0] - a[0], qy = p[1] - a[1];
+      const double len2 = ex * ex + ey * ey;
+      const double cr = ex * qy - ey * qx, dt = ex * qx + ey * qy;
+      if (len2 > 0.0 && fabs(cr) <= tol * sqrt(len2) && dt >= 0.0 && dt <= len2) return true;
+    }
+    if (xhi < px - T || yhi < py - T) continue;  // behind the node in x or y
+    const float sa = dx * (q.y - py) - dy * (q.x - px);
+    const float sb = dx * (q.w - py) - dy * (q.z - px);
+    if ((sa > T && sb > T) || (sa < -T && sb < -T)) continue;  // off the ray's line
+    const double *a = s.x + 2 * s.e[2 * k], *b = s.x + 2 * s.e[2 * k + 1];
+    if ((a[0] < p[0] && b[0] < p[0]) || (a[1] < p[1] && b[1] < p[1])) continue;
+    if (seg_ray_cross(p, c_ray2, a, b)) par ^= 1u << st.body[k];
+  }
+  return par != 0;
+}
+
 // Nearest crossing of x_b -> x_b - c over all elements; fills the link.
-__device__ void link_hit(const SurfaceDev &s, const double *xb, int cx, int cy, int cz, Link &L) {
+__device__ void link_hit(const SurfaceDev &s, const double *xb, int cx, int cy, int cz, Link &L,
+                         const SegStage *st = nullptr) {
   const double eps = 1e-9;
   const double d[3] = {-(double)cx, -(double)cy, -(double)cz};
   int best = -1;
@@ -228,8 +289,16 @@ __device__ void link_hit(const SurfaceDev &s, const double *xb, int cx, int cy, 
     lo[a] = fmin(xb[a], xb[a] + d[a]) - 1e-6;
     hi[a] = fmax(xb[a], xb[a] + d[a]) + 1e-6;
   }
+  const float flo0 = (float)lo[0], fhi0 = (float)hi[0], flo1 = (float)lo[1], fhi1 = (float)hi[1];
   for (int k = 0; k < s.ne; ++k) {
     if (s.dim == 2) {
+      if (st) {
+        const float4 q = st->seg[k];
+        const float T = seg_margin(q, flo0, flo1);
+        if (fmaxf(q.x, q.z) < flo0 - T || fminf(q.x, q.z) > fhi0 + T ||
+            fmaxf(q.y, q.w) < flo1 - T || fminf(q.y, q.w) > fhi1 + T)
+          continue;
+      }
       const double *a = s.x + 2 * s.e[2 * k], *b = s.x + 2 * s.e[2 * k + 1];
       if (fmax(a[0], b[0]) < lo[0] || fmin(a[0], b[0]) > hi[0] || fmax(a[1], b[1]) < lo[1] ||
           fmin(a[1], b[1]) > hi[1])
@@ -287,13 +356,19 @@ __device__ __forceinline__ void solid_flags_body(long long t, const Grid &g, con
                                                  const SurfaceDev &s, uint8_t *flags,
                                                  int64_t *fresh, int *nfresh, int cap,
                                                  int track_fresh) {
+  __shared__ SegStage st;
   const int bx = bd.x1 - bd.x0, by = bd.y1 - bd.y0, bz = bd.z1 - bd.z0;
-  if (t >= (long long)bx * by * bz) return;
+  const long long nbnd = (long long)bx * by * bz;
+  if ((long long)(t - threadIdx.x) >= nbnd) return;  // whole CTA past the band
+  const bool staged = stage_segments(s, st);
+  __syncthreads();
+  if (t >= nbnd) return;
   const int x = bd.x0 + (int)(t % bx), y = bd.y0 + (int)((t / bx) % by),
             z = bd.z0 + (int)(t / ((long long)bx * by));
   const double p[3] = {x + 0.5, y + 0.5, z + 0.5};  // cell-centred node position
   const long long k = sidx(g, x + g.px, y + g.py, z + g.pz);
-  const uint8_t now = inside_any(s, p) ? NODE_SOLID : NODE_FLUID;
+  const uint8_t now = (staged ? inside_any_staged(s, st, p) : inside_any(s, p)) ? NODE_SOLID
+                                                                               : NODE_FLUID;
   const uint8_t before = flags[k];
   if (before == NODE_GHOST) return;
   if (track_fresh && before == NODE_SOLID && now == NODE_FLUID) {
@@ -316,8 +391,13 @@ __device__ __forceinline__ void build_links_body(long long t, const Grid &g, con
                                                  BNode *bnodes, int *nbn, int bcap, Link *links,
                                                  int *nl, int lcap, int *err) {
   using L = Lat<Q>;
+  __shared__ SegStage st;
   const int bx = bd.x1 - bd.x0, by = bd.y1 - bd.y0, bz = bd.z1 - bd.z0;
-  if (t >= (long long)bx * by * bz) return;
+  const long long nbnd = (long long)bx * by * bz;
+  if ((long long)(t - threadIdx.x) >= nbnd) return;  // whole CTA past the band
+  const bool staged = stage_segments(s, st);
+  __syncthreads();
+  if (t >= nbnd) return;
   const int x = bd.x0 + (int)(t % bx), y = bd.y0 + (int)((t / bx) % by),
             z = bd.z0 + (int)(t / ((long long)bx * by));
   const int X = x + g.px, Y = y + g.py, Z = z + g.pz;
@@ -351,7 +431,7 @@ __device__ __forceinline__ void build_links_body(long long t, const Grid &g, con
     if (!(mask & (1u << i))) continue;
     Link lk;
     lk.i = i;
-    link_hit(s, xb, L::cx(i), L::cy(i), L::cz(i), lk);
+    link_hit(s, xb, L::cx(i), L::cy(i), L::cz(i), lk, staged ? &st : nullptr);
     links[l0 + m++] = lk;
   }
 }

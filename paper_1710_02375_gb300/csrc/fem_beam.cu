@@ -33,6 +33,7 @@ namespace kbc {
 
 constexpr int KB = 5;            // half bandwidth
 constexpr int BW = 2 * KB + 1;   // band width
+constexpr int kMaxN = 3 * kMaxBeamNodes, kMaxE = kMaxBeamNodes - 1;
 
 
 __device__ __forceinline__ double &band(double *A, int i, int j) { return A[i * BW + (j - i + KB)]; }
@@ -125,6 +126,17 @@ __device__ void element_mass(const BeamParams &p, const double *X, int e, double
     }
 }
 
+// Consistent mass matrix (band storage), constant: the reference orientation.
+__global__ void k_beam_mass(BeamParams p, const double *X, double *M) {
+  const int n = 3 * p.nn, ne = p.nn - 1;
+  for (int i = threadIdx.x; i < n * BW; i += blockDim.x) M[i] = 0.0;
+  __syncthreads();
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int e = 2 * threadIdx.x + pass; e < ne; e += 2 * blockDim.x) element_mass(p, X, e, M);
+    __syncthreads();
+  }
+}
+
 // Surface of the flag around the beam: bottom vertices 0..nn-1 (node order),
 // top vertices nn..2nn-1 (reverse node order), offset h/2 along the normal of
 // each cross-section.
@@ -140,39 +152,128 @@ __device__ void flag_vertex(const BeamParams &p, const double *X, const double *
   vt[0] = v[3 * j] + 0.5 * p.h * dnx; vt[1] = v[3 * j + 1] + 0.5 * p.h * dny;
 }
 
+// ---- per-step work split for GB300's FP64 rate: each FP64 warp instruction
+// occupies the FP64 pipe for many cycles, so the step is organised to keep
+// FP64 instruction counts per warp low -- element scalars once per element,
+// internal forces and tangent entries spread over the CTA, the banded
+// factorisation with one lane per update entry, no divisions in loops.
+
+// Reciprocal by Newton's iteration for 1/x, r <- r (2 - x r), from the FP32
+// reciprocal as seed (relative error below 2^-22): two iterations leave an
+// error below 2^-52 before the final rounding.
+__device__ __forceinline__ double recip_newton(double x) {
+  if (!(fabs(x) > 1e-30 && fabs(x) < 1e30)) return 1.0 / x;  // outside the FP32 seed's range
+  double r = (double)(1.0f / (float)x);
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
+// Upper-triangle index pairs (k <= l) of a 6 x 6 element matrix.
+__constant__ unsigned char c_pk[21] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 2, 2, 2, 2, 3, 3, 3, 4, 4, 5};
+__constant__ unsigned char c_pl[21] = {0, 1, 2, 3, 4, 5, 1, 2, 3, 4, 5, 2, 3, 4, 5, 3, 4, 5, 4, 5, 5};
+
+// r and z vectors of the co-rotational element (local DOF k of nodes a, b).
+__device__ __forceinline__ double elem_r(int k, double c, double s) {
+  const double v = (k % 3 == 0) ? c : ((k % 3 == 1) ? s : 0.0);
+  return k < 3 ? -v : v;
+}
+__device__ __forceinline__ double elem_z(int k, double c, double s) {
+  const double v = (k % 3 == 0) ? s : ((k % 3 == 1) ? -c : 0.0);
+  return k < 3 ? v : -v;
+}
+
+struct BeamShared {
+  double J[kMaxN * BW], M[kMaxN * BW];
+  double u[kMaxN], u0[kMaxN], v0[kMaxN], f0[kMaxN], F1[kMaxN], R[kMaxN], D[kMaxN];
+  double inv[kMaxN];
+  double X[2 * kMaxBeamNodes];
+  // element scalars: constants of the step, then the current state's
+  double L0[kMaxE], b0[kMaxE], EAL0[kMaxE], k2[kMaxE];
+  double c[kMaxE], s[kMaxE], iL[kMaxE], N[kMaxE], M1[kMaxE], M2[kMaxE];
+  double red[4];
+};
+
+// Element state scalars at the displacement in S.u (thread per element).
+__device__ __forceinline__ void elem_state(const BeamParams &p, BeamShared &S, const double *u,
+                                           int ne) {
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+    const int a = e, b = e + 1;
+    const double dx = S.X[2 * b] - S.X[2 * a] + u[3 * b] - u[3 * a];
+    const double dy = S.X[2 * b + 1] - S.X[2 * a + 1] + u[3 * b + 1] - u[3 * a + 1];
+    const double L = sqrt(dx * dx + dy * dy);
+    const double iL = 1.0 / L;
+    double rot = atan2(dy, dx) - S.b0[e];
+    const double PI = 3.14159265358979323846;
+    if (rot > PI) rot -= 2 * PI;
+    if (rot <= -PI) rot += 2 * PI;
+    const double t1 = u[3 * a + 2] - rot, t2 = u[3 * b + 2] - rot;
+    S.c[e] = dx * iL;
+    S.s[e] = dy * iL;
+    S.iL[e] = iL;
+    S.N[e] = S.EAL0[e] * (L - S.L0[e]);
+    S.M1[e] = S.k2[e] * (2 * t1 + t2);
+    S.M2[e] = S.k2[e] * (t1 + 2 * t2);
+  }
+}
+
+// Internal force of DOF i from its (at most two) elements.
+__device__ __forceinline__ double dof_internal(const BeamShared &S, int i, int ne) {
+  const int j = i / 3, q = i % 3;
+  double f = 0.0;
+  for (int side = 0; side < 2; ++side) {
+    const int e = side == 0 ? j - 1 : j;  // element with node j as its b / a node
+    if (e < 0 || e >= ne) continue;
+    const int k = side == 0 ? 3 + q : q;
+    const double c = S.c[e], s = S.s[e];
+    f += elem_r(k, c, s) * S.N[e] - elem_z(k, c, s) * S.iL[e] * (S.M1[e] + S.M2[e]) +
+         (k == 2 ? S.M1[e] : 0.0) + (k == 5 ? S.M2[e] : 0.0);
+  }
+  return f;
+}
+
+// Block sum of one value per thread (all threads call; result to all).
+__device__ __forceinline__ double block_sum(BeamShared &S, double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) S.red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += S.red[k];
+  return t;
+}
+
 // One structural step.  Loads F1 come from F1_in (standalone) or from the
 // momentum-exchange forces of the flag's surface vertices (coupled: vforce,
 // surf_x / surf_v of the whole surface, the flag's vertices start at v0).
+// Launch: one CTA of 128 threads per beam.
 template <bool COUPLED>
 __device__ __forceinline__ void beam_step_body(const BeamParams &p, const BeamDev &d,
                                                const double *__restrict__ F1_in,
                                                const double *__restrict__ vforce, double *surf_x,
                                                double *surf_v, int v0) {
-  __shared__ double sJ[3 * kMaxBeamNodes * BW], sM[3 * kMaxBeamNodes * BW];
-  __shared__ double su[3 * kMaxBeamNodes], su0[3 * kMaxBeamNodes], sv0[3 * kMaxBeamNodes];
-  __shared__ double sf0[3 * kMaxBeamNodes], sf1[3 * kMaxBeamNodes], sF1[3 * kMaxBeamNodes];
-  __shared__ double sR[3 * kMaxBeamNodes], sX[2 * kMaxBeamNodes];
-  __shared__ double red[128];
-  __shared__ int s_done;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  __shared__ BeamShared S;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
   const int nn = p.nn, n = 3 * nn, ne = nn - 1;
+  const double a_v = 1.0 / (p.theta * p.dt), i_th = 1.0 / p.theta, i_dt = 1.0 / p.dt;
+  const double cM = 1.0 / (p.theta * p.dt * p.dt);
   for (int i = tid; i < n; i += nt) {
-    su0[i] = d.u[i];
-    su[i] = (d.u_guess && !d.fixed[i]) ? d.u_guess[i] : d.u[i];
-    sv0[i] = d.v[i];
-    sf0[i] = 0.0;
-    sf1[i] = 0.0;
+    S.u0[i] = d.u[i];
+    S.u[i] = (d.u_guess && !d.fixed[i]) ? d.u_guess[i] : d.u[i];
+    S.v0[i] = d.v[i];
   }
-  for (int i = tid; i < 2 * nn; i += nt) sX[i] = d.X[i];
-  for (int i = tid; i < n * BW; i += nt) sM[i] = 0.0;
+  for (int i = tid; i < n * BW; i += nt) S.M[i] = d.M[i];
+  for (int i = tid; i < 2 * nn; i += nt) S.X[i] = d.X[i];
   __syncthreads();
-  // ---- mass matrix and f(u0), two colour passes
-  for (int pass = 0; pass < 2; ++pass) {
-    for (int e = 2 * tid + pass; e < ne; e += 2 * nt) {
-      element_mass(p, sX, e, sM);
-      element_internal(p, sX, su0, e, sf0, nullptr);
-    }
-    __syncthreads();
+  for (int e = tid; e < ne; e += nt) {
+    const double X0x = S.X[2 * e + 2] - S.X[2 * e], X0y = S.X[2 * e + 3] - S.X[2 * e + 1];
+    const double L0 = sqrt(X0x * X0x + X0y * X0y);
+    S.L0[e] = L0;
+    S.b0[e] = atan2(X0y, X0x);
+    S.EAL0[e] = p.EA / L0;
+    S.k2[e] = 2.0 * p.EI / L0;
   }
   // ---- loads F1
   if (COUPLED) {
@@ -181,88 +282,61 @@ __device__ __forceinline__ void beam_step_body(const BeamParams &p, const BeamDe
     // rotation is a stiff mode that the staggered one-step lag destabilises)
     for (int j = tid; j < nn; j += nt) {
       const int vb = v0 + j, vt = v0 + 2 * nn - 1 - j;
-      sF1[3 * j] = vforce[3 * vb] + vforce[3 * vt];
-      sF1[3 * j + 1] = vforce[3 * vb + 1] + vforce[3 * vt + 1];
-      sF1[3 * j + 2] = 0.0;
+      S.F1[3 * j] = vforce[3 * vb] + vforce[3 * vt];
+      S.F1[3 * j + 1] = vforce[3 * vb + 1] + vforce[3 * vt + 1];
+      S.F1[3 * j + 2] = 0.0;
     }
   } else {
-    for (int i = tid; i < n; i += nt) sF1[i] = F1_in[i];
+    for (int i = tid; i < n; i += nt) S.F1[i] = F1_in[i];
   }
   __syncthreads();
+  // ---- f(u0)
+  elem_state(p, S, S.u0, ne);
+  __syncthreads();
+  double fe2 = 0.0;
+  for (int i = tid; i < n; i += nt) {
+    S.f0[i] = dof_internal(S, i, ne);
+    const double fe = d.fixed[i] ? 0.0 : p.theta * S.F1[i] + (1.0 - p.theta) * d.F0[i];
+    fe2 += fe * fe;
+  }
+  __syncthreads();
+  const double fext = sqrt(block_sum(S, fe2));
   // ---- Newton iterations with the constant relaxation lambda.  The
-  // convergence test is relative to the residual at the start u0 (f(u0) is
-  // sf0), also when the iteration starts from a surrogate guess, so that a
-  // guess changes where Newton starts but not where it stops.
+  // convergence test is relative to the residual at the start u0, also when
+  // the iteration starts from a surrogate guess, so that a guess changes
+  // where Newton starts but not where it stops.
   double r0 = -1.0;
   if (d.u_guess) {
     double part = 0.0;
     for (int i = tid; i < n; i += nt) {
       double mv = 0.0;
       for (int j = (i - KB > 0 ? i - KB : 0); j <= (i + KB < n - 1 ? i + KB : n - 1); ++j)
-        mv += band(sM, i, j) * (-(1.0 - p.theta) / p.theta * sv0[j] - sv0[j]);
-      double R = mv / p.dt - p.theta * (sF1[i] - sf0[i]) - (1.0 - p.theta) * (d.F0[i] - sf0[i]);
+        mv += band(S.M, i, j) * (-S.v0[j] * i_th);
+      const double R = mv * i_dt - p.theta * (S.F1[i] - S.f0[i]) - (1.0 - p.theta) * (d.F0[i] - S.f0[i]);
       if (!d.fixed[i]) part += R * R;
     }
-    red[tid] = part;
-    __syncthreads();
-    if (tid == 0) {
-      double t = 0.0;
-      for (int k = 0; k < nt; ++k) t += red[k];
-      red[0] = sqrt(t);
-    }
-    __syncthreads();
-    r0 = red[0];
-    __syncthreads();
+    r0 = sqrt(block_sum(S, part));
   }
   int it = 0, conv = 0;
   for (it = 0; it < p.max_it; ++it) {
-    for (int i = tid; i < n; i += nt) sf1[i] = 0.0;
-    for (int i = tid; i < n * BW; i += nt) sJ[i] = 0.0;
+    elem_state(p, S, S.u, ne);
+    for (int i = tid; i < n; i += nt) S.D[i] = (S.u[i] - S.u0[i]) * a_v - S.v0[i] * i_th;
     __syncthreads();
-    for (int pass = 0; pass < 2; ++pass) {
-      for (int e = 2 * tid + pass; e < ne; e += 2 * nt) element_internal(p, sX, su, e, sf1, sJ);
-      __syncthreads();
-    }
-    // residual
     double part = 0.0;
     for (int i = tid; i < n; i += nt) {
       double mv = 0.0;
-      for (int j = (i - KB > 0 ? i - KB : 0); j <= (i + KB < n - 1 ? i + KB : n - 1); ++j) {
-        const double v1 = ((su[j] - su0[j]) / p.dt - (1.0 - p.theta) * sv0[j]) / p.theta;
-        mv += band(sM, i, j) * (v1 - sv0[j]);
-      }
-      double R = mv / p.dt - p.theta * (sF1[i] - sf1[i]) - (1.0 - p.theta) * (d.F0[i] - sf0[i]);
+      for (int j = (i - KB > 0 ? i - KB : 0); j <= (i + KB < n - 1 ? i + KB : n - 1); ++j)
+        mv += band(S.M, i, j) * S.D[j];
+      const double f = dof_internal(S, i, ne);
+      double R = mv * i_dt - p.theta * (S.F1[i] - f) - (1.0 - p.theta) * (d.F0[i] - S.f0[i]);
       if (d.fixed[i]) R = 0.0;
-      sR[i] = R;
+      S.R[i] = -R;  // right-hand side of J du = -R
       part += R * R;
     }
-    red[tid] = part;
-    __syncthreads();
-    if (tid == 0) {
-      double t = 0.0;
-      for (int k = 0; k < nt; ++k) t += red[k];
-      red[0] = sqrt(t);
-    }
-    __syncthreads();
-    const double rn = red[0];
+    const double rn = sqrt(block_sum(S, part));
     if (it == 0 && d.u_guess && p.accept_tol > 0.0) {
       // surrogate guess: accept it when the residual is small against the loads
-      double fp = 0.0;
-      for (int i = tid; i < n; i += nt) {
-        const double fe = d.fixed[i] ? 0.0 : p.theta * sF1[i] + (1.0 - p.theta) * d.F0[i];
-        fp += fe * fe;
-      }
-      __syncthreads();
-      red[tid] = fp;
-      __syncthreads();
-      if (tid == 0) {
-        double tsum = 0.0;
-        for (int k = 0; k < nt; ++k) tsum += red[k];
-        red[0] = sqrt(tsum);
-      }
-      __syncthreads();
-      const bool accept = rn <= p.accept_tol * red[0];
-      __syncthreads();
+      const bool accept = rn <= p.accept_tol * fext;
       if (tid == 0 && d.stats) atomicAdd(&d.stats[accept ? 0 : 1], 1);
       if (accept) {
         conv = 1;
@@ -274,48 +348,72 @@ __device__ __forceinline__ void beam_step_body(const BeamParams &p, const BeamDe
       conv = 1;
       break;
     }
-    // Jacobian M/(th dt^2) + th K with Dirichlet rows/columns
+    // ---- Jacobian M / (theta dt^2) + theta K (band), Dirichlet rows/columns
+    for (int i = tid; i < n * BW; i += nt) S.J[i] = S.M[i] * cM;
+    __syncthreads();
+    for (int colour = 0; colour < 2; ++colour) {
+      const int nel = (ne - colour + 1) / 2;  // elements colour, colour + 2, ...
+      for (int w = tid; w < nel * 21; w += nt) {
+        const int e = colour + 2 * (w / 21), pk = c_pk[w % 21], pl = c_pl[w % 21];
+        const double c = S.c[e], s = S.s[e], iL = S.iL[e], k2 = S.k2[e];
+        const double rk = elem_r(pk, c, s), rl = elem_r(pl, c, s);
+        const double zk = elem_z(pk, c, s), zl = elem_z(pl, c, s);
+        const double b1k = -zk * iL + (pk == 2 ? 1.0 : 0.0), b2k = -zk * iL + (pk == 5 ? 1.0 : 0.0);
+        const double b1l = -zl * iL + (pl == 2 ? 1.0 : 0.0), b2l = -zl * iL + (pl == 5 ? 1.0 : 0.0);
+        double v = S.EAL0[e] * rk * rl + b1k * (2 * k2 * b1l + k2 * b2l) +
+                   b2k * (k2 * b1l + 2 * k2 * b2l) + S.N[e] * iL * zk * zl +
+                   (S.M1[e] + S.M2[e]) * iL * iL * (rk * zl + zk * rl);
+        v *= p.theta;
+        const int gi = 3 * e + pk, gj = 3 * e + pl;
+        band(S.J, gi, gj) += v;
+        if (pk != pl) band(S.J, gj, gi) += v;
+      }
+      __syncthreads();
+    }
     for (int idx = tid; idx < n * BW; idx += nt) {
       const int i = idx / BW, j = i + idx % BW - KB;
-      double v = 0.0;
-      if (j >= 0 && j < n) v = sM[idx] / (p.theta * p.dt * p.dt) + p.theta * sJ[idx];
-      if (j >= 0 && j < n && (d.fixed[i] || d.fixed[j])) v = (i == j) ? 1.0 : 0.0;
-      sJ[idx] = v;
+      if (j >= 0 && j < n && (d.fixed[i] || d.fixed[j])) S.J[idx] = (i == j) ? 1.0 : 0.0;
     }
     __syncthreads();
-    if (tid == 0) {
-      // banded LU (Doolittle, no pivoting) on -R, in place
-      for (int i = 0; i < n; ++i) sR[i] = -sR[i];
+    if (tid < 32) {
+      // banded LU without pivoting (Doolittle) on J du = -R: one lane per
+      // entry of the KB x KB trailing update and of the KB right-hand sides
+      const int r = lane < 25 ? lane / 5 + 1 : lane - 24, c = lane < 25 ? lane % 5 + 1 : 0;
       for (int k = 0; k < n; ++k) {
-        const double piv = band(sJ, k, k);
-        const int iend = (k + KB < n - 1) ? k + KB : n - 1;
-        for (int i = k + 1; i <= iend; ++i) {
-          const double m = band(sJ, i, k) / piv;
-          if (m == 0.0) continue;
-          for (int j = k + 1; j <= iend; ++j) band(sJ, i, j) -= m * band(sJ, k, j);
-          sR[i] -= m * sR[k];
+        const double inv = recip_newton(band(S.J, k, k));
+        if (lane < 30 && k + r < n) {
+          const double m = band(S.J, k + r, k) * inv;
+          if (lane < 25) {
+            if (k + c < n) band(S.J, k + r, k + c) -= m * band(S.J, k, k + c);
+          } else {
+            S.R[k + r] -= m * S.R[k];
+          }
+        }
+        if (lane == 0) S.inv[k] = inv;
+        __syncwarp();
+      }
+      if (lane == 0) {
+        for (int k = n - 1; k >= 0; --k) {
+          double sum = S.R[k];
+          const int jend = (k + KB < n - 1) ? k + KB : n - 1;
+          for (int j = k + 1; j <= jend; ++j) sum -= band(S.J, k, j) * S.R[j];
+          S.R[k] = sum * S.inv[k];
         }
       }
-      for (int k = n - 1; k >= 0; --k) {
-        double sum = sR[k];
-        const int jend = (k + KB < n - 1) ? k + KB : n - 1;
-        for (int j = k + 1; j <= jend; ++j) sum -= band(sJ, k, j) * sR[j];
-        sR[k] = sum / band(sJ, k, k);
-      }
     }
     __syncthreads();
-    for (int i = tid; i < n; i += nt) su[i] += p.lambda * sR[i];
+    for (int i = tid; i < n; i += nt) S.u[i] += p.lambda * S.R[i];
     __syncthreads();
   }
   // ---- final velocities, state, loads
   for (int i = tid; i < n; i += nt) {
-    double ui = su[i], vi = ((su[i] - su0[i]) / p.dt - (1.0 - p.theta) * sv0[i]) / p.theta;
+    double ui = S.u[i], vi = (S.u[i] - S.u0[i]) * a_v - (1.0 - p.theta) * i_th * S.v0[i];
     if (d.fixed[i]) { ui = 0.0; vi = 0.0; }
     d.u[i] = ui;
     d.v[i] = vi;
-    d.F0[i] = sF1[i];
-    su[i] = ui;
-    sR[i] = vi;
+    d.F0[i] = S.F1[i];
+    S.u[i] = ui;
+    S.R[i] = vi;
   }
   if (tid == 0) {
     *d.iters = conv ? it : -it - 1;
@@ -329,7 +427,7 @@ __device__ __forceinline__ void beam_step_body(const BeamParams &p, const BeamDe
     // transfer displacement and velocity to the surface mesh
     for (int j = tid; j < nn; j += nt) {
       double xb[2], vb[2], xt[2], vt[2];
-      flag_vertex(p, sX, su, sR, j, xb, vb, xt, vt);
+      flag_vertex(p, S.X, S.u, S.R, j, xb, vb, xt, vt);
       const int ib = v0 + j, it2 = v0 + 2 * nn - 1 - j;
       surf_x[2 * ib] = xb[0]; surf_x[2 * ib + 1] = xb[1];
       surf_v[2 * ib] = vb[0]; surf_v[2 * ib + 1] = vb[1];
@@ -337,7 +435,6 @@ __device__ __forceinline__ void beam_step_body(const BeamParams &p, const BeamDe
       surf_v[2 * it2] = vt[0]; surf_v[2 * it2 + 1] = vt[1];
     }
   }
-  (void)s_done;
 }
 
 template <bool COUPLED>
@@ -387,6 +484,7 @@ static size_t fem_bytes(int nn) {
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
   const size_t nin = surrogate_inputs(nn), nout = 3 * (size_t)nn - 3;
   return al(sizeof(double) * 2 * nn) + al(sizeof(int32_t) * n) + 4 * al(sizeof(double) * n) +
+         al(sizeof(double) * n * BW) +
          al(sizeof(int)) + al(sizeof(double) * 6 * nn) + al(sizeof(double) * n) +
          al(kFemStats * sizeof(int)) + 2 * al(sizeof(float) * nin) + 2 * al(sizeof(float) * nout);
 }
@@ -446,6 +544,7 @@ lbm_status fem_beam_create(const fem_beam_config *c, void *workspace, size_t byt
   double *F0 = (double *)p; p += al(sizeof(double) * n);
   double *F1 = (double *)p; p += al(sizeof(double) * n);
   int *iters = (int *)p; p += al(sizeof(int));
+  double *Mb = (double *)p; p += al(sizeof(double) * n * BW);
   const size_t nin = surrogate_inputs(nn), nout = 3 * (size_t)nn - 3;
   f->hist = (double *)p; p += al(sizeof(double) * 6 * nn);
   f->u_guess = (double *)p; p += al(sizeof(double) * n);
@@ -456,7 +555,7 @@ lbm_status fem_beam_create(const fem_beam_config *c, void *workspace, size_t byt
   f->out_std = (float *)p;
   f->p = BeamParams{nn, c->EA, c->EI, c->rhoA, c->thickness, c->theta, c->lambda, c->rtol,
                     c->atol, c->dt, c->max_it, 0.0};
-  f->d = BeamDev{X, fx, u, v, F0, iters, nullptr, f->stats};
+  f->d = BeamDev{X, fx, u, v, F0, iters, nullptr, f->stats, Mb};
   f->F1 = F1;
   cudaError_t e = cudaMemcpyAsync(X, c->X, sizeof(double) * 2 * nn, cudaMemcpyDefault, f->stream);
   if (e == cudaSuccess)
@@ -465,6 +564,10 @@ lbm_status fem_beam_create(const fem_beam_config *c, void *workspace, size_t byt
   if (e == cudaSuccess) e = cudaMemsetAsync(v, 0, sizeof(double) * n, f->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(F0, 0, sizeof(double) * n, f->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(iters, 0, sizeof(int), f->stream);
+  if (e == cudaSuccess) {
+    k_beam_mass<<<1, 128, 0, f->stream>>>(f->p, X, Mb);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(f->hist, 0, sizeof(double) * 6 * nn, f->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(f->stats, 0, kFemStats * sizeof(int), f->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);

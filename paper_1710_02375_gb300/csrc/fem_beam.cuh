@@ -5,7 +5,7 @@
 
 namespace kbc {
 
-constexpr int kMaxBeamNodes = 64;
+constexpr int kMaxBeamNodes = 48;
 
 struct BeamParams {
   int nn;
@@ -21,7 +21,8 @@ struct BeamDev {
   double *u, *v, *F0;  // [3nn] state and previous loads
   int *iters;          // last step's Newton iteration count (negative: not converged)
   const double *u_guess;  // [3nn] Newton initial guess (nullptr: the current state)
-  int *stats;          // [2]: guesses accepted, guesses rejected (FEM fallback)
+  int *stats;          // accepted / rejected guesses, Newton solves, steps
+  const double *M;     // [3nn][11] consistent mass matrix, band storage (constant)
 };
 
 // A coupled beam of a batch: its state and the surface arrays of its lattice.

@@ -41,15 +41,6 @@ def oracle_pairs(args):
 
 def gpu_run(Re, seed=0):
     """(Lattice, Beam) of the CUDA library, coupled, at step 0."""
-    from paper_1710_02375_gb300 import lbm as abi
-    from paper_1710_02375_gb300.lbm import Beam, Lattice
-    c = case(Re, seed)
-    X, EA, EI, rhoA, fixed = c["beam"]
-    L = Lattice(9, NX, NY, 1, c["beta"], bc=BC, max_links=4000, max_vertices=len(c["x"]),
-                max_elements=len(c["e"]), inlet_ramp_steps=RAMP)
-    L.set_inlet_profile(0, c["prof"])
-    L.set_geometry(c["x"], c["e"], c["body"], band_margin=8.0)
-    L.init_equilibrium(np.ones((1, NY, NX)), np.zeros((2, 1, NY, NX)))
-    gb = Beam(X, EA, EI, rhoA, fixed, thickness=H, stream=L.stream)
-    abi.fsi_couple(L.ctx, gb.ctx, c["ncyl"])
+    from paper_1710_02375_gb300.cases import c1_coupled
+    L, gb, _ = c1_coupled(Re, seed)
     return L, gb
