@@ -341,6 +341,22 @@ lbm_status fsi_set_surrogate(lbm_ctx *ctx, mlp_ctx *mlp, const float *in_mean, c
  * Synchronises. */
 lbm_status fsi_get_structure_stats(lbm_ctx *ctx, int stats[4], int reset);
 
+/* Fluid-stress traction on the immersed surfaces (the paper's force path,
+ * section "Fluid-structure coupling"; the momentum-exchange force of
+ * lbm_get_interface_force is the primary one).  While enabled, every step
+ * evaluates sigma_f = -(rho - 1) c_s^2 I - (1 - beta) (Pi - Pi_eq) at the
+ * immersed boundary nodes from the step's pre-collision populations (after
+ * the Grad fill), gives each surface element the stress of the boundary node
+ * nearest to its centroid (ties: lower node index), and integrates
+ * t = sigma n over the element (n: outward unit normal of its body in the
+ * current configuration; length per unit depth in 2-D, area in 3-D).
+ * Outputs (FP64, like lbm_get_interface_force): vert_force[nv][3] (each
+ * element's force shared equally by its vertices) and body_force[nbodies][3].
+ * lbm_get_traction_force fails with LBM_ESTATE while the output is off.
+ * Synchronises. */
+lbm_status lbm_set_traction_output(lbm_ctx *ctx, int enable);
+lbm_status lbm_get_traction_force(lbm_ctx *ctx, double *vert_force, double *body_force);
+
 /* Density rho[nz][ny][nx] and velocity u[dim][nz][ny][nx] of the current
  * state (FP64 outputs; solid nodes give rho = 0, u = 0).  Synchronises. */
 lbm_status lbm_get_macros(lbm_ctx *ctx, double *rho, double *u);

@@ -350,18 +350,51 @@ static double grad_pop(const lat_t *L, int i, double rho, const double *u, const
   return L->w[i] * (rho + rho * cu / cs2 + contr / (2.0 * cs2 * cs2));
 }
 
+/* Fluid stress at a node from its pre-collision populations f (section
+ * "Fluid-structure coupling": sigma_f = -p I - (1 - beta) Pi^(1)), with the
+ * pressure relative to the rest state, p = (rho - 1) c_s^2, and
+ * Pi^(1) = Pi - Pi_eq, both second moments summed over the populations and
+ * over the entropic equilibrium of (rho, u).  out: xx, yy, zz, xy, xz, yz
+ * (zz = 0 on D2Q9), then 1. */
+static void node_stress(const lat_t *L, int lat, double beta, const double *f, double *out) {
+  double rho = 0.0, j[3] = {0, 0, 0};
+  for (int i = 0; i < L->Q; ++i) {
+    rho += f[i];
+    for (int a = 0; a < 3; ++a) j[a] += L->c[i][a] * f[i];
+  }
+  double u[3] = {j[0] / rho, j[1] / rho, j[2] / rho};
+  double feq[MAXQ];
+  or_equilibrium(lat, rho, u, feq);
+  const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+  const double p = (rho - 1.0) / 3.0;
+  for (int m = 0; m < 6; ++m) {
+    double P = 0.0, E = 0.0;
+    for (int i = 0; i < L->Q; ++i) {
+      const double cc = (double)(L->c[i][ia[m]] * L->c[i][ib[m]]);
+      P += cc * f[i];
+      E += cc * feq[i];
+    }
+    out[m] = (m < 3 ? -p : 0.0) - (1.0 - beta) * (P - E);
+  }
+  if (L->D == 2) out[2] = 0.0;
+  out[6] = 1.0;
+}
+
 /* One time step with boundaries.
  *  bc[6], face_u[6][3]: face kinds / velocities; inlet_u: per face an array
  *  [3][face nodes] (NULL entries: face_u is used), scaled by inlet_scale.
  *  solid[n]: immersed solid mask (interior); surface: mesh for link data.
  *  fin/fout: [Q][n] post-collision states (fout of solid nodes is set to 0).
  *  vforce[nv][3] and bforce[nb][3] are overwritten with the momentum-exchange
- *  force of this step (may be NULL).  Returns the number of immersed links. */
+ *  force of this step (may be NULL).  sigma[n][7] (may be NULL): at every
+ *  fluid node with an immersed solid neighbour the fluid stress of its
+ *  pre-collision populations (node_stress), other nodes untouched.
+ *  Returns the number of immersed links. */
 int or_step_bc(int lat, int nx, int ny, int nz, double beta, int mode, const int *bc,
                const double *face_u, const double *const *inlet_u, double inlet_scale,
                const uint8_t *solid, int nv, int ne, int nb, const double *vx, const double *vv,
                const int32_t *el, const int32_t *eb, const double *fin, double *fout,
-               double *vforce, double *bforce) {
+               double *vforce, double *bforce, double *sigma) {
   lat_t L;
   if (lat_make(lat, &L)) return -1;
   field_t F;
@@ -514,6 +547,11 @@ int or_step_bc(int lat, int nx, int ny, int nz, double beta, int mode, const int
               }
             }
           }
+        }
+        if (sigma) {
+          int immersed = 0;
+          for (int i = 0; i < Q; ++i) immersed |= miss[i] && face_of[i] < 0;
+          if (immersed) node_stress(&L, lat, beta, f, sigma + 7 * k);
         }
         double fo[MAXQ];
         or_collide(lat, beta, mode, f, fo, NULL, NULL, NULL, NULL);

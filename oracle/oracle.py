@@ -62,7 +62,7 @@ def _declare(L):
     L.or_solid_mask.argtypes = [c_int, c_int, c_int, c_int, c_int, c_int, c_int, D, I32, I32, U8]
     L.or_step_bc.argtypes = [c_int, c_int, c_int, c_int, c_double, c_int, I32, D,
                              ctypes.POINTER(D), c_double, U8, c_int, c_int, c_int, D, D, I32, I32,
-                             D, D, D, D]
+                             D, D, D, D, D]
     L.or_beam_step.argtypes = [c_int, D, c_double, c_double, c_double, I32, c_double, c_double,
                                c_double, c_double, c_double, c_int, D, D, D, D]
     L.or_beam_static.argtypes = [c_int, D, c_double, c_double, I32, D, c_double, c_double, c_double,
@@ -191,11 +191,14 @@ def solid_mask(shape, surf: "Surface") -> np.ndarray:
 
 
 def step_bc(lat, beta, f, bc, face_u=None, inlet=None, inlet_scale=1.0, surf=None, solid=None,
-            mode=0):
+            mode=0, want_sigma=False):
     """One step with Grad boundaries (walls, open faces, immersed surfaces).
 
     bc: 6 face kinds; face_u[6,3]; inlet: dict face -> profile [3, face nodes];
-    returns (f_new, vertex_force[nv,3], body_force[nb,3], n_links)."""
+    returns (f_new, vertex_force[nv,3], body_force[nb,3], n_links), plus
+    sigma[nz, ny, nx, 7] when want_sigma (fluid stress xx, yy, zz, xy, xz, yz
+    of the pre-collision state at immersed boundary nodes, last entry 1 there
+    and 0 elsewhere)."""
     f = np.ascontiguousarray(f, dtype=np.float64)
     Q, nz, ny, nx = f.shape
     dim = 2 if lat == 9 else 3
@@ -222,11 +225,65 @@ def step_bc(lat, beta, f, bc, face_u=None, inlet=None, inlet_scale=1.0, surf=Non
     v = surf.v if nv else np.zeros((1, dim))
     e = surf.e if ne else np.zeros((1, dim), np.int32)
     b = surf.body if ne else np.zeros(1, np.int32)
+    sig = np.zeros((nz, ny, nx, 7)) if want_sigma else None
     n = lib().or_step_bc(lat, nx, ny, nz, float(beta), int(mode), bcv.ctypes.data_as(I32), _p(fu), arr,
                          float(inlet_scale), solid.ctypes.data_as(U8), nv, ne, surf.nb, _p(x), _p(v),
-                         e.ctypes.data_as(I32), b.ctypes.data_as(I32), _p(f), _p(fo), _p(vf), _p(bf))
+                         e.ctypes.data_as(I32), b.ctypes.data_as(I32), _p(f), _p(fo), _p(vf), _p(bf),
+                         _p(sig) if sig is not None else None)
     _check(n)
+    if want_sigma:
+        return fo, vf[:nv], bf[: surf.nb], n, sig
     return fo, vf[:nv], bf[: surf.nb], n
+
+
+def traction(surf: "Surface", sigma):
+    """Surface traction forces from the boundary-node stresses of step_bc
+    (section "Fluid-structure coupling", the stress path): each element takes
+    the stress of the boundary node nearest to its centroid (squared distance
+    summed over the axes in order; ties: the lower node index (z, y, x)),
+    t = sigma n with n the outward unit normal of its body (orientation from
+    the body's signed area / volume), times the element length (2-D) or area
+    (3-D); the force is shared equally by the element's vertices.
+    Returns (vertex_force[nv,3], body_force[nb,3], element_force[ne,3])."""
+    dim = surf.x.shape[1]
+    nz, ny, nx, _ = sigma.shape
+    zz, yy, xx = np.nonzero(sigma[..., 6] == 1.0)          # C order = increasing index
+    pos = np.stack([xx + 0.5, yy + 0.5, zz + 0.5], axis=1)
+    orient = np.zeros(surf.nb)
+    for k, el in enumerate(surf.e):
+        P = surf.x[el]
+        if dim == 2:
+            orient[surf.body[k]] += 0.5 * (P[0, 0] * P[1, 1] - P[1, 0] * P[0, 1])
+        else:
+            orient[surf.body[k]] += np.dot(P[0], np.cross(P[1], P[2])) / 6.0
+    vf = np.zeros((surf.x.shape[0], 3))
+    bf = np.zeros((surf.nb, 3))
+    ef = np.zeros((surf.e.shape[0], 3))
+    if len(pos) == 0:
+        return vf, bf, ef
+    for k, el in enumerate(surf.e):
+        P = surf.x[el]
+        sg = 1.0 if orient[surf.body[k]] >= 0.0 else -1.0
+        nA = np.zeros(3)
+        if dim == 2:
+            xc = np.array([0.5 * (P[0, 0] + P[1, 0]), 0.5 * (P[0, 1] + P[1, 1]), 0.0])
+            nA[0] = sg * (P[1, 1] - P[0, 1])
+            nA[1] = -sg * (P[1, 0] - P[0, 0])
+        else:
+            xc = (P[0] + P[1] + P[2]) / 3.0
+            nA = 0.5 * sg * np.cross(P[1] - P[0], P[2] - P[0])
+        d2 = np.zeros(len(pos))
+        for q in range(dim):
+            d2 = d2 + (pos[:, q] - xc[q]) ** 2
+        best = int(np.argmin(d2))                           # first minimum = lowest index
+        s6 = sigma[zz[best], yy[best], xx[best], :6]
+        S = np.array([[s6[0], s6[3], s6[4]], [s6[3], s6[1], s6[5]], [s6[4], s6[5], s6[2]]])
+        F = S @ nA
+        ef[k, :dim] = F[:dim]
+        bf[surf.body[k], :dim] += F[:dim]
+        for m in range(dim):
+            vf[el[m], :dim] += F[:dim] / dim
+    return vf, bf, ef
 
 
 def links(lat, shape, surf: "Surface", periodic=(1, 1, 1), solid=None):

@@ -43,7 +43,7 @@ def _deps_mtime():
 # Per-file flags: the geometry and boundary code keeps IEEE operation-by-operation
 # FP64 arithmetic (no fused multiply-add contraction), so that solid/fluid and
 # cut-link decisions on degenerate geometry are reproducible.
-FILE_FLAGS = {"boundary.cu": ["-fmad=false"]}
+FILE_FLAGS = {"boundary.cu": ["-fmad=false"], "traction.cu": ["-fmad=false"]}
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:

@@ -37,12 +37,6 @@
 namespace kbc {
 
 // ---------------------------------------------------------------- helpers
-__device__ __forceinline__ void decompose(const Grid &g, long long k, int &X, int &Y, int &Z) {
-  X = (int)(k % g.pitch);
-  const long long r = k / g.pitch;
-  Y = (int)(r % g.NY);
-  Z = (int)(r / g.NY);
-}
 
 // Stored coordinate S + c on one axis; -1 if it leaves the interior of a
 // padded (non-periodic) axis.

@@ -76,4 +76,12 @@ struct InstDesc {
   int lcap;
 };
 
+// Stored coordinates of the linear stored index k.
+__device__ __forceinline__ void decompose(const Grid &g, long long k, int &X, int &Y, int &Z) {
+  X = (int)(k % g.pitch);
+  const long long r = k / g.pitch;
+  Y = (int)(r % g.NY);
+  Z = (int)(r / g.NY);
+}
+
 }  // namespace kbc

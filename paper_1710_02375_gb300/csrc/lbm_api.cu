@@ -29,6 +29,7 @@ constexpr int kMaxBodies = 16;
 struct Layout {
   size_t f[2], flags, err, stage;
   size_t sx, sv, se, seb, links, bnodes, fresh, counters, vforce, bforce, inlet[6];
+  size_t sigma, orient, tvforce, tbforce;  // stress-traction output
   int nface, bcap, inlet_n[6];
   size_t total;
 };
@@ -78,6 +79,10 @@ Layout make_layout(const lbm_config &c) {
   L.counters = off; off += kAlign;  // nbn, nl, nfresh, step, nface
   L.vforce = off; off += align_up(sizeof(double) * 3 * (size_t)std::max(nv, 1));
   L.bforce = off; off += align_up(sizeof(double) * 3 * kMaxBodies);
+  L.sigma = off; off += align_up(sizeof(double) * 6 * (size_t)std::max(nl, 1));
+  L.orient = off; off += align_up(sizeof(double) * kMaxBodies);
+  L.tvforce = off; off += align_up(sizeof(double) * 3 * (size_t)std::max(nv, 1));
+  L.tbforce = off; off += align_up(sizeof(double) * 3 * kMaxBodies);
   for (int fc = 0; fc < 6; ++fc) {
     L.inlet_n[fc] = 0;
     L.inlet[fc] = 0;
@@ -150,6 +155,7 @@ struct lbm_ctx {
   fem_ctx *fem = nullptr;    // coupled beam (conventional serial staggered loop)
   int fem_v0 = 0;
   mlp_ctx *mlp = nullptr;    // structural-step surrogate (Newton initial guess)
+  bool traction_on = false;  // stress-traction output each step
   double accept_tol = 0.0;
   // CUDA graph of graph_n steps (replayed by lbm_step_graph)
   cudaGraphExec_t gexec = nullptr;
@@ -376,6 +382,7 @@ lbm_status lbm_get_populations(lbm_ctx *ctx, double *f) {
 }
 
 static lbm_status run_geometry(lbm_ctx *ctx, int track_fresh);
+static SurfaceDev surface_dev(lbm_ctx *ctx);
 
 lbm_status lbm_step(lbm_ctx *ctx, int n) {
   GUARD();
@@ -403,6 +410,13 @@ lbm_status lbm_step(lbm_ctx *ctx, int n) {
     CK(launch_sweep(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur], ctx->f[1 - ctx->cur],
                     ctx->has_solid ? ctx->flags : nullptr, beta, bgk, ctx->err, ctx->stream,
                     ctx->sweep_variant));
+    if (ctx->traction_on && ctx->nbodies > 0)
+      CK(launch_traction(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur],
+                         (const BNode *)(ctx->ws + ctx->lay.bnodes) + ctx->nface, ctx->counters,
+                         ctx->cfg.max_links, ctx->cfg.beta, surface_dev(ctx),
+                         (double *)(ctx->ws + ctx->lay.sigma), (double *)(ctx->ws + ctx->lay.orient),
+                         (double *)(ctx->ws + ctx->lay.tvforce),
+                         (double *)(ctx->ws + ctx->lay.tbforce), ctx->nbodies, ctx->stream));
     ctx->cur = 1 - ctx->cur;
     if (ctx->fem && ctx->mlp) {
       // surrogate: network guess of the increment, accepted by the FEM
@@ -548,6 +562,33 @@ lbm_status lbm_get_interface_force(lbm_ctx *ctx, double *vert_force, double *bod
                        cudaMemcpyDefault, ctx->stream));
   if (body_force)
     CK(cudaMemcpyAsync(body_force, ctx->ws + ctx->lay.bforce, sizeof(double) * 3 * ctx->nbodies,
+                       cudaMemcpyDefault, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_set_traction_output(lbm_ctx *ctx, int enable) {
+  GUARD();
+  ctx->traction_on = enable != 0;
+  ctx->graph_dirty = true;
+  if (ctx->traction_on) {
+    CK(cudaMemsetAsync(ctx->ws + ctx->lay.tvforce, 0, sizeof(double) * 3 * (size_t)std::max(ctx->nv, 1),
+                       ctx->stream));
+    CK(cudaMemsetAsync(ctx->ws + ctx->lay.tbforce, 0, sizeof(double) * 3 * kMaxBodies, ctx->stream));
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_get_traction_force(lbm_ctx *ctx, double *vert_force, double *body_force) {
+  GUARD();
+  if (ctx->nbodies == 0) return fail(ctx, LBM_ESTATE, "lbm_get_traction_force: no geometry set");
+  if (!ctx->traction_on)
+    return fail(ctx, LBM_ESTATE, "lbm_get_traction_force: enable it with lbm_set_traction_output");
+  if (vert_force)
+    CK(cudaMemcpyAsync(vert_force, ctx->ws + ctx->lay.tvforce, sizeof(double) * 3 * ctx->nv,
+                       cudaMemcpyDefault, ctx->stream));
+  if (body_force)
+    CK(cudaMemcpyAsync(body_force, ctx->ws + ctx->lay.tbforce, sizeof(double) * 3 * ctx->nbodies,
                        cudaMemcpyDefault, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return LBM_OK;

@@ -76,6 +76,13 @@ cudaError_t launch_grad(int Q, int storage, const Grid &g, void *f, const uint8_
                         double *bforce, int nbodies, cudaStream_t s);
 cudaError_t launch_step_counter(int *step, cudaStream_t s);
 // Immersed boundary nodes and cut links of the band for the current flags.
+// Fluid stress at the immersed boundary nodes (pre-collision state of the
+// step in f) and the traction forces it gives on every surface element.
+cudaError_t launch_traction(int Q, int storage, const Grid &g, const void *f, const BNode *bn,
+                            const int *nbn, int cap, double beta, const SurfaceDev &sd,
+                            double *sigma, double *orient, double *vforce, double *bforce,
+                            int nbodies, cudaStream_t s);
+
 cudaError_t launch_build_links(int Q, const Grid &g, const Band &bd, const SurfaceDev &sd,
                                const uint8_t *flags, BNode *bnodes, int *nbn, int bcap,
                                Link *links, int *nl, int lcap, int *err, cudaStream_t s);

@@ -72,6 +72,10 @@ def load():
     L.lbm_set_geometry.argtypes = [vp, i32, vp, i32, vp, i32, vp, vp, ctypes.c_double]
     L.lbm_update_surface.argtypes = [vp, vp, vp]
     L.lbm_get_interface_force.argtypes = [vp, vp, vp]
+    L.lbm_get_traction_force.argtypes = [vp, vp, vp]
+    L.lbm_get_traction_force.restype = ctypes.c_int
+    L.lbm_set_traction_output.argtypes = [vp, ctypes.c_int]
+    L.lbm_set_traction_output.restype = ctypes.c_int
     L.lbm_get_boundary_info.argtypes = [vp, vp]
     for name in ("lbm_set_inlet_profile", "lbm_set_geometry", "lbm_update_surface",
                  "lbm_get_interface_force", "lbm_get_boundary_info"):
@@ -202,6 +206,14 @@ def lbm_get_interface_force(ctx, vert_force, body_force):
     _chk(ctx, load().lbm_get_interface_force(ctx, _ptr(vert_force), _ptr(body_force)))
 
 
+def lbm_set_traction_output(ctx, enable):
+    _chk(ctx, load().lbm_set_traction_output(ctx, int(bool(enable))))
+
+
+def lbm_get_traction_force(ctx, vert_force, body_force):
+    _chk(ctx, load().lbm_get_traction_force(ctx, _ptr(vert_force), _ptr(body_force)))
+
+
 def lbm_get_boundary_info(ctx, info):
     _chk(ctx, load().lbm_get_boundary_info(ctx, _ptr(info)))
 
@@ -324,6 +336,16 @@ class Lattice:
         vf = np.zeros((self._nv, 3))
         bf = np.zeros((self._nb, 3))
         lbm_get_interface_force(self.ctx, vf, bf)
+        return vf, bf
+
+    def set_traction_output(self, enable=True):
+        lbm_set_traction_output(self.ctx, enable)
+
+    def traction_force(self):
+        """Stress-path surface forces of the last step: (vertex[nv,3], body[nb,3])."""
+        vf = np.zeros((self._nv, 3))
+        bf = np.zeros((self._nb, 3))
+        lbm_get_traction_force(self.ctx, vf, bf)
         return vf, bf
 
     def boundary_info(self):
@@ -466,10 +488,39 @@ class Batch:
     def set_tuning(self, rows_per_tile, ctas_per_sm):
         _batch_chk(self.b, load().lbm_batch_set_tuning(self.b, int(rows_per_tile), int(ctas_per_sm)))
 
-    def autotune(self, steps=4):
+    def size_bucket(self):
+        """Autotuner cache key: lattice, storage, member count and the total
+        node count rounded to a power of two."""
+        nodes = sum(int(np.prod(L.shape)) for L in self.lattices)
+        L0 = self.lattices[0]
+        return f"Q{L0.Q}-s{int(L0.cfg.storage)}-m{len(self.lattices)}-n2^{int(round(np.log2(max(nodes, 1))))}"
+
+    def autotune(self, steps=4, cache=None):
+        """Pick the sweep's tile height and resident CTAs per SM by timing
+        (lbm_batch_autotune; the timed steps advance the batch).  With a JSON
+        cache path, a size bucket tuned before is applied without timing and a
+        new result is added to the file.  Returns (rows, ctas, us_per_step or
+        None when taken from the cache)."""
+        import json
+        import os
+        key = self.size_bucket()
+        table = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as fh:
+                table = json.load(fh)
+            if key in table:
+                rows, ctas = table[key]["rows_per_tile"], table[key]["ctas_per_sm"]
+                self.set_tuning(rows, ctas)
+                return rows, ctas, None
         r, c, us = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
         _batch_chk(self.b, load().lbm_batch_autotune(self.b, int(steps), ctypes.byref(r), ctypes.byref(c),
                                                       ctypes.byref(us)))
+        if cache:
+            table[key] = {"rows_per_tile": r.value, "ctas_per_sm": c.value, "us_per_step": us.value}
+            tmp = cache + ".tmp"
+            with open(tmp, "w") as fh:
+                json.dump(table, fh, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
         return r.value, c.value, us.value
 
     def close(self):

@@ -52,3 +52,12 @@ def test_batch_graph_replay_and_autotune():
         assert np.array_equal(La.get_populations(), Lb.get_populations())
     rows, ctas, us = Ba.autotune(steps=2)
     assert rows in (1, 2, 4, 8) and 3 <= ctas <= 8 and us > 0
+    # JSON cache per size bucket: tuned once, then applied without timing
+    import json
+    import os
+    import tempfile
+    path = os.path.join(tempfile.mkdtemp(), "tune.json")
+    r1, c1, u1 = Ba.autotune(steps=2, cache=path)
+    assert u1 is not None and Ba.size_bucket() in json.load(open(path))
+    r2, c2, u2 = Bb.autotune(steps=2, cache=path)
+    assert (r2, c2, u2) == (r1, c1, None)

@@ -234,3 +234,57 @@ def test_graph_replay_matches_direct_stepping():
         assert L.boundary_info()[3] == 120  # ramp clock advanced once per step
         L.close()
     assert np.array_equal(out[0], out[1])
+
+
+def test_stress_traction_matches_oracle():
+    """Stress-path traction (lbm_set_traction_output): immersed Couette walls
+    (the exact wall shear rho nu U / H) and the C1 cylinder with a rigid flag
+    after 300 steps, against the oracle's boundary-node stresses and element
+    quadrature; per body <= 1e-3, per vertex <= 1e-3 of the largest."""
+    # Couette
+    nx, ny, U, beta, steps = 5, 16, 0.01, 0.7, 400
+    x, v, e, body = slabs(nx, ny, 2.3, 13.6, U)
+    L = lattice(9, (1, ny, nx), beta, max_links=400, max_vertices=16, max_elements=16)
+    L.set_geometry(x, e, body, vel=v)
+    L.set_traction_output(True)
+    rho0, u0 = np.ones((1, ny, nx)), np.zeros((2, 1, ny, nx))
+    L.init_equilibrium(rho0, u0)
+    L.step(steps)
+    L.check()
+    tv_g, tb_g = L.traction_force()
+    surf = orc.Surface(x, v, e, body)
+    f = orc.init_equilibrium(9, rho0, u0)
+    solid = orc.solid_mask((1, ny, nx), surf)
+    for _ in range(steps):
+        f, _, _, _, sig = orc.step_bc(9, beta, f, bc=(0,) * 6, surf=surf, solid=solid,
+                                      want_sigma=True)
+    tv_o, tb_o, _ = orc.traction(surf, sig)
+    for b in range(2):
+        assert np.linalg.norm(tb_g[b] - tb_o[b]) <= 1e-3 * np.linalg.norm(tb_o[b]), (tb_g, tb_o)
+    assert np.max(np.abs(tv_g - tv_o)) <= 1e-3 * np.max(np.abs(tv_o))
+    # C1 geometry, rigid flag
+    nx, ny, beta, prof, x, e, body = c1_setup(True)
+    bc = (INLET, OUTLET, WALL, WALL, 0, 0)
+    steps = 300
+    L = lattice(9, (1, ny, nx), beta, bc=bc, max_links=4000, max_vertices=200, max_elements=200,
+                inlet_ramp_steps=1000)
+    L.set_inlet_profile(0, prof)
+    L.set_geometry(x, e, body)
+    L.set_traction_output(True)
+    L.init_equilibrium(np.ones((1, ny, nx)), np.zeros((2, 1, ny, nx)))
+    L.step(steps)
+    L.check()
+    tv_g, tb_g = L.traction_force()
+    _, mb_g = L.interface_force()
+    surf = orc.Surface(x, np.zeros_like(x), e, body)
+    solid = orc.solid_mask((1, ny, nx), surf)
+    f = orc.init_equilibrium(9, np.ones((1, ny, nx)), np.zeros((2, 1, ny, nx)))
+    for t in range(steps):
+        s = 0.5 * (1 - np.cos(np.pi * t / 1000))
+        f, _, _, _, sig = orc.step_bc(9, beta, f, bc=bc, inlet={0: prof}, inlet_scale=s, surf=surf,
+                                      solid=solid, want_sigma=True)
+    tv_o, tb_o, _ = orc.traction(surf, sig)
+    for b in range(2):
+        assert np.linalg.norm(tb_g[b] - tb_o[b]) <= 1e-3 * np.linalg.norm(tb_o[b]), (tb_g, tb_o)
+    assert np.max(np.abs(tv_g - tv_o)) <= 1e-3 * np.max(np.abs(tv_o))
+    print("TRACTION vs momentum exchange (C1, 300 steps):", tb_g[:, :2].tolist(), mb_g[:, :2].tolist())

@@ -33,6 +33,36 @@ def test_beam_prescribed_loads_matches_oracle():
     assert np.max(np.abs(u[1::3])) > 0.5  # large deflection regime reached
 
 
+def test_beam_csm3_matches_oracle():
+    """CSM3 (flag under gravity, large deflection, dt = 5 ms, 1200 steps) on
+    the GPU beam against the oracle beam, which the paper's CSM3 table pins."""
+    from paper_1710_02375_gb300.lbm import Beam
+    E, nu_s, rho_s, grav, Lb, h, ne, dt = 1.4e6, 0.4, 1e3, 2.0, 0.35, 0.02, 20, 0.005
+    Ep = E / (1 - nu_s ** 2)
+    X = np.stack([np.linspace(0, Lb, ne + 1), np.zeros(ne + 1)], 1)
+    fixed = np.zeros(3 * (ne + 1), np.int32)
+    fixed[:3] = 1
+    args = (X, Ep * h, Ep * h ** 3 / 12, rho_s * h, fixed)
+    gb = Beam(*args, thickness=h, dt=dt, atol=1e-14)
+    ob = orc.Beam(*args)
+    F = np.zeros(3 * (ne + 1))
+    F[1::3] = -rho_s * grav * h * Lb / ne
+    F[1] *= 0.5
+    F[-2] *= 0.5
+    u, v = np.zeros(3 * (ne + 1)), np.zeros(3 * (ne + 1))
+    gb.step(F)  # the first step's previous load F0 is zero on the GPU beam
+    u, v, _ = ob.step(u, v, np.zeros_like(F), F, dt=dt, atol=1e-14)
+    worst = 0.0
+    for _ in range(1199):
+        gb.step(F)
+        u, v, it = ob.step(u, v, F, F, dt=dt, atol=1e-14)
+        ug, _, itg = gb.state()
+        assert it >= 0 and itg >= 0
+        worst = max(worst, np.max(np.abs(ug - u)) / np.max(np.abs(u)))
+    assert worst < 1e-8, worst
+    assert np.min(u[1::3]) < -0.1  # past the first downswing
+
+
 def test_coupled_flag_c1_matches_oracle():
     """C1 (Turek-type cylinder + elastic flag, Re = 100, rho_s/rho_f = 10,
     Ae = 1.4e3): 400 coupled steps of fluid + Grad + force + beam + geometry."""

@@ -146,3 +146,52 @@ def test_sphere_links_and_mask_3d():
         disc = b * b - 4 * a * cc
         s = (-b - np.sqrt(max(disc, 0))) / (2 * a)
         assert abs(L["q"][k] - s) * np.sqrt(a) < 2 * tol
+
+
+@pytest.mark.parametrize("y_lo,y_hi", [(2.25, 13.75), (2.75, 13.3)])
+def test_stress_traction_couette_wall_shear(y_lo, y_hi):
+    """The stress path (sigma_f = -p I - (1 - beta) Pi^(1) at the boundary
+    nodes, t = sigma n on the wall elements): steady Couette gives the wall
+    shear stress rho nu U / H exactly on both walls (the fluid drags the
+    resting wall forward and the moving wall back) and no normal traction."""
+    nx, ny, U = 3, 16, 0.01
+    nu = 1.0 / 6.0
+    beta = 1.0 / (6 * nu + 1)
+    surf = slab_surface(nx, y_lo, y_hi, ny, U)
+    f = orc.init_equilibrium(9, np.ones((1, ny, nx)), np.zeros((2, 1, ny, nx)))
+    for _ in range(3000):
+        f, _, _, _, sig = orc.step_bc(9, beta, f, bc=(0,) * 6, surf=surf, want_sigma=True)
+    _, _, ef = orc.traction(surf, sig)
+    tau = nu * U / (y_hi - y_lo)
+    seen = 0
+    for k, el in enumerate(surf.e):
+        P = surf.x[el]
+        if abs(P[0, 1] - P[1, 1]) > 0 or not (0 < P[0, 1] < ny):
+            continue
+        L = abs(P[1, 0] - P[0, 0])
+        want = tau if P[0, 1] == y_lo else -tau
+        assert abs(ef[k, 0] / L - want) <= 1e-9 * tau, (ef[k], want)
+        assert abs(ef[k, 1] / L) <= 1e-9 * tau
+        seen += 1
+    assert seen == 2
+
+
+def test_stress_traction_uniform_pressure():
+    """A resting body in a uniform fluid at rho0 = 1.01: every element carries
+    exactly -(rho0 - 1) c_s^2 times its outward area vector, so the closed
+    body's total vanishes while each element feels the gauge pressure."""
+    ny = nx = 16
+    rho0 = 1.01
+    xs, es = synth.circle_polygon(8.0, 8.0, 3.3, 24)
+    surf = orc.Surface(xs, np.zeros_like(xs), es, np.zeros(len(es), np.int32))
+    f = orc.init_equilibrium(9, np.full((1, ny, nx), rho0), np.zeros((2, 1, ny, nx)))
+    for _ in range(3):
+        f, _, _, _, sig = orc.step_bc(9, 0.9, f, bc=(0,) * 6, surf=surf, want_sigma=True)
+    vf, bf, ef = orc.traction(surf, sig)
+    area = 0.5 * sum(xs[a, 0] * xs[b, 1] - xs[b, 0] * xs[a, 1] for a, b in es)
+    sg = 1.0 if area > 0 else -1.0
+    p = (rho0 - 1.0) / 3.0
+    for k, (a, b) in enumerate(es):
+        nA = sg * np.array([xs[b, 1] - xs[a, 1], -(xs[b, 0] - xs[a, 0])])
+        np.testing.assert_allclose(ef[k, :2], -p * nA, rtol=0, atol=1e-12)
+    assert np.max(np.abs(bf)) <= 1e-12
