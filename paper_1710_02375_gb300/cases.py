@@ -51,3 +51,22 @@ def c1_coupled(Re, seed=0, stream=None):
     beam = Beam(X, EA, EI, rhoA, fixed, thickness=c["h"], stream=L.stream)
     lbm.fsi_couple(L.ctx, beam.ctx, ncyl)
     return L, beam, ncyl
+
+
+def flag_coupled(inst, stream=None, ramp=1000):
+    """A synth.flag_channel case (e.g. synth.c5_case) CSS-coupled: walls top
+    and bottom, parabolic inlet on -x with the inflow ramp, outlet on +x.
+    Returns (Lattice, Beam)."""
+    from . import lbm
+    from .lbm import Beam, Lattice
+    nx, ny = inst["nx"], inst["ny"]
+    L = Lattice(9, nx, ny, 1, inst["beta"], bc=(2, 3, 1, 1, 0, 0), max_links=16000,
+                max_vertices=len(inst["x"]), max_elements=len(inst["e"]), inlet_ramp_steps=ramp,
+                stream=stream)
+    L.set_inlet_profile(0, inst["inlet"])
+    L.set_geometry(inst["x"], inst["e"], inst["body"], band_margin=0.5 * inst["D"])
+    L.init_equilibrium(np.ones((1, ny, nx)), np.zeros((2, 1, ny, nx)))
+    X, EA, EI, rhoA, fixed = inst["beam"]
+    beam = Beam(X, EA, EI, rhoA, fixed, thickness=inst["h"], stream=L.stream)
+    lbm.fsi_couple(L.ctx, beam.ctx, inst["ncyl"])
+    return L, beam

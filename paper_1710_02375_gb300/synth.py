@@ -179,6 +179,34 @@ def c1_flag_beam(cx=20.0, cy=20.0, d=10.0, flag_len=35.0, flag_h=2.0, n_beam=20,
 
 
 
+def flag_channel(s, Re, Ae=1.4e3, seed=0, n_cyl=48, n_beam=20, u_max=0.05):
+    """One flag-in-channel case at scale s: nx = round(200 s), ny = round(40 s),
+    cylinder of diameter D = ny / 4.1 at (2D, 2D), flag of length 3.5 D and
+    thickness 0.2 D (n_beam beam elements), parabolic inflow u_max with 1e-4
+    static noise (seed), Re on the mean inflow speed 2/3 u_max and D,
+    aeroelastic number Ae, density ratio 10.  Returns a dict with the lattice
+    size, beta, inflow profile, surface mesh (cylinder then flag) and beam
+    data."""
+    nx, ny = int(round(200 * s)), int(round(40 * s))
+    D = ny / 4.1
+    U = 2.0 / 3.0 * u_max
+    nu = U * D / Re
+    beta = 1.0 / (6 * nu + 1)
+    prof = parabolic_profile(ny, u_max, noise=1e-4, seed=seed)
+    x, e, body, _ = cylinder_flag_2d(cx=2 * D, cy=2 * D, d=D, flag_len=3.5 * D, flag_h=0.2 * D,
+                                     n_cyl=n_cyl, n_beam=n_beam)
+    X, EA, EI, rhoA, fixed = c1_flag_beam(cx=2 * D, cy=2 * D, d=D, flag_len=3.5 * D,
+                                          flag_h=0.2 * D, n_beam=n_beam, u_max=u_max, Ae=Ae)
+    return dict(nx=nx, ny=ny, beta=beta, Re=Re, Ae=Ae, D=D, inlet=prof, x=x, e=e, body=body,
+                ncyl=n_cyl, beam=(X, EA, EI, rhoA, fixed), h=0.2 * D)
+
+
+def c5_case(Re, seed=0):
+    """The surrogate workload: the flag channel at scale 4 (800 x 160,
+    D = 39.0), a 31-element flag (32 beam nodes, 64 surface vertices)."""
+    return flag_channel(4.0, Re, seed=seed, n_beam=31)
+
+
 def c4_instances(n=64, seed=0, n_cyl=48, n_beam=20, u_max=0.05, Ae0=1.4e3):
     """The batched ensemble: n flag-in-channel instances.  Instance k draws
     (seed + k) a scale s ~ U[1, 4] (nx = round(200 s), ny = round(40 s), so
@@ -192,18 +220,8 @@ def c4_instances(n=64, seed=0, n_cyl=48, n_beam=20, u_max=0.05, Ae0=1.4e3):
     for k in range(n):
         rng = np.random.default_rng(seed + k)
         s = rng.uniform(1.0, 4.0)
-        nx, ny = int(round(200 * s)), int(round(40 * s))
-        D = ny / 4.1
         Re = rng.uniform(50.0, 200.0)
         Ae = Ae0 * 10 ** rng.uniform(-0.5, 0.5)
-        U = 2.0 / 3.0 * u_max
-        nu = U * D / Re
-        beta = 1.0 / (6 * nu + 1)
-        prof = parabolic_profile(ny, u_max, noise=1e-4, seed=seed + k)
-        x, e, body, _ = cylinder_flag_2d(cx=2 * D, cy=2 * D, d=D, flag_len=3.5 * D, flag_h=0.2 * D,
-                                         n_cyl=n_cyl, n_beam=n_beam)
-        X, EA, EI, rhoA, fixed = c1_flag_beam(cx=2 * D, cy=2 * D, d=D, flag_len=3.5 * D,
-                                              flag_h=0.2 * D, n_beam=n_beam, u_max=u_max, Ae=Ae)
-        out.append(dict(nx=nx, ny=ny, beta=beta, Re=Re, Ae=Ae, D=D, inlet=prof, x=x, e=e, body=body,
-                        ncyl=n_cyl, beam=(X, EA, EI, rhoA, fixed), h=0.2 * D))
+        out.append(flag_channel(s, Re, Ae=Ae, seed=seed + k, n_cyl=n_cyl, n_beam=n_beam,
+                                u_max=u_max))
     return out

@@ -39,6 +39,26 @@ def oracle_pairs(args):
     return X, Y
 
 
+def oracle_run_inst(inst, ramp=RAMP):
+    """Coupled oracle run of a synth.flag_channel case (walls top and bottom,
+    inlet -x, outlet +x)."""
+    from oracle import fsi_oracle
+    from oracle import oracle as orc
+    X, EA, EI, rhoA, fixed = inst["beam"]
+    ob = orc.Beam(X, EA, EI, rhoA, fixed)
+    nc = inst["ncyl"]
+    return fsi_oracle.CSSFlag(9, (1, inst["ny"], inst["nx"]), inst["beta"], BC, None, {0: inst["inlet"]},
+                              ramp, inst["x"][:nc], inst["e"], inst["body"], ob, inst["h"])
+
+
+def c5_pairs(args):
+    """(X, Y) surrogate pairs of `steps` steps of the oracle C5 flag run at (Re, seed)."""
+    from oracle import surrogate_data
+    Re, seed, steps = args
+    X, Y, _ = surrogate_data.pairs_from_run(oracle_run_inst(synth.c5_case(Re, seed)), steps)
+    return X, Y
+
+
 def gpu_run(Re, seed=0):
     """(Lattice, Beam) of the CUDA library, coupled, at step 0."""
     from paper_1710_02375_gb300.cases import c1_coupled

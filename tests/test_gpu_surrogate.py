@@ -30,11 +30,11 @@ def pairs():
     return X, Y
 
 
-def run(steps, mlp=None, stats=None, chunk=50):
+def run(steps, mlp=None, stats=None, chunk=50, make=None):
     import torch
     from paper_1710_02375_gb300 import lbm as abi
     from paper_1710_02375_gb300 import surrogate
-    L, gb = c1.gpu_run(RE_TEST)
+    L, gb = make() if make else c1.gpu_run(RE_TEST)
     if mlp is not None:
         surrogate.attach(L, mlp, stats, accept_tol=1e-3)
     tips = []
@@ -86,4 +86,43 @@ def test_surrogate_gain_over_newton(pairs):
     assert c_s[2] < c_z[2], summary
     assert c_s[0] > 0, summary
     # accepted guesses leave the flag's motion close to the Newton run's
+    assert dev <= 5e-2, summary
+
+
+@pytest.mark.slow
+def test_surrogate_c5_scale():
+    """The surrogate workload's size: 800 x 160 channel, D = 39, a 32-node
+    flag (465 network inputs, 93 outputs).  Training pairs: 1500 steps of
+    coupled oracle runs at Re = 100, 150, 250 and 300 (6000 pairs, the
+    start-up through the 1000-step inflow ramp); deployment: a coupled GPU run
+    at Re = 200 over the same 1500 steps.  Checks the gain in Newton solves
+    and the flag motion against the Newton-only run, and reports time per
+    step."""
+    from paper_1710_02375_gb300 import surrogate, synth
+    from paper_1710_02375_gb300.cases import flag_coupled
+    from paper_1710_02375_gb300.lbm import Mlp
+    from oracle import mlp_oracle as mo
+    steps, res = 1500, (100.0, 150.0, 250.0, 300.0)
+    with mp.get_context("spawn").Pool(len(res)) as pool:
+        out = pool.map(c1.c5_pairs, [(re, k + 1, steps) for k, re in enumerate(res)])
+    X = np.concatenate([o[0] for o in out])
+    Y = np.concatenate([o[1] for o in out])
+    nn = 32
+    assert X.shape[1] == surrogate.input_width(nn) and Y.shape[1] == 3 * nn - 3
+    stats = surrogate.normalisation(X, Y)
+    dims = [X.shape[1], 128, 128, 128, Y.shape[1]]
+    net = Mlp(dims, max_batch=256)
+    net.set_params(mo.init_params(dims, 0))
+    hist = surrogate.train(net, X, Y, stats, steps=8000, lr=1e-3, log_every=500)
+    make = lambda: flag_coupled(synth.c5_case(RE_TEST))  # noqa: E731
+    tip_n, c_n, ms_n = run(steps, make=make)
+    tip_s, c_s, ms_s = run(steps, net, stats, make=make)
+    amp = np.max(np.abs(tip_n[:, :2]))
+    dev = np.max(np.abs(tip_s[:, :2] - tip_n[:, :2])) / amp
+    summary = dict(steps=steps, pairs=int(X.shape[0]), newton=dict(counts=c_n, ms_per_step=ms_n),
+                   network=dict(counts=c_s, ms_per_step=ms_s, tip_dev=dev),
+                   train_loss=[hist[0][1], hist[-1][1]], tip_amplitude=amp)
+    print("SURROGATE_C5", json.dumps(summary))
+    assert c_n[3] == steps and c_s[0] + c_s[1] == steps
+    assert c_s[2] <= 0.85 * c_n[2], summary
     assert dev <= 5e-2, summary
