@@ -18,7 +18,7 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SOURCES = ["kbc_oracle.c", "kbc_oracle_bc.c", "fem_oracle.c"]
+_SOURCES = ["kbc_oracle.c", "kbc_oracle_bc.c", "fem_oracle.c", "shell_oracle.c"]
 _LIB_PATH = os.path.join(_HERE, "libkbc_oracle.so")
 _lib = None
 
@@ -68,6 +68,12 @@ def _declare(L):
     L.or_beam_static.argtypes = [c_int, D, c_double, c_double, I32, D, c_double, c_double, c_double,
                                  c_int, D]
     L.or_beam_internal.argtypes = [c_int, D, c_double, c_double, D, D, D]
+    L.or_shell_internal.argtypes = [c_int, c_int, D, c_double, c_double, c_double, c_double, I32, D, D, D]
+    L.or_shell_mass.argtypes = [c_int, c_int, D, c_double, c_double, c_double, c_double, D, D]
+    L.or_shell_step.argtypes = [c_int, c_int, D, c_double, c_double, c_double, c_double, I32, c_double,
+                                c_double, c_double, c_double, c_double, c_int, D, D, D, D, D]
+    L.or_shell_static.argtypes = [c_int, c_int, D, c_double, c_double, c_double, I32, D, c_double,
+                                  c_double, c_double, c_int, D, D]
     L.or_beam_mass.argtypes = [c_int, D, c_double, D]
     L.or_fresh_init.argtypes = [c_int, c_int, c_int, c_int, I32, U8, U8, c_int, D, D, D]
     L.or_links.argtypes = [c_int, c_int, c_int, c_int, I32, U8, c_int, c_int, c_int, D, D, I32, I32,
@@ -367,3 +373,63 @@ class Beam:
         it = lib().or_beam_static(self.nn, _p(self.X), self.EA, self.EI, self.fixed.ctypes.data_as(I32),
                                   _p(F), lam, rtol, atol, max_it, _p(u))
         return u, it
+
+
+class Shell:
+    """3-D co-rotational flat shell of 4-node quadrilaterals on an nx x ny node
+    grid (FP64 oracle): reference nodes X[nx*ny, 3] (node i*ny + j), Young's
+    modulus E, Poisson ratio nu, thickness h, density rho, fixed[6 nn] mask
+    (ux, uy, uz, three rotations per node).  State: u[nn,3] translations,
+    R[nn,3,3] nodal rotation matrices, v[nn,6] translational and angular
+    velocities."""
+
+    def __init__(self, X, nx, ny, E, nu, h, rho, fixed):
+        self.X = np.ascontiguousarray(X, dtype=np.float64)
+        self.nx, self.ny = int(nx), int(ny)
+        self.nn = self.nx * self.ny
+        assert self.X.shape == (self.nn, 3)
+        self.E, self.nu, self.h, self.rho = float(E), float(nu), float(h), float(rho)
+        self.fixed = np.ascontiguousarray(fixed, dtype=np.int32)
+
+    def rest(self):
+        u = np.zeros((self.nn, 3))
+        R = np.tile(np.eye(3), (self.nn, 1, 1))
+        v = np.zeros((self.nn, 6))
+        return u, R, v
+
+    def internal(self, u, R):
+        f = np.zeros((self.nn, 6))
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        R = np.ascontiguousarray(R, dtype=np.float64)
+        _check(lib().or_shell_internal(self.nx, self.ny, _p(self.X), self.E, self.nu, self.h, self.rho,
+                                       self.fixed.ctypes.data_as(I32), _p(u), _p(R), _p(f)))
+        return f
+
+    def mass(self):
+        m = np.zeros(self.nn)
+        J = np.zeros(self.nn)
+        _check(lib().or_shell_mass(self.nx, self.ny, _p(self.X), self.E, self.nu, self.h, self.rho,
+                                   _p(m), _p(J)))
+        return m, J
+
+    def step(self, u, R, v, F0, F1, dt=1.0, theta=0.5, lam=0.7, rtol=1e-10, atol=1e-13, max_it=200):
+        """One theta-scheme step; returns (u1, R1, v1, iterations)."""
+        u = np.array(u, dtype=np.float64)
+        R = np.array(R, dtype=np.float64)
+        v = np.array(v, dtype=np.float64)
+        F0 = np.ascontiguousarray(F0, dtype=np.float64)
+        F1 = np.ascontiguousarray(F1, dtype=np.float64)
+        it = lib().or_shell_step(self.nx, self.ny, _p(self.X), self.E, self.nu, self.h, self.rho,
+                                 self.fixed.ctypes.data_as(I32), dt, theta, lam, rtol, atol, max_it,
+                                 _p(F0), _p(F1), _p(u), _p(R), _p(v))
+        return u, R, v, it
+
+    def static(self, F, lam=1.0, rtol=1e-12, atol=1e-14, max_it=200, u=None, R=None):
+        u0, R0, _ = self.rest()
+        u = u0 if u is None else np.array(u, dtype=np.float64)
+        R = R0 if R is None else np.array(R, dtype=np.float64)
+        F = np.ascontiguousarray(F, dtype=np.float64)
+        it = lib().or_shell_static(self.nx, self.ny, _p(self.X), self.E, self.nu, self.h,
+                                   self.fixed.ctypes.data_as(I32), _p(F), lam, rtol, atol, max_it,
+                                   _p(u), _p(R))
+        return u, R, it

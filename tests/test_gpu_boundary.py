@@ -240,7 +240,8 @@ def test_stress_traction_matches_oracle():
     """Stress-path traction (lbm_set_traction_output): immersed Couette walls
     (the exact wall shear rho nu U / H) and the C1 cylinder with a rigid flag
     after 300 steps, against the oracle's boundary-node stresses and element
-    quadrature; per body <= 1e-3, per vertex <= 1e-3 of the largest."""
+    quadrature; per vertex <= 1e-3 of the largest vertex force, per body
+    <= 1e-3 of the body force (C1) or of the vertex scale (Couette)."""
     # Couette
     nx, ny, U, beta, steps = 5, 16, 0.01, 0.7, 400
     x, v, e, body = slabs(nx, ny, 2.3, 13.6, U)
@@ -259,9 +260,11 @@ def test_stress_traction_matches_oracle():
         f, _, _, _, sig = orc.step_bc(9, beta, f, bc=(0,) * 6, surf=surf, solid=solid,
                                       want_sigma=True)
     tv_o, tb_o, _ = orc.traction(surf, sig)
-    for b in range(2):
-        assert np.linalg.norm(tb_g[b] - tb_o[b]) <= 1e-3 * np.linalg.norm(tb_o[b]), (tb_g, tb_o)
-    assert np.max(np.abs(tv_g - tv_o)) <= 1e-3 * np.max(np.abs(tv_o))
+    # the slabs' totals cancel (their far faces lie outside the periodic box
+    # and see the same stress), so they are compared on the vertex-force scale
+    scale = np.max(np.abs(tv_o))
+    assert scale > 0 and np.max(np.abs(tb_g - tb_o)) <= 1e-3 * scale, (tb_g, tb_o)
+    assert np.max(np.abs(tv_g - tv_o)) <= 1e-3 * scale
     # C1 geometry, rigid flag
     nx, ny, beta, prof, x, e, body = c1_setup(True)
     bc = (INLET, OUTLET, WALL, WALL, 0, 0)
