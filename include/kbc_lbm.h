@@ -233,6 +233,49 @@ lbm_status fem_beam_set_state(fem_ctx *f, const double *u, const double *v, cons
 const char *fem_last_error(const fem_ctx *f);
 void fem_destroy(fem_ctx *f);
 
+/* ---------------------------------------------------------------------------
+ * 3-D structure: co-rotational flat shell for the plate (replaces the paper's
+ * Q2 continuum elements of section "Structural modeling"), FP64 on the GPU.
+ * Structured nx x ny node grid, node i*ny + j at X[node][3]; element (i, j)
+ * joins nodes (i,j), (i+1,j), (i+1,j+1), (i,j+1).  Six DOFs per node:
+ * translations (ux, uy, uz) and a rotation, reported as a 3x3 rotation
+ * matrix (row-major) and, for velocities and loads, as angular components.
+ * Local element: plane-stress membrane and Mindlin bending (2x2 Gauss), MITC4
+ * transverse shear, drilling stiffness 1e-3 D; co-rotational frame and
+ * projector; lumped mass.  Theta-scheme (Eq. timeInt), Newton with the
+ * constant relaxation lambda (stop at |R| <= rtol |R0| + atol, R0 the
+ * residual at the step's start), linearised systems by Jacobi-preconditioned
+ * conjugate gradients to cg_rtol (0: 1e-13) within max_cg iterations (0:
+ * 4 x DOFs); one cooperative launch per step.
+ * ------------------------------------------------------------------------- */
+typedef struct fem_shell_ctx fem_shell_ctx;
+typedef struct {
+  int nx, ny;             /* nodes along the length and the width, nx*ny <= 4096 */
+  const double *X;        /* [nx*ny][3] reference positions (host or device) */
+  double E, nu, h, rho;   /* Young's modulus, Poisson ratio, thickness, density */
+  const int32_t *fixed;   /* [6 nn] 1: DOF held at its reference value */
+  double theta, lambda, rtol, atol;
+  int max_it;
+  double dt;
+  int max_cg;
+  double cg_rtol;
+  void *stream;           /* cudaStream_t; NULL: library-owned */
+} fem_shell_config;
+lbm_status fem_shell_workspace_size(const fem_shell_config *c, size_t *bytes);
+lbm_status fem_shell_create(const fem_shell_config *c, void *workspace, size_t bytes,
+                            fem_shell_ctx **out);
+/* One structural step with loads F1[nn][6] (forces, then moments; global
+ * axes); the previous step's loads are kept (zero before the first step). */
+lbm_status fem_shell_step(fem_shell_ctx *s, const double *F1);
+/* u[nn][3], R[nn][9], v[nn][6] (translational, angular) and iters[2]
+ * (Newton iterations of the last step, negative when max_it was reached;
+ * conjugate-gradient iterations of that step); NULL skips.  Synchronises. */
+lbm_status fem_shell_get_state(fem_shell_ctx *s, double *u, double *R, double *v, int *iters);
+lbm_status fem_shell_set_state(fem_shell_ctx *s, const double *u, const double *R,
+                               const double *v, const double *F0);
+const char *fem_shell_last_error(const fem_shell_ctx *s);
+void fem_shell_destroy(fem_shell_ctx *s);
+
 /* Couple a beam to the lattice (conventional serial staggered scheme,
  * section "Fluid-structure coupling"): the beam's flag surface occupies
  * surface vertices [first_vertex, first_vertex + 2 nn) of the geometry given

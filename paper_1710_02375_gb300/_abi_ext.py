@@ -19,6 +19,23 @@ class fem_beam_config(ctypes.Structure):
     ]
 
 
+class fem_shell_config(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("X", ctypes.c_void_p),
+        ("E", ctypes.c_double), ("nu", ctypes.c_double), ("h", ctypes.c_double),
+        ("rho", ctypes.c_double),
+        ("fixed", ctypes.c_void_p),
+        ("theta", ctypes.c_double), ("lambda_", ctypes.c_double),
+        ("rtol", ctypes.c_double), ("atol", ctypes.c_double),
+        ("max_it", ctypes.c_int),
+        ("dt", ctypes.c_double),
+        ("max_cg", ctypes.c_int),
+        ("cg_rtol", ctypes.c_double),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
 class mlp_config(ctypes.Structure):
     _fields_ = [
         ("n_layers", ctypes.c_int),
@@ -42,6 +59,18 @@ def declare(L):
     L.fem_destroy.argtypes = [vp]
     L.fem_destroy.restype = None
     L.fsi_couple.argtypes = [vp, vp, i32]
+    L.fem_shell_workspace_size.argtypes = [ctypes.POINTER(fem_shell_config), ctypes.POINTER(sz)]
+    L.fem_shell_create.argtypes = [ctypes.POINTER(fem_shell_config), vp, sz, ctypes.POINTER(vp)]
+    L.fem_shell_step.argtypes = [vp, vp]
+    L.fem_shell_get_state.argtypes = [vp, vp, vp, vp, vp]
+    L.fem_shell_set_state.argtypes = [vp, vp, vp, vp, vp]
+    L.fem_shell_last_error.argtypes = [vp]
+    L.fem_shell_last_error.restype = ctypes.c_char_p
+    L.fem_shell_destroy.argtypes = [vp]
+    L.fem_shell_destroy.restype = None
+    for name in ("fem_shell_workspace_size", "fem_shell_create", "fem_shell_step",
+                 "fem_shell_get_state", "fem_shell_set_state"):
+        getattr(L, name).restype = ctypes.c_int
     L.lbm_batch_workspace_size.argtypes = [vp, i32, ctypes.POINTER(sz)]
     L.lbm_batch_create.argtypes = [vp, i32, vp, sz, ctypes.POINTER(vp)]
     L.lbm_batch_step.argtypes = [vp, i32]

@@ -1,0 +1,845 @@
+// fem_shell.cu -- GPU co-rotational flat shell for the 3-D plate (FP64).
+//
+// Structural model (replacing the paper's Q2 continuum elements of section
+// "Structural modeling" for the plate cases): 4-node quadrilaterals on a
+// structured nx x ny node grid (node i*ny + j, element (i, j) with nodes
+// (i,j), (i+1,j), (i+1,j+1), (i,j+1)), six DOFs per node (translations and a
+// rotation, carried as a rotation matrix).  Local element: linear and
+// constant -- plane-stress membrane and Mindlin plate bending at 2x2 Gauss
+// points, MITC4 transverse shear (covariant strains tied at the edge
+// midpoints, shear factor 5/6), drilling stiffness 1e-3 D on the rotation
+// about the element normal.  Co-rotation: element frame from the diagonals
+// (normal) and the mean of the two x-running sides (e1); local deformations
+// d = (R_e^T (x - c) - x_ref, log(R_e^T R_node R_e0)); internal force
+// T^T P^T K_l d with P the projector that removes the frame's rigid motion
+// (written as I - U V, rank 6); tangent T^T P^T K_l P T.  Lumped mass.
+//
+// Time step: theta-scheme in the two-field form (Eq. timeInt), Newton with
+// the paper's constant relaxation lambda on the step increments (rotation
+// vectors for the rotations); every linearised system is solved by
+// Jacobi-preconditioned conjugate gradients on the element tangents (no
+// assembled matrix).  One cooperative launch runs the whole step: one CTA per
+// element (grid-stride), grid-wide barriers between the phases, reductions
+// by FP64 atomics into three rotating slots.
+#include <cooperative_groups.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/kbc_lbm.h"
+#include "lbm_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace kbc {
+
+constexpr int kShellThreads = 64;
+constexpr int kShellMaxNodes = 4096;
+
+struct ShellParams {
+  int nx, ny, nn, ne, n;
+  double E, nu, h, rho;
+  double theta, lambda, rtol, atol, dt;
+  int max_it, max_cg;
+  double cg_rtol;
+};
+
+struct ShellDev {
+  const double *X;           // [nn][3]
+  const int32_t *fixed;      // [6 nn]
+  double *Kl;                // [ne][576] local stiffness
+  double *Re0;               // [ne][9] reference frames (row-major, columns e1 e2 e3)
+  double *xb0;               // [ne][12] reference local node positions
+  double *mt, *mr;           // [nn] lumped translational / rotational mass
+  double *u, *R, *v, *F0;    // state: [nn][3], [nn][9], [6 nn], previous loads [6 nn]
+  double *u0, *R0, *v0;      // state at the start of the step
+  double *u1, *R1;           // current Newton iterate
+  double *dq;                // [6 nn] step increments (translations, rotation vectors)
+  double *f0, *f, *kd;       // internal force at start / current, diagonal of K
+  double *Ke;                // [ne][576] element tangents, global frame
+  double *rhs, *x, *r, *z, *p, *Ap;
+  double *red;               // [3][2] reduction slots
+  const double *F1;          // [6 nn] loads of the step
+  int *iters;                // [2]: Newton iterations of the last step, CG iterations
+};
+
+__device__ __forceinline__ void elem_ids(const ShellParams &P, int e, int id[4]) {
+  const int i = e / (P.ny - 1), j = e % (P.ny - 1);
+  id[0] = i * P.ny + j;
+  id[1] = (i + 1) * P.ny + j;
+  id[2] = (i + 1) * P.ny + j + 1;
+  id[3] = i * P.ny + j + 1;
+}
+
+// Frame (row-major, columns e1 e2 e3) and centre of four points xs[4][3].
+__device__ void quad_frame_dev(const double *xs, double *Re, double *c) {
+  double d13[3], d24[3], a[3];
+  for (int k = 0; k < 3; ++k) {
+    c[k] = 0.25 * (xs[k] + xs[3 + k] + xs[6 + k] + xs[9 + k]);
+    d13[k] = xs[6 + k] - xs[k];
+    d24[k] = xs[9 + k] - xs[3 + k];
+    a[k] = xs[3 + k] + xs[6 + k] - xs[k] - xs[9 + k];
+  }
+  double e3[3] = {d13[1] * d24[2] - d13[2] * d24[1], d13[2] * d24[0] - d13[0] * d24[2],
+                  d13[0] * d24[1] - d13[1] * d24[0]};
+  const double in3 = 1.0 / sqrt(e3[0] * e3[0] + e3[1] * e3[1] + e3[2] * e3[2]);
+  for (int k = 0; k < 3; ++k) e3[k] *= in3;
+  const double ad = a[0] * e3[0] + a[1] * e3[1] + a[2] * e3[2];
+  double e1[3] = {a[0] - ad * e3[0], a[1] - ad * e3[1], a[2] - ad * e3[2]};
+  const double in1 = 1.0 / sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+  for (int k = 0; k < 3; ++k) e1[k] *= in1;
+  const double e2[3] = {e3[1] * e1[2] - e3[2] * e1[1], e3[2] * e1[0] - e3[0] * e1[2],
+                        e3[0] * e1[1] - e3[1] * e1[0]};
+  for (int k = 0; k < 3; ++k) {
+    Re[3 * k] = e1[k];
+    Re[3 * k + 1] = e2[k];
+    Re[3 * k + 2] = e3[k];
+  }
+}
+
+// exp of the skew matrix of phi (Rodrigues), row-major.
+__device__ void rodrigues(const double *phi, double *Rm) {
+  const double t2 = phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2];
+  const double t = sqrt(t2);
+  double s1, s2;
+  if (t < 1e-6) {
+    s1 = 1.0 - t2 / 6.0;
+    s2 = 0.5 - t2 / 24.0;
+  } else {
+    s1 = sin(t) / t;
+    s2 = (1.0 - cos(t)) / t2;
+  }
+  const double x = phi[0], y = phi[1], z = phi[2];
+  // I + s1 S + s2 S^2 with S^2 = phi phi^T - t2 I
+  Rm[0] = 1.0 + s2 * (x * x - t2); Rm[1] = -s1 * z + s2 * x * y;      Rm[2] = s1 * y + s2 * x * z;
+  Rm[3] = s1 * z + s2 * x * y;      Rm[4] = 1.0 + s2 * (y * y - t2); Rm[5] = -s1 * x + s2 * y * z;
+  Rm[6] = -s1 * y + s2 * x * z;     Rm[7] = s1 * x + s2 * y * z;      Rm[8] = 1.0 + s2 * (z * z - t2);
+}
+
+// Rotation vector of Rm (angle below pi).
+__device__ void rotvec(const double *Rm, double *phi) {
+  double ct = 0.5 * (Rm[0] + Rm[4] + Rm[8] - 1.0);
+  ct = fmin(1.0, fmax(-1.0, ct));
+  const double t = acos(ct);
+  const double g = (t < 1e-6) ? 0.5 + t * t / 12.0 : 0.5 * t / sin(t);
+  phi[0] = g * (Rm[7] - Rm[5]);
+  phi[1] = g * (Rm[2] - Rm[6]);
+  phi[2] = g * (Rm[3] - Rm[1]);
+}
+
+// ---------------------------------------------------------------- set-up
+// Reference frame, local positions, local stiffness and lumped masses of
+// element blockIdx.x (one CTA per element).
+__global__ void __launch_bounds__(kShellThreads) k_shell_setup(ShellParams P, ShellDev D) {
+  const int e = blockIdx.x, t = threadIdx.x;
+  __shared__ double xs[12], Re[9], c[3], xl[4][2];
+  __shared__ double Bm[4][3][24], Bb[4][3][24], Bs[4][2][24], dj[4];
+  __shared__ double tie[4][24];  // covariant shear rows at A(0,-1), C(0,1), D(-1,0), B(1,0)
+  int id[4];
+  elem_ids(P, e, id);
+  if (t < 12) xs[t] = D.X[3 * id[t / 3] + t % 3];
+  __syncthreads();
+  if (t == 0) quad_frame_dev(xs, Re, c);
+  __syncthreads();
+  if (t < 12) {
+    const int a = t / 3, k = t % 3;
+    double s = 0.0;
+    for (int q = 0; q < 3; ++q) s += Re[3 * q + k] * (xs[3 * a + q] - c[q]);
+    D.xb0[12 * e + t] = s;
+    if (k < 2) xl[a][k] = s;
+  }
+  if (t < 9) D.Re0[9 * e + t] = Re[t];
+  __syncthreads();
+  const double sgn_xi[4] = {-1, 1, 1, -1}, sgn_eta[4] = {-1, -1, 1, 1};
+  // tying rows (threads 0..3) and Gauss-point rows (threads 4..7)
+  if (t < 8) {
+    const bool tying = t < 4;
+    const double gp = 0.57735026918962576;
+    double xi, eta;
+    if (tying) {
+      const double txi[4] = {0, 0, -1, 1}, teta[4] = {-1, 1, 0, 0};
+      xi = txi[t];
+      eta = teta[t];
+    } else {
+      xi = gp * sgn_xi[t - 4];
+      eta = gp * sgn_eta[t - 4];
+    }
+    double N[4], Nx[4], Ne[4];
+    for (int a = 0; a < 4; ++a) {
+      N[a] = 0.25 * (1 + xi * sgn_xi[a]) * (1 + eta * sgn_eta[a]);
+      Nx[a] = 0.25 * sgn_xi[a] * (1 + eta * sgn_eta[a]);
+      Ne[a] = 0.25 * sgn_eta[a] * (1 + xi * sgn_xi[a]);
+    }
+    double j00 = 0, j01 = 0, j10 = 0, j11 = 0;
+    for (int a = 0; a < 4; ++a) {
+      j00 += Nx[a] * xl[a][0]; j01 += Nx[a] * xl[a][1];
+      j10 += Ne[a] * xl[a][0]; j11 += Ne[a] * xl[a][1];
+    }
+    if (tying) {
+      // covariant shear along xi (A, C) or eta (D, B): w_,s + beta_x x_,s + beta_y y_,s,
+      // beta_x = theta_y, beta_y = -theta_x
+      const bool along_xi = t < 2;
+      const double xd = along_xi ? j00 : j10, yd = along_xi ? j01 : j11;
+      for (int a = 0; a < 4; ++a) {
+        tie[t][6 * a + 0] = 0; tie[t][6 * a + 1] = 0; tie[t][6 * a + 5] = 0;
+        tie[t][6 * a + 2] = along_xi ? Nx[a] : Ne[a];
+        tie[t][6 * a + 3] = -N[a] * yd;
+        tie[t][6 * a + 4] = N[a] * xd;
+      }
+    } else {
+      const int g = t - 4;
+      const double det = j00 * j11 - j01 * j10;
+      dj[g] = det;
+      const double i00 = j11 / det, i01 = -j01 / det, i10 = -j10 / det, i11 = j00 / det;
+      for (int col = 0; col < 24; ++col) {
+        Bm[g][0][col] = Bm[g][1][col] = Bm[g][2][col] = 0.0;
+        Bb[g][0][col] = Bb[g][1][col] = Bb[g][2][col] = 0.0;
+      }
+      for (int a = 0; a < 4; ++a) {
+        const double dx = i00 * Nx[a] + i01 * Ne[a], dy = i10 * Nx[a] + i11 * Ne[a];
+        Bm[g][0][6 * a] = dx;
+        Bm[g][1][6 * a + 1] = dy;
+        Bm[g][2][6 * a] = dy;
+        Bm[g][2][6 * a + 1] = dx;
+        Bb[g][0][6 * a + 4] = dx;
+        Bb[g][1][6 * a + 3] = -dy;
+        Bb[g][2][6 * a + 4] = dy;
+        Bb[g][2][6 * a + 3] = -dx;
+      }
+    }
+  }
+  __syncthreads();
+  // Cartesian shear rows at the Gauss points from the tied covariant strains
+  for (int w = t; w < 4 * 24; w += blockDim.x) {
+    const int g = w / 24, col = w % 24;
+    const double gp = 0.57735026918962576;
+    const double xi = gp * sgn_xi[g], eta = gp * sgn_eta[g];
+    const double sxi = 0.5 * (1 - eta) * tie[0][col] + 0.5 * (1 + eta) * tie[1][col];
+    const double seta = 0.5 * (1 - xi) * tie[2][col] + 0.5 * (1 + xi) * tie[3][col];
+    // inverse Jacobian at the point
+    double j00 = 0, j01 = 0, j10 = 0, j11 = 0;
+    for (int a = 0; a < 4; ++a) {
+      const double nx = 0.25 * sgn_xi[a] * (1 + eta * sgn_eta[a]);
+      const double ne = 0.25 * sgn_eta[a] * (1 + xi * sgn_xi[a]);
+      j00 += nx * xl[a][0]; j01 += nx * xl[a][1];
+      j10 += ne * xl[a][0]; j11 += ne * xl[a][1];
+    }
+    const double det = j00 * j11 - j01 * j10;
+    Bs[g][0][col] = (j11 * sxi - j01 * seta) / det;
+    Bs[g][1][col] = (-j10 * sxi + j00 * seta) / det;
+  }
+  __syncthreads();
+  const double cm = P.E * P.h / (1 - P.nu * P.nu);
+  const double cb = P.E * P.h * P.h * P.h / (12 * (1 - P.nu * P.nu));
+  const double ks = 5.0 / 6.0 * P.E / (2 * (1 + P.nu)) * P.h;
+  for (int w = t; w < 576; w += blockDim.x) {
+    const int i = w / 24, j = w % 24;
+    double s = 0.0;
+    for (int g = 0; g < 4; ++g) {
+      const double m0 = Bm[g][0][i], m1 = Bm[g][1][i], m2 = Bm[g][2][i];
+      const double n0 = Bm[g][0][j], n1 = Bm[g][1][j], n2 = Bm[g][2][j];
+      const double mem = cm * (m0 * (n0 + P.nu * n1) + m1 * (P.nu * n0 + n1) + 0.5 * (1 - P.nu) * m2 * n2);
+      const double b0 = Bb[g][0][i], b1 = Bb[g][1][i], b2 = Bb[g][2][i];
+      const double c0 = Bb[g][0][j], c1 = Bb[g][1][j], c2 = Bb[g][2][j];
+      const double ben = cb * (b0 * (c0 + P.nu * c1) + b1 * (P.nu * c0 + c1) + 0.5 * (1 - P.nu) * b2 * c2);
+      const double she = ks * (Bs[g][0][i] * Bs[g][0][j] + Bs[g][1][i] * Bs[g][1][j]);
+      s += (mem + ben + she) * dj[g];
+    }
+    if (i == j && i % 6 == 5) s += 1e-3 * cb;
+    D.Kl[576 * (long long)e + w] = s;
+  }
+  if (t == 0) {
+    const double A = 0.5 * fabs((xl[2][0] - xl[0][0]) * (xl[3][1] - xl[1][1]) -
+                                (xl[2][1] - xl[0][1]) * (xl[3][0] - xl[1][0]));
+    for (int a = 0; a < 4; ++a) {
+      atomicAdd(D.mt + id[a], P.rho * P.h * A * 0.25);
+      atomicAdd(D.mr + id[a], P.rho * P.h * P.h * P.h / 12.0 * A * 0.25);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- element work
+struct ShellSmem {
+  double xs[12], Rs[36], Re[9], c[3], xb[12], d[24], fl[24], fp[24], w6[6];
+  double U[24][6], V[6][24], KU[24][6], W[6][24];
+  double A[24][24], B[24][24];
+  int id[4];
+};
+
+// Internal force of element e at (u, R) scattered into fout; with Ke, also
+// the element tangent (global frame) and its diagonal into kd.
+__device__ void shell_element(const ShellParams &P, const ShellDev &D, int e, const double *u,
+                              const double *R, double *fout, double *Ke, double *kd,
+                              ShellSmem &S) {
+  const int t = threadIdx.x, nt = blockDim.x;
+  if (t < 4) {
+    int id[4];
+    elem_ids(P, e, id);
+    S.id[t] = id[t];
+  }
+  __syncthreads();
+  if (t < 12) S.xs[t] = D.X[3 * S.id[t / 3] + t % 3] + u[3 * S.id[t / 3] + t % 3];
+  if (t < 36) S.Rs[t] = R[9 * S.id[t / 9] + t % 9];
+  __syncthreads();
+  if (t == 0) quad_frame_dev(S.xs, S.Re, S.c);
+  __syncthreads();
+  if (t < 12) {
+    const int a = t / 3, k = t % 3;
+    double s = 0.0;
+    for (int q = 0; q < 3; ++q) s += S.Re[3 * q + k] * (S.xs[3 * a + q] - S.c[q]);
+    S.xb[t] = s;
+    S.d[6 * a + k] = s - D.xb0[12 * e + t];
+  } else if (t < 16) {
+    // deformational rotation R_e^T R_a R_e0 of node a
+    const int a = t - 12;
+    const double *R0 = D.Re0 + 9 * e;
+    double T1[9], Rd[9];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        double s = 0.0;
+        for (int q = 0; q < 3; ++q) s += S.Re[3 * q + i] * S.Rs[9 * a + 3 * q + j];
+        T1[3 * i + j] = s;
+      }
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        double s = 0.0;
+        for (int q = 0; q < 3; ++q) s += T1[3 * i + q] * R0[3 * q + j];
+        Rd[3 * i + j] = s;
+      }
+    rotvec(Rd, S.d + 6 * a + 3);
+  }
+  __syncthreads();
+  // U (24 x 6) and V (6 x 24) of the projector P = I - U V
+  for (int w = t; w < 144; w += nt) {
+    const int i = w / 6, k = w % 6, a = i / 6, s = i % 6;
+    double val = 0.0;
+    if (s < 3) {
+      if (k < 3) val = (k == s) ? 1.0 : 0.0;
+      else {
+        // -S(xb_a) column (k-3): -(xb_a x e_{k-3})_s
+        const double *xa = S.xb + 3 * a;
+        const int m = k - 3;
+        const double ex[3] = {m == 0 ? 1.0 : 0.0, m == 1 ? 1.0 : 0.0, m == 2 ? 1.0 : 0.0};
+        const double cr[3] = {xa[1] * ex[2] - xa[2] * ex[1], xa[2] * ex[0] - xa[0] * ex[2],
+                              xa[0] * ex[1] - xa[1] * ex[0]};
+        val = -cr[s];
+      }
+    } else {
+      val = (k >= 3 && k - 3 == s - 3) ? 1.0 : 0.0;
+    }
+    S.U[i][k] = val;
+  }
+  for (int w = t; w < 144; w += nt) {
+    const int k = w / 24, j = w % 24, b = j / 6, s = j % 6;
+    double val = 0.0;
+    if (k < 3) {
+      val = (s == k) ? 0.25 : 0.0;
+    } else {
+      // spin of the frame: x and y tilts from the diagonals, z from the sides
+      const double a1 = S.xb[6] - S.xb[0], a2 = S.xb[7] - S.xb[1];
+      const double b1 = S.xb[9] - S.xb[3], b2 = S.xb[10] - S.xb[4];
+      const double Nn = a1 * b2 - a2 * b1;
+      const double ap = S.xb[3] + S.xb[6] - S.xb[0] - S.xb[9];
+      if (k == 3 && s == 2) val = (b == 2 ? -b1 : b == 0 ? b1 : b == 3 ? a1 : -a1) / Nn;
+      if (k == 4 && s == 2) val = (b == 2 ? -b2 : b == 0 ? b2 : b == 3 ? a2 : -a2) / Nn;
+      if (k == 5 && s == 1) val = (b == 1 || b == 2 ? 1.0 : -1.0) / ap;
+    }
+    S.V[k][j] = val;
+  }
+  __syncthreads();
+  const double *Kl = D.Kl + 576 * (long long)e;
+  if (t < 24) {
+    double s = 0.0;
+    for (int j = 0; j < 24; ++j) s += Kl[24 * t + j] * S.d[j];
+    S.fl[t] = s;
+  }
+  __syncthreads();
+  if (t < 6) {
+    double s = 0.0;
+    for (int i = 0; i < 24; ++i) s += S.U[i][t] * S.fl[i];
+    S.w6[t] = s;
+  }
+  __syncthreads();
+  if (t < 24) {
+    double s = S.fl[t];
+    for (int k = 0; k < 6; ++k) s -= S.V[k][t] * S.w6[k];
+    S.fp[t] = s;
+  }
+  __syncthreads();
+  if (t < 24) {
+    const int blk = t / 3, k = t % 3, a = blk / 2, kind = blk % 2;
+    double s = 0.0;
+    for (int q = 0; q < 3; ++q) s += S.Re[3 * k + q] * S.fp[3 * blk + q];
+    atomicAdd(fout + 6 * S.id[a] + 3 * kind + k, s);
+  }
+  if (!Ke) return;
+  // tangent: A = K_l P = K_l - (K_l U) V, B = P^T A = A - V^T (U^T A), then rotate
+  for (int w = t; w < 144; w += nt) {
+    const int i = w / 6, k = w % 6;
+    double s = 0.0;
+    for (int j = 0; j < 24; ++j) s += Kl[24 * i + j] * S.U[j][k];
+    S.KU[i][k] = s;
+  }
+  __syncthreads();
+  for (int w = t; w < 576; w += nt) {
+    const int i = w / 24, j = w % 24;
+    double s = Kl[w];
+    for (int k = 0; k < 6; ++k) s -= S.KU[i][k] * S.V[k][j];
+    S.A[i][j] = s;
+  }
+  __syncthreads();
+  for (int w = t; w < 144; w += nt) {
+    const int k = w / 24, j = w % 24;
+    double s = 0.0;
+    for (int i = 0; i < 24; ++i) s += S.U[i][k] * S.A[i][j];
+    S.W[k][j] = s;
+  }
+  __syncthreads();
+  for (int w = t; w < 576; w += nt) {
+    const int i = w / 24, j = w % 24;
+    double s = S.A[i][j];
+    for (int k = 0; k < 6; ++k) s -= S.V[k][i] * S.W[k][j];
+    S.B[i][j] = s;
+  }
+  __syncthreads();
+  // A = B R^T per 3x3 block column, then Ke = R A per block row
+  for (int w = t; w < 576; w += nt) {
+    const int i = w / 24, j = w % 24, bj = j / 3, jj = j % 3;
+    double s = 0.0;
+    for (int q = 0; q < 3; ++q) s += S.B[i][3 * bj + q] * S.Re[3 * jj + q];
+    S.A[i][j] = s;
+  }
+  __syncthreads();
+  double *Kg = Ke + 576 * (long long)e;
+  for (int w = t; w < 576; w += nt) {
+    const int i = w / 24, j = w % 24, bi = i / 3, ii = i % 3;
+    double s = 0.0;
+    for (int q = 0; q < 3; ++q) s += S.Re[3 * ii + q] * S.A[3 * bi + q][j];
+    Kg[w] = s;
+    if (i == j) {
+      const int a = bi / 2, kind = bi % 2;
+      atomicAdd(kd + 6 * S.id[a] + 3 * kind + ii, s);
+    }
+  }
+  __syncthreads();
+}
+
+// y += theta Ke p for element e (global frame), scattered by atomics.
+__device__ void shell_matvec(const ShellParams &P, const ShellDev &D, int e, const double *p,
+                             double *y, ShellSmem &S) {
+  const int t = threadIdx.x;
+  if (t < 4) {
+    int id[4];
+    elem_ids(P, e, id);
+    S.id[t] = id[t];
+  }
+  __syncthreads();
+  if (t < 24) S.d[t] = p[6 * S.id[t / 6] + t % 6];
+  __syncthreads();
+  if (t < 24) {
+    const double *Kg = D.Ke + 576 * (long long)e + 24 * t;
+    double s = 0.0;
+    for (int j = 0; j < 24; ++j) s += Kg[j] * S.d[j];
+    atomicAdd(y + 6 * S.id[t / 6] + t % 6, P.theta * s);
+  }
+  __syncthreads();
+}
+
+// Grid-wide sums of two values: block reduction, one atomic per block into
+// slot s, grid barrier, read; the slot two ahead is cleared for later use.
+__device__ __forceinline__ void grid_sum2(cg::grid_group &grid, double *red, int &slot, double a,
+                                          double b, double &ra, double &rb) {
+  __shared__ double part[2][kShellThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    part[0][w] = a;
+    part[1][w] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0.0, sb = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      sa += part[0][k];
+      sb += part[1][k];
+    }
+    atomicAdd(red + 2 * slot, sa);
+    atomicAdd(red + 2 * slot + 1, sb);
+  }
+  grid.sync();
+  ra = *(volatile double *)(red + 2 * slot);
+  rb = *(volatile double *)(red + 2 * slot + 1);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int clr = (slot + 2) % 3;
+    red[2 * clr] = 0.0;
+    red[2 * clr + 1] = 0.0;
+  }
+  slot = (slot + 1) % 3;
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kShellThreads) k_shell_step(ShellParams P, ShellDev D) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ ShellSmem S;
+  const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long gs = (long long)gridDim.x * blockDim.x;
+  const int n = P.n, nn = P.nn;
+  int slot = 0;
+  double ra, rb;
+  for (long long i = gt; i < n; i += gs) {
+    D.v0[i] = D.v[i];
+    D.dq[i] = 0.0;
+    D.f0[i] = 0.0;
+  }
+  for (long long i = gt; i < 3 * nn; i += gs) D.u0[i] = D.u[i];
+  for (long long i = gt; i < 9 * nn; i += gs) D.R0[i] = D.R[i];
+  if (gt < 6) D.red[gt] = 0.0;
+  grid.sync();
+  for (int e = blockIdx.x; e < P.ne; e += gridDim.x)
+    shell_element(P, D, e, D.u0, D.R0, D.f0, nullptr, nullptr, S);
+  grid.sync();
+  const double ith = 1.0 / P.theta, idt = 1.0 / P.dt, cM = 1.0 / (P.theta * P.dt * P.dt);
+  double r0 = -1.0;
+  int it = 0, conv = 0, cg_total = 0;
+  for (it = 0;; ++it) {
+    // current iterate from the step increments
+    for (long long a = gt; a < nn; a += gs) {
+      for (int k = 0; k < 3; ++k) D.u1[3 * a + k] = D.u0[3 * a + k] + D.dq[6 * a + k];
+      double Ex[9];
+      rodrigues(D.dq + 6 * a + 3, Ex);
+      const double *Ra = D.R0 + 9 * a;
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+          D.R1[9 * a + 3 * i + j] = Ex[3 * i] * Ra[j] + Ex[3 * i + 1] * Ra[3 + j] + Ex[3 * i + 2] * Ra[6 + j];
+    }
+    for (long long i = gt; i < n; i += gs) {
+      D.f[i] = 0.0;
+      D.kd[i] = 0.0;
+    }
+    grid.sync();
+    for (int e = blockIdx.x; e < P.ne; e += gridDim.x)
+      shell_element(P, D, e, D.u1, D.R1, D.f, D.Ke, D.kd, S);
+    grid.sync();
+    double part = 0.0;
+    for (long long i = gt; i < n; i += gs) {
+      const long long a = i / 6;
+      const double m = (i % 6) < 3 ? D.mt[a] : D.mr[a];
+      const double v1 = (D.dq[i] * idt - (1.0 - P.theta) * D.v0[i]) * ith;
+      double Rv = m * (v1 - D.v0[i]) * idt - P.theta * (D.F1[i] - D.f[i]) -
+                  (1.0 - P.theta) * (D.F0[i] - D.f0[i]);
+      if (D.fixed[i]) Rv = 0.0;
+      D.rhs[i] = -Rv;
+      part += Rv * Rv;
+    }
+    grid_sum2(grid, D.red, slot, part, 0.0, ra, rb);
+    const double rn = sqrt(ra);
+    if (r0 < 0.0) r0 = rn;
+    if (rn <= P.rtol * r0 + P.atol) {
+      conv = 1;
+      break;
+    }
+    if (it >= P.max_it) break;
+    // preconditioned conjugate gradients on J x = rhs
+    double rz0 = 0.0, rr0 = 0.0;
+    for (long long i = gt; i < n; i += gs) {
+      const long long a = i / 6;
+      const double m = (i % 6) < 3 ? D.mt[a] : D.mr[a];
+      const double dJ = D.fixed[i] ? 1.0 : m * cM + P.theta * D.kd[i];
+      const double ri = D.rhs[i];
+      D.x[i] = 0.0;
+      D.r[i] = ri;
+      D.z[i] = ri / dJ;
+      D.p[i] = ri / dJ;
+      rz0 += ri * ri / dJ;
+      rr0 += ri * ri;
+    }
+    double rz, bnorm2;
+    grid_sum2(grid, D.red, slot, rz0, rr0, rz, bnorm2);
+    const double stop2 = P.cg_rtol * P.cg_rtol * bnorm2;
+    for (int k = 0; k < P.max_cg && bnorm2 > 0.0; ++k) {
+      for (long long i = gt; i < n; i += gs) D.Ap[i] = 0.0;
+      grid.sync();
+      for (int e = blockIdx.x; e < P.ne; e += gridDim.x) shell_matvec(P, D, e, D.p, D.Ap, S);
+      grid.sync();
+      double pap = 0.0;
+      for (long long i = gt; i < n; i += gs) {
+        const long long a = i / 6;
+        const double m = (i % 6) < 3 ? D.mt[a] : D.mr[a];
+        double y = D.fixed[i] ? D.p[i] : D.Ap[i] + m * cM * D.p[i];
+        D.Ap[i] = y;
+        pap += D.p[i] * y;
+      }
+      double pAp;
+      grid_sum2(grid, D.red, slot, pap, 0.0, pAp, rb);
+      const double alpha = rz / pAp;
+      double rzp = 0.0, rrp = 0.0;
+      for (long long i = gt; i < n; i += gs) {
+        const long long a = i / 6;
+        const double m = (i % 6) < 3 ? D.mt[a] : D.mr[a];
+        const double dJ = D.fixed[i] ? 1.0 : m * cM + P.theta * D.kd[i];
+        D.x[i] += alpha * D.p[i];
+        const double ri = D.r[i] - alpha * D.Ap[i];
+        D.r[i] = ri;
+        D.z[i] = ri / dJ;
+        rzp += ri * ri / dJ;
+        rrp += ri * ri;
+      }
+      double rzn, rr;
+      grid_sum2(grid, D.red, slot, rzp, rrp, rzn, rr);
+      ++cg_total;
+      if (rr <= stop2) break;
+      const double beta = rzn / rz;
+      rz = rzn;
+      for (long long i = gt; i < n; i += gs) D.p[i] = D.z[i] + beta * D.p[i];
+      grid.sync();
+    }
+    for (long long i = gt; i < n; i += gs) D.dq[i] += P.lambda * D.x[i];
+    grid.sync();
+  }
+  // final state
+  for (long long i = gt; i < n; i += gs) {
+    const double v1 = (D.dq[i] * idt - (1.0 - P.theta) * D.v0[i]) * ith;
+    D.v[i] = D.fixed[i] ? 0.0 : v1;
+    D.F0[i] = D.F1[i];
+  }
+  for (long long i = gt; i < 3 * nn; i += gs) D.u[i] = D.u1[i];
+  for (long long i = gt; i < 9 * nn; i += gs) D.R[i] = D.R1[i];
+  if (gt == 0) {
+    D.iters[0] = conv ? it : -it - 1;
+    D.iters[1] = cg_total;
+  }
+}
+
+}  // namespace kbc
+
+using namespace kbc;
+
+struct fem_shell_ctx {
+  ShellParams p;
+  ShellDev d;
+  double *F1 = nullptr;
+  char *ws = nullptr;
+  bool own_ws = false;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int grid = 0;
+  bool poisoned = false;
+  char msg[256] = {0};
+};
+
+namespace {
+
+thread_local char g_shell_msg[256];
+
+size_t al(size_t b) { return (b + 255) / 256 * 256; }
+
+size_t shell_layout(int nx, int ny, fem_shell_ctx *s) {
+  const size_t nn = (size_t)nx * ny, ne = (size_t)(nx - 1) * (ny - 1), n = 6 * nn;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += al(bytes);
+    return o;
+  };
+  const size_t oX = take(sizeof(double) * 3 * nn), ofx = take(sizeof(int32_t) * n);
+  const size_t oKl = take(sizeof(double) * 576 * ne), oRe0 = take(sizeof(double) * 9 * ne);
+  const size_t oxb0 = take(sizeof(double) * 12 * ne), omt = take(sizeof(double) * nn),
+               omr = take(sizeof(double) * nn);
+  const size_t ou = take(sizeof(double) * 3 * nn), oR = take(sizeof(double) * 9 * nn),
+               ov = take(sizeof(double) * n), oF0 = take(sizeof(double) * n);
+  const size_t ou0 = take(sizeof(double) * 3 * nn), oR0 = take(sizeof(double) * 9 * nn),
+               ov0 = take(sizeof(double) * n);
+  const size_t ou1 = take(sizeof(double) * 3 * nn), oR1 = take(sizeof(double) * 9 * nn);
+  const size_t odq = take(sizeof(double) * n), of0 = take(sizeof(double) * n),
+               of = take(sizeof(double) * n), okd = take(sizeof(double) * n);
+  const size_t oKe = take(sizeof(double) * 576 * ne);
+  size_t ovec[6];
+  for (int k = 0; k < 6; ++k) ovec[k] = take(sizeof(double) * n);
+  const size_t ored = take(sizeof(double) * 6), oF1 = take(sizeof(double) * n),
+               oit = take(sizeof(int) * 2);
+  if (s) {
+    char *w = s->ws;
+    ShellDev &d = s->d;
+    d.X = (const double *)(w + oX);
+    d.fixed = (const int32_t *)(w + ofx);
+    d.Kl = (double *)(w + oKl); d.Re0 = (double *)(w + oRe0); d.xb0 = (double *)(w + oxb0);
+    d.mt = (double *)(w + omt); d.mr = (double *)(w + omr);
+    d.u = (double *)(w + ou); d.R = (double *)(w + oR); d.v = (double *)(w + ov);
+    d.F0 = (double *)(w + oF0);
+    d.u0 = (double *)(w + ou0); d.R0 = (double *)(w + oR0); d.v0 = (double *)(w + ov0);
+    d.u1 = (double *)(w + ou1); d.R1 = (double *)(w + oR1);
+    d.dq = (double *)(w + odq); d.f0 = (double *)(w + of0); d.f = (double *)(w + of);
+    d.kd = (double *)(w + okd);
+    d.Ke = (double *)(w + oKe);
+    d.rhs = (double *)(w + ovec[0]); d.x = (double *)(w + ovec[1]); d.r = (double *)(w + ovec[2]);
+    d.z = (double *)(w + ovec[3]); d.p = (double *)(w + ovec[4]); d.Ap = (double *)(w + ovec[5]);
+    d.red = (double *)(w + ored);
+    s->F1 = (double *)(w + oF1);
+    d.F1 = s->F1;
+    d.iters = (int *)(w + oit);
+  }
+  return off;
+}
+
+const char *shell_validate(const fem_shell_config *c) {
+  if (!c) return "config is NULL";
+  if (c->nx < 2 || c->ny < 2 || (long long)c->nx * c->ny > kShellMaxNodes)
+    return "nx, ny >= 2 and nx * ny <= 4096";
+  if (!c->X || !c->fixed) return "X and fixed are required";
+  if (!(c->E > 0 && c->h > 0 && c->rho > 0 && c->nu >= 0 && c->nu < 0.5))
+    return "E, h, rho > 0 and 0 <= nu < 0.5";
+  if (!(c->theta > 0 && c->theta <= 1) || !(c->lambda > 0 && c->lambda <= 1) || c->max_it < 1 ||
+      !(c->dt > 0))
+    return "bad time-integration parameters";
+  return nullptr;
+}
+
+}  // namespace
+
+#define SHELL_CK(call)                                                              \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      s->poisoned = true;                                                           \
+      snprintf(s->msg, sizeof(s->msg), "%s: %s", #call, cudaGetErrorString(e_));    \
+      return LBM_ECUDA;                                                             \
+    }                                                                               \
+  } while (0)
+
+extern "C" {
+
+lbm_status fem_shell_workspace_size(const fem_shell_config *c, size_t *bytes) {
+  if (!bytes || shell_validate(c)) return LBM_EINVAL;
+  *bytes = shell_layout(c->nx, c->ny, nullptr);
+  return LBM_OK;
+}
+
+lbm_status fem_shell_create(const fem_shell_config *c, void *workspace, size_t bytes,
+                            fem_shell_ctx **out) {
+  if (!out) return LBM_EINVAL;
+  *out = nullptr;
+  if (const char *why = shell_validate(c)) {
+    snprintf(g_shell_msg, sizeof(g_shell_msg), "fem_shell_create: %s", why);
+    return LBM_EINVAL;
+  }
+  fem_shell_ctx *s = new (std::nothrow) fem_shell_ctx();
+  if (!s) return LBM_ENOMEM;
+  const size_t need = shell_layout(c->nx, c->ny, nullptr);
+  if (workspace) {
+    if (bytes < need || ((uintptr_t)workspace % 256)) {
+      delete s;
+      snprintf(g_shell_msg, sizeof(g_shell_msg), "fem_shell_create: workspace needs %zu bytes", need);
+      return LBM_ENOMEM;
+    }
+    s->ws = (char *)workspace;
+  } else {
+    if (cudaMalloc((void **)&s->ws, need) != cudaSuccess) {
+      delete s;
+      return LBM_ENOMEM;
+    }
+    s->own_ws = true;
+  }
+  if (c->stream) {
+    s->stream = (cudaStream_t)c->stream;
+  } else {
+    cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    s->own_stream = true;
+  }
+  shell_layout(c->nx, c->ny, s);
+  ShellParams &p = s->p;
+  p.nx = c->nx; p.ny = c->ny; p.nn = c->nx * c->ny; p.ne = (c->nx - 1) * (c->ny - 1);
+  p.n = 6 * p.nn;
+  p.E = c->E; p.nu = c->nu; p.h = c->h; p.rho = c->rho;
+  p.theta = c->theta; p.lambda = c->lambda; p.rtol = c->rtol; p.atol = c->atol; p.dt = c->dt;
+  p.max_it = c->max_it;
+  p.max_cg = c->max_cg > 0 ? c->max_cg : 4 * p.n;
+  p.cg_rtol = c->cg_rtol > 0 ? c->cg_rtol : 1e-13;
+  cudaError_t e = cudaMemsetAsync(s->ws, 0, need, s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync((void *)s->d.X, c->X, sizeof(double) * 3 * p.nn, cudaMemcpyDefault, s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync((void *)s->d.fixed, c->fixed, sizeof(int32_t) * p.n, cudaMemcpyDefault,
+                        s->stream);
+  if (e == cudaSuccess) {
+    std::vector<double> Rid(9 * (size_t)p.nn, 0.0);
+    for (int a = 0; a < p.nn; ++a) Rid[9 * a] = Rid[9 * a + 4] = Rid[9 * a + 8] = 1.0;
+    e = cudaMemcpyAsync(s->d.R, Rid.data(), sizeof(double) * 9 * p.nn, cudaMemcpyHostToDevice,
+                        s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  }
+  if (e == cudaSuccess) {
+    k_shell_setup<<<p.ne, kShellThreads, 0, s->stream>>>(p, s->d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  int dev = 0, sms = 0, per_sm = 0, coop = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shell_step, kShellThreads, 0);
+  if (e != cudaSuccess || !coop || per_sm < 1) {
+    snprintf(g_shell_msg, sizeof(g_shell_msg), "fem_shell_create: %s",
+             e != cudaSuccess ? cudaGetErrorString(e) : "cooperative launch unavailable");
+    if (s->own_ws) cudaFree(s->ws);
+    if (s->own_stream) cudaStreamDestroy(s->stream);
+    delete s;
+    return LBM_ECUDA;
+  }
+  s->grid = p.ne < sms * per_sm ? p.ne : sms * per_sm;
+  *out = s;
+  return LBM_OK;
+}
+
+lbm_status fem_shell_step(fem_shell_ctx *s, const double *F1) {
+  if (!s || !F1) return LBM_EINVAL;
+  if (s->poisoned) return LBM_ESTATE;
+  SHELL_CK(cudaMemcpyAsync(s->F1, F1, sizeof(double) * s->p.n, cudaMemcpyDefault, s->stream));
+  void *args[] = {(void *)&s->p, (void *)&s->d};
+  SHELL_CK(cudaLaunchCooperativeKernel((const void *)k_shell_step, dim3(s->grid), dim3(kShellThreads),
+                                       args, 0, s->stream));
+  return LBM_OK;
+}
+
+lbm_status fem_shell_get_state(fem_shell_ctx *s, double *u, double *R, double *v, int *iters) {
+  if (!s) return LBM_EINVAL;
+  if (s->poisoned) return LBM_ESTATE;
+  const size_t nn = s->p.nn;
+  if (u) SHELL_CK(cudaMemcpyAsync(u, s->d.u, sizeof(double) * 3 * nn, cudaMemcpyDefault, s->stream));
+  if (R) SHELL_CK(cudaMemcpyAsync(R, s->d.R, sizeof(double) * 9 * nn, cudaMemcpyDefault, s->stream));
+  if (v) SHELL_CK(cudaMemcpyAsync(v, s->d.v, sizeof(double) * 6 * nn, cudaMemcpyDefault, s->stream));
+  if (iters) SHELL_CK(cudaMemcpyAsync(iters, s->d.iters, sizeof(int) * 2, cudaMemcpyDefault, s->stream));
+  SHELL_CK(cudaStreamSynchronize(s->stream));
+  return LBM_OK;
+}
+
+lbm_status fem_shell_set_state(fem_shell_ctx *s, const double *u, const double *R, const double *v,
+                               const double *F0) {
+  if (!s) return LBM_EINVAL;
+  if (s->poisoned) return LBM_ESTATE;
+  const size_t nn = s->p.nn;
+  if (u) SHELL_CK(cudaMemcpyAsync(s->d.u, u, sizeof(double) * 3 * nn, cudaMemcpyDefault, s->stream));
+  if (R) SHELL_CK(cudaMemcpyAsync(s->d.R, R, sizeof(double) * 9 * nn, cudaMemcpyDefault, s->stream));
+  if (v) SHELL_CK(cudaMemcpyAsync(s->d.v, v, sizeof(double) * 6 * nn, cudaMemcpyDefault, s->stream));
+  if (F0) SHELL_CK(cudaMemcpyAsync(s->d.F0, F0, sizeof(double) * 6 * nn, cudaMemcpyDefault, s->stream));
+  SHELL_CK(cudaStreamSynchronize(s->stream));
+  return LBM_OK;
+}
+
+const char *fem_shell_last_error(const fem_shell_ctx *s) { return s ? s->msg : g_shell_msg; }
+
+void fem_shell_destroy(fem_shell_ctx *s) {
+  if (!s) return;
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  if (s->own_stream) cudaStreamDestroy(s->stream);
+  if (s->own_ws) cudaFree(s->ws);
+  delete s;
+}
+
+}  // extern "C"

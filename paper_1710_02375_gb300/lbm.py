@@ -458,6 +458,68 @@ def _batch_chk(b, st):
         raise LbmError(st, load().lbm_batch_last_error(b).decode(errors="replace"))
 
 
+class Shell:
+    """GPU co-rotational flat shell (fem_shell_*): nx x ny node grid with
+    reference positions X[nn, 3], Dirichlet mask fixed[6 nn]; torch
+    allocates the workspace."""
+
+    def __init__(self, X, nx, ny, E, nu, h, rho, fixed, theta=0.5, lam=0.7, rtol=1e-10, atol=1e-13,
+                 max_it=200, dt=1.0, max_cg=0, cg_rtol=0.0, stream=None, device="cuda"):
+        import torch
+        from ._abi_ext import fem_shell_config
+        L = load()
+        self.nx, self.ny = int(nx), int(ny)
+        self.nn = self.nx * self.ny
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=torch.device(device))
+        self._X = np.ascontiguousarray(X, dtype=np.float64)
+        self._fixed = np.ascontiguousarray(fixed, dtype=np.int32)
+        c = fem_shell_config()
+        c.nx, c.ny = self.nx, self.ny
+        c.X = self._X.ctypes.data
+        c.E, c.nu, c.h, c.rho = E, nu, h, rho
+        c.fixed = self._fixed.ctypes.data
+        c.theta, c.lambda_, c.rtol, c.atol, c.max_it, c.dt = theta, lam, rtol, atol, max_it, dt
+        c.max_cg, c.cg_rtol = max_cg, cg_rtol
+        c.stream = self.stream.cuda_stream
+        n = ctypes.c_size_t()
+        if L.fem_shell_workspace_size(ctypes.byref(c), ctypes.byref(n)) != LBM_OK:
+            raise LbmError(LBM_EINVAL, "fem_shell_workspace_size")
+        self.workspace = torch.empty(n.value, dtype=torch.uint8, device=torch.device(device))
+        out = ctypes.c_void_p()
+        st = L.fem_shell_create(ctypes.byref(c), self.workspace.data_ptr(), n.value, ctypes.byref(out))
+        if st != LBM_OK:
+            raise LbmError(st, L.fem_shell_last_error(None).decode())
+        self.ctx = out.value
+
+    def _chk(self, st):
+        if st != LBM_OK:
+            raise LbmError(st, load().fem_shell_last_error(self.ctx).decode(errors="replace"))
+
+    def step(self, F1):
+        F1 = np.ascontiguousarray(F1, dtype=np.float64).reshape(-1)
+        self._chk(load().fem_shell_step(self.ctx, _ptr(F1)))
+        self._F1 = F1  # the copy is asynchronous
+
+    def state(self):
+        u = np.zeros((self.nn, 3))
+        R = np.zeros((self.nn, 3, 3))
+        v = np.zeros((self.nn, 6))
+        it = np.zeros(2, dtype=np.int32)
+        self._chk(load().fem_shell_get_state(self.ctx, _ptr(u), _ptr(R), _ptr(v), _ptr(it)))
+        return u, R, v, (int(it[0]), int(it[1]))
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            load().fem_shell_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Batch:
     """Many Lattice objects advanced with one launch per phase (lbm_batch_*).
 
