@@ -6,7 +6,7 @@ the 129 MB L2, so no L2 flush is needed between steps).  A step is one pass of
 the hot path over the whole lattice: pull-stream + KBC collision, one kernel.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload tgv128|c4|c4-coupled|c1-fsi]
+                  [--workload tgv128|c4|c4-coupled|c1-fsi|c3-fsi]
 
 The default line also carries "patterns": the same workload with FP16 and
 BF16 storage, as speedups over FP32.  --workload c4 / c4-coupled time the
@@ -409,6 +409,48 @@ def run_c1_fsi(args):
     print(json.dumps(line), flush=True)
 
 
+def run_c3_fsi(args):
+    """The 3-D plate in uniform flow (D3Q27 256 x 128 x 128, plate 40 x 20 x 2
+    clamped at its leading edge as a 16 x 8 co-rotational shell, Re = 400,
+    bending number 1e-4, rho_s / rho_f = 20, initial tip deflection 1e-3 L),
+    CSS-coupled, with FP32 and FP16 population storage."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1710_02375_gb300 import synth
+    from paper_1710_02375_gb300.cases import plate_coupled
+    c = synth.plate_case()
+    nodes = c["nx"] * c["ny"] * c["nz"]
+    out = {}
+    for name, storage in (("f32", 0), ("f16", 1)):
+        stream = torch.cuda.Stream()
+        L, S = plate_coupled(c, storage=storage, stream=stream)
+        L.step(args.warmup)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        L.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        L.check()
+        ms = e0.elapsed_time(e1) / args.steps
+        u, _, _, (it, ncg) = S.state()
+        out[name] = {"ms_per_step": ms, "steps_per_s": 1e3 / ms, "mlups": nodes / (ms * 1e-3) / 1e6,
+                     "newton_last_step": it, "cg_last_step": ncg, "tip": u[-1].tolist()}
+        L.close()
+        S.close()
+    line = {
+        "metric": "coupled FSI steps/s (3-D plate)", "value": out["f32"]["steps_per_s"], "unit": "steps/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["f32"]["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": "D3Q27 256x128x128 channel, plate 40x20x2 (16x8 shell), Re=400, K_B=1e-4",
+                   "nodes": nodes},
+        "forms": out, "f16_speedup": out["f32"]["ms_per_step"] / out["f16"]["ms_per_step"],
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -416,7 +458,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=500)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["tgv128", "c4", "c4-coupled", "c1-fsi"], default="tgv128")
+    ap.add_argument("--workload", choices=["tgv128", "c4", "c4-coupled", "c1-fsi", "c3-fsi"],
+                    default="tgv128")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -426,6 +469,8 @@ def main():
         run_c4(args)
     elif args.workload == "c1-fsi":
         run_c1_fsi(args)
+    elif args.workload == "c3-fsi":
+        run_c3_fsi(args)
     else:
         run_ours(args)
 

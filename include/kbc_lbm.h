@@ -276,6 +276,18 @@ lbm_status fem_shell_set_state(fem_shell_ctx *s, const double *u, const double *
 const char *fem_shell_last_error(const fem_shell_ctx *s);
 void fem_shell_destroy(fem_shell_ctx *s);
 
+/* Couple a plate (fem_shell) to a D3Q27 lattice: the shell's surface
+ * occupies vertices [first_vertex, first_vertex + 2 nn) of the geometry --
+ * vertex first_vertex + n lies h/2 above node n along the rotated reference
+ * normal (the node's rotation applied to (0, 0, 1)), first_vertex + nn + n
+ * h/2 below it (the triangles are the caller's).  From then on every
+ * lbm_step runs fluid -> forces -> nodal loads (each node: the forces of its
+ * two vertices, no moments) -> one shell step -> surface positions and
+ * velocities -> geometry, on the lattice stream (create the shell on the
+ * lattice's stream).  The surface is set from the shell state at once.
+ * s NULL uncouples. */
+lbm_status fsi_couple_shell(lbm_ctx *ctx, fem_shell_ctx *s, int first_vertex);
+
 /* Couple a beam to the lattice (conventional serial staggered scheme,
  * section "Fluid-structure coupling"): the beam's flag surface occupies
  * surface vertices [first_vertex, first_vertex + 2 nn) of the geometry given

@@ -106,3 +106,62 @@ class CSSFlag:
         orc.fresh_init(self.lat, self.f, self.solid, new_solid, self.surf, periodic=(0, 0, 1))
         self.solid = new_solid
         self.t += 1
+
+
+def plate_vertices(X, u, R, h):
+    """Plate surface vertices [2 nn, 3]: node position plus / minus h/2 times
+    the rotated reference normal (third column of the node rotation)."""
+    d = R[:, :, 2]
+    x = X + u
+    return np.concatenate([x + 0.5 * h * d, x - 0.5 * h * d])
+
+
+def plate_velocities(v, R, h):
+    d = 0.5 * h * R[:, :, 2]
+    w = np.cross(v[:, 3:], d)
+    return np.concatenate([v[:, :3] + w, v[:, :3] - w])
+
+
+class CSSPlate:
+    """Conventional serial staggered loop of the 3-D plate: D3Q27 fluid step
+    with Grad boundaries, nodal loads (each shell node: the forces of its
+    vertices above and below, no moments), one shell step, new surface,
+    solid mask and fresh nodes.  The plate is the only body; its surface
+    mesh e (triangles over vertices [top nodes, bottom nodes]) is fixed."""
+
+    def __init__(self, shape, beta, bc, face_u, shell: "orc.Shell", e, h, u0=None, R0=None,
+                 rho0=None, vel0=None, periodic=(0, 1, 0)):
+        self.shape, self.beta, self.bc, self.face_u = shape, beta, bc, face_u
+        self.shell, self.e, self.h, self.periodic = shell, np.asarray(e, np.int32), h, periodic
+        u, R, v = shell.rest()
+        self.u = u if u0 is None else np.array(u0, dtype=np.float64)
+        self.R = R if R0 is None else np.array(R0, dtype=np.float64)
+        self.v = v
+        self.F0 = np.zeros((shell.nn, 6))
+        nz, ny, nx = shape
+        rho0 = np.ones(shape) if rho0 is None else rho0
+        vel0 = np.zeros((3,) + shape) if vel0 is None else vel0
+        self.f = orc.init_equilibrium(27, rho0, vel0)
+        self.surf = self._surface()
+        self.solid = orc.solid_mask(shape, self.surf)
+        self.iterations = []
+
+    def _surface(self):
+        x = plate_vertices(self.shell.X, self.u, self.R, self.h)
+        vel = plate_velocities(self.v, self.R, self.h)
+        return orc.Surface(x, vel, self.e, np.zeros(len(self.e), np.int32))
+
+    def step(self, **shell_kw):
+        self.f, vf, bf, _ = orc.step_bc(27, self.beta, self.f, bc=self.bc, face_u=self.face_u,
+                                        surf=self.surf, solid=self.solid)
+        self.vforce, self.bforce = vf, bf
+        nn = self.shell.nn
+        F1 = np.zeros((nn, 6))
+        F1[:, :3] = vf[:nn] + vf[nn:]
+        self.u, self.R, self.v, it = self.shell.step(self.u, self.R, self.v, self.F0, F1, **shell_kw)
+        self.iterations.append(it)
+        self.F0 = F1
+        self.surf = self._surface()
+        new_solid = orc.solid_mask(self.shape, self.surf)
+        orc.fresh_init(27, self.f, self.solid, new_solid, self.surf, periodic=self.periodic)
+        self.solid = new_solid

@@ -59,6 +59,8 @@ def declare(L):
     L.fem_destroy.argtypes = [vp]
     L.fem_destroy.restype = None
     L.fsi_couple.argtypes = [vp, vp, i32]
+    L.fsi_couple_shell.argtypes = [vp, vp, i32]
+    L.fsi_couple_shell.restype = ctypes.c_int
     L.fem_shell_workspace_size.argtypes = [ctypes.POINTER(fem_shell_config), ctypes.POINTER(sz)]
     L.fem_shell_create.argtypes = [ctypes.POINTER(fem_shell_config), vp, sz, ctypes.POINTER(vp)]
     L.fem_shell_step.argtypes = [vp, vp]

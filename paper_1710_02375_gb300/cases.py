@@ -70,3 +70,27 @@ def flag_coupled(inst, stream=None, ramp=1000):
     beam = Beam(X, EA, EI, rhoA, fixed, thickness=inst["h"], stream=L.stream)
     lbm.fsi_couple(L.ctx, beam.ctx, inst["ncyl"])
     return L, beam
+
+
+def plate_coupled(c, storage=0, stream=None, band=None, atol=1e-13):
+    """A synth.plate_case lattice with its CSS-coupled shell (fsi_couple_shell),
+    started from uniform flow at the inflow speed with the plate's initial
+    deflection.  Returns (Lattice, Shell)."""
+    from . import lbm, synth
+    from .lbm import Lattice, Shell
+    sh = c["shell"]
+    nn = sh["nx"] * sh["ny"]
+    L = Lattice(27, c["nx"], c["ny"], c["nz"], c["beta"], storage=storage, bc=c["bc"],
+                face_velocity=c["face_u"], max_links=200000, max_vertices=2 * nn,
+                max_elements=len(c["e"]), stream=stream)
+    x = synth.plate_vertices(sh["X"], c["u0"], c["R0"], sh["h"])
+    L.set_geometry(x, c["e"], np.zeros(len(c["e"]), np.int32),
+                   band_margin=0.5 * c["L"] if band is None else band)
+    vel = np.zeros((3, c["nz"], c["ny"], c["nx"]))
+    vel[0] = c["u_in"]
+    L.init_equilibrium(np.ones((c["nz"], c["ny"], c["nx"])), vel)
+    S = Shell(sh["X"], sh["nx"], sh["ny"], sh["E"], sh["nu"], sh["h"], sh["rho"], sh["fixed"],
+              atol=atol, stream=L.stream)
+    S.set_state(u=c["u0"], R=c["R0"])
+    lbm.fsi_couple_shell(L.ctx, S.ctx, 0)
+    return L, S

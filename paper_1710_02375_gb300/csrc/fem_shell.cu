@@ -616,6 +616,39 @@ __global__ void __launch_bounds__(kShellThreads) k_shell_step(ShellParams P, She
   }
 }
 
+// Nodal loads of a coupled plate: each node takes the momentum-exchange
+// forces of its two surface vertices (above and below), no moments.
+__global__ void k_shell_loads(ShellParams P, double *F1, const double *vforce, int v0) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= P.nn) return;
+  const int vt = v0 + a, vb = v0 + P.nn + a;
+  for (int k = 0; k < 3; ++k) {
+    F1[6 * a + k] = vforce[3 * vt + k] + vforce[3 * vb + k];
+    F1[6 * a + 3 + k] = 0.0;
+  }
+}
+
+// Surface vertices and velocities of the plate from the shell state: node
+// position plus / minus h/2 times the rotated reference normal (third column
+// of the nodal rotation), velocities v +- omega x (h/2 d).
+__global__ void k_shell_surface(ShellParams P, ShellDev D, double *surf_x, double *surf_v, int v0) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= P.nn) return;
+  const double *Ra = D.R + 9 * a;
+  const double hd[3] = {0.5 * P.h * Ra[2], 0.5 * P.h * Ra[5], 0.5 * P.h * Ra[8]};
+  const double *w = D.v + 6 * a + 3;
+  const double wx[3] = {w[1] * hd[2] - w[2] * hd[1], w[2] * hd[0] - w[0] * hd[2],
+                        w[0] * hd[1] - w[1] * hd[0]};
+  const int vt = v0 + a, vb = v0 + P.nn + a;
+  for (int k = 0; k < 3; ++k) {
+    const double x = D.X[3 * a + k] + D.u[3 * a + k];
+    surf_x[3 * vt + k] = x + hd[k];
+    surf_x[3 * vb + k] = x - hd[k];
+    surf_v[3 * vt + k] = D.v[6 * a + k] + wx[k];
+    surf_v[3 * vb + k] = D.v[6 * a + k] - wx[k];
+  }
+}
+
 }  // namespace kbc
 
 using namespace kbc;
@@ -843,3 +876,29 @@ void fem_shell_destroy(fem_shell_ctx *s) {
 }
 
 }  // extern "C"
+
+namespace kbc {
+
+int shell_nodes(const fem_shell_ctx *s) { return s->p.nn; }
+
+cudaError_t launch_shell_surface(fem_shell_ctx *s, double *surf_x, double *surf_v, int v0,
+                                 cudaStream_t st) {
+  k_shell_surface<<<(s->p.nn + 127) / 128, 128, 0, st>>>(s->p, s->d, surf_x, surf_v, v0);
+  return cudaGetLastError();
+}
+
+// Coupled structural step on the lattice stream: nodal loads from the
+// surface forces, the cooperative shell step, the new plate surface.
+cudaError_t launch_shell_coupled(fem_shell_ctx *s, const double *vforce, double *surf_x,
+                                 double *surf_v, int v0, cudaStream_t st) {
+  k_shell_loads<<<(s->p.nn + 127) / 128, 128, 0, st>>>(s->p, s->F1, vforce, v0);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  void *args[] = {(void *)&s->p, (void *)&s->d};
+  e = cudaLaunchCooperativeKernel((const void *)k_shell_step, dim3(s->grid), dim3(kShellThreads), args,
+                                  0, st);
+  if (e != cudaSuccess) return e;
+  return launch_shell_surface(s, surf_x, surf_v, v0, st);
+}
+
+}  // namespace kbc

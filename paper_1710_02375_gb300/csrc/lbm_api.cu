@@ -154,6 +154,8 @@ struct lbm_ctx {
   BoundaryParams bp;
   fem_ctx *fem = nullptr;    // coupled beam (conventional serial staggered loop)
   int fem_v0 = 0;
+  fem_shell_ctx *shell = nullptr;  // coupled plate (3-D)
+  int shell_v0 = 0;
   mlp_ctx *mlp = nullptr;    // structural-step surrogate (Newton initial guess)
   bool traction_on = false;  // stress-traction output each step
   double accept_tol = 0.0;
@@ -432,6 +434,12 @@ lbm_status lbm_step(lbm_ctx *ctx, int n) {
                                    ctx->stream));
       st = run_geometry(ctx, 1);
       if (st != LBM_OK) return st;
+    } else if (ctx->shell) {
+      CK(launch_shell_coupled(ctx->shell, (const double *)(ctx->ws + ctx->lay.vforce),
+                              (double *)(ctx->ws + ctx->lay.sx), (double *)(ctx->ws + ctx->lay.sv),
+                              ctx->shell_v0, ctx->stream));
+      lbm_status st = run_geometry(ctx, 1);
+      if (st != LBM_OK) return st;
     } else if (ctx->fem) {
       // structural step from this step's forces, transfer to the surface, new geometry
       CK(launch_beam_coupled(ctx->fem, (const double *)(ctx->ws + ctx->lay.vforce),
@@ -630,6 +638,28 @@ lbm_status fsi_couple(lbm_ctx *ctx, fem_ctx *f, int first_vertex) {
   if (fem_reset_stats(f) != LBM_OK) return fail(ctx, LBM_ECUDA, "fsi_couple: counter reset failed");
   CK(launch_flag_surface(f, (double *)(ctx->ws + ctx->lay.sx), (double *)(ctx->ws + ctx->lay.sv),
                          first_vertex, ctx->stream));
+  return run_geometry(ctx, 1);
+}
+
+lbm_status fsi_couple_shell(lbm_ctx *ctx, fem_shell_ctx *s, int first_vertex) {
+  GUARD();
+  if (!s) {
+    ctx->shell = nullptr;
+    ctx->graph_dirty = true;
+    return LBM_OK;
+  }
+  if (ctx->Q != 27) return fail(ctx, LBM_EINVAL, "fsi_couple_shell: the shell couples to D3Q27 lattices");
+  if (ctx->nbodies == 0) return fail(ctx, LBM_ESTATE, "fsi_couple_shell: set the geometry first");
+  if (ctx->fem) return fail(ctx, LBM_ESTATE, "fsi_couple_shell: a beam is coupled already");
+  const int nn = shell_nodes(s);
+  if (first_vertex < 0 || first_vertex + 2 * nn > ctx->nv)
+    return fail(ctx, LBM_EINVAL, "fsi_couple_shell: vertices [%d, %d) outside the surface (%d)",
+                first_vertex, first_vertex + 2 * nn, ctx->nv);
+  ctx->shell = s;
+  ctx->shell_v0 = first_vertex;
+  ctx->graph_dirty = true;
+  CK(launch_shell_surface(s, (double *)(ctx->ws + ctx->lay.sx), (double *)(ctx->ws + ctx->lay.sv),
+                          first_vertex, ctx->stream));
   return run_geometry(ctx, 1);
 }
 

@@ -123,5 +123,10 @@ cudaError_t launch_beam_coupled(fem_ctx *f, const double *vforce, double *surf_x
                                 int v0, cudaStream_t s);
 cudaError_t launch_flag_surface(fem_ctx *f, double *surf_x, double *surf_v, int v0,
                                 cudaStream_t s);
+int shell_nodes(const fem_shell_ctx *s);
+cudaError_t launch_shell_surface(fem_shell_ctx *s, double *surf_x, double *surf_v, int v0,
+                                 cudaStream_t st);
+cudaError_t launch_shell_coupled(fem_shell_ctx *s, const double *vforce, double *surf_x,
+                                 double *surf_v, int v0, cudaStream_t st);
 
 }  // namespace kbc

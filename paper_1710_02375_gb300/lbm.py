@@ -222,6 +222,10 @@ def lbm_probe_interface_force_static(ctx, vert_force, body_force):
     _chk(ctx, load().lbm_probe_interface_force_static(ctx, _ptr(vert_force), _ptr(body_force)))
 
 
+def fsi_couple_shell(ctx, shell_ctx, first_vertex):
+    _chk(ctx, load().fsi_couple_shell(ctx, shell_ctx, int(first_vertex)))
+
+
 def fsi_set_surrogate(ctx, mlp_ctx, in_mean, in_std, out_mean, out_std, accept_tol):
     """Attach (mlp_ctx not None) or remove the structural-step surrogate."""
     if mlp_ctx is None:
@@ -499,6 +503,10 @@ class Shell:
         F1 = np.ascontiguousarray(F1, dtype=np.float64).reshape(-1)
         self._chk(load().fem_shell_step(self.ctx, _ptr(F1)))
         self._F1 = F1  # the copy is asynchronous
+
+    def set_state(self, u=None, R=None, v=None, F0=None):
+        arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in (u, R, v, F0)]
+        self._chk(load().fem_shell_set_state(self.ctx, *[_ptr(a) for a in arrs]))
 
     def state(self):
         u = np.zeros((self.nn, 3))

@@ -225,3 +225,77 @@ def c4_instances(n=64, seed=0, n_cyl=48, n_beam=20, u_max=0.05, Ae0=1.4e3):
         out.append(flag_channel(s, Re, Ae=Ae, seed=seed + k, n_cyl=n_cyl, n_beam=n_beam,
                                 u_max=u_max))
     return out
+
+
+def plate_surface(nx, ny):
+    """Closed triangle mesh of a thin plate around an nx x ny node mid-surface
+    grid (node i*ny + j): top vertices 0..nn-1 (vertex n above node n),
+    bottom vertices nn..2nn-1, two triangles per top and bottom quad and per
+    side quad of the rim, all wound with the outward normal for a plate whose
+    mid-surface normal is (i, j) -> x_i cross y_j.  Returns e[ne, 3]."""
+    nn = nx * ny
+
+    def nid(i, j):
+        return i * ny + j
+    tri = []
+    for i in range(nx - 1):
+        for j in range(ny - 1):
+            a, b, c, d = nid(i, j), nid(i + 1, j), nid(i + 1, j + 1), nid(i, j + 1)
+            tri += [(a, b, c), (a, c, d)]                                  # top, normal +n
+            tri += [(nn + a, nn + c, nn + b), (nn + a, nn + d, nn + c)]    # bottom, normal -n
+    rim = ([nid(i, 0) for i in range(nx)] + [nid(nx - 1, j) for j in range(1, ny)] +
+           [nid(i, ny - 1) for i in range(nx - 2, -1, -1)] + [nid(0, j) for j in range(ny - 2, 0, -1)])
+    for k in range(len(rim)):
+        p, q = rim[k], rim[(k + 1) % len(rim)]
+        tri += [(p, nn + p, nn + q), (p, nn + q, q)]
+    return np.array(tri, dtype=np.int32)
+
+
+def plate_case(nxl=256, nyl=128, nzl=128, L=40.0, b=20.0, h=2.0, x0=64.0, u_in=0.04, Re=400.0,
+               K_B=1e-4, nu_s=0.4, density_ratio=None, ex=16, ey=8, perturb=1e-3):
+    """The plate-in-crossflow case: D3Q27 channel nxl x nyl x nzl, inflow
+    u_in along +x (-x face), outlet on +x, periodic in y (span), free stream
+    on the z faces; a plate of length L (x), width b (y), thickness h (z),
+    clamped at its leading edge x = x0, centred in y and z, as an ex x ey
+    element flat shell.  Re = u_in L / nu; bending number
+    K_B = E h^3 / (12 (1 - nu_s^2) rho_f u_in^2 L^3); density ratio L / h
+    unless given.  Initial shape: a tip deflection perturb * L along z with
+    the quadratic profile of a clamped plate, rotations consistent with it.
+    Returns a dict (lattice size, beta, bc, face velocities, shell data,
+    surface mesh, initial u and R)."""
+    nu = u_in * L / Re
+    beta = 1.0 / (6 * nu + 1)
+    E = K_B * 12 * (1 - nu_s ** 2) * u_in ** 2 * L ** 3 / h ** 3
+    rho_s = (L / h) if density_ratio is None else density_ratio
+    nx, ny = ex + 1, ey + 1
+    zc, yc = nzl / 2.0, nyl / 2.0
+    xs = x0 + np.linspace(0.0, L, nx)
+    ys = yc + np.linspace(-b / 2, b / 2, ny)
+    X = np.array([[x, y, zc] for x in xs for y in ys])
+    fixed = np.zeros(6 * nx * ny, np.int32)
+    fixed[: 6 * ny] = 1
+    xi = (X[:, 0] - x0) / L
+    u0 = np.zeros((nx * ny, 3))
+    u0[:, 2] = perturb * L * xi ** 2
+    th_y = -2.0 * perturb * xi          # slope d(u_z)/dx, rotation about y tilts the normal to -x
+    R0 = np.zeros((nx * ny, 3, 3))
+    c, s = np.cos(th_y), np.sin(th_y)
+    R0[:, 0, 0] = c
+    R0[:, 0, 2] = s
+    R0[:, 1, 1] = 1.0
+    R0[:, 2, 0] = -s
+    R0[:, 2, 2] = c
+    face_u = np.zeros((6, 3))
+    face_u[0, 0] = u_in
+    face_u[4, 0] = face_u[5, 0] = u_in
+    return dict(nx=nxl, ny=nyl, nz=nzl, beta=beta, bc=(2, 3, 0, 0, 4, 4), face_u=face_u, u_in=u_in,
+                shell=dict(X=X, nx=nx, ny=ny, E=E, nu=nu_s, h=h, rho=rho_s, fixed=fixed),
+                e=plate_surface(nx, ny), u0=u0, R0=R0, L=L)
+
+
+def plate_vertices(X, u, R, h):
+    """Surface vertices [2 nn, 3] of the plate around the shell state: node
+    position plus / minus h/2 times the rotated reference normal (0, 0, 1)."""
+    d = R[:, :, 2]
+    x = X + u
+    return np.concatenate([x + 0.5 * h * d, x - 0.5 * h * d])

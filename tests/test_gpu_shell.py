@@ -47,3 +47,47 @@ def test_shell_prescribed_loads_matches_oracle():
     print("SHELL iterations (oracle, gpu, cg) first/last:", its[0], its[-1], "worst", worst)
     assert worst < 1e-7, worst
     assert np.max(np.abs(u[:, 2])) > 2.0  # tip deflection of several lattice units
+
+
+def small_plate_case():
+    from paper_1710_02375_gb300 import synth
+    return synth.plate_case(nxl=48, nyl=24, nzl=24, L=16.0, b=8.0, h=2.0, x0=12.0, u_in=0.04,
+                            Re=100.0, ex=8, ey=4, perturb=2e-2)
+
+
+def gpu_plate(c, steps, storage=0, band=6.0):
+    from paper_1710_02375_gb300.cases import plate_coupled
+    L, S = plate_coupled(c, storage=storage, band=band)
+    L.step(steps)
+    L.check()
+    return L, S
+
+
+def test_plate_coupled_small_matches_oracle():
+    """The plate-in-crossflow case at small size (48 x 24 x 24, plate
+    16 x 8 x 2 as 8 x 4 shell elements, Re = 100, an initial tip deflection of
+    2e-2 L): 40 coupled steps of D3Q27 fluid + Grad + forces + shell + geometry
+    against the oracle's CSS loop (fluid velocity 1e-5, shell displacement
+    1e-4 of its largest value, body force 1e-4)."""
+    from oracle import fsi_oracle
+    c = small_plate_case()
+    steps = 40
+    L, S = gpu_plate(c, steps)
+    _, ug = L.macros()
+    _, bf_g = L.interface_force()
+    u_g, R_g, _, _ = S.state()
+    sh = c["shell"]
+    shell = orc.Shell(sh["X"], sh["nx"], sh["ny"], sh["E"], sh["nu"], sh["h"], sh["rho"], sh["fixed"])
+    vel = np.zeros((3, c["nz"], c["ny"], c["nx"]))
+    vel[0] = c["u_in"]
+    css = fsi_oracle.CSSPlate((c["nz"], c["ny"], c["nx"]), c["beta"], c["bc"], c["face_u"], shell, c["e"],
+                              sh["h"], u0=c["u0"], R0=c["R0"], vel0=vel)
+    for _ in range(steps):
+        css.step(atol=1e-13)
+    _, uo = orc.macros(27, css.f)
+    uo[:, css.solid.astype(bool)] = 0
+    err_u = np.max(np.abs(ug - uo)) / np.max(np.abs(uo))
+    err_s = np.max(np.abs(u_g - css.u)) / np.max(np.abs(css.u))
+    err_f = np.linalg.norm(bf_g[0] - css.bforce[0]) / np.linalg.norm(css.bforce[0])
+    print("PLATE small: err_u", err_u, "err_shell", err_s, "err_force", err_f, "tip", css.u[-1])
+    assert err_u <= 1e-5 and err_s <= 1e-4 and err_f <= 1e-4
