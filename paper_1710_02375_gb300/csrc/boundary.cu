@@ -142,6 +142,27 @@ __device__ bool tri_ray(const double *p, const double *d, const double *a, const
   return true;
 }
 
+// Within tol of triangle (a, b, c): distance to its plane <= tol |n| and the
+// in-plane barycentrics in [0, 1].
+__device__ bool on_triangle(const double *p, const double *a, const double *b, const double *c,
+                            double tol) {
+  const double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+  const double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+  const double w[3] = {p[0] - a[0], p[1] - a[1], p[2] - a[2]};
+  const double nr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                        e1[0] * e2[1] - e1[1] * e2[0]};
+  const double nn = sqrt(nr[0] * nr[0] + nr[1] * nr[1] + nr[2] * nr[2]);
+  if (nn == 0.0 || fabs(nr[0] * w[0] + nr[1] * w[1] + nr[2] * w[2]) > tol * nn) return false;
+  const double d11 = e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2];
+  const double d12 = e1[0] * e2[0] + e1[1] * e2[1] + e1[2] * e2[2];
+  const double d22 = e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2];
+  const double dw1 = w[0] * e1[0] + w[1] * e1[1] + w[2] * e1[2];
+  const double dw2 = w[0] * e2[0] + w[1] * e2[1] + w[2] * e2[2];
+  const double den = d11 * d22 - d12 * d12;
+  const double u = (d22 * dw1 - d12 * dw2) / den, v = (d11 * dw2 - d12 * dw1) / den;
+  return u >= 0.0 && v >= 0.0 && u + v <= 1.0;
+}
+
 // Within 1e-12 of an element: a node exactly on a face is solid (the parity
 // test alone would depend on the ray direction there).
 __device__ bool on_surface(const SurfaceDev &s, const double *p) {
@@ -156,23 +177,9 @@ __device__ bool on_surface(const SurfaceDev &s, const double *p) {
       // a zero-length element has no surface
       if (len2 > 0.0 && fabs(cr) <= tol * sqrt(len2) && dt >= 0.0 && dt <= len2) return true;
     } else {
-      const double *a = s.x + 3 * s.e[3 * k], *b = s.x + 3 * s.e[3 * k + 1],
-                   *c = s.x + 3 * s.e[3 * k + 2];
-      const double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
-      const double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
-      const double w[3] = {p[0] - a[0], p[1] - a[1], p[2] - a[2]};
-      const double nr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
-                            e1[0] * e2[1] - e1[1] * e2[0]};
-      const double nn = sqrt(nr[0] * nr[0] + nr[1] * nr[1] + nr[2] * nr[2]);
-      if (nn == 0.0 || fabs(nr[0] * w[0] + nr[1] * w[1] + nr[2] * w[2]) > tol * nn) continue;
-      const double d11 = e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2];
-      const double d12 = e1[0] * e2[0] + e1[1] * e2[1] + e1[2] * e2[2];
-      const double d22 = e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2];
-      const double dw1 = w[0] * e1[0] + w[1] * e1[1] + w[2] * e1[2];
-      const double dw2 = w[0] * e2[0] + w[1] * e2[1] + w[2] * e2[2];
-      const double den = d11 * d22 - d12 * d12;
-      const double u = (d22 * dw1 - d12 * dw2) / den, v = (d11 * dw2 - d12 * dw1) / den;
-      if (u >= 0.0 && v >= 0.0 && u + v <= 1.0) return true;
+      if (on_triangle(p, s.x + 3 * s.e[3 * k], s.x + 3 * s.e[3 * k + 1], s.x + 3 * s.e[3 * k + 2],
+                      tol))
+        return true;
     }
   }
   return false;
@@ -218,17 +225,29 @@ __device__ bool inside_any(const SurfaceDev &s, const double *p) {
 constexpr int kStageSeg = 1024;
 
 struct SegStage {
-  float4 seg[kStageSeg];          // (ax, ay, bx, by) rounded to FP32
+  union {
+    float4 seg[kStageSeg];        // 2-D: (ax, ay, bx, by) rounded to FP32
+    float tri[kStageSeg][9];      // 3-D: (a, b, c) rounded to FP32
+  };
   unsigned char body[kStageSeg];
 };
 
-// Stage the elements of a 2-D surface (all threads of the CTA; the caller
-// synchronises).  Returns false when the surface is 3-D or too large.
+// Stage the elements of the surface (all threads of the CTA; the caller
+// synchronises).  Returns false when the surface is too large.
 __device__ bool stage_segments(const SurfaceDev &s, SegStage &st) {
-  if (s.dim != 2 || s.ne > kStageSeg) return false;
+  if (s.ne > kStageSeg) return false;
   for (int k = threadIdx.x; k < s.ne; k += blockDim.x) {
-    const double *a = s.x + 2 * s.e[2 * k], *b = s.x + 2 * s.e[2 * k + 1];
-    st.seg[k] = make_float4((float)a[0], (float)a[1], (float)b[0], (float)b[1]);
+    if (s.dim == 2) {
+      const double *a = s.x + 2 * s.e[2 * k], *b = s.x + 2 * s.e[2 * k + 1];
+      st.seg[k] = make_float4((float)a[0], (float)a[1], (float)b[0], (float)b[1]);
+    } else {
+      for (int m = 0; m < 3; ++m) {
+        const double *v = s.x + 3 * s.e[3 * k + m];
+        st.tri[k][3 * m] = (float)v[0];
+        st.tri[k][3 * m + 1] = (float)v[1];
+        st.tri[k][3 * m + 2] = (float)v[2];
+      }
+    }
     st.body[k] = (unsigned char)s.eb[k];
   }
   return true;
@@ -265,6 +284,56 @@ __device__ bool inside_any_staged(const SurfaceDev &s, const SegStage &st, const
     const double *a = s.x + 2 * s.e[2 * k], *b = s.x + 2 * s.e[2 * k + 1];
     if ((a[0] < p[0] && b[0] < p[0]) || (a[1] < p[1] && b[1] < p[1])) continue;
     if (seg_ray_cross(p, c_ray2, a, b)) par ^= 1u << st.body[k];
+  }
+  return par != 0;
+}
+
+// Triple product d . ((A - p) x (B - p)) in FP32 and a bound far above its
+// rounding error (the Pluecker side of the ray's line against edge A-B).
+__device__ __forceinline__ float edge_side(const float *A, const float *B, const float *p,
+                                           const float *d, float mag, float &bound) {
+  const float a0 = A[0] - p[0], a1 = A[1] - p[1], a2 = A[2] - p[2];
+  const float b0 = B[0] - p[0], b1 = B[1] - p[1], b2 = B[2] - p[2];
+  const float S = fabsf(a0) + fabsf(a1) + fabsf(a2) + fabsf(b0) + fabsf(b1) + fabsf(b2);
+  bound = 2e-6f * (mag + S) * (1.f + S);
+  return d[0] * (a1 * b2 - a2 * b1) + d[1] * (a2 * b0 - a0 * b2) + d[2] * (a0 * b1 - a1 * b0);
+}
+
+// inside_any for a 3-D surface through the staged filters: a triangle is
+// skipped when the node is off its bounding box (on-surface test), when it
+// lies behind the node on an axis, or when two of its edges put the ray's
+// line on strictly opposite sides (the line misses it).
+__device__ bool inside_any_staged3(const SurfaceDev &s, const SegStage &st, const double *p) {
+  const float pf[3] = {(float)p[0], (float)p[1], (float)p[2]};
+  const float d[3] = {(float)c_ray3[0], (float)c_ray3[1], (float)c_ray3[2]};
+  unsigned par = 0;
+  for (int k = 0; k < s.ne; ++k) {
+    const float *t = st.tri[k];
+    float mag = 1.f + fabsf(pf[0]) + fabsf(pf[1]) + fabsf(pf[2]);
+    for (int q = 0; q < 9; ++q) mag += fabsf(t[q]);
+    const float T = 4e-6f * mag;
+    bool near = true, behind = false;
+    for (int q = 0; q < 3; ++q) {
+      const float lo = fminf(fminf(t[q], t[3 + q]), t[6 + q]);
+      const float hi = fmaxf(fmaxf(t[q], t[3 + q]), t[6 + q]);
+      near = near && pf[q] >= lo - T && pf[q] <= hi + T;
+      behind = behind || hi < pf[q] - T;
+    }
+    const double *a = s.x + 3 * s.e[3 * k], *b = s.x + 3 * s.e[3 * k + 1], *c = s.x + 3 * s.e[3 * k + 2];
+    if (near && on_triangle(p, a, b, c, 1e-12)) return true;
+    if (behind) continue;
+    float b0, b1, b2;
+    const float s0 = edge_side(t, t + 3, pf, d, mag, b0);
+    const float s1 = edge_side(t + 3, t + 6, pf, d, mag, b1);
+    const float s2 = edge_side(t + 6, t, pf, d, mag, b2);
+    const bool pos = s0 > b0 || s1 > b1 || s2 > b2, neg = s0 < -b0 || s1 < -b1 || s2 < -b2;
+    if (pos && neg) continue;
+    if ((a[0] < p[0] && b[0] < p[0] && c[0] < p[0]) || (a[1] < p[1] && b[1] < p[1] && c[1] < p[1]) ||
+        (a[2] < p[2] && b[2] < p[2] && c[2] < p[2]))
+      continue;
+    double tt, u, v;
+    if (tri_ray(p, c_ray3, a, b, c, tt, u, v) && tt > 0.0 && u >= 0.0 && v >= 0.0 && u + v < 1.0)
+      par ^= 1u << st.body[k];
   }
   return par != 0;
 }
@@ -310,6 +379,18 @@ __device__ void link_hit(const SurfaceDev &s, const double *xb, int cx, int cy, 
         bw[0] = 1.0 - tt; bw[1] = tt; bw[2] = 0.0;
       }
     } else {
+      if (st) {
+        const float *t = st->tri[k];
+        float mag = 1.f + fabsf((float)lo[0]) + fabsf((float)lo[1]) + fabsf((float)lo[2]);
+        for (int q = 0; q < 9; ++q) mag += fabsf(t[q]);
+        const float T = 4e-6f * mag;
+        bool off = false;
+        for (int q = 0; q < 3; ++q) {
+          off = off || fmaxf(fmaxf(t[q], t[3 + q]), t[6 + q]) < (float)lo[q] - T ||
+                fminf(fminf(t[q], t[3 + q]), t[6 + q]) > (float)hi[q] + T;
+        }
+        if (off) continue;
+      }
       const double *a = s.x + 3 * s.e[3 * k], *b = s.x + 3 * s.e[3 * k + 1],
                    *c = s.x + 3 * s.e[3 * k + 2];
       bool out = false;
@@ -361,8 +442,9 @@ __device__ __forceinline__ void solid_flags_body(long long t, const Grid &g, con
             z = bd.z0 + (int)(t / ((long long)bx * by));
   const double p[3] = {x + 0.5, y + 0.5, z + 0.5};  // cell-centred node position
   const long long k = sidx(g, x + g.px, y + g.py, z + g.pz);
-  const uint8_t now = (staged ? inside_any_staged(s, st, p) : inside_any(s, p)) ? NODE_SOLID
-                                                                               : NODE_FLUID;
+  const bool in = staged ? (s.dim == 2 ? inside_any_staged(s, st, p) : inside_any_staged3(s, st, p))
+                         : inside_any(s, p);
+  const uint8_t now = in ? NODE_SOLID : NODE_FLUID;
   const uint8_t before = flags[k];
   if (before == NODE_GHOST) return;
   if (track_fresh && before == NODE_SOLID && now == NODE_FLUID) {

@@ -55,7 +55,7 @@ def small_plate_case():
                             Re=100.0, ex=8, ey=4, perturb=2e-2)
 
 
-def gpu_plate(c, steps, storage=0, band=6.0):
+def gpu_plate(c, steps, storage=0, band=4.0):
     from paper_1710_02375_gb300.cases import plate_coupled
     L, S = plate_coupled(c, storage=storage, band=band)
     L.step(steps)
