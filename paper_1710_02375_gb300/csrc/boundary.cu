@@ -339,8 +339,11 @@ __device__ bool inside_any_staged3(const SurfaceDev &s, const SegStage &st, cons
 }
 
 // Nearest crossing of x_b -> x_b - c over all elements; fills the link.
+// With nl = 32 the 32 lanes of a warp (all entering together) split the
+// elements (lane, lane + 32, ...) and the nearest crossing is reduced over
+// the warp (ties: lower element index, as in the serial scan).
 __device__ void link_hit(const SurfaceDev &s, const double *xb, int cx, int cy, int cz, Link &L,
-                         const SegStage *st = nullptr) {
+                         const SegStage *st = nullptr, int lane = 0, int nl = 1) {
   const double eps = 1e-9;
   const double d[3] = {-(double)cx, -(double)cy, -(double)cz};
   int best = -1;
@@ -353,7 +356,7 @@ __device__ void link_hit(const SurfaceDev &s, const double *xb, int cx, int cy, 
     hi[a] = fmax(xb[a], xb[a] + d[a]) + 1e-6;
   }
   const float flo0 = (float)lo[0], fhi0 = (float)hi[0], flo1 = (float)lo[1], fhi1 = (float)hi[1];
-  for (int k = 0; k < s.ne; ++k) {
+  for (int k = lane; k < s.ne; k += nl) {
     if (s.dim == 2) {
       if (st) {
         const float4 q = st->seg[k];
@@ -405,6 +408,18 @@ __device__ void link_hit(const SurfaceDev &s, const double *xb, int cx, int cy, 
         bw[0] = 1.0 - u - v; bw[1] = u; bw[2] = v;
       }
     }
+  }
+  if (nl > 1) {
+    for (int o = 16; o > 0; o >>= 1) {
+      const double obs = __shfl_xor_sync(0xffffffffu, bs, o);
+      const int ob = __shfl_xor_sync(0xffffffffu, best, o);
+      if (ob >= 0 && (best < 0 || obs < bs || (obs == bs && ob < best))) {
+        bs = obs;
+        best = ob;
+      }
+    }
+    const int owner = best >= 0 ? best % nl : 0;
+    for (int q = 0; q < 3; ++q) bw[q] = __shfl_sync(0xffffffffu, bw[q], owner);
   }
   L.uw[0] = L.uw[1] = L.uw[2] = 0.f;
   L.v[0] = L.v[1] = L.v[2] = 0;
@@ -460,19 +475,16 @@ __global__ void k_solid_flags(Grid g, Band bd, SurfaceDev s, uint8_t *flags, int
                    nfresh, cap, track_fresh);
 }
 
-// Immersed boundary nodes of the band and their cut links.
+// Immersed boundary nodes of the band: slots in the node list and ranges in
+// the link list (the links themselves: link_fill_body).
 template <int Q>
 __device__ __forceinline__ void build_links_body(long long t, const Grid &g, const Band &bd,
                                                  const SurfaceDev &s, const uint8_t *flags,
                                                  BNode *bnodes, int *nbn, int bcap, Link *links,
                                                  int *nl, int lcap, int *err) {
   using L = Lat<Q>;
-  __shared__ SegStage st;
   const int bx = bd.x1 - bd.x0, by = bd.y1 - bd.y0, bz = bd.z1 - bd.z0;
   const long long nbnd = (long long)bx * by * bz;
-  if ((long long)(t - threadIdx.x) >= nbnd) return;  // whole CTA past the band
-  const bool staged = stage_segments(s, st);
-  __syncthreads();
   if (t >= nbnd) return;
   const int x = bd.x0 + (int)(t % bx), y = bd.y0 + (int)((t / bx) % by),
             z = bd.z0 + (int)(t / ((long long)bx * by));
@@ -500,16 +512,49 @@ __device__ __forceinline__ void build_links_body(long long t, const Grid &g, con
     bnodes[slot] = BNode{k, -1, 0};
     return;
   }
-  bnodes[slot] = BNode{k, l0, n};
-  const double xb[3] = {x + 0.5, y + 0.5, z + 0.5};
-  int m = 0;
-  for (int i = 0; i < Q; ++i) {
-    if (!(mask & (1u << i))) continue;
-    Link lk;
-    lk.i = i;
-    link_hit(s, xb, L::cx(i), L::cy(i), L::cz(i), lk, staged ? &st : nullptr);
-    links[l0 + m++] = lk;
+  bnodes[slot] = BNode{k, l0, n};  // its links follow in link_fill_body
+}
+
+// Cut links of the listed boundary nodes: one warp per node (grid-stride
+// over the list), the lanes splitting the surface elements of each link.
+template <int Q>
+__device__ __forceinline__ void link_fill_body(const Grid &g, const SurfaceDev &s,
+                                               const uint8_t *flags, const BNode *bnodes,
+                                               const int *nbn, int bcap, Link *links, int warp0,
+                                               int nwarps) {
+  using L = Lat<Q>;
+  __shared__ SegStage st;
+  const bool staged = stage_segments(s, st);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int n = *nbn < bcap ? *nbn : bcap;
+  for (int w = warp0; w < n; w += nwarps) {
+    const BNode b = bnodes[w];
+    if (b.nlink <= 0) continue;
+    int X, Y, Z;
+    decompose(g, b.k, X, Y, Z);
+    const double xb[3] = {X - g.px + 0.5, Y - g.py + 0.5, Z - g.pz + 0.5};
+    int m = 0;
+    for (int i = 0; i < Q; ++i) {
+      const int Xs = nbr(X, -L::cx(i), g.NX), Ys = nbr(Y, -L::cy(i), g.NY),
+                Zs = (L::D == 3) ? nbr(Z, -L::cz(i), g.NZ) : Z;
+      if (flags[sidx(g, Xs, Ys, Zs)] != NODE_SOLID) continue;
+      Link lk;
+      lk.i = i;
+      link_hit(s, xb, L::cx(i), L::cy(i), L::cz(i), lk, staged ? &st : nullptr, lane, 32);
+      if (lane == 0) links[b.link0 + m] = lk;
+      ++m;
+    }
   }
+}
+
+template <int Q>
+__global__ void __launch_bounds__(256) k_link_fill(Grid g, SurfaceDev s, const uint8_t *flags,
+                                                   const BNode *bnodes, const int *nbn, int bcap,
+                                                   Link *links) {
+  link_fill_body<Q>(g, s, flags, bnodes, nbn, bcap, links,
+                    (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5),
+                    (int)((gridDim.x * blockDim.x) >> 5));
 }
 
 template <int Q>
@@ -833,6 +878,29 @@ __global__ void k_step_counter(int *step) { *step += 1; }
 // ---------------------------------------------------------------- launchers
 static inline unsigned nb_(long long n, int b) { return (unsigned)((n + b - 1) / b); }
 
+// Grid of the link-fill pass: four 256-thread CTAs per SM, warps striding
+// over the boundary-node list.
+static unsigned fill_grid() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+      sms = 128;
+  }
+  return 4u * (unsigned)sms;
+}
+
+static cudaError_t launch_link_fill(int Q, const Grid &g, const SurfaceDev &sd, const uint8_t *flags,
+                                    const BNode *bnodes, const int *nbn, int bcap, Link *links,
+                                    cudaStream_t s) {
+  if (Q == 9)
+    k_link_fill<9><<<fill_grid(), 256, 0, s>>>(g, sd, flags, bnodes, nbn, bcap, links);
+  else
+    k_link_fill<27><<<fill_grid(), 256, 0, s>>>(g, sd, flags, bnodes, nbn, bcap, links);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_mark_ghosts(const Grid &g, uint8_t *flags, cudaStream_t s) {
   k_mark_ghosts<<<nb_(g.N, 256), 256, 0, s>>>(g, flags);
   return cudaGetLastError();
@@ -876,7 +944,9 @@ cudaError_t launch_geometry(int Q, int storage, const Grid &g, const Band &bd, c
   else
     k_build_links<27><<<nb_(nb, 128), 128, 0, s>>>(g, bd, sd, flags, bnodes, nbn, bcap, links,
                                                     nl, lcap, err);
-  return cudaGetLastError();
+  cudaError_t e2 = cudaGetLastError();
+  if (e2 != cudaSuccess) return e2;
+  return launch_link_fill(Q, g, sd, flags, bnodes, nbn, bcap, links, s);
 }
 
 cudaError_t launch_grad(int Q, int storage, const Grid &g, void *f, const uint8_t *flags,
@@ -921,7 +991,9 @@ cudaError_t launch_build_links(int Q, const Grid &g, const Band &bd, const Surfa
   else
     k_build_links<27><<<nb_(nb, 128), 128, 0, s>>>(g, bd, sd, flags, bnodes, nbn, bcap, links,
                                                     nl, lcap, err);
-  return cudaGetLastError();
+  cudaError_t e2 = cudaGetLastError();
+  if (e2 != cudaSuccess) return e2;
+  return launch_link_fill(Q, g, sd, flags, bnodes, nbn, bcap, links, s);
 }
 
 // ---------------------------------------------------------------- batched phases
@@ -976,6 +1048,15 @@ __global__ void k_links_batch(const InstDesc *__restrict__ d, const int *__restr
                       b.bnodes + b.nfixed, b.nbn, b.lcap, b.links, b.nl, b.lcap, b.err);
 }
 
+template <int Q>
+__global__ void __launch_bounds__(256) k_link_fill_batch(const InstDesc *__restrict__ d,
+                                                         const int *__restrict__ idx) {
+  const InstDesc &b = d[idx[blockIdx.y]];
+  link_fill_body<Q>(b.g, b.sd, b.flags, b.bnodes + b.nfixed, b.nbn, b.lcap, b.links,
+                    (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5),
+                    (int)((gridDim.x * blockDim.x) >> 5));
+}
+
 cudaError_t launch_batch_pre(const InstDesc *d, int n, int max_nv3, int *ticket, cudaStream_t s) {
   dim3 grid(nb_(max_nv3 > 0 ? max_nv3 : 1, 128), n);
   k_batch_pre<<<grid, 128, 0, s>>>(d, ticket);
@@ -1004,8 +1085,12 @@ cudaError_t launch_geometry_batch(int Q, int storage, const InstDesc *d, const i
   KBC_DISPATCH(Q, storage, {
     k_fresh_batch<QQ, SS><<<gf, 128, 0, s>>>(d, idx, parity);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const dim3 gl(8, n);
     if (QQ == 9) k_links_batch<9><<<gb, 128, 0, s>>>(d, idx);
     else k_links_batch<27><<<gb, 128, 0, s>>>(d, idx);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (QQ == 9) k_link_fill_batch<9><<<gl, 256, 0, s>>>(d, idx);
+    else k_link_fill_batch<27><<<gl, 256, 0, s>>>(d, idx);
     return cudaGetLastError();
   });
 }
