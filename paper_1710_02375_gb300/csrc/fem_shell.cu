@@ -36,7 +36,7 @@ namespace cg = cooperative_groups;
 
 namespace kbc {
 
-constexpr int kShellThreads = 64;
+constexpr int kShellThreads = 128;
 constexpr int kShellMaxNodes = 4096;
 
 struct ShellParams {
@@ -556,15 +556,16 @@ __global__ void __launch_bounds__(kShellThreads) k_shell_step(ShellParams P, She
       D.r[i] = ri;
       D.z[i] = ri / dJ;
       D.p[i] = ri / dJ;
+      D.Ap[i] = 0.0;
       rz0 += ri * ri / dJ;
       rr0 += ri * ri;
     }
     double rz, bnorm2;
     grid_sum2(grid, D.red, slot, rz0, rr0, rz, bnorm2);
     const double stop2 = P.cg_rtol * P.cg_rtol * bnorm2;
+    // (p and the zeroed Ap of each iteration are visible after the barrier
+    // of the reduction above or of the p update below)
     for (int k = 0; k < P.max_cg && bnorm2 > 0.0; ++k) {
-      for (long long i = gt; i < n; i += gs) D.Ap[i] = 0.0;
-      grid.sync();
       for (int e = blockIdx.x; e < P.ne; e += gridDim.x) shell_matvec(P, D, e, D.p, D.Ap, S);
       grid.sync();
       double pap = 0.0;
@@ -596,7 +597,10 @@ __global__ void __launch_bounds__(kShellThreads) k_shell_step(ShellParams P, She
       if (rr <= stop2) break;
       const double beta = rzn / rz;
       rz = rzn;
-      for (long long i = gt; i < n; i += gs) D.p[i] = D.z[i] + beta * D.p[i];
+      for (long long i = gt; i < n; i += gs) {
+        D.p[i] = D.z[i] + beta * D.p[i];
+        D.Ap[i] = 0.0;
+      }
       grid.sync();
     }
     for (long long i = gt; i < n; i += gs) D.dq[i] += P.lambda * D.x[i];
