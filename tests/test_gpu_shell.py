@@ -91,3 +91,38 @@ def test_plate_coupled_small_matches_oracle():
     err_f = np.linalg.norm(bf_g[0] - css.bforce[0]) / np.linalg.norm(css.bforce[0])
     print("PLATE small: err_u", err_u, "err_shell", err_s, "err_force", err_f, "tip", css.u[-1])
     assert err_u <= 1e-5 and err_s <= 1e-4 and err_f <= 1e-4
+
+
+@pytest.mark.slow
+def test_plate_full_size_two_steps_sampled():
+    """The 3-D plate workload at full size (256 x 128 x 128, plate 40 x 20 x 2
+    as 16 x 8 shell elements, the launch configuration of the c3-fsi bench):
+    two coupled steps against the oracle's CSS loop on the same grid; fluid
+    velocity on the nodes within 6 cells of the plate and the shell state."""
+    from oracle import fsi_oracle
+    from paper_1710_02375_gb300 import synth
+    from paper_1710_02375_gb300.cases import plate_coupled
+    c = synth.plate_case()
+    steps = 2
+    L, S = plate_coupled(c)
+    L.step(steps)
+    L.check()
+    _, ug = L.macros()
+    u_g, _, _, _ = S.state()
+    sh = c["shell"]
+    shell = orc.Shell(sh["X"], sh["nx"], sh["ny"], sh["E"], sh["nu"], sh["h"], sh["rho"], sh["fixed"])
+    vel = np.zeros((3, c["nz"], c["ny"], c["nx"]))
+    vel[0] = c["u_in"]
+    css = fsi_oracle.CSSPlate((c["nz"], c["ny"], c["nx"]), c["beta"], c["bc"], c["face_u"], shell, c["e"],
+                              sh["h"], u0=c["u0"], R0=c["R0"], vel0=vel)
+    for _ in range(steps):
+        css.step(atol=1e-13)
+    _, uo = orc.macros(27, css.f)
+    uo[:, css.solid.astype(bool)] = 0
+    win = (slice(58, 71), slice(48, 81), slice(56, 111))  # z, y, x around the plate
+    err_u = np.max(np.abs(ug[(slice(None),) + win] - uo[(slice(None),) + win])) / np.max(np.abs(uo))
+    du = np.max(np.abs(css.u - c["u0"]))
+    err_s = np.max(np.abs(u_g - css.u)) / max(du, 1e-30)
+    print("PLATE full size: err_u", err_u, "shell increment error", err_s)
+    assert err_u <= 1e-5
+    assert err_s <= 1e-3
