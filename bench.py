@@ -66,6 +66,24 @@ def recorded_traffic():
     return float(m_t.group(1))
 
 
+def max_over_ranks(x: float, device="cpu") -> float:
+    """The largest x over the ranks of the default process group (x itself
+    without one): every rank's timed region ends when the slowest ends."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(world: int, nodes: int, steps: int, seconds: float) -> float:
+    """Whole-job MLUPS of `world` independent replicas that each advanced
+    `nodes` nodes `steps` times within `seconds` (the slowest rank's time)."""
+    return world * nodes * steps / seconds / 1e6
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -227,12 +245,10 @@ def run_ours(args):
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
     L.check()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    dev = "cuda" if world > 1 else "cpu"
+    ms = max_over_ranks(ms, dev)
     nodes = N_LATTICE ** 3
-    value = world * nodes * args.steps / (ms * 1e-3) / 1e6
+    value = replica_rate(world, nodes, args.steps, ms * 1e-3)
     per_launch_s = ms * 1e-3 / args.steps
     alg_bytes = 2 * Q * 4 * nodes
     peak, peak_kind = measured_peaks()
@@ -258,7 +274,8 @@ def run_ours(args):
     barrier()
     h2d = (rho.nbytes + u.nbytes) / e2e_steps
     d2h = rho.nbytes + u.nbytes
-    e2e_val = world * nodes * e2e_steps / e2e_s / 1e6
+    e2e_s = max_over_ranks(e2e_s, dev)
+    e2e_val = replica_rate(world, nodes, e2e_steps, e2e_s)
     L.close()
 
     # ---- reduced-precision storage (FP16 / BF16 of f/W - 1) on the same
@@ -275,9 +292,9 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
         Lp.check()
-        ms_p = e0.elapsed_time(e1) / ksteps
+        ms_p = max_over_ranks(e0.elapsed_time(e1) / ksteps, dev)
         Lp.close()
-        v = world * nodes / (ms_p * 1e-3) / 1e6
+        v = replica_rate(world, nodes, 1, ms_p * 1e-3)
         patterns[name] = {"value": v, "unit": UNIT, "ms_per_step": ms_p, "steps": ksteps,
                           "speedup_vs_f32": v / value,
                           "achieved_gbs": 2 * Q * 2 * nodes / (ms_p * 1e-3) / 1e9}
