@@ -59,7 +59,7 @@ struct ShellDev {
   double *u1, *R1;           // current Newton iterate
   double *dq;                // [6 nn] step increments (translations, rotation vectors)
   double *f0, *f, *kd;       // internal force at start / current, diagonal of K
-  double *Ke;                // [ne][576] element tangents, global frame
+  double *eg;                // [ne][kEG] frame data of the current iterate
   double *rhs, *x, *r, *z, *p, *Ap;
   double *red;               // [3][2] reduction slots
   const double *F1;          // [6 nn] loads of the step
@@ -262,45 +262,90 @@ __global__ void __launch_bounds__(kShellThreads) k_shell_setup(ShellParams P, Sh
 }
 
 // ---------------------------------------------------------------- element work
-struct ShellSmem {
-  double xs[12], Rs[36], Re[9], c[3], xb[12], d[24], fl[24], fp[24], w6[6];
-  double U[24][6], V[6][24], KU[24][6], W[6][24];
-  double A[24][24], B[24][24];
+// One warp per element: lanes over the 24 element DOFs, per-warp scratch in
+// shared memory, warp-synchronous.  The tangent is never formed: its product
+// with a vector is T^T P^T K_l P T p, P = I - U V (rank 6), and the frame
+// data it needs (R_e, local positions, frame-spin coefficients) is kept per
+// element from the force evaluation of the current iterate.
+constexpr int kEG = 28;  // per-element geometry: R_e (9), xb (12), spin coefficients (6), pad
+
+struct ShellWarp {
+  double xs[12], Rs[36], Re[9], c[3], xb[12], d[24], fl[24], w6[6], gc[6];
+  double U[24][6], V[6][24];
   int id[4];
 };
 
-// Internal force of element e at (u, R) scattered into fout; with Ke, also
-// the element tangent (global frame) and its diagonal into kd.
-__device__ void shell_element(const ShellParams &P, const ShellDev &D, int e, const double *u,
-                              const double *R, double *fout, double *Ke, double *kd,
-                              ShellSmem &S) {
-  const int t = threadIdx.x, nt = blockDim.x;
-  if (t < 4) {
+// U and V of the projector from the local positions xb and the spin
+// coefficients gc = (a1, a2, b1, b2, N, ap).
+__device__ __forceinline__ void warp_projector(ShellWarp &W, int lane) {
+  for (int w = lane; w < 144; w += 32) {
+    const int i = w / 6, k = w % 6, a = i / 6, s = i % 6;
+    double val = 0.0;
+    if (s < 3) {
+      if (k < 3) {
+        val = (k == s) ? 1.0 : 0.0;
+      } else {
+        // -(xb_a x e_m)_s, m = k - 3
+        const double *xa = W.xb + 3 * a;
+        const int m = k - 3;
+        const double em[3] = {m == 0 ? 1.0 : 0.0, m == 1 ? 1.0 : 0.0, m == 2 ? 1.0 : 0.0};
+        const double cr[3] = {xa[1] * em[2] - xa[2] * em[1], xa[2] * em[0] - xa[0] * em[2],
+                              xa[0] * em[1] - xa[1] * em[0]};
+        val = -cr[s];
+      }
+    } else {
+      val = (k >= 3 && k - 3 == s - 3) ? 1.0 : 0.0;
+    }
+    W.U[i][k] = val;
+  }
+  for (int w = lane; w < 144; w += 32) {
+    const int k = w / 24, j = w % 24, b = j / 6, s = j % 6;
+    const double a1 = W.gc[0], a2 = W.gc[1], b1 = W.gc[2], b2 = W.gc[3], Nn = W.gc[4], ap = W.gc[5];
+    double val = 0.0;
+    if (k < 3) {
+      val = (s == k) ? 0.25 : 0.0;
+    } else {
+      // frame spin: x and y tilts from the diagonals, z from the sides
+      if (k == 3 && s == 2) val = (b == 2 ? -b1 : b == 0 ? b1 : b == 3 ? a1 : -a1) / Nn;
+      if (k == 4 && s == 2) val = (b == 2 ? -b2 : b == 0 ? b2 : b == 3 ? a2 : -a2) / Nn;
+      if (k == 5 && s == 1) val = (b == 1 || b == 2 ? 1.0 : -1.0) / ap;
+    }
+    W.V[k][j] = val;
+  }
+  __syncwarp();
+}
+
+// Internal force of element e at (u, R) scattered into fout; with eg, the
+// element's frame data is stored, with kd the diagonal of T^T K_l T added.
+__device__ void warp_element_force(const ShellParams &P, const ShellDev &D, int e, const double *u,
+                                   const double *R, double *fout, double *eg, double *kd,
+                                   ShellWarp &W, int lane) {
+  if (lane < 4) {
     int id[4];
     elem_ids(P, e, id);
-    S.id[t] = id[t];
+    W.id[lane] = id[lane];
   }
-  __syncthreads();
-  if (t < 12) S.xs[t] = D.X[3 * S.id[t / 3] + t % 3] + u[3 * S.id[t / 3] + t % 3];
-  if (t < 36) S.Rs[t] = R[9 * S.id[t / 9] + t % 9];
-  __syncthreads();
-  if (t == 0) quad_frame_dev(S.xs, S.Re, S.c);
-  __syncthreads();
-  if (t < 12) {
-    const int a = t / 3, k = t % 3;
+  __syncwarp();
+  if (lane < 12) W.xs[lane] = D.X[3 * W.id[lane / 3] + lane % 3] + u[3 * W.id[lane / 3] + lane % 3];
+  for (int w = lane; w < 36; w += 32) W.Rs[w] = R[9 * W.id[w / 9] + w % 9];
+  __syncwarp();
+  if (lane == 0) quad_frame_dev(W.xs, W.Re, W.c);
+  __syncwarp();
+  if (lane < 12) {
+    const int a = lane / 3, k = lane % 3;
     double s = 0.0;
-    for (int q = 0; q < 3; ++q) s += S.Re[3 * q + k] * (S.xs[3 * a + q] - S.c[q]);
-    S.xb[t] = s;
-    S.d[6 * a + k] = s - D.xb0[12 * e + t];
-  } else if (t < 16) {
+    for (int q = 0; q < 3; ++q) s += W.Re[3 * q + k] * (W.xs[3 * a + q] - W.c[q]);
+    W.xb[lane] = s;
+    W.d[6 * a + k] = s - D.xb0[12 * e + lane];
+  } else if (lane < 16) {
     // deformational rotation R_e^T R_a R_e0 of node a
-    const int a = t - 12;
+    const int a = lane - 12;
     const double *R0 = D.Re0 + 9 * e;
     double T1[9], Rd[9];
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j) {
         double s = 0.0;
-        for (int q = 0; q < 3; ++q) s += S.Re[3 * q + i] * S.Rs[9 * a + 3 * q + j];
+        for (int q = 0; q < 3; ++q) s += W.Re[3 * q + i] * W.Rs[9 * a + 3 * q + j];
         T1[3 * i + j] = s;
       }
     for (int i = 0; i < 3; ++i)
@@ -309,149 +354,144 @@ __device__ void shell_element(const ShellParams &P, const ShellDev &D, int e, co
         for (int q = 0; q < 3; ++q) s += T1[3 * i + q] * R0[3 * q + j];
         Rd[3 * i + j] = s;
       }
-    rotvec(Rd, S.d + 6 * a + 3);
+    rotvec(Rd, W.d + 6 * a + 3);
   }
-  __syncthreads();
-  // U (24 x 6) and V (6 x 24) of the projector P = I - U V
-  for (int w = t; w < 144; w += nt) {
-    const int i = w / 6, k = w % 6, a = i / 6, s = i % 6;
-    double val = 0.0;
-    if (s < 3) {
-      if (k < 3) val = (k == s) ? 1.0 : 0.0;
-      else {
-        // -S(xb_a) column (k-3): -(xb_a x e_{k-3})_s
-        const double *xa = S.xb + 3 * a;
-        const int m = k - 3;
-        const double ex[3] = {m == 0 ? 1.0 : 0.0, m == 1 ? 1.0 : 0.0, m == 2 ? 1.0 : 0.0};
-        const double cr[3] = {xa[1] * ex[2] - xa[2] * ex[1], xa[2] * ex[0] - xa[0] * ex[2],
-                              xa[0] * ex[1] - xa[1] * ex[0]};
-        val = -cr[s];
-      }
-    } else {
-      val = (k >= 3 && k - 3 == s - 3) ? 1.0 : 0.0;
-    }
-    S.U[i][k] = val;
+  __syncwarp();
+  if (lane == 0) {
+    W.gc[0] = W.xb[6] - W.xb[0];
+    W.gc[1] = W.xb[7] - W.xb[1];
+    W.gc[2] = W.xb[9] - W.xb[3];
+    W.gc[3] = W.xb[10] - W.xb[4];
+    W.gc[4] = W.gc[0] * W.gc[3] - W.gc[1] * W.gc[2];
+    W.gc[5] = W.xb[3] + W.xb[6] - W.xb[0] - W.xb[9];
   }
-  for (int w = t; w < 144; w += nt) {
-    const int k = w / 24, j = w % 24, b = j / 6, s = j % 6;
-    double val = 0.0;
-    if (k < 3) {
-      val = (s == k) ? 0.25 : 0.0;
-    } else {
-      // spin of the frame: x and y tilts from the diagonals, z from the sides
-      const double a1 = S.xb[6] - S.xb[0], a2 = S.xb[7] - S.xb[1];
-      const double b1 = S.xb[9] - S.xb[3], b2 = S.xb[10] - S.xb[4];
-      const double Nn = a1 * b2 - a2 * b1;
-      const double ap = S.xb[3] + S.xb[6] - S.xb[0] - S.xb[9];
-      if (k == 3 && s == 2) val = (b == 2 ? -b1 : b == 0 ? b1 : b == 3 ? a1 : -a1) / Nn;
-      if (k == 4 && s == 2) val = (b == 2 ? -b2 : b == 0 ? b2 : b == 3 ? a2 : -a2) / Nn;
-      if (k == 5 && s == 1) val = (b == 1 || b == 2 ? 1.0 : -1.0) / ap;
-    }
-    S.V[k][j] = val;
-  }
-  __syncthreads();
+  __syncwarp();
+  warp_projector(W, lane);
   const double *Kl = D.Kl + 576 * (long long)e;
-  if (t < 24) {
+  if (lane < 24) {
     double s = 0.0;
-    for (int j = 0; j < 24; ++j) s += Kl[24 * t + j] * S.d[j];
-    S.fl[t] = s;
+    for (int j = 0; j < 24; ++j) s += Kl[24 * lane + j] * W.d[j];
+    W.fl[lane] = s;
   }
-  __syncthreads();
-  if (t < 6) {
+  __syncwarp();
+  if (lane < 6) {
     double s = 0.0;
-    for (int i = 0; i < 24; ++i) s += S.U[i][t] * S.fl[i];
-    S.w6[t] = s;
+    for (int i = 0; i < 24; ++i) s += W.U[i][lane] * W.fl[i];
+    W.w6[lane] = s;
   }
-  __syncthreads();
-  if (t < 24) {
-    double s = S.fl[t];
-    for (int k = 0; k < 6; ++k) s -= S.V[k][t] * S.w6[k];
-    S.fp[t] = s;
+  __syncwarp();
+  double fp = 0.0;
+  if (lane < 24) {
+    fp = W.fl[lane];
+    for (int k = 0; k < 6; ++k) fp -= W.V[k][lane] * W.w6[k];
   }
-  __syncthreads();
-  if (t < 24) {
-    const int blk = t / 3, k = t % 3, a = blk / 2, kind = blk % 2;
+  __syncwarp();
+  if (lane < 24) W.d[lane] = fp;  // reuse as the projected local force
+  __syncwarp();
+  if (lane < 24) {
+    const int blk = lane / 3, k = lane % 3, a = blk / 2, kind = blk % 2;
     double s = 0.0;
-    for (int q = 0; q < 3; ++q) s += S.Re[3 * k + q] * S.fp[3 * blk + q];
-    atomicAdd(fout + 6 * S.id[a] + 3 * kind + k, s);
-  }
-  if (!Ke) return;
-  // tangent: A = K_l P = K_l - (K_l U) V, B = P^T A = A - V^T (U^T A), then rotate
-  for (int w = t; w < 144; w += nt) {
-    const int i = w / 6, k = w % 6;
-    double s = 0.0;
-    for (int j = 0; j < 24; ++j) s += Kl[24 * i + j] * S.U[j][k];
-    S.KU[i][k] = s;
-  }
-  __syncthreads();
-  for (int w = t; w < 576; w += nt) {
-    const int i = w / 24, j = w % 24;
-    double s = Kl[w];
-    for (int k = 0; k < 6; ++k) s -= S.KU[i][k] * S.V[k][j];
-    S.A[i][j] = s;
-  }
-  __syncthreads();
-  for (int w = t; w < 144; w += nt) {
-    const int k = w / 24, j = w % 24;
-    double s = 0.0;
-    for (int i = 0; i < 24; ++i) s += S.U[i][k] * S.A[i][j];
-    S.W[k][j] = s;
-  }
-  __syncthreads();
-  for (int w = t; w < 576; w += nt) {
-    const int i = w / 24, j = w % 24;
-    double s = S.A[i][j];
-    for (int k = 0; k < 6; ++k) s -= S.V[k][i] * S.W[k][j];
-    S.B[i][j] = s;
-  }
-  __syncthreads();
-  // A = B R^T per 3x3 block column, then Ke = R A per block row
-  for (int w = t; w < 576; w += nt) {
-    const int i = w / 24, j = w % 24, bj = j / 3, jj = j % 3;
-    double s = 0.0;
-    for (int q = 0; q < 3; ++q) s += S.B[i][3 * bj + q] * S.Re[3 * jj + q];
-    S.A[i][j] = s;
-  }
-  __syncthreads();
-  double *Kg = Ke + 576 * (long long)e;
-  for (int w = t; w < 576; w += nt) {
-    const int i = w / 24, j = w % 24, bi = i / 3, ii = i % 3;
-    double s = 0.0;
-    for (int q = 0; q < 3; ++q) s += S.Re[3 * ii + q] * S.A[3 * bi + q][j];
-    Kg[w] = s;
-    if (i == j) {
-      const int a = bi / 2, kind = bi % 2;
-      atomicAdd(kd + 6 * S.id[a] + 3 * kind + ii, s);
+    for (int q = 0; q < 3; ++q) s += W.Re[3 * k + q] * W.d[3 * blk + q];
+    atomicAdd(fout + 6 * W.id[a] + 3 * kind + k, s);
+    if (kd) {
+      // (T^T K_l T)_{ii} for the global DOF (block blk, axis k)
+      double t = 0.0;
+      for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q)
+          t += W.Re[3 * k + p] * Kl[24 * (3 * blk + p) + 3 * blk + q] * W.Re[3 * k + q];
+      atomicAdd(kd + 6 * W.id[a] + 3 * kind + k, t);
     }
   }
-  __syncthreads();
+  if (eg && lane < kEG) {
+    double v = 0.0;
+    if (lane < 9) v = W.Re[lane];
+    else if (lane < 21) v = W.xb[lane - 9];
+    else if (lane < 27) v = W.gc[lane - 21];
+    eg[kEG * (long long)e + lane] = v;
+  }
+  __syncwarp();
 }
 
-// y += theta Ke p for element e (global frame), scattered by atomics.
-__device__ void shell_matvec(const ShellParams &P, const ShellDev &D, int e, const double *p,
-                             double *y, ShellSmem &S) {
-  const int t = threadIdx.x;
-  if (t < 4) {
+// y += theta T^T P^T K_l P T p for element e (frame data from eg).
+__device__ void warp_element_matvec(const ShellParams &P, const ShellDev &D, int e, const double *eg,
+                                    const double *p, double *y, ShellWarp &W, int lane) {
+  if (lane < 4) {
     int id[4];
     elem_ids(P, e, id);
-    S.id[t] = id[t];
+    W.id[lane] = id[lane];
   }
-  __syncthreads();
-  if (t < 24) S.d[t] = p[6 * S.id[t / 6] + t % 6];
-  __syncthreads();
-  if (t < 24) {
-    const double *Kg = D.Ke + 576 * (long long)e + 24 * t;
+  if (lane < kEG) {
+    const double v = eg[kEG * (long long)e + lane];
+    if (lane < 9) W.Re[lane] = v;
+    else if (lane < 21) W.xb[lane - 9] = v;
+    else if (lane < 27) W.gc[lane - 21] = v;
+  }
+  __syncwarp();
+  warp_projector(W, lane);
+  if (lane < 24) {
+    // q = T p: block of three rotated into the element frame
+    const int blk = lane / 3, k = lane % 3, a = blk / 2, kind = blk % 2;
+    const double *pg = p + 6 * W.id[a] + 3 * kind;
+    W.fl[lane] = W.Re[k] * pg[0] + W.Re[3 + k] * pg[1] + W.Re[6 + k] * pg[2];
+  }
+  __syncwarp();
+  if (lane < 6) {
     double s = 0.0;
-    for (int j = 0; j < 24; ++j) s += Kg[j] * S.d[j];
-    atomicAdd(y + 6 * S.id[t / 6] + t % 6, P.theta * s);
+    for (int j = 0; j < 24; ++j) s += W.V[lane][j] * W.fl[j];
+    W.w6[lane] = s;
   }
-  __syncthreads();
+  __syncwarp();
+  if (lane < 24) {
+    double s = W.fl[lane];
+    for (int k = 0; k < 6; ++k) s -= W.U[lane][k] * W.w6[k];
+    W.d[lane] = s;  // P T p
+  }
+  __syncwarp();
+  const double *Kl = D.Kl + 576 * (long long)e;
+  double z = 0.0;
+  if (lane < 24)
+    for (int j = 0; j < 24; ++j) z += Kl[24 * lane + j] * W.d[j];
+  __syncwarp();
+  if (lane < 24) W.fl[lane] = z;
+  __syncwarp();
+  if (lane < 6) {
+    double s = 0.0;
+    for (int i = 0; i < 24; ++i) s += W.U[i][lane] * W.fl[i];
+    W.w6[lane] = s;
+  }
+  __syncwarp();
+  if (lane < 24) {
+    double s = W.fl[lane];
+    for (int k = 0; k < 6; ++k) s -= W.V[k][lane] * W.w6[k];
+    W.d[lane] = s;  // P^T K_l P T p
+  }
+  __syncwarp();
+  if (lane < 24) {
+    const int blk = lane / 3, k = lane % 3, a = blk / 2, kind = blk % 2;
+    double s = 0.0;
+    for (int q = 0; q < 3; ++q) s += W.Re[3 * k + q] * W.d[3 * blk + q];
+    atomicAdd(y + 6 * W.id[a] + 3 * kind + k, P.theta * s);
+  }
+  __syncwarp();
 }
 
-// Grid-wide sums of two values: block reduction, one atomic per block into
-// slot s, grid barrier, read; the slot two ahead is cleared for later use.
-__device__ __forceinline__ void grid_sum2(cg::grid_group &grid, double *red, int &slot, double a,
-                                          double b, double &ra, double &rb) {
+// Barrier over all CTAs of the step: the cooperative grid, or the single
+// thread-block cluster (with a device-scope fence for the global updates).
+template <bool CLUSTER>
+__device__ __forceinline__ void step_sync() {
+  if constexpr (CLUSTER) {
+    __threadfence();
+    cg::this_cluster().sync();
+  } else {
+    cg::this_grid().sync();
+  }
+}
+
+// Sums of two values over all CTAs: block reduction, one atomic per block
+// into slot s, barrier, read; the slot two ahead is cleared for later use.
+template <bool CLUSTER>
+__device__ __forceinline__ void step_sum2(double *red, int &slot, double a, double b, double &ra,
+                                          double &rb) {
   __shared__ double part[2][kShellThreads / 32];
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_xor_sync(0xffffffffu, a, o);
@@ -472,7 +512,7 @@ __device__ __forceinline__ void grid_sum2(cg::grid_group &grid, double *red, int
     atomicAdd(red + 2 * slot, sa);
     atomicAdd(red + 2 * slot + 1, sb);
   }
-  grid.sync();
+  step_sync<CLUSTER>();
   ra = *(volatile double *)(red + 2 * slot);
   rb = *(volatile double *)(red + 2 * slot + 1);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -484,9 +524,12 @@ __device__ __forceinline__ void grid_sum2(cg::grid_group &grid, double *red, int
   __syncthreads();
 }
 
+template <bool CLUSTER>
 __global__ void __launch_bounds__(kShellThreads) k_shell_step(ShellParams P, ShellDev D) {
-  cg::grid_group grid = cg::this_grid();
-  __shared__ ShellSmem S;
+  __shared__ ShellWarp Wsh[kShellThreads / 32];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  ShellWarp &W = Wsh[wl];
+  const int wg = blockIdx.x * (kShellThreads / 32) + wl, nwg = gridDim.x * (kShellThreads / 32);
   const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long gs = (long long)gridDim.x * blockDim.x;
   const int n = P.n, nn = P.nn;
@@ -500,10 +543,10 @@ __global__ void __launch_bounds__(kShellThreads) k_shell_step(ShellParams P, She
   for (long long i = gt; i < 3 * nn; i += gs) D.u0[i] = D.u[i];
   for (long long i = gt; i < 9 * nn; i += gs) D.R0[i] = D.R[i];
   if (gt < 6) D.red[gt] = 0.0;
-  grid.sync();
-  for (int e = blockIdx.x; e < P.ne; e += gridDim.x)
-    shell_element(P, D, e, D.u0, D.R0, D.f0, nullptr, nullptr, S);
-  grid.sync();
+  step_sync<CLUSTER>();
+  for (int e = wg; e < P.ne; e += nwg)
+    warp_element_force(P, D, e, D.u0, D.R0, D.f0, nullptr, nullptr, W, lane);
+  step_sync<CLUSTER>();
   const double ith = 1.0 / P.theta, idt = 1.0 / P.dt, cM = 1.0 / (P.theta * P.dt * P.dt);
   double r0 = -1.0;
   int it = 0, conv = 0, cg_total = 0;
@@ -522,10 +565,10 @@ __global__ void __launch_bounds__(kShellThreads) k_shell_step(ShellParams P, She
       D.f[i] = 0.0;
       D.kd[i] = 0.0;
     }
-    grid.sync();
-    for (int e = blockIdx.x; e < P.ne; e += gridDim.x)
-      shell_element(P, D, e, D.u1, D.R1, D.f, D.Ke, D.kd, S);
-    grid.sync();
+    step_sync<CLUSTER>();
+    for (int e = wg; e < P.ne; e += nwg)
+      warp_element_force(P, D, e, D.u1, D.R1, D.f, D.eg, D.kd, W, lane);
+    step_sync<CLUSTER>();
     double part = 0.0;
     for (long long i = gt; i < n; i += gs) {
       const long long a = i / 6;
@@ -537,7 +580,7 @@ __global__ void __launch_bounds__(kShellThreads) k_shell_step(ShellParams P, She
       D.rhs[i] = -Rv;
       part += Rv * Rv;
     }
-    grid_sum2(grid, D.red, slot, part, 0.0, ra, rb);
+    step_sum2<CLUSTER>(D.red, slot, part, 0.0, ra, rb);
     const double rn = sqrt(ra);
     if (r0 < 0.0) r0 = rn;
     if (rn <= P.rtol * r0 + P.atol) {
@@ -545,7 +588,9 @@ __global__ void __launch_bounds__(kShellThreads) k_shell_step(ShellParams P, She
       break;
     }
     if (it >= P.max_it) break;
-    // preconditioned conjugate gradients on J x = rhs
+    // preconditioned conjugate gradients on J x = rhs (J applied element by
+    // element, never assembled); Jacobi preconditioner from the mass and the
+    // diagonal of T^T K_l T
     double rz0 = 0.0, rr0 = 0.0;
     for (long long i = gt; i < n; i += gs) {
       const long long a = i / 6;
@@ -561,13 +606,13 @@ __global__ void __launch_bounds__(kShellThreads) k_shell_step(ShellParams P, She
       rr0 += ri * ri;
     }
     double rz, bnorm2;
-    grid_sum2(grid, D.red, slot, rz0, rr0, rz, bnorm2);
+    step_sum2<CLUSTER>(D.red, slot, rz0, rr0, rz, bnorm2);
     const double stop2 = P.cg_rtol * P.cg_rtol * bnorm2;
     // (p and the zeroed Ap of each iteration are visible after the barrier
     // of the reduction above or of the p update below)
     for (int k = 0; k < P.max_cg && bnorm2 > 0.0; ++k) {
-      for (int e = blockIdx.x; e < P.ne; e += gridDim.x) shell_matvec(P, D, e, D.p, D.Ap, S);
-      grid.sync();
+      for (int e = wg; e < P.ne; e += nwg) warp_element_matvec(P, D, e, D.eg, D.p, D.Ap, W, lane);
+      step_sync<CLUSTER>();
       double pap = 0.0;
       for (long long i = gt; i < n; i += gs) {
         const long long a = i / 6;
@@ -577,7 +622,7 @@ __global__ void __launch_bounds__(kShellThreads) k_shell_step(ShellParams P, She
         pap += D.p[i] * y;
       }
       double pAp;
-      grid_sum2(grid, D.red, slot, pap, 0.0, pAp, rb);
+      step_sum2<CLUSTER>(D.red, slot, pap, 0.0, pAp, rb);
       const double alpha = rz / pAp;
       double rzp = 0.0, rrp = 0.0;
       for (long long i = gt; i < n; i += gs) {
@@ -592,7 +637,7 @@ __global__ void __launch_bounds__(kShellThreads) k_shell_step(ShellParams P, She
         rrp += ri * ri;
       }
       double rzn, rr;
-      grid_sum2(grid, D.red, slot, rzp, rrp, rzn, rr);
+      step_sum2<CLUSTER>(D.red, slot, rzp, rrp, rzn, rr);
       ++cg_total;
       if (rr <= stop2) break;
       const double beta = rzn / rz;
@@ -601,10 +646,10 @@ __global__ void __launch_bounds__(kShellThreads) k_shell_step(ShellParams P, She
         D.p[i] = D.z[i] + beta * D.p[i];
         D.Ap[i] = 0.0;
       }
-      grid.sync();
+      step_sync<CLUSTER>();
     }
     for (long long i = gt; i < n; i += gs) D.dq[i] += P.lambda * D.x[i];
-    grid.sync();
+    step_sync<CLUSTER>();
   }
   // final state
   for (long long i = gt; i < n; i += gs) {
@@ -665,10 +710,32 @@ struct fem_shell_ctx {
   bool own_ws = false;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  int grid = 0;
+  int grid = 0;      // CTAs of the cooperative launch
+  int cluster = 0;   // CTAs of the single-cluster launch (0: not available)
   bool poisoned = false;
   char msg[256] = {0};
 };
+
+// One structural step: a single cluster when available, else the cooperative grid.
+static cudaError_t launch_shell_step(fem_shell_ctx *s, cudaStream_t st) {
+  if (s->cluster > 0) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3(s->cluster);
+    cfg.blockDim = dim3(kShellThreads);
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = s->cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_shell_step<true>, s->p, s->d);
+  }
+  void *args[] = {(void *)&s->p, (void *)&s->d};
+  return cudaLaunchCooperativeKernel((const void *)k_shell_step<false>, dim3(s->grid),
+                                     dim3(kShellThreads), args, 0, st);
+}
 
 namespace {
 
@@ -695,7 +762,7 @@ size_t shell_layout(int nx, int ny, fem_shell_ctx *s) {
   const size_t ou1 = take(sizeof(double) * 3 * nn), oR1 = take(sizeof(double) * 9 * nn);
   const size_t odq = take(sizeof(double) * n), of0 = take(sizeof(double) * n),
                of = take(sizeof(double) * n), okd = take(sizeof(double) * n);
-  const size_t oKe = take(sizeof(double) * 576 * ne);
+  const size_t oeg = take(sizeof(double) * kEG * ne);
   size_t ovec[6];
   for (int k = 0; k < 6; ++k) ovec[k] = take(sizeof(double) * n);
   const size_t ored = take(sizeof(double) * 6), oF1 = take(sizeof(double) * n),
@@ -713,7 +780,7 @@ size_t shell_layout(int nx, int ny, fem_shell_ctx *s) {
     d.u1 = (double *)(w + ou1); d.R1 = (double *)(w + oR1);
     d.dq = (double *)(w + odq); d.f0 = (double *)(w + of0); d.f = (double *)(w + of);
     d.kd = (double *)(w + okd);
-    d.Ke = (double *)(w + oKe);
+    d.eg = (double *)(w + oeg);
     d.rhs = (double *)(w + ovec[0]); d.x = (double *)(w + ovec[1]); d.r = (double *)(w + ovec[2]);
     d.z = (double *)(w + ovec[3]); d.p = (double *)(w + ovec[4]); d.Ap = (double *)(w + ovec[5]);
     d.red = (double *)(w + ored);
@@ -820,7 +887,7 @@ lbm_status fem_shell_create(const fem_shell_config *c, void *workspace, size_t b
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shell_step, kShellThreads, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shell_step<false>, kShellThreads, 0);
   if (e != cudaSuccess || !coop || per_sm < 1) {
     snprintf(g_shell_msg, sizeof(g_shell_msg), "fem_shell_create: %s",
              e != cudaSuccess ? cudaGetErrorString(e) : "cooperative launch unavailable");
@@ -829,7 +896,34 @@ lbm_status fem_shell_create(const fem_shell_config *c, void *workspace, size_t b
     delete s;
     return LBM_ECUDA;
   }
-  s->grid = p.ne < sms * per_sm ? p.ne : sms * per_sm;
+  const int warps = kShellThreads / 32;
+  s->grid = (p.ne + warps - 1) / warps;
+  if (s->grid > sms * per_sm) s->grid = sms * per_sm;
+  // one thread-block cluster of up to 16 CTAs when the device can hold it
+  // (hardware cluster barriers instead of grid-wide ones)
+  int want = (p.ne + warps - 1) / warps;
+  if (want > 16) want = 16;
+  if (want > 8 &&
+      cudaFuncSetAttribute(k_shell_step<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    want = 8;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  cfg.gridDim = dim3(want);
+  cfg.blockDim = dim3(kShellThreads);
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = want;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, k_shell_step<true>, &cfg) == cudaSuccess &&
+      nclusters >= 1)
+    s->cluster = want;
+  cudaGetLastError();
   *out = s;
   return LBM_OK;
 }
@@ -838,9 +932,7 @@ lbm_status fem_shell_step(fem_shell_ctx *s, const double *F1) {
   if (!s || !F1) return LBM_EINVAL;
   if (s->poisoned) return LBM_ESTATE;
   SHELL_CK(cudaMemcpyAsync(s->F1, F1, sizeof(double) * s->p.n, cudaMemcpyDefault, s->stream));
-  void *args[] = {(void *)&s->p, (void *)&s->d};
-  SHELL_CK(cudaLaunchCooperativeKernel((const void *)k_shell_step, dim3(s->grid), dim3(kShellThreads),
-                                       args, 0, s->stream));
+  SHELL_CK(launch_shell_step(s, s->stream));
   return LBM_OK;
 }
 
@@ -898,9 +990,7 @@ cudaError_t launch_shell_coupled(fem_shell_ctx *s, const double *vforce, double 
   k_shell_loads<<<(s->p.nn + 127) / 128, 128, 0, st>>>(s->p, s->F1, vforce, v0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  void *args[] = {(void *)&s->p, (void *)&s->d};
-  e = cudaLaunchCooperativeKernel((const void *)k_shell_step, dim3(s->grid), dim3(kShellThreads), args,
-                                  0, st);
+  e = launch_shell_step(s, st);
   if (e != cudaSuccess) return e;
   return launch_shell_surface(s, surf_x, surf_v, v0, st);
 }
