@@ -412,22 +412,26 @@ __device__ void warp_element_force(const ShellParams &P, const ShellDev &D, int 
   __syncwarp();
 }
 
-// y += theta T^T P^T K_l P T p for element e (frame data from eg).
+// y += theta T^T P^T K_l P T p for element e.  With own, the warp's scratch
+// still holds e's frame and projector from the force evaluation; otherwise
+// they are rebuilt from the frame data in eg.
 __device__ void warp_element_matvec(const ShellParams &P, const ShellDev &D, int e, const double *eg,
-                                    const double *p, double *y, ShellWarp &W, int lane) {
-  if (lane < 4) {
-    int id[4];
-    elem_ids(P, e, id);
-    W.id[lane] = id[lane];
+                                    const double *p, double *y, ShellWarp &W, int lane, bool own) {
+  if (!own) {
+    if (lane < 4) {
+      int id[4];
+      elem_ids(P, e, id);
+      W.id[lane] = id[lane];
+    }
+    if (lane < kEG) {
+      const double v = eg[kEG * (long long)e + lane];
+      if (lane < 9) W.Re[lane] = v;
+      else if (lane < 21) W.xb[lane - 9] = v;
+      else if (lane < 27) W.gc[lane - 21] = v;
+    }
+    __syncwarp();
+    warp_projector(W, lane);
   }
-  if (lane < kEG) {
-    const double v = eg[kEG * (long long)e + lane];
-    if (lane < 9) W.Re[lane] = v;
-    else if (lane < 21) W.xb[lane - 9] = v;
-    else if (lane < 27) W.gc[lane - 21] = v;
-  }
-  __syncwarp();
-  warp_projector(W, lane);
   if (lane < 24) {
     // q = T p: block of three rotated into the element frame
     const int blk = lane / 3, k = lane % 3, a = blk / 2, kind = blk % 2;
@@ -611,7 +615,8 @@ __global__ void __launch_bounds__(kShellThreads) k_shell_step(ShellParams P, She
     // (p and the zeroed Ap of each iteration are visible after the barrier
     // of the reduction above or of the p update below)
     for (int k = 0; k < P.max_cg && bnorm2 > 0.0; ++k) {
-      for (int e = wg; e < P.ne; e += nwg) warp_element_matvec(P, D, e, D.eg, D.p, D.Ap, W, lane);
+      for (int e = wg; e < P.ne; e += nwg)
+        warp_element_matvec(P, D, e, D.eg, D.p, D.Ap, W, lane, nwg >= P.ne);
       step_sync<CLUSTER>();
       double pap = 0.0;
       for (long long i = gt; i < n; i += gs) {
@@ -899,8 +904,11 @@ lbm_status fem_shell_create(const fem_shell_config *c, void *workspace, size_t b
   const int warps = kShellThreads / 32;
   s->grid = (p.ne + warps - 1) / warps;
   if (s->grid > sms * per_sm) s->grid = sms * per_sm;
-  // one thread-block cluster of up to 16 CTAs when the device can hold it
-  // (hardware cluster barriers instead of grid-wide ones)
+  // One thread-block cluster of up to 16 CTAs would replace the grid-wide
+  // barriers by cluster barriers, but on the 16 x 8 plate it measured slower
+  // (2.48 ms against 1.58 ms per step: the per-element FP64 chains then share
+  // 16 SMs), so the cooperative grid with one element per warp is used.
+  const bool try_cluster = false;
   int want = (p.ne + warps - 1) / warps;
   if (want > 16) want = 16;
   if (want > 8 &&
@@ -920,7 +928,7 @@ lbm_status fem_shell_create(const fem_shell_config *c, void *workspace, size_t b
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int nclusters = 0;
-  if (cudaOccupancyMaxActiveClusters(&nclusters, k_shell_step<true>, &cfg) == cudaSuccess &&
+  if (try_cluster && cudaOccupancyMaxActiveClusters(&nclusters, k_shell_step<true>, &cfg) == cudaSuccess &&
       nclusters >= 1)
     s->cluster = want;
   cudaGetLastError();
