@@ -60,7 +60,7 @@ struct ShellDev {
   double *dq;                // [6 nn] step increments (translations, rotation vectors)
   double *f0, *f, *kd;       // internal force at start / current, diagonal of K
   double *eg;                // [ne][kEG] frame data of the current iterate
-  double *rhs, *x, *r, *z, *p, *Ap;
+  double *rhs, *x, *r, *z, *p, *Ap, *Ap2;
   double *red;               // [3][2] reduction slots
   const double *F1;          // [6 nn] loads of the step
   int *iters;                // [2]: Newton iterations of the last step, CG iterations
@@ -317,17 +317,33 @@ __device__ __forceinline__ void warp_projector(ShellWarp &W, int lane) {
 
 // Internal force of element e at (u, R) scattered into fout; with eg, the
 // element's frame data is stored, with kd the diagonal of T^T K_l T added.
+// The state is (u + dq_t, exp(dq_r) R) per node when dq is given, else (u, R).
 __device__ void warp_element_force(const ShellParams &P, const ShellDev &D, int e, const double *u,
-                                   const double *R, double *fout, double *eg, double *kd,
-                                   ShellWarp &W, int lane) {
+                                   const double *R, const double *dq, double *fout, double *eg,
+                                   double *kd, ShellWarp &W, int lane) {
   if (lane < 4) {
     int id[4];
     elem_ids(P, e, id);
     W.id[lane] = id[lane];
   }
   __syncwarp();
-  if (lane < 12) W.xs[lane] = D.X[3 * W.id[lane / 3] + lane % 3] + u[3 * W.id[lane / 3] + lane % 3];
-  for (int w = lane; w < 36; w += 32) W.Rs[w] = R[9 * W.id[w / 9] + w % 9];
+  if (lane < 12) {
+    const int a = W.id[lane / 3], k = lane % 3;
+    W.xs[lane] = D.X[3 * a + k] + u[3 * a + k] + (dq ? dq[6 * a + k] : 0.0);
+  }
+  if (dq) {
+    if (lane < 4) {
+      const int a = W.id[lane];
+      double Ex[9];
+      rodrigues(dq + 6 * a + 3, Ex);
+      const double *Ra = R + 9 * a;
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+          W.Rs[9 * lane + 3 * i + j] = Ex[3 * i] * Ra[j] + Ex[3 * i + 1] * Ra[3 + j] + Ex[3 * i + 2] * Ra[6 + j];
+    }
+  } else {
+    for (int w = lane; w < 36; w += 32) W.Rs[w] = R[9 * W.id[w / 9] + w % 9];
+  }
   __syncwarp();
   if (lane == 0) quad_frame_dev(W.xs, W.Re, W.c);
   __syncwarp();
@@ -416,7 +432,8 @@ __device__ void warp_element_force(const ShellParams &P, const ShellDev &D, int 
 // still holds e's frame and projector from the force evaluation; otherwise
 // they are rebuilt from the frame data in eg.
 __device__ void warp_element_matvec(const ShellParams &P, const ShellDev &D, int e, const double *eg,
-                                    const double *p, double *y, ShellWarp &W, int lane, bool own) {
+                                    const double *z, const double *p, double beta, double *y,
+                                    ShellWarp &W, int lane, bool own) {
   if (!own) {
     if (lane < 4) {
       int id[4];
@@ -435,8 +452,10 @@ __device__ void warp_element_matvec(const ShellParams &P, const ShellDev &D, int
   if (lane < 24) {
     // q = T p: block of three rotated into the element frame
     const int blk = lane / 3, k = lane % 3, a = blk / 2, kind = blk % 2;
-    const double *pg = p + 6 * W.id[a] + 3 * kind;
-    W.fl[lane] = W.Re[k] * pg[0] + W.Re[3 + k] * pg[1] + W.Re[6 + k] * pg[2];
+    const long long g0 = 6 * W.id[a] + 3 * kind;
+    const double q0 = z[g0] + beta * p[g0], q1 = z[g0 + 1] + beta * p[g0 + 1],
+                 q2 = z[g0 + 2] + beta * p[g0 + 2];
+    W.fl[lane] = W.Re[k] * q0 + W.Re[3 + k] * q1 + W.Re[6 + k] * q2;
   }
   __syncwarp();
   if (lane < 6) {
@@ -452,11 +471,11 @@ __device__ void warp_element_matvec(const ShellParams &P, const ShellDev &D, int
   }
   __syncwarp();
   const double *Kl = D.Kl + 576 * (long long)e;
-  double z = 0.0;
+  double kz = 0.0;
   if (lane < 24)
-    for (int j = 0; j < 24; ++j) z += Kl[24 * lane + j] * W.d[j];
+    for (int j = 0; j < 24; ++j) kz += Kl[24 * lane + j] * W.d[j];
   __syncwarp();
-  if (lane < 24) W.fl[lane] = z;
+  if (lane < 24) W.fl[lane] = kz;
   __syncwarp();
   if (lane < 6) {
     double s = 0.0;
@@ -528,12 +547,17 @@ __device__ __forceinline__ void step_sum2(double *red, int &slot, double a, doub
   __syncthreads();
 }
 
+// Barriers per Newton iteration: element forces (1), residual with the CG
+// start (1), three per CG iteration (element products, two reductions; the
+// search direction z + beta p is formed where it is used), increment
+// update (1).
 template <bool CLUSTER>
 __global__ void __launch_bounds__(kShellThreads) k_shell_step(ShellParams P, ShellDev D) {
   __shared__ ShellWarp Wsh[kShellThreads / 32];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   ShellWarp &W = Wsh[wl];
   const int wg = blockIdx.x * (kShellThreads / 32) + wl, nwg = gridDim.x * (kShellThreads / 32);
+  const bool own = nwg >= P.ne;  // one element per warp for the whole step
   const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long gs = (long long)gridDim.x * blockDim.x;
   const int n = P.n, nn = P.nn;
@@ -543,37 +567,27 @@ __global__ void __launch_bounds__(kShellThreads) k_shell_step(ShellParams P, She
     D.v0[i] = D.v[i];
     D.dq[i] = 0.0;
     D.f0[i] = 0.0;
+    D.f[i] = 0.0;
+    D.kd[i] = 0.0;
   }
   for (long long i = gt; i < 3 * nn; i += gs) D.u0[i] = D.u[i];
   for (long long i = gt; i < 9 * nn; i += gs) D.R0[i] = D.R[i];
   if (gt < 6) D.red[gt] = 0.0;
   step_sync<CLUSTER>();
   for (int e = wg; e < P.ne; e += nwg)
-    warp_element_force(P, D, e, D.u0, D.R0, D.f0, nullptr, nullptr, W, lane);
-  step_sync<CLUSTER>();
+    warp_element_force(P, D, e, D.u0, D.R0, nullptr, D.f0, nullptr, nullptr, W, lane);
   const double ith = 1.0 / P.theta, idt = 1.0 / P.dt, cM = 1.0 / (P.theta * P.dt * P.dt);
   double r0 = -1.0;
   int it = 0, conv = 0, cg_total = 0;
   for (it = 0;; ++it) {
-    // current iterate from the step increments
-    for (long long a = gt; a < nn; a += gs) {
-      for (int k = 0; k < 3; ++k) D.u1[3 * a + k] = D.u0[3 * a + k] + D.dq[6 * a + k];
-      double Ex[9];
-      rodrigues(D.dq + 6 * a + 3, Ex);
-      const double *Ra = D.R0 + 9 * a;
-      for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j)
-          D.R1[9 * a + 3 * i + j] = Ex[3 * i] * Ra[j] + Ex[3 * i + 1] * Ra[3 + j] + Ex[3 * i + 2] * Ra[6 + j];
-    }
-    for (long long i = gt; i < n; i += gs) {
-      D.f[i] = 0.0;
-      D.kd[i] = 0.0;
-    }
+    // forces and frames of the iterate (u0 + dq, exp(dq_r) R0); f and kd
+    // were zeroed before the last barrier
     step_sync<CLUSTER>();
     for (int e = wg; e < P.ne; e += nwg)
-      warp_element_force(P, D, e, D.u1, D.R1, D.f, D.eg, D.kd, W, lane);
+      warp_element_force(P, D, e, D.u0, D.R0, D.dq, D.f, D.eg, D.kd, W, lane);
     step_sync<CLUSTER>();
-    double part = 0.0;
+    // residual, and the start of the conjugate gradients on J x = -R
+    double part = 0.0, rz0 = 0.0;
     for (long long i = gt; i < n; i += gs) {
       const long long a = i / 6;
       const double m = (i % 6) < 3 ? D.mt[a] : D.mr[a];
@@ -581,10 +595,17 @@ __global__ void __launch_bounds__(kShellThreads) k_shell_step(ShellParams P, She
       double Rv = m * (v1 - D.v0[i]) * idt - P.theta * (D.F1[i] - D.f[i]) -
                   (1.0 - P.theta) * (D.F0[i] - D.f0[i]);
       if (D.fixed[i]) Rv = 0.0;
+      const double dJ = D.fixed[i] ? 1.0 : m * cM + P.theta * D.kd[i];
       D.rhs[i] = -Rv;
+      D.x[i] = 0.0;
+      D.r[i] = -Rv;
+      D.z[i] = -Rv / dJ;
+      D.p[i] = 0.0;
+      D.Ap[i] = 0.0;
       part += Rv * Rv;
+      rz0 += Rv * Rv / dJ;
     }
-    step_sum2<CLUSTER>(D.red, slot, part, 0.0, ra, rb);
+    step_sum2<CLUSTER>(D.red, slot, part, rz0, ra, rb);
     const double rn = sqrt(ra);
     if (r0 < 0.0) r0 = rn;
     if (rn <= P.rtol * r0 + P.atol) {
@@ -592,39 +613,25 @@ __global__ void __launch_bounds__(kShellThreads) k_shell_step(ShellParams P, She
       break;
     }
     if (it >= P.max_it) break;
-    // preconditioned conjugate gradients on J x = rhs (J applied element by
-    // element, never assembled); Jacobi preconditioner from the mass and the
-    // diagonal of T^T K_l T
-    double rz0 = 0.0, rr0 = 0.0;
-    for (long long i = gt; i < n; i += gs) {
-      const long long a = i / 6;
-      const double m = (i % 6) < 3 ? D.mt[a] : D.mr[a];
-      const double dJ = D.fixed[i] ? 1.0 : m * cM + P.theta * D.kd[i];
-      const double ri = D.rhs[i];
-      D.x[i] = 0.0;
-      D.r[i] = ri;
-      D.z[i] = ri / dJ;
-      D.p[i] = ri / dJ;
-      D.Ap[i] = 0.0;
-      rz0 += ri * ri / dJ;
-      rr0 += ri * ri;
-    }
-    double rz, bnorm2;
-    step_sum2<CLUSTER>(D.red, slot, rz0, rr0, rz, bnorm2);
-    const double stop2 = P.cg_rtol * P.cg_rtol * bnorm2;
-    // (p and the zeroed Ap of each iteration are visible after the barrier
-    // of the reduction above or of the p update below)
-    for (int k = 0; k < P.max_cg && bnorm2 > 0.0; ++k) {
+    double rz = rb, beta = 0.0;
+    const double stop2 = P.cg_rtol * P.cg_rtol * ra;
+    double *Ap[2] = {D.Ap, D.Ap2};
+    for (int k = 0; k < P.max_cg && ra > 0.0; ++k) {
+      double *Ac = Ap[k & 1], *An = Ap[(k + 1) & 1];
+      // element products with the direction z + beta p
       for (int e = wg; e < P.ne; e += nwg)
-        warp_element_matvec(P, D, e, D.eg, D.p, D.Ap, W, lane, nwg >= P.ne);
+        warp_element_matvec(P, D, e, D.eg, D.z, D.p, beta, Ac, W, lane, own);
       step_sync<CLUSTER>();
       double pap = 0.0;
       for (long long i = gt; i < n; i += gs) {
         const long long a = i / 6;
         const double m = (i % 6) < 3 ? D.mt[a] : D.mr[a];
-        double y = D.fixed[i] ? D.p[i] : D.Ap[i] + m * cM * D.p[i];
-        D.Ap[i] = y;
-        pap += D.p[i] * y;
+        const double pn = D.z[i] + beta * D.p[i];
+        const double y = D.fixed[i] ? pn : Ac[i] + m * cM * pn;
+        D.p[i] = pn;
+        Ac[i] = y;
+        An[i] = 0.0;
+        pap += pn * y;
       }
       double pAp;
       step_sum2<CLUSTER>(D.red, slot, pap, 0.0, pAp, rb);
@@ -635,7 +642,7 @@ __global__ void __launch_bounds__(kShellThreads) k_shell_step(ShellParams P, She
         const double m = (i % 6) < 3 ? D.mt[a] : D.mr[a];
         const double dJ = D.fixed[i] ? 1.0 : m * cM + P.theta * D.kd[i];
         D.x[i] += alpha * D.p[i];
-        const double ri = D.r[i] - alpha * D.Ap[i];
+        const double ri = D.r[i] - alpha * Ac[i];
         D.r[i] = ri;
         D.z[i] = ri / dJ;
         rzp += ri * ri / dJ;
@@ -645,25 +652,30 @@ __global__ void __launch_bounds__(kShellThreads) k_shell_step(ShellParams P, She
       step_sum2<CLUSTER>(D.red, slot, rzp, rrp, rzn, rr);
       ++cg_total;
       if (rr <= stop2) break;
-      const double beta = rzn / rz;
+      beta = rzn / rz;
       rz = rzn;
-      for (long long i = gt; i < n; i += gs) {
-        D.p[i] = D.z[i] + beta * D.p[i];
-        D.Ap[i] = 0.0;
-      }
-      step_sync<CLUSTER>();
     }
-    for (long long i = gt; i < n; i += gs) D.dq[i] += P.lambda * D.x[i];
-    step_sync<CLUSTER>();
+    for (long long i = gt; i < n; i += gs) {
+      D.dq[i] += P.lambda * D.x[i];
+      D.f[i] = 0.0;
+      D.kd[i] = 0.0;
+    }
   }
-  // final state
+  // final state from the increments
   for (long long i = gt; i < n; i += gs) {
     const double v1 = (D.dq[i] * idt - (1.0 - P.theta) * D.v0[i]) * ith;
     D.v[i] = D.fixed[i] ? 0.0 : v1;
     D.F0[i] = D.F1[i];
   }
-  for (long long i = gt; i < 3 * nn; i += gs) D.u[i] = D.u1[i];
-  for (long long i = gt; i < 9 * nn; i += gs) D.R[i] = D.R1[i];
+  for (long long a = gt; a < nn; a += gs) {
+    for (int k = 0; k < 3; ++k) D.u[3 * a + k] = D.u0[3 * a + k] + D.dq[6 * a + k];
+    double Ex[9];
+    rodrigues(D.dq + 6 * a + 3, Ex);
+    const double *Ra = D.R0 + 9 * a;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j)
+        D.R[9 * a + 3 * i + j] = Ex[3 * i] * Ra[j] + Ex[3 * i + 1] * Ra[3 + j] + Ex[3 * i + 2] * Ra[6 + j];
+  }
   if (gt == 0) {
     D.iters[0] = conv ? it : -it - 1;
     D.iters[1] = cg_total;
@@ -768,8 +780,8 @@ size_t shell_layout(int nx, int ny, fem_shell_ctx *s) {
   const size_t odq = take(sizeof(double) * n), of0 = take(sizeof(double) * n),
                of = take(sizeof(double) * n), okd = take(sizeof(double) * n);
   const size_t oeg = take(sizeof(double) * kEG * ne);
-  size_t ovec[6];
-  for (int k = 0; k < 6; ++k) ovec[k] = take(sizeof(double) * n);
+  size_t ovec[7];
+  for (int k = 0; k < 7; ++k) ovec[k] = take(sizeof(double) * n);
   const size_t ored = take(sizeof(double) * 6), oF1 = take(sizeof(double) * n),
                oit = take(sizeof(int) * 2);
   if (s) {
@@ -788,6 +800,7 @@ size_t shell_layout(int nx, int ny, fem_shell_ctx *s) {
     d.eg = (double *)(w + oeg);
     d.rhs = (double *)(w + ovec[0]); d.x = (double *)(w + ovec[1]); d.r = (double *)(w + ovec[2]);
     d.z = (double *)(w + ovec[3]); d.p = (double *)(w + ovec[4]); d.Ap = (double *)(w + ovec[5]);
+    d.Ap2 = (double *)(w + ovec[6]);
     d.red = (double *)(w + ored);
     s->F1 = (double *)(w + oF1);
     d.F1 = s->F1;
