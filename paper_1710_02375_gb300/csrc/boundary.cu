@@ -230,27 +230,66 @@ struct SegStage {
     float tri[kStageSeg][9];      // 3-D: (a, b, c) rounded to FP32
   };
   unsigned char body[kStageSeg];
+  float wbox[8][6];  // per-warp bounding boxes of the staged vertices (lo xyz, hi xyz)
 };
 
-// Stage the elements of the surface (all threads of the CTA; the caller
-// synchronises).  Returns false when the surface is too large.
+// Stage the elements of the surface (all threads of the CTA, at most 256;
+// the caller synchronises).  Returns false when the surface is too large.
 __device__ bool stage_segments(const SurfaceDev &s, SegStage &st) {
   if (s.ne > kStageSeg) return false;
+  float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
   for (int k = threadIdx.x; k < s.ne; k += blockDim.x) {
     if (s.dim == 2) {
       const double *a = s.x + 2 * s.e[2 * k], *b = s.x + 2 * s.e[2 * k + 1];
       st.seg[k] = make_float4((float)a[0], (float)a[1], (float)b[0], (float)b[1]);
+      for (int q = 0; q < 2; ++q) {
+        lo[q] = fminf(lo[q], fminf((float)a[q], (float)b[q]));
+        hi[q] = fmaxf(hi[q], fmaxf((float)a[q], (float)b[q]));
+      }
+      lo[2] = hi[2] = 0.5f;
     } else {
       for (int m = 0; m < 3; ++m) {
         const double *v = s.x + 3 * s.e[3 * k + m];
-        st.tri[k][3 * m] = (float)v[0];
-        st.tri[k][3 * m + 1] = (float)v[1];
-        st.tri[k][3 * m + 2] = (float)v[2];
+        for (int q = 0; q < 3; ++q) {
+          const float c = (float)v[q];
+          st.tri[k][3 * m + q] = c;
+          lo[q] = fminf(lo[q], c);
+          hi[q] = fmaxf(hi[q], c);
+        }
       }
     }
     st.body[k] = (unsigned char)s.eb[k];
   }
+  for (int q = 0; q < 3; ++q)
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[q] = fminf(lo[q], __shfl_xor_sync(0xffffffffu, lo[q], o));
+      hi[q] = fmaxf(hi[q], __shfl_xor_sync(0xffffffffu, hi[q], o));
+    }
+  if ((threadIdx.x & 31) == 0 && (threadIdx.x >> 5) < 8)
+    for (int q = 0; q < 3; ++q) {
+      st.wbox[threadIdx.x >> 5][q] = lo[q];
+      st.wbox[threadIdx.x >> 5][3 + q] = hi[q];
+    }
   return true;
+}
+
+// Whether node p lies outside the staged surface's bounding box by a margin
+// far above the FP32 rounding of the vertices: then it is neither inside a
+// body nor on the surface.
+__device__ __forceinline__ bool outside_staged_box(const SegStage &st, const double *p, int dim) {
+  const int nw = min((int)(blockDim.x >> 5), 8);
+  for (int q = 0; q < dim; ++q) {
+    float lo = 3e38f, hi = -3e38f;
+    for (int w = 0; w < nw; ++w) {
+      lo = fminf(lo, st.wbox[w][q]);
+      hi = fmaxf(hi, st.wbox[w][3 + q]);
+    }
+    const float pq = (float)p[q];
+    if (pq < lo - 1e-5f * (1.f + fabsf(pq) + fabsf(lo)) ||
+        pq > hi + 1e-5f * (1.f + fabsf(pq) + fabsf(hi)))
+      return true;
+  }
+  return false;
 }
 
 __device__ __forceinline__ float seg_margin(const float4 &q, float px, float py) {
@@ -338,89 +377,71 @@ __device__ bool inside_any_staged3(const SurfaceDev &s, const SegStage &st, cons
   return par != 0;
 }
 
-// Nearest crossing of x_b -> x_b - c over all elements; fills the link.
-// With nl = 32 the 32 lanes of a warp (all entering together) split the
-// elements (lane, lane + 32, ...) and the nearest crossing is reduced over
-// the warp (ties: lower element index, as in the serial scan).
-__device__ void link_hit(const SurfaceDev &s, const double *xb, int cx, int cy, int cz, Link &L,
-                         const SegStage *st = nullptr, int lane = 0, int nl = 1) {
-  const double eps = 1e-9;
-  const double d[3] = {-(double)cx, -(double)cy, -(double)cz};
-  int best = -1;
-  double bs = 2.0, bw[3] = {0, 0, 0};
-  // bounding box of the link (with the crossing tolerance): elements outside
-  // it cannot be hit
-  double lo[3], hi[3];
+// ---- cut links.  The link from x_b along -c_i has the box [lo, hi] (with
+// the crossing tolerance); link_may_hit is the exact FP32 prefilter of an
+// element against it, link_crossing the FP64 test (parameter sp in
+// (eps, 1 + eps] along the link, barycentric weights bw), link_finish fills
+// the Link from the nearest crossing.
+__device__ __forceinline__ void link_box(const double *xb, const double *d, double *lo, double *hi) {
   for (int a = 0; a < 3; ++a) {
     lo[a] = fmin(xb[a], xb[a] + d[a]) - 1e-6;
     hi[a] = fmax(xb[a], xb[a] + d[a]) + 1e-6;
   }
-  const float flo0 = (float)lo[0], fhi0 = (float)hi[0], flo1 = (float)lo[1], fhi1 = (float)hi[1];
-  for (int k = lane; k < s.ne; k += nl) {
-    if (s.dim == 2) {
-      if (st) {
-        const float4 q = st->seg[k];
-        const float T = seg_margin(q, flo0, flo1);
-        if (fmaxf(q.x, q.z) < flo0 - T || fminf(q.x, q.z) > fhi0 + T ||
-            fmaxf(q.y, q.w) < flo1 - T || fminf(q.y, q.w) > fhi1 + T)
-          continue;
-      }
-      const double *a = s.x + 2 * s.e[2 * k], *b = s.x + 2 * s.e[2 * k + 1];
-      if (fmax(a[0], b[0]) < lo[0] || fmin(a[0], b[0]) > hi[0] || fmax(a[1], b[1]) < lo[1] ||
-          fmin(a[1], b[1]) > hi[1])
-        continue;
-      const double ex = b[0] - a[0], ey = b[1] - a[1];
-      const double den = d[0] * (-ey) - d[1] * (-ex);
-      if (fabs(den) < 1e-300) continue;
-      const double rx = a[0] - xb[0], ry = a[1] - xb[1];
-      const double sp = (rx * (-ey) - ry * (-ex)) / den;
-      const double t = (d[0] * ry - d[1] * rx) / den;
-      if (sp > eps && sp <= 1.0 + eps && t >= -eps && t <= 1.0 + eps && sp < bs) {
-        bs = sp;
-        best = k;
-        const double tt = t < 0 ? 0 : (t > 1 ? 1 : t);
-        bw[0] = 1.0 - tt; bw[1] = tt; bw[2] = 0.0;
-      }
-    } else {
-      if (st) {
-        const float *t = st->tri[k];
-        float mag = 1.f + fabsf((float)lo[0]) + fabsf((float)lo[1]) + fabsf((float)lo[2]);
-        for (int q = 0; q < 9; ++q) mag += fabsf(t[q]);
-        const float T = 4e-6f * mag;
-        bool off = false;
-        for (int q = 0; q < 3; ++q) {
-          off = off || fmaxf(fmaxf(t[q], t[3 + q]), t[6 + q]) < (float)lo[q] - T ||
-                fminf(fminf(t[q], t[3 + q]), t[6 + q]) > (float)hi[q] + T;
-        }
-        if (off) continue;
-      }
-      const double *a = s.x + 3 * s.e[3 * k], *b = s.x + 3 * s.e[3 * k + 1],
-                   *c = s.x + 3 * s.e[3 * k + 2];
-      bool out = false;
-      for (int q = 0; q < 3; ++q)
-        out |= fmax(fmax(a[q], b[q]), c[q]) < lo[q] || fmin(fmin(a[q], b[q]), c[q]) > hi[q];
-      if (out) continue;
-      double sp, u, v;
-      if (!tri_ray(xb, d, a, b, c, sp, u, v)) continue;
-      if (sp > eps && sp <= 1.0 + eps && u >= -eps && v >= -eps && u + v <= 1.0 + eps && sp < bs) {
-        bs = sp;
-        best = k;
-        bw[0] = 1.0 - u - v; bw[1] = u; bw[2] = v;
-      }
-    }
+}
+
+__device__ __forceinline__ bool link_may_hit(const SurfaceDev &s, const SegStage *st, int k,
+                                             const double *lo, const double *hi) {
+  if (!st) return true;
+  if (s.dim == 2) {
+    const float4 q = st->seg[k];
+    const float flo0 = (float)lo[0], fhi0 = (float)hi[0], flo1 = (float)lo[1], fhi1 = (float)hi[1];
+    const float T = seg_margin(q, flo0, flo1);
+    return !(fmaxf(q.x, q.z) < flo0 - T || fminf(q.x, q.z) > fhi0 + T ||
+             fmaxf(q.y, q.w) < flo1 - T || fminf(q.y, q.w) > fhi1 + T);
   }
-  if (nl > 1) {
-    for (int o = 16; o > 0; o >>= 1) {
-      const double obs = __shfl_xor_sync(0xffffffffu, bs, o);
-      const int ob = __shfl_xor_sync(0xffffffffu, best, o);
-      if (ob >= 0 && (best < 0 || obs < bs || (obs == bs && ob < best))) {
-        bs = obs;
-        best = ob;
-      }
-    }
-    const int owner = best >= 0 ? best % nl : 0;
-    for (int q = 0; q < 3; ++q) bw[q] = __shfl_sync(0xffffffffu, bw[q], owner);
+  const float *t = st->tri[k];
+  float mag = 1.f + fabsf((float)lo[0]) + fabsf((float)lo[1]) + fabsf((float)lo[2]);
+  for (int q = 0; q < 9; ++q) mag += fabsf(t[q]);
+  const float T = 4e-6f * mag;
+  for (int q = 0; q < 3; ++q)
+    if (fmaxf(fmaxf(t[q], t[3 + q]), t[6 + q]) < (float)lo[q] - T ||
+        fminf(fminf(t[q], t[3 + q]), t[6 + q]) > (float)hi[q] + T)
+      return false;
+  return true;
+}
+
+__device__ bool link_crossing(const SurfaceDev &s, const double *xb, const double *d,
+                              const double *lo, const double *hi, int k, double &sp, double *bw) {
+  const double eps = 1e-9;
+  if (s.dim == 2) {
+    const double *a = s.x + 2 * s.e[2 * k], *b = s.x + 2 * s.e[2 * k + 1];
+    if (fmax(a[0], b[0]) < lo[0] || fmin(a[0], b[0]) > hi[0] || fmax(a[1], b[1]) < lo[1] ||
+        fmin(a[1], b[1]) > hi[1])
+      return false;
+    const double ex = b[0] - a[0], ey = b[1] - a[1];
+    const double den = d[0] * (-ey) - d[1] * (-ex);
+    if (fabs(den) < 1e-300) return false;
+    const double rx = a[0] - xb[0], ry = a[1] - xb[1];
+    sp = (rx * (-ey) - ry * (-ex)) / den;
+    const double t = (d[0] * ry - d[1] * rx) / den;
+    if (!(sp > eps && sp <= 1.0 + eps && t >= -eps && t <= 1.0 + eps)) return false;
+    const double tt = t < 0 ? 0 : (t > 1 ? 1 : t);
+    bw[0] = 1.0 - tt; bw[1] = tt; bw[2] = 0.0;
+    return true;
   }
+  const double *a = s.x + 3 * s.e[3 * k], *b = s.x + 3 * s.e[3 * k + 1], *c = s.x + 3 * s.e[3 * k + 2];
+  bool out = false;
+  for (int q = 0; q < 3; ++q)
+    out |= fmax(fmax(a[q], b[q]), c[q]) < lo[q] || fmin(fmin(a[q], b[q]), c[q]) > hi[q];
+  if (out) return false;
+  double u, v;
+  if (!tri_ray(xb, d, a, b, c, sp, u, v)) return false;
+  if (!(sp > eps && sp <= 1.0 + eps && u >= -eps && v >= -eps && u + v <= 1.0 + eps)) return false;
+  bw[0] = 1.0 - u - v; bw[1] = u; bw[2] = v;
+  return true;
+}
+
+__device__ void link_finish(const SurfaceDev &s, int best, double bs, const double *bw, Link &L) {
   L.uw[0] = L.uw[1] = L.uw[2] = 0.f;
   L.v[0] = L.v[1] = L.v[2] = 0;
   L.vw[0] = L.vw[1] = L.vw[2] = 0.f;
@@ -457,8 +478,12 @@ __device__ __forceinline__ void solid_flags_body(long long t, const Grid &g, con
             z = bd.z0 + (int)(t / ((long long)bx * by));
   const double p[3] = {x + 0.5, y + 0.5, z + 0.5};  // cell-centred node position
   const long long k = sidx(g, x + g.px, y + g.py, z + g.pz);
-  const bool in = staged ? (s.dim == 2 ? inside_any_staged(s, st, p) : inside_any_staged3(s, st, p))
-                         : inside_any(s, p);
+  bool in;
+  if (staged)
+    in = !outside_staged_box(st, p, s.dim) &&
+         (s.dim == 2 ? inside_any_staged(s, st, p) : inside_any_staged3(s, st, p));
+  else
+    in = inside_any(s, p);
   const uint8_t now = in ? NODE_SOLID : NODE_FLUID;
   const uint8_t before = flags[k];
   if (before == NODE_GHOST) return;
@@ -516,7 +541,53 @@ __device__ __forceinline__ void build_links_body(long long t, const Grid &g, con
 }
 
 // Cut links of the listed boundary nodes: one warp per node (grid-stride
-// over the list), the lanes splitting the surface elements of each link.
+// over the list).  The lanes prefilter the surface elements of all the
+// node's links in FP32 and compact the candidates (link, element); the FP64
+// crossing tests then run one candidate per lane, and each link keeps its
+// nearest crossing (ties: the lower element index, as in the serial scan).
+constexpr int kLinkCand = 64;
+
+struct LinkScratch {
+  short cm[kLinkCand], ck[kLinkCand];
+  double csp[kLinkCand];
+  double bsp[27];
+  int bk[27];
+  int dir[27];
+};
+
+__device__ __forceinline__ void link_dir(int Q, int i, double *d) {
+  if (Q == 9) {
+    d[0] = -(double)(i % 3 - 1); d[1] = -(double)(i / 3 - 1); d[2] = 0.0;
+  } else {
+    d[0] = -(double)(i % 3 - 1); d[1] = -(double)((i / 3) % 3 - 1); d[2] = -(double)(i / 9 - 1);
+  }
+}
+
+template <int Q>
+__device__ __forceinline__ void link_flush(const SurfaceDev &s, const double *xb, LinkScratch &S,
+                                           int count, int nm, int lane) {
+  __syncwarp();
+  for (int j = lane; j < count; j += 32) {
+    double d[3], lo[3], hi[3], sp, w[3];
+    link_dir(Q, S.dir[S.cm[j]], d);
+    link_box(xb, d, lo, hi);
+    S.csp[j] = link_crossing(s, xb, d, lo, hi, S.ck[j], sp, w) ? sp : 4.0;
+  }
+  __syncwarp();
+  if (lane < nm) {
+    for (int j = 0; j < count; ++j) {
+      if (S.cm[j] != lane || S.csp[j] > 3.0) continue;
+      const double sp = S.csp[j];
+      const int k = S.ck[j];
+      if (sp < S.bsp[lane] || (sp == S.bsp[lane] && k < S.bk[lane])) {
+        S.bsp[lane] = sp;
+        S.bk[lane] = k;
+      }
+    }
+  }
+  __syncwarp();
+}
+
 template <int Q>
 __device__ __forceinline__ void link_fill_body(const Grid &g, const SurfaceDev &s,
                                                const uint8_t *flags, const BNode *bnodes,
@@ -524,9 +595,11 @@ __device__ __forceinline__ void link_fill_body(const Grid &g, const SurfaceDev &
                                                int nwarps) {
   using L = Lat<Q>;
   __shared__ SegStage st;
+  __shared__ LinkScratch scratch[4];
   const bool staged = stage_segments(s, st);
   __syncthreads();
   const int lane = threadIdx.x & 31;
+  LinkScratch &S = scratch[(threadIdx.x >> 5) & 3];
   const int n = *nbn < bcap ? *nbn : bcap;
   for (int w = warp0; w < n; w += nwarps) {
     const BNode b = bnodes[w];
@@ -534,22 +607,94 @@ __device__ __forceinline__ void link_fill_body(const Grid &g, const SurfaceDev &
     int X, Y, Z;
     decompose(g, b.k, X, Y, Z);
     const double xb[3] = {X - g.px + 0.5, Y - g.py + 0.5, Z - g.pz + 0.5};
-    int m = 0;
-    for (int i = 0; i < Q; ++i) {
-      const int Xs = nbr(X, -L::cx(i), g.NX), Ys = nbr(Y, -L::cy(i), g.NY),
-                Zs = (L::D == 3) ? nbr(Z, -L::cz(i), g.NZ) : Z;
-      if (flags[sidx(g, Xs, Ys, Zs)] != NODE_SOLID) continue;
-      Link lk;
-      lk.i = i;
-      link_hit(s, xb, L::cx(i), L::cy(i), L::cz(i), lk, staged ? &st : nullptr, lane, 32);
-      if (lane == 0) links[b.link0 + m] = lk;
-      ++m;
+    // the node's missing directions, in direction order
+    bool solid = false;
+    if (lane < Q) {
+      const int Xs = nbr(X, -L::cx(lane), g.NX), Ys = nbr(Y, -L::cy(lane), g.NY),
+                Zs = (L::D == 3) ? nbr(Z, -L::cz(lane), g.NZ) : Z;
+      solid = flags[sidx(g, Xs, Ys, Zs)] == NODE_SOLID;
     }
+    const unsigned mask = __ballot_sync(0xffffffffu, solid);
+    const int nm = __popc(mask);
+    if (solid) {
+      const int m = __popc(mask & ((1u << lane) - 1u));
+      S.dir[m] = lane;
+      S.bsp[m] = 2.0;
+      S.bk[m] = -1;
+    }
+    __syncwarp();
+    if (!staged) {
+      // large surfaces: the lanes split the elements of each link in turn
+      for (int m = 0; m < nm; ++m) {
+        double d[3], lo[3], hi[3];
+        link_dir(Q, S.dir[m], d);
+        link_box(xb, d, lo, hi);
+        double bs = 2.0;
+        int best = -1;
+        for (int k = lane; k < s.ne; k += 32) {
+          double sp, wv[3];
+          if (link_crossing(s, xb, d, lo, hi, k, sp, wv) && sp < bs) {
+            bs = sp;
+            best = k;
+          }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          const double obs = __shfl_xor_sync(0xffffffffu, bs, o);
+          const int ob = __shfl_xor_sync(0xffffffffu, best, o);
+          if (ob >= 0 && (best < 0 || obs < bs || (obs == bs && ob < best))) {
+            bs = obs;
+            best = ob;
+          }
+        }
+        if (lane == 0) {
+          S.bsp[m] = bs;
+          S.bk[m] = best;
+        }
+        __syncwarp();
+      }
+    } else {
+      int count = 0;
+      for (int m = 0; m < nm; ++m) {
+        double d[3], lo[3], hi[3];
+        link_dir(Q, S.dir[m], d);
+        link_box(xb, d, lo, hi);
+        for (int k0 = 0; k0 < s.ne; k0 += 32) {
+          const int k = k0 + lane;
+          const bool pass = k < s.ne && link_may_hit(s, &st, k, lo, hi);
+          const unsigned pm = __ballot_sync(0xffffffffu, pass);
+          if (pass) {
+            const int pos = count + __popc(pm & ((1u << lane) - 1u));
+            S.cm[pos] = (short)m;
+            S.ck[pos] = (short)k;
+          }
+          count += __popc(pm);
+          if (count > kLinkCand - 32) {
+            link_flush<Q>(s, xb, S, count, nm, lane);
+            count = 0;
+          }
+        }
+      }
+      link_flush<Q>(s, xb, S, count, nm, lane);
+    }
+    if (lane < nm) {
+      Link lk;
+      lk.i = S.dir[lane];
+      double d[3], lo[3], hi[3], sp = 2.0, bw[3] = {0, 0, 0};
+      const int best = S.bk[lane];
+      if (best >= 0) {
+        link_dir(Q, S.dir[lane], d);
+        link_box(xb, d, lo, hi);
+        link_crossing(s, xb, d, lo, hi, best, sp, bw);
+      }
+      link_finish(s, best, sp, bw, lk);
+      links[b.link0 + lane] = lk;
+    }
+    __syncwarp();
   }
 }
 
 template <int Q>
-__global__ void __launch_bounds__(256) k_link_fill(Grid g, SurfaceDev s, const uint8_t *flags,
+__global__ void __launch_bounds__(128) k_link_fill(Grid g, SurfaceDev s, const uint8_t *flags,
                                                    const BNode *bnodes, const int *nbn, int bcap,
                                                    Link *links) {
   link_fill_body<Q>(g, s, flags, bnodes, nbn, bcap, links,
@@ -878,7 +1023,7 @@ __global__ void k_step_counter(int *step) { *step += 1; }
 // ---------------------------------------------------------------- launchers
 static inline unsigned nb_(long long n, int b) { return (unsigned)((n + b - 1) / b); }
 
-// Grid of the link-fill pass: four 256-thread CTAs per SM, warps striding
+// Grid of the link-fill pass: four 128-thread CTAs per SM, warps striding
 // over the boundary-node list.
 static unsigned fill_grid() {
   static int sms = 0;
@@ -895,9 +1040,9 @@ static cudaError_t launch_link_fill(int Q, const Grid &g, const SurfaceDev &sd, 
                                     const BNode *bnodes, const int *nbn, int bcap, Link *links,
                                     cudaStream_t s) {
   if (Q == 9)
-    k_link_fill<9><<<fill_grid(), 256, 0, s>>>(g, sd, flags, bnodes, nbn, bcap, links);
+    k_link_fill<9><<<fill_grid(), 128, 0, s>>>(g, sd, flags, bnodes, nbn, bcap, links);
   else
-    k_link_fill<27><<<fill_grid(), 256, 0, s>>>(g, sd, flags, bnodes, nbn, bcap, links);
+    k_link_fill<27><<<fill_grid(), 128, 0, s>>>(g, sd, flags, bnodes, nbn, bcap, links);
   return cudaGetLastError();
 }
 
@@ -1049,7 +1194,7 @@ __global__ void k_links_batch(const InstDesc *__restrict__ d, const int *__restr
 }
 
 template <int Q>
-__global__ void __launch_bounds__(256) k_link_fill_batch(const InstDesc *__restrict__ d,
+__global__ void __launch_bounds__(128) k_link_fill_batch(const InstDesc *__restrict__ d,
                                                          const int *__restrict__ idx) {
   const InstDesc &b = d[idx[blockIdx.y]];
   link_fill_body<Q>(b.g, b.sd, b.flags, b.bnodes + b.nfixed, b.nbn, b.lcap, b.links,
@@ -1085,12 +1230,12 @@ cudaError_t launch_geometry_batch(int Q, int storage, const InstDesc *d, const i
   KBC_DISPATCH(Q, storage, {
     k_fresh_batch<QQ, SS><<<gf, 128, 0, s>>>(d, idx, parity);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const dim3 gl(8, n);
+    const dim3 gl(16, n);
     if (QQ == 9) k_links_batch<9><<<gb, 128, 0, s>>>(d, idx);
     else k_links_batch<27><<<gb, 128, 0, s>>>(d, idx);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (QQ == 9) k_link_fill_batch<9><<<gl, 256, 0, s>>>(d, idx);
-    else k_link_fill_batch<27><<<gl, 256, 0, s>>>(d, idx);
+    if (QQ == 9) k_link_fill_batch<9><<<gl, 128, 0, s>>>(d, idx);
+    else k_link_fill_batch<27><<<gl, 128, 0, s>>>(d, idx);
     return cudaGetLastError();
   });
 }
