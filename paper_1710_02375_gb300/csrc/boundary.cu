@@ -462,6 +462,50 @@ __device__ void link_finish(const SurfaceDev &s, int best, double bs, const doub
   for (int a = 0; a < 3; ++a) L.uw[a] = (float)uw[a];
 }
 
+// Bounding box of the surface vertices (one CTA), rounded to FP32.
+__device__ __forceinline__ void surface_box_body(const SurfaceDev &s) {
+  __shared__ float red[6][8];
+  float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
+  for (int v = threadIdx.x; v < s.nv; v += blockDim.x)
+    for (int q = 0; q < s.dim; ++q) {
+      const float c = (float)s.x[s.dim * v + q];
+      lo[q] = fminf(lo[q], c);
+      hi[q] = fmaxf(hi[q], c);
+    }
+  for (int q = 0; q < 3; ++q)
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[q] = fminf(lo[q], __shfl_xor_sync(0xffffffffu, lo[q], o));
+      hi[q] = fmaxf(hi[q], __shfl_xor_sync(0xffffffffu, hi[q], o));
+    }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0)
+    for (int q = 0; q < 3; ++q) {
+      red[q][w] = lo[q];
+      red[3 + q][w] = hi[q];
+    }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    const bool is_lo = threadIdx.x < 3;
+    float v = is_lo ? 3e38f : -3e38f;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k)
+      v = is_lo ? fminf(v, red[threadIdx.x][k]) : fmaxf(v, red[threadIdx.x][k]);
+    s.box[threadIdx.x] = v;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_surface_box(SurfaceDev s) { surface_box_body(s); }
+
+// Whether node p lies outside box by a margin far above the FP32 rounding of
+// the box: then it is neither inside a body nor on the surface.
+__device__ __forceinline__ bool outside_box(const float *box, const double *p, int dim) {
+  for (int q = 0; q < dim; ++q) {
+    const float pq = (float)p[q], lo = box[q], hi = box[3 + q];
+    if (pq < lo - 1e-5f * (1.f + fabsf(pq) + fabsf(lo)) || pq > hi + 1e-5f * (1.f + fabsf(pq) + fabsf(hi)))
+      return true;
+  }
+  return false;
+}
+
 // New solid flags inside the band; nodes that turn fluid are listed as fresh.
 __device__ __forceinline__ void solid_flags_body(long long t, const Grid &g, const Band &bd,
                                                  const SurfaceDev &s, uint8_t *flags,
@@ -471,15 +515,25 @@ __device__ __forceinline__ void solid_flags_body(long long t, const Grid &g, con
   const int bx = bd.x1 - bd.x0, by = bd.y1 - bd.y0, bz = bd.z1 - bd.z0;
   const long long nbnd = (long long)bx * by * bz;
   if ((long long)(t - threadIdx.x) >= nbnd) return;  // whole CTA past the band
-  const bool staged = stage_segments(s, st);
-  __syncthreads();
-  if (t >= nbnd) return;
-  const int x = bd.x0 + (int)(t % bx), y = bd.y0 + (int)((t / bx) % by),
-            z = bd.z0 + (int)(t / ((long long)bx * by));
+  const bool live = t < nbnd;
+  const long long tt = live ? t : nbnd - 1;
+  const int x = bd.x0 + (int)(tt % bx), y = bd.y0 + (int)((tt / bx) % by),
+            z = bd.z0 + (int)(tt / ((long long)bx * by));
   const double p[3] = {x + 0.5, y + 0.5, z + 0.5};  // cell-centred node position
   const long long k = sidx(g, x + g.px, y + g.py, z + g.pz);
+  // a CTA whose nodes all lie outside the surface's box needs no element tests
+  const bool far = s.box && outside_box(s.box, p, s.dim);
+  const bool all_far = s.box ? __syncthreads_and(far) != 0 : false;
+  bool staged = false;
+  if (!all_far) {
+    staged = stage_segments(s, st);
+    __syncthreads();
+  }
+  if (!live) return;
   bool in;
-  if (staged)
+  if (far)
+    in = false;
+  else if (staged)
     in = !outside_staged_box(st, p, s.dim) &&
          (s.dim == 2 ? inside_any_staged(s, st, p) : inside_any_staged3(s, st, p));
   else
@@ -1077,6 +1131,10 @@ cudaError_t launch_geometry(int Q, int storage, const Grid &g, const Band &bd, c
   if ((e = cudaMemsetAsync(nfresh, 0, sizeof(int), s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(nbn, 0, sizeof(int), s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(nl, 0, sizeof(int), s)) != cudaSuccess) return e;
+  if (sd.box) {
+    k_surface_box<<<1, 256, 0, s>>>(sd);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   k_solid_flags<<<nb_(nb, 128), 128, 0, s>>>(g, bd, sd, flags, fresh, nfresh, fresh_cap,
                                               track_fresh);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1171,6 +1229,12 @@ __global__ void k_geom_reset_batch(const InstDesc *__restrict__ d, const int *__
   *b.nfresh = 0;
 }
 
+__global__ void __launch_bounds__(256) k_surface_box_batch(const InstDesc *__restrict__ d,
+                                                           const int *__restrict__ idx) {
+  const InstDesc &b = d[idx[blockIdx.x]];
+  if (b.sd.box) surface_box_body(b.sd);
+}
+
 __global__ void k_solid_flags_batch(const InstDesc *__restrict__ d, const int *__restrict__ idx) {
   const InstDesc &b = d[idx[blockIdx.y]];
   solid_flags_body(blockIdx.x * (long long)blockDim.x + threadIdx.x, b.g, b.band, b.sd, b.flags,
@@ -1225,6 +1289,8 @@ cudaError_t launch_geometry_batch(int Q, int storage, const InstDesc *d, const i
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   dim3 gb(nb_(max_band, 128), n), gf(nb_(max_fresh, 128), n);
+  k_surface_box_batch<<<n, 256, 0, s>>>(d, idx);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_solid_flags_batch<<<gb, 128, 0, s>>>(d, idx);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   KBC_DISPATCH(Q, storage, {

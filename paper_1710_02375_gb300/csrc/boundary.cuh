@@ -34,6 +34,7 @@ struct SurfaceDev {
   const double *v;     // [nv][dim] vertex velocities
   const int32_t *e;    // [ne][dim] element vertex ids
   const int32_t *eb;   // [ne] body id
+  float *box;          // [6] bounding box of the vertices (lo xyz, hi xyz), or nullptr
 };
 
 struct Band {          // box of interior coordinates, inclusive lower, exclusive upper

@@ -30,6 +30,7 @@ struct Layout {
   size_t f[2], flags, err, stage;
   size_t sx, sv, se, seb, links, bnodes, fresh, counters, vforce, bforce, inlet[6];
   size_t sigma, orient, tvforce, tbforce;  // stress-traction output
+  size_t sbox;                             // bounding box of the surface (6 floats)
   int nface, bcap, inlet_n[6];
   size_t total;
 };
@@ -83,6 +84,7 @@ Layout make_layout(const lbm_config &c) {
   L.orient = off; off += align_up(sizeof(double) * kMaxBodies);
   L.tvforce = off; off += align_up(sizeof(double) * 3 * (size_t)std::max(nv, 1));
   L.tbforce = off; off += align_up(sizeof(double) * 3 * kMaxBodies);
+  L.sbox = off; off += align_up(sizeof(float) * 8);
   for (int fc = 0; fc < 6; ++fc) {
     L.inlet_n[fc] = 0;
     L.inlet[fc] = 0;
@@ -468,6 +470,7 @@ static SurfaceDev surface_dev(lbm_ctx *ctx) {
   s.v = (const double *)(ctx->ws + ctx->lay.sv);
   s.e = (const int32_t *)(ctx->ws + ctx->lay.se);
   s.eb = (const int32_t *)(ctx->ws + ctx->lay.seb);
+  s.box = (float *)(ctx->ws + ctx->lay.sbox);
   return s;
 }
 
