@@ -385,11 +385,21 @@ void mlp_destroy(mlp_ctx *x);
  * |R| <= accept_tol |theta F1 + (1 - theta) F0| (free DOFs); otherwise Newton
  * continues from it (FEM fallback) to the usual stopping test, which stays
  * relative to the residual at the start u.  Network: 15 nn - 15 inputs,
- * 3 nn - 3 outputs (LBM_EINVAL otherwise).  mlp NULL removes the surrogate.
- * The network context must outlive its use by the lattice. */
+ * 3 nn - 3 outputs (LBM_EINVAL otherwise).
+ * With a coupled shell (fsi_couple_shell) the same scheme runs on its nf
+ * free DOFs (6 per node not held, node-major, in (ux, uy, uz, phix, phiy,
+ * phiz) order): input blocks F(t) - f, F(t-1) - f, F(t-2) - f (nodal loads
+ * as in fsi_couple_shell; f: the internal force at the state before the
+ * step), the state (translations and nodal rotation vectors) and the
+ * velocities; output: the step's increment (translations, rotation vector
+ * of R1 R0^T) beyond dt v.  Network: 5 nf inputs, nf outputs; the guess is
+ * accepted when |R| <= accept_tol |theta F1 + (1 - theta) F0|.
+ * mlp NULL removes the surrogate; fsi_couple / fsi_couple_shell remove it
+ * too.  The network context must outlive its use by the lattice. */
 lbm_status fsi_set_surrogate(lbm_ctx *ctx, mlp_ctx *mlp, const float *in_mean, const float *in_std,
                              const float *out_mean, const float *out_std, double accept_tol);
-/* Structural-step counters of the coupled beam since fsi_couple,
+/* Structural-step counters of the coupled beam or shell since fsi_couple
+ * (fsi_couple_shell),
  * fsi_set_surrogate or the last reset: stats[0] guesses accepted, stats[1]
  * guesses rejected, stats[2] Newton solves (linearised systems solved),
  * stats[3] structural steps.  reset != 0 zeroes them after reading.

@@ -64,6 +64,10 @@ struct ShellDev {
   double *red;               // [3][2] reduction slots
   const double *F1;          // [6 nn] loads of the step
   int *iters;                // [2]: Newton iterations of the last step, CG iterations
+  double *Fm2;               // [6 nn] loads two steps back (surrogate input)
+  const double *dqg;         // [6 nn] Newton start (surrogate guess), nullptr: zero
+  double accept_tol;         // > 0: accept the guess when |R| <= accept_tol |F_ext|
+  int *stats;                // [4]: guesses accepted, rejected, Newton solves, steps
 };
 
 __device__ __forceinline__ void elem_ids(const ShellParams &P, int e, int id[4]) {
@@ -565,7 +569,7 @@ __global__ void __launch_bounds__(kShellThreads) k_shell_step(ShellParams P, She
   double ra, rb;
   for (long long i = gt; i < n; i += gs) {
     D.v0[i] = D.v[i];
-    D.dq[i] = 0.0;
+    D.dq[i] = D.dqg ? D.dqg[i] : 0.0;
     D.f0[i] = 0.0;
     D.f[i] = 0.0;
     D.kd[i] = 0.0;
@@ -607,6 +611,34 @@ __global__ void __launch_bounds__(kShellThreads) k_shell_step(ShellParams P, She
     }
     step_sum2<CLUSTER>(D.red, slot, part, rz0, ra, rb);
     const double rn = sqrt(ra);
+    if (it == 0 && D.dqg) {
+      // started from a guess: the stopping test stays relative to the
+      // residual at the step's start (dq = 0), and the guess is accepted
+      // outright when its residual is small against the loads
+      double p0 = 0.0, pf = 0.0;
+      for (long long i = gt; i < n; i += gs) {
+        if (D.fixed[i]) continue;
+        const long long a = i / 6;
+        const double m = (i % 6) < 3 ? D.mt[a] : D.mr[a];
+        const double v1 = -(1.0 - P.theta) * D.v0[i] * ith;
+        const double R0 = m * (v1 - D.v0[i]) * idt - P.theta * (D.F1[i] - D.f0[i]) -
+                          (1.0 - P.theta) * (D.F0[i] - D.f0[i]);
+        const double fe = P.theta * D.F1[i] + (1.0 - P.theta) * D.F0[i];
+        p0 += R0 * R0;
+        pf += fe * fe;
+      }
+      double r0sq, fe2;
+      step_sum2<CLUSTER>(D.red, slot, p0, pf, r0sq, fe2);
+      r0 = sqrt(r0sq);
+      if (D.accept_tol > 0.0) {
+        const bool accept = rn <= D.accept_tol * sqrt(fe2);
+        if (gt == 0 && D.stats) atomicAdd(&D.stats[accept ? 0 : 1], 1);
+        if (accept) {
+          conv = 1;
+          break;
+        }
+      }
+    }
     if (r0 < 0.0) r0 = rn;
     if (rn <= P.rtol * r0 + P.atol) {
       conv = 1;
@@ -665,6 +697,7 @@ __global__ void __launch_bounds__(kShellThreads) k_shell_step(ShellParams P, She
   for (long long i = gt; i < n; i += gs) {
     const double v1 = (D.dq[i] * idt - (1.0 - P.theta) * D.v0[i]) * ith;
     D.v[i] = D.fixed[i] ? 0.0 : v1;
+    D.Fm2[i] = D.F0[i];
     D.F0[i] = D.F1[i];
   }
   for (long long a = gt; a < nn; a += gs) {
@@ -679,7 +712,58 @@ __global__ void __launch_bounds__(kShellThreads) k_shell_step(ShellParams P, She
   if (gt == 0) {
     D.iters[0] = conv ? it : -it - 1;
     D.iters[1] = cg_total;
+    if (D.stats) {
+      atomicAdd(&D.stats[2], it);  // Newton solves of this step
+      atomicAdd(&D.stats[3], 1);
+    }
   }
+}
+
+// Internal force of the current state (one warp per element).
+__global__ void __launch_bounds__(kShellThreads) k_shell_force_now(ShellParams P, ShellDev D,
+                                                                   double *fout) {
+  __shared__ ShellWarp Wsh[kShellThreads / 32];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int wg = blockIdx.x * (kShellThreads / 32) + wl, nwg = gridDim.x * (kShellThreads / 32);
+  for (int e = wg; e < P.ne; e += nwg)
+    warp_element_force(P, D, e, D.u, D.R, nullptr, fout, nullptr, nullptr, Wsh[wl], lane);
+}
+
+// Surrogate input of the coming step (normalised, FP32): out-of-balance loads
+// F1 - f, F0 - f, Fm2 - f, then the state (translations, rotation vectors)
+// and the velocities, each block over the free DOFs in freemap order.
+__global__ void k_shell_surr_input(ShellParams P, ShellDev D, const double *fcur,
+                                   const int *freemap, int nf, const float *xm, const float *xs,
+                                   float *xin) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= 5 * nf) return;
+  const int blk = j / nf, i = freemap[j % nf], a = i / 6, c = i % 6;
+  double val;
+  if (blk == 0) val = D.F1[i] - fcur[i];
+  else if (blk == 1) val = D.F0[i] - fcur[i];
+  else if (blk == 2) val = D.Fm2[i] - fcur[i];
+  else if (blk == 3) {
+    if (c < 3) {
+      val = D.u[3 * a + c];
+    } else {
+      double phi[3];
+      rotvec(D.R + 9 * a, phi);
+      val = phi[c - 3];
+    }
+  } else {
+    val = D.v[i];
+  }
+  xin[j] = (float)((val - (double)xm[j]) / (double)xs[j]);
+}
+
+// Newton start of the step: dt v plus the network's correction on the free
+// DOFs (the held DOFs stay zero: dqg is cleared when the surrogate is set).
+__global__ void k_shell_surr_guess(ShellParams P, ShellDev D, const float *yhat, const int *freemap,
+                                   int nf, const float *ym, const float *ys, double *dqg) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nf) return;
+  const int i = freemap[j];
+  dqg[i] = P.dt * D.v[i] + (double)(yhat[j] * ys[j] + ym[j]);
 }
 
 // Nodal loads of a coupled plate: each node takes the momentum-exchange
@@ -727,10 +811,15 @@ struct fem_shell_ctx {
   bool own_ws = false;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  double *dqg = nullptr, *fcur = nullptr;  // surrogate guess, internal force at the state
+  int *freemap = nullptr;                  // free DOF indices (surrogate feature order)
+  int nfree = 0;
+  float *xm = nullptr, *xs = nullptr, *ym = nullptr, *ys = nullptr;
   int grid = 0;      // CTAs of the cooperative launch
   int cluster = 0;   // CTAs of the single-cluster launch (0: not available)
   bool poisoned = false;
   char msg[256] = {0};
+  std::vector<int32_t> fixed_h;  // Dirichlet mask (host copy)
 };
 
 // One structural step: a single cluster when available, else the cooperative grid.
@@ -784,6 +873,12 @@ size_t shell_layout(int nx, int ny, fem_shell_ctx *s) {
   for (int k = 0; k < 7; ++k) ovec[k] = take(sizeof(double) * n);
   const size_t ored = take(sizeof(double) * 6), oF1 = take(sizeof(double) * n),
                oit = take(sizeof(int) * 2);
+  const size_t oFm2 = take(sizeof(double) * n), ostats = take(sizeof(int) * 4);
+  // surrogate: guess, current internal force, free-DOF map, normalisation
+  const size_t odqg = take(sizeof(double) * n), ofc = take(sizeof(double) * n),
+               ofree = take(sizeof(int) * n), oxm = take(sizeof(float) * 5 * n),
+               oxs = take(sizeof(float) * 5 * n), oym = take(sizeof(float) * n),
+               oys = take(sizeof(float) * n);
   if (s) {
     char *w = s->ws;
     ShellDev &d = s->d;
@@ -805,6 +900,15 @@ size_t shell_layout(int nx, int ny, fem_shell_ctx *s) {
     s->F1 = (double *)(w + oF1);
     d.F1 = s->F1;
     d.iters = (int *)(w + oit);
+    d.Fm2 = (double *)(w + oFm2);
+    d.stats = (int *)(w + ostats);
+    d.dqg = nullptr;
+    d.accept_tol = 0.0;
+    s->dqg = (double *)(w + odqg);
+    s->fcur = (double *)(w + ofc);
+    s->freemap = (int *)(w + ofree);
+    s->xm = (float *)(w + oxm); s->xs = (float *)(w + oxs);
+    s->ym = (float *)(w + oym); s->ys = (float *)(w + oys);
   }
   return off;
 }
@@ -888,6 +992,10 @@ lbm_status fem_shell_create(const fem_shell_config *c, void *workspace, size_t b
   if (e == cudaSuccess)
     e = cudaMemcpyAsync((void *)s->d.fixed, c->fixed, sizeof(int32_t) * p.n, cudaMemcpyDefault,
                         s->stream);
+  if (e == cudaSuccess) {
+    s->fixed_h.resize(p.n);
+    e = cudaMemcpy(s->fixed_h.data(), c->fixed, sizeof(int32_t) * p.n, cudaMemcpyDefault);
+  }
   if (e == cudaSuccess) {
     std::vector<double> Rid(9 * (size_t)p.nn, 0.0);
     for (int a = 0; a < p.nn; ++a) Rid[9 * a] = Rid[9 * a + 4] = Rid[9 * a + 8] = 1.0;
@@ -1012,6 +1120,73 @@ cudaError_t launch_shell_coupled(fem_shell_ctx *s, const double *vforce, double 
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = launch_shell_step(s, st);
+  if (e != cudaSuccess) return e;
+  return launch_shell_surface(s, surf_x, surf_v, v0, st);
+}
+
+}  // namespace kbc
+
+namespace kbc {
+
+int shell_free_dofs(const fem_shell_ctx *s) {
+  int nf = 0;
+  for (int32_t f : s->fixed_h) nf += f ? 0 : 1;
+  return nf;
+}
+
+// Normalisation of the surrogate network (5 nf inputs, nf outputs) and the
+// free-DOF map; clears the guess and the counters.
+lbm_status shell_set_surrogate(fem_shell_ctx *s, const float *in_mean, const float *in_std,
+                               const float *out_mean, const float *out_std) {
+  std::vector<int> map;
+  for (int i = 0; i < s->p.n; ++i)
+    if (!s->fixed_h[i]) map.push_back(i);
+  const size_t nf = map.size();
+  s->nfree = (int)nf;
+  cudaError_t e = cudaMemcpyAsync(s->freemap, map.data(), sizeof(int) * nf, cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s->xm, in_mean, sizeof(float) * 5 * nf, cudaMemcpyDefault, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s->xs, in_std, sizeof(float) * 5 * nf, cudaMemcpyDefault, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s->ym, out_mean, sizeof(float) * nf, cudaMemcpyDefault, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s->ys, out_std, sizeof(float) * nf, cudaMemcpyDefault, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->dqg, 0, sizeof(double) * s->p.n, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d.stats, 0, sizeof(int) * 4, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  return e == cudaSuccess ? LBM_OK : LBM_ECUDA;
+}
+
+lbm_status shell_get_stats(fem_shell_ctx *s, int *stats, int reset) {
+  cudaError_t e = cudaMemcpyAsync(stats, s->d.stats, sizeof(int) * 4, cudaMemcpyDefault, s->stream);
+  if (e == cudaSuccess && reset) e = cudaMemsetAsync(s->d.stats, 0, sizeof(int) * 4, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  return e == cudaSuccess ? LBM_OK : LBM_ECUDA;
+}
+
+// Coupled step with the surrogate: loads, internal force of the state,
+// network input, forward pass, guess, shell step started from the guess
+// (accepted by its residual or refined by Newton), surface.
+cudaError_t launch_shell_coupled_guess(fem_shell_ctx *s, const double *vforce, double *surf_x,
+                                       double *surf_v, int v0, double accept_tol, mlp_ctx *mlp,
+                                       cudaStream_t st) {
+  k_shell_loads<<<(s->p.nn + 127) / 128, 128, 0, st>>>(s->p, s->F1, vforce, v0);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->fcur, 0, sizeof(double) * s->p.n, st);
+  if (e != cudaSuccess) return e;
+  k_shell_force_now<<<(s->p.ne + 3) / 4, kShellThreads, 0, st>>>(s->p, s->d, s->fcur);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int nf = s->nfree;
+  k_shell_surr_input<<<(5 * nf + 127) / 128, 128, 0, st>>>(s->p, s->d, s->fcur, s->freemap, nf, s->xm,
+                                                          s->xs, mlp_input_buffer(mlp));
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  float *yhat = nullptr, *xin = nullptr;
+  if (mlp_forward_device(mlp, 1, st, &yhat, &xin) != LBM_OK) return cudaErrorLaunchFailure;
+  k_shell_surr_guess<<<(nf + 127) / 128, 128, 0, st>>>(s->p, s->d, yhat, s->freemap, nf, s->ym, s->ys,
+                                                      s->dqg);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  ShellDev saved = s->d;
+  s->d.dqg = s->dqg;
+  s->d.accept_tol = accept_tol;
+  e = launch_shell_step(s, st);
+  s->d = saved;
   if (e != cudaSuccess) return e;
   return launch_shell_surface(s, surf_x, surf_v, v0, st);
 }

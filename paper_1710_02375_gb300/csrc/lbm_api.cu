@@ -436,6 +436,13 @@ lbm_status lbm_step(lbm_ctx *ctx, int n) {
                                    ctx->stream));
       st = run_geometry(ctx, 1);
       if (st != LBM_OK) return st;
+    } else if (ctx->shell && ctx->mlp) {
+      CK(launch_shell_coupled_guess(ctx->shell, (const double *)(ctx->ws + ctx->lay.vforce),
+                                    (double *)(ctx->ws + ctx->lay.sx),
+                                    (double *)(ctx->ws + ctx->lay.sv), ctx->shell_v0,
+                                    ctx->accept_tol, ctx->mlp, ctx->stream));
+      lbm_status st = run_geometry(ctx, 1);
+      if (st != LBM_OK) return st;
     } else if (ctx->shell) {
       CK(launch_shell_coupled(ctx->shell, (const double *)(ctx->ws + ctx->lay.vforce),
                               (double *)(ctx->ws + ctx->lay.sx), (double *)(ctx->ws + ctx->lay.sv),
@@ -624,6 +631,7 @@ lbm_status lbm_set_inlet_profile(lbm_ctx *ctx, int face, const double *u) {
 
 lbm_status fsi_couple(lbm_ctx *ctx, fem_ctx *f, int first_vertex) {
   GUARD();
+  ctx->mlp = nullptr;
   if (!f) {
     ctx->fem = nullptr;
     ctx->graph_dirty = true;
@@ -646,6 +654,7 @@ lbm_status fsi_couple(lbm_ctx *ctx, fem_ctx *f, int first_vertex) {
 
 lbm_status fsi_couple_shell(lbm_ctx *ctx, fem_shell_ctx *s, int first_vertex) {
   GUARD();
+  ctx->mlp = nullptr;
   if (!s) {
     ctx->shell = nullptr;
     ctx->graph_dirty = true;
@@ -658,6 +667,9 @@ lbm_status fsi_couple_shell(lbm_ctx *ctx, fem_shell_ctx *s, int first_vertex) {
   if (first_vertex < 0 || first_vertex + 2 * nn > ctx->nv)
     return fail(ctx, LBM_EINVAL, "fsi_couple_shell: vertices [%d, %d) outside the surface (%d)",
                 first_vertex, first_vertex + 2 * nn, ctx->nv);
+  int zero[4];
+  if (shell_get_stats(s, zero, 1) != LBM_OK)
+    return fail(ctx, LBM_ECUDA, "fsi_couple_shell: counter reset failed");
   ctx->shell = s;
   ctx->shell_v0 = first_vertex;
   ctx->graph_dirty = true;
@@ -674,7 +686,22 @@ lbm_status fsi_set_surrogate(lbm_ctx *ctx, mlp_ctx *mlp, const float *in_mean, c
     ctx->graph_dirty = true;
     return LBM_OK;
   }
-  if (!ctx->fem) return fail(ctx, LBM_ESTATE, "fsi_set_surrogate: couple a beam first");
+  if (!in_mean || !in_std || !out_mean || !out_std || !(accept_tol > 0.0))
+    return fail(ctx, LBM_EINVAL, "fsi_set_surrogate: bad normalisation or tolerance");
+  if (ctx->shell) {
+    const int nf = shell_free_dofs(ctx->shell);
+    if (mlp_dim(mlp, 0) != 5 * nf || mlp_dim(mlp, mlp_layers(mlp)) != nf)
+      return fail(ctx, LBM_EINVAL,
+                  "fsi_set_surrogate: the network must map %d inputs to %d outputs for this shell",
+                  5 * nf, nf);
+    lbm_status st = shell_set_surrogate(ctx->shell, in_mean, in_std, out_mean, out_std);
+    if (st != LBM_OK) return fail(ctx, st, "fsi_set_surrogate: copy failed");
+    ctx->mlp = mlp;
+    ctx->accept_tol = accept_tol;
+    ctx->graph_dirty = true;
+    return LBM_OK;
+  }
+  if (!ctx->fem) return fail(ctx, LBM_ESTATE, "fsi_set_surrogate: couple a beam or a shell first");
   const int nn = fem_nodes(ctx->fem);
   if (mlp_dim(mlp, 0) != surrogate_inputs(nn) || mlp_dim(mlp, mlp_layers(mlp)) != 3 * nn - 3)
     return fail(ctx, LBM_EINVAL,
@@ -693,8 +720,14 @@ lbm_status fsi_set_surrogate(lbm_ctx *ctx, mlp_ctx *mlp, const float *in_mean, c
 lbm_status fsi_get_structure_stats(lbm_ctx *ctx, int stats[4], int reset) {
   GUARD();
   if (!stats) return fail(ctx, LBM_EINVAL, "fsi_get_structure_stats: NULL");
-  if (!ctx->fem) return fail(ctx, LBM_ESTATE, "fsi_get_structure_stats: no beam coupled");
+  if (!ctx->fem && !ctx->shell)
+    return fail(ctx, LBM_ESTATE, "fsi_get_structure_stats: no structure coupled");
   CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->shell) {
+    lbm_status st = shell_get_stats(ctx->shell, stats, reset);
+    if (st != LBM_OK) return fail(ctx, st, "fsi_get_structure_stats: copy failed");
+    return LBM_OK;
+  }
   lbm_status st = fem_get_stats(ctx->fem, stats);
   if (st == LBM_OK && reset) st = fem_reset_stats(ctx->fem);
   if (st != LBM_OK) return fail(ctx, st, "fsi_get_structure_stats: copy failed");

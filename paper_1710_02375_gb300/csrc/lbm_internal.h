@@ -128,5 +128,12 @@ cudaError_t launch_shell_surface(fem_shell_ctx *s, double *surf_x, double *surf_
                                  cudaStream_t st);
 cudaError_t launch_shell_coupled(fem_shell_ctx *s, const double *vforce, double *surf_x,
                                  double *surf_v, int v0, cudaStream_t st);
+int shell_free_dofs(const fem_shell_ctx *s);
+lbm_status shell_set_surrogate(fem_shell_ctx *s, const float *in_mean, const float *in_std,
+                               const float *out_mean, const float *out_std);
+lbm_status shell_get_stats(fem_shell_ctx *s, int *stats, int reset);
+cudaError_t launch_shell_coupled_guess(fem_shell_ctx *s, const double *vforce, double *surf_x,
+                                       double *surf_v, int v0, double accept_tol, mlp_ctx *mlp,
+                                       cudaStream_t st);
 
 }  // namespace kbc

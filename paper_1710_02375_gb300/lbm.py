@@ -236,7 +236,7 @@ def fsi_set_surrogate(ctx, mlp_ctx, in_mean, in_std, out_mean, out_std, accept_t
 
 
 def fsi_get_structure_stats(ctx, reset=False):
-    """(accepted, rejected, newton_solves, steps) of the coupled beam."""
+    """(accepted, rejected, newton_solves, steps) of the coupled beam or shell."""
     st = (ctypes.c_int * 4)()
     _chk(ctx, load().fsi_get_structure_stats(ctx, st, int(bool(reset))))
     return tuple(st)

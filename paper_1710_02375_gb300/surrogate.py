@@ -18,6 +18,12 @@ def input_width(nn):
     return 15 * nn - 15
 
 
+def shell_input_width(nfree):
+    """Network inputs for a shell with nfree free DOFs: three out-of-balance
+    load vectors, the state and the velocities, each on the free DOFs."""
+    return 5 * nfree
+
+
 def normalisation(X, Y, floor=1e-30):
     """Per-feature mean and standard deviation (FP32) of inputs and targets;
     constant features get a unit scale."""
@@ -55,7 +61,8 @@ def train(mlp, X, Y, stats, steps=8000, batch=256, lr=1e-3, seed=0, log_every=0)
 
 
 def attach(lattice, mlp, stats, accept_tol=1e-3):
-    """Use the network as the Newton initial guess of the coupled beam."""
+    """Use the network as the Newton initial guess of the coupled beam or
+    shell."""
     xm, xs, ym, ys = stats
     abi.fsi_set_surrogate(lattice.ctx, mlp.ctx, xm, xs, ym, ys, accept_tol)
 
