@@ -48,37 +48,104 @@ __device__ __forceinline__ int step_axis(int S, int c, int NS, int pad) {
   return s;
 }
 
-// Deviation moments of a node.  D3Q27: sums of the stored values in FP32,
-// returned in the caller's type (FP64 adds are scarce on this part and 27 of
-// them per neighbour dominate the boundary pass).  D2Q9: sums in the caller's
-// type, so that the FP64 boundary path adds the stored values exactly.
+// Knuth's TwoSum: s + e == a + b exactly in round-to-nearest FP32 (the
+// additions are kept in this order: no fast-math, no contraction here).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bv = s - a;
+  e = (a - (s - bv)) + (b - bv);
+}
+
+// Sum of stored FP32 values in the caller's precision.  FP64: cascaded
+// TwoSum with the rounding errors gathered in a second FP32 word (Ogita,
+// Rump and Oishi's Sum2); hi + lo is the sum to within about (n 2^-24)^2 of
+// the sum of magnitudes -- FP64 summation accuracy for a handful of terms --
+// with every add on the FP32 pipes (FP64 instructions are scarce on this
+// part and the boundary pass is bound by them).  FP32: a plain running sum.
+template <typename R>
+struct PopSum {
+  float s = 0.f;
+  __device__ __forceinline__ void add(float x) { s += x; }
+  __device__ __forceinline__ void sub(float x) { s -= x; }
+  __device__ __forceinline__ float value() const { return s; }
+};
+template <>
+struct PopSum<double> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    float t, e;
+    two_sum(hi, x, t, e);
+    hi = t;
+    lo += e;
+  }
+  __device__ __forceinline__ void sub(float x) { add(-x); }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// Per-direction constants for directions known only at run time (the same
+// values as weight<L>, read from constant memory instead of recomputed in
+// FP64): W_i, W_i and 1 / W_i in FP32.
+template <int Q>
+struct DirTab {
+  double w[Q];
+  float wf[Q], iwf[Q];
+  constexpr DirTab() : w(), wf(), iwf() {
+    for (int i = 0; i < Q; ++i) {
+      w[i] = weight<Lat<Q>>(i);
+      wf[i] = (float)w[i];
+      iwf[i] = (float)(1.0 / w[i]);
+    }
+  }
+};
+__constant__ DirTab<9> c_dir9 = DirTab<9>();
+__constant__ DirTab<27> c_dir27 = DirTab<27>();
+template <int Q>
+__device__ __forceinline__ const DirTab<Q> &dir_tab() {
+  if constexpr (Q == 9) return c_dir9;
+  else return c_dir27;
+}
+
+// Deviation moments of a node.  D2Q9 in FP64 (the boundary path): the
+// stored values summed with PopSum<double>.  Otherwise FP32 sums returned in
+// the caller's type (27 FP64 adds per neighbour would dominate the 3-D
+// boundary pass).  Directions with a zero component skip that moment.
 template <int Q, int S, typename R = float>
 __device__ void dev_moments(const Grid &g, const typename Store<S>::T *f, long long k, R &drho,
                             R (&j)[3]) {
   using L = Lat<Q>;
-  using A = typename std::conditional<Q == 9, R, float>::type;
-  A dr = 0, jx = 0, jy = 0, jz = 0;
+  using A = typename std::conditional<Q == 9 && std::is_same<R, double>::value, double, float>::type;
+  PopSum<A> dr, jx, jy, jz;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const A v = (A)Store<S>::load(f + (long long)i * g.N + k, (float)weight<L>(i));
-    dr += v;
-    jx += L::cx(i) * v;
-    jy += L::cy(i) * v;
-    jz += L::cz(i) * v;
+    const float v = Store<S>::load(f + (long long)i * g.N + k, (float)weight<L>(i));
+    dr.add(v);
+    if (L::cx(i) > 0) jx.add(v);
+    if (L::cx(i) < 0) jx.sub(v);
+    if (L::cy(i) > 0) jy.add(v);
+    if (L::cy(i) < 0) jy.sub(v);
+    if (L::cz(i) > 0) jz.add(v);
+    if (L::cz(i) < 0) jz.sub(v);
   }
-  drho = (R)dr;
-  j[0] = (R)jx;
-  j[1] = (R)jy;
-  j[2] = (R)jz;
+  drho = (R)dr.value();
+  j[0] = (R)jx.value();
+  j[1] = (R)jy.value();
+  j[2] = L::D == 3 ? (R)jz.value() : (R)0;
 }
 
+// Velocity (and density) of a node; in FP64 one reciprocal of rho instead of
+// a division per component.
 template <int Q, int S, typename R = float>
 __device__ void dev_velocity(const Grid &g, const typename Store<S>::T *f, long long k, R (&u)[3],
                              R *rho = nullptr) {
   R dr, j[3];
   dev_moments<Q, S, R>(g, f, k, dr, j);
   const R r = (R)1 + dr;
-  for (int a = 0; a < 3; ++a) u[a] = j[a] / r;
+  if constexpr (std::is_same<R, double>::value) {
+    const R ir = (R)1 / r;
+    for (int a = 0; a < 3; ++a) u[a] = j[a] * ir;
+  } else {
+    for (int a = 0; a < 3; ++a) u[a] = j[a] / r;
+  }
   if (rho) *rho = r;
 }
 
@@ -840,6 +907,7 @@ __device__ __forceinline__ void grad_body(int tb, const Grid &g, typename Store<
                                           double *bforce, int nbodies) {
   using L = Lat<Q>;
   using St = Store<S>;
+  constexpr int D = L::D;
   // threads [0, nfixed) take the face nodes, the rest the immersed nodes
   const int t = tb + first;
   int dyn = nbn ? *nbn : 0;
@@ -856,7 +924,7 @@ __device__ __forceinline__ void grad_body(int tb, const Grid &g, typename Store<
     long long src[Q];
     int face_of[Q];
     uint32_t miss = 0;
-    R gk[Q];
+    float gk[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const int Xs = nbr(X, -L::cx(i), g.NX), Ys = nbr(Y, -L::cy(i), g.NY),
@@ -866,7 +934,7 @@ __device__ __forceinline__ void grad_body(int tb, const Grid &g, typename Store<
       face_of[i] = -1;
       gk[i] = 0;
       if (fl == NODE_FLUID) {
-        gk[i] = (R)St::load(f + (long long)i * g.N + src[i], (float)weight<L>(i));
+        gk[i] = St::load(f + (long long)i * g.N + src[i], (float)weight<L>(i));
       } else {
         miss |= 1u << i;
         if (fl == NODE_GHOST) {
@@ -913,22 +981,27 @@ __device__ __forceinline__ void grad_body(int tb, const Grid &g, typename Store<
           if (ax == 0) { fidx = (long long)z * g.ny + y; fn = (long long)g.ny * g.nz; }
           else if (ax == 1) { fidx = (long long)z * g.nx + x; fn = (long long)g.nx * g.nz; }
           else { fidx = (long long)y * g.nx + x; fn = (long long)g.nx * g.ny; }
-          for (int a = 0; a < L::D; ++a)
+          for (int a = 0; a < D; ++a)
             ut[a] = scale * (R)(prof ? prof[a * fn + fidx] : bp.face_u[open_face][a]);
           rho_t = r0;
         } else if (bp.bc[open_face] == BCK_OUTLET) {
-          for (int a = 0; a < 3; ++a) ut[a] = u0[a];
+          for (int a = 0; a < D; ++a) ut[a] = u0[a];
           rho_t = 1;
         } else {
-          for (int a = 0; a < L::D; ++a) ut[a] = bp.face_u[open_face][a];
+          for (int a = 0; a < D; ++a) ut[a] = bp.face_u[open_face][a];
           rho_t = 1;
           zero_grad = true;
         }
       } else {
-        R drt = 0;
-        int m = 0;
+        // known populations and the missing ones' opposites: PopSum; the
+        // wall-velocity terms 6 W_i c_i.u_w: a separate sum in R
+        PopSum<R> pops;
+        R wterm = 0;
         for (int i = 0; i < Q; ++i) {
-          if (!((miss >> i) & 1u)) { drt += gk[i]; continue; }
+          if (!((miss >> i) & 1u)) {
+            pops.add(gk[i]);
+            continue;
+          }
           R q = 0.5, uw[3] = {0, 0, 0};
           if (face_of[i] >= 0) {
             for (int a = 0; a < 3; ++a) uw[a] = bp.face_u[face_of[i]][a];
@@ -943,29 +1016,32 @@ __device__ __forceinline__ void grad_body(int tb, const Grid &g, typename Store<
               }
             }
           }
-          const R cuw = L::cx(i) * uw[0] + L::cy(i) * uw[1] + L::cz(i) * uw[2];
-          drt += (R)St::load(f + (long long)(Q - 1 - i) * g.N + k, (float)weight<L>(i)) +
-                 (R)6 * (R)weight<L>(i) * cuw;
+          const double wi = dir_tab<Q>().w[i];
+          R cuw = L::cx(i) * uw[0] + L::cy(i) * uw[1];
+          if (D == 3) cuw += L::cz(i) * uw[2];
+          pops.add(St::load(f + (long long)(Q - 1 - i) * g.N + k, dir_tab<Q>().wf[i]));
+          wterm += (R)(6.0 * wi) * cuw;
           const int Xn = step_axis(X, L::cx(i), g.NX, g.px), Yn = step_axis(Y, L::cy(i), g.NY, g.py);
           const int Zn = (L::D == 3) ? step_axis(Z, L::cz(i), g.NZ, g.pz) : Z;
           R ui[3] = {uw[0], uw[1], uw[2]};
           if (Xn >= 0 && Yn >= 0 && Zn >= 0 && flags[sidx(g, Xn, Yn, Zn)] == NODE_FLUID) {
             R un[3];
             dev_velocity<Q, S, R>(g, f, sidx(g, Xn, Yn, Zn), un);
-            for (int a = 0; a < 3; ++a) ui[a] = (uw[a] + q * un[a]) / ((R)1 + q);
+            const R iq = (R)1 / ((R)1 + q);
+            for (int a = 0; a < D; ++a) ui[a] = (uw[a] + q * un[a]) * iq;
           }
-          for (int a = 0; a < 3; ++a) ut[a] += ui[a];
-          ++m;
+          for (int a = 0; a < D; ++a) ut[a] += ui[a];
         }
-        for (int a = 0; a < 3; ++a) ut[a] /= (R)nmiss;
-        rho_t = (R)1 + drt;
+        const R inm = (R)1 / (R)nmiss;
+        for (int a = 0; a < D; ++a) ut[a] *= inm;
+        rho_t = (R)1 + ((R)pops.value() + wterm);
       }
       // ---- velocity gradient G[a][b] = d u_a / d x_b (previous step)
       R G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
       if (!zero_grad) {
         R u0[3];
         dev_velocity<Q, S, R>(g, f, k, u0);
-        for (int b = 0; b < L::D; ++b) {
+        for (int b = 0; b < D; ++b) {
           int P1[3] = {X, Y, Z}, M1[3] = {X, Y, Z}, P2[3] = {X, Y, Z}, M2[3] = {X, Y, Z};
           const int NS = b == 0 ? g.NX : (b == 1 ? g.NY : g.NZ);
           const int pad = b == 0 ? g.px : (b == 1 ? g.py : g.pz);
@@ -985,44 +1061,65 @@ __device__ __forceinline__ void grad_body(int tb, const Grid &g, typename Store<
           if (fp && fm) {
             vel(P1, a1);
             vel(M1, a2);
-            for (int a = 0; a < 3; ++a) G[a][b] = (R)0.5 * (a1[a] - a2[a]);
+            for (int a = 0; a < D; ++a) G[a][b] = (R)0.5 * (a1[a] - a2[a]);
           } else if (fp) {
             vel(P1, a1);
             if (fluid(P2)) {
               vel(P2, a2);
-              for (int a = 0; a < 3; ++a) G[a][b] = (R)0.5 * ((R)-3 * u0[a] + (R)4 * a1[a] - a2[a]);
+              for (int a = 0; a < D; ++a) G[a][b] = (R)0.5 * ((R)-3 * u0[a] + (R)4 * a1[a] - a2[a]);
             } else {
-              for (int a = 0; a < 3; ++a) G[a][b] = a1[a] - u0[a];
+              for (int a = 0; a < D; ++a) G[a][b] = a1[a] - u0[a];
             }
           } else if (fm) {
             vel(M1, a1);
             if (fluid(M2)) {
               vel(M2, a2);
-              for (int a = 0; a < 3; ++a) G[a][b] = (R)0.5 * ((R)3 * u0[a] - (R)4 * a1[a] + a2[a]);
+              for (int a = 0; a < D; ++a) G[a][b] = (R)0.5 * ((R)3 * u0[a] - (R)4 * a1[a] + a2[a]);
             } else {
-              for (int a = 0; a < 3; ++a) G[a][b] = u0[a] - a1[a];
+              for (int a = 0; a < D; ++a) G[a][b] = u0[a] - a1[a];
             }
           }
         }
       }
       // ---- Grad's approximation, Eq. (grad)
-      R A[3][3];
+      // A = rho u u + Pi_neq on the lattice's axes; c.A.c and c.u per
+      // direction with the components fixed at compile time (zero
+      // components skipped, unit ones added or subtracted)
+      R A[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
       const R cneq = -rho_t / ((R)6 * (R)bp.beta);
-      for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) A[a][b] = rho_t * ut[a] * ut[b] + cneq * (G[a][b] + G[b][a]);
-      const R trA = A[0][0] + A[1][1] + A[2][2];
+      for (int a = 0; a < D; ++a)
+        for (int b = 0; b < D; ++b) A[a][b] = rho_t * ut[a] * ut[b] + cneq * (G[a][b] + G[b][a]);
+      R trA = A[0][0] + A[1][1];
+      if (D == 3) trA += A[2][2];
+      const R tr3 = trA * (R)(1.0 / 3.0);
+      const R A01 = A[0][1] + A[1][0], A02 = A[0][2] + A[2][0], A12 = A[1][2] + A[2][1];
+      const R r3 = (R)3 * rho_t, rm1 = rho_t - (R)1;
       int l = 0;
+      // D2Q9: unrolled, the components fold at compile time; D3Q27: one
+      // loop body (27 copies would crowd the instruction cache), the
+      // branches on c_i are uniform across the warp
+#pragma unroll(Q == 9 ? 9 : 1)
       for (int i = 0; i < Q; ++i) {
         if (!((miss >> i) & 1u)) continue;
         const int c[3] = {L::cx(i), L::cy(i), L::cz(i)};
-        R cAc = 0;
-        for (int a = 0; a < 3; ++a)
-          for (int b = 0; b < 3; ++b) cAc += c[a] * c[b] * A[a][b];
-        const R cu = c[0] * ut[0] + c[1] * ut[1] + c[2] * ut[2];
-        const float W = (float)weight<L>(i);
-        const R gstar =
-            (R)weight<L>(i) * ((rho_t - (R)1) + (R)3 * rho_t * cu + (R)4.5 * (cAc - trA / (R)3));
-        St::store(f + (long long)i * g.N + src[i], (float)gstar, (float)(1.0 / weight<L>(i)));
+        R cAc = 0, cu = 0;
+        for (int a = 0; a < D; ++a) {
+          if (c[a] != 0) cAc += A[a][a];
+          if (c[a] > 0) cu += ut[a];
+          if (c[a] < 0) cu -= ut[a];
+        }
+        if (c[0] * c[1] > 0) cAc += A01;
+        if (c[0] * c[1] < 0) cAc -= A01;
+        if (D == 3) {
+          if (c[0] * c[2] > 0) cAc += A02;
+          if (c[0] * c[2] < 0) cAc -= A02;
+          if (c[1] * c[2] > 0) cAc += A12;
+          if (c[1] * c[2] < 0) cAc -= A12;
+        }
+        const DirTab<Q> &dt = dir_tab<Q>();
+        const float W = dt.wf[i];
+        const R gstar = (R)dt.w[i] * (rm1 + r3 * cu + (R)4.5 * (cAc - tr3));
+        St::store(f + (long long)i * g.N + src[i], (float)gstar, dt.iwf[i]);
         if (face_of[i] < 0) {
           // momentum exchange on the immersed surface, FP64 accumulation
           while (l < bn.nlink && links[bn.link0 + l].i != i) ++l;
@@ -1032,9 +1129,10 @@ __device__ __forceinline__ void grad_body(int tb, const Grid &g, typename Store<
               const double gop = (double)St::load(f + (long long)(Q - 1 - i) * g.N + k, W);
               // gauge form: the rest state f = W (ambient pressure) is taken out
               const double fsum = gop + (double)(float)gstar;
-              for (int a = 0; a < L::D; ++a) {
-                const double Fa = -(double)c[a] * fsum;
-                for (int m = 0; m < L::D; ++m)
+              for (int a = 0; a < D; ++a) {
+                if (c[a] == 0) continue;
+                const double Fa = c[a] > 0 ? -fsum : fsum;
+                for (int m = 0; m < D; ++m)
                   atomicAdd(&vforce[3 * lk.v[m] + a], (double)lk.vw[m] * Fa);
                 if (lk.body == my_body || my_body < 0) {
                   my_body = lk.body;
