@@ -21,8 +21,10 @@
 
 namespace kbc {
 
-// One node (interior coordinates x, y, z) of the fused sweep.
-template <int Q, int S, bool FLAGS>
+// One node (interior coordinates x, y, z) of the fused sweep.  IX: index
+// type of the population offsets (32-bit when Q N < 2^31: fewer address
+// instructions per load and store).
+template <int Q, int S, bool FLAGS, typename IX = long long>
 __device__ __forceinline__ void sweep_node(const Grid &g,
                                            const typename Store<S>::T *__restrict__ fin,
                                            typename Store<S>::T *__restrict__ fout,
@@ -31,7 +33,7 @@ __device__ __forceinline__ void sweep_node(const Grid &g,
   using L = Lat<Q>;
   using St = Store<S>;
   const int X = x + g.px, Y = y + g.py, Z = z + g.pz;
-  const long long k = sidx(g, X, Y, Z);
+  const IX k = (IX)sidx(g, X, Y, Z);
   if (FLAGS && flags[k] != NODE_FLUID) return;
 
   const int xs[3] = {nbr(X, 1, g.NX), X, nbr(X, -1, g.NX)};  // source x for cx = -1, 0, +1
@@ -42,21 +44,30 @@ __device__ __forceinline__ void sweep_node(const Grid &g,
     zs[2] = nbr(Z, -1, g.NZ);
   }
   float v[Q];
+  const IX N = (IX)g.N;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const long long src = ((long long)zs[L::cz(i) + 1] * g.NY + ys[L::cy(i) + 1]) * g.pitch +
-                          xs[L::cx(i) + 1];
-    v[i] = St::load(fin + (long long)i * g.N + src, (float)weight<L>(i));
+    const IX src = ((IX)zs[L::cz(i) + 1] * (IX)g.NY + (IX)ys[L::cy(i) + 1]) * (IX)g.pitch +
+                   (IX)xs[L::cx(i) + 1];
+    v[i] = St::load(fin + ((IX)i * N + src), (float)weight<L>(i));
   }
   const float rho = collide<L, S == STORE_F32>(v, beta, bgk != 0);
   if (!(rho > 0.f && rho < 1e30f)) atomicOr(err, 1);
-  typename St::T *po = fout + k;
 #pragma unroll
-  for (int i = 0; i < Q; ++i, po += g.N) St::store(po, v[i], (float)(1.0 / weight<L>(i)));
+  for (int i = 0; i < Q; ++i) St::store(fout + ((IX)i * N + k), v[i], (float)(1.0 / weight<L>(i)));
 }
 
-template <int Q, int S, bool FLAGS>
-__global__ void __launch_bounds__(128, KBC_MIN_CTAS)
+// Resident CTAs per SM for the direct sweep, measured on the periodic 128^3
+// D3Q27 lattice: FP32 storage 5 / 6 / 7 / 8 CTAs -> 84.6 / 81.9 / 84.4 /
+// 88.8 us per sweep (6: 80 registers, a few bytes of spills to L1); 16-bit
+// storage 72.0 / 69.6 / 68.7 / 70.5 us.
+template <int Q, int S>
+struct SweepOcc {
+  static constexpr int ctas = (Q == 27 && S != STORE_F32) ? 7 : 6;
+};
+
+template <int Q, int S, bool FLAGS, typename IX>
+__global__ void __launch_bounds__(128, SweepOcc<Q, S>::ctas)
     k_sweep(Grid g, const typename Store<S>::T *__restrict__ fin,
             typename Store<S>::T *__restrict__ fout, const uint8_t *__restrict__ flags,
             float beta, int bgk, int *__restrict__ err) {
@@ -64,7 +75,7 @@ __global__ void __launch_bounds__(128, KBC_MIN_CTAS)
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
   if (x >= g.nx || y >= g.ny) return;
-  sweep_node<Q, S, FLAGS>(g, fin, fout, flags, beta, bgk, err, x, y, z);
+  sweep_node<Q, S, FLAGS, IX>(g, fin, fout, flags, beta, bgk, err, x, y, z);
 }
 
 
@@ -388,10 +399,17 @@ static cudaError_t sweep_t(const Grid &g, const void *fin, void *fout, const uin
   }
   dim3 b = sweep_block(g);
   dim3 grid((g.nx + b.x - 1) / b.x, (g.ny + b.y - 1) / b.y, g.nz);
-  if (flags)
-    k_sweep<Q, S, true><<<grid, b, 0, s>>>(g, (const T *)fin, (T *)fout, flags, beta, bgk, err);
+  const bool narrow = (long long)Q * g.N < (1LL << 31);  // every offset fits an int
+  if (flags && narrow)
+    k_sweep<Q, S, true, int><<<grid, b, 0, s>>>(g, (const T *)fin, (T *)fout, flags, beta, bgk, err);
+  else if (flags)
+    k_sweep<Q, S, true, long long><<<grid, b, 0, s>>>(g, (const T *)fin, (T *)fout, flags, beta, bgk,
+                                                      err);
+  else if (narrow)
+    k_sweep<Q, S, false, int><<<grid, b, 0, s>>>(g, (const T *)fin, (T *)fout, flags, beta, bgk, err);
   else
-    k_sweep<Q, S, false><<<grid, b, 0, s>>>(g, (const T *)fin, (T *)fout, flags, beta, bgk, err);
+    k_sweep<Q, S, false, long long><<<grid, b, 0, s>>>(g, (const T *)fin, (T *)fout, flags, beta, bgk,
+                                                       err);
   return cudaGetLastError();
 }
 
