@@ -359,6 +359,9 @@ def run_c4(args):
     group = [c4_lattice(i, coupled, stream) for i in insts]
     B = Batch([L for L, _ in group])
     B.step(args.warmup)
+    # the autotuner picks the sweep's tile height and resident CTAs per SM
+    # (its trial steps advance the ensemble; they are not timed here)
+    rows, ctas, _ = B.autotune(steps=4)
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     time.sleep(0.3)
@@ -381,6 +384,7 @@ def run_c4(args):
         "individual": {"ms_per_step": ms_solo, "value": nodes / (ms_solo * 1e-3) / 1e6,
                        "steps": k_solo},
         "speedup_vs_individual": ms_solo / ms,
+        "tuning": {"rows_per_tile": rows, "ctas_per_sm": ctas},
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)

@@ -326,7 +326,9 @@ lbm_status lbm_batch_create(lbm_ctx *const *ctxs, int n, void *workspace, size_t
 lbm_status lbm_batch_step(lbm_batch *b, int n);
 /* n * repeats steps by replaying a CUDA graph of n batched steps (n even). */
 lbm_status lbm_batch_step_graph(lbm_batch *b, int n, int repeats);
-/* Tile height (rows per tile, 1..64) and resident CTAs per SM of the sweep. */
+/* Tile height (rows per tile, 1..64) and resident CTAs per SM of the sweep.
+ * Defaults: 5 CTAs per SM; D2Q9 4 rows (gathered together by each
+ * thread), D3Q27 1 row. */
 lbm_status lbm_batch_set_tuning(lbm_batch *b, int rows_per_tile, int ctas_per_sm);
 /* Times every (rows per tile, CTAs per SM) candidate over `steps` batched
  * steps and keeps the fastest; the trial steps advance the simulation. */

@@ -59,6 +59,7 @@ struct InstDesc {
   float beta;
   int bgk;
   int *err;
+  int narrow;             // Q N < 2^31: 32-bit population offsets in the sweep
   // boundary fill and force
   BNode *bnodes;          // face nodes, then immersed nodes
   int *nbn;               // immersed node counter (nullptr: no bodies)

@@ -16,10 +16,11 @@
 //
 // One CTA per beam.  Matrices are banded (node-major DOFs: half bandwidth 5)
 // in shared memory; element loops run in two colour passes (even, odd
-// elements) so no two threads add into the same entries; the banded LU
-// (no pivoting: the mass term keeps J diagonally dominant at these steps)
-// runs on one warp in FP32 (an inexact Newton step: residual, stopping test
-// and state stay FP64).
+// elements) so no two threads add into the same entries; the Newton system
+// (block tridiagonal in the 3 x 3 node blocks; no pivoting: the mass term
+// keeps J diagonally dominant at these steps) is solved by block elimination
+// on one thread in FP32 registers (an inexact Newton step: residual,
+// stopping test and state stay FP64).
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -39,6 +40,9 @@ constexpr int kMaxN = 3 * kMaxBeamNodes, kMaxE = kMaxBeamNodes - 1;
 
 __device__ __forceinline__ double &band(double *A, int i, int j) { return A[i * BW + (j - i + KB)]; }
 __device__ __forceinline__ float &bandf(float *A, int i, int j) { return A[i * BW + (j - i + KB)]; }
+__device__ __forceinline__ float bandf(const float *__restrict__ A, int i, int j) {
+  return A[i * BW + (j - i + KB)];
+}
 
 __device__ void element_geom(const BeamParams &p, const double *X, const double *u, int a,
                              double &L0, double &L, double &c, double &s, double &rot) {
@@ -158,7 +162,7 @@ __device__ void flag_vertex(const BeamParams &p, const double *X, const double *
 // occupies the FP64 pipe for many cycles, so the step is organised to keep
 // FP64 instruction counts per warp low -- element scalars once per element,
 // internal forces and tangent entries spread over the CTA, the tangent and
-// the banded factorisation (one lane per update entry) in FP32.
+// the block-tridiagonal solve in FP32.
 
 // Upper-triangle index pairs (k <= l) of a 6 x 6 element matrix.
 __constant__ unsigned char c_pk[21] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 2, 2, 2, 2, 3, 3, 3, 4, 4, 5};
@@ -183,11 +187,94 @@ __device__ __forceinline__ float elem_zf(int k, float c, float s) {
   return k < 3 ? v : -v;
 }
 
+// J x = rhs for the block-tridiagonal J of the node-major beam DOFs (3 x 3
+// blocks D_i, L_i = J[i][i-1], U_i = J[i][i+1], read from band storage):
+// block elimination (Thomas' algorithm with 3 x 3 blocks, no pivoting: the
+// mass term keeps the diagonal blocks well conditioned) on one thread in
+// FP32 registers, W_i = S_i^-1 U_i kept in Wsc for the back substitution.
+// x overwrites rhs.
+__device__ __forceinline__ void block_thomas(const float *__restrict__ J, float *__restrict__ rhs,
+                                             float *__restrict__ Wsc, int nn) {
+  float Wp[9], gp[3];
+  for (int q = 0; q < 9; ++q) Wp[q] = 0.f;
+  gp[0] = gp[1] = gp[2] = 0.f;
+  for (int i = 0; i < nn; ++i) {
+    const int r0 = 3 * i;
+    float S[9], b[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      b[a] = rhs[r0 + a];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) S[3 * a + c] = bandf(J, r0 + a, r0 + c);
+    }
+    if (i > 0) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        float L[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) L[c] = bandf(J, r0 + a, r0 - 3 + c);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          S[3 * a + c] -= L[0] * Wp[c] + L[1] * Wp[3 + c] + L[2] * Wp[6 + c];
+        b[a] -= L[0] * gp[0] + L[1] * gp[1] + L[2] * gp[2];
+      }
+    }
+    // S^-1 by the adjugate
+    float A[9];
+    A[0] = S[4] * S[8] - S[5] * S[7];
+    A[1] = S[2] * S[7] - S[1] * S[8];
+    A[2] = S[1] * S[5] - S[2] * S[4];
+    A[3] = S[5] * S[6] - S[3] * S[8];
+    A[4] = S[0] * S[8] - S[2] * S[6];
+    A[5] = S[2] * S[3] - S[0] * S[5];
+    A[6] = S[3] * S[7] - S[4] * S[6];
+    A[7] = S[1] * S[6] - S[0] * S[7];
+    A[8] = S[0] * S[4] - S[1] * S[3];
+    const float idet = __frcp_rn(S[0] * A[0] + S[1] * A[3] + S[2] * A[6]);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) A[q] *= idet;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      gp[a] = A[3 * a] * b[0] + A[3 * a + 1] * b[1] + A[3 * a + 2] * b[2];
+      rhs[r0 + a] = gp[a];
+    }
+    if (i + 1 < nn) {
+      float U[9];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) U[3 * a + c] = bandf(J, r0 + a, r0 + 3 + c);
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          Wp[3 * a + c] = A[3 * a] * U[c] + A[3 * a + 1] * U[3 + c] + A[3 * a + 2] * U[6 + c];
+          Wsc[9 * i + 3 * a + c] = Wp[3 * a + c];
+        }
+    }
+  }
+  float xn[3] = {rhs[3 * nn - 3], rhs[3 * nn - 2], rhs[3 * nn - 1]};
+  for (int i = nn - 2; i >= 0; --i) {
+    float x[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float *w = Wsc + 9 * i + 3 * a;
+      x[a] = rhs[3 * i + a] - (w[0] * xn[0] + w[1] * xn[1] + w[2] * xn[2]);
+      rhs[3 * i + a] = x[a];
+    }
+    xn[0] = x[0];
+    xn[1] = x[1];
+    xn[2] = x[2];
+  }
+}
+
 struct BeamShared {
   float J[kMaxN * BW], MJ[kMaxN * BW];  // Newton matrix (FP32), its mass part
   double M[kMaxN * BW];
   double u[kMaxN], u0[kMaxN], v0[kMaxN], f0[kMaxN], F1[kMaxN], R[kMaxN], D[kMaxN];
-  float rhs[kMaxN], inv[kMaxN];
+  double Rc[kMaxN];         // load part of the residual, theta F1 + (1 - theta)(F0 - f(u0))
+  unsigned char fx[kMaxN];  // Dirichlet mask
+  float rhs[kMaxN], W[kMaxBeamNodes * 9];
   double X[2 * kMaxBeamNodes];
   // element scalars: constants of the step, then the current state's
   double L0[kMaxE], b0[kMaxE], EAL0[kMaxE], k2[kMaxE];
@@ -262,7 +349,7 @@ __device__ __forceinline__ void beam_step_body(const BeamParams &p, const BeamDe
                                                const double *__restrict__ vforce, double *surf_x,
                                                double *surf_v, int v0) {
   __shared__ BeamShared S;
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+  const int tid = threadIdx.x, nt = blockDim.x;
   const int nn = p.nn, n = 3 * nn, ne = nn - 1;
   const double a_v = 1.0 / (p.theta * p.dt), i_th = 1.0 / p.theta, i_dt = 1.0 / p.dt;
   const double cM = 1.0 / (p.theta * p.dt * p.dt);
@@ -307,8 +394,12 @@ __device__ __forceinline__ void beam_step_body(const BeamParams &p, const BeamDe
   __syncthreads();
   double fe2 = 0.0;
   for (int i = tid; i < n; i += nt) {
-    S.f0[i] = dof_internal(S, i, ne);
-    const double fe = d.fixed[i] ? 0.0 : p.theta * S.F1[i] + (1.0 - p.theta) * d.F0[i];
+    const double f0 = dof_internal(S, i, ne), F0 = d.F0[i];
+    const bool fixed = d.fixed[i] != 0;
+    S.f0[i] = f0;
+    S.fx[i] = fixed;
+    S.Rc[i] = p.theta * S.F1[i] + (1.0 - p.theta) * (F0 - f0);
+    const double fe = fixed ? 0.0 : p.theta * S.F1[i] + (1.0 - p.theta) * F0;
     fe2 += fe * fe;
   }
   __syncthreads();
@@ -340,8 +431,8 @@ __device__ __forceinline__ void beam_step_body(const BeamParams &p, const BeamDe
       for (int j = (i - KB > 0 ? i - KB : 0); j <= (i + KB < n - 1 ? i + KB : n - 1); ++j)
         mv += band(S.M, i, j) * S.D[j];
       const double f = dof_internal(S, i, ne);
-      double R = mv * i_dt - p.theta * (S.F1[i] - f) - (1.0 - p.theta) * (d.F0[i] - S.f0[i]);
-      if (d.fixed[i]) R = 0.0;
+      double R = mv * i_dt + p.theta * f - S.Rc[i];
+      if (S.fx[i]) R = 0.0;
       S.rhs[i] = (float)-R;  // right-hand side of J du = -R
       part += R * R;
     }
@@ -364,7 +455,7 @@ __device__ __forceinline__ void beam_step_body(const BeamParams &p, const BeamDe
     // rows / columns, and the solve of J du = -R in FP32: an inexact Newton
     // step (relative error ~1e-6 on this diagonally dominant J) while the
     // residual and its stopping test stay FP64, so the converged state
-    // meets the same FP64 test; FP32 keeps the serial factorisation chain
+    // meets the same FP64 test; FP32 keeps the serial elimination chain
     // off GB300's scarce FP64 pipe
     for (int i = tid; i < n * BW; i += nt) S.J[i] = S.MJ[i];
     __syncthreads();
@@ -390,35 +481,10 @@ __device__ __forceinline__ void beam_step_body(const BeamParams &p, const BeamDe
     }
     for (int idx = tid; idx < n * BW; idx += nt) {
       const int i = idx / BW, j = i + idx % BW - KB;
-      if (j >= 0 && j < n && (d.fixed[i] || d.fixed[j])) S.J[idx] = (i == j) ? 1.f : 0.f;
+      if (j >= 0 && j < n && (S.fx[i] || S.fx[j])) S.J[idx] = (i == j) ? 1.f : 0.f;
     }
     __syncthreads();
-    if (tid < 32) {
-      // banded LU without pivoting (Doolittle) on J du = -R: one lane per
-      // entry of the KB x KB trailing update and of the KB right-hand sides
-      const int r = lane < 25 ? lane / 5 + 1 : lane - 24, c = lane < 25 ? lane % 5 + 1 : 0;
-      for (int k = 0; k < n; ++k) {
-        const float inv = __frcp_rn(bandf(S.J, k, k));
-        if (lane < 30 && k + r < n) {
-          const float m = bandf(S.J, k + r, k) * inv;
-          if (lane < 25) {
-            if (k + c < n) bandf(S.J, k + r, k + c) -= m * bandf(S.J, k, k + c);
-          } else {
-            S.rhs[k + r] -= m * S.rhs[k];
-          }
-        }
-        if (lane == 0) S.inv[k] = inv;
-        __syncwarp();
-      }
-      if (lane == 0) {
-        for (int k = n - 1; k >= 0; --k) {
-          float sum = S.rhs[k];
-          const int jend = (k + KB < n - 1) ? k + KB : n - 1;
-          for (int j = k + 1; j <= jend; ++j) sum -= bandf(S.J, k, j) * S.rhs[j];
-          S.rhs[k] = sum * S.inv[k];
-        }
-      }
-    }
+    if (tid == 0) block_thomas(S.J, S.rhs, S.W, nn);
     __syncthreads();
     for (int i = tid; i < n; i += nt) S.u[i] += p.lambda * (double)S.rhs[i];
     __syncthreads();

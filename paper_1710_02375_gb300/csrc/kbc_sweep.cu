@@ -21,6 +21,40 @@
 
 namespace kbc {
 
+// Pull of the Q populations of stored node (X, Y, Z) from their sources
+// (X - c_i), and the store of the post-collision values at stored index k.
+template <int Q, int S, typename IX>
+__device__ __forceinline__ void sweep_gather(const Grid &g,
+                                             const typename Store<S>::T *__restrict__ fin, int X,
+                                             int Y, int Z, float (&v)[Q]) {
+  using L = Lat<Q>;
+  using St = Store<S>;
+  const int xs[3] = {nbr(X, 1, g.NX), X, nbr(X, -1, g.NX)};  // source x for cx = -1, 0, +1
+  const int ys[3] = {nbr(Y, 1, g.NY), Y, nbr(Y, -1, g.NY)};
+  int zs[3] = {Z, Z, Z};
+  if (L::D == 3) {
+    zs[0] = nbr(Z, 1, g.NZ);
+    zs[2] = nbr(Z, -1, g.NZ);
+  }
+  const IX N = (IX)g.N;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const IX src = ((IX)zs[L::cz(i) + 1] * (IX)g.NY + (IX)ys[L::cy(i) + 1]) * (IX)g.pitch +
+                   (IX)xs[L::cx(i) + 1];
+    v[i] = St::load(fin + ((IX)i * N + src), (float)weight<L>(i));
+  }
+}
+
+template <int Q, int S, typename IX>
+__device__ __forceinline__ void sweep_scatter(const Grid &g, typename Store<S>::T *__restrict__ fout,
+                                              IX k, const float (&v)[Q]) {
+  using L = Lat<Q>;
+  using St = Store<S>;
+  const IX N = (IX)g.N;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) St::store(fout + ((IX)i * N + k), v[i], (float)(1.0 / weight<L>(i)));
+}
+
 // One node (interior coordinates x, y, z) of the fused sweep.  IX: index
 // type of the population offsets (32-bit when Q N < 2^31: fewer address
 // instructions per load and store).
@@ -35,26 +69,11 @@ __device__ __forceinline__ void sweep_node(const Grid &g,
   const int X = x + g.px, Y = y + g.py, Z = z + g.pz;
   const IX k = (IX)sidx(g, X, Y, Z);
   if (FLAGS && flags[k] != NODE_FLUID) return;
-
-  const int xs[3] = {nbr(X, 1, g.NX), X, nbr(X, -1, g.NX)};  // source x for cx = -1, 0, +1
-  const int ys[3] = {nbr(Y, 1, g.NY), Y, nbr(Y, -1, g.NY)};
-  int zs[3] = {Z, Z, Z};
-  if (L::D == 3) {
-    zs[0] = nbr(Z, 1, g.NZ);
-    zs[2] = nbr(Z, -1, g.NZ);
-  }
   float v[Q];
-  const IX N = (IX)g.N;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const IX src = ((IX)zs[L::cz(i) + 1] * (IX)g.NY + (IX)ys[L::cy(i) + 1]) * (IX)g.pitch +
-                   (IX)xs[L::cx(i) + 1];
-    v[i] = St::load(fin + ((IX)i * N + src), (float)weight<L>(i));
-  }
+  sweep_gather<Q, S, IX>(g, fin, X, Y, Z, v);
   const float rho = collide<L, S == STORE_F32>(v, beta, bgk != 0);
   if (!(rho > 0.f && rho < 1e30f)) atomicOr(err, 1);
-#pragma unroll
-  for (int i = 0; i < Q; ++i) St::store(fout + ((IX)i * N + k), v[i], (float)(1.0 / weight<L>(i)));
+  sweep_scatter<Q, S, IX>(g, fout, k, v);
 }
 
 // Resident CTAs per SM for the direct sweep, measured on the periodic 128^3
@@ -335,6 +354,36 @@ static cudaError_t sweep_async_t(const Grid &g, const void *fin, void *fout, con
 // from an atomic ticket until the list is exhausted; lattices of any shape
 // share one launch.  Block 0 also advances every lattice's inlet-ramp clock
 // (this kernel runs after the boundary fill of the step).
+// Up to R consecutive interior rows (r0 .. r0 + m - 1) of one x column:
+// every row's populations are gathered before the first collision, so a
+// thread keeps R nodes' loads in flight (the D2Q9 node has little arithmetic
+// to hide a load's latency behind).
+template <int Q, int S, int R>
+__device__ __forceinline__ void sweep_rows(const Grid &g, const typename Store<S>::T *__restrict__ fin,
+                                           typename Store<S>::T *__restrict__ fout,
+                                           const uint8_t *__restrict__ flags, float beta, int bgk,
+                                           int *__restrict__ err, int x, int r0, int m) {
+  using L = Lat<Q>;
+  float v[R][Q];
+  int k[R];
+  bool live[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const int r = r0 + q;
+    const int X = x + g.px, Y = r % g.ny + g.py, Z = r / g.ny + g.pz;
+    k[q] = (int)sidx(g, X, Y, Z);
+    live[q] = q < m && flags[k[q]] == NODE_FLUID;
+    if (live[q]) sweep_gather<Q, S, int>(g, fin, X, Y, Z, v[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    if (!live[q]) continue;
+    const float rho = collide<L, S == STORE_F32>(v[q], beta, bgk != 0);
+    if (!(rho > 0.f && rho < 1e30f)) atomicOr(err, 1);
+    sweep_scatter<Q, S, int>(g, fout, k[q], v[q]);
+  }
+}
+
 template <int Q, int S>
 __global__ void __launch_bounds__(128, KBC_MIN_CTAS)
     k_sweep_batch(const InstDesc *__restrict__ d, int n, const int4 *__restrict__ tiles,
@@ -357,10 +406,16 @@ __global__ void __launch_bounds__(128, KBC_MIN_CTAS)
     const int x = tl.z * 128 + threadIdx.x;
     const int nrows = b.g.ny * b.g.nz;
     const int rend = min(tl.y + rows_per_tile, nrows);
-    if (x < b.g.nx)
-      for (int r = tl.y; r < rend; ++r)
-        sweep_node<Q, S, true>(b.g, fin, fout, b.flags, b.beta, b.bgk, b.err, x, r % b.g.ny,
-                               r / b.g.ny);
+    if (x < b.g.nx) {
+      if (Q == 9 && b.narrow) {
+        for (int r = tl.y; r < rend; r += 4)
+          sweep_rows<Q, S, 4>(b.g, fin, fout, b.flags, b.beta, b.bgk, b.err, x, r, rend - r);
+      } else {
+        for (int r = tl.y; r < rend; ++r)
+          sweep_node<Q, S, true>(b.g, fin, fout, b.flags, b.beta, b.bgk, b.err, x, r % b.g.ny,
+                                 r / b.g.ny);
+      }
+    }
   }
 }
 

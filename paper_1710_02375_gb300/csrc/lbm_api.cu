@@ -1015,6 +1015,7 @@ lbm_status lbm_batch_create(lbm_ctx *const *ctxs, int n, void *workspace, size_t
   b->ctx.assign(ctxs, ctxs + n);
   b->Q = ctxs[0]->Q;
   b->storage = ctxs[0]->cfg.storage;
+  if (b->Q == 9) b->rows_per_tile = 4;  // D2Q9: the sweep gathers 4 rows together
   b->stream = ctxs[0]->stream;
   const BatchLayout L = batch_layout(ctxs, n);
   if (workspace) {
@@ -1053,6 +1054,7 @@ lbm_status lbm_batch_create(lbm_ctx *const *ctxs, int n, void *workspace, size_t
     d.beta = (float)c->cfg.beta;
     d.bgk = c->cfg.collision == LBM_COLLIDE_BGK;
     d.err = c->err;
+    d.narrow = (long long)c->Q * c->g.N < (1LL << 31);
     d.bnodes = (BNode *)(c->ws + c->lay.bnodes);
     d.nbn = c->nbodies > 0 ? c->counters : nullptr;
     d.nfixed = c->nface;
