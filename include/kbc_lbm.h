@@ -245,8 +245,10 @@ void fem_destroy(fem_ctx *f);
  * projector; lumped mass.  Theta-scheme (Eq. timeInt), Newton with the
  * constant relaxation lambda (stop at |R| <= rtol |R0| + atol, R0 the
  * residual at the step's start), linearised systems by Jacobi-preconditioned
- * conjugate gradients to cg_rtol (0: 1e-13) within max_cg iterations (0:
- * 4 x DOFs); one cooperative launch per step.
+ * conjugate gradients to cg_rtol (0: 1e-3, an inexact Newton step; the
+ * residual and its stopping test stay FP64, and with lambda = 0.7 the
+ * Newton count is the same as with exact solves) within max_cg iterations
+ * (0: 4 x DOFs); one cooperative launch per step.
  * ------------------------------------------------------------------------- */
 typedef struct fem_shell_ctx fem_shell_ctx;
 typedef struct {

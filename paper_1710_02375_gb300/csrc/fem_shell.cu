@@ -89,11 +89,11 @@ __device__ void quad_frame_dev(const double *xs, double *Re, double *c) {
   }
   double e3[3] = {d13[1] * d24[2] - d13[2] * d24[1], d13[2] * d24[0] - d13[0] * d24[2],
                   d13[0] * d24[1] - d13[1] * d24[0]};
-  const double in3 = 1.0 / sqrt(e3[0] * e3[0] + e3[1] * e3[1] + e3[2] * e3[2]);
+  const double in3 = rsqrt(e3[0] * e3[0] + e3[1] * e3[1] + e3[2] * e3[2]);
   for (int k = 0; k < 3; ++k) e3[k] *= in3;
   const double ad = a[0] * e3[0] + a[1] * e3[1] + a[2] * e3[2];
   double e1[3] = {a[0] - ad * e3[0], a[1] - ad * e3[1], a[2] - ad * e3[2]};
-  const double in1 = 1.0 / sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+  const double in1 = rsqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
   for (int k = 0; k < 3; ++k) e1[k] *= in1;
   const double e2[3] = {e3[1] * e1[2] - e3[2] * e1[1], e3[2] * e1[0] - e3[0] * e1[2],
                         e3[0] * e1[1] - e3[1] * e1[0]};
@@ -113,8 +113,11 @@ __device__ void rodrigues(const double *phi, double *Rm) {
     s1 = 1.0 - t2 / 6.0;
     s2 = 0.5 - t2 / 24.0;
   } else {
-    s1 = sin(t) / t;
-    s2 = (1.0 - cos(t)) / t2;
+    // sin and cos from one call; 1 - cos t = sin^2 t / (1 + cos t) (t < pi)
+    double st, ct;
+    sincos(t, &st, &ct);
+    s1 = st / t;
+    s2 = s1 * s1 / (1.0 + ct);
   }
   const double x = phi[0], y = phi[1], z = phi[2];
   // I + s1 S + s2 S^2 with S^2 = phi phi^T - t2 I
@@ -124,14 +127,18 @@ __device__ void rodrigues(const double *phi, double *Rm) {
 }
 
 // Rotation vector of Rm (angle below pi).
+// w = (R32 - R23, R13 - R31, R21 - R12) = 2 sin(t) n and cos(t) = (tr R - 1) / 2,
+// so t = atan2(|w| / 2, cos t) and phi = t w / |w| (one atan2 instead of an
+// acos and a sin; accurate at small angles, where acos is not).
 __device__ void rotvec(const double *Rm, double *phi) {
-  double ct = 0.5 * (Rm[0] + Rm[4] + Rm[8] - 1.0);
-  ct = fmin(1.0, fmax(-1.0, ct));
-  const double t = acos(ct);
-  const double g = (t < 1e-6) ? 0.5 + t * t / 12.0 : 0.5 * t / sin(t);
-  phi[0] = g * (Rm[7] - Rm[5]);
-  phi[1] = g * (Rm[2] - Rm[6]);
-  phi[2] = g * (Rm[3] - Rm[1]);
+  const double ct = 0.5 * (Rm[0] + Rm[4] + Rm[8] - 1.0);
+  const double w[3] = {Rm[7] - Rm[5], Rm[2] - Rm[6], Rm[3] - Rm[1]};
+  const double sw = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+  const double t = atan2(0.5 * sw, ct);
+  const double g = (sw < 1e-12) ? 0.5 + t * t / 12.0 : t / sw;
+  phi[0] = g * w[0];
+  phi[1] = g * w[1];
+  phi[2] = g * w[2];
 }
 
 // ---------------------------------------------------------------- set-up
@@ -302,17 +309,19 @@ __device__ __forceinline__ void warp_projector(ShellWarp &W, int lane) {
     }
     W.U[i][k] = val;
   }
+  // one reciprocal of N and of ap per warp instead of a division per entry
+  const double iN = 1.0 / W.gc[4], iap = 1.0 / W.gc[5];
   for (int w = lane; w < 144; w += 32) {
     const int k = w / 24, j = w % 24, b = j / 6, s = j % 6;
-    const double a1 = W.gc[0], a2 = W.gc[1], b1 = W.gc[2], b2 = W.gc[3], Nn = W.gc[4], ap = W.gc[5];
+    const double a1 = W.gc[0], a2 = W.gc[1], b1 = W.gc[2], b2 = W.gc[3];
     double val = 0.0;
     if (k < 3) {
       val = (s == k) ? 0.25 : 0.0;
     } else {
       // frame spin: x and y tilts from the diagonals, z from the sides
-      if (k == 3 && s == 2) val = (b == 2 ? -b1 : b == 0 ? b1 : b == 3 ? a1 : -a1) / Nn;
-      if (k == 4 && s == 2) val = (b == 2 ? -b2 : b == 0 ? b2 : b == 3 ? a2 : -a2) / Nn;
-      if (k == 5 && s == 1) val = (b == 1 || b == 2 ? 1.0 : -1.0) / ap;
+      if (k == 3 && s == 2) val = (b == 2 ? -b1 : b == 0 ? b1 : b == 3 ? a1 : -a1) * iN;
+      if (k == 4 && s == 2) val = (b == 2 ? -b2 : b == 0 ? b2 : b == 3 ? a2 : -a2) * iN;
+      if (k == 5 && s == 1) val = (b == 1 || b == 2 ? iap : -iap);
     }
     W.V[k][j] = val;
   }
@@ -985,7 +994,7 @@ lbm_status fem_shell_create(const fem_shell_config *c, void *workspace, size_t b
   p.theta = c->theta; p.lambda = c->lambda; p.rtol = c->rtol; p.atol = c->atol; p.dt = c->dt;
   p.max_it = c->max_it;
   p.max_cg = c->max_cg > 0 ? c->max_cg : 4 * p.n;
-  p.cg_rtol = c->cg_rtol > 0 ? c->cg_rtol : 1e-13;
+  p.cg_rtol = c->cg_rtol > 0 ? c->cg_rtol : 1e-3;
   cudaError_t e = cudaMemsetAsync(s->ws, 0, need, s->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync((void *)s->d.X, c->X, sizeof(double) * 3 * p.nn, cudaMemcpyDefault, s->stream);
