@@ -427,7 +427,11 @@ lbm_status lbm_set_traction_output(lbm_ctx *ctx, int enable);
 lbm_status lbm_get_traction_force(lbm_ctx *ctx, double *vert_force, double *body_force);
 
 /* Density rho[nz][ny][nx] and velocity u[dim][nz][ny][nx] of the current
- * state (FP64 outputs; solid nodes give rho = 0, u = 0).  Synchronises. */
+ * state (FP64 outputs; solid nodes give rho = 0, u = 0).  Synchronises.
+ * Field arrays of lbm_init_equilibrium / lbm_get_macros may be device
+ * memory, page-locked host memory (cudaHostAlloc, cudaHostRegister; the
+ * kernel reads or writes it in place over the host link, no staging copy)
+ * or pageable host memory (staged through the workspace in chunks). */
 lbm_status lbm_get_macros(lbm_ctx *ctx, double *rho, double *u);
 
 /* Kernel form of the fused sweep.  AUTO (default) and DIRECT: one thread per

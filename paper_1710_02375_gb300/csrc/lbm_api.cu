@@ -199,6 +199,18 @@ static bool is_device_ptr(const void *p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Device address of page-locked host memory (cudaHostAlloc / cudaHostRegister,
+// e.g. torch's pin_memory()), which kernels read and write in place over the
+// host link; nullptr for any other pointer.
+static void *mapped_host_ptr(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 static thread_local char g_create_msg[512];
 
 extern "C" {
@@ -319,6 +331,14 @@ lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const double *rho, const double *u
   if (dev) {
     CK(launch_init_eq(ctx->Q, ctx->cfg.storage, ctx->g, rho, u, n, 0, n, ctx->f[ctx->cur],
                       ctx->stream));
+    return LBM_OK;
+  }
+  const double *mr = (const double *)mapped_host_ptr(rho), *mu = (const double *)mapped_host_ptr(u);
+  if (mr && mu) {
+    // page-locked host arrays: the kernel reads them in place
+    CK(launch_init_eq(ctx->Q, ctx->cfg.storage, ctx->g, mr, mu, n, 0, n, ctx->f[ctx->cur],
+                      ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));  // the host arrays may be released on return
     return LBM_OK;
   }
   const long long chunk = (long long)(kStageBytes / (sizeof(double) * (1 + dim)));
@@ -809,6 +829,14 @@ lbm_status lbm_get_macros(lbm_ctx *ctx, double *rho, double *u) {
   const uint8_t *fl = ctx->has_solid ? ctx->flags : nullptr;
   if (is_device_ptr(rho) && is_device_ptr(u)) {
     CK(launch_macros(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur], fl, rho, u, n, 0, n,
+                     ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+  }
+  double *mr = (double *)mapped_host_ptr(rho), *mu = (double *)mapped_host_ptr(u);
+  if (mr && mu) {
+    // page-locked host arrays: the kernel writes them in place (no staging)
+    CK(launch_macros(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur], fl, mr, mu, n, 0, n,
                      ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return LBM_OK;

@@ -54,6 +54,44 @@ def test_set_get_roundtrip_f32():
     assert np.max(np.abs(got - f0) / w) <= 0.05 * 2 ** -23 * 1.01
 
 
+@pytest.mark.parametrize("lat,shape", [(27, (5, 7, 33)), (9, (1, 21, 70))])
+def test_field_transfers_pinned_pageable_device_agree(lat, shape):
+    """lbm_init_equilibrium and lbm_get_macros give identical results for
+    pageable host arrays (staged), page-locked host arrays (read and written
+    in place by the kernels) and device arrays."""
+    import torch
+    from paper_1710_02375_gb300 import lbm as abi
+    dim = 2 if lat == 9 else 3
+    rng = np.random.default_rng(3)
+    rho = 1.0 + 0.01 * rng.standard_normal(shape)
+    u = 0.03 * rng.standard_normal((dim,) + shape)
+    out = []
+    for kind in ("pageable", "pinned", "device"):
+        L = make(lat, shape, 0.9)
+        if kind == "pageable":
+            r_in, u_in = rho, u
+            r_out, u_out = np.zeros(shape), np.zeros((dim,) + shape)
+        elif kind == "pinned":
+            r_in, u_in = torch.from_numpy(rho).pin_memory(), torch.from_numpy(u).pin_memory()
+            r_out = torch.zeros(shape, dtype=torch.float64).pin_memory()
+            u_out = torch.zeros((dim,) + shape, dtype=torch.float64).pin_memory()
+        else:
+            r_in, u_in = torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda()
+            r_out = torch.zeros(shape, dtype=torch.float64, device="cuda")
+            u_out = torch.zeros((dim,) + shape, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()  # torch's stream is not the library's
+        abi.lbm_init_equilibrium(L.ctx, r_in, u_in)
+        L.step(3)
+        abi.lbm_get_macros(L.ctx, r_out, u_out)
+        L.check()
+        to_np = (lambda a: a.cpu().numpy()) if kind != "pageable" else (lambda a: a)
+        out.append((to_np(r_out).copy(), to_np(u_out).copy()))
+        L.close()
+    for r, v in out[1:]:
+        assert np.array_equal(r, out[0][0]) and np.array_equal(v, out[0][1])
+    assert np.max(np.abs(out[0][1])) > 0.01
+
+
 @pytest.mark.parametrize("lat,shape,u0,nu", [(27, (16, 20, 24), 0.05, 0.002), (9, (1, 48, 64), 0.05, 0.005)])
 def test_taylor_green_1000_steps_laminar(lat, shape, u0, nu):
     nz, ny, nx = shape
