@@ -99,6 +99,70 @@ __global__ void __launch_bounds__(128)
   }
 }
 
+// Small-batch inference in one launch: all layers of the network for
+// B <= 16 rows (one 16-row MMA tile) in one CTA; the BF16 activations stay in
+// shared memory (two buffers of 16 x ld), the weights come from L2.  Every
+// output element is computed as k_gemm computes it (same fragments, same
+// k order, same epilogue), so results equal the layer-by-layer forward pass.
+struct MlpInferDesc {
+  int nl, B;
+  int dims[kMlpMaxLayers + 1];
+  const __nv_bfloat16 *w[kMlpMaxLayers];  // [dims[l+1]][dims[l]]
+  const float *b[kMlpMaxLayers];
+};
+constexpr int kInferThreads = 512;
+
+__global__ void __launch_bounds__(kInferThreads)
+    k_mlp_infer(MlpInferDesc d, int ld, const float *__restrict__ xin, float *__restrict__ yhat) {
+  extern __shared__ __align__(16) __nv_bfloat16 act[];
+  __nv_bfloat16 *cur = act, *nxt = act + 16 * ld;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int gid = lane >> 2, tig = lane & 3;
+  const __nv_bfloat16 zero = __float2bfloat16(0.0f);
+  const int n0 = d.dims[0];
+  for (int t = tid; t < 16 * ld; t += blockDim.x) {
+    const int m = t / ld, k = t % ld;
+    cur[t] = (m < d.B && k < n0) ? __float2bfloat16(xin[m * n0 + k]) : zero;
+  }
+  __syncthreads();
+  for (int l = 0; l < d.nl; ++l) {
+    const int K = d.dims[l], N = d.dims[l + 1];
+    const bool last = l == d.nl - 1;
+    const __nv_bfloat16 *__restrict__ W = d.w[l];
+    auto ldA = [&](int m, int k) { return (m < d.B && k < K) ? cur[m * ld + k] : zero; };
+    auto ldB = [&](int k, int n) { return (k < K && n < N) ? W[(long long)n * K + k] : zero; };
+    for (int tn = warp; tn < (N + 7) / 8; tn += nw) {
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      const int n0t = tn * 8, nc = n0t + gid;
+#pragma unroll 4
+      for (int k0 = 0; k0 < K; k0 += 16) {
+        uint32_t a[4], b[2];
+        const int kc = k0 + tig * 2;
+        a[0] = pack2(ldA(gid, kc), ldA(gid, kc + 1));
+        a[1] = pack2(ldA(gid + 8, kc), ldA(gid + 8, kc + 1));
+        a[2] = pack2(ldA(gid, kc + 8), ldA(gid, kc + 9));
+        a[3] = pack2(ldA(gid + 8, kc + 8), ldA(gid + 8, kc + 9));
+        b[0] = pack2(ldB(kc, nc), ldB(kc + 1, nc));
+        b[1] = pack2(ldB(kc + 8, nc), ldB(kc + 9, nc));
+        mma_bf16(acc, a, b);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int m = gid + (q >= 2 ? 8 : 0);
+        const int n = n0t + tig * 2 + (q & 1);
+        if (m >= d.B || n >= N) continue;
+        const float v = acc[q] + d.b[l][n];
+        if (last) yhat[(long long)m * N + n] = v;
+        else nxt[m * ld + n] = __float2bfloat16(gelu(v));
+      }
+    }
+    __syncthreads();
+    __nv_bfloat16 *t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+}
+
 __global__ void k_to_bf16(const float *__restrict__ x, __nv_bfloat16 *__restrict__ y,
                           __nv_bfloat16 *__restrict__ yt, int rows, int cols) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -309,6 +373,39 @@ static lbm_status forward(mlp_ctx *x, int B) {
   return LBM_OK;
 }
 
+// Single-launch inference (k_mlp_infer) for B <= 16 when two 16-row BF16
+// activation buffers of the widest layer fit in shared memory; a context that
+// needs more than the default 48 KB raises the kernel's limit to the 200 KB
+// bound at creation.
+static size_t infer_smem(const mlp_ctx *x, int *ld) {
+  int maxw = 0;
+  for (int l = 0; l <= x->nl; ++l) maxw = x->dims[l] > maxw ? x->dims[l] : maxw;
+  *ld = (maxw + 15) / 16 * 16;
+  return sizeof(__nv_bfloat16) * 2 * 16 * (size_t)*ld;
+}
+constexpr size_t kInferMaxSmem = 200u * 1024u;
+
+static bool fused_ok(const mlp_ctx *x, int B) {
+  int ld;
+  return B >= 1 && B <= 16 && infer_smem(x, &ld) <= kInferMaxSmem;
+}
+
+static lbm_status forward_fused(mlp_ctx *x, int B, cudaStream_t s) {
+  int ld;
+  const size_t smem = infer_smem(x, &ld);
+  MlpInferDesc d{};
+  d.nl = x->nl;
+  d.B = B;
+  for (int l = 0; l <= x->nl; ++l) d.dims[l] = x->dims[l];
+  for (int l = 0; l < x->nl; ++l) {
+    d.w[l] = x->wb[l];
+    d.b[l] = x->p + x->boff[l];
+  }
+  k_mlp_infer<<<1, kInferThreads, smem, s>>>(d, ld, x->xin, x->yhat);
+  MCK(cudaGetLastError());
+  return LBM_OK;
+}
+
 // Backward pass (after forward) from dY = dLoss/dYhat in dz / dzt; gradients
 // into x->g.
 static lbm_status backward(mlp_ctx *x, int B) {
@@ -374,6 +471,16 @@ lbm_status mlp_create(const mlp_config *cfg, void *workspace, size_t bytes, mlp_
   }
   mlp_layout(cfg, x);
   cudaMemsetAsync(x->ws, 0, need, x->stream);
+  int ld;
+  const size_t smem = infer_smem(x, &ld);
+  if (smem > 48u * 1024u && smem <= kInferMaxSmem &&
+      cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kInferMaxSmem) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    mlp_destroy(x);
+    return LBM_ECUDA;
+  }
   *out = x;
   return LBM_OK;
 }
@@ -403,7 +510,7 @@ lbm_status mlp_forward(mlp_ctx *x, const float *X, int B, float *Y) {
   if (!x || !X || !Y || B < 1 || B > x->max_batch) return LBM_EINVAL;
   MCK(cudaMemcpyAsync(x->xin, X, sizeof(float) * (size_t)B * x->dims[0], cudaMemcpyDefault,
                       x->stream));
-  lbm_status st = forward(x, B);
+  lbm_status st = fused_ok(x, B) ? forward_fused(x, B, x->stream) : forward(x, B);
   if (st != LBM_OK) return st;
   MCK(cudaMemcpyAsync(Y, x->yhat, sizeof(float) * (size_t)B * x->dims[x->nl], cudaMemcpyDefault,
                       x->stream));
@@ -486,6 +593,9 @@ namespace kbc {
 
 // Device-side forward for the coupled surrogate: input already in xin.
 lbm_status mlp_forward_device(mlp_ctx *x, int B, cudaStream_t s, float **yhat, float **xin) {
+  *yhat = x->yhat;
+  *xin = x->xin;
+  if (fused_ok(x, B)) return forward_fused(x, B, s);
   cudaStream_t old = x->stream;
   x->stream = s;
   lbm_status st = forward(x, B);

@@ -49,3 +49,23 @@ def test_training_fits_a_smooth_map():
     pred = m.forward(X[:256])
     final = float(np.mean((pred - Y[:256]) ** 2))
     assert final < 0.05 * first, (first, final)
+
+
+@pytest.mark.parametrize("dims", [[465, 128, 128, 128, 93], [1200, 256, 256, 256, 240], [7, 33, 5]])
+def test_single_launch_inference_equals_layer_by_layer(dims):
+    """Batches of 1..16 rows go through the one-launch inference kernel, larger
+    ones layer by layer; the rows of a small batch come out bit for bit as
+    they do inside a large batch, and both agree with the FP64 oracle within
+    the BF16 bound."""
+    from paper_1710_02375_gb300.lbm import Mlp
+    rng = np.random.default_rng(1)
+    p = mo.init_params(dims, 5)
+    X = rng.standard_normal((40, dims[0]))
+    m = Mlp(dims, max_batch=64)
+    m.set_params(p)
+    big = m.forward(X)
+    for B in (1, 3, 16):
+        small = m.forward(X[:B])
+        assert np.array_equal(small, big[:B]), B
+    yo, _, _ = mo.forward(p, dims, X)
+    assert np.max(np.abs(big - yo)) <= 2e-2 * np.max(np.abs(yo))
