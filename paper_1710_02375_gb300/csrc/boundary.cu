@@ -1394,7 +1394,9 @@ cudaError_t launch_geometry_batch(int Q, int storage, const InstDesc *d, const i
   KBC_DISPATCH(Q, storage, {
     k_fresh_batch<QQ, SS><<<gf, 128, 0, s>>>(d, idx, parity);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const dim3 gl(16, n);
+    // 64 CTAs (256 warps) per member: the largest member's boundary nodes,
+    // one warp each, bound the pass; surplus warps of small members exit
+    const dim3 gl(64, n);
     if (QQ == 9) k_links_batch<9><<<gb, 128, 0, s>>>(d, idx);
     else k_links_batch<27><<<gb, 128, 0, s>>>(d, idx);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
