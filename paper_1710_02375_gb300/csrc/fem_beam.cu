@@ -19,8 +19,8 @@
 // elements) so no two threads add into the same entries; the Newton system
 // (block tridiagonal in the 3 x 3 node blocks; no pivoting: the mass term
 // keeps J diagonally dominant at these steps) is solved by block elimination
-// on one thread in FP32 registers (an inexact Newton step: residual,
-// stopping test and state stay FP64).
+// from both ends at once on two threads in FP32 registers (an inexact Newton
+// step: residual, stopping test and state stay FP64).
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -187,84 +187,141 @@ __device__ __forceinline__ float elem_zf(int k, float c, float s) {
   return k < 3 ? v : -v;
 }
 
-// J x = rhs for the block-tridiagonal J of the node-major beam DOFs (3 x 3
-// blocks D_i, L_i = J[i][i-1], U_i = J[i][i+1], read from band storage):
-// block elimination (Thomas' algorithm with 3 x 3 blocks, no pivoting: the
-// mass term keeps the diagonal blocks well conditioned) on one thread in
-// FP32 registers, W_i = S_i^-1 U_i kept in Wsc for the back substitution.
-// x overwrites rhs.
-__device__ __forceinline__ void block_thomas(const float *__restrict__ J, float *__restrict__ rhs,
-                                             float *__restrict__ Wsc, int nn) {
-  float Wp[9], gp[3];
-  for (int q = 0; q < 9; ++q) Wp[q] = 0.f;
-  gp[0] = gp[1] = gp[2] = 0.f;
-  for (int i = 0; i < nn; ++i) {
-    const int r0 = 3 * i;
-    float S[9], b[3];
+// 3 x 3 helpers (row-major, FP32 registers).
+__device__ __forceinline__ void inv3(const float (&S)[9], float (&A)[9]) {
+  A[0] = S[4] * S[8] - S[5] * S[7];
+  A[1] = S[2] * S[7] - S[1] * S[8];
+  A[2] = S[1] * S[5] - S[2] * S[4];
+  A[3] = S[5] * S[6] - S[3] * S[8];
+  A[4] = S[0] * S[8] - S[2] * S[6];
+  A[5] = S[2] * S[3] - S[0] * S[5];
+  A[6] = S[3] * S[7] - S[4] * S[6];
+  A[7] = S[1] * S[6] - S[0] * S[7];
+  A[8] = S[0] * S[4] - S[1] * S[3];
+  const float idet = __frcp_rn(S[0] * A[0] + S[1] * A[3] + S[2] * A[6]);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) A[q] *= idet;
+}
+__device__ __forceinline__ void load_block(const float *__restrict__ J, int r0, int c0, float (&B)[9]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) B[3 * a + c] = bandf(J, r0 + a, c0 + c);
+}
+
+// One elimination step of the block-tridiagonal system from either end
+// (Thomas' algorithm with 3 x 3 blocks): node i with diagonal block D_i, the
+// coupling C to the node eliminated before (L_i going down, U_i going up) and
+// the coupling E to the node after (U_i going down, L_i going up):
+//   S = D_i - C W_prev,  g = S^-1 (b_i - C g_prev),  W = S^-1 E
+// g overwrites rhs_i, W goes to Wsc[i].  last: no E (end of the sweep).
+__device__ __forceinline__ void thomas_step(const float *__restrict__ J, float *__restrict__ rhs,
+                                            float *__restrict__ Wsc, int i, int prev, int next,
+                                            float (&Wp)[9], float (&gp)[3], bool first) {
+  const int r0 = 3 * i;
+  float S[9], b[3];
+  load_block(J, r0, r0, S);
+  b[0] = rhs[r0];
+  b[1] = rhs[r0 + 1];
+  b[2] = rhs[r0 + 2];
+  if (!first) {
+    float C[9];
+    load_block(J, r0, 3 * prev, C);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      b[a] = rhs[r0 + a];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) S[3 * a + c] = bandf(J, r0 + a, r0 + c);
-    }
-    if (i > 0) {
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        float L[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) L[c] = bandf(J, r0 + a, r0 - 3 + c);
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-          S[3 * a + c] -= L[0] * Wp[c] + L[1] * Wp[3 + c] + L[2] * Wp[6 + c];
-        b[a] -= L[0] * gp[0] + L[1] * gp[1] + L[2] * gp[2];
-      }
-    }
-    // S^-1 by the adjugate
-    float A[9];
-    A[0] = S[4] * S[8] - S[5] * S[7];
-    A[1] = S[2] * S[7] - S[1] * S[8];
-    A[2] = S[1] * S[5] - S[2] * S[4];
-    A[3] = S[5] * S[6] - S[3] * S[8];
-    A[4] = S[0] * S[8] - S[2] * S[6];
-    A[5] = S[2] * S[3] - S[0] * S[5];
-    A[6] = S[3] * S[7] - S[4] * S[6];
-    A[7] = S[1] * S[6] - S[0] * S[7];
-    A[8] = S[0] * S[4] - S[1] * S[3];
-    const float idet = __frcp_rn(S[0] * A[0] + S[1] * A[3] + S[2] * A[6]);
-#pragma unroll
-    for (int q = 0; q < 9; ++q) A[q] *= idet;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      gp[a] = A[3 * a] * b[0] + A[3 * a + 1] * b[1] + A[3 * a + 2] * b[2];
-      rhs[r0 + a] = gp[a];
-    }
-    if (i + 1 < nn) {
-      float U[9];
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) U[3 * a + c] = bandf(J, r0 + a, r0 + 3 + c);
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          Wp[3 * a + c] = A[3 * a] * U[c] + A[3 * a + 1] * U[3 + c] + A[3 * a + 2] * U[6 + c];
-          Wsc[9 * i + 3 * a + c] = Wp[3 * a + c];
-        }
+      for (int c = 0; c < 3; ++c)
+        S[3 * a + c] -= C[3 * a] * Wp[c] + C[3 * a + 1] * Wp[3 + c] + C[3 * a + 2] * Wp[6 + c];
+      b[a] -= C[3 * a] * gp[0] + C[3 * a + 1] * gp[1] + C[3 * a + 2] * gp[2];
     }
   }
-  float xn[3] = {rhs[3 * nn - 3], rhs[3 * nn - 2], rhs[3 * nn - 1]};
-  for (int i = nn - 2; i >= 0; --i) {
-    float x[3];
+  float A[9];
+  inv3(S, A);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    gp[a] = A[3 * a] * b[0] + A[3 * a + 1] * b[1] + A[3 * a + 2] * b[2];
+    rhs[r0 + a] = gp[a];
+  }
+  if (next >= 0) {
+    float E[9];
+    load_block(J, r0, 3 * next, E);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        Wp[3 * a + c] = A[3 * a] * E[c] + A[3 * a + 1] * E[3 + c] + A[3 * a + 2] * E[6 + c];
+        Wsc[9 * i + 3 * a + c] = Wp[3 * a + c];
+      }
+  }
+}
+
+// J x = rhs for the block-tridiagonal J of the node-major beam DOFs (3 x 3
+// node blocks read from band storage; no pivoting: the mass term keeps the
+// diagonal blocks well conditioned), eliminated from both ends at once
+// (twisted block factorisation): thread 0 (warp 0) sweeps nodes 0 .. m-1
+// downwards, thread 32 (warp 1) nodes nn-1 .. m+1 upwards, thread 0 then
+// solves node m from both sides, and each thread substitutes back along its
+// half.  All FP32 registers; x overwrites rhs.  Called by every thread of the
+// CTA (it contains barriers).
+__device__ __forceinline__ void block_twisted(const float *__restrict__ J, float *__restrict__ rhs,
+                                              float *__restrict__ Wsc, float *__restrict__ gm,
+                                              int nn) {
+  const int tid = threadIdx.x, m = nn / 2;
+  if (tid == 0 || tid == 32) {
+    float Wp[9], gp[3];
+    if (tid == 0) {
+      for (int i = 0; i < m; ++i) thomas_step(J, rhs, Wsc, i, i - 1, i + 1, Wp, gp, i == 0);
+    } else {
+      for (int i = nn - 1; i > m; --i) thomas_step(J, rhs, Wsc, i, i + 1, i - 1, Wp, gp, i == nn - 1);
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    // node m: (D_m - L_m W_{m-1} - U_m W_{m+1}) x_m = b_m - L_m g_{m-1} - U_m g_{m+1}
+    const int r0 = 3 * m;
+    float S[9], b[3];
+    load_block(J, r0, r0, S);
+    b[0] = rhs[r0];
+    b[1] = rhs[r0 + 1];
+    b[2] = rhs[r0 + 2];
+    for (int side = 0; side < 2; ++side) {
+      const int o = side == 0 ? m - 1 : m + 1;
+      if (o < 0 || o >= nn) continue;
+      float C[9];
+      load_block(J, r0, 3 * o, C);
+      const float *W = Wsc + 9 * o, *g = rhs + 3 * o;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          S[3 * a + c] -= C[3 * a] * W[c] + C[3 * a + 1] * W[3 + c] + C[3 * a + 2] * W[6 + c];
+        b[a] -= C[3 * a] * g[0] + C[3 * a + 1] * g[1] + C[3 * a + 2] * g[2];
+      }
+    }
+    float A[9];
+    inv3(S, A);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const float *w = Wsc + 9 * i + 3 * a;
-      x[a] = rhs[3 * i + a] - (w[0] * xn[0] + w[1] * xn[1] + w[2] * xn[2]);
-      rhs[3 * i + a] = x[a];
+      gm[a] = A[3 * a] * b[0] + A[3 * a + 1] * b[1] + A[3 * a + 2] * b[2];
+      rhs[r0 + a] = gm[a];
     }
-    xn[0] = x[0];
-    xn[1] = x[1];
-    xn[2] = x[2];
+  }
+  __syncthreads();
+  if (tid == 0 || tid == 32) {
+    float xn[3] = {gm[0], gm[1], gm[2]};
+    const int step = tid == 0 ? -1 : 1;
+    for (int i = m + step; i >= 0 && i < nn; i += step) {
+      float x[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float *w = Wsc + 9 * i + 3 * a;
+        x[a] = rhs[3 * i + a] - (w[0] * xn[0] + w[1] * xn[1] + w[2] * xn[2]);
+        rhs[3 * i + a] = x[a];
+      }
+      xn[0] = x[0];
+      xn[1] = x[1];
+      xn[2] = x[2];
+    }
   }
 }
 
@@ -274,7 +331,7 @@ struct BeamShared {
   double u[kMaxN], u0[kMaxN], v0[kMaxN], f0[kMaxN], F1[kMaxN], R[kMaxN], D[kMaxN];
   double Rc[kMaxN];         // load part of the residual, theta F1 + (1 - theta)(F0 - f(u0))
   unsigned char fx[kMaxN];  // Dirichlet mask
-  float rhs[kMaxN], W[kMaxBeamNodes * 9];
+  float rhs[kMaxN], W[kMaxBeamNodes * 9], gm[3];
   double X[2 * kMaxBeamNodes];
   // element scalars: constants of the step, then the current state's
   double L0[kMaxE], b0[kMaxE], EAL0[kMaxE], k2[kMaxE];
@@ -484,7 +541,7 @@ __device__ __forceinline__ void beam_step_body(const BeamParams &p, const BeamDe
       if (j >= 0 && j < n && (S.fx[i] || S.fx[j])) S.J[idx] = (i == j) ? 1.f : 0.f;
     }
     __syncthreads();
-    if (tid == 0) block_thomas(S.J, S.rhs, S.W, nn);
+    block_twisted(S.J, S.rhs, S.W, S.gm, nn);
     __syncthreads();
     for (int i = tid; i < n; i += nt) S.u[i] += p.lambda * (double)S.rhs[i];
     __syncthreads();
