@@ -1257,8 +1257,16 @@ cudaError_t launch_grad(int Q, int storage, const Grid &g, void *f, const uint8_
   if (cap <= 0) return cudaSuccess;
   KBC_DISPATCH(Q, storage, {
     using T = typename Store<SS>::T;
-    // face nodes: FP64 arithmetic on 2-D lattices, FP32 on 3-D ones (where
-    // their count scales with the lattice faces)
+    if (QQ == 9) {
+      // 2-D: face and immersed nodes both in FP64, one launch (as in the
+      // batched form), so the two latency-bound node sets run side by side
+      k_grad<QQ, SS, double><<<nb_(cap, 128), 128, 0, s>>>(g, (T *)f, flags, bnodes, nbn, nfixed,
+                                                            cap, 0, -1, links, bp, vforce, bforce,
+                                                            nbodies);
+      return cudaGetLastError();
+    }
+    // 3-D face nodes in FP32 (their count scales with the lattice faces),
+    // immersed nodes in FP64
     if (nfixed > 0) {
       if (QQ == 9)
         k_grad<QQ, SS, double><<<nb_(nfixed, 128), 128, 0, s>>>(
