@@ -923,7 +923,7 @@ __device__ __forceinline__ void grad_body(int tb, const Grid &g, typename Store<
     decompose(g, k, X, Y, Z);
     long long src[Q];
     int face_of[Q];
-    uint32_t miss = 0;
+    uint32_t miss = 0, solid_miss = 0;
     float gk[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -937,6 +937,7 @@ __device__ __forceinline__ void grad_body(int tb, const Grid &g, typename Store<
         gk[i] = St::load(f + (long long)i * g.N + src[i], (float)weight<L>(i));
       } else {
         miss |= 1u << i;
+        if (fl == NODE_SOLID) solid_miss |= 1u << i;
         if (fl == NODE_GHOST) {
           if (g.px && (Xs == 0 || Xs == g.NX - 1)) face_of[i] = Xs == 0 ? 0 : 1;
           else if (g.py && (Ys == 0 || Ys == g.NY - 1)) face_of[i] = Ys == 0 ? 2 : 3;
@@ -944,6 +945,12 @@ __device__ __forceinline__ void grad_body(int tb, const Grid &g, typename Store<
         }
       }
     }
+    // a face node next to an immersed body would also be in the immersed
+    // list, whose entry carries its cut links: that entry alone fills such a
+    // node, since the face and immersed sets run in the same launch
+    // (lbm_set_geometry keeps bodies two nodes inside non-periodic faces, so
+    // this is a guard)
+    if (t < nfixed && solid_miss) miss = 0;
     if (miss) {
       const int nmiss = __popc(miss);
       int open_face = -1;
@@ -1170,6 +1177,24 @@ __global__ void __launch_bounds__(128)
                      first, last, links, bp, vforce, bforce, nbodies);
 }
 
+// 3-D boundary fill in one launch: the first face_blocks CTAs take the face
+// nodes in FP32, the rest the immersed nodes in FP64 (with the force
+// gather), so the two sets run side by side.
+template <int Q, int S>
+__global__ void __launch_bounds__(128)
+    k_grad_split(Grid g, typename Store<S>::T *f, const uint8_t *__restrict__ flags,
+                 const BNode *__restrict__ bnodes, const int *__restrict__ nbn, int nfixed, int cap,
+                 const Link *__restrict__ links, BoundaryParams bp, double *vforce, double *bforce,
+                 int nbodies, int face_blocks) {
+  if ((int)blockIdx.x < face_blocks)
+    grad_body<Q, S, float>(blockIdx.x * blockDim.x + threadIdx.x, g, f, flags, bnodes, nullptr,
+                           nfixed, cap, 0, nfixed, links, bp, vforce, bforce, 0);
+  else
+    grad_body<Q, S, double>((blockIdx.x - face_blocks) * blockDim.x + threadIdx.x, g, f, flags,
+                            bnodes, nbn, nfixed, cap, nfixed, -1, links, bp, vforce, bforce,
+                            nbodies);
+}
+
 __global__ void k_step_counter(int *step) { *step += 1; }
 
 // ---------------------------------------------------------------- launchers
@@ -1266,7 +1291,13 @@ cudaError_t launch_grad(int Q, int storage, const Grid &g, void *f, const uint8_
       return cudaGetLastError();
     }
     // 3-D face nodes in FP32 (their count scales with the lattice faces),
-    // immersed nodes in FP64
+    // immersed nodes in FP64; both sets in one launch when both exist
+    if (nfixed > 0 && cap > nfixed) {
+      const int fb = (int)nb_(nfixed, 128);
+      k_grad_split<QQ, SS><<<fb + nb_(cap - nfixed, 128), 128, 0, s>>>(
+          g, (T *)f, flags, bnodes, nbn, nfixed, cap, links, bp, vforce, bforce, nbodies, fb);
+      return cudaGetLastError();
+    }
     if (nfixed > 0) {
       if (QQ == 9)
         k_grad<QQ, SS, double><<<nb_(nfixed, 128), 128, 0, s>>>(

@@ -291,3 +291,4 @@ def test_stress_traction_matches_oracle():
         assert np.linalg.norm(tb_g[b] - tb_o[b]) <= 1e-3 * np.linalg.norm(tb_o[b]), (tb_g, tb_o)
     assert np.max(np.abs(tv_g - tv_o)) <= 1e-3 * np.max(np.abs(tv_o))
     print("TRACTION vs momentum exchange (C1, 300 steps):", tb_g[:, :2].tolist(), mb_g[:, :2].tolist())
+
