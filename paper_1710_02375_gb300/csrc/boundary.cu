@@ -82,6 +82,18 @@ struct PopSum<double> {
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
+// (nh + nl) / (dh + dl) for unevaluated FP32 pairs, as a double: the FP32
+// quotient q1, its exact remainder nh - q1 dh (one fused multiply-add), the
+// correction q2 from the remainder and the low parts; q1 + q2 carries about
+// 44 bits.
+__device__ __forceinline__ double df_div(float nh, float nl, float dh, float dl) {
+  const float q1 = __fdiv_rn(nh, dh);
+  float r = fmaf(-q1, dh, nh);
+  r = (r + nl) - q1 * dl;
+  const float q2 = __fdiv_rn(r, dh);
+  return (double)q1 + (double)q2;
+}
+
 // Per-direction constants for directions known only at run time (the same
 // values as weight<L>, read from constant memory instead of recomputed in
 // FP64): W_i, W_i and 1 / W_i in FP32.
@@ -137,6 +149,31 @@ __device__ void dev_moments(const Grid &g, const typename Store<S>::T *f, long l
 template <int Q, int S, typename R = float>
 __device__ void dev_velocity(const Grid &g, const typename Store<S>::T *f, long long k, R (&u)[3],
                              R *rho = nullptr) {
+  if constexpr (Q == 9 && std::is_same<R, double>::value) {
+    // D2Q9 in FP64: the moments stay unevaluated FP32 pairs (hi + lo) and
+    // rho = 1 + drho and u = j / rho are formed in double-float arithmetic
+    // on the FP32 pipes (about 44 bits), with one conversion pair per
+    // result instead of FP64 sums and an FP64 division
+    using L = Lat<Q>;
+    PopSum<double> dr, jx, jy;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const float v = Store<S>::load(f + (long long)i * g.N + k, (float)weight<L>(i));
+      dr.add(v);
+      if (L::cx(i) > 0) jx.add(v);
+      if (L::cx(i) < 0) jx.sub(v);
+      if (L::cy(i) > 0) jy.add(v);
+      if (L::cy(i) < 0) jy.sub(v);
+    }
+    float rh, rl;
+    two_sum(1.0f, dr.hi, rh, rl);
+    rl += dr.lo;
+    u[0] = df_div(jx.hi, jx.lo, rh, rl);
+    u[1] = df_div(jy.hi, jy.lo, rh, rl);
+    u[2] = 0.0;
+    if (rho) *rho = (double)rh + (double)rl;
+    return;
+  }
   R dr, j[3];
   dev_moments<Q, S, R>(g, f, k, dr, j);
   const R r = (R)1 + dr;
