@@ -174,6 +174,18 @@ __device__ void dev_velocity(const Grid &g, const typename Store<S>::T *f, long 
     if (rho) *rho = (double)rh + (double)rl;
     return;
   }
+  if constexpr (Q == 27 && std::is_same<R, double>::value) {
+    // D3Q27 in FP64: FP32 moment sums (as in dev_moments), then rho and the
+    // quotients in double-float arithmetic (as above) instead of an FP64
+    // division
+    float drf, jf[3];
+    dev_moments<Q, S, float>(g, f, k, drf, jf);
+    float rh, rl;
+    two_sum(1.0f, drf, rh, rl);
+    for (int a = 0; a < 3; ++a) u[a] = df_div(jf[a], 0.0f, rh, rl);
+    if (rho) *rho = (double)rh + (double)rl;
+    return;
+  }
   R dr, j[3];
   dev_moments<Q, S, R>(g, f, k, dr, j);
   const R r = (R)1 + dr;
