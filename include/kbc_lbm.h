@@ -433,6 +433,10 @@ lbm_status lbm_get_traction_force(lbm_ctx *ctx, double *vert_force, double *body
  * kernel reads or writes it in place over the host link, no staging copy)
  * or pageable host memory (staged through the workspace in chunks). */
 lbm_status lbm_get_macros(lbm_ctx *ctx, double *rho, double *u);
+/* The same fields in FP32 (rho = 1 + sum of the stored deviations and
+ * u = j / rho formed in FP32; half the bytes of lbm_get_macros).  Same
+ * layouts and memory kinds.  Synchronises. */
+lbm_status lbm_get_macros_f32(lbm_ctx *ctx, float *rho, float *u);
 
 /* Kernel form of the fused sweep.  AUTO (default) and DIRECT: one thread per
  * node, Q coalesced global loads and stores.  ROWS: a persistent kernel that

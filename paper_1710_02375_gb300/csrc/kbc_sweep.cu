@@ -552,7 +552,7 @@ template <int Q, int S>
 __global__ void k_macros(Grid g, const typename Store<S>::T *__restrict__ f,
                          const uint8_t *__restrict__ flags, double *__restrict__ rho,
                          double *__restrict__ u, long long ustride, long long begin,
-                         long long count) {
+                         long long count, float *__restrict__ rho32, float *__restrict__ u32) {
   using L = Lat<Q>;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= count) return;
@@ -570,10 +570,26 @@ __global__ void k_macros(Grid g, const typename Store<S>::T *__restrict__ f,
       jy += L::cy(i) * v;
       jz += L::cz(i) * v;
     }
+    if (rho32) {
+      // FP32 outputs: rho and u = j / rho in FP32
+      const float rf = 1.f + dr, ir = 1.f / rf;
+      rho32[t] = rf;
+      u32[t] = jx * ir;
+      u32[ustride + t] = jy * ir;
+      if (L::D == 3) u32[2 * ustride + t] = jz * ir;
+      return;
+    }
     r = 1.0 + (double)dr;
     ux = (double)jx / r;
     uy = (double)jy / r;
     uz = (double)jz / r;
+  }
+  if (rho32) {
+    rho32[t] = 0.f;
+    u32[t] = 0.f;
+    u32[ustride + t] = 0.f;
+    if (L::D == 3) u32[2 * ustride + t] = 0.f;
+    return;
   }
   rho[t] = r;
   u[t] = ux;
@@ -616,11 +632,11 @@ cudaError_t launch_get_pop(int Q, int storage, const Grid &g, int i, double *dst
 
 cudaError_t launch_macros(int Q, int storage, const Grid &g, const void *f, const uint8_t *flags,
                           double *rho, double *u, long long ustride, long long begin,
-                          long long count, cudaStream_t s) {
+                          long long count, cudaStream_t s, float *rho32, float *u32) {
   if (count <= 0) return cudaSuccess;
   KBC_DISPATCH(Q, storage, {
     k_macros<QQ, SS><<<nblk(count, 256), 256, 0, s>>>(
-        g, (const typename Store<SS>::T *)f, flags, rho, u, ustride, begin, count);
+        g, (const typename Store<SS>::T *)f, flags, rho, u, ustride, begin, count, rho32, u32);
     return cudaGetLastError();
   });
 }

@@ -821,6 +821,42 @@ lbm_status lbm_check(lbm_ctx *ctx) {
   return LBM_OK;
 }
 
+lbm_status lbm_get_macros_f32(lbm_ctx *ctx, float *rho, float *u) {
+  GUARD();
+  if (!rho || !u) return fail(ctx, LBM_EINVAL, "lbm_get_macros_f32: NULL argument");
+  const int dim = ctx->Q == 9 ? 2 : 3;
+  const long long n = (long long)ctx->g.nx * ctx->g.ny * ctx->g.nz;
+  const uint8_t *fl = ctx->has_solid ? ctx->flags : nullptr;
+  float *dr = nullptr, *du = nullptr;
+  if (is_device_ptr(rho) && is_device_ptr(u)) {
+    dr = rho;
+    du = u;
+  } else {
+    dr = (float *)mapped_host_ptr(rho);
+    du = (float *)mapped_host_ptr(u);
+  }
+  if (dr && du) {
+    // device or page-locked host arrays: written in place
+    CK(launch_macros(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur], fl, nullptr, nullptr, n,
+                     0, n, ctx->stream, dr, du));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+  }
+  const long long chunk = (long long)(kStageBytes / (sizeof(float) * (1 + dim)));
+  float *s = (float *)ctx->stage;
+  for (long long b = 0; b < n; b += chunk) {
+    const long long cnt = (n - b < chunk) ? n - b : chunk;
+    CK(launch_macros(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur], fl, nullptr, nullptr, cnt,
+                     b, cnt, ctx->stream, s, s + cnt));
+    CK(cudaMemcpyAsync(rho + b, s, cnt * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    for (int a = 0; a < dim; ++a)
+      CK(cudaMemcpyAsync(u + a * n + b, s + (1 + a) * cnt, cnt * sizeof(float),
+                         cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  return LBM_OK;
+}
+
 lbm_status lbm_get_macros(lbm_ctx *ctx, double *rho, double *u) {
   GUARD();
   if (!rho || !u) return fail(ctx, LBM_EINVAL, "lbm_get_macros: NULL argument");

@@ -52,9 +52,11 @@ cudaError_t launch_get_pop(int Q, int storage, const Grid &g, int i, double *dst
 
 // rho[count], u[dim][ustride] for interior nodes [begin, begin+count); solid
 // nodes give zeros.
+// FP64 outputs rho / u, or FP32 outputs rho32 / u32 when rho32 is given.
 cudaError_t launch_macros(int Q, int storage, const Grid &g, const void *f, const uint8_t *flags,
                           double *rho, double *u, long long ustride, long long begin,
-                          long long count, cudaStream_t s);
+                          long long count, cudaStream_t s, float *rho32 = nullptr,
+                          float *u32 = nullptr);
 
 }  // namespace kbc
 

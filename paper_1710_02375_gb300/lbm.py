@@ -67,6 +67,7 @@ def load():
     L.lbm_get_populations.argtypes = [vp, vp]
     L.lbm_step.argtypes = [vp, i32]
     L.lbm_get_macros.argtypes = [vp, vp, vp]
+    L.lbm_get_macros_f32.argtypes = [vp, vp, vp]
     L.lbm_check.argtypes = [vp]
     L.lbm_set_inlet_profile.argtypes = [vp, i32, vp]
     L.lbm_set_geometry.argtypes = [vp, i32, vp, i32, vp, i32, vp, vp, ctypes.c_double]
@@ -97,7 +98,8 @@ def load():
     L.lbm_destroy.argtypes = [vp]
     L.lbm_destroy.restype = None
     for name in ("lbm_workspace_size", "lbm_create", "lbm_init_equilibrium", "lbm_set_populations",
-                 "lbm_get_populations", "lbm_step", "lbm_get_macros", "lbm_check"):
+                 "lbm_get_populations", "lbm_step", "lbm_get_macros", "lbm_get_macros_f32",
+                 "lbm_check"):
         getattr(L, name).restype = ctypes.c_int
     _extend(L)
     _lib = L
@@ -180,6 +182,11 @@ def lbm_step_graph(ctx, n: int, repeats: int):
 
 def lbm_get_macros(ctx, rho, u):
     _chk(ctx, load().lbm_get_macros(ctx, _ptr(rho), _ptr(u)))
+
+
+def lbm_get_macros_f32(ctx, rho, u):
+    """FP32 density and velocity (float32 arrays, host or device)."""
+    _chk(ctx, load().lbm_get_macros_f32(ctx, _ptr(rho), _ptr(u)))
 
 
 LBM_SWEEP_AUTO, LBM_SWEEP_DIRECT, LBM_SWEEP_ROWS, LBM_SWEEP_ASYNC = 0, 1, 2, 3

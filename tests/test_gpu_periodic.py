@@ -90,6 +90,27 @@ def test_field_transfers_pinned_pageable_device_agree(lat, shape):
     for r, v in out[1:]:
         assert np.array_equal(r, out[0][0]) and np.array_equal(v, out[0][1])
     assert np.max(np.abs(out[0][1])) > 0.01
+    # FP32 fields: the same values to FP32 rounding, for every memory kind
+    ref_r, ref_u = out[0]
+    L = make(lat, shape, 0.9)
+    abi.lbm_init_equilibrium(L.ctx, rho, u)
+    L.step(3)
+    for kind in ("pageable", "pinned", "device"):
+        if kind == "pageable":
+            r32, u32 = np.zeros(shape, np.float32), np.zeros((dim,) + shape, np.float32)
+        elif kind == "pinned":
+            r32 = torch.zeros(shape, dtype=torch.float32).pin_memory()
+            u32 = torch.zeros((dim,) + shape, dtype=torch.float32).pin_memory()
+        else:
+            r32 = torch.zeros(shape, dtype=torch.float32, device="cuda")
+            u32 = torch.zeros((dim,) + shape, dtype=torch.float32, device="cuda")
+            torch.cuda.synchronize()
+        abi.lbm_get_macros_f32(L.ctx, r32, u32)
+        r32 = r32 if kind == "pageable" else r32.cpu().numpy()
+        u32 = u32 if kind == "pageable" else u32.cpu().numpy()
+        assert np.max(np.abs(r32 - ref_r)) <= 4e-7, kind
+        assert np.max(np.abs(u32 - ref_u)) <= 4e-7 * np.max(np.abs(ref_u)) + 1e-9, kind
+    L.close()
 
 
 @pytest.mark.parametrize("lat,shape,u0,nu", [(27, (16, 20, 24), 0.05, 0.002), (9, (1, 48, 64), 0.05, 0.005)])
