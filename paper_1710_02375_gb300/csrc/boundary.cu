@@ -413,32 +413,49 @@ __device__ __forceinline__ float seg_margin(const float4 &q, float px, float py)
 }
 
 // inside_any for a 2-D surface through the staged filters.
+// Segment k of the staged 2-D surface against node p: whether p lies on
+// it (FP64 test behind an FP32 filter) and whether the parity ray from p
+// crosses it.
+__device__ __forceinline__ void seg_test(const SurfaceDev &s, const SegStage &st, int k,
+                                         const double *p, float px, float py, float dx, float dy,
+                                         bool &on, bool &cross) {
+  const double tol = 1e-12;
+  on = false;
+  cross = false;
+  const float4 q = st.seg[k];
+  const float T = seg_margin(q, px, py);
+  const float xlo = fminf(q.x, q.z), xhi = fmaxf(q.x, q.z);
+  const float ylo = fminf(q.y, q.w), yhi = fmaxf(q.y, q.w);
+  const bool near = px >= xlo - T && px <= xhi + T && py >= ylo - T && py <= yhi + T;
+  if (near) {  // on-surface test (as in on_surface)
+    const double *a = s.x + 2 * s.e[2 * k], *b = s.x + 2 * s.e[2 * k + 1];
+    const double ex = b[0] - a[0], ey = b[1] - a[1];
+    const double qx = p[0] - a[0], qy = p[1] - a[1];
+    const double len2 = ex * ex + ey * ey;
+    const double cr = ex * qy - ey * qx, dt = ex * qx + ey * qy;
+    if (len2 > 0.0 && fabs(cr) <= tol * sqrt(len2) && dt >= 0.0 && dt <= len2) {
+      on = true;
+      return;
+    }
+  }
+  if (xhi < px - T || yhi < py - T) return;  // behind the node in x or y
+  const float sa = dx * (q.y - py) - dy * (q.x - px);
+  const float sb = dx * (q.w - py) - dy * (q.z - px);
+  if ((sa > T && sb > T) || (sa < -T && sb < -T)) return;  // off the ray's line
+  const double *a = s.x + 2 * s.e[2 * k], *b = s.x + 2 * s.e[2 * k + 1];
+  if ((a[0] < p[0] && b[0] < p[0]) || (a[1] < p[1] && b[1] < p[1])) return;
+  cross = seg_ray_cross(p, c_ray2, a, b);
+}
+
 __device__ bool inside_any_staged(const SurfaceDev &s, const SegStage &st, const double *p) {
   const float px = (float)p[0], py = (float)p[1];
   const float dx = (float)c_ray2[0], dy = (float)c_ray2[1];
-  const double tol = 1e-12;
   unsigned par = 0;
   for (int k = 0; k < s.ne; ++k) {
-    const float4 q = st.seg[k];
-    const float T = seg_margin(q, px, py);
-    const float xlo = fminf(q.x, q.z), xhi = fmaxf(q.x, q.z);
-    const float ylo = fminf(q.y, q.w), yhi = fmaxf(q.y, q.w);
-    const bool near = px >= xlo - T && px <= xhi + T && py >= ylo - T && py <= yhi + T;
-    if (near) {  // on-surface test (as in on_surface)
-      const double *a = s.x + 2 * s.e[2 * k], *b = s.x + 2 * s.e[2 * k + 1];
-      const double ex = b[0] - a[0], ey = b[1] - a[1];
-      const double qx = p[0] - a[0], qy = p[1] - a[1];
-      const double len2 = ex * ex + ey * ey;
-      const double cr = ex * qy - ey * qx, dt = ex * qx + ey * qy;
-      if (len2 > 0.0 && fabs(cr) <= tol * sqrt(len2) && dt >= 0.0 && dt <= len2) return true;
-    }
-    if (xhi < px - T || yhi < py - T) continue;  // behind the node in x or y
-    const float sa = dx * (q.y - py) - dy * (q.x - px);
-    const float sb = dx * (q.w - py) - dy * (q.z - px);
-    if ((sa > T && sb > T) || (sa < -T && sb < -T)) continue;  // off the ray's line
-    const double *a = s.x + 2 * s.e[2 * k], *b = s.x + 2 * s.e[2 * k + 1];
-    if ((a[0] < p[0] && b[0] < p[0]) || (a[1] < p[1] && b[1] < p[1])) continue;
-    if (seg_ray_cross(p, c_ray2, a, b)) par ^= 1u << st.body[k];
+    bool on, cross;
+    seg_test(s, st, k, p, px, py, dx, dy, on, cross);
+    if (on) return true;
+    if (cross) par ^= 1u << st.body[k];
   }
   return par != 0;
 }
@@ -458,39 +475,83 @@ __device__ __forceinline__ float edge_side(const float *A, const float *B, const
 // skipped when the node is off its bounding box (on-surface test), when it
 // lies behind the node on an axis, or when two of its edges put the ray's
 // line on strictly opposite sides (the line misses it).
+// Triangle k of the staged 3-D surface against node p (as seg_test).
+__device__ __forceinline__ void tri_test(const SurfaceDev &s, const SegStage &st, int k,
+                                         const double *p, const float *pf, const float *d,
+                                         bool &on, bool &cross) {
+  on = false;
+  cross = false;
+  const float *t = st.tri[k];
+  float mag = 1.f + fabsf(pf[0]) + fabsf(pf[1]) + fabsf(pf[2]);
+  for (int q = 0; q < 9; ++q) mag += fabsf(t[q]);
+  const float T = 4e-6f * mag;
+  bool near = true, behind = false;
+  for (int q = 0; q < 3; ++q) {
+    const float lo = fminf(fminf(t[q], t[3 + q]), t[6 + q]);
+    const float hi = fmaxf(fmaxf(t[q], t[3 + q]), t[6 + q]);
+    near = near && pf[q] >= lo - T && pf[q] <= hi + T;
+    behind = behind || hi < pf[q] - T;
+  }
+  const double *a = s.x + 3 * s.e[3 * k], *b = s.x + 3 * s.e[3 * k + 1], *c = s.x + 3 * s.e[3 * k + 2];
+  if (near && on_triangle(p, a, b, c, 1e-12)) {
+    on = true;
+    return;
+  }
+  if (behind) return;
+  float b0, b1, b2;
+  const float s0 = edge_side(t, t + 3, pf, d, mag, b0);
+  const float s1 = edge_side(t + 3, t + 6, pf, d, mag, b1);
+  const float s2 = edge_side(t + 6, t, pf, d, mag, b2);
+  const bool pos = s0 > b0 || s1 > b1 || s2 > b2, neg = s0 < -b0 || s1 < -b1 || s2 < -b2;
+  if (pos && neg) return;
+  if ((a[0] < p[0] && b[0] < p[0] && c[0] < p[0]) || (a[1] < p[1] && b[1] < p[1] && c[1] < p[1]) ||
+      (a[2] < p[2] && b[2] < p[2] && c[2] < p[2]))
+    return;
+  double tt, u, v;
+  cross = tri_ray(p, c_ray3, a, b, c, tt, u, v) && tt > 0.0 && u >= 0.0 && v >= 0.0 && u + v < 1.0;
+}
+
 __device__ bool inside_any_staged3(const SurfaceDev &s, const SegStage &st, const double *p) {
   const float pf[3] = {(float)p[0], (float)p[1], (float)p[2]};
   const float d[3] = {(float)c_ray3[0], (float)c_ray3[1], (float)c_ray3[2]};
   unsigned par = 0;
   for (int k = 0; k < s.ne; ++k) {
-    const float *t = st.tri[k];
-    float mag = 1.f + fabsf(pf[0]) + fabsf(pf[1]) + fabsf(pf[2]);
-    for (int q = 0; q < 9; ++q) mag += fabsf(t[q]);
-    const float T = 4e-6f * mag;
-    bool near = true, behind = false;
-    for (int q = 0; q < 3; ++q) {
-      const float lo = fminf(fminf(t[q], t[3 + q]), t[6 + q]);
-      const float hi = fmaxf(fmaxf(t[q], t[3 + q]), t[6 + q]);
-      near = near && pf[q] >= lo - T && pf[q] <= hi + T;
-      behind = behind || hi < pf[q] - T;
-    }
-    const double *a = s.x + 3 * s.e[3 * k], *b = s.x + 3 * s.e[3 * k + 1], *c = s.x + 3 * s.e[3 * k + 2];
-    if (near && on_triangle(p, a, b, c, 1e-12)) return true;
-    if (behind) continue;
-    float b0, b1, b2;
-    const float s0 = edge_side(t, t + 3, pf, d, mag, b0);
-    const float s1 = edge_side(t + 3, t + 6, pf, d, mag, b1);
-    const float s2 = edge_side(t + 6, t, pf, d, mag, b2);
-    const bool pos = s0 > b0 || s1 > b1 || s2 > b2, neg = s0 < -b0 || s1 < -b1 || s2 < -b2;
-    if (pos && neg) continue;
-    if ((a[0] < p[0] && b[0] < p[0] && c[0] < p[0]) || (a[1] < p[1] && b[1] < p[1] && c[1] < p[1]) ||
-        (a[2] < p[2] && b[2] < p[2] && c[2] < p[2]))
-      continue;
-    double tt, u, v;
-    if (tri_ray(p, c_ray3, a, b, c, tt, u, v) && tt > 0.0 && u >= 0.0 && v >= 0.0 && u + v < 1.0)
-      par ^= 1u << st.body[k];
+    bool on, cross;
+    tri_test(s, st, k, p, pf, d, on, cross);
+    if (on) return true;
+    if (cross) par ^= 1u << st.body[k];
   }
   return par != 0;
+}
+
+// Whether band node p is inside a body or on the surface, with the warp's
+// lanes splitting the staged elements (on-surface: any lane; parity: XOR of
+// the lanes' per-body crossing masks).  All lanes call it with the same p.
+__device__ bool inside_any_warp(const SurfaceDev &s, const SegStage &st, const double *p,
+                                int lane) {
+  bool on_any = false;
+  unsigned par = 0;
+  if (s.dim == 2) {
+    const float px = (float)p[0], py = (float)p[1];
+    const float dx = (float)c_ray2[0], dy = (float)c_ray2[1];
+    for (int k = lane; k < s.ne; k += 32) {
+      bool on, cross;
+      seg_test(s, st, k, p, px, py, dx, dy, on, cross);
+      on_any = on_any || on;
+      if (!on && cross) par ^= 1u << st.body[k];
+    }
+  } else {
+    const float pf[3] = {(float)p[0], (float)p[1], (float)p[2]};
+    const float d[3] = {(float)c_ray3[0], (float)c_ray3[1], (float)c_ray3[2]};
+    for (int k = lane; k < s.ne; k += 32) {
+      bool on, cross;
+      tri_test(s, st, k, p, pf, d, on, cross);
+      on_any = on_any || on;
+      if (!on && cross) par ^= 1u << st.body[k];
+    }
+  }
+  if (__any_sync(0xffffffffu, on_any)) return true;
+  return __reduce_xor_sync(0xffffffffu, par) != 0;
 }
 
 // ---- cut links.  The link from x_b along -c_i has the box [lo, hi] (with
@@ -623,10 +684,36 @@ __device__ __forceinline__ bool outside_box(const float *box, const double *p, i
 }
 
 // New solid flags inside the band; nodes that turn fluid are listed as fresh.
+// Flag update of band node t (shared by the node pass and the deferred
+// warp pass): solid or fluid, and a solid -> fluid change recorded as fresh.
+__device__ __forceinline__ void set_solid_flag(uint8_t *flags, long long k, bool in, int64_t *fresh,
+                                               int *nfresh, int cap, int track_fresh) {
+  const uint8_t now = in ? NODE_SOLID : NODE_FLUID;
+  const uint8_t before = flags[k];
+  if (before == NODE_GHOST) return;
+  if (track_fresh && before == NODE_SOLID && now == NODE_FLUID) {
+    const int slot = atomicAdd(nfresh, 1);
+    if (slot < cap) fresh[slot] = k;
+  }
+  flags[k] = now;
+}
+
+__device__ __forceinline__ void band_node(const Band &bd, long long t, int &x, int &y, int &z) {
+  const int bx = bd.x1 - bd.x0, by = bd.y1 - bd.y0;
+  x = bd.x0 + (int)(t % bx);
+  y = bd.y0 + (int)((t / bx) % by);
+  z = bd.z0 + (int)(t / ((long long)bx * by));
+}
+
+// Solid flags of the band.  Nodes inside the staged surface's box, where
+// every element has to be tested, are deferred to the warp pass
+// (solid_near_body) through near_list / near_cnt when a list is given and
+// has room; the rest are decided here.
 __device__ __forceinline__ void solid_flags_body(long long t, const Grid &g, const Band &bd,
                                                  const SurfaceDev &s, uint8_t *flags,
                                                  int64_t *fresh, int *nfresh, int cap,
-                                                 int track_fresh) {
+                                                 int track_fresh, int *near_list = nullptr,
+                                                 int *near_cnt = nullptr, int near_cap = 0) {
   __shared__ SegStage st;
   const int bx = bd.x1 - bd.x0, by = bd.y1 - bd.y0, bz = bd.z1 - bd.z0;
   const long long nbnd = (long long)bx * by * bz;
@@ -647,27 +734,66 @@ __device__ __forceinline__ void solid_flags_body(long long t, const Grid &g, con
   }
   if (!live) return;
   bool in;
-  if (far)
+  if (far) {
     in = false;
-  else if (staged)
-    in = !outside_staged_box(st, p, s.dim) &&
-         (s.dim == 2 ? inside_any_staged(s, st, p) : inside_any_staged3(s, st, p));
-  else
+  } else if (staged) {
+    if (outside_staged_box(st, p, s.dim)) {
+      in = false;
+    } else {
+      if (near_list) {
+        const int slot = atomicAdd(near_cnt, 1);
+        if (slot < near_cap) {
+          near_list[slot] = (int)tt;
+          return;
+        }
+      }
+      in = s.dim == 2 ? inside_any_staged(s, st, p) : inside_any_staged3(s, st, p);
+    }
+  } else {
     in = inside_any(s, p);
-  const uint8_t now = in ? NODE_SOLID : NODE_FLUID;
-  const uint8_t before = flags[k];
-  if (before == NODE_GHOST) return;
-  if (track_fresh && before == NODE_SOLID && now == NODE_FLUID) {
-    const int slot = atomicAdd(nfresh, 1);
-    if (slot < cap) fresh[slot] = k;
   }
-  flags[k] = now;
+  set_solid_flag(flags, k, in, fresh, nfresh, cap, track_fresh);
+}
+
+// Deferred band nodes, one warp each (warp w of nw takes list entries w,
+// w + nw, ...): the lanes split the surface elements.
+__device__ __forceinline__ void solid_near_body(const Grid &g, const Band &bd, const SurfaceDev &s,
+                                                uint8_t *flags, int64_t *fresh, int *nfresh,
+                                                int cap, int track_fresh, const int *near_list,
+                                                const int *near_cnt, int near_cap, int w, int nw) {
+  __shared__ SegStage st;
+  int n = *near_cnt;
+  if (n > near_cap) n = near_cap;
+  if ((int)(blockIdx.x * (blockDim.x >> 5)) >= n) return;  // whole CTA idle
+  if (!stage_segments(s, st)) return;  // nodes are only deferred when staging fits
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  for (int j = w; j < n; j += nw) {
+    int x, y, z;
+    band_node(bd, near_list[j], x, y, z);
+    const double p[3] = {x + 0.5, y + 0.5, z + 0.5};
+    const bool in = inside_any_warp(s, st, p, lane);
+    if (lane == 0)
+      set_solid_flag(flags, sidx(g, x + g.px, y + g.py, z + g.pz), in, fresh, nfresh, cap,
+                     track_fresh);
+  }
 }
 
 __global__ void k_solid_flags(Grid g, Band bd, SurfaceDev s, uint8_t *flags, int64_t *fresh,
-                              int *nfresh, int cap, int track_fresh) {
+                              int *nfresh, int cap, int track_fresh, int *near_list,
+                              int *near_cnt, int near_cap) {
   solid_flags_body(blockIdx.x * (long long)blockDim.x + threadIdx.x, g, bd, s, flags, fresh,
-                   nfresh, cap, track_fresh);
+                   nfresh, cap, track_fresh, near_list, near_cnt, near_cap);
+}
+
+__global__ void __launch_bounds__(128)
+    k_solid_near(Grid g, Band bd, SurfaceDev s, uint8_t *flags, int64_t *fresh, int *nfresh,
+                 int cap, int track_fresh, const int *near_list, const int *near_cnt,
+                 int near_cap) {
+  const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  solid_near_body(g, bd, s, flags, fresh, nfresh, cap, track_fresh, near_list, near_cnt, near_cap,
+                  w, nw);
 }
 
 // Immersed boundary nodes of the band: slots in the node list and ranges in
@@ -1307,9 +1433,18 @@ cudaError_t launch_geometry(int Q, int storage, const Grid &g, const Band &bd, c
     k_surface_box<<<1, 256, 0, s>>>(sd);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  // nodes inside the surface's box go to a second, warp-per-node pass; the
+  // immersed-node list (rebuilt below) holds their indices meanwhile, its
+  // counter counts them
+  int *near_list = reinterpret_cast<int *>(bnodes);
+  const int near_cap = (int)((long long)bcap * sizeof(BNode) / sizeof(int));
   k_solid_flags<<<nb_(nb, 128), 128, 0, s>>>(g, bd, sd, flags, fresh, nfresh, fresh_cap,
-                                              track_fresh);
+                                              track_fresh, near_list, nbn, near_cap);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_solid_near<<<fill_grid(), 128, 0, s>>>(g, bd, sd, flags, fresh, nfresh, fresh_cap, track_fresh,
+                                           near_list, nbn, near_cap);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(nbn, 0, sizeof(int), s)) != cudaSuccess) return e;
   if (track_fresh && (e = launch_fresh(Q, storage, g, f, flags, fresh, nfresh, fresh_cap, sd, s)) !=
                          cudaSuccess)
     return e;
@@ -1423,6 +1558,8 @@ __global__ void __launch_bounds__(256) k_surface_box_batch(const InstDesc *__res
 
 __global__ void k_solid_flags_batch(const InstDesc *__restrict__ d, const int *__restrict__ idx) {
   const InstDesc &b = d[idx[blockIdx.y]];
+  // one pass: across 64 members the in-box nodes already fill the GPU one
+  // thread each (the warp-per-node pass measured slower here)
   solid_flags_body(blockIdx.x * (long long)blockDim.x + threadIdx.x, b.g, b.band, b.sd, b.flags,
                    b.fresh, b.nfresh, b.lcap, 1);
 }
