@@ -1072,6 +1072,22 @@ __global__ void k_fresh_init(Grid g, typename Store<S>::T *f, const uint8_t *fla
 }
 
 // ---------------------------------------------------------------- Grad fill + force
+// Per-body force totals of a warp: reduction per body id, one atomic per warp
+// and body (all lanes call it).
+__device__ __forceinline__ void body_reduce(int nbodies, int my_body, const double (&Fd)[3],
+                                            double *bforce) {
+  for (int b = 0; b < nbodies; ++b) {
+    double v[3];
+    for (int a = 0; a < 3; ++a) v[a] = (my_body == b) ? Fd[a] : 0.0;
+    const unsigned any = __ballot_sync(0xffffffffu, my_body == b);
+    if (!any) continue;
+    for (int off = 16; off > 0; off >>= 1)
+      for (int a = 0; a < 3; ++a) v[a] += __shfl_down_sync(0xffffffffu, v[a], off);
+    if ((threadIdx.x & 31) == 0)
+      for (int a = 0; a < 3; ++a) atomicAdd(&bforce[3 * b + a], v[a]);
+  }
+}
+
 template <int Q, int S, typename R>
 __device__ __forceinline__ void grad_body(int tb, const Grid &g, typename Store<S>::T *f,
                                           const uint8_t *__restrict__ flags,
@@ -1329,17 +1345,7 @@ __device__ __forceinline__ void grad_body(int tb, const Grid &g, typename Store<
       }
     }
   }
-  // per-body totals: warp reduction per body id, one atomic per warp and body
-  for (int b = 0; b < nbodies; ++b) {
-    double v[3];
-    for (int a = 0; a < 3; ++a) v[a] = (my_body == b) ? Fd[a] : 0.0;
-    const unsigned any = __ballot_sync(0xffffffffu, my_body == b);
-    if (!any) continue;
-    for (int off = 16; off > 0; off >>= 1)
-      for (int a = 0; a < 3; ++a) v[a] += __shfl_down_sync(0xffffffffu, v[a], off);
-    if ((threadIdx.x & 31) == 0)
-      for (int a = 0; a < 3; ++a) atomicAdd(&bforce[3 * b + a], v[a]);
-  }
+  body_reduce(nbodies, my_body, Fd, bforce);
 }
 
 template <int Q, int S, typename R>
@@ -1352,9 +1358,342 @@ __global__ void __launch_bounds__(128)
                      first, last, links, bp, vforce, bforce, nbodies);
 }
 
+// ---- the same fill with one warp per boundary node (FP64), for single
+// lattices, where a few hundred to a few thousand nodes would otherwise run
+// their chains of neighbour velocities one after another on few warps: lane
+// i gathers direction i and computes the velocity of the neighbour x_b + c_i
+// when it is needed (lanes 0..5 then the second neighbours of one-sided
+// gradients), lane 0 assembles the targets and the stress exactly as
+// grad_body does (same operations in the same order, velocities from the
+// lanes), and lane i forms, stores and gathers the force of its missing
+// direction.  Every value written equals grad_body's; only the order of the
+// FP64 force atomics differs.
+template <int Q>
+struct GradWarpSh {
+  double vel[Q + 6][3];  // [i < Q]: node x_b + c_i; [Q + 2b (+1)]: x_b + 2 e_b (- 2 e_b)
+  double rho[Q];
+  float gk[Q], gop[Q];   // known populations; f_opp(i)(x_b) of missing i
+  float q[Q], uw[Q][3];  // link fraction and wall velocity of missing i
+  double ut[3], Ad[3], A01, A02, A12, tr3, r3, rm1;
+};
+
+template <int Q>
+__device__ __forceinline__ int dir_index(int cx, int cy, int cz) {
+  return Q == 9 ? (cy + 1) * 3 + (cx + 1) : (cz + 1) * 9 + (cy + 1) * 3 + (cx + 1);
+}
+
+template <int Q, int S>
+__device__ __forceinline__ void grad_warp_node(int t, const Grid &g, typename Store<S>::T *f,
+                                               const uint8_t *__restrict__ flags,
+                                               const BNode *__restrict__ bnodes, int nfixed,
+                                               const Link *__restrict__ links,
+                                               const BoundaryParams &bp, double *vforce,
+                                               double *bforce, GradWarpSh<Q> &W, int lane,
+                                               int &my_body, double (&Fd)[3]) {
+  using L = Lat<Q>;
+  using St = Store<S>;
+  using R = double;
+  constexpr int D = L::D;
+  constexpr unsigned FULL = 0xffffffffu;
+  const int rest = (Q - 1) / 2;
+  const BNode bn = bnodes[t];
+  const long long k = bn.k;
+  int X, Y, Z;
+  decompose(g, k, X, Y, Z);
+  // ---- gather: lane i takes direction i
+  const bool dl = lane < Q;
+  const int i = dl ? lane : 0;
+  const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+  long long src = 0;
+  int face = -1;
+  uint8_t fl = NODE_FLUID;
+  if (dl) {
+    const int Xs = nbr(X, -cx, g.NX), Ys = nbr(Y, -cy, g.NY), Zs = (D == 3) ? nbr(Z, -cz, g.NZ) : Z;
+    src = sidx(g, Xs, Ys, Zs);
+    fl = flags[src];
+    if (fl == NODE_FLUID) {
+      W.gk[i] = St::load(f + (long long)i * g.N + src, dir_tab<Q>().wf[i]);
+    } else if (fl == NODE_GHOST) {
+      if (g.px && (Xs == 0 || Xs == g.NX - 1)) face = Xs == 0 ? 0 : 1;
+      else if (g.py && (Ys == 0 || Ys == g.NY - 1)) face = Ys == 0 ? 2 : 3;
+      else face = Zs == 0 ? 4 : 5;
+    }
+  }
+  uint32_t miss = __ballot_sync(FULL, dl && fl != NODE_FLUID);
+  const uint32_t solid_miss = __ballot_sync(FULL, dl && fl == NODE_SOLID);
+  if (t < nfixed && solid_miss) miss = 0;  // as in grad_body
+  if (!miss) return;
+  const bool mi = dl && ((miss >> i) & 1u);
+  // ---- open face: the first face (in face order) crossed by a missing link
+  int open_face = -1;
+  for (int fc = 0; fc < 6; ++fc) {
+    const bool open = bp.bc[fc] == BCK_INLET || bp.bc[fc] == BCK_OUTLET || bp.bc[fc] == BCK_FREESTREAM;
+    if (open && __any_sync(FULL, mi && face == fc)) {
+      open_face = fc;
+      break;
+    }
+  }
+  const bool zero_grad = open_face >= 0 && bp.bc[open_face] == BCK_FREESTREAM;
+  int kn_dir = rest;
+  if (open_face >= 0) {
+    const int ax = open_face / 2, dir = (open_face % 2 == 0) ? 1 : -1;
+    int Xn = X, Yn = Y, Zn = Z;
+    if (ax == 0) Xn = step_axis(X, dir, g.NX, g.px);
+    if (ax == 1) Yn = step_axis(Y, dir, g.NY, g.py);
+    if (ax == 2) Zn = step_axis(Z, dir, g.NZ, g.pz);
+    if (Xn >= 0 && Yn >= 0 && Zn >= 0 && flags[sidx(g, Xn, Yn, Zn)] == NODE_FLUID)
+      kn_dir = dir_index<Q>(ax == 0 ? dir : 0, ax == 1 ? dir : 0, ax == 2 ? dir : 0);
+  }
+  // ---- neighbour velocities, lane i: x_b + c_i
+  bool nfluid = false;
+  int Xn = X, Yn = Y, Zn = Z;
+  if (dl) {
+    Xn = step_axis(X, cx, g.NX, g.px);
+    Yn = step_axis(Y, cy, g.NY, g.py);
+    Zn = (D == 3) ? step_axis(Z, cz, g.NZ, g.pz) : Z;
+    nfluid = Xn >= 0 && Yn >= 0 && Zn >= 0 && flags[sidx(g, Xn, Yn, Zn)] == NODE_FLUID;
+  }
+  const uint32_t fmask = __ballot_sync(FULL, dl && nfluid);
+  bool need = false;
+  if (dl) {
+    const int nnz = (cx != 0) + (cy != 0) + (cz != 0);
+    need = open_face >= 0 ? i == kn_dir : (mi && nfluid);
+    if (!zero_grad && (i == rest || (nnz == 1 && nfluid))) need = true;
+  }
+  if (need) {
+    R u[3], r;
+    dev_velocity<Q, S, R>(g, f, sidx(g, Xn, Yn, Zn), u, &r);
+    W.vel[i][0] = u[0];
+    W.vel[i][1] = u[1];
+    W.vel[i][2] = u[2];
+    W.rho[i] = r;
+  }
+  // second neighbours of one-sided gradients: lane j < 2 D, axis j / 2
+  uint32_t f2mask = 0;
+  if (!zero_grad) {
+    bool f2 = false;
+    if (lane < 2 * D) {
+      const int b = lane / 2, sgn = (lane % 2 == 0) ? 1 : -1;
+      const int ip = dir_index<Q>(b == 0, b == 1, b == 2), im = dir_index<Q>(-(b == 0), -(b == 1), -(b == 2));
+      const bool fp = (fmask >> ip) & 1u, fm = (fmask >> im) & 1u;
+      if (sgn > 0 ? (fp && !fm) : (fm && !fp)) {
+        int P[3] = {X, Y, Z};
+        const int NS = b == 0 ? g.NX : (b == 1 ? g.NY : g.NZ);
+        const int pad = b == 0 ? g.px : (b == 1 ? g.py : g.pz);
+        P[b] = step_axis(P[b], 2 * sgn, NS, pad);
+        if (P[b] >= 0 && flags[sidx(g, P[0], P[1], P[2])] == NODE_FLUID) {
+          f2 = true;
+          R u[3];
+          dev_velocity<Q, S, R>(g, f, sidx(g, P[0], P[1], P[2]), u);
+          W.vel[Q + lane][0] = u[0];
+          W.vel[Q + lane][1] = u[1];
+          W.vel[Q + lane][2] = u[2];
+        }
+      }
+    }
+    f2mask = __ballot_sync(FULL, f2);
+  }
+  // link data of the missing directions
+  if (mi) {
+    float q = 0.5f, uw[3] = {0.f, 0.f, 0.f};
+    if (face >= 0) {
+      for (int a = 0; a < 3; ++a) uw[a] = bp.face_u[face][a];
+    } else {
+      for (int l = 0; l < bn.nlink; ++l) {
+        const Link &lk = links[bn.link0 + l];
+        if (lk.i == i) {
+          q = lk.q;
+          for (int a = 0; a < 3; ++a) uw[a] = lk.uw[a];
+          break;
+        }
+      }
+    }
+    W.q[i] = q;
+    for (int a = 0; a < 3; ++a) W.uw[i][a] = uw[a];
+    W.gop[i] = St::load(f + (long long)(Q - 1 - i) * g.N + k, dir_tab<Q>().wf[i]);
+  }
+  __syncwarp();
+  // ---- targets and stress on lane 0 (grad_body's arithmetic)
+  if (lane == 0) {
+    const int nmiss = __popc(miss);
+    R rho_t, ut[3] = {0, 0, 0};
+    if (open_face >= 0) {
+      const int ax = open_face / 2;
+      const R u0[3] = {W.vel[kn_dir][0], W.vel[kn_dir][1], W.vel[kn_dir][2]};
+      const R r0 = W.rho[kn_dir];
+      if (bp.bc[open_face] == BCK_INLET) {
+        R scale = 1;
+        if (bp.ramp_steps > 0 && bp.step) {
+          const int st = *bp.step;
+          if (st < bp.ramp_steps) scale = (R)0.5 * ((R)1 - cospi((double)st / bp.ramp_steps));
+        }
+        const float *prof = bp.inlet[open_face];
+        const int x = X - g.px, y = Y - g.py, z = Z - g.pz;
+        long long fidx, fn;
+        if (ax == 0) { fidx = (long long)z * g.ny + y; fn = (long long)g.ny * g.nz; }
+        else if (ax == 1) { fidx = (long long)z * g.nx + x; fn = (long long)g.nx * g.nz; }
+        else { fidx = (long long)y * g.nx + x; fn = (long long)g.nx * g.ny; }
+        for (int a = 0; a < D; ++a)
+          ut[a] = scale * (R)(prof ? prof[a * fn + fidx] : bp.face_u[open_face][a]);
+        rho_t = r0;
+      } else if (bp.bc[open_face] == BCK_OUTLET) {
+        for (int a = 0; a < D; ++a) ut[a] = u0[a];
+        rho_t = 1;
+      } else {
+        for (int a = 0; a < D; ++a) ut[a] = bp.face_u[open_face][a];
+        rho_t = 1;
+      }
+    } else {
+      PopSum<R> pops;
+      R wterm = 0;
+      for (int j = 0; j < Q; ++j) {
+        if (!((miss >> j) & 1u)) {
+          pops.add(W.gk[j]);
+          continue;
+        }
+        const R q = W.q[j];
+        const R uw[3] = {W.uw[j][0], W.uw[j][1], W.uw[j][2]};
+        const double wi = dir_tab<Q>().w[j];
+        R cuw = L::cx(j) * uw[0] + L::cy(j) * uw[1];
+        if (D == 3) cuw += L::cz(j) * uw[2];
+        pops.add(W.gop[j]);
+        wterm += (R)(6.0 * wi) * cuw;
+        R ui[3] = {uw[0], uw[1], uw[2]};
+        if ((fmask >> j) & 1u) {
+          const R iq = (R)1 / ((R)1 + q);
+          for (int a = 0; a < D; ++a) ui[a] = (uw[a] + q * W.vel[j][a]) * iq;
+        }
+        for (int a = 0; a < D; ++a) ut[a] += ui[a];
+      }
+      const R inm = (R)1 / (R)nmiss;
+      for (int a = 0; a < D; ++a) ut[a] *= inm;
+      rho_t = (R)1 + ((R)pops.value() + wterm);
+    }
+    R G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    if (!zero_grad) {
+      const R u0[3] = {W.vel[rest][0], W.vel[rest][1], W.vel[rest][2]};
+      for (int b = 0; b < D; ++b) {
+        const int ip = dir_index<Q>(b == 0, b == 1, b == 2), im = dir_index<Q>(-(b == 0), -(b == 1), -(b == 2));
+        const bool fp = (fmask >> ip) & 1u, fm = (fmask >> im) & 1u;
+        if (fp && fm) {
+          for (int a = 0; a < D; ++a) G[a][b] = (R)0.5 * (W.vel[ip][a] - W.vel[im][a]);
+        } else if (fp) {
+          if ((f2mask >> (2 * b)) & 1u) {
+            for (int a = 0; a < D; ++a)
+              G[a][b] = (R)0.5 * ((R)-3 * u0[a] + (R)4 * W.vel[ip][a] - W.vel[Q + 2 * b][a]);
+          } else {
+            for (int a = 0; a < D; ++a) G[a][b] = W.vel[ip][a] - u0[a];
+          }
+        } else if (fm) {
+          if ((f2mask >> (2 * b + 1)) & 1u) {
+            for (int a = 0; a < D; ++a)
+              G[a][b] = (R)0.5 * ((R)3 * u0[a] - (R)4 * W.vel[im][a] + W.vel[Q + 2 * b + 1][a]);
+          } else {
+            for (int a = 0; a < D; ++a) G[a][b] = u0[a] - W.vel[im][a];
+          }
+        }
+      }
+    }
+    R A[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    const R cneq = -rho_t / ((R)6 * (R)bp.beta);
+    for (int a = 0; a < D; ++a)
+      for (int b = 0; b < D; ++b) A[a][b] = rho_t * ut[a] * ut[b] + cneq * (G[a][b] + G[b][a]);
+    R trA = A[0][0] + A[1][1];
+    if (D == 3) trA += A[2][2];
+    W.tr3 = trA * (R)(1.0 / 3.0);
+    W.A01 = A[0][1] + A[1][0];
+    W.A02 = A[0][2] + A[2][0];
+    W.A12 = A[1][2] + A[2][1];
+    W.r3 = (R)3 * rho_t;
+    W.rm1 = rho_t - (R)1;
+    for (int a = 0; a < 3; ++a) {
+      W.Ad[a] = A[a][a];
+      W.ut[a] = ut[a];
+    }
+  }
+  __syncwarp();
+  // ---- lane i: f*_i of its missing direction, its store and its force
+  if (mi) {
+    const int c[3] = {cx, cy, cz};
+    R cAc = 0, cu = 0;
+    for (int a = 0; a < D; ++a) {
+      if (c[a] != 0) cAc += W.Ad[a];
+      if (c[a] > 0) cu += W.ut[a];
+      if (c[a] < 0) cu -= W.ut[a];
+    }
+    if (c[0] * c[1] > 0) cAc += W.A01;
+    if (c[0] * c[1] < 0) cAc -= W.A01;
+    if (D == 3) {
+      if (c[0] * c[2] > 0) cAc += W.A02;
+      if (c[0] * c[2] < 0) cAc -= W.A02;
+      if (c[1] * c[2] > 0) cAc += W.A12;
+      if (c[1] * c[2] < 0) cAc -= W.A12;
+    }
+    const DirTab<Q> &dt = dir_tab<Q>();
+    const R gstar = (R)dt.w[i] * (W.rm1 + W.r3 * cu + (R)4.5 * (cAc - W.tr3));
+    St::store(f + (long long)i * g.N + src, (float)gstar, dt.iwf[i]);
+    if (face < 0) {
+      int l = 0;
+      while (l < bn.nlink && links[bn.link0 + l].i != i) ++l;
+      if (l < bn.nlink) {
+        const Link &lk = links[bn.link0 + l];
+        if (lk.body >= 0) {
+          const double fsum = (double)W.gop[i] + (double)(float)gstar;
+          for (int a = 0; a < D; ++a) {
+            if (c[a] == 0) continue;
+            const double Fa = c[a] > 0 ? -fsum : fsum;
+            for (int m = 0; m < D; ++m) atomicAdd(&vforce[3 * lk.v[m] + a], (double)lk.vw[m] * Fa);
+            if (lk.body == my_body || my_body < 0) {
+              my_body = lk.body;
+              Fd[a] += Fa;
+            } else {
+              atomicAdd(&bforce[3 * lk.body + a], Fa);
+            }
+          }
+        }
+      }
+    }
+  }
+  __syncwarp();
+}
+
+// Warps stride over the boundary nodes [first, count) (count = nfixed +
+// immersed when last < 0, else last).
+template <int Q, int S>
+__device__ __forceinline__ void grad_warp_range(const Grid &g, typename Store<S>::T *f,
+                                                const uint8_t *__restrict__ flags,
+                                                const BNode *__restrict__ bnodes,
+                                                const int *__restrict__ nbn, int nfixed, int cap,
+                                                int first, int last, const Link *__restrict__ links,
+                                                const BoundaryParams &bp, double *vforce,
+                                                double *bforce, int nbodies, int w0, int nw) {
+  __shared__ GradWarpSh<Q> sh[4];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  int dyn = nbn ? *nbn : 0;
+  if (dyn > cap - nfixed) dyn = cap - nfixed;
+  const int count = last < 0 ? nfixed + dyn : last;
+  int my_body = -1;
+  double Fd[3] = {0, 0, 0};
+  for (int t = first + w0; t < count; t += nw)
+    grad_warp_node<Q, S>(t, g, f, flags, bnodes, nfixed, links, bp, vforce, bforce, sh[wl], lane,
+                         my_body, Fd);
+  body_reduce(nbodies, my_body, Fd, bforce);
+}
+
+template <int Q, int S>
+__global__ void __launch_bounds__(128)
+    k_grad_warp(Grid g, typename Store<S>::T *f, const uint8_t *__restrict__ flags,
+                const BNode *__restrict__ bnodes, const int *__restrict__ nbn, int nfixed, int cap,
+                int first, int last, const Link *__restrict__ links, BoundaryParams bp,
+                double *vforce, double *bforce, int nbodies) {
+  grad_warp_range<Q, S>(g, f, flags, bnodes, nbn, nfixed, cap, first, last, links, bp, vforce,
+                        bforce, nbodies, (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5),
+                        (int)((gridDim.x * blockDim.x) >> 5));
+}
+
 // 3-D boundary fill in one launch: the first face_blocks CTAs take the face
-// nodes in FP32, the rest the immersed nodes in FP64 (with the force
-// gather), so the two sets run side by side.
+// nodes in FP32 (one thread each), the rest the immersed nodes in FP64 with
+// the force gather (one warp each), so the two sets run side by side.
 template <int Q, int S>
 __global__ void __launch_bounds__(128)
     k_grad_split(Grid g, typename Store<S>::T *f, const uint8_t *__restrict__ flags,
@@ -1365,9 +1704,10 @@ __global__ void __launch_bounds__(128)
     grad_body<Q, S, float>(blockIdx.x * blockDim.x + threadIdx.x, g, f, flags, bnodes, nullptr,
                            nfixed, cap, 0, nfixed, links, bp, vforce, bforce, 0);
   else
-    grad_body<Q, S, double>((blockIdx.x - face_blocks) * blockDim.x + threadIdx.x, g, f, flags,
-                            bnodes, nbn, nfixed, cap, nfixed, -1, links, bp, vforce, bforce,
-                            nbodies);
+    grad_warp_range<Q, S>(g, f, flags, bnodes, nbn, nfixed, cap, nfixed, -1, links, bp, vforce,
+                          bforce, nbodies,
+                          (int)(((blockIdx.x - face_blocks) * blockDim.x + threadIdx.x) >> 5),
+                          (int)(((gridDim.x - face_blocks) * blockDim.x) >> 5));
 }
 
 __global__ void k_step_counter(int *step) { *step += 1; }
@@ -1467,18 +1807,17 @@ cudaError_t launch_grad(int Q, int storage, const Grid &g, void *f, const uint8_
   KBC_DISPATCH(Q, storage, {
     using T = typename Store<SS>::T;
     if (QQ == 9) {
-      // 2-D: face and immersed nodes both in FP64, one launch (as in the
-      // batched form), so the two latency-bound node sets run side by side
-      k_grad<QQ, SS, double><<<nb_(cap, 128), 128, 0, s>>>(g, (T *)f, flags, bnodes, nbn, nfixed,
-                                                            cap, 0, -1, links, bp, vforce, bforce,
-                                                            nbodies);
+      // 2-D: face and immersed nodes both in FP64, one launch, one warp per
+      // node (striding over the lists)
+      k_grad_warp<QQ, SS><<<fill_grid(), 128, 0, s>>>(g, (T *)f, flags, bnodes, nbn, nfixed, cap, 0,
+                                                      -1, links, bp, vforce, bforce, nbodies);
       return cudaGetLastError();
     }
     // 3-D face nodes in FP32 (their count scales with the lattice faces),
     // immersed nodes in FP64; both sets in one launch when both exist
     if (nfixed > 0 && cap > nfixed) {
       const int fb = (int)nb_(nfixed, 128);
-      k_grad_split<QQ, SS><<<fb + nb_(cap - nfixed, 128), 128, 0, s>>>(
+      k_grad_split<QQ, SS><<<fb + fill_grid(), 128, 0, s>>>(
           g, (T *)f, flags, bnodes, nbn, nfixed, cap, links, bp, vforce, bforce, nbodies, fb);
       return cudaGetLastError();
     }
