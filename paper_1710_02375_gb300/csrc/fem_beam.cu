@@ -336,24 +336,56 @@ struct BeamShared {
   // element scalars: constants of the step, then the current state's
   double L0[kMaxE], b0[kMaxE], EAL0[kMaxE], k2[kMaxE];
   double c[kMaxE], s[kMaxE], iL[kMaxE], N[kMaxE], M1[kMaxE], M2[kMaxE];
+  double rot0[kMaxE], c0[kMaxE], s0[kMaxE];  // chord rotation and direction at the step's start
   // FP32 copies for the tangent: c, s, 1/L, N/L, (M1 + M2)/L^2, EA/L0, k2
   float tc[kMaxE], ts[kMaxE], tiL[kMaxE], tNL[kMaxE], tML[kMaxE], tEA[kMaxE], tk2[kMaxE];
   double red[4];
 };
 
-// Element state scalars at the displacement in S.u (thread per element).
+// Element state scalars at the displacement u (thread per element).  base:
+// the step's start state, whose chord rotation comes from a full atan2 and is
+// kept with the chord direction; otherwise the rotation is that start value
+// plus the angle from the start chord to the current one, by the arctangent
+// series when it is small (|tan| < 0.1: terms to t^15, truncation below
+// 1e-17 relative) and by atan2 otherwise.
 __device__ __forceinline__ void elem_state(const BeamParams &p, BeamShared &S, const double *u,
-                                           int ne) {
+                                           int ne, bool base) {
   for (int e = threadIdx.x; e < ne; e += blockDim.x) {
     const int a = e, b = e + 1;
     const double dx = S.X[2 * b] - S.X[2 * a] + u[3 * b] - u[3 * a];
     const double dy = S.X[2 * b + 1] - S.X[2 * a + 1] + u[3 * b + 1] - u[3 * a + 1];
     const double L = sqrt(dx * dx + dy * dy);
     const double iL = 1.0 / L;
-    double rot = atan2(dy, dx) - S.b0[e];
     const double PI = 3.14159265358979323846;
-    if (rot > PI) rot -= 2 * PI;
-    if (rot <= -PI) rot += 2 * PI;
+    double rot;
+    if (base) {
+      rot = atan2(dy, dx) - S.b0[e];
+      if (rot > PI) rot -= 2 * PI;
+      if (rot <= -PI) rot += 2 * PI;
+      S.rot0[e] = rot;
+      S.c0[e] = dx * iL;
+      S.s0[e] = dy * iL;
+    } else {
+      const double y = S.c0[e] * dy - S.s0[e] * dx, x = S.c0[e] * dx + S.s0[e] * dy;
+      double dr;
+      if (x > 0.0 && fabs(y) < 0.1 * x) {
+        const double t = y / x, t2 = t * t;
+        double q = -1.0 / 15.0;
+        q = q * t2 + 1.0 / 13.0;
+        q = q * t2 - 1.0 / 11.0;
+        q = q * t2 + 1.0 / 9.0;
+        q = q * t2 - 1.0 / 7.0;
+        q = q * t2 + 1.0 / 5.0;
+        q = q * t2 - 1.0 / 3.0;
+        q = q * t2 + 1.0;
+        dr = t * q;
+      } else {
+        dr = atan2(y, x);
+      }
+      rot = S.rot0[e] + dr;
+      if (rot > PI) rot -= 2 * PI;
+      if (rot <= -PI) rot += 2 * PI;
+    }
     const double t1 = u[3 * a + 2] - rot, t2 = u[3 * b + 2] - rot;
     S.c[e] = dx * iL;
     S.s[e] = dy * iL;
@@ -447,7 +479,7 @@ __device__ __forceinline__ void beam_step_body(const BeamParams &p, const BeamDe
   }
   __syncthreads();
   // ---- f(u0)
-  elem_state(p, S, S.u0, ne);
+  elem_state(p, S, S.u0, ne, true);
   __syncthreads();
   double fe2 = 0.0;
   for (int i = tid; i < n; i += nt) {
@@ -479,7 +511,7 @@ __device__ __forceinline__ void beam_step_body(const BeamParams &p, const BeamDe
   }
   int it = 0, conv = 0;
   for (it = 0; it < p.max_it; ++it) {
-    elem_state(p, S, S.u, ne);
+    elem_state(p, S, S.u, ne, false);
     for (int i = tid; i < n; i += nt) S.D[i] = (S.u[i] - S.u0[i]) * a_v - S.v0[i] * i_th;
     __syncthreads();
     double part = 0.0;
