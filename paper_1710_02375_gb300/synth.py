@@ -299,3 +299,19 @@ def plate_vertices(X, u, R, h):
     d = R[:, :, 2]
     x = X + u
     return np.concatenate([x + 0.5 * h * d, x - 0.5 * h * d])
+
+
+def box_surface(lo, hi):
+    """Closed triangle mesh of the axis-aligned box [lo, hi] (8 corners, 12
+    triangles wound with outward normals).  Returns (x[8,3], e[12,3])."""
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    x = np.array([[(hi if (k >> a) & 1 else lo)[a] for a in range(3)] for k in range(8)])
+    # corner k has bit a set when it sits on the hi side of axis a
+    quads = [(0, 4, 6, 2), (1, 3, 7, 5),    # x = lo, x = hi
+             (0, 1, 5, 4), (2, 6, 7, 3),    # y = lo, y = hi
+             (0, 2, 3, 1), (4, 5, 7, 6)]    # z = lo, z = hi
+    e = []
+    for a, b, c, d in quads:
+        e += [(a, b, c), (a, c, d)]
+    return x, np.array(e, dtype=np.int32)
