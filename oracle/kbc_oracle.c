@@ -26,6 +26,14 @@
  *   - k = {rho, j}; s = trace-free (deviatoric) part of the second moments;
  *     h = everything else (trace, third and fourth order moments).
  *   - gamma = 2 (plain BGK with omega = 2 beta) when <dh|dh> <= 1e-30.
+ *   - gamma is held in [0, 2/beta]: Eq. (gamma_min_approx) is the vertex of
+ *     the quadratic entropy norm of f', a convex parabola in gamma, and the
+ *     post-collision higher-order part is (1 - beta gamma) dh, which grows
+ *     outside that range.  The paper gives the estimate without bounds; the
+ *     clip is the minimum of the same norm over the non-growing rates.  (Seen
+ *     unbounded in a channel start-up: gamma up to 6.7 at outlet nodes next
+ *     to the walls, which grew round-off differences a hundred-thousand-fold
+ *     within a few dozen steps.)
  *
  * Population layout (the library's interface layout as well): structure of
  * arrays f[i][z][y][x], direction index i = (cz+1)*9 + (cy+1)*3 + (cx+1) for
@@ -176,7 +184,14 @@ static void collide(const or_lattice *L, double beta, int mode, const double *f,
     hh += dh[i] * dh[i] / feq[i];
   }
   double gamma = 2.0;
-  if (mode == 0 && hh > 1e-30) gamma = 1.0 / beta - (2.0 - 1.0 / beta) * sh / hh;
+  if (mode == 0 && hh > 1e-30) {
+    gamma = 1.0 / beta - (2.0 - 1.0 / beta) * sh / hh;
+    /* the quadratic entropy norm is a convex parabola in gamma; its minimum
+     * over the rates at which the higher-order part does not grow,
+     * |1 - beta gamma| <= 1, is the vertex clipped to [0, 2/beta] */
+    if (gamma > 2.0 / beta) gamma = 2.0 / beta;
+    if (gamma < 0.0) gamma = 0.0;
+  }
 
   for (int i = 0; i < Q; ++i) {
     /* f_mirr = k + (2 s_eq - s) + ((1 - gamma) h + gamma h_eq) = f - 2 ds - gamma dh */

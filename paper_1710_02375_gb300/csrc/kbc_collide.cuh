@@ -12,7 +12,9 @@
 //   gamma = 1/beta - (2 - 1/beta) <ds|dh>/<dh|dh>, <X|Y> = sum X Y / feq
 //                                                   -- Eq. (gamma_min_approx)
 //   f' = f - beta (2 ds + gamma dh)                 -- Eqs. (f_equations), (f_mirr)
-// gamma = 2 (LBGK, omega = 2 beta) when <dh|dh> <= 1e-30 or BGK is requested.
+// gamma = 2 (LBGK, omega = 2 beta) when <dh|dh> <= 1e-30 or BGK is requested;
+// otherwise gamma is held in [0, 2/beta], where (1 - beta gamma) dh, the
+// post-collision higher-order part, does not grow.
 // The metric weights are evaluated up to the common factor 1/rho, so the
 // degenerate-case threshold applies to rho <dh|dh>.
 #pragma once
@@ -168,7 +170,12 @@ __device__ __forceinline__ float collide(float (&g)[L::Q], float beta, bool bgk)
   const float ib = __fdividef(1.0f, beta);
   float gamma = 2.f;
   // <.|.> carries a common factor rho that cancels in the ratio
-  if (!bgk && hh > 1e-30f) gamma = ib - (2.f - ib) * __fdividef(sh, hh);
+  if (!bgk && hh > 1e-30f) {
+    gamma = ib - (2.f - ib) * __fdividef(sh, hh);
+    // the vertex of the quadratic entropy norm clipped to the rates at which
+    // the higher-order part does not grow, |1 - beta gamma| <= 1
+    gamma = fminf(fmaxf(gamma, 0.f), 2.f * ib);
+  }
 
   // ---- conservation of the FP32 update: df carries no mass or momentum in
   // exact arithmetic; its rounding residue (dm, dj) would otherwise leak into

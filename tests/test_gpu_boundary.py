@@ -89,15 +89,13 @@ def c1_setup(with_flag=False):
     return nx, ny, beta, prof, x, e, body
 
 
-def run_c1(with_flag, steps, ramp=1000, perturb=0.0):
+def run_c1(with_flag, steps, ramp=1000):
     """Oracle run of the C1 channel; returns (u, solid, vertex forces, body forces)."""
     nx, ny, beta, prof, x, e, body = c1_setup(with_flag)
     bc = (INLET, OUTLET, WALL, WALL, 0, 0)
     surf = orc.Surface(x, np.zeros_like(x), e, body)
     solid = orc.solid_mask((1, ny, nx), surf)
     f = orc.init_equilibrium(9, np.ones((1, ny, nx)), np.zeros((2, 1, ny, nx)))
-    if perturb:
-        f = f * (1 + perturb * np.random.default_rng(1).standard_normal(f.shape))
     for t in range(steps):
         s = 0.5 * (1 - np.cos(np.pi * t / ramp)) if t < ramp else 1.0
         f, vf_o, bf_o, _ = orc.step_bc(9, beta, f, bc=bc, inlet={0: prof}, inlet_scale=s, surf=surf,
@@ -135,22 +133,25 @@ def test_channel_cylinder_c1_geometry_700_steps(with_flag):
     assert np.max(np.abs(vf_g - vf_o)) <= 1e-4 * np.max(np.abs(vf_o))
 
 
-def test_channel_cylinder_c1_1000_steps_within_oracle_spread():
-    """Between steps 800 and 1000 of this start-up the discrete flow near the
-    outlet amplifies perturbations (a 1e-8 relative perturbation of the oracle's
-    own initial state grows to ~6e-4 by step 1000), so the GPU is held to the
-    oracle's own sensitivity there: error <= max(1e-5, 3 x the spread between
-    the oracle and a copy perturbed at the FP32 level, 1e-7 relative)."""
-    ug, _, _, _ = gpu_c1(False, 1000)
-    uo, _, _, _ = run_c1(False, 1000)
-    up, _, _, _ = run_c1(False, 1000, perturb=1e-7)
-    spread = rel(up, uo)
-    assert rel(ug, uo) <= max(1e-5, 3 * spread), (rel(ug, uo), spread)
+@pytest.mark.parametrize("with_flag", [False, True])
+def test_channel_cylinder_c1_1000_steps(with_flag):
+    """The C1 channel over the whole 1000-step inflow ramp at the plain FP32
+    bounds.  (With gamma unbounded, gamma reached 6.7 at the outlet nodes next
+    to the walls near step 830 and grew round-off differences 1e5-fold; held
+    in [0, 2/beta] the oracle's own 1e-8 perturbation stays at 5e-10.)"""
+    ug, vf_g, bf_g, body = gpu_c1(with_flag, 1000)
+    uo, solid, vf_o, bf_o = run_c1(with_flag, 1000)
+    assert rel(ug, uo) <= 1e-5, rel(ug, uo)
+    for b in range(body.max() + 1):
+        assert np.linalg.norm(bf_g[b] - bf_o[b]) <= 1e-4 * np.linalg.norm(bf_o[b])
+    assert np.max(np.abs(vf_g - vf_o)) <= 1e-4 * np.max(np.abs(vf_o))
 
 
 def test_sphere_channel_d3q27():
+    """Steady flow past a sphere (D = 8.4, Re = 29) in a D3Q27 channel with an
+    inlet, an outlet, face walls and free-stream faces, 1000 steps."""
     nx, ny, nz = 36, 20, 18
-    beta, steps = 0.95, 200
+    beta, steps = 0.95, 1000
     bc = (INLET, OUTLET, WALL, WALL, FREE, FREE)
     fu = np.zeros((6, 3))
     fu[0, 0] = 0.03

@@ -85,6 +85,15 @@ def parabola_argmin(qfun):
     return -b / (2 * a)
 
 
+def bounded_argmin(qfun, lo, hi):
+    """Minimiser of a convex quadratic over [lo, hi]: its vertex if inside,
+    else the end point with the smaller value (compared, not assumed)."""
+    g = parabola_argmin(qfun)
+    if lo <= g <= hi:
+        return g
+    return lo if qfun(lo) <= qfun(hi) else hi
+
+
 LATS = [(9, 2), (27, 3)]
 
 
@@ -163,6 +172,43 @@ def test_gamma_is_argmin_of_quadratic_entropy(lat, dim):
 
 
 @pytest.mark.parametrize("lat,dim", LATS)
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+def test_gamma_outside_the_non_growing_range_is_the_bounded_argmin(lat, dim, sign):
+    """A state built with a large shear part and a small higher-order part
+    correlated (sign -1) or anti-correlated (sign +1) with it in the
+    1/feq-weighted product puts the vertex of the quadratic entropy norm
+    outside [0, 2/beta], where (1 - beta gamma) dh would grow; gamma is then
+    the norm's minimiser over that range, found here by a scan of the range."""
+    c, w = orc.lattice(lat)
+    M, tags = moment_matrix(c, dim)
+    beta = 0.97
+    f0 = synth.random_state(lat, (1,), 0.02, 321)[:, 0]
+    rho = f0.sum()
+    feq = newton_equilibrium(c, w, rho, (f0 @ c) / rho, dim)
+    ds0, dh0 = part(M, tags, f0 - feq, "s"), part(M, tags, f0 - feq, "h")
+    ip, hh = np.sum(ds0 * dh0 / feq), np.sum(dh0 * dh0 / feq)
+    # f = feq + ds0 + b dh0: the vertex is 1/beta - (2 - 1/beta) ip / (b hh);
+    # b is chosen to put it one unit beyond the range
+    target = 2.0 / beta + 1.0 if sign > 0 else -1.0
+    b = (2.0 - 1.0 / beta) * ip / (hh * (1.0 / beta - target))
+    f = feq + ds0 + b * dh0
+    assert np.all(f > 0)
+    fpost, gamma, ds, dh, _ = orc.collide(lat, beta, f)
+
+    def qnorm(g):
+        fp = f - beta * (2 * ds + g * dh)
+        return np.sum((fp - feq) ** 2 / feq)
+
+    vertex = parabola_argmin(qnorm)
+    assert vertex > 2.0 / beta if sign > 0 else vertex < 0.0, vertex
+    grid = np.linspace(0.0, 2.0 / beta, 20001)
+    g_scan = grid[np.argmin([qnorm(g) for g in grid])]
+    assert gamma == (2.0 / beta if sign > 0 else 0.0)
+    assert abs(gamma - g_scan) < 2e-4
+    np.testing.assert_allclose(fpost, f - beta * (2 * ds + gamma * dh), rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("lat,dim", LATS)
 def test_gamma_approximates_entropy_argmin_near_equilibrium(lat, dim):
     """Eq. (gamma_min_approx) is the small-deviation estimate of the gamma that
     minimises H(f') itself; the two approach each other as f -> feq."""
@@ -226,7 +272,7 @@ def brute_force_step(lat, dim, beta, f):
             fp = (1 - beta) * fi + beta * mirr(g)
             return np.sum((fp - feq) ** 2 / feq)
 
-        g = parabola_argmin(qnorm)
+        g = bounded_argmin(qnorm, 0.0, 2.0 / beta)
         out[:, z, y, x] = (1 - beta) * fi + beta * mirr(g)
     return out
 
