@@ -23,6 +23,9 @@
  *   - Every call returns an lbm_status.  On failure lbm_last_error() gives a
  *     one-line message.  A CUDA error poisons the context: every later call
  *     except lbm_last_error/lbm_destroy returns LBM_ESTATE.
+ *   - A context belongs to the CUDA device that is current when lbm_create
+ *     runs; calls on a context with another device current return
+ *     LBM_EINVAL.
  *   - Units are lattice units (dx = dt = 1).
  *
  * Population layout (the interface layout of every populations array):
@@ -181,12 +184,15 @@ lbm_status lbm_get_interface_force(lbm_ctx *ctx, double *vert_force, double *bod
  * every GPU loading the library keeps until the process exits; it calls no
  * cudaMalloc, cudaFree or allocating library routine.  Fixed maxima: 16384
  * surface vertices, 65536 boundary nodes, 65536 cut links; beyond them it
- * returns LBM_ECAPACITY with a message.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress, with that device
- * current), so make that first call before any stream capture.  All calls
- * share the array: calls that overlap on the GPU (several streams or host
- * threads at once) race on it.  The Grad values written into solid slots are
- * the ones the next step writes there anyway.  Synchronises. */
+ * returns LBM_ECAPACITY with a message.  The context's device must be
+ * current (LBM_EINVAL otherwise): the first call on a device looks up the
+ * array's device address for that device (cudaGetSymbolAddress, once per
+ * device, safe when several host threads make their first call together).
+ * The probe synchronises its stream, so it must not be called while that
+ * stream is being captured (LBM_ESTATE).  All calls share the array: calls
+ * that overlap on the GPU (several streams or host threads at once) race on
+ * it.  The Grad values written into solid slots are the ones the next step
+ * writes there anyway.  Synchronises. */
 lbm_status lbm_probe_interface_force_static(lbm_ctx *ctx, double *vert_force, double *body_force);
 
 /* info[4] = {face boundary nodes, immersed boundary nodes, cut links,

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <new>
+#include <mutex>
 #include <vector>
 
 #include "../../include/kbc_lbm.h"
@@ -137,6 +138,7 @@ struct lbm_ctx {
   Grid g;
   Layout lay;
   int Q = 0;
+  int device = 0;            // the CUDA device current at lbm_create (workspace, stream)
   char *ws = nullptr;
   bool own_ws = false;
   cudaStream_t stream = nullptr;
@@ -234,6 +236,11 @@ lbm_status lbm_create(const lbm_config *cfg, void *workspace, size_t workspace_b
   if (!ctx) return LBM_ENOMEM;
   ctx->cfg = *cfg;
   ctx->Q = cfg->lattice;
+  if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+    snprintf(g_create_msg, sizeof(g_create_msg), "lbm_create: no current CUDA device");
+    delete ctx;
+    return LBM_ECUDA;
+  }
   ctx->g = make_grid(*cfg);
   ctx->lay = make_layout(*cfg);
   if (workspace) {
@@ -320,7 +327,21 @@ void lbm_destroy(lbm_ctx *ctx) {
   do {                                                                       \
     if (!ctx) return LBM_EINVAL;                                             \
     if (ctx->poisoned) return fail(ctx, LBM_ESTATE, "context poisoned: %s", ctx->msg); \
+    if (!on_ctx_device(ctx))                                                 \
+      return fail(ctx, LBM_EINVAL, "the current CUDA device is not the context's device %d", \
+                  ctx->device);                                              \
   } while (0)
+
+// The context's stream and workspace belong to the device that was current at
+// lbm_create; every call expects that device to be current again.
+static bool on_ctx_device(const lbm_ctx *ctx) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return dev == ctx->device;
+}
 
 lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const double *rho, const double *u) {
   GUARD();
@@ -921,7 +942,11 @@ constexpr size_t kProbeBytes = kProbeCountOff + kAlign;  // about 5.4 MB
 static __device__ __align__(256) unsigned char g_probe_scratch[kProbeBytes];
 
 constexpr int kProbeMaxDevices = 64;
-static char *g_probe_ptr[kProbeMaxDevices];  // device address of g_probe_scratch per device
+// device address of g_probe_scratch per device, looked up once per device
+// (std::call_once: host threads making their first call together agree)
+static char *g_probe_ptr[kProbeMaxDevices];
+static cudaError_t g_probe_err[kProbeMaxDevices];
+static std::once_flag g_probe_once[kProbeMaxDevices];
 
 }  // namespace
 
@@ -933,18 +958,31 @@ extern "C" lbm_status lbm_probe_interface_force_static(lbm_ctx *ctx, double *ver
     return fail(ctx, LBM_ECAPACITY,
                 "lbm_probe_interface_force_static: %d surface vertices exceed the fixed maximum %d",
                 ctx->nv, kProbeMaxVertices);
+  // the array's address is per device: the context's device must be current
   int dev = 0;
   CK(cudaGetDevice(&dev));
+  if (dev != ctx->device)
+    return fail(ctx, LBM_EINVAL,
+                "lbm_probe_interface_force_static: device %d is current, the context lives on "
+                "device %d",
+                dev, ctx->device);
   if (dev < 0 || dev >= kProbeMaxDevices)
     return fail(ctx, LBM_EINVAL, "lbm_probe_interface_force_static: device %d unsupported", dev);
-  if (!g_probe_ptr[dev]) {
-    // first call on this device (device current): the host-side name of the
-    // array is only a stand-in, the kernels need its device address
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(ctx->stream, &cap));
+  if (cap != cudaStreamCaptureStatusNone)
+    return fail(ctx, LBM_ESTATE,
+                "lbm_probe_interface_force_static: the stream is being captured (the probe "
+                "synchronises)");
+  // first call on this device (device current): the host-side name of the
+  // array is only a stand-in, the kernels need its device address
+  std::call_once(g_probe_once[dev], [dev]() {
     void *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_probe_scratch);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGetSymbolAddress(g_probe_scratch)");
+    g_probe_err[dev] = cudaGetSymbolAddress(&p, g_probe_scratch);
     g_probe_ptr[dev] = (char *)p;
-  }
+  });
+  if (g_probe_err[dev] != cudaSuccess)
+    return cuda_fail(ctx, g_probe_err[dev], "cudaGetSymbolAddress(g_probe_scratch)");
   char *base = g_probe_ptr[dev];
   Link *links = (Link *)(base + kProbeLinksOff);
   BNode *nodes = (BNode *)(base + kProbeNodesOff);

@@ -44,3 +44,31 @@ def test_probe_matches_next_step_force_twice():
         assert np.max(np.abs(vp - vf)) <= 1e-4 * np.max(np.abs(vf))
         assert np.linalg.norm(bf[0]) > 0
     L.check()
+
+
+def test_probe_matches_next_step_force_twice_d3q27():
+    """D3Q27: a sphere in a channel with inlet, outlet, face walls and
+    free-stream faces, so lbm_step fills face and immersed nodes in one split
+    launch while the probe fills the immersed nodes alone."""
+    from paper_1710_02375_gb300 import lbm
+    from paper_1710_02375_gb300.lbm import Lattice
+    nx, ny, nz = 36, 20, 18
+    fu = np.zeros((6, 3))
+    fu[0, 0] = fu[4, 0] = fu[5, 0] = 0.03
+    x, e = synth.icosphere((12.3, 9.6, 8.7), 4.2, level=2)
+    body = np.zeros(len(e), np.int32)
+    L = Lattice(27, nx, ny, nz, 0.95, bc=(2, 3, 1, 1, 4, 4), face_velocity=fu, max_links=20000,
+                max_vertices=len(x), max_elements=len(e), inlet_ramp_steps=50)
+    L.set_geometry(x, e, body)
+    L.init_equilibrium(np.ones((nz, ny, nx)), np.zeros((3, nz, ny, nx)))
+    L.step(100)
+    for _ in range(2):
+        vp = np.zeros((len(x), 3))
+        bp = np.zeros((1, 3))
+        lbm.lbm_probe_interface_force_static(L.ctx, vp, bp)
+        L.step(1)
+        vf, bf = L.interface_force()
+        assert np.linalg.norm(bf[0]) > 0
+        assert np.linalg.norm(bp[0] - bf[0]) <= 1e-4 * np.linalg.norm(bf[0])
+        assert np.max(np.abs(vp - vf)) <= 1e-4 * np.max(np.abs(vf))
+    L.check()
