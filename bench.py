@@ -279,10 +279,11 @@ def run_ours(args):
     e2e_val = replica_rate(world, nodes, e2e_steps, e2e_s)
     L.close()
 
-    # ---- reduced-precision storage (FP16 / BF16 of f/W - 1) on the same
-    # workload, as speedups over the FP32 form above
+    # ---- reduced-precision storage (IEEE half, bfloat16 and the narrow-range
+    # 16-bit float F16N of f/W - 1) on the same workload, as speedups over
+    # the FP32 form above
     patterns = {}
-    for name, storage in (("f16", 1), ("bf16", 2)):
+    for name, storage in (("f16", 1), ("bf16", 2), ("f16n", 4)):
         Lp = Lattice(Q, N_LATTICE, N_LATTICE, N_LATTICE, beta, storage=storage, stream=stream)
         Lp.init_equilibrium(rho, u)
         Lp.step(args.warmup)

@@ -62,8 +62,14 @@ enum { LBM_D2Q9 = 9, LBM_D3Q27 = 27 };
 /* Storage of populations in device memory (computation is always FP32):
  *   F32  stores f_i - W_i        (deviation from the lattice weight)
  *   F16  stores f_i / W_i - 1    (scaled deviation, IEEE half, round to nearest even)
- *   BF16 stores f_i / W_i - 1    (scaled deviation, bfloat16, round to nearest even) */
-enum { LBM_STORE_F32 = 0, LBM_STORE_F16 = 1, LBM_STORE_BF16 = 2 };
+ *   BF16 stores f_i / W_i - 1    (scaled deviation, bfloat16, round to nearest even)
+ *   F16N stores f_i / W_i - 1    (scaled deviation, 16-bit float with the
+ *        exponent range narrowed to [2^-6, 2): sign, 3 exponent bits, 12
+ *        stored significand bits, evenly spaced steps of 2^-18 below 2^-6;
+ *        round to nearest, ties away from zero; |f_i/W_i - 1| >= 2 saturates).
+ *        The same bytes as F16 with a step four times finer for the O(u)
+ *        deviations.  (Code 3 is not used.) */
+enum { LBM_STORE_F32 = 0, LBM_STORE_F16 = 1, LBM_STORE_BF16 = 2, LBM_STORE_F16N = 4 };
 
 /* Collision: KBC (entropic multi-relaxation time, gamma from
  * Eq. gamma_min_approx) or BGK (gamma fixed to 2, i.e. LBGK with omega = 2 beta). */

@@ -39,9 +39,9 @@ __host__ __device__ constexpr double weight(int i) {
 }
 
 // ---- storage of one population ------------------------------------------
-// F32 keeps g = f - W; F16 / BF16 keep h = f/W - 1 so that every direction
-// uses the full mantissa around O(u) deviations.
-enum { STORE_F32 = 0, STORE_F16 = 1, STORE_BF16 = 2 };
+// F32 keeps g = f - W; F16 / BF16 / F16N keep h = f/W - 1 so that every
+// direction uses the full mantissa around O(u) deviations.
+enum { STORE_F32 = 0, STORE_F16 = 1, STORE_BF16 = 2, STORE_F16N = 4 };
 
 template <int S>
 struct Store;
@@ -94,6 +94,48 @@ struct Store<STORE_BF16> {
   }
   __device__ __forceinline__ static double decode(T v, double w) {
     return w * (double)__bfloat162float(v);
+  }
+};
+
+// F16N: a 16-bit float of h = f/W - 1 with its exponent range narrowed to
+// what h needs: sign, 3 exponent bits, 12 stored significand bits.  Codes
+// e = 1..7 hold (1 + m/4096) 2^(e-7), |h| in [2^-6, 2); e = 0 holds m 2^-18
+// (evenly spaced below 2^-6).  Against IEEE half (5 exponent bits, 10 stored
+// significand bits) the step is four times finer wherever |h| >= 2^-6, which
+// covers the O(u) deviations of the moving populations; |h| >= 2 saturates
+// at the largest code (h is below 1.4 for |u| <= 0.1).
+// The 15 magnitude bits shifted left by 11 are the FP32 bit pattern of
+// |h| 2^-120 (codes e = 0 land on FP32 subnormals, which keep their exact
+// value: no flush-to-zero in this build), so decoding is two shifts, one
+// logic operation and the multiply by W 2^120; encoding is the multiply by
+// 2^-120 / W, rounding the 11 dropped bits to nearest (ties away from zero)
+// with an integer add that carries into the exponent, and a saturating min.
+template <>
+struct Store<STORE_F16N> {
+  using T = uint16_t;
+  static constexpr int bytes = 2;
+  __device__ __forceinline__ static float bits_to_scaled(uint32_t c) {
+    return __uint_as_float(((c & 0x8000u) << 16) | ((c & 0x7FFFu) << 11));  // |h| 2^-120, signed
+  }
+  __device__ __forceinline__ static uint16_t scaled_to_bits(float x) {
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t a = min((b & 0x7FFFFFFFu) + 0x400u, 0x3FFFFFFu);
+    return (uint16_t)(((b >> 16) & 0x8000u) | (a >> 11));
+  }
+  __device__ __forceinline__ static float load(const T *p, float w) {
+    return bits_to_scaled(__ldg(p)) * (w * 0x1p120f);
+  }
+  __device__ __forceinline__ static float load_smem(const T *p, float w) {
+    return bits_to_scaled(*p) * (w * 0x1p120f);
+  }
+  __device__ __forceinline__ static void store(T *p, float g, float invw) {
+    *p = scaled_to_bits(g * (invw * 0x1p-120f));
+  }
+  __device__ __forceinline__ static T encode(double g, double w) {
+    return scaled_to_bits((float)(g / w * 0x1p-120));
+  }
+  __device__ __forceinline__ static double decode(T v, double w) {
+    return w * 0x1p120 * (double)bits_to_scaled(v);
   }
 };
 

@@ -107,7 +107,9 @@ const char *validate(const lbm_config *c) {
   if (c->lattice == LBM_D2Q9 && c->nz != 1) return "D2Q9 needs nz == 1";
   if (c->ny > 65535 || c->nz > 65535) return "ny and nz must be <= 65535";
   if (!(c->beta > 0.0 && c->beta < 1.0)) return "beta must lie in (0, 1)";
-  if (c->storage < LBM_STORE_F32 || c->storage > LBM_STORE_BF16) return "unknown storage";
+  if (c->storage != LBM_STORE_F32 && c->storage != LBM_STORE_F16 && c->storage != LBM_STORE_BF16 &&
+      c->storage != LBM_STORE_F16N)
+    return "unknown storage";
   if (c->collision != LBM_COLLIDE_KBC && c->collision != LBM_COLLIDE_BGK)
     return "unknown collision";
   const int naxes = c->lattice == LBM_D2Q9 ? 2 : 3;

@@ -18,10 +18,12 @@ namespace kbc {
       if (storage == STORE_F32) { constexpr int QQ = 9, SS = STORE_F32; __VA_ARGS__; }     \
       if (storage == STORE_F16) { constexpr int QQ = 9, SS = STORE_F16; __VA_ARGS__; }     \
       if (storage == STORE_BF16) { constexpr int QQ = 9, SS = STORE_BF16; __VA_ARGS__; }   \
+      if (storage == STORE_F16N) { constexpr int QQ = 9, SS = STORE_F16N; __VA_ARGS__; }   \
     } else if (Q == 27) {                                                           \
       if (storage == STORE_F32) { constexpr int QQ = 27, SS = STORE_F32; __VA_ARGS__; }    \
       if (storage == STORE_F16) { constexpr int QQ = 27, SS = STORE_F16; __VA_ARGS__; }    \
       if (storage == STORE_BF16) { constexpr int QQ = 27, SS = STORE_BF16; __VA_ARGS__; }  \
+      if (storage == STORE_F16N) { constexpr int QQ = 27, SS = STORE_F16N; __VA_ARGS__; }  \
     }                                                                               \
     return cudaErrorInvalidValue;                                                   \
   } while (0)

@@ -47,6 +47,7 @@ def test_bad_configs_rejected_on_host(lib):
         lbm.make_config(27, 8, 8, 8, 1.5),                # beta outside (0,1)
         lbm.make_config(27, 0, 8, 8, 0.9),                # empty lattice
         lbm.make_config(27, 8, 8, 8, 0.9, storage=7),     # unknown storage
+        lbm.make_config(27, 8, 8, 8, 0.9, storage=3),     # unused storage code
         lbm.make_config(27, 8, 8, 8, 0.9, bc=(0, 1, 0, 0, 0, 0)),  # unpaired periodic face
     ]
     for cfg in bad:
@@ -62,8 +63,10 @@ def test_workspace_size_counts_populations(lib):
     from paper_1710_02375_gb300 import lbm
     a = lbm.lbm_workspace_size(lbm.make_config(27, 64, 64, 64, 0.9))
     b = lbm.lbm_workspace_size(lbm.make_config(27, 64, 64, 64, 0.9, storage=lbm.LBM_STORE_F16))
+    c = lbm.lbm_workspace_size(lbm.make_config(27, 64, 64, 64, 0.9, storage=lbm.LBM_STORE_F16N))
     pops = 2 * 27 * 64 ** 3
     assert a - b == pops * 2
+    assert b == c
     assert a >= pops * 4
 
 
