@@ -450,15 +450,22 @@ lbm_status lbm_get_macros(lbm_ctx *ctx, double *rho, double *u);
  * layouts and memory kinds.  Synchronises. */
 lbm_status lbm_get_macros_f32(lbm_ctx *ctx, float *rho, float *u);
 
-/* Kernel form of the fused sweep.  AUTO (default) and DIRECT: one thread per
- * node, Q coalesced global loads and stores.  ROWS: a persistent kernel that
- * fetches the Q source rows of every output row into shared memory with bulk
- * asynchronous copies (mbarrier pipeline), when its shared-memory plan fits
- * the device.  ASYNC (FP32 storage): each thread prefetches the 27 source
- * values of its node in the next row with per-thread asynchronous copies into
- * shared memory while it collides the current one (other storage: DIRECT).
- * Results are identical.  LBM_EINVAL for an unknown value. */
-enum { LBM_SWEEP_AUTO = 0, LBM_SWEEP_DIRECT = 1, LBM_SWEEP_ROWS = 2, LBM_SWEEP_ASYNC = 3 };
+/* Kernel form of the fused sweep.  AUTO (default) and PAIR: one thread per
+ * two neighbouring nodes of a row, the collision of both on the paired FP32
+ * instructions (two results per instruction), the c_x = 0 sources as aligned
+ * two-element loads and the results as two-element stores.  DIRECT: one
+ * thread per node, Q coalesced global loads and stores.  ROWS: a persistent
+ * kernel that fetches the Q source rows of every output row into shared
+ * memory with bulk asynchronous copies (mbarrier pipeline), when its
+ * shared-memory plan fits the device.  ASYNC (FP32 storage): each thread
+ * prefetches the 27 source values of its node in the next row with
+ * per-thread asynchronous copies into shared memory while it collides the
+ * current one (other storage: DIRECT).  DIRECT, ROWS and ASYNC give
+ * identical results; PAIR performs the same IEEE operations on the paired
+ * instructions and agrees with them to the last bit or so.  LBM_EINVAL for
+ * an unknown value. */
+enum { LBM_SWEEP_AUTO = 0, LBM_SWEEP_DIRECT = 1, LBM_SWEEP_ROWS = 2, LBM_SWEEP_ASYNC = 3,
+       LBM_SWEEP_PAIR = 4 };
 lbm_status lbm_set_sweep_variant(lbm_ctx *ctx, int variant);
 
 /* Wait for the stream and report LBM_EUNSTABLE if any sweep since the last

@@ -22,32 +22,94 @@
 
 namespace kbc {
 
-struct AxisEq {
-  float e[3];   // phi(c) - 1 for c = -1, 0, +1
-  float r[3];   // 1 / (w(c) phi(c)): per-axis factor of the entropic metric 1/feq
-  float d;      // S - 1
+// ---- arithmetic on one node (float) or on two nodes at once (f2) ----------
+// f2 holds the same quantity of two nodes; its operations issue the paired
+// FP32 instructions of sm_100+ (one instruction, two IEEE results), so the
+// two-node sweep spends half the FP32 issue slots per node.  The special
+// functions (reciprocal, reciprocal square root) stay one per value.
+struct f2 {
+  float2 v;
 };
+__device__ __forceinline__ f2 mk2(float a, float b) { return f2{make_float2(a, b)}; }
+template <class V>
+__device__ __forceinline__ V vc(float a);
+template <>
+__device__ __forceinline__ float vc<float>(float a) { return a; }
+template <>
+__device__ __forceinline__ f2 vc<f2>(float a) { return mk2(a, a); }
 
-__device__ __forceinline__ AxisEq axis_eq(float u) {
-  AxisEq a;
-  const float u2 = u * u;
-  const float x = fmaf(3.0f, u2, 1.0f);
-  const float S = x * rsqrtf(x);                       // sqrt(1 + 3u^2)
-  const float d = __fdividef(3.0f * u2, 1.0f + S);     // S - 1 without cancellation
-  const float om = 1.0f - d;                           // 2 - S
-  const float ip = __fdividef(1.0f, 1.0f - u);
-  const float im = __fdividef(1.0f, 1.0f + u);
-  a.e[1] = -d;
-  a.e[2] = fmaf(om, (d + 3.0f * u) * ip, -d);
-  a.e[0] = fmaf(om, (d - 3.0f * u) * im, -d);
-  a.r[0] = __fdividef(6.0f, 1.0f + a.e[0]);
-  a.r[1] = __fdividef(1.5f, om);
-  a.r[2] = __fdividef(6.0f, 1.0f + a.e[2]);
+// The float forms are the IEEE operations of the paired ones (no contraction
+// of a product into a following sum), so one-node and two-node sweeps agree
+// to the last bit.
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ f2 vadd(f2 a, f2 b) { return f2{__fadd2_rn(a.v, b.v)}; }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+// a - b as fma(b, -1, a): exact product, one rounding, one paired instruction
+__device__ __forceinline__ f2 vsub(f2 a, f2 b) {
+  return f2{__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)};
+}
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ f2 vmul(f2 a, f2 b) { return f2{__fmul2_rn(a.v, b.v)}; }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ f2 vfma(f2 a, f2 b, f2 c) { return f2{__ffma2_rn(a.v, b.v, c.v)}; }
+__device__ __forceinline__ float vrsqrt(float a) { return rsqrtf(a); }
+__device__ __forceinline__ f2 vrsqrt(f2 a) { return mk2(rsqrtf(a.v.x), rsqrtf(a.v.y)); }
+__device__ __forceinline__ float vdivf(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ f2 vdivf(f2 a, f2 b) {
+  return mk2(__fdividef(a.v.x, b.v.x), __fdividef(a.v.y, b.v.y));
+}
+
+template <class V>
+struct AxisEqT {
+  V e[3];  // phi(c) - 1 for c = -1, 0, +1
+  V r[3];  // 1 / (w(c) phi(c)): per-axis factor of the entropic metric 1/feq
+  V d;     // S - 1
+};
+using AxisEq = AxisEqT<float>;
+
+template <class V>
+__device__ __forceinline__ AxisEqT<V> axis_eq(V u) {
+  AxisEqT<V> a;
+  const V u2 = vmul(u, u);
+  const V x = vfma(vc<V>(3.0f), u2, vc<V>(1.0f));
+  const V S = vmul(x, vrsqrt(x));                                  // sqrt(1 + 3u^2)
+  const V d = vdivf(vmul(vc<V>(3.0f), u2), vadd(vc<V>(1.0f), S));  // S - 1 without cancellation
+  const V om = vsub(vc<V>(1.0f), d);                               // 2 - S
+  const V ip = vdivf(vc<V>(1.0f), vsub(vc<V>(1.0f), u));
+  const V im = vdivf(vc<V>(1.0f), vadd(vc<V>(1.0f), u));
+  const V u3 = vmul(vc<V>(3.0f), u);
+  const V nd = vsub(vc<V>(0.0f), d);
+  a.e[1] = nd;
+  a.e[2] = vfma(om, vmul(vadd(d, u3), ip), nd);
+  a.e[0] = vfma(om, vmul(vsub(d, u3), im), nd);
+  a.r[0] = vdivf(vc<V>(6.0f), vadd(vc<V>(1.0f), a.e[0]));
+  a.r[1] = vdivf(vc<V>(1.5f), om);
+  a.r[2] = vdivf(vc<V>(6.0f), vadd(vc<V>(1.0f), a.e[2]));
   a.d = d;
   return a;
 }
 
-// In-place collision of g[Q] (deviations g_i = f_i - W_i).  Returns rho.
+// gamma of Eq. (gamma_min_approx) from the two entropic products, held in
+// [0, 2/beta]; 2 (LBGK) when bgk or <dh|dh> <= 1e-30.
+__device__ __forceinline__ float kbc_gamma(float sh, float hh, float ib, bool bgk) {
+  float gamma = 2.f;
+  if (!bgk && hh > 1e-30f) {
+    gamma = ib - (2.f - ib) * __fdividef(sh, hh);
+    // the vertex of the quadratic entropy norm clipped to the rates at which
+    // the higher-order part does not grow, |1 - beta gamma| <= 1
+    gamma = fminf(fmaxf(gamma, 0.f), 2.f * ib);
+  }
+  return gamma;
+}
+__device__ __forceinline__ float vgamma(float sh, float hh, float ib, bool bgk) {
+  return kbc_gamma(sh, hh, ib, bgk);
+}
+__device__ __forceinline__ f2 vgamma(f2 sh, f2 hh, float ib, bool bgk) {
+  return mk2(kbc_gamma(sh.v.x, hh.v.x, ib, bgk), kbc_gamma(sh.v.y, hh.v.y, ib, bgk));
+}
+
+// In-place collision of g[Q] (deviations g_i = f_i - W_i), of one node (V =
+// float) or of two nodes (V = f2).  Returns rho.
 //
 // Sums are taken in the tensor-product structure of the lattice (rows of
 // three x-neighbours, then planes), the equilibrium factors and the metric
@@ -57,178 +119,198 @@ __device__ __forceinline__ AxisEq axis_eq(float u) {
 // CONSERVE: remove the FP32 rounding residue of mass and momentum from the
 // non-equilibrium part (used with FP32 storage, where it would otherwise be
 // the dominant error; with 16-bit storage the storage rounding dominates).
-template <class L, bool CONSERVE = true>
-__device__ __forceinline__ float collide(float (&g)[L::Q], float beta, bool bgk) {
+template <class L, bool CONSERVE, class V>
+__device__ __forceinline__ V collide_v(V (&g)[L::Q], float beta, bool bgk) {
   constexpr int Q = L::Q;
   constexpr int NR = Q / 3;  // rows of three x-neighbours (cy, cz)
+  const V zero = vc<V>(0.f);
   // ---- moments of the deviations (Eq. conservationLaws and second moments)
-  float rs[NR], rd[NR], rm[NR];  // per row: g+ + g-, g+ - g-, g- + g0 + g+
+  V rs[NR], rd[NR], rm[NR];  // per row: g+ + g-, g+ - g-, g- + g0 + g+
 #pragma unroll
   for (int r = 0; r < NR; ++r) {
-    rs[r] = g[3 * r + 2] + g[3 * r];
-    rd[r] = g[3 * r + 2] - g[3 * r];
-    rm[r] = rs[r] + g[3 * r + 1];
+    rs[r] = vadd(g[3 * r + 2], g[3 * r]);
+    rd[r] = vsub(g[3 * r + 2], g[3 * r]);
+    rm[r] = vadd(rs[r], g[3 * r + 1]);
   }
   // row r has cy = r % 3 - 1, cz = r / 3 - 1
-  float drho = 0.f, jx = 0.f, pxx = 0.f;
-  float yp = 0.f, ym = 0.f, zp = 0.f, zm = 0.f;      // sums of rm over cy = +-1, cz = +-1
-  float pxy = 0.f, pxz = 0.f, pyz = 0.f;
+  V drho = zero, jx = zero, pxx = zero;
+  V yp = zero, ym = zero, zp = zero, zm = zero;  // sums of rm over cy = +-1, cz = +-1
+  V pxy = zero, pxz = zero, pyz = zero;
 #pragma unroll
   for (int r = 0; r < NR; ++r) {
     const int cy = r % 3 - 1, cz = (L::D == 3) ? r / 3 - 1 : 0;
-    drho += rm[r];
-    jx += rd[r];
-    pxx += rs[r];
-    if (cy > 0) yp += rm[r];
-    if (cy < 0) ym += rm[r];
-    if (cz > 0) zp += rm[r];
-    if (cz < 0) zm += rm[r];
-    if (cy) pxy += cy * rd[r];
-    if (cz) pxz += cz * rd[r];
-    if (cy && cz) pyz += cy * cz * rm[r];
+    drho = vadd(drho, rm[r]);
+    jx = vadd(jx, rd[r]);
+    pxx = vadd(pxx, rs[r]);
+    if (cy > 0) yp = vadd(yp, rm[r]);
+    if (cy < 0) ym = vadd(ym, rm[r]);
+    if (cz > 0) zp = vadd(zp, rm[r]);
+    if (cz < 0) zm = vadd(zm, rm[r]);
+    if (cy > 0) pxy = vadd(pxy, rd[r]);
+    if (cy < 0) pxy = vsub(pxy, rd[r]);
+    if (cz > 0) pxz = vadd(pxz, rd[r]);
+    if (cz < 0) pxz = vsub(pxz, rd[r]);
+    if (cy * cz > 0) pyz = vadd(pyz, rm[r]);
+    if (cy * cz < 0) pyz = vsub(pyz, rm[r]);
   }
-  const float jy = yp - ym, pyy = yp + ym;
-  const float jz = zp - zm, pzz = zp + zm;
+  const V jy = vsub(yp, ym), pyy = vadd(yp, ym);
+  const V jz = vsub(zp, zm), pzz = vadd(zp, zm);
 
-  const float rho = 1.0f + drho;
-  const float irho = __fdividef(1.0f, rho);
-  const float ux = jx * irho, uy = jy * irho, uz = jz * irho;
+  const V rho = vadd(vc<V>(1.0f), drho);
+  const V irho = vdivf(vc<V>(1.0f), rho);
+  const V ux = vmul(jx, irho), uy = vmul(jy, irho), uz = vmul(jz, irho);
 
-  const AxisEq ax = axis_eq(ux), ay = axis_eq(uy);
-  AxisEq az;
+  const AxisEqT<V> ax = axis_eq(ux), ay = axis_eq(uy);
+  AxisEqT<V> az;
   if (L::D == 3) az = axis_eq(uz);
 
   // ---- shear part of f - feq from the deviatoric non-equilibrium stress
   // dPi_aa = P_aa - (drho + 2 rho d_a)/3, dPi_ab = P_ab - rho u_a u_b
-  const float dxx = pxx - (drho + 2.f * rho * ax.d) * (1.f / 3.f);
-  const float dyy = pyy - (drho + 2.f * rho * ay.d) * (1.f / 3.f);
-  float sv[6];  // ds of the x, y, z faces and of the xy, xz, yz edges (sign +)
+  const V rho2 = vmul(vc<V>(2.f), rho);
+  const V third = vc<V>(1.f / 3.f);
+  const V dxx = vsub(pxx, vmul(vfma(rho2, ax.d, drho), third));
+  const V dyy = vsub(pyy, vmul(vfma(rho2, ay.d, drho), third));
+  V sv[6];  // ds of the x, y, z faces and of the xy, xz, yz edges (sign +)
+  const V quarter = vc<V>(0.25f);
   if (L::D == 2) {
-    const float N = dxx - dyy;
-    sv[0] = 0.25f * N;
-    sv[1] = -0.25f * N;
-    sv[2] = 0.f;
-    sv[3] = 0.25f * (pxy - rho * ux * uy);
-    sv[4] = sv[5] = 0.f;
+    const V N = vsub(dxx, dyy);
+    sv[0] = vmul(quarter, N);
+    sv[1] = vmul(vc<V>(-0.25f), N);
+    sv[2] = zero;
+    sv[3] = vmul(quarter, vsub(pxy, vmul(vmul(rho, ux), uy)));
+    sv[4] = sv[5] = zero;
   } else {
-    const float dzz = pzz - (drho + 2.f * rho * az.d) * (1.f / 3.f);
-    const float Nxz = dxx - dzz, Nyz = dyy - dzz;
-    sv[0] = (2.f * Nxz - Nyz) * (1.f / 6.f);
-    sv[1] = (2.f * Nyz - Nxz) * (1.f / 6.f);
-    sv[2] = -(Nxz + Nyz) * (1.f / 6.f);
-    sv[3] = 0.25f * (pxy - rho * ux * uy);
-    sv[4] = 0.25f * (pxz - rho * ux * uz);
-    sv[5] = 0.25f * (pyz - rho * uy * uz);
+    const V dzz = vsub(pzz, vmul(vfma(rho2, az.d, drho), third));
+    const V Nxz = vsub(dxx, dzz), Nyz = vsub(dyy, dzz);
+    const V sixth = vc<V>(1.f / 6.f);
+    sv[0] = vmul(vsub(vadd(Nxz, Nxz), Nyz), sixth);
+    sv[1] = vmul(vsub(vadd(Nyz, Nyz), Nxz), sixth);
+    sv[2] = vmul(vadd(Nxz, Nyz), vc<V>(-1.f / 6.f));
+    const V rux = vmul(rho, ux);
+    sv[3] = vmul(quarter, vsub(pxy, vmul(rux, uy)));
+    sv[4] = vmul(quarter, vsub(pxz, vmul(rux, uz)));
+    sv[5] = vmul(quarter, vsub(pyz, vmul(vmul(rho, uy), uz)));
   }
 
   // ---- per-direction non-equilibrium part and the entropic products
-  // (1 + e_x)(1 + e_y) - 1 = e_x + e_y (1 + e_x), and likewise with e_z
-  float exy[9], qxy[9], mxy[9];
-  float px1[3];
+  // (1 + e_x)(1 + e_y) - 1 = e_x + e_y (1 + e_x), and likewise with e_z.
+  // Directions are visited by (c_x, c_y) pair k2 with c_z innermost, so the
+  // x-y factors of a pair live only while its (up to) three directions are
+  // processed; the non-equilibrium part df_i is not kept: the relaxation
+  // below forms it again by the same operations (same value).
+  V px1[3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) px1[a] = 1.0f + ax.e[a];
+  for (int a = 0; a < 3; ++a) px1[a] = vadd(vc<V>(1.0f), ax.e[a]);
+  V grp[6] = {zero, zero, zero, zero, zero, zero};  // signed sums of m_i dh_i per ds group
+  V hh = zero;
+  // mass and momentum of df (zero in exact arithmetic; see CONSERVE)
+  V qm = zero, qx = zero, qy = zero, qz = zero;
 #pragma unroll
-  for (int b = 0; b < 3; ++b)
+  for (int k2 = 0; k2 < 9; ++k2) {
+    const int a = k2 % 3, b = k2 / 3;  // a = cx + 1, b = cy + 1
+    const V exy = vfma(ay.e[b], px1[a], ax.e[a]);
+    const V qxy = vadd(vc<V>(1.0f), exy);
+    const V mxy = vmul(ax.r[a], ay.r[b]);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      exy[3 * b + a] = fmaf(ay.e[b], px1[a], ax.e[a]);
-      if (L::D == 3) qxy[3 * b + a] = 1.0f + exy[3 * b + a];
-      mxy[3 * b + a] = ax.r[a] * ay.r[b];
+    for (int zc = 0; zc < (L::D == 3 ? 3 : 1); ++zc) {
+      const int i = (L::D == 3 ? 9 * zc : 0) + k2;
+      const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+      V e = exy, m = mxy;
+      if (L::D == 3) {
+        e = vfma(az.e[cz + 1], qxy, e);
+        m = vmul(m, az.r[cz + 1]);
+      }
+      // feq_i - W_i = W_i (drho + rho e_i);  df_i = g_i - (feq_i - W_i)
+      const V d = vfma(vc<V>(-(float)weight<L>(i)), vfma(rho, e, drho), g[i]);
+      const int nnz = (cx != 0) + (cy != 0) + (cz != 0);
+      int gi = -1, sg = 1;
+      if (nnz == 1) gi = cx ? 0 : (cy ? 1 : 2);
+      if (nnz == 2) {
+        if (cx && cy) { gi = 3; sg = cx * cy; }
+        else if (cx && cz) { gi = 4; sg = cx * cz; }
+        else { gi = 5; sg = cy * cz; }
+      }
+      V dh = d;
+      if (gi >= 0) dh = (sg > 0) ? vsub(d, sv[gi]) : vadd(d, sv[gi]);
+      const V t = vmul(m, dh);
+      hh = vfma(t, dh, hh);
+      if (gi >= 0) grp[gi] = (sg > 0) ? vadd(grp[gi], t) : vsub(grp[gi], t);
+      if (CONSERVE) {
+        qm = vadd(qm, d);
+        if (cx > 0) qx = vadd(qx, d);
+        if (cx < 0) qx = vsub(qx, d);
+        if (cy > 0) qy = vadd(qy, d);
+        if (cy < 0) qy = vsub(qy, d);
+        if (cz > 0) qz = vadd(qz, d);
+        if (cz < 0) qz = vsub(qz, d);
+      }
     }
-  float df[Q];
-  float grp[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // signed sums of m_i dh_i per ds group
-  float hh = 0.f;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-    const int k2 = 3 * (cy + 1) + (cx + 1);
-    float e = exy[k2], m = mxy[k2];
-    if (L::D == 3) {
-      e = fmaf(az.e[cz + 1], qxy[k2], e);
-      m *= az.r[cz + 1];
-    }
-    // feq_i - W_i = W_i (drho + rho e_i);  df_i = g_i - (feq_i - W_i)
-    const float d = fmaf(-(float)weight<L>(i), fmaf(rho, e, drho), g[i]);
-    df[i] = d;
-    const int nnz = (cx != 0) + (cy != 0) + (cz != 0);
-    int gi = -1, sg = 1;
-    if (nnz == 1) gi = cx ? 0 : (cy ? 1 : 2);
-    if (nnz == 2) {
-      if (cx && cy) { gi = 3; sg = cx * cy; }
-      else if (cx && cz) { gi = 4; sg = cx * cz; }
-      else { gi = 5; sg = cy * cz; }
-    }
-    const float dh = (gi >= 0) ? d - sg * sv[gi < 0 ? 0 : gi] : d;
-    const float t = m * dh;
-    hh = fmaf(t, dh, hh);
-    if (gi >= 0) grp[gi] += sg * t;
   }
-  float sh = 0.f;
+  V sh = zero;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) sh = fmaf(sv[k], grp[k], sh);
+  for (int k = 0; k < 6; ++k) sh = vfma(sv[k], grp[k], sh);
 
   const float ib = __fdividef(1.0f, beta);
-  float gamma = 2.f;
   // <.|.> carries a common factor rho that cancels in the ratio
-  if (!bgk && hh > 1e-30f) {
-    gamma = ib - (2.f - ib) * __fdividef(sh, hh);
-    // the vertex of the quadratic entropy norm clipped to the rates at which
-    // the higher-order part does not grow, |1 - beta gamma| <= 1
-    gamma = fminf(fmaxf(gamma, 0.f), 2.f * ib);
-  }
+  const V gamma = vgamma(sh, hh, ib, bgk);
 
-  // ---- conservation of the FP32 update: df carries no mass or momentum in
-  // exact arithmetic; its rounding residue (dm, dj) would otherwise leak into
-  // the conserved moments every step, so it is removed along W_i (1, 3 c_i).
-  float qm = 0.f, qx = 0.f, qyp = 0.f, qym = 0.f, qzp = 0.f, qzm = 0.f;
+  // ---- relaxation f' = f - beta (2 ds + gamma dh) = f - beta (gamma df + (2 - gamma) ds).
+  // Conservation of the FP32 update (CONSERVE): df carries no mass or
+  // momentum in exact arithmetic; its rounding residue (qm, q) would otherwise
+  // leak into the conserved moments every step, so it is removed along
+  // W_i (1, 3 c_i).
+  const V bg = vmul(vc<V>(beta), gamma);
+  const V b2g = vmul(vc<V>(beta), vsub(vc<V>(2.f), gamma));
+  const V bg3 = vmul(vc<V>(3.f), bg);
+  const V A = vmul(bg, qm), Bx = vmul(bg3, qx), By = vmul(bg3, qy), Bz = vmul(bg3, qz);
+  V bs[6], nbs[6];
 #pragma unroll
-  for (int r = 0; r < (CONSERVE ? NR : 0); ++r) {
-    const int cy = r % 3 - 1, cz = (L::D == 3) ? r / 3 - 1 : 0;
-    const float m = df[3 * r] + df[3 * r + 1] + df[3 * r + 2];
-    qm += m;
-    qx += df[3 * r + 2] - df[3 * r];
-    if (cy > 0) qyp += m;
-    if (cy < 0) qym += m;
-    if (cz > 0) qzp += m;
-    if (cz < 0) qzm += m;
-  }
-
-  // ---- relaxation f' = f - beta (2 ds + gamma dh) = f - beta (gamma df + (2 - gamma) ds)
-  const float bg = beta * gamma, b2g = beta * (2.f - gamma);
-  const float A = bg * qm, Bx = 3.f * bg * qx, By = 3.f * bg * (qyp - qym),
-              Bz = 3.f * bg * (qzp - qzm);
-  float bs[6];
-#pragma unroll
-  for (int k = 0; k < 6; ++k) bs[k] = b2g * sv[k];
-  // projection term A + c_i.B built row by row: (cy, cz) part once per row
-  float tyz[NR];
-#pragma unroll
-  for (int r = 0; r < NR; ++r) {
-    const int cy = r % 3 - 1, cz = (L::D == 3) ? r / 3 - 1 : 0;
-    float t = A;
-    if (cy) t += cy * By;
-    if (cz) t += cz * Bz;
-    tyz[r] = t;
+  for (int k = 0; k < 6; ++k) {
+    bs[k] = vmul(b2g, sv[k]);
+    nbs[k] = vsub(zero, bs[k]);
   }
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-    const int nnz = (cx != 0) + (cy != 0) + (cz != 0);
-    float sds = 0.f;
-    if (nnz == 1) sds = cx ? bs[0] : (cy ? bs[1] : bs[2]);
-    if (nnz == 2) {
-      if (cx && cy) sds = cx * cy * bs[3];
-      else if (cx && cz) sds = cx * cz * bs[4];
-      else sds = cy * cz * bs[5];
+  for (int k2 = 0; k2 < 9; ++k2) {
+    const int a = k2 % 3, b = k2 / 3;
+    const V exy = vfma(ay.e[b], px1[a], ax.e[a]);
+    const V qxy = vadd(vc<V>(1.0f), exy);
+#pragma unroll
+    for (int zc = 0; zc < (L::D == 3 ? 3 : 1); ++zc) {
+      const int i = (L::D == 3 ? 9 * zc : 0) + k2;
+      const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+      V e = exy;
+      if (L::D == 3) e = vfma(az.e[cz + 1], qxy, e);
+      const V d = vfma(vc<V>(-(float)weight<L>(i)), vfma(rho, e, drho), g[i]);
+      const int nnz = (cx != 0) + (cy != 0) + (cz != 0);
+      V sds = zero;
+      int gk = -1, sg = 1;
+      if (nnz == 1) gk = cx ? 0 : (cy ? 1 : 2);
+      if (nnz == 2) {
+        if (cx && cy) { gk = 3; sg = cx * cy; }
+        else if (cx && cz) { gk = 4; sg = cx * cz; }
+        else { gk = 5; sg = cy * cz; }
+      }
+      if (gk >= 0) sds = (sg > 0) ? bs[gk] : nbs[gk];
+      if (CONSERVE) {
+        V t = A;
+        if (cx > 0) t = vadd(t, Bx);
+        if (cx < 0) t = vsub(t, Bx);
+        if (cy > 0) t = vadd(t, By);
+        if (cy < 0) t = vsub(t, By);
+        if (cz > 0) t = vadd(t, Bz);
+        if (cz < 0) t = vsub(t, Bz);
+        sds = vfma(vc<V>(-(float)weight<L>(i)), t, sds);
+      }
+      g[i] = vsub(g[i], vfma(bg, d, sds));
     }
-    if (CONSERVE) {
-      float t = tyz[i / 3];
-      if (cx) t += cx * Bx;
-      sds = fmaf(-(float)weight<L>(i), t, sds);
-    }
-    g[i] = g[i] - fmaf(bg, df[i], sds);
   }
   return rho;
+}
+
+// One node in FP32 (the form every single-node kernel uses).
+template <class L, bool CONSERVE = true>
+__device__ __forceinline__ float collide(float (&g)[L::Q], float beta, bool bgk) {
+  return collide_v<L, CONSERVE, float>(g, beta, bgk);
 }
 
 }  // namespace kbc

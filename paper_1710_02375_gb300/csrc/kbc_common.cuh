@@ -55,6 +55,13 @@ struct Store<STORE_F32> {
   __device__ __forceinline__ static void store(T *p, float g, float /*invw*/) { *p = g; }
   __device__ __forceinline__ static T encode(double g, double /*w*/) { return (float)g; }
   __device__ __forceinline__ static double decode(T v, double /*w*/) { return (double)v; }
+  // two neighbouring values (8-byte aligned pair)
+  __device__ __forceinline__ static float2 load2(const T *p, float /*w*/) {
+    return __ldg(reinterpret_cast<const float2 *>(p));
+  }
+  __device__ __forceinline__ static void store2(T *p, float2 g, float /*invw*/) {
+    *reinterpret_cast<float2 *>(p) = g;
+  }
 };
 
 template <>
@@ -73,6 +80,14 @@ struct Store<STORE_F16> {
   __device__ __forceinline__ static T encode(double g, double w) { return __double2half(g / w); }
   __device__ __forceinline__ static double decode(T v, double w) {
     return w * (double)__half2float(v);
+  }
+  __device__ __forceinline__ static float2 load2(const T *p, float w) {
+    const float2 h = __half22float2(__ldg(reinterpret_cast<const __half2 *>(p)));
+    return __fmul2_rn(h, make_float2(w, w));
+  }
+
+  __device__ __forceinline__ static void store2(T *p, float2 g, float invw) {
+    *reinterpret_cast<__half2 *>(p) = __float22half2_rn(__fmul2_rn(g, make_float2(invw, invw)));
   }
 };
 
@@ -94,6 +109,15 @@ struct Store<STORE_BF16> {
   }
   __device__ __forceinline__ static double decode(T v, double w) {
     return w * (double)__bfloat162float(v);
+  }
+  __device__ __forceinline__ static float2 load2(const T *p, float w) {
+    const float2 h = __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162 *>(p)));
+    return __fmul2_rn(h, make_float2(w, w));
+  }
+
+  __device__ __forceinline__ static void store2(T *p, float2 g, float invw) {
+    *reinterpret_cast<__nv_bfloat162 *>(p) =
+        __float22bfloat162_rn(__fmul2_rn(g, make_float2(invw, invw)));
   }
 };
 
@@ -136,6 +160,18 @@ struct Store<STORE_F16N> {
   }
   __device__ __forceinline__ static double decode(T v, double w) {
     return w * 0x1p120 * (double)bits_to_scaled(v);
+  }
+  __device__ __forceinline__ static float2 load2(const T *p, float w) {
+    const uint32_t c = __ldg(reinterpret_cast<const unsigned int *>(p));
+    const float2 x = make_float2(bits_to_scaled(c & 0xFFFFu), bits_to_scaled(c >> 16));
+    const float s = w * 0x1p120f;
+    return __fmul2_rn(x, make_float2(s, s));
+  }
+  __device__ __forceinline__ static void store2(T *p, float2 g, float invw) {
+    const float s = invw * 0x1p-120f;
+    const float2 x = __fmul2_rn(g, make_float2(s, s));
+    *reinterpret_cast<unsigned int *>(p) =
+        (uint32_t)scaled_to_bits(x.x) | ((uint32_t)scaled_to_bits(x.y) << 16);
   }
 };
 

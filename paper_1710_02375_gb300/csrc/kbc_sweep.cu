@@ -98,6 +98,121 @@ __global__ void __launch_bounds__(128, SweepOcc<Q, S>::ctas)
 }
 
 
+// ---------------------------------------------------------------- two-node sweep
+// Each thread takes the stored columns (X, X + 1), X even, of one row: the
+// c_x = 0 sources of both nodes are one aligned two-element load, the c_x =
+// +-1 sources two single loads, and the collision of both nodes runs on the
+// paired FP32 instructions (collide_v with V = f2).  Nodes of the pair that
+// are ghosts, solid or in the row padding are computed on whatever their
+// slots hold and never stored (their loads stay inside the row: x sources
+// wrap with nbr), so the written populations are those of the one-node
+// sweep.  Pairs of a row: X = 0, 2, .. covering the interior columns
+// [px, px + nx).
+template <int Q, int S, typename IX>
+__device__ __forceinline__ void sweep_pair_gather(const Grid &g,
+                                                  const typename Store<S>::T *__restrict__ fin,
+                                                  int X, int Y, int Z, f2 (&v)[Q]) {
+  using L = Lat<Q>;
+  using St = Store<S>;
+  // source x of the first / second node for cx = -1, 0, +1
+  const int xa[3] = {nbr(X, 1, g.NX), X, nbr(X, -1, g.NX)};
+  const int xb[3] = {nbr(X + 1, 1, g.NX), X + 1, X};
+  const int ys[3] = {nbr(Y, 1, g.NY), Y, nbr(Y, -1, g.NY)};
+  int zs[3] = {Z, Z, Z};
+  if (L::D == 3) {
+    zs[0] = nbr(Z, 1, g.NZ);
+    zs[2] = nbr(Z, -1, g.NZ);
+  }
+  const IX N = (IX)g.N;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int cx = L::cx(i);
+    const IX row = ((IX)zs[L::cz(i) + 1] * (IX)g.NY + (IX)ys[L::cy(i) + 1]) * (IX)g.pitch + (IX)i * N;
+    const float w = (float)weight<L>(i);
+    if (cx == 0) {
+      v[i] = f2{St::load2(fin + (row + (IX)X), w)};
+    } else {
+      v[i] = mk2(St::load(fin + (row + (IX)xa[cx + 1]), w), St::load(fin + (row + (IX)xb[cx + 1]), w));
+    }
+  }
+}
+
+// Resident 128-thread CTAs per SM the two-node D3Q27 kernel's registers are
+// sized for.
+#ifndef KBC_PAIR_CTAS27
+#define KBC_PAIR_CTAS27 3
+#endif
+template <int Q, int S>
+struct Sweep2Occ {
+  static constexpr int ctas = Q == 27 ? KBC_PAIR_CTAS27 : 5;
+};
+
+template <int Q, int S, bool FLAGS, typename IX>
+__global__ void __launch_bounds__(128, Sweep2Occ<Q, S>::ctas)
+    k_sweep2(Grid g, const typename Store<S>::T *__restrict__ fin,
+             typename Store<S>::T *__restrict__ fout, const uint8_t *__restrict__ flags, float beta,
+             int bgk, int *__restrict__ err) {
+  using L = Lat<Q>;
+  using St = Store<S>;
+  const int X = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (X >= g.px + g.nx || y >= g.ny) return;
+  const int Y = y + g.py, Z = z + g.pz;
+  const IX k = (IX)sidx(g, X, Y, Z);
+  bool ia = X >= g.px, ib = X + 1 < g.px + g.nx;
+  if (FLAGS) {
+    const uint16_t fl = *reinterpret_cast<const uint16_t *>(flags + k);
+    ia = ia && (fl & 0xFFu) == NODE_FLUID;
+    ib = ib && (fl >> 8) == NODE_FLUID;
+    if (!ia && !ib) return;
+  }
+  f2 v[Q];
+  sweep_pair_gather<Q, S, IX>(g, fin, X, Y, Z, v);
+  const f2 rho = collide_v<L, S == STORE_F32, f2>(v, beta, bgk != 0);
+  if ((ia && !(rho.v.x > 0.f && rho.v.x < 1e30f)) || (ib && !(rho.v.y > 0.f && rho.v.y < 1e30f)))
+    atomicOr(err, 1);
+  const IX N = (IX)g.N;
+  if (ia && ib) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) St::store2(fout + ((IX)i * N + k), v[i].v, (float)(1.0 / weight<L>(i)));
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const float iw = (float)(1.0 / weight<L>(i));
+      if (ia) St::store(fout + ((IX)i * N + k), v[i].v.x, iw);
+      if (ib) St::store(fout + ((IX)i * N + k + 1), v[i].v.y, iw);
+    }
+  }
+}
+
+static dim3 sweep2_block(int npairs) {
+  if (npairs >= 128) return dim3(128, 1, 1);
+  if (npairs >= 64) return dim3(64, 2, 1);
+  return dim3(32, 4, 1);
+}
+
+template <int Q, int S>
+static cudaError_t sweep2_t(const Grid &g, const void *fin, void *fout, const uint8_t *flags,
+                            float beta, int bgk, int *err, cudaStream_t s) {
+  using T = typename Store<S>::T;
+  const int npairs = (g.px + g.nx + 1) / 2;
+  const dim3 b = sweep2_block(npairs);
+  const dim3 grid((npairs + b.x - 1) / b.x, (g.ny + b.y - 1) / b.y, g.nz);
+  const bool narrow = (long long)Q * g.N < (1LL << 31);
+  if (flags && narrow)
+    k_sweep2<Q, S, true, int><<<grid, b, 0, s>>>(g, (const T *)fin, (T *)fout, flags, beta, bgk, err);
+  else if (flags)
+    k_sweep2<Q, S, true, long long><<<grid, b, 0, s>>>(g, (const T *)fin, (T *)fout, flags, beta, bgk,
+                                                       err);
+  else if (narrow)
+    k_sweep2<Q, S, false, int><<<grid, b, 0, s>>>(g, (const T *)fin, (T *)fout, flags, beta, bgk, err);
+  else
+    k_sweep2<Q, S, false, long long><<<grid, b, 0, s>>>(g, (const T *)fin, (T *)fout, flags, beta,
+                                                        bgk, err);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- row-staged sweep
 // Persistent form of the same sweep.  A CTA walks output rows (y, z) of the
 // interior; for each it fetches, with the bulk-copy engine, the Q source rows
@@ -452,6 +567,8 @@ static cudaError_t sweep_t(const Grid &g, const void *fin, void *fout, const uin
     cudaError_t e = sweep_rows_t<Q, S>(g, fin, fout, flags, beta, bgk, err, s, &used);
     if (e != cudaSuccess || used) return e;
   }
+  if (variant == SWEEP_AUTO || variant == SWEEP_PAIR)
+    return sweep2_t<Q, S>(g, fin, fout, flags, beta, bgk, err, s);
   dim3 b = sweep_block(g);
   dim3 grid((g.nx + b.x - 1) / b.x, (g.ny + b.y - 1) / b.y, g.nz);
   const bool narrow = (long long)Q * g.N < (1LL << 31);  // every offset fits an int

@@ -823,7 +823,7 @@ lbm_status lbm_step_graph(lbm_ctx *ctx, int n, int repeats) {
 
 lbm_status lbm_set_sweep_variant(lbm_ctx *ctx, int variant) {
   GUARD();
-  if (variant < LBM_SWEEP_AUTO || variant > LBM_SWEEP_ASYNC)
+  if (variant < LBM_SWEEP_AUTO || variant > LBM_SWEEP_PAIR)
     return fail(ctx, LBM_EINVAL, "lbm_set_sweep_variant: unknown variant %d", variant);
   ctx->sweep_variant = variant;
   ctx->graph_dirty = true;

