@@ -6,12 +6,17 @@ the 129 MB L2, so no L2 flush is needed between steps).  A step is one pass of
 the hot path over the whole lattice: pull-stream + KBC collision, one kernel.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload tgv128|c4|c4-coupled|c1-fsi|c3-fsi]
+                  [--workload tgv128|c4|c4-coupled|c1-fsi|c3-fsi] [--quick]
 
-The default line also carries "patterns": the same workload with FP16 and
-BF16 storage, as speedups over FP32.  --workload c4 / c4-coupled time the
-batched ensemble and --workload c1-fsi the coupled C1 flag (one extra JSON
-line per call, not the headline).
+The default line also carries "patterns": the same workload with IEEE half,
+bfloat16 and the narrow-range 16-bit float F16N storage, as speedups over
+FP32; and "forms": the batched 64-member D2Q9 ensemble (rigid and elastic
+flags; FP32, F16N and half storage) against stepping each member on its own,
+the coupled C1 flag and the coupled 3-D plate (FP32, F16N, half), each with
+its time per step (not the headline; --quick leaves them out).  The error of
+each form against the FP64 oracle is the parity tests' measurement, stated
+in "stated_error_vs_oracle".  --workload c4 / c4-coupled / c1-fsi / c3-fsi
+print one extra JSON line for that form alone.
 
 Prints one JSON line.  With N > 1 (torchrun) every rank advances its own
 independent replica of the workload ("replicas only": the path has no
@@ -152,19 +157,51 @@ def tgv_problem(n=N_LATTICE):
     return beta, rho, u
 
 
+def _oracle_slab_worker(args):
+    """One host core: `steps` oracle steps of a periodic 128 x R x Z slab of the
+    128^3 fields (spawned process; returns node updates and seconds)."""
+    R, Z, steps = args
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    from oracle import oracle as orc
+    beta, rho, u = tgv_problem()
+    f = orc.init_equilibrium(Q, np.ascontiguousarray(rho[:Z, :R, :]),
+                             np.ascontiguousarray(u[:, :Z, :R, :]))
+    t0 = time.perf_counter()
+    orc.run_periodic(Q, beta, f, steps)
+    return N_LATTICE * R * Z * steps, time.perf_counter() - t0
+
+
 def cpu_baseline_oracle(steps=2):
     """The FP64 oracle, as it stands, on the host cores: `steps` time steps of the
-    full 128^3 workload (single-threaded plain C)."""
+    full 128^3 workload single-threaded, and one process per host core each
+    stepping its own 128 x 32 x 32 slab of the same fields (the oracle is plain
+    single-threaded C; the cores are used by independent processes)."""
+    import multiprocessing as mp
     from oracle import oracle as orc
+    orc.build()
     beta, rho, u = tgv_problem()
     f = orc.init_equilibrium(Q, rho, u)
     t0 = time.perf_counter()
     orc.run_periodic(Q, beta, f, steps)
     dt = time.perf_counter() - t0
     nodes = N_LATTICE ** 3
-    return {"value": nodes * steps / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} steps of the 128^3 D3Q27 TGV workload ({nodes} nodes), FP64, "
-                      f"single-threaded, {dt:.1f} s"}
+    single = nodes * steps / dt / 1e6
+    cores = os.cpu_count() or 1
+    slab_steps = 16
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_slab_worker, [(32, 32, slab_steps)] * cores)
+    # the processes step side by side; the slowest one's stepping time (its
+    # start-up and imports excluded) bounds the aggregate
+    wall = max(r[1] for r in res)
+    all_cores = sum(r[0] for r in res) / wall / 1e6
+    return {"value": all_cores, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} processes (nproc), each {slab_steps} oracle steps of a periodic "
+                      f"128x32x32 slab of the 128^3 D3Q27 TGV fields, FP64 plain C, slowest process "
+                      f"{wall:.1f} s",
+            "single_core": {"value": single, "cores": 1,
+                            "sample": f"{steps} steps of the full 128^3 workload ({nodes} nodes), "
+                                      f"single-threaded, {dt:.1f} s"}}
 
 
 def run_reference(args):
@@ -301,6 +338,18 @@ def run_ours(args):
                           "speedup_vs_f32": v / value,
                           "achieved_gbs": 2 * Q * 2 * nodes / (ms_p * 1e-3) / 1e9}
 
+    # ---- the batched and coupled forms of the same hot path (not the headline)
+    forms = {}
+    if not args.quick and rank == 0:
+        forms["batched_c4_rigid"] = c4_leg(args, coupled=False)
+        forms["batched_c4_coupled"] = c4_leg(args, coupled=True)
+        forms["coupled_c1"] = c1_leg(args)
+        forms["coupled_c3"] = c3_leg(args)
+        forms["surrogate"] = {
+            "measured_in": "tests/test_gpu_surrogate.py, tests/test_gpu_plate_surrogate.py",
+            "why_not_here": "its training pairs come from coupled FP64 oracle runs, which this "
+                            "script runs only in its CPU-baseline leg"}
+
     if rank != 0:
         return
     cpu = None if args.no_cpu_baseline else cpu_baseline_oracle()
@@ -321,8 +370,133 @@ def run_ours(args):
         "gpu_launches": args.steps,
         "clocks": clocks,
         "patterns": patterns,
+        "stated_error_vs_oracle": STATED_ERRORS,
+        "forms": forms,
     }
     print(json.dumps(line), flush=True)
+
+
+# Error of each form against the FP64 oracle, as the parity tests measure it
+# (relative velocity max |u - u_oracle| / max |u_oracle|; force per body).
+STATED_ERRORS = {
+    "f32": "laminar TGV 1000 steps 2.3e-6 (D3Q27), 8e-7 (D2Q9); C1 1000 steps <= 1e-5, forces <= 1e-4 "
+           "(tests/test_gpu_periodic.py, tests/test_gpu_boundary.py)",
+    "f16": "laminar TGV 1000 steps 2.5e-3 (D3Q27), 1.3e-3 (D2Q9) (tests/test_gpu_precision.py)",
+    "bf16": "laminar TGV 1000 steps 1.7e-2 (D3Q27), 1.0e-2 (D2Q9) (tests/test_gpu_precision.py)",
+    "f16n": "laminar TGV 1000 steps 5.8e-4 (D3Q27), 3.0e-4 (D2Q9) (tests/test_gpu_precision.py)",
+    "batched_c4": "members vs oracle after 400 steps: FP32 velocity <= 1.8e-6, force <= 1.1e-5; "
+                  "F16N 2.5e-4 / 8.5e-3 (tests/test_gpu_batch.py); batch vs member-by-member "
+                  "bitwise equal (rigid), 1e-9 (coupled)",
+    "coupled_c1": "600 coupled steps: velocity <= 1e-5, tip <= 1e-4, body forces <= 1e-4 "
+                  "(tests/test_gpu_fem.py)",
+    "coupled_c3": "small plate (48x24x24, 8x4 shell) 40 coupled steps: velocity 4.4e-7, shell 1.1e-7; "
+                  "full size 2 steps sampled 2.6e-7 (tests/test_gpu_shell.py)",
+}
+
+
+def _timed(stream, fn, steps):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def c4_leg(args, coupled, n=64):
+    """The 64-member flag ensemble (D2Q9, 200x40 .. 800x160, 3.78M nodes)
+    stepped member by member (the plain FP32 form) and as one batch under
+    CUDA-graph replay with FP32, F16N and FP16 storage."""
+    import torch
+    from paper_1710_02375_gb300 import synth
+    from paper_1710_02375_gb300.cases import c4_lattice
+    from paper_1710_02375_gb300.lbm import Batch
+    insts = synth.c4_instances(n=n, seed=0)
+    nodes = sum(i["nx"] * i["ny"] for i in insts)
+    stream = torch.cuda.Stream()
+    solo = [c4_lattice(i, coupled, stream) for i in insts]
+    for L, _ in solo:
+        L.step(3)
+    k_solo = 20
+    ms_solo = _timed(stream, lambda k: [L.step(k) for L, _ in solo], k_solo)
+    for L, b in solo:
+        L.check()
+        L.close()
+        if b:
+            b.close()
+    out = {"nodes": nodes, "members": n, "member_by_member_f32": {"ms_per_step": ms_solo,
+                                                                  "steps": k_solo}}
+    for name, storage in (("f32", 0), ("f16n", 4), ("f16", 1)):
+        group = [c4_lattice(i, coupled, stream, storage) for i in insts]
+        B = Batch([L for L, _ in group])
+        B.step(3)
+        rows, ctas, _ = B.autotune(steps=4)
+        chunk, reps = 10, 20
+        B.step_graph(chunk, 1)
+        ms = _timed(stream, lambda k: B.step_graph(chunk, k), reps) / chunk
+        for L, b in group:
+            L.check()
+        B.close()
+        for L, b in group:
+            L.close()
+            if b:
+                b.close()
+        out[name] = {"ms_per_step": ms, "mlups": nodes / (ms * 1e-3) / 1e6, "steps": chunk * reps,
+                     "speedup_vs_member_by_member_f32": ms_solo / ms,
+                     "tuning": {"rows_per_tile": rows, "ctas_per_sm": ctas}}
+    return out
+
+
+def c1_leg(args):
+    """The coupled C1 flag (fluid, Grad boundaries, forces, beam Newton step,
+    surface transfer, geometry), Re = 100, CUDA-graph replay of 10-step
+    graphs and direct launches, after 100 start-up steps."""
+    import torch
+    from paper_1710_02375_gb300 import lbm as abi
+    from paper_1710_02375_gb300.cases import c1_coupled
+    stream = torch.cuda.Stream()
+    L, beam, _ = c1_coupled(100.0, stream=stream)
+    L.step(100)
+    chunk, reps = 10, 30
+    L.step_graph(chunk, 1)
+    abi.fsi_get_structure_stats(L.ctx, reset=True)
+    ms = _timed(stream, lambda k: L.step_graph(chunk, k), reps) / chunk
+    _, _, solves, steps = abi.fsi_get_structure_stats(L.ctx)
+    ms_direct = _timed(stream, L.step, chunk * reps)
+    L.check()
+    L.close()
+    beam.close()
+    return {"ms_per_step": ms, "steps_per_s": 1e3 / ms, "direct_launch_ms_per_step": ms_direct,
+            "newton_solves_per_step": solves / max(1, steps), "steps": chunk * reps,
+            "config": "D2Q9 220x41, Re=100, 21-node beam, steps 110-410 of the inflow ramp"}
+
+
+def c3_leg(args):
+    """The 3-D plate (D3Q27 256x128x128, 16x8 shell, Re = 400) CSS-coupled,
+    CUDA-graph replay, with FP32, F16N and FP16 population storage."""
+    import torch
+    from paper_1710_02375_gb300 import synth
+    from paper_1710_02375_gb300.cases import plate_coupled
+    c = synth.plate_case()
+    nodes = c["nx"] * c["ny"] * c["nz"]
+    out = {"nodes": nodes}
+    for name, storage in (("f32", 0), ("f16n", 4), ("f16", 1)):
+        stream = torch.cuda.Stream()
+        L, S = plate_coupled(c, storage=storage, stream=stream)
+        L.step(5)
+        chunk, reps = 10, 10
+        L.step_graph(chunk, 1)
+        ms = _timed(stream, lambda k: L.step_graph(chunk, k), reps) / chunk
+        L.check()
+        out[name] = {"ms_per_step": ms, "steps_per_s": 1e3 / ms, "mlups": nodes / (ms * 1e-3) / 1e6,
+                     "steps": chunk * reps}
+        L.close()
+        S.close()
+    for name in ("f16n", "f16"):
+        out[name]["speedup_vs_f32"] = out["f32"]["ms_per_step"] / out[name]["ms_per_step"]
+    return out
 
 
 def run_c4(args):
@@ -508,6 +682,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=500)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true",
+                    help="only the headline workload and its storage patterns")
     ap.add_argument("--workload", choices=["tgv128", "c4", "c4-coupled", "c1-fsi", "c3-fsi"],
                     default="tgv128")
     args = ap.parse_args()
