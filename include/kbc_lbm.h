@@ -59,7 +59,7 @@ typedef enum {
 
 enum { LBM_D2Q9 = 9, LBM_D3Q27 = 27 };
 
-/* Storage of populations in device memory (computation is always FP32):
+/* Storage of populations in device memory (computation in FP32 except F64):
  *   F32  stores f_i - W_i        (deviation from the lattice weight)
  *   F16  stores f_i / W_i - 1    (scaled deviation, IEEE half, round to nearest even)
  *   BF16 stores f_i / W_i - 1    (scaled deviation, bfloat16, round to nearest even)
@@ -68,8 +68,13 @@ enum { LBM_D2Q9 = 9, LBM_D3Q27 = 27 };
  *        stored significand bits, evenly spaced steps of 2^-18 below 2^-6;
  *        round to nearest, ties away from zero; |f_i/W_i - 1| >= 2 saturates).
  *        The same bytes as F16 with a step four times finer for the O(u)
- *        deviations.  (Code 3 is not used.) */
-enum { LBM_STORE_F32 = 0, LBM_STORE_F16 = 1, LBM_STORE_BF16 = 2, LBM_STORE_F16N = 4 };
+ *        deviations.
+ *   F64  stores f_i - W_i in double precision and computes the sweep and
+ *        the boundary fill in FP64 (D2Q9 only; the test storage).  Inputs
+ *        kept in FP32 by the boundary data (link fractions, wall and face
+ *        velocities, inlet profiles) stay FP32. */
+enum { LBM_STORE_F32 = 0, LBM_STORE_F16 = 1, LBM_STORE_BF16 = 2, LBM_STORE_F64 = 3,
+       LBM_STORE_F16N = 4 };
 
 /* Collision: KBC (entropic multi-relaxation time, gamma from
  * Eq. gamma_min_approx) or BGK (gamma fixed to 2, i.e. LBGK with omega = 2 beta). */

@@ -72,14 +72,17 @@ struct PopSum {
 template <>
 struct PopSum<double> {
   float hi = 0.f, lo = 0.f;
+  double d = 0.0;  // FP64 stored values (F64 storage) are summed in FP64
   __device__ __forceinline__ void add(float x) {
     float t, e;
     two_sum(hi, x, t, e);
     hi = t;
     lo += e;
   }
+  __device__ __forceinline__ void add(double x) { d += x; }
   __device__ __forceinline__ void sub(float x) { add(-x); }
-  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+  __device__ __forceinline__ void sub(double x) { d -= x; }
+  __device__ __forceinline__ double value() const { return ((double)hi + (double)lo) + d; }
 };
 
 // (nh + nl) / (dh + dl) for unevaluated FP32 pairs, as a double: the FP32
@@ -129,7 +132,7 @@ __device__ void dev_moments(const Grid &g, const typename Store<S>::T *f, long l
   PopSum<A> dr, jx, jy, jz;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const float v = Store<S>::load(f + (long long)i * g.N + k, (float)weight<L>(i));
+    const auto v = Store<S>::load(f + (long long)i * g.N + k, (typename Store<S>::C)weight<L>(i));
     dr.add(v);
     if (L::cx(i) > 0) jx.add(v);
     if (L::cx(i) < 0) jx.sub(v);
@@ -149,7 +152,23 @@ __device__ void dev_moments(const Grid &g, const typename Store<S>::T *f, long l
 template <int Q, int S, typename R = float>
 __device__ void dev_velocity(const Grid &g, const typename Store<S>::T *f, long long k, R (&u)[3],
                              R *rho = nullptr) {
-  if constexpr (Q == 9 && std::is_same<R, double>::value) {
+  if constexpr (std::is_same<typename Store<S>::C, double>::value) {
+    // FP64 storage: FP64 sums and one FP64 reciprocal of rho
+    using L = Lat<Q>;
+    double dr = 0, j[3] = {0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const double v = Store<S>::load(f + (long long)i * g.N + k, weight<L>(i));
+      dr += v;
+      if (L::cx(i)) j[0] += L::cx(i) * v;
+      if (L::cy(i)) j[1] += L::cy(i) * v;
+      if (L::cz(i)) j[2] += L::cz(i) * v;
+    }
+    const double r = 1.0 + dr, ir = 1.0 / r;
+    for (int a = 0; a < 3; ++a) u[a] = (R)(j[a] * ir);
+    if (rho) *rho = (R)r;
+    return;
+  } else if constexpr (Q == 9 && std::is_same<R, double>::value) {
     // D2Q9 in FP64: the moments stay unevaluated FP32 pairs (hi + lo) and
     // rho = 1 + drho and u = j / rho are formed in double-float arithmetic
     // on the FP32 pipes (about 44 bits), with one conversion pair per
@@ -1115,7 +1134,7 @@ __device__ __forceinline__ void grad_body(int tb, const Grid &g, typename Store<
     long long src[Q];
     int face_of[Q];
     uint32_t miss = 0, solid_miss = 0;
-    float gk[Q];
+    typename St::C gk[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const int Xs = nbr(X, -L::cx(i), g.NX), Ys = nbr(Y, -L::cy(i), g.NY),
@@ -1125,7 +1144,7 @@ __device__ __forceinline__ void grad_body(int tb, const Grid &g, typename Store<
       face_of[i] = -1;
       gk[i] = 0;
       if (fl == NODE_FLUID) {
-        gk[i] = St::load(f + (long long)i * g.N + src[i], (float)weight<L>(i));
+        gk[i] = St::load(f + (long long)i * g.N + src[i], (typename St::C)weight<L>(i));
       } else {
         miss |= 1u << i;
         if (fl == NODE_SOLID) solid_miss |= 1u << i;
@@ -1217,7 +1236,8 @@ __device__ __forceinline__ void grad_body(int tb, const Grid &g, typename Store<
           const double wi = dir_tab<Q>().w[i];
           R cuw = L::cx(i) * uw[0] + L::cy(i) * uw[1];
           if (D == 3) cuw += L::cz(i) * uw[2];
-          pops.add(St::load(f + (long long)(Q - 1 - i) * g.N + k, dir_tab<Q>().wf[i]));
+          pops.add(St::load(f + (long long)(Q - 1 - i) * g.N + k,
+                            (typename St::C)dir_tab<Q>().w[i]));
           wterm += (R)(6.0 * wi) * cuw;
           const int Xn = step_axis(X, L::cx(i), g.NX, g.px), Yn = step_axis(Y, L::cy(i), g.NY, g.py);
           const int Zn = (L::D == 3) ? step_axis(Z, L::cz(i), g.NZ, g.pz) : Z;
@@ -1315,18 +1335,19 @@ __device__ __forceinline__ void grad_body(int tb, const Grid &g, typename Store<
           if (c[1] * c[2] < 0) cAc -= A12;
         }
         const DirTab<Q> &dt = dir_tab<Q>();
-        const float W = dt.wf[i];
         const R gstar = (R)dt.w[i] * (rm1 + r3 * cu + (R)4.5 * (cAc - tr3));
-        St::store(f + (long long)i * g.N + src[i], (float)gstar, dt.iwf[i]);
+        using C = typename St::C;
+        St::store(f + (long long)i * g.N + src[i], (C)gstar, (C)dt.iwf[i]);
         if (face_of[i] < 0) {
           // momentum exchange on the immersed surface, FP64 accumulation
           while (l < bn.nlink && links[bn.link0 + l].i != i) ++l;
           if (l < bn.nlink) {
             const Link &lk = links[bn.link0 + l];
             if (lk.body >= 0) {
-              const double gop = (double)St::load(f + (long long)(Q - 1 - i) * g.N + k, W);
+              const double gop =
+                  (double)St::load(f + (long long)(Q - 1 - i) * g.N + k, (C)dt.w[i]);
               // gauge form: the rest state f = W (ambient pressure) is taken out
-              const double fsum = gop + (double)(float)gstar;
+              const double fsum = gop + (double)(C)gstar;
               for (int a = 0; a < D; ++a) {
                 if (c[a] == 0) continue;
                 const double Fa = c[a] > 0 ? -fsum : fsum;
@@ -1368,11 +1389,11 @@ __global__ void __launch_bounds__(128)
 // lanes), and lane i forms, stores and gathers the force of its missing
 // direction.  Every value written equals grad_body's; only the order of the
 // FP64 force atomics differs.
-template <int Q>
+template <int Q, typename C>
 struct GradWarpSh {
   double vel[Q + 6][3];  // [i < Q]: node x_b + c_i; [Q + 2b (+1)]: x_b + 2 e_b (- 2 e_b)
   double rho[Q];
-  float gk[Q], gop[Q];   // known populations; f_opp(i)(x_b) of missing i
+  C gk[Q], gop[Q];       // known populations; f_opp(i)(x_b) of missing i
   float q[Q], uw[Q][3];  // link fraction and wall velocity of missing i
   double ut[3], Ad[3], A01, A02, A12, tr3, r3, rm1;
 };
@@ -1388,7 +1409,8 @@ __device__ __forceinline__ void grad_warp_node(int t, const Grid &g, typename St
                                                const BNode *__restrict__ bnodes, int nfixed,
                                                const Link *__restrict__ links,
                                                const BoundaryParams &bp, double *vforce,
-                                               double *bforce, GradWarpSh<Q> &W, int lane,
+                                               double *bforce,
+                                               GradWarpSh<Q, typename Store<S>::C> &W, int lane,
                                                int &my_body, double (&Fd)[3]) {
   using L = Lat<Q>;
   using St = Store<S>;
@@ -1412,7 +1434,7 @@ __device__ __forceinline__ void grad_warp_node(int t, const Grid &g, typename St
     src = sidx(g, Xs, Ys, Zs);
     fl = flags[src];
     if (fl == NODE_FLUID) {
-      W.gk[i] = St::load(f + (long long)i * g.N + src, dir_tab<Q>().wf[i]);
+      W.gk[i] = St::load(f + (long long)i * g.N + src, (typename St::C)dir_tab<Q>().w[i]);
     } else if (fl == NODE_GHOST) {
       if (g.px && (Xs == 0 || Xs == g.NX - 1)) face = Xs == 0 ? 0 : 1;
       else if (g.py && (Ys == 0 || Ys == g.NY - 1)) face = Ys == 0 ? 2 : 3;
@@ -1510,7 +1532,7 @@ __device__ __forceinline__ void grad_warp_node(int t, const Grid &g, typename St
     }
     W.q[i] = q;
     for (int a = 0; a < 3; ++a) W.uw[i][a] = uw[a];
-    W.gop[i] = St::load(f + (long long)(Q - 1 - i) * g.N + k, dir_tab<Q>().wf[i]);
+    W.gop[i] = St::load(f + (long long)(Q - 1 - i) * g.N + k, (typename St::C)dir_tab<Q>().w[i]);
   }
   __syncwarp();
   // ---- targets and stress on lane 0 (grad_body's arithmetic)
@@ -1631,14 +1653,15 @@ __device__ __forceinline__ void grad_warp_node(int t, const Grid &g, typename St
     }
     const DirTab<Q> &dt = dir_tab<Q>();
     const R gstar = (R)dt.w[i] * (W.rm1 + W.r3 * cu + (R)4.5 * (cAc - W.tr3));
-    St::store(f + (long long)i * g.N + src, (float)gstar, dt.iwf[i]);
+    using C = typename St::C;
+    St::store(f + (long long)i * g.N + src, (C)gstar, (C)dt.iwf[i]);
     if (face < 0) {
       int l = 0;
       while (l < bn.nlink && links[bn.link0 + l].i != i) ++l;
       if (l < bn.nlink) {
         const Link &lk = links[bn.link0 + l];
         if (lk.body >= 0) {
-          const double fsum = (double)W.gop[i] + (double)(float)gstar;
+          const double fsum = (double)W.gop[i] + (double)(C)gstar;
           for (int a = 0; a < D; ++a) {
             if (c[a] == 0) continue;
             const double Fa = c[a] > 0 ? -fsum : fsum;
@@ -1667,7 +1690,7 @@ __device__ __forceinline__ void grad_warp_range(const Grid &g, typename Store<S>
                                                 int first, int last, const Link *__restrict__ links,
                                                 const BoundaryParams &bp, double *vforce,
                                                 double *bforce, int nbodies, int w0, int nw) {
-  __shared__ GradWarpSh<Q> sh[4];
+  __shared__ GradWarpSh<Q, typename Store<S>::C> sh[4];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   int dyn = nbn ? *nbn : 0;
   if (dyn > cap - nfixed) dyn = cap - nfixed;

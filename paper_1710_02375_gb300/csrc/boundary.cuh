@@ -45,7 +45,7 @@ struct BoundaryParams {
   int bc[6];
   float face_u[6][3];
   const float *inlet[6];  // per face [3][face nodes] prescribed velocity or nullptr
-  float beta;
+  double beta;
   int ramp_steps;         // inlet velocity ramp (1 - cos(pi t / T)) / 2, 0 = none
   const int *step;        // device step counter (ramp clock)
 };
@@ -56,7 +56,7 @@ struct InstDesc {
   void *f[2];             // population buffers; step parity p reads f[(cur0 + p) & 1]
   int cur0;
   uint8_t *flags;
-  float beta;
+  double beta;
   int bgk;
   int *err;
   int narrow;             // Q N < 2^31: 32-bit population offsets in the sweep

@@ -31,12 +31,25 @@ struct f2 {
   float2 v;
 };
 __device__ __forceinline__ f2 mk2(float a, float b) { return f2{make_float2(a, b)}; }
+// scalar type of a value type (parameters such as beta)
 template <class V>
-__device__ __forceinline__ V vc(float a);
+struct ScalarOf {
+  using type = float;
+};
 template <>
-__device__ __forceinline__ float vc<float>(float a) { return a; }
+struct ScalarOf<double> {
+  using type = double;
+};
+// a constant in the value type (constants are written in double and rounded
+// once to FP32 for the FP32 forms)
+template <class V>
+__device__ __forceinline__ V vc(double a);
 template <>
-__device__ __forceinline__ f2 vc<f2>(float a) { return mk2(a, a); }
+__device__ __forceinline__ float vc<float>(double a) { return (float)a; }
+template <>
+__device__ __forceinline__ f2 vc<f2>(double a) { return mk2((float)a, (float)a); }
+template <>
+__device__ __forceinline__ double vc<double>(double a) { return a; }
 
 // The float forms are the IEEE operations of the paired ones (no contraction
 // of a product into a following sum), so one-node and two-node sweeps agree
@@ -52,6 +65,13 @@ __device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b)
 __device__ __forceinline__ f2 vmul(f2 a, f2 b) { return f2{__fmul2_rn(a.v, b.v)}; }
 __device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ f2 vfma(f2 a, f2 b, f2 c) { return f2{__ffma2_rn(a.v, b.v, c.v)}; }
+// FP64 forms (the F64 test storage)
+__device__ __forceinline__ double vadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double vsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double vmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double vfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ double vrsqrt(double a) { return 1.0 / sqrt(a); }
+__device__ __forceinline__ double vdivf(double a, double b) { return a / b; }
 __device__ __forceinline__ float vrsqrt(float a) { return rsqrtf(a); }
 __device__ __forceinline__ f2 vrsqrt(f2 a) { return mk2(rsqrtf(a.v.x), rsqrtf(a.v.y)); }
 __device__ __forceinline__ float vdivf(float a, float b) { return __fdividef(a, b); }
@@ -104,6 +124,14 @@ __device__ __forceinline__ float kbc_gamma(float sh, float hh, float ib, bool bg
 __device__ __forceinline__ float vgamma(float sh, float hh, float ib, bool bgk) {
   return kbc_gamma(sh, hh, ib, bgk);
 }
+__device__ __forceinline__ double vgamma(double sh, double hh, double ib, bool bgk) {
+  double gamma = 2.0;
+  if (!bgk && hh > 1e-30) {
+    gamma = ib - (2.0 - ib) * (sh / hh);
+    gamma = fmin(fmax(gamma, 0.0), 2.0 * ib);
+  }
+  return gamma;
+}
 __device__ __forceinline__ f2 vgamma(f2 sh, f2 hh, float ib, bool bgk) {
   return mk2(kbc_gamma(sh.v.x, hh.v.x, ib, bgk), kbc_gamma(sh.v.y, hh.v.y, ib, bgk));
 }
@@ -120,10 +148,11 @@ __device__ __forceinline__ f2 vgamma(f2 sh, f2 hh, float ib, bool bgk) {
 // non-equilibrium part (used with FP32 storage, where it would otherwise be
 // the dominant error; with 16-bit storage the storage rounding dominates).
 template <class L, bool CONSERVE, class V>
-__device__ __forceinline__ V collide_v(V (&g)[L::Q], float beta, bool bgk) {
+__device__ __forceinline__ V collide_v(V (&g)[L::Q], typename ScalarOf<V>::type beta, bool bgk) {
+  using SC = typename ScalarOf<V>::type;
   constexpr int Q = L::Q;
   constexpr int NR = Q / 3;  // rows of three x-neighbours (cy, cz)
-  const V zero = vc<V>(0.f);
+  const V zero = vc<V>(0.0);
   // ---- moments of the deviations (Eq. conservationLaws and second moments)
   V rs[NR], rd[NR], rm[NR];  // per row: g+ + g-, g+ - g-, g- + g0 + g+
 #pragma unroll
@@ -167,7 +196,7 @@ __device__ __forceinline__ V collide_v(V (&g)[L::Q], float beta, bool bgk) {
   // ---- shear part of f - feq from the deviatoric non-equilibrium stress
   // dPi_aa = P_aa - (drho + 2 rho d_a)/3, dPi_ab = P_ab - rho u_a u_b
   const V rho2 = vmul(vc<V>(2.f), rho);
-  const V third = vc<V>(1.f / 3.f);
+  const V third = vc<V>(1.0 / 3.0);
   const V dxx = vsub(pxx, vmul(vfma(rho2, ax.d, drho), third));
   const V dyy = vsub(pyy, vmul(vfma(rho2, ay.d, drho), third));
   V sv[6];  // ds of the x, y, z faces and of the xy, xz, yz edges (sign +)
@@ -175,17 +204,17 @@ __device__ __forceinline__ V collide_v(V (&g)[L::Q], float beta, bool bgk) {
   if (L::D == 2) {
     const V N = vsub(dxx, dyy);
     sv[0] = vmul(quarter, N);
-    sv[1] = vmul(vc<V>(-0.25f), N);
+    sv[1] = vmul(vc<V>(-0.25), N);
     sv[2] = zero;
     sv[3] = vmul(quarter, vsub(pxy, vmul(vmul(rho, ux), uy)));
     sv[4] = sv[5] = zero;
   } else {
     const V dzz = vsub(pzz, vmul(vfma(rho2, az.d, drho), third));
     const V Nxz = vsub(dxx, dzz), Nyz = vsub(dyy, dzz);
-    const V sixth = vc<V>(1.f / 6.f);
+    const V sixth = vc<V>(1.0 / 6.0);
     sv[0] = vmul(vsub(vadd(Nxz, Nxz), Nyz), sixth);
     sv[1] = vmul(vsub(vadd(Nyz, Nyz), Nxz), sixth);
-    sv[2] = vmul(vadd(Nxz, Nyz), vc<V>(-1.f / 6.f));
+    sv[2] = vmul(vadd(Nxz, Nyz), vc<V>(-1.0 / 6.0));
     const V rux = vmul(rho, ux);
     sv[3] = vmul(quarter, vsub(pxy, vmul(rux, uy)));
     sv[4] = vmul(quarter, vsub(pxz, vmul(rux, uz)));
@@ -221,7 +250,7 @@ __device__ __forceinline__ V collide_v(V (&g)[L::Q], float beta, bool bgk) {
         m = vmul(m, az.r[cz + 1]);
       }
       // feq_i - W_i = W_i (drho + rho e_i);  df_i = g_i - (feq_i - W_i)
-      const V d = vfma(vc<V>(-(float)weight<L>(i)), vfma(rho, e, drho), g[i]);
+      const V d = vfma(vc<V>(-weight<L>(i)), vfma(rho, e, drho), g[i]);
       const int nnz = (cx != 0) + (cy != 0) + (cz != 0);
       int gi = -1, sg = 1;
       if (nnz == 1) gi = cx ? 0 : (cy ? 1 : 2);
@@ -250,7 +279,7 @@ __device__ __forceinline__ V collide_v(V (&g)[L::Q], float beta, bool bgk) {
 #pragma unroll
   for (int k = 0; k < 6; ++k) sh = vfma(sv[k], grp[k], sh);
 
-  const float ib = __fdividef(1.0f, beta);
+  const SC ib = vdivf((SC)1, beta);
   // <.|.> carries a common factor rho that cancels in the ratio
   const V gamma = vgamma(sh, hh, ib, bgk);
 
@@ -280,7 +309,7 @@ __device__ __forceinline__ V collide_v(V (&g)[L::Q], float beta, bool bgk) {
       const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
       V e = exy;
       if (L::D == 3) e = vfma(az.e[cz + 1], qxy, e);
-      const V d = vfma(vc<V>(-(float)weight<L>(i)), vfma(rho, e, drho), g[i]);
+      const V d = vfma(vc<V>(-weight<L>(i)), vfma(rho, e, drho), g[i]);
       const int nnz = (cx != 0) + (cy != 0) + (cz != 0);
       V sds = zero;
       int gk = -1, sg = 1;
@@ -299,7 +328,7 @@ __device__ __forceinline__ V collide_v(V (&g)[L::Q], float beta, bool bgk) {
         if (cy < 0) t = vsub(t, By);
         if (cz > 0) t = vadd(t, Bz);
         if (cz < 0) t = vsub(t, Bz);
-        sds = vfma(vc<V>(-(float)weight<L>(i)), t, sds);
+        sds = vfma(vc<V>(-weight<L>(i)), t, sds);
       }
       g[i] = vsub(g[i], vfma(bg, d, sds));
     }

@@ -41,13 +41,16 @@ __host__ __device__ constexpr double weight(int i) {
 // ---- storage of one population ------------------------------------------
 // F32 keeps g = f - W; F16 / BF16 / F16N keep h = f/W - 1 so that every
 // direction uses the full mantissa around O(u) deviations.
-enum { STORE_F32 = 0, STORE_F16 = 1, STORE_BF16 = 2, STORE_F16N = 4 };
+// F64 keeps g = f - W in double precision and computes in FP64 (the test
+// storage: the FP32-compute path's reference on the GPU).
+enum { STORE_F32 = 0, STORE_F16 = 1, STORE_BF16 = 2, STORE_F64 = 3, STORE_F16N = 4 };
 
 template <int S>
 struct Store;
 
 template <>
 struct Store<STORE_F32> {
+  using C = float;  // compute type
   using T = float;
   static constexpr int bytes = 4;
   __device__ __forceinline__ static float load(const T *p, float /*w*/) { return __ldg(p); }
@@ -66,6 +69,7 @@ struct Store<STORE_F32> {
 
 template <>
 struct Store<STORE_F16> {
+  using C = float;  // compute type
   using T = __half;
   static constexpr int bytes = 2;
   __device__ __forceinline__ static float load(const T *p, float w) {
@@ -93,6 +97,7 @@ struct Store<STORE_F16> {
 
 template <>
 struct Store<STORE_BF16> {
+  using C = float;  // compute type
   using T = __nv_bfloat16;
   static constexpr int bytes = 2;
   __device__ __forceinline__ static float load(const T *p, float w) {
@@ -121,6 +126,17 @@ struct Store<STORE_BF16> {
   }
 };
 
+template <>
+struct Store<STORE_F64> {
+  using T = double;
+  using C = double;  // compute type
+  static constexpr int bytes = 8;
+  __device__ __forceinline__ static double load(const T *p, double /*w*/) { return __ldg(p); }
+  __device__ __forceinline__ static void store(T *p, double g, double /*invw*/) { *p = g; }
+  __device__ __forceinline__ static T encode(double g, double /*w*/) { return g; }
+  __device__ __forceinline__ static double decode(T v, double /*w*/) { return v; }
+};
+
 // F16N: a 16-bit float of h = f/W - 1 with its exponent range narrowed to
 // what h needs: sign, 3 exponent bits, 12 stored significand bits.  Codes
 // e = 1..7 hold (1 + m/4096) 2^(e-7), |h| in [2^-6, 2); e = 0 holds m 2^-18
@@ -136,6 +152,7 @@ struct Store<STORE_BF16> {
 // with an integer add that carries into the exponent, and a saturating min.
 template <>
 struct Store<STORE_F16N> {
+  using C = float;  // compute type
   using T = uint16_t;
   static constexpr int bytes = 2;
   __device__ __forceinline__ static float bits_to_scaled(uint32_t c) {

@@ -26,7 +26,7 @@ namespace kbc {
 template <int Q, int S, typename IX>
 __device__ __forceinline__ void sweep_gather(const Grid &g,
                                              const typename Store<S>::T *__restrict__ fin, int X,
-                                             int Y, int Z, float (&v)[Q]) {
+                                             int Y, int Z, typename Store<S>::C (&v)[Q]) {
   using L = Lat<Q>;
   using St = Store<S>;
   const int xs[3] = {nbr(X, 1, g.NX), X, nbr(X, -1, g.NX)};  // source x for cx = -1, 0, +1
@@ -41,18 +41,19 @@ __device__ __forceinline__ void sweep_gather(const Grid &g,
   for (int i = 0; i < Q; ++i) {
     const IX src = ((IX)zs[L::cz(i) + 1] * (IX)g.NY + (IX)ys[L::cy(i) + 1]) * (IX)g.pitch +
                    (IX)xs[L::cx(i) + 1];
-    v[i] = St::load(fin + ((IX)i * N + src), (float)weight<L>(i));
+    v[i] = St::load(fin + ((IX)i * N + src), (typename St::C)weight<L>(i));
   }
 }
 
 template <int Q, int S, typename IX>
 __device__ __forceinline__ void sweep_scatter(const Grid &g, typename Store<S>::T *__restrict__ fout,
-                                              IX k, const float (&v)[Q]) {
+                                              IX k, const typename Store<S>::C (&v)[Q]) {
   using L = Lat<Q>;
   using St = Store<S>;
   const IX N = (IX)g.N;
 #pragma unroll
-  for (int i = 0; i < Q; ++i) St::store(fout + ((IX)i * N + k), v[i], (float)(1.0 / weight<L>(i)));
+  for (int i = 0; i < Q; ++i)
+    St::store(fout + ((IX)i * N + k), v[i], (typename St::C)(1.0 / weight<L>(i)));
 }
 
 // One node (interior coordinates x, y, z) of the fused sweep.  IX: index
@@ -62,16 +63,18 @@ template <int Q, int S, bool FLAGS, typename IX = long long>
 __device__ __forceinline__ void sweep_node(const Grid &g,
                                            const typename Store<S>::T *__restrict__ fin,
                                            typename Store<S>::T *__restrict__ fout,
-                                           const uint8_t *__restrict__ flags, float beta, int bgk,
+                                           const uint8_t *__restrict__ flags,
+                                           typename Store<S>::C beta, int bgk,
                                            int *__restrict__ err, int x, int y, int z) {
   using L = Lat<Q>;
-  using St = Store<S>;
+  using C = typename Store<S>::C;
   const int X = x + g.px, Y = y + g.py, Z = z + g.pz;
   const IX k = (IX)sidx(g, X, Y, Z);
   if (FLAGS && flags[k] != NODE_FLUID) return;
-  float v[Q];
+  C v[Q];
   sweep_gather<Q, S, IX>(g, fin, X, Y, Z, v);
-  const float rho = collide<L, S == STORE_F32>(v, beta, bgk != 0);
+  // the conservation projection removes FP32 rounding residue (FP32 storage)
+  const C rho = collide_v<L, S == STORE_F32, C>(v, beta, bgk != 0);
   if (!(rho > 0.f && rho < 1e30f)) atomicOr(err, 1);
   sweep_scatter<Q, S, IX>(g, fout, k, v);
 }
@@ -89,7 +92,7 @@ template <int Q, int S, bool FLAGS, typename IX>
 __global__ void __launch_bounds__(128, SweepOcc<Q, S>::ctas)
     k_sweep(Grid g, const typename Store<S>::T *__restrict__ fin,
             typename Store<S>::T *__restrict__ fout, const uint8_t *__restrict__ flags,
-            float beta, int bgk, int *__restrict__ err) {
+            typename Store<S>::C beta, int bgk, int *__restrict__ err) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
@@ -476,10 +479,12 @@ static cudaError_t sweep_async_t(const Grid &g, const void *fin, void *fout, con
 template <int Q, int S, int R>
 __device__ __forceinline__ void sweep_rows(const Grid &g, const typename Store<S>::T *__restrict__ fin,
                                            typename Store<S>::T *__restrict__ fout,
-                                           const uint8_t *__restrict__ flags, float beta, int bgk,
+                                           const uint8_t *__restrict__ flags,
+                                           typename Store<S>::C beta, int bgk,
                                            int *__restrict__ err, int x, int r0, int m) {
   using L = Lat<Q>;
-  float v[R][Q];
+  using C = typename Store<S>::C;
+  C v[R][Q];
   int k[R];
   bool live[R];
 #pragma unroll
@@ -493,7 +498,7 @@ __device__ __forceinline__ void sweep_rows(const Grid &g, const typename Store<S
 #pragma unroll
   for (int q = 0; q < R; ++q) {
     if (!live[q]) continue;
-    const float rho = collide<L, S == STORE_F32>(v[q], beta, bgk != 0);
+    const C rho = collide_v<L, S == STORE_F32, C>(v[q], beta, bgk != 0);
     if (!(rho > 0.f && rho < 1e30f)) atomicOr(err, 1);
     sweep_scatter<Q, S, int>(g, fout, k[q], v[q]);
   }
@@ -524,10 +529,12 @@ __global__ void __launch_bounds__(128, KBC_MIN_CTAS)
     if (x < b.g.nx) {
       if (Q == 9 && b.narrow) {
         for (int r = tl.y; r < rend; r += 4)
-          sweep_rows<Q, S, 4>(b.g, fin, fout, b.flags, b.beta, b.bgk, b.err, x, r, rend - r);
+          sweep_rows<Q, S, 4>(b.g, fin, fout, b.flags, (typename Store<S>::C)b.beta, b.bgk, b.err,
+                              x, r, rend - r);
       } else {
         for (int r = tl.y; r < rend; ++r)
-          sweep_node<Q, S, true>(b.g, fin, fout, b.flags, b.beta, b.bgk, b.err, x, r % b.g.ny,
+          sweep_node<Q, S, true>(b.g, fin, fout, b.flags, (typename Store<S>::C)b.beta, b.bgk,
+                                 b.err, x, r % b.g.ny,
                                  r / b.g.ny);
       }
     }
@@ -557,18 +564,22 @@ static dim3 sweep_block(const Grid &g) {
 
 template <int Q, int S>
 static cudaError_t sweep_t(const Grid &g, const void *fin, void *fout, const uint8_t *flags,
-                           float beta, int bgk, int *err, cudaStream_t s, int variant) {
+                           double beta_d, int bgk, int *err, cudaStream_t s, int variant) {
   using T = typename Store<S>::T;
-  if (variant == SWEEP_ASYNC && S == STORE_F32 &&
-      (long long)g.ny * g.nz <= 65535LL * 8)
-    return sweep_async_t<Q>(g, fin, fout, flags, beta, bgk, err, s);
-  if (variant == SWEEP_ROWS) {
-    bool used = false;
-    cudaError_t e = sweep_rows_t<Q, S>(g, fin, fout, flags, beta, bgk, err, s, &used);
-    if (e != cudaSuccess || used) return e;
+  using C = typename Store<S>::C;
+  const C beta = (C)beta_d;
+  // FP64 storage: the one-node kernel only
+  if constexpr (S != STORE_F64) {
+    if (variant == SWEEP_ASYNC && S == STORE_F32 && (long long)g.ny * g.nz <= 65535LL * 8)
+      return sweep_async_t<Q>(g, fin, fout, flags, beta, bgk, err, s);
+    if (variant == SWEEP_ROWS) {
+      bool used = false;
+      cudaError_t e = sweep_rows_t<Q, S>(g, fin, fout, flags, beta, bgk, err, s, &used);
+      if (e != cudaSuccess || used) return e;
+    }
+    if (variant == SWEEP_AUTO || variant == SWEEP_PAIR)
+      return sweep2_t<Q, S>(g, fin, fout, flags, beta, bgk, err, s);
   }
-  if (variant == SWEEP_AUTO || variant == SWEEP_PAIR)
-    return sweep2_t<Q, S>(g, fin, fout, flags, beta, bgk, err, s);
   dim3 b = sweep_block(g);
   dim3 grid((g.nx + b.x - 1) / b.x, (g.ny + b.y - 1) / b.y, g.nz);
   const bool narrow = (long long)Q * g.N < (1LL << 31);  // every offset fits an int
@@ -588,7 +599,7 @@ static cudaError_t sweep_t(const Grid &g, const void *fin, void *fout, const uin
 
 
 cudaError_t launch_sweep(int Q, int storage, const Grid &g, const void *fin, void *fout,
-                         const uint8_t *flags, float beta, int bgk, int *err, cudaStream_t s,
+                         const uint8_t *flags, double beta, int bgk, int *err, cudaStream_t s,
                          int variant) {
   KBC_DISPATCH(Q, storage,
                return (sweep_t<QQ, SS>(g, fin, fout, flags, beta, bgk, err, s, variant)));
@@ -678,10 +689,11 @@ __global__ void k_macros(Grid g, const typename Store<S>::T *__restrict__ f,
   if (!flags || flags[k] == NODE_FLUID) {
     // sums of the stored deviations in FP32 (exact to the storage precision),
     // rho = 1 + sum and u = j / rho in FP64
-    float dr = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+    using C = typename Store<S>::C;
+    C dr = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const float v = Store<S>::load(f + (long long)i * g.N + k, (float)weight<L>(i));
+      const C v = Store<S>::load(f + (long long)i * g.N + k, (C)weight<L>(i));
       dr += v;
       jx += L::cx(i) * v;
       jy += L::cy(i) * v;
@@ -689,11 +701,11 @@ __global__ void k_macros(Grid g, const typename Store<S>::T *__restrict__ f,
     }
     if (rho32) {
       // FP32 outputs: rho and u = j / rho in FP32
-      const float rf = 1.f + dr, ir = 1.f / rf;
+      const float rf = 1.f + (float)dr, ir = 1.f / rf;
       rho32[t] = rf;
-      u32[t] = jx * ir;
-      u32[ustride + t] = jy * ir;
-      if (L::D == 3) u32[2 * ustride + t] = jz * ir;
+      u32[t] = (float)jx * ir;
+      u32[ustride + t] = (float)jy * ir;
+      if (L::D == 3) u32[2 * ustride + t] = (float)jz * ir;
       return;
     }
     r = 1.0 + (double)dr;

@@ -36,7 +36,9 @@ struct Layout {
   size_t total;
 };
 
-int pop_bytes(int storage) { return storage == LBM_STORE_F32 ? 4 : 2; }
+int pop_bytes(int storage) {
+  return storage == LBM_STORE_F64 ? 8 : (storage == LBM_STORE_F32 ? 4 : 2);
+}
 
 Grid make_grid(const lbm_config &c) {
   Grid g;
@@ -108,8 +110,9 @@ const char *validate(const lbm_config *c) {
   if (c->ny > 65535 || c->nz > 65535) return "ny and nz must be <= 65535";
   if (!(c->beta > 0.0 && c->beta < 1.0)) return "beta must lie in (0, 1)";
   if (c->storage != LBM_STORE_F32 && c->storage != LBM_STORE_F16 && c->storage != LBM_STORE_BF16 &&
-      c->storage != LBM_STORE_F16N)
+      c->storage != LBM_STORE_F16N && c->storage != LBM_STORE_F64)
     return "unknown storage";
+  if (c->storage == LBM_STORE_F64 && c->lattice != LBM_D2Q9) return "FP64 storage is D2Q9 only";
   if (c->collision != LBM_COLLIDE_KBC && c->collision != LBM_COLLIDE_BGK)
     return "unknown collision";
   const int naxes = c->lattice == LBM_D2Q9 ? 2 : 3;
@@ -293,7 +296,7 @@ lbm_status lbm_create(const lbm_config *cfg, void *workspace, size_t workspace_b
     for (int a = 0; a < 3; ++a) ctx->bp.face_u[fc][a] = (float)cfg->face_velocity[fc][a];
     ctx->bp.inlet[fc] = nullptr;
   }
-  ctx->bp.beta = (float)cfg->beta;
+  ctx->bp.beta = cfg->beta;
   ctx->bp.ramp_steps = cfg->inlet_ramp_steps;
   ctx->bp.step = ctx->counters + 3;
   if (ctx->g.px || ctx->g.py || ctx->g.pz) {
@@ -434,7 +437,7 @@ static SurfaceDev surface_dev(lbm_ctx *ctx);
 lbm_status lbm_step(lbm_ctx *ctx, int n) {
   GUARD();
   if (n < 0) return fail(ctx, LBM_EINVAL, "lbm_step: n < 0");
-  const float beta = (float)ctx->cfg.beta;
+  const double beta = ctx->cfg.beta;
   const int bgk = ctx->cfg.collision == LBM_COLLIDE_BGK;
   const bool bnd = ctx->nface > 0 || ctx->nbodies > 0;
   const int cap = ctx->nface + (ctx->nbodies > 0 ? ctx->cfg.max_links : 0);
@@ -1155,7 +1158,7 @@ lbm_status lbm_batch_create(lbm_ctx *const *ctxs, int n, void *workspace, size_t
     d.cur0 = c->cur;
     b->cur0[i] = c->cur;
     d.flags = c->flags;
-    d.beta = (float)c->cfg.beta;
+    d.beta = c->cfg.beta;
     d.bgk = c->cfg.collision == LBM_COLLIDE_BGK;
     d.err = c->err;
     d.narrow = (long long)c->Q * c->g.N < (1LL << 31);

@@ -11,7 +11,7 @@
 namespace kbc {
 
 // Dispatch a runtime (lattice, storage) pair to compile-time constants QQ, SS;
-// every branch must return.
+// every branch must return.  FP64 storage exists for D2Q9 only.
 #define KBC_DISPATCH(Q, storage, ...)                                               \
   do {                                                                              \
     if (Q == 9) {                                                                   \
@@ -19,6 +19,7 @@ namespace kbc {
       if (storage == STORE_F16) { constexpr int QQ = 9, SS = STORE_F16; __VA_ARGS__; }     \
       if (storage == STORE_BF16) { constexpr int QQ = 9, SS = STORE_BF16; __VA_ARGS__; }   \
       if (storage == STORE_F16N) { constexpr int QQ = 9, SS = STORE_F16N; __VA_ARGS__; }   \
+      if (storage == STORE_F64) { constexpr int QQ = 9, SS = STORE_F64; __VA_ARGS__; }     \
     } else if (Q == 27) {                                                           \
       if (storage == STORE_F32) { constexpr int QQ = 27, SS = STORE_F32; __VA_ARGS__; }    \
       if (storage == STORE_F16) { constexpr int QQ = 27, SS = STORE_F16; __VA_ARGS__; }    \
@@ -37,7 +38,7 @@ enum { SWEEP_AUTO = 0, SWEEP_DIRECT = 1, SWEEP_ROWS = 2, SWEEP_ASYNC = 3, SWEEP_
 // row-staged bulk-copy kernel when its shared-memory plan fits (else the
 // one-node kernel).
 cudaError_t launch_sweep(int Q, int storage, const Grid &g, const void *fin, void *fout,
-                         const uint8_t *flags, float beta, int bgk, int *err, cudaStream_t s,
+                         const uint8_t *flags, double beta, int bgk, int *err, cudaStream_t s,
                          int variant = SWEEP_AUTO);
 
 // f = feq(rho, u) for interior nodes [begin, begin+count) of the linear

@@ -22,7 +22,7 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ECAP
 STATUS_NAMES = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA", -4: "LBM_EUNSTABLE",
                 -5: "LBM_ETIMEOUT", -6: "LBM_ECAPACITY", -7: "LBM_ESTATE"}
 LBM_D2Q9, LBM_D3Q27 = 9, 27
-LBM_STORE_F32, LBM_STORE_F16, LBM_STORE_BF16, LBM_STORE_F16N = 0, 1, 2, 4
+LBM_STORE_F32, LBM_STORE_F16, LBM_STORE_BF16, LBM_STORE_F64, LBM_STORE_F16N = 0, 1, 2, 3, 4
 LBM_COLLIDE_KBC, LBM_COLLIDE_BGK = 0, 1
 LBM_BC_PERIODIC, LBM_BC_WALL, LBM_BC_INLET, LBM_BC_OUTLET, LBM_BC_FREESTREAM = 0, 1, 2, 3, 4
 

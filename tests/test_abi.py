@@ -47,7 +47,7 @@ def test_bad_configs_rejected_on_host(lib):
         lbm.make_config(27, 8, 8, 8, 1.5),                # beta outside (0,1)
         lbm.make_config(27, 0, 8, 8, 0.9),                # empty lattice
         lbm.make_config(27, 8, 8, 8, 0.9, storage=7),     # unknown storage
-        lbm.make_config(27, 8, 8, 8, 0.9, storage=3),     # unused storage code
+        lbm.make_config(27, 8, 8, 8, 0.9, storage=3),     # FP64 storage is D2Q9 only
         lbm.make_config(27, 8, 8, 8, 0.9, bc=(0, 1, 0, 0, 0, 0)),  # unpaired periodic face
     ]
     for cfg in bad:
@@ -68,6 +68,9 @@ def test_workspace_size_counts_populations(lib):
     assert a - b == pops * 2
     assert b == c
     assert a >= pops * 4
+    d9 = lbm.lbm_workspace_size(lbm.make_config(9, 64, 64, 1, 0.9, storage=lbm.LBM_STORE_F64))
+    f9 = lbm.lbm_workspace_size(lbm.make_config(9, 64, 64, 1, 0.9))
+    assert d9 - f9 >= 2 * 9 * 64 * 64 * 4
 
 
 def test_null_context_calls_fail_cleanly(lib):
