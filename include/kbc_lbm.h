@@ -233,6 +233,10 @@ typedef struct {
   int max_it;             /* Newton iteration limit */
   double dt;              /* structural time step (lattice steps) */
   void *stream;           /* cudaStream_t, NULL: library-owned */
+  int solve_fp64;         /* 0: Newton matrix and its solve in FP32 (an inexact
+                             Newton step: residual, stopping test and state stay
+                             FP64); 1: matrix and solve in FP64 (the exact Newton
+                             step) */
 } fem_beam_config;
 
 lbm_status fem_beam_workspace_size(const fem_beam_config *cfg, size_t *bytes);
@@ -262,10 +266,11 @@ void fem_destroy(fem_ctx *f);
  * projector; lumped mass.  Theta-scheme (Eq. timeInt), Newton with the
  * constant relaxation lambda (stop at |R| <= rtol |R0| + atol, R0 the
  * residual at the step's start), linearised systems by Jacobi-preconditioned
- * conjugate gradients to cg_rtol (0: 1e-3, an inexact Newton step; the
- * residual and its stopping test stay FP64, and with lambda = 0.7 the
- * Newton count is the same as with exact solves) within max_cg iterations
- * (0: 4 x DOFs); one cooperative launch per step.
+ * conjugate gradients in FP64 to cg_rtol (0: 1e-3, an inexact Newton step;
+ * the residual and its stopping test stay FP64, and with lambda = 0.7 the
+ * Newton count is the same as with exact solves; 1e-14: the FP64 solve of
+ * the exact Newton step) within max_cg iterations (0: 4 x DOFs); one
+ * cooperative launch per step.
  * ------------------------------------------------------------------------- */
 typedef struct fem_shell_ctx fem_shell_ctx;
 typedef struct {

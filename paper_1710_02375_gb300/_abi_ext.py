@@ -16,6 +16,7 @@ class fem_beam_config(ctypes.Structure):
         ("max_it", ctypes.c_int),
         ("dt", ctypes.c_double),
         ("stream", ctypes.c_void_p),
+        ("solve_fp64", ctypes.c_int),
     ]
 
 

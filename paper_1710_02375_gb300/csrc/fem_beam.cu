@@ -26,6 +26,7 @@
 #include <string.h>
 
 #include <new>
+#include <type_traits>
 
 #include "../../include/kbc_lbm.h"
 #include "fem_beam.cuh"
@@ -39,8 +40,10 @@ constexpr int kMaxN = 3 * kMaxBeamNodes, kMaxE = kMaxBeamNodes - 1;
 
 
 __device__ __forceinline__ double &band(double *A, int i, int j) { return A[i * BW + (j - i + KB)]; }
-__device__ __forceinline__ float &bandf(float *A, int i, int j) { return A[i * BW + (j - i + KB)]; }
-__device__ __forceinline__ float bandf(const float *__restrict__ A, int i, int j) {
+template <typename T>
+__device__ __forceinline__ T &bandf(T *A, int i, int j) { return A[i * BW + (j - i + KB)]; }
+template <typename T>
+__device__ __forceinline__ T bandf(const T *__restrict__ A, int i, int j) {
   return A[i * BW + (j - i + KB)];
 }
 
@@ -178,17 +181,23 @@ __device__ __forceinline__ double elem_z(int k, double c, double s) {
   return k < 3 ? v : -v;
 }
 
-__device__ __forceinline__ float elem_rf(int k, float c, float s) {
-  const float v = (k % 3 == 0) ? c : ((k % 3 == 1) ? s : 0.f);
+template <typename T>
+__device__ __forceinline__ T elem_rf(int k, T c, T s) {
+  const T v = (k % 3 == 0) ? c : ((k % 3 == 1) ? s : (T)0);
   return k < 3 ? -v : v;
 }
-__device__ __forceinline__ float elem_zf(int k, float c, float s) {
-  const float v = (k % 3 == 0) ? s : ((k % 3 == 1) ? -c : 0.f);
+template <typename T>
+__device__ __forceinline__ T elem_zf(int k, T c, T s) {
+  const T v = (k % 3 == 0) ? s : ((k % 3 == 1) ? -c : (T)0);
   return k < 3 ? v : -v;
 }
 
-// 3 x 3 helpers (row-major, FP32 registers).
-__device__ __forceinline__ void inv3(const float (&S)[9], float (&A)[9]) {
+__device__ __forceinline__ float recip_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip_rn(double x) { return 1.0 / x; }
+
+// 3 x 3 helpers (row-major, registers of the solve precision T).
+template <typename T>
+__device__ __forceinline__ void inv3(const T (&S)[9], T (&A)[9]) {
   A[0] = S[4] * S[8] - S[5] * S[7];
   A[1] = S[2] * S[7] - S[1] * S[8];
   A[2] = S[1] * S[5] - S[2] * S[4];
@@ -198,11 +207,12 @@ __device__ __forceinline__ void inv3(const float (&S)[9], float (&A)[9]) {
   A[6] = S[3] * S[7] - S[4] * S[6];
   A[7] = S[1] * S[6] - S[0] * S[7];
   A[8] = S[0] * S[4] - S[1] * S[3];
-  const float idet = __frcp_rn(S[0] * A[0] + S[1] * A[3] + S[2] * A[6]);
+  const T idet = recip_rn(S[0] * A[0] + S[1] * A[3] + S[2] * A[6]);
 #pragma unroll
   for (int q = 0; q < 9; ++q) A[q] *= idet;
 }
-__device__ __forceinline__ void load_block(const float *__restrict__ J, int r0, int c0, float (&B)[9]) {
+template <typename T>
+__device__ __forceinline__ void load_block(const T *__restrict__ J, int r0, int c0, T (&B)[9]) {
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -215,17 +225,18 @@ __device__ __forceinline__ void load_block(const float *__restrict__ J, int r0, 
 // the coupling E to the node after (U_i going down, L_i going up):
 //   S = D_i - C W_prev,  g = S^-1 (b_i - C g_prev),  W = S^-1 E
 // g overwrites rhs_i, W goes to Wsc[i].  last: no E (end of the sweep).
-__device__ __forceinline__ void thomas_step(const float *__restrict__ J, float *__restrict__ rhs,
-                                            float *__restrict__ Wsc, int i, int prev, int next,
-                                            float (&Wp)[9], float (&gp)[3], bool first) {
+template <typename T>
+__device__ __forceinline__ void thomas_step(const T *__restrict__ J, T *__restrict__ rhs,
+                                            T *__restrict__ Wsc, int i, int prev, int next,
+                                            T (&Wp)[9], T (&gp)[3], bool first) {
   const int r0 = 3 * i;
-  float S[9], b[3];
+  T S[9], b[3];
   load_block(J, r0, r0, S);
   b[0] = rhs[r0];
   b[1] = rhs[r0 + 1];
   b[2] = rhs[r0 + 2];
   if (!first) {
-    float C[9];
+    T C[9];
     load_block(J, r0, 3 * prev, C);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -235,7 +246,7 @@ __device__ __forceinline__ void thomas_step(const float *__restrict__ J, float *
       b[a] -= C[3 * a] * gp[0] + C[3 * a + 1] * gp[1] + C[3 * a + 2] * gp[2];
     }
   }
-  float A[9];
+  T A[9];
   inv3(S, A);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -243,7 +254,7 @@ __device__ __forceinline__ void thomas_step(const float *__restrict__ J, float *
     rhs[r0 + a] = gp[a];
   }
   if (next >= 0) {
-    float E[9];
+    T E[9];
     load_block(J, r0, 3 * next, E);
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -261,14 +272,14 @@ __device__ __forceinline__ void thomas_step(const float *__restrict__ J, float *
 // (twisted block factorisation): thread 0 (warp 0) sweeps nodes 0 .. m-1
 // downwards, thread 32 (warp 1) nodes nn-1 .. m+1 upwards, thread 0 then
 // solves node m from both sides, and each thread substitutes back along its
-// half.  All FP32 registers; x overwrites rhs.  Called by every thread of the
-// CTA (it contains barriers).
-__device__ __forceinline__ void block_twisted(const float *__restrict__ J, float *__restrict__ rhs,
-                                              float *__restrict__ Wsc, float *__restrict__ gm,
-                                              int nn) {
+// half.  Registers of the solve precision T; x overwrites rhs.  Called by
+// every thread of the CTA (it contains barriers).
+template <typename T>
+__device__ __forceinline__ void block_twisted(const T *__restrict__ J, T *__restrict__ rhs,
+                                              T *__restrict__ Wsc, T *__restrict__ gm, int nn) {
   const int tid = threadIdx.x, m = nn / 2;
   if (tid == 0 || tid == 32) {
-    float Wp[9], gp[3];
+    T Wp[9], gp[3];
     if (tid == 0) {
       for (int i = 0; i < m; ++i) thomas_step(J, rhs, Wsc, i, i - 1, i + 1, Wp, gp, i == 0);
     } else {
@@ -279,7 +290,7 @@ __device__ __forceinline__ void block_twisted(const float *__restrict__ J, float
   if (tid == 0) {
     // node m: (D_m - L_m W_{m-1} - U_m W_{m+1}) x_m = b_m - L_m g_{m-1} - U_m g_{m+1}
     const int r0 = 3 * m;
-    float S[9], b[3];
+    T S[9], b[3];
     load_block(J, r0, r0, S);
     b[0] = rhs[r0];
     b[1] = rhs[r0 + 1];
@@ -287,9 +298,9 @@ __device__ __forceinline__ void block_twisted(const float *__restrict__ J, float
     for (int side = 0; side < 2; ++side) {
       const int o = side == 0 ? m - 1 : m + 1;
       if (o < 0 || o >= nn) continue;
-      float C[9];
+      T C[9];
       load_block(J, r0, 3 * o, C);
-      const float *W = Wsc + 9 * o, *g = rhs + 3 * o;
+      const T *W = Wsc + 9 * o, *g = rhs + 3 * o;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
 #pragma unroll
@@ -298,7 +309,7 @@ __device__ __forceinline__ void block_twisted(const float *__restrict__ J, float
         b[a] -= C[3 * a] * g[0] + C[3 * a + 1] * g[1] + C[3 * a + 2] * g[2];
       }
     }
-    float A[9];
+    T A[9];
     inv3(S, A);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -308,13 +319,13 @@ __device__ __forceinline__ void block_twisted(const float *__restrict__ J, float
   }
   __syncthreads();
   if (tid == 0 || tid == 32) {
-    float xn[3] = {gm[0], gm[1], gm[2]};
+    T xn[3] = {gm[0], gm[1], gm[2]};
     const int step = tid == 0 ? -1 : 1;
     for (int i = m + step; i >= 0 && i < nn; i += step) {
-      float x[3];
+      T x[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        const float *w = Wsc + 9 * i + 3 * a;
+        const T *w = Wsc + 9 * i + 3 * a;
         x[a] = rhs[3 * i + a] - (w[0] * xn[0] + w[1] * xn[1] + w[2] * xn[2]);
         rhs[3 * i + a] = x[a];
       }
@@ -325,20 +336,34 @@ __device__ __forceinline__ void block_twisted(const float *__restrict__ J, float
   }
 }
 
+// T: precision of the Newton matrix and its solve (float: the default inexact
+// Newton step; double: the FP64 mode).  FP32 keeps the matrix's mass part
+// in MJ; FP64 forms it from M each iteration (the shared memory of the
+// FP64 matrix takes the place of both FP32 arrays).
+template <typename T>
+struct BeamMat {
+  float J[kMaxN * BW], MJ[kMaxN * BW];
+};
+template <>
+struct BeamMat<double> {
+  double J[kMaxN * BW];
+};
+template <typename T>
 struct BeamShared {
-  float J[kMaxN * BW], MJ[kMaxN * BW];  // Newton matrix (FP32), its mass part
+  BeamMat<T> mat;  // Newton matrix (band storage)
   double M[kMaxN * BW];
   double u[kMaxN], u0[kMaxN], v0[kMaxN], f0[kMaxN], F1[kMaxN], R[kMaxN], D[kMaxN];
   double Rc[kMaxN];         // load part of the residual, theta F1 + (1 - theta)(F0 - f(u0))
   unsigned char fx[kMaxN];  // Dirichlet mask
-  float rhs[kMaxN], W[kMaxBeamNodes * 9], gm[3];
+  T rhs[kMaxN], W[kMaxBeamNodes * 9], gm[3];
   double X[2 * kMaxBeamNodes];
   // element scalars: constants of the step, then the current state's
   double L0[kMaxE], b0[kMaxE], EAL0[kMaxE], k2[kMaxE];
   double c[kMaxE], s[kMaxE], iL[kMaxE], N[kMaxE], M1[kMaxE], M2[kMaxE];
   double rot0[kMaxE], c0[kMaxE], s0[kMaxE];  // chord rotation and direction at the step's start
-  // FP32 copies for the tangent: c, s, 1/L, N/L, (M1 + M2)/L^2, EA/L0, k2
-  float tc[kMaxE], ts[kMaxE], tiL[kMaxE], tNL[kMaxE], tML[kMaxE], tEA[kMaxE], tk2[kMaxE];
+  // copies in the solve precision for the tangent: c, s, 1/L, N/L,
+  // (M1 + M2)/L^2, EA/L0, k2
+  T tc[kMaxE], ts[kMaxE], tiL[kMaxE], tNL[kMaxE], tML[kMaxE], tEA[kMaxE], tk2[kMaxE];
   double red[4];
 };
 
@@ -348,7 +373,8 @@ struct BeamShared {
 // plus the angle from the start chord to the current one, by the arctangent
 // series when it is small (|tan| < 0.1: terms to t^15, truncation below
 // 1e-17 relative) and by atan2 otherwise.
-__device__ __forceinline__ void elem_state(const BeamParams &p, BeamShared &S, const double *u,
+template <typename T>
+__device__ __forceinline__ void elem_state(const BeamParams &p, BeamShared<T> &S, const double *u,
                                            int ne, bool base) {
   for (int e = threadIdx.x; e < ne; e += blockDim.x) {
     const int a = e, b = e + 1;
@@ -393,16 +419,17 @@ __device__ __forceinline__ void elem_state(const BeamParams &p, BeamShared &S, c
     S.N[e] = S.EAL0[e] * (L - S.L0[e]);
     S.M1[e] = S.k2[e] * (2 * t1 + t2);
     S.M2[e] = S.k2[e] * (t1 + 2 * t2);
-    S.tc[e] = (float)S.c[e];
-    S.ts[e] = (float)S.s[e];
-    S.tiL[e] = (float)iL;
-    S.tNL[e] = (float)(S.N[e] * iL);
-    S.tML[e] = (float)((S.M1[e] + S.M2[e]) * iL * iL);
+    S.tc[e] = (T)S.c[e];
+    S.ts[e] = (T)S.s[e];
+    S.tiL[e] = (T)iL;
+    S.tNL[e] = (T)(S.N[e] * iL);
+    S.tML[e] = (T)((S.M1[e] + S.M2[e]) * iL * iL);
   }
 }
 
 // Internal force of DOF i from its (at most two) elements.
-__device__ __forceinline__ double dof_internal(const BeamShared &S, int i, int ne) {
+template <typename T>
+__device__ __forceinline__ double dof_internal(const BeamShared<T> &S, int i, int ne) {
   const int j = i / 3, q = i % 3;
   double f = 0.0;
   for (int side = 0; side < 2; ++side) {
@@ -417,7 +444,8 @@ __device__ __forceinline__ double dof_internal(const BeamShared &S, int i, int n
 }
 
 // Block sum of one value per thread (all threads call; result to all).
-__device__ __forceinline__ double block_sum(BeamShared &S, double v) {
+template <typename T>
+__device__ __forceinline__ double block_sum(BeamShared<T> &S, double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int w = threadIdx.x >> 5;
   __syncthreads();
@@ -432,12 +460,13 @@ __device__ __forceinline__ double block_sum(BeamShared &S, double v) {
 // momentum-exchange forces of the flag's surface vertices (coupled: vforce,
 // surf_x / surf_v of the whole surface, the flag's vertices start at v0).
 // Launch: one CTA of 128 threads per beam.
-template <bool COUPLED>
+template <bool COUPLED, typename T>
 __device__ __forceinline__ void beam_step_body(const BeamParams &p, const BeamDev &d,
                                                const double *__restrict__ F1_in,
                                                const double *__restrict__ vforce, double *surf_x,
                                                double *surf_v, int v0) {
-  __shared__ BeamShared S;
+  __shared__ BeamShared<T> S;
+  constexpr bool FP64 = std::is_same<T, double>::value;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nn = p.nn, n = 3 * nn, ne = nn - 1;
   const double a_v = 1.0 / (p.theta * p.dt), i_th = 1.0 / p.theta, i_dt = 1.0 / p.dt;
@@ -449,7 +478,7 @@ __device__ __forceinline__ void beam_step_body(const BeamParams &p, const BeamDe
   }
   for (int i = tid; i < n * BW; i += nt) {
     S.M[i] = d.M[i];
-    S.MJ[i] = (float)(d.M[i] * cM);
+    if constexpr (!FP64) S.mat.MJ[i] = (float)(d.M[i] * cM);
   }
   for (int i = tid; i < 2 * nn; i += nt) S.X[i] = d.X[i];
   __syncthreads();
@@ -460,8 +489,8 @@ __device__ __forceinline__ void beam_step_body(const BeamParams &p, const BeamDe
     S.b0[e] = atan2(X0y, X0x);
     S.EAL0[e] = p.EA / L0;
     S.k2[e] = 2.0 * p.EI / L0;
-    S.tEA[e] = (float)S.EAL0[e];
-    S.tk2[e] = (float)S.k2[e];
+    S.tEA[e] = (T)S.EAL0[e];
+    S.tk2[e] = (T)S.k2[e];
   }
   // ---- loads F1
   if (COUPLED) {
@@ -522,7 +551,7 @@ __device__ __forceinline__ void beam_step_body(const BeamParams &p, const BeamDe
       const double f = dof_internal(S, i, ne);
       double R = mv * i_dt + p.theta * f - S.Rc[i];
       if (S.fx[i]) R = 0.0;
-      S.rhs[i] = (float)-R;  // right-hand side of J du = -R
+      S.rhs[i] = (T)-R;  // right-hand side of J du = -R
       part += R * R;
     }
     const double rn = sqrt(block_sum(S, part));
@@ -541,39 +570,43 @@ __device__ __forceinline__ void beam_step_body(const BeamParams &p, const BeamDe
       break;
     }
     // ---- Newton matrix J = M / (theta dt^2) + theta K (band), Dirichlet
-    // rows / columns, and the solve of J du = -R in FP32: an inexact Newton
-    // step (relative error ~1e-6 on this diagonally dominant J) while the
-    // residual and its stopping test stay FP64, so the converged state
-    // meets the same FP64 test; FP32 keeps the serial elimination chain
-    // off GB300's scarce FP64 pipe
-    for (int i = tid; i < n * BW; i += nt) S.J[i] = S.MJ[i];
+    // rows / columns, and the solve of J du = -R in precision T.  FP32 (the
+    // default): an inexact Newton step (relative error ~1e-6 on this
+    // diagonally dominant J) while the residual and its stopping test stay
+    // FP64, so the converged state meets the same FP64 test, and the serial
+    // elimination chain stays off GB300's scarce FP64 pipe.  FP64: the exact
+    // Newton step of the oracle.
+    for (int i = tid; i < n * BW; i += nt) {
+      if constexpr (FP64) S.mat.J[i] = S.M[i] * cM;
+      else S.mat.J[i] = S.mat.MJ[i];
+    }
     __syncthreads();
-    const float thf = (float)p.theta;
+    const T thf = (T)p.theta;
     for (int colour = 0; colour < 2; ++colour) {
       const int nel = (ne - colour + 1) / 2;  // elements colour, colour + 2, ...
       for (int w = tid; w < nel * 21; w += nt) {
         const int e = colour + 2 * (w / 21), pk = c_pk[w % 21], pl = c_pl[w % 21];
-        const float c = S.tc[e], s = S.ts[e], iL = S.tiL[e], k2 = S.tk2[e];
-        const float rk = elem_rf(pk, c, s), rl = elem_rf(pl, c, s);
-        const float zk = elem_zf(pk, c, s), zl = elem_zf(pl, c, s);
-        const float b1k = -zk * iL + (pk == 2 ? 1.f : 0.f), b2k = -zk * iL + (pk == 5 ? 1.f : 0.f);
-        const float b1l = -zl * iL + (pl == 2 ? 1.f : 0.f), b2l = -zl * iL + (pl == 5 ? 1.f : 0.f);
-        float v = S.tEA[e] * rk * rl + b1k * (2.f * k2 * b1l + k2 * b2l) +
-                  b2k * (k2 * b1l + 2.f * k2 * b2l) + S.tNL[e] * zk * zl +
-                  S.tML[e] * (rk * zl + zk * rl);
+        const T c = S.tc[e], s = S.ts[e], iL = S.tiL[e], k2 = S.tk2[e];
+        const T rk = elem_rf(pk, c, s), rl = elem_rf(pl, c, s);
+        const T zk = elem_zf(pk, c, s), zl = elem_zf(pl, c, s);
+        const T b1k = -zk * iL + (pk == 2 ? (T)1 : (T)0), b2k = -zk * iL + (pk == 5 ? (T)1 : (T)0);
+        const T b1l = -zl * iL + (pl == 2 ? (T)1 : (T)0), b2l = -zl * iL + (pl == 5 ? (T)1 : (T)0);
+        T v = S.tEA[e] * rk * rl + b1k * ((T)2 * k2 * b1l + k2 * b2l) +
+              b2k * (k2 * b1l + (T)2 * k2 * b2l) + S.tNL[e] * zk * zl +
+              S.tML[e] * (rk * zl + zk * rl);
         v *= thf;
         const int gi = 3 * e + pk, gj = 3 * e + pl;
-        bandf(S.J, gi, gj) += v;
-        if (pk != pl) bandf(S.J, gj, gi) += v;
+        bandf(S.mat.J, gi, gj) += v;
+        if (pk != pl) bandf(S.mat.J, gj, gi) += v;
       }
       __syncthreads();
     }
     for (int idx = tid; idx < n * BW; idx += nt) {
       const int i = idx / BW, j = i + idx % BW - KB;
-      if (j >= 0 && j < n && (S.fx[i] || S.fx[j])) S.J[idx] = (i == j) ? 1.f : 0.f;
+      if (j >= 0 && j < n && (S.fx[i] || S.fx[j])) S.mat.J[idx] = (i == j) ? (T)1 : (T)0;
     }
     __syncthreads();
-    block_twisted(S.J, S.rhs, S.W, S.gm, nn);
+    block_twisted(S.mat.J, S.rhs, S.W, S.gm, nn);
     __syncthreads();
     for (int i = tid; i < n; i += nt) S.u[i] += p.lambda * (double)S.rhs[i];
     __syncthreads();
@@ -610,22 +643,38 @@ __device__ __forceinline__ void beam_step_body(const BeamParams &p, const BeamDe
   }
 }
 
-template <bool COUPLED>
+template <bool COUPLED, typename T>
 __global__ void __launch_bounds__(128)
     k_beam_step(BeamParams p, BeamDev d, const double *__restrict__ F1_in,
                 const double *__restrict__ vforce, double *surf_x, double *surf_v, int v0) {
-  beam_step_body<COUPLED>(p, d, F1_in, vforce, surf_x, surf_v, v0);
+  beam_step_body<COUPLED, T>(p, d, F1_in, vforce, surf_x, surf_v, v0);
 }
 
-// One CTA per coupled beam of a batch.
+// Launch of one beam step in the solve precision the beam's parameters ask for.
+template <bool COUPLED>
+static cudaError_t launch_beam_step(const BeamParams &p, const BeamDev &d, const double *F1_in,
+                                    const double *vforce, double *surf_x, double *surf_v, int v0,
+                                    cudaStream_t s) {
+  if (p.solve64)
+    k_beam_step<COUPLED, double><<<1, 128, 0, s>>>(p, d, F1_in, vforce, surf_x, surf_v, v0);
+  else
+    k_beam_step<COUPLED, float><<<1, 128, 0, s>>>(p, d, F1_in, vforce, surf_x, surf_v, v0);
+  return cudaGetLastError();
+}
+
+// One CTA per coupled beam of a batch; each launch takes the beams of its
+// solve precision.
+template <typename T>
 __global__ void __launch_bounds__(128) k_beam_step_batch(const BeamBatchDesc *__restrict__ d) {
   const BeamBatchDesc &b = d[blockIdx.x];
-  beam_step_body<true>(b.p, b.d, nullptr, b.vforce, b.surf_x, b.surf_v, b.v0);
+  if ((b.p.solve64 != 0) != std::is_same<T, double>::value) return;
+  beam_step_body<true, T>(b.p, b.d, nullptr, b.vforce, b.surf_x, b.surf_v, b.v0);
 }
 
-cudaError_t launch_beam_batch(const BeamBatchDesc *d, int n, cudaStream_t s) {
+cudaError_t launch_beam_batch(const BeamBatchDesc *d, int n, int any_fp64, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_beam_step_batch<<<n, 128, 0, s>>>(d);
+  k_beam_step_batch<float><<<n, 128, 0, s>>>(d);
+  if (any_fp64) k_beam_step_batch<double><<<n, 128, 0, s>>>(d);
   return cudaGetLastError();
 }
 
@@ -727,7 +776,7 @@ lbm_status fem_beam_create(const fem_beam_config *c, void *workspace, size_t byt
   f->out_mean = (float *)p; p += al(sizeof(float) * nout);
   f->out_std = (float *)p;
   f->p = BeamParams{nn, c->EA, c->EI, c->rhoA, c->thickness, c->theta, c->lambda, c->rtol,
-                    c->atol, c->dt, c->max_it, 0.0};
+                    c->atol, c->dt, c->max_it, 0.0, c->solve_fp64 != 0};
   f->d = BeamDev{X, fx, u, v, F0, iters, nullptr, f->stats, Mb};
   f->F1 = F1;
   cudaError_t e = cudaMemcpyAsync(X, c->X, sizeof(double) * 2 * nn, cudaMemcpyDefault, f->stream);
@@ -768,8 +817,7 @@ lbm_status fem_beam_step(fem_ctx *f, const double *F1) {
   if (!f || !F1) return LBM_EINVAL;
   if (f->poisoned) return LBM_ESTATE;
   FEM_CK(cudaMemcpyAsync(f->F1, F1, sizeof(double) * 3 * f->p.nn, cudaMemcpyDefault, f->stream));
-  k_beam_step<false><<<1, 128, 0, f->stream>>>(f->p, f->d, f->F1, nullptr, nullptr, nullptr, 0);
-  FEM_CK(cudaGetLastError());
+  FEM_CK(launch_beam_step<false>(f->p, f->d, f->F1, nullptr, nullptr, nullptr, 0, f->stream));
   return LBM_OK;
 }
 
@@ -821,8 +869,7 @@ void fem_describe(const fem_ctx *f, BeamParams *p, BeamDev *d) {
 // forces of vertices [v0, v0 + 2 nn), then the new flag surface.
 cudaError_t launch_beam_coupled(fem_ctx *f, const double *vforce, double *surf_x, double *surf_v,
                                 int v0, cudaStream_t s) {
-  k_beam_step<true><<<1, 128, 0, s>>>(f->p, f->d, nullptr, vforce, surf_x, surf_v, v0);
-  return cudaGetLastError();
+  return launch_beam_step<true>(f->p, f->d, nullptr, vforce, surf_x, surf_v, v0, s);
 }
 
 // Flag surface of the current beam state (used when coupling starts).
@@ -916,8 +963,7 @@ cudaError_t launch_beam_coupled_guess(fem_ctx *f, const double *vforce, double *
   p.accept_tol = accept_tol;
   BeamDev d = f->d;
   d.u_guess = f->u_guess;
-  k_beam_step<true><<<1, 128, 0, s>>>(p, d, nullptr, vforce, surf_x, surf_v, v0);
-  return cudaGetLastError();
+  return launch_beam_step<true>(p, d, nullptr, vforce, surf_x, surf_v, v0, s);
 }
 
 lbm_status fem_set_normalisation(fem_ctx *f, const float *in_mean, const float *in_std,

@@ -13,6 +13,7 @@ struct BeamParams {
   double theta, lambda, rtol, atol, dt;
   int max_it;
   double accept_tol;   // > 0: accept the initial guess when |R| <= accept_tol |F_ext|
+  int solve64;         // 1: Newton matrix and solve in FP64, 0: in FP32 (inexact Newton)
 };
 
 struct BeamDev {

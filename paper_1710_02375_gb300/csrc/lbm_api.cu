@@ -1034,6 +1034,7 @@ struct lbm_batch {
   int *d_coupled = nullptr;
   BeamBatchDesc *d_beam = nullptr;
   int ncoupled = 0;
+  int beam_fp64 = 0;  // some coupled beam solves its Newton systems in FP64
   int max_cap = 0, max_nv3 = 0, max_fresh = 0;
   long long max_band = 0;
   int ntiles = 0, max_tiles = 0;
@@ -1189,6 +1190,7 @@ lbm_status lbm_batch_create(lbm_ctx *const *ctxs, int n, void *workspace, size_t
       bd.surf_x = (double *)(c->ws + c->lay.sx);
       bd.surf_v = (double *)(c->ws + c->lay.sv);
       bd.v0 = c->fem_v0;
+      if (bd.p.solve64) b->beam_fp64 = 1;
       beams.push_back(bd);
       const Band &B = c->band;
       b->max_band = std::max(b->max_band, (long long)(B.x1 - B.x0) * (B.y1 - B.y0) * (B.z1 - B.z0));
@@ -1238,7 +1240,7 @@ static lbm_status batch_steps(lbm_batch *b, int nsteps) {
                            b->parity, b->rows_per_tile, b->ctas_per_sm, b->stream));
     b->parity ^= 1;
     if (b->ncoupled) {
-      BCK(launch_beam_batch(b->d_beam, b->ncoupled, b->stream));
+      BCK(launch_beam_batch(b->d_beam, b->ncoupled, b->beam_fp64, b->stream));
       BCK(launch_geometry_batch(b->Q, b->storage, b->d_desc, b->d_coupled, b->ncoupled,
                                 b->max_band, b->max_fresh, b->parity, b->stream));
     }

@@ -124,7 +124,7 @@ float *mlp_input_buffer(mlp_ctx *x);
 int mlp_dim(const mlp_ctx *x, int l);
 int mlp_layers(const mlp_ctx *x);
 void fem_describe(const fem_ctx *f, BeamParams *p, BeamDev *d);
-cudaError_t launch_beam_batch(const BeamBatchDesc *d, int n, cudaStream_t s);
+cudaError_t launch_beam_batch(const BeamBatchDesc *d, int n, int any_fp64, cudaStream_t s);
 cudaError_t launch_beam_coupled(fem_ctx *f, const double *vforce, double *surf_x, double *surf_v,
                                 int v0, cudaStream_t s);
 cudaError_t launch_flag_surface(fem_ctx *f, double *surf_x, double *surf_v, int v0,

@@ -416,7 +416,7 @@ class Beam:
     Newton with relaxation lambda); torch allocates the workspace."""
 
     def __init__(self, X, EA, EI, rhoA, fixed, thickness=0.0, theta=0.5, lam=0.7, rtol=1e-10,
-                 atol=1e-13, max_it=200, dt=1.0, stream=None, device="cuda"):
+                 atol=1e-13, max_it=200, dt=1.0, stream=None, device="cuda", solve_fp64=False):
         import torch
         from ._abi_ext import fem_beam_config
         load()
@@ -431,6 +431,7 @@ class Beam:
         c.fixed = self.fixed.ctypes.data
         c.theta, c.lambda_, c.rtol, c.atol, c.max_it, c.dt = theta, lam, rtol, atol, max_it, dt
         c.stream = self.stream.cuda_stream
+        c.solve_fp64 = int(bool(solve_fp64))
         n = ctypes.c_size_t()
         st = load().fem_beam_workspace_size(ctypes.byref(c), ctypes.byref(n))
         if st != LBM_OK:

@@ -33,6 +33,48 @@ def test_beam_prescribed_loads_matches_oracle():
     assert np.max(np.abs(u[1::3])) > 0.5  # large deflection regime reached
 
 
+def test_beam_solve_precision_modes():
+    """The Newton matrix and its solve in FP64 (solve_fp64: the exact Newton
+    step of the oracle) and in FP32 (the default inexact step), the same
+    prescribed large-deflection loads: FP64 agrees with the oracle to
+    round-off, FP32 to the Newton stopping test; time per step of each."""
+    import time
+    import torch
+    from paper_1710_02375_gb300.lbm import Beam
+    X, EA, EI, rhoA, fixed = synth.c1_flag_beam()
+    n = 3 * len(X)
+    s = (X[:, 0] - X[0, 0]) / (X[-1, 0] - X[0, 0])
+    loads = []
+    for t in range(300):
+        F1 = np.zeros(n)
+        F1[1::3] = 2e-3 * np.sin(0.02 * t) * s
+        F1[0::3] = 5e-4 * s
+        loads.append(F1)
+    ob = orc.Beam(X, EA, EI, rhoA, fixed)
+    u, v, F0 = np.zeros(n), np.zeros(n), np.zeros(n)
+    ref = []
+    for F1 in loads:
+        u, v, _ = ob.step(u, v, F0, F1)
+        F0 = F1
+        ref.append(u.copy())
+    out = {}
+    for fp64 in (True, False):
+        gb = Beam(X, EA, EI, rhoA, fixed, thickness=2.0, solve_fp64=fp64)
+        worst, t_total = 0.0, 0.0
+        for k, F1 in enumerate(loads):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            gb.step(F1)
+            ug, _, itg = gb.state()
+            t_total += time.perf_counter() - t0
+            assert itg >= 0
+            worst = max(worst, np.max(np.abs(ug - ref[k])) / max(np.max(np.abs(ref[k])), 1e-30))
+        out["fp64" if fp64 else "fp32"] = (worst, 1e3 * t_total / len(loads))
+    print("BEAM SOLVE MODES (max relative error vs oracle, ms per step incl. readback):", out)
+    assert out["fp64"][0] < 1e-12, out
+    assert out["fp32"][0] < 1e-8, out
+
+
 def test_beam_csm3_matches_oracle():
     """CSM3 (flag under gravity, large deflection, dt = 5 ms, 1200 steps) on
     the GPU beam against the oracle beam, which the paper's CSM3 table pins."""

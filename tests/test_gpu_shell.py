@@ -49,6 +49,36 @@ def test_shell_prescribed_loads_matches_oracle():
     assert np.max(np.abs(u[:, 2])) > 2.0  # tip deflection of several lattice units
 
 
+def test_shell_fp64_solve_mode_matches_oracle_to_roundoff():
+    """cg_rtol = 1e-14: the linearised systems solved to FP64 accuracy (the
+    exact Newton step of the oracle's banded solve); the default 1e-3 is the
+    inexact step of the other shell tests."""
+    from paper_1710_02375_gb300.lbm import Shell
+    nx, ny = 17, 9
+    X, fixed = plate(nx, ny)
+    E, nu, h, rho = 0.0129, 0.4, 2.0, 20.0
+    args = (X, nx, ny, E, nu, h, rho, fixed)
+    gs = Shell(*args, atol=1e-12, cg_rtol=1e-14)
+    os_ = orc.Shell(*args)
+    u, R, v = os_.rest()
+    F0 = np.zeros((nx * ny, 6))
+    s = X[:, 0] / 40.0
+    worst = 0.0
+    for t in range(60):
+        F1 = np.zeros((nx * ny, 6))
+        F1[:, 2] = 0.08 * s * (1.0 + 0.5 * np.sin(0.05 * t))
+        F1[:, 0] = 0.01 * s
+        gs.step(F1)
+        u, R, v, it = os_.step(u, R, v, F0, F1, atol=1e-12)
+        F0 = F1
+        ug, Rg, vg, (itg, ncg) = gs.state()
+        assert it >= 0 and itg >= 0, (it, itg)
+        worst = max(worst, np.max(np.abs(ug - u)) / max(np.max(np.abs(u)), 1e-30),
+                    np.max(np.abs(Rg - R)))
+    print("SHELL FP64 solve mode: worst", worst, "cg iterations last step", ncg)
+    assert worst < 1e-12, worst
+
+
 def small_plate_case():
     from paper_1710_02375_gb300 import synth
     return synth.plate_case(nxl=48, nyl=24, nzl=24, L=16.0, b=8.0, h=2.0, x0=12.0, u_in=0.04,
