@@ -344,6 +344,7 @@ def run_ours(args):
         forms["batched_c4_rigid"] = c4_leg(args, coupled=False)
         forms["batched_c4_coupled"] = c4_leg(args, coupled=True)
         forms["coupled_c1"] = c1_leg(args)
+        forms["coupled_turek_quasi2d"] = turek_leg(args)
         forms["coupled_c3"] = c3_leg(args)
         forms["surrogate"] = {
             "measured_in": "tests/test_gpu_surrogate.py, tests/test_gpu_plate_surrogate.py",
@@ -391,6 +392,8 @@ STATED_ERRORS = {
                   "(tests/test_gpu_fem.py)",
     "coupled_c3": "small plate (48x24x24, 8x4 shell) 40 coupled steps: velocity 4.4e-7, shell 1.1e-7; "
                   "full size 2 steps sampled 2.6e-7 (tests/test_gpu_shell.py)",
+    "coupled_turek_quasi2d": "220x41x2, 600 coupled steps: velocity 5.5e-7, tip 3.5e-5, body force "
+                             "5.2e-6 (tests/test_gpu_turek_span.py)",
 }
 
 
@@ -471,6 +474,30 @@ def c1_leg(args):
     return {"ms_per_step": ms, "steps_per_s": 1e3 / ms, "direct_launch_ms_per_step": ms_direct,
             "newton_solves_per_step": solves / max(1, steps), "steps": chunk * reps,
             "config": "D2Q9 220x41, Re=100, 21-node beam, steps 110-410 of the inflow ramp"}
+
+
+def turek_leg(args, nz=4):
+    """The quasi-2-D Turek set-up on the C1 geometry (D3Q27 220 x 41 x 4,
+    periodic span, cylinder and flag extruded, beam coupled per unit span),
+    CUDA-graph replay after 100 start-up steps."""
+    import torch
+    from paper_1710_02375_gb300 import lbm as abi
+    from paper_1710_02375_gb300.cases import turek_span_coupled
+    stream = torch.cuda.Stream()
+    L, beam = turek_span_coupled(nz=nz, stream=stream)
+    L.step(100)
+    chunk, reps = 10, 20
+    L.step_graph(chunk, 1)
+    abi.fsi_get_structure_stats(L.ctx, reset=True)
+    ms = _timed(stream, lambda k: L.step_graph(chunk, k), reps) / chunk
+    _, _, solves, steps = abi.fsi_get_structure_stats(L.ctx)
+    L.check()
+    L.close()
+    beam.close()
+    nodes = 220 * 41 * nz
+    return {"ms_per_step": ms, "steps_per_s": 1e3 / ms, "mlups": nodes / (ms * 1e-3) / 1e6,
+            "newton_solves_per_step": solves / max(1, steps), "steps": chunk * reps,
+            "config": f"D3Q27 220x41x{nz}, periodic span, Re=100, 21-node beam per unit span"}
 
 
 def c3_leg(args):

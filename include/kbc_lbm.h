@@ -324,6 +324,23 @@ lbm_status fsi_couple_shell(lbm_ctx *ctx, fem_shell_ctx *s, int first_vertex);
  * The fem context must stay alive while coupled.  LBM_EINVAL on a bad range. */
 lbm_status fsi_couple(lbm_ctx *ctx, fem_ctx *f, int first_vertex);
 
+/* Quasi-two-dimensional coupling of a beam to a D3Q27 lattice (section
+ * "Turek Benchmark": a few lattice points spanwise, periodic for the fluid,
+ * plane strain for the solid).  The z axis must be periodic; the flag is
+ * the beam's polygon extruded along z over [z0, z1] with z0 < 0 and
+ * z1 > nz (the closed triangle mesh, end caps included, is the caller's
+ * geometry; the caps lie outside the periodic box).  The polygon's vertices
+ * at z0 are surface vertices [first_vertex_z0, first_vertex_z0 + 2 nn), those
+ * at z1 [first_vertex_z1, first_vertex_z1 + 2 nn), each range in the order of
+ * fsi_couple.  Nodal loads are per unit span: the four vertex forces of a
+ * beam node summed and divided by nz (the beam's stiffness and mass are per
+ * unit span, the plane-strain values for a flag of the paper's kind).  The
+ * structural step and the transfer back to the surface are those of
+ * fsi_couple.  LBM_EINVAL on a bad lattice, z axis, span or vertex range; no
+ * surrogate with this coupling. */
+lbm_status fsi_couple_span(lbm_ctx *ctx, fem_ctx *f, int first_vertex_z0, int first_vertex_z1,
+                           double z0, double z1);
+
 /* Advance n * repeats steps by replaying a CUDA graph of n steps (n even, so
  * the two population buffers return to their roles).  The graph is captured
  * on the first call and again after any call that changes what a step

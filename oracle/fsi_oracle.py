@@ -165,3 +165,66 @@ class CSSPlate:
         new_solid = orc.solid_mask(self.shape, self.surf)
         orc.fresh_init(27, self.f, self.solid, new_solid, self.surf, periodic=self.periodic)
         self.solid = new_solid
+
+
+class CSSFlagSpan:
+    """Quasi-two-dimensional form of CSSFlag (section "Turek Benchmark": a few
+    lattice points spanwise, periodic for the fluid, plane strain for the
+    solid): D3Q27 fluid on shape (nz, ny, nx) periodic along z; the rigid
+    outlines and the flag polygon extruded along z over [z0, z1] (z0 < 0,
+    z1 > nz, so the end caps lie outside the periodic box).  Vertex k of the
+    2-D outline (rigid vertices, then the flag's 2 nn) sits at z0 as vertex k
+    and at z1 as vertex n + k; the triangles e3 and their bodies are given.
+    Nodal loads per unit span: the forces of a node's four vertices (two
+    edges, two ends) summed and divided by nz; moments are not transferred,
+    as in the 2-D loop."""
+
+    def __init__(self, shape, beta, bc, inlet, ramp, x_rigid, e3, body3, beam: "orc.Beam", h,
+                 z0, z1):
+        self.shape, self.beta, self.bc, self.inlet, self.ramp = shape, beta, bc, inlet, ramp
+        self.x_rigid = np.asarray(x_rigid, dtype=np.float64)
+        self.e3, self.body3 = np.asarray(e3, np.int32), np.asarray(body3, np.int32)
+        self.beam, self.h, self.z0, self.z1 = beam, h, z0, z1
+        n = 3 * beam.nn
+        self.u = np.zeros(n)
+        self.v = np.zeros(n)
+        self.F0 = np.zeros(n)
+        self.t = 0
+        self.f = orc.init_equilibrium(27, np.ones(shape), np.zeros((3,) + tuple(shape)))
+        self.surf = self._surface()
+        self.solid = orc.solid_mask(shape, self.surf)
+
+    def _surface(self):
+        xf, vf = flag_vertices(self.beam.X, self.u, self.v, self.h)
+        x2 = np.concatenate([self.x_rigid, xf])
+        v2 = np.concatenate([np.zeros_like(self.x_rigid), vf])
+        n = len(x2)
+        x3 = np.zeros((2 * n, 3))
+        v3 = np.zeros((2 * n, 3))
+        x3[:n, :2], x3[n:, :2] = x2, x2
+        x3[:n, 2], x3[n:, 2] = self.z0, self.z1
+        v3[:n, :2], v3[n:, :2] = v2, v2
+        return orc.Surface(x3, v3, self.e3, self.body3)
+
+    def step(self):
+        s = 1.0
+        if self.ramp and self.t < self.ramp:
+            s = 0.5 * (1 - np.cos(np.pi * self.t / self.ramp))
+        self.f, vf, bf, _ = orc.step_bc(27, self.beta, self.f, bc=self.bc, inlet=self.inlet,
+                                        inlet_scale=s, surf=self.surf, solid=self.solid)
+        self.vforce, self.bforce = vf, bf
+        nn, nr = self.beam.nn, self.x_rigid.shape[0]
+        n = nr + 2 * nn
+        F1 = np.zeros((nn, 3))
+        for j in range(nn):
+            for vtx in (nr + j, nr + 2 * nn - 1 - j, n + nr + j, n + nr + 2 * nn - 1 - j):
+                F1[j, 0] += vf[vtx, 0]
+                F1[j, 1] += vf[vtx, 1]
+        F1 = F1.reshape(-1) / self.shape[0]
+        self.u, self.v, it = self.beam.step(self.u, self.v, self.F0, F1)
+        self.F0 = F1
+        self.surf = self._surface()
+        new_solid = orc.solid_mask(self.shape, self.surf)
+        orc.fresh_init(27, self.f, self.solid, new_solid, self.surf, periodic=(0, 0, 1))
+        self.solid = new_solid
+        self.t += 1

@@ -60,6 +60,8 @@ def declare(L):
     L.fem_destroy.argtypes = [vp]
     L.fem_destroy.restype = None
     L.fsi_couple.argtypes = [vp, vp, i32]
+    L.fsi_couple_span.argtypes = [vp, vp, i32, i32, ctypes.c_double, ctypes.c_double]
+    L.fsi_couple_span.restype = ctypes.c_int
     L.fsi_couple_shell.argtypes = [vp, vp, i32]
     L.fsi_couple_shell.restype = ctypes.c_int
     L.fem_shell_workspace_size.argtypes = [ctypes.POINTER(fem_shell_config), ctypes.POINTER(sz)]

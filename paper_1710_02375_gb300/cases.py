@@ -94,3 +94,32 @@ def plate_coupled(c, storage=0, stream=None, band=None, atol=1e-13):
     S.set_state(u=c["u0"], R=c["R0"])
     lbm.fsi_couple_shell(L.ctx, S.ctx, 0)
     return L, S
+
+
+def turek_span_coupled(nz=2, Re=100.0, stream=None, seed=0):
+    """The quasi-2-D Turek set-up on the C1 geometry (section "Turek
+    Benchmark"): D3Q27 channel 220 x 41 x nz periodic along z, parabolic
+    inflow with the 1000-step ramp, cylinder and flag extruded along z over
+    [-2, nz + 2], the flag an elastic beam coupled per unit span
+    (fsi_couple_span).  Returns (Lattice, Beam)."""
+    from . import lbm, synth
+    from .lbm import Beam, Lattice
+    c = C1
+    nx, ny = c["nx"], c["ny"]
+    nu = (2.0 / 3.0) * c["u_max"] * c["D"] / Re
+    beta = 1.0 / (6 * nu + 1)
+    prof2 = synth.parabolic_profile(ny, c["u_max"], noise=1e-4, seed=seed)
+    prof = np.tile(prof2, (1, nz))           # face index z * ny + y
+    x2, e2, body2, _ = synth.cylinder_flag_2d()
+    z0, z1 = -2.0, nz + 2.0
+    x3, e3, b3 = synth.extrude_polygons(x2, e2, body2, z0, z1)
+    ncyl = int(np.sum(body2 == 0))
+    L = Lattice(27, nx, ny, nz, beta, bc=c["bc"], max_links=20000, max_vertices=len(x3),
+                max_elements=len(e3), inlet_ramp_steps=c["ramp"], stream=stream)
+    L.set_inlet_profile(0, prof)
+    L.set_geometry(x3, e3, b3, band_margin=8.0)
+    L.init_equilibrium(np.ones((nz, ny, nx)), np.zeros((3, nz, ny, nx)))
+    X, EA, EI, rhoA, fixed = synth.c1_flag_beam()
+    beam = Beam(X, EA, EI, rhoA, fixed, thickness=c["h"], stream=L.stream)
+    lbm.fsi_couple_span(L.ctx, beam.ctx, ncyl, len(x2) + ncyl, z0, z1)
+    return L, beam

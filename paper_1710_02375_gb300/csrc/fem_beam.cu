@@ -161,6 +161,35 @@ __device__ void flag_vertex(const BeamParams &p, const double *X, const double *
   vt[0] = v[3 * j] + 0.5 * p.h * dnx; vt[1] = v[3 * j + 1] + 0.5 * p.h * dny;
 }
 
+// The two surface vertices of beam node j (bottom edge vertex v0 + j, top
+// edge vertex v0 + 2 nn - 1 - j): 2-D positions and velocities, or, for the
+// spanwise extrusion, 3-D vertices at z0 (from v0) and at z1 (from p.v1)
+// moving in the plane.
+__device__ void store_flag_vertices(const BeamParams &p, const double *X, const double *u,
+                                    const double *v, int j, int v0, double *surf_x,
+                                    double *surf_v) {
+  double xb[2], vb[2], xt[2], vt[2];
+  flag_vertex(p, X, u, v, j, xb, vb, xt, vt);
+  const int nn = p.nn;
+  if (!p.span) {
+    const int ib = v0 + j, it = v0 + 2 * nn - 1 - j;
+    surf_x[2 * ib] = xb[0]; surf_x[2 * ib + 1] = xb[1];
+    surf_v[2 * ib] = vb[0]; surf_v[2 * ib + 1] = vb[1];
+    surf_x[2 * it] = xt[0]; surf_x[2 * it + 1] = xt[1];
+    surf_v[2 * it] = vt[0]; surf_v[2 * it + 1] = vt[1];
+    return;
+  }
+  for (int end = 0; end < 2; ++end) {
+    const int base = end == 0 ? v0 : p.v1;
+    const double z = end == 0 ? p.z0 : p.z1;
+    const int ib = base + j, it = base + 2 * nn - 1 - j;
+    surf_x[3 * ib] = xb[0]; surf_x[3 * ib + 1] = xb[1]; surf_x[3 * ib + 2] = z;
+    surf_v[3 * ib] = vb[0]; surf_v[3 * ib + 1] = vb[1]; surf_v[3 * ib + 2] = 0.0;
+    surf_x[3 * it] = xt[0]; surf_x[3 * it + 1] = xt[1]; surf_x[3 * it + 2] = z;
+    surf_v[3 * it] = vt[0]; surf_v[3 * it + 1] = vt[1]; surf_v[3 * it + 2] = 0.0;
+  }
+}
+
 // ---- per-step work split for GB300's FP64 rate: each FP64 warp instruction
 // occupies the FP64 pipe for many cycles, so the step is organised to keep
 // FP64 instruction counts per warp low -- element scalars once per element,
@@ -499,8 +528,16 @@ __device__ __forceinline__ void beam_step_body(const BeamParams &p, const BeamDe
     // rotation is a stiff mode that the staggered one-step lag destabilises)
     for (int j = tid; j < nn; j += nt) {
       const int vb = v0 + j, vt = v0 + 2 * nn - 1 - j;
-      S.F1[3 * j] = vforce[3 * vb] + vforce[3 * vt];
-      S.F1[3 * j + 1] = vforce[3 * vb + 1] + vforce[3 * vt + 1];
+      double fx = vforce[3 * vb] + vforce[3 * vt], fy = vforce[3 * vb + 1] + vforce[3 * vt + 1];
+      if (p.span) {
+        // quasi-2-D: the same polygon vertices at the far end of the span,
+        // the summed force per unit span
+        const int wb = p.v1 + j, wt = p.v1 + 2 * nn - 1 - j;
+        fx = (fx + (vforce[3 * wb] + vforce[3 * wt])) * p.inv_depth;
+        fy = (fy + (vforce[3 * wb + 1] + vforce[3 * wt + 1])) * p.inv_depth;
+      }
+      S.F1[3 * j] = fx;
+      S.F1[3 * j + 1] = fy;
       S.F1[3 * j + 2] = 0.0;
     }
   } else {
@@ -631,15 +668,7 @@ __device__ __forceinline__ void beam_step_body(const BeamParams &p, const BeamDe
   __syncthreads();
   if (COUPLED) {
     // transfer displacement and velocity to the surface mesh
-    for (int j = tid; j < nn; j += nt) {
-      double xb[2], vb[2], xt[2], vt[2];
-      flag_vertex(p, S.X, S.u, S.R, j, xb, vb, xt, vt);
-      const int ib = v0 + j, it2 = v0 + 2 * nn - 1 - j;
-      surf_x[2 * ib] = xb[0]; surf_x[2 * ib + 1] = xb[1];
-      surf_v[2 * ib] = vb[0]; surf_v[2 * ib + 1] = vb[1];
-      surf_x[2 * it2] = xt[0]; surf_x[2 * it2 + 1] = xt[1];
-      surf_v[2 * it2] = vt[0]; surf_v[2 * it2 + 1] = vt[1];
-    }
+    for (int j = tid; j < nn; j += nt) store_flag_vertices(p, S.X, S.u, S.R, j, v0, surf_x, surf_v);
   }
 }
 
@@ -876,13 +905,7 @@ cudaError_t launch_beam_coupled(fem_ctx *f, const double *vforce, double *surf_x
 __global__ void k_flag_surface(BeamParams p, BeamDev d, double *surf_x, double *surf_v, int v0) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= p.nn) return;
-  double xb[2], vb[2], xt[2], vt[2];
-  flag_vertex(p, d.X, d.u, d.v, j, xb, vb, xt, vt);
-  const int ib = v0 + j, it = v0 + 2 * p.nn - 1 - j;
-  surf_x[2 * ib] = xb[0]; surf_x[2 * ib + 1] = xb[1];
-  surf_v[2 * ib] = vb[0]; surf_v[2 * ib + 1] = vb[1];
-  surf_x[2 * it] = xt[0]; surf_x[2 * it + 1] = xt[1];
-  surf_v[2 * it] = vt[0]; surf_v[2 * it + 1] = vt[1];
+  store_flag_vertices(p, d.X, d.u, d.v, j, v0, surf_x, surf_v);
 }
 
 // Network input of the surrogate for step t: the out-of-balance loads
@@ -989,6 +1012,16 @@ lbm_status fem_get_stats(fem_ctx *f, int *stats) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
   return e == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }
+
+void fem_set_span(fem_ctx *f, int span, int v1, double z0, double z1, double inv_depth) {
+  f->p.span = span;
+  f->p.v1 = v1;
+  f->p.z0 = z0;
+  f->p.z1 = z1;
+  f->p.inv_depth = inv_depth;
+}
+
+int fem_span(const fem_ctx *f) { return f->p.span; }
 
 cudaError_t launch_flag_surface(fem_ctx *f, double *surf_x, double *surf_v, int v0,
                                 cudaStream_t s) {

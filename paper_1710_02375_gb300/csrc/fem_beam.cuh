@@ -14,6 +14,12 @@ struct BeamParams {
   int max_it;
   double accept_tol;   // > 0: accept the initial guess when |R| <= accept_tol |F_ext|
   int solve64;         // 1: Newton matrix and solve in FP64, 0: in FP32 (inexact Newton)
+  // spanwise extrusion (quasi-2-D coupling to a D3Q27 lattice periodic in z):
+  // the flag polygon's vertices at z = z0 start at the coupling's first
+  // vertex, those at z = z1 at v1; loads per unit span are the four vertex
+  // forces of a node summed and times inv_depth
+  int span, v1;
+  double z0, z1, inv_depth;
 };
 
 struct BeamDev {

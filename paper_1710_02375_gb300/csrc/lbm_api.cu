@@ -692,9 +692,40 @@ lbm_status fsi_couple(lbm_ctx *ctx, fem_ctx *f, int first_vertex) {
   ctx->fem = f;
   ctx->fem_v0 = first_vertex;
   ctx->graph_dirty = true;
+  fem_set_span(f, 0, 0, 0.0, 0.0, 1.0);
   if (fem_reset_stats(f) != LBM_OK) return fail(ctx, LBM_ECUDA, "fsi_couple: counter reset failed");
   CK(launch_flag_surface(f, (double *)(ctx->ws + ctx->lay.sx), (double *)(ctx->ws + ctx->lay.sv),
                          first_vertex, ctx->stream));
+  return run_geometry(ctx, 1);
+}
+
+lbm_status fsi_couple_span(lbm_ctx *ctx, fem_ctx *f, int first_vertex_z0, int first_vertex_z1,
+                           double z0, double z1) {
+  GUARD();
+  ctx->mlp = nullptr;
+  if (!f) return fail(ctx, LBM_EINVAL, "fsi_couple_span: no beam");
+  if (ctx->Q != 27) return fail(ctx, LBM_EINVAL, "fsi_couple_span: the spanwise coupling is D3Q27");
+  if (ctx->cfg.bc[4] != LBM_BC_PERIODIC)
+    return fail(ctx, LBM_EINVAL, "fsi_couple_span: the z axis must be periodic");
+  if (!(z0 < 0.0 && z1 > (double)ctx->g.nz))
+    return fail(ctx, LBM_EINVAL, "fsi_couple_span: the flag must span the periodic box (z0 < 0, z1 > nz)");
+  if (ctx->nbodies == 0) return fail(ctx, LBM_ESTATE, "fsi_couple_span: set the geometry first");
+  if (ctx->shell) return fail(ctx, LBM_ESTATE, "fsi_couple_span: a shell is coupled already");
+  const int nn = fem_nodes(f);
+  if (first_vertex_z0 < 0 || first_vertex_z0 + 2 * nn > ctx->nv || first_vertex_z1 < 0 ||
+      first_vertex_z1 + 2 * nn > ctx->nv ||
+      (first_vertex_z0 < first_vertex_z1 + 2 * nn && first_vertex_z1 < first_vertex_z0 + 2 * nn))
+    return fail(ctx, LBM_EINVAL, "fsi_couple_span: vertex ranges [%d, +%d) and [%d, +%d) invalid "
+                "for a surface of %d vertices", first_vertex_z0, 2 * nn, first_vertex_z1, 2 * nn,
+                ctx->nv);
+  ctx->fem = f;
+  ctx->fem_v0 = first_vertex_z0;
+  ctx->graph_dirty = true;
+  fem_set_span(f, 1, first_vertex_z1, z0, z1, 1.0 / (double)ctx->g.nz);
+  if (fem_reset_stats(f) != LBM_OK)
+    return fail(ctx, LBM_ECUDA, "fsi_couple_span: counter reset failed");
+  CK(launch_flag_surface(f, (double *)(ctx->ws + ctx->lay.sx), (double *)(ctx->ws + ctx->lay.sv),
+                         first_vertex_z0, ctx->stream));
   return run_geometry(ctx, 1);
 }
 
@@ -748,6 +779,8 @@ lbm_status fsi_set_surrogate(lbm_ctx *ctx, mlp_ctx *mlp, const float *in_mean, c
     return LBM_OK;
   }
   if (!ctx->fem) return fail(ctx, LBM_ESTATE, "fsi_set_surrogate: couple a beam or a shell first");
+  if (ctx->fem && fem_span(ctx->fem))
+    return fail(ctx, LBM_EINVAL, "fsi_set_surrogate: not for a spanwise-coupled beam");
   const int nn = fem_nodes(ctx->fem);
   if (mlp_dim(mlp, 0) != surrogate_inputs(nn) || mlp_dim(mlp, mlp_layers(mlp)) != 3 * nn - 3)
     return fail(ctx, LBM_EINVAL,

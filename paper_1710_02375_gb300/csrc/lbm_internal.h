@@ -104,6 +104,9 @@ cudaError_t launch_geometry_batch(int Q, int storage, const InstDesc *d, const i
                                   long long max_band, int max_fresh, int parity, cudaStream_t s);
 
 int fem_nodes(const fem_ctx *f);
+// Spanwise extrusion of a coupled beam's flag (quasi-2-D coupling, D3Q27).
+void fem_set_span(fem_ctx *f, int span, int v1, double z0, double z1, double inv_depth);
+int fem_span(const fem_ctx *f);
 cudaError_t launch_surrogate_input(fem_ctx *f, const double *vforce, int v0, float *xin,
                                    cudaStream_t s);
 cudaError_t launch_surrogate_guess(fem_ctx *f, const float *yhat, cudaStream_t s);

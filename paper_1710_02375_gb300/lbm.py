@@ -411,6 +411,13 @@ def fsi_couple(ctx, f, first_vertex):
     _chk(ctx, load().fsi_couple(ctx, f, int(first_vertex)))
 
 
+def fsi_couple_span(ctx, f, first_vertex_z0, first_vertex_z1, z0, z1):
+    """Quasi-2-D coupling of a beam to a D3Q27 lattice periodic in z (the
+    flag polygon extruded over [z0, z1])."""
+    _chk(ctx, load().fsi_couple_span(ctx, f, int(first_vertex_z0), int(first_vertex_z1),
+                                     float(z0), float(z1)))
+
+
 class Beam:
     """Owner of one GPU beam context (FP64 co-rotational beam, theta-scheme,
     Newton with relaxation lambda); torch allocates the workspace."""

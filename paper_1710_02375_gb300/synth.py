@@ -315,3 +315,62 @@ def box_surface(lo, hi):
     for a, b, c, d in quads:
         e += [(a, b, c), (a, c, d)]
     return x, np.array(e, dtype=np.int32)
+
+
+def _ear_clip(poly):
+    """Triangles (index triples into poly, counter-clockwise) of a simple
+    counter-clockwise polygon poly[n,2] by ear clipping."""
+    idx = list(range(len(poly)))
+    tris = []
+
+    def cross(o, a, b):
+        return (a[0] - o[0]) * (b[1] - o[1]) - (a[1] - o[1]) * (b[0] - o[0])
+
+    guard = 0
+    while len(idx) > 3 and guard < 100000:
+        guard += 1
+        for k in range(len(idx)):
+            i0, i1, i2 = idx[k - 1], idx[k], idx[(k + 1) % len(idx)]
+            a, b, c = poly[i0], poly[i1], poly[i2]
+            if cross(a, b, c) <= 0.0:
+                continue  # reflex or degenerate corner
+            inside = False
+            for j in idx:
+                if j in (i0, i1, i2):
+                    continue
+                p = poly[j]
+                if cross(a, b, p) >= 0.0 and cross(b, c, p) >= 0.0 and cross(c, a, p) >= 0.0:
+                    inside = True
+                    break
+            if not inside:
+                tris.append((i0, i1, i2))
+                idx.pop(k)
+                break
+    tris.append(tuple(idx))
+    return tris
+
+
+def extrude_polygons(x, e, body, z0, z1):
+    """Closed triangle meshes of 2-D closed counter-clockwise polygons (x[n,2],
+    segments e[m,2], body per segment) extruded along z over [z0, z1]: vertex
+    k at z0 is k, at z1 is n + k; two side triangles per segment and both end
+    caps (ear-clipped), all wound with outward normals.  Returns
+    (x3[2n,3], e3[ne,3], body3[ne])."""
+    x = np.asarray(x, dtype=np.float64)
+    n = len(x)
+    x3 = np.concatenate([np.column_stack([x, np.full(n, z0)]), np.column_stack([x, np.full(n, z1)])])
+    tri, tb = [], []
+    for (a, b), bd in zip(np.asarray(e), np.asarray(body)):
+        tri += [(a, b, n + b), (a, n + b, n + a)]
+        tb += [bd, bd]
+    for bd in np.unique(body):
+        segs = np.asarray(e)[np.asarray(body) == bd]
+        nxt = {int(a): int(b) for a, b in segs}
+        loop = [int(segs[0, 0])]
+        while nxt[loop[-1]] != loop[0]:
+            loop.append(nxt[loop[-1]])
+        for i, j, k in _ear_clip(x[loop]):
+            tri.append((n + loop[i], n + loop[j], n + loop[k]))   # top cap, normal +z
+            tri.append((loop[i], loop[k], loop[j]))               # bottom cap, normal -z
+            tb += [bd, bd]
+    return x3, np.array(tri, dtype=np.int32), np.array(tb, dtype=np.int32)
