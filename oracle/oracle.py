@@ -78,6 +78,9 @@ def _declare(L):
     L.or_fresh_init.argtypes = [c_int, c_int, c_int, c_int, I32, U8, U8, c_int, D, D, D]
     L.or_links.argtypes = [c_int, c_int, c_int, c_int, I32, U8, c_int, c_int, c_int, D, D, I32, I32,
                            c_int, I32, I32, D, I32, D]
+    L.or_eos.argtypes = [c_int, c_int, D, D]
+    L.or_step_multiphase.argtypes = [c_int, c_int, c_int, c_int, c_double, c_int, c_double, c_int, D,
+                                     D, D, D]
 
 
 def _p(a: np.ndarray):
@@ -326,6 +329,38 @@ def fresh_init(lat, f, old_solid, new_solid, surf: "Surface", periodic=(0, 0, 1)
     return _check(lib().or_fresh_init(lat, nx, ny, nz, per.ctypes.data_as(I32), a.ctypes.data_as(U8),
                                       b.ctypes.data_as(U8), surf.x.shape[0], _p(surf.x), _p(surf.v),
                                       _p(f)))
+
+
+# ---------------------------------------------------------------- multiphase
+def eos(rho, kind=0):
+    """Pressure of Eq. (eos) (kind 0) or of the ideal gas rho c_s^2 (kind 1)."""
+    r = np.ascontiguousarray(np.atleast_1d(rho), dtype=np.float64)
+    p = np.zeros_like(r)
+    _check(lib().or_eos(int(kind), r.size, _p(r), _p(p)))
+    return p
+
+
+def step_multiphase(lat, beta, f, kappa, eos_kind=0, g_ext=None, mode=0, want_force=False):
+    """One periodic multiphase KBC step (mean-field Korteweg force, exact
+    difference forcing, shifted entropic product for gamma); returns f_new
+    (and the force field F[3, nz, ny, nx] when want_force)."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    _, nz, ny, nx = f.shape
+    fo = np.zeros_like(f)
+    g = None if g_ext is None else np.ascontiguousarray(g_ext, dtype=np.float64)
+    F = np.zeros((3, nz, ny, nx)) if want_force else None
+    _check(lib().or_step_multiphase(lat, nx, ny, nz, float(beta), int(mode), float(kappa), int(eos_kind),
+                                    _p(g) if g is not None else None, _p(f), _p(fo),
+                                    _p(F) if F is not None else None))
+    return (fo, F) if want_force else fo
+
+
+def macros_forced(lat, f, F):
+    """Density and fluid velocity of a post-collision state f of a forced step
+    with force F: the momentum before the step's forcing was j - F, the fluid
+    velocity of the step (j - F/2) / rho."""
+    rho, u = macros(lat, f)
+    return rho, u - 0.5 * F / rho
 
 
 # ---------------------------------------------------------------- structure

@@ -374,3 +374,34 @@ def extrude_polygons(x, e, body, z0, z1):
             tri.append((loop[i], loop[k], loop[j]))               # bottom cap, normal -z
             tb += [bd, bd]
     return x3, np.array(tri, dtype=np.int32), np.array(tb, dtype=np.int32)
+
+
+# ------------------------------------------------------------------ two-phase inputs
+RHO_L, RHO_V = 7.55, 0.073   # liquid and vapour densities quoted for the polynomial EOS
+
+
+def slab_density(n, rho_l=RHO_L, rho_v=RHO_V, width=3.0, frac=0.5):
+    """1-D periodic density profile [n]: a liquid slab of length frac*n centred
+    in the box, tanh interfaces of the given width on both sides."""
+    x = np.arange(n) + 0.5
+    a, b = 0.5 * n * (1 - frac), 0.5 * n * (1 + frac)
+    return rho_v + (rho_l - rho_v) * 0.5 * (np.tanh((x - a) / width) - np.tanh((x - b) / width))
+
+
+def droplet_density(shape, radius, center=None, rho_l=RHO_L, rho_v=RHO_V, width=2.0, noise=0.0,
+                    seed=0):
+    """Density field [nz, ny, nx] of a liquid droplet (circle for nz = 1,
+    sphere otherwise) of the given radius in vapour, tanh interface; optional
+    multiplicative noise of relative amplitude `noise`."""
+    nz, ny, nx = shape
+    if center is None:
+        center = (0.5 * nx, 0.5 * ny, 0.5 * nz)
+    z, y, x = np.meshgrid(np.arange(nz) + 0.5, np.arange(ny) + 0.5, np.arange(nx) + 0.5,
+                          indexing="ij")
+    d2 = (x - center[0]) ** 2 + (y - center[1]) ** 2
+    if nz > 1:
+        d2 = d2 + (z - center[2]) ** 2
+    rho = rho_v + (rho_l - rho_v) * 0.5 * (1 - np.tanh((np.sqrt(d2) - radius) / width))
+    if noise:
+        rho = rho * (1 + noise * np.random.default_rng(seed).uniform(-1, 1, size=rho.shape))
+    return rho
