@@ -103,6 +103,7 @@ typedef struct {
   int max_elements;       /* capacity of surface-mesh elements over all bodies */
   int inlet_ramp_steps;   /* inlet velocity ramp (1 - cos(pi t/T))/2 over T steps, 0: none */
   void *stream;           /* cudaStream_t to run on; NULL: the library creates one */
+  int multiphase;         /* 1: reserve the fields of the multiphase model (lbm_set_multiphase) */
 } lbm_config;
 
 /* Bytes of device workspace lbm_create needs for this configuration. */
@@ -494,6 +495,49 @@ lbm_status lbm_get_macros_f32(lbm_ctx *ctx, float *rho, float *u);
 enum { LBM_SWEEP_AUTO = 0, LBM_SWEEP_DIRECT = 1, LBM_SWEEP_ROWS = 2, LBM_SWEEP_ASYNC = 3,
        LBM_SWEEP_PAIR = 4 };
 lbm_status lbm_set_sweep_variant(lbm_ctx *ctx, int variant);
+
+/* ---------------------------------------------------------------------------
+ * Multiphase model (section "Extensions to fluid-structure interaction in
+ * multiphase flow"): the body force F = F_f of Eq. (Force) (mean-field
+ * force, Eqs. (force1) and (Korteweg)) imposed by the exact difference
+ * method, Eq. (force_mp), with gamma of Eq. (gamma_min_approx) taken in the
+ * shifted entropic product <X|Y> = sum X_i Y_i / feq_i(rho, u + du).
+ *
+ * Per step: rho(x) = sum_i f_i(x - c_i) (the pulled populations),
+ * phi = sqrt(max(rho c_s^2 - p(rho), 0)), lap rho = 6 sum_i W_i (rho(x + c_i)
+ * - rho(x)), and at every node
+ *     F = 2 phi d(phi) + kappa rho d(lap rho) + rho g,
+ *     d_a psi(x) = 3 sum_i W_i c_ia psi(x + c_i)   (isotropic lattice gradient),
+ *     du = F / rho,   u = j / rho,
+ *     f_i' = f_i - beta (2 ds_i + gamma dh_i) + feq_i(rho, u + du) - feq_i(rho, u).
+ * The sign of the capillary term is that of the divergence of the Korteweg
+ * tensor (Eq. (force2) prints it negative).  p: LBM_EOS_PAPER, the
+ * polynomial of Eq. (eos) (coexisting densities about 7.55 and 0.073), or
+ * LBM_EOS_IDEAL, p = rho c_s^2 (phi = 0).  g: a uniform acceleration.
+ *
+ * Scope: every face periodic, no immersed bodies; FP32 storage (D2Q9 and
+ * D3Q27) or FP64 storage (D2Q9).  The lattice must be created with
+ * lbm_config.multiphase = 1 (the workspace then holds one density and one
+ * (phi, lap rho) pair per node in the compute precision).
+ *
+ * lbm_set_multiphase switches the context to the multiphase step (params
+ * copied; NULL switches back to the single-phase step).  LBM_EINVAL for a
+ * context outside the scope, kappa < 0 or an unknown eos; LBM_ESTATE when
+ * the context was created without multiphase = 1.
+ * While the model is on, lbm_get_macros / lbm_get_macros_f32 return the
+ * fluid velocity (j - F/2) / rho of the stored post-collision state, F the
+ * force of the step that produced it (F = 0 before the first step and after
+ * lbm_init_equilibrium / lbm_set_populations).
+ * lbm_get_force_field writes that force, F[3][nz][ny][nx] (FP64; z
+ * components zero for D2Q9; host or device memory).  Synchronises. */
+enum { LBM_EOS_PAPER = 0, LBM_EOS_IDEAL = 1 };
+typedef struct {
+  double kappa;   /* capillary coefficient of Eq. (Korteweg), >= 0 */
+  int eos;        /* LBM_EOS_* */
+  double g[3];    /* uniform acceleration (lattice units) */
+} lbm_multiphase_params;
+lbm_status lbm_set_multiphase(lbm_ctx *ctx, const lbm_multiphase_params *params);
+lbm_status lbm_get_force_field(lbm_ctx *ctx, double *F);
 
 /* Wait for the stream and report LBM_EUNSTABLE if any sweep since the last
  * check met a non-finite or non-positive density, LBM_ETIMEOUT if a bounded

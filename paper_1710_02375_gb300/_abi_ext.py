@@ -48,8 +48,20 @@ class mlp_config(ctypes.Structure):
     ]
 
 
+class lbm_multiphase_params(ctypes.Structure):
+    _fields_ = [
+        ("kappa", ctypes.c_double),
+        ("eos", ctypes.c_int),
+        ("g", ctypes.c_double * 3),
+    ]
+
+
 def declare(L):
     vp, i32, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    L.lbm_set_multiphase.argtypes = [vp, ctypes.POINTER(lbm_multiphase_params)]
+    L.lbm_set_multiphase.restype = ctypes.c_int
+    L.lbm_get_force_field.argtypes = [vp, vp]
+    L.lbm_get_force_field.restype = ctypes.c_int
     L.fem_beam_workspace_size.argtypes = [ctypes.POINTER(fem_beam_config), ctypes.POINTER(sz)]
     L.fem_beam_create.argtypes = [ctypes.POINTER(fem_beam_config), vp, sz, ctypes.POINTER(vp)]
     L.fem_beam_step.argtypes = [vp, vp]

@@ -12,6 +12,9 @@
 //   gamma = 1/beta - (2 - 1/beta) <ds|dh>/<dh|dh>, <X|Y> = sum X Y / feq
 //                                                   -- Eq. (gamma_min_approx)
 //   f' = f - beta (2 ds + gamma dh)                 -- Eqs. (f_equations), (f_mirr)
+// Forced form (multiphase model, Eq. (force_mp)): with a velocity increment
+// du = F / rho the entropic products take the shifted metric 1 / feq(rho,
+// u + du) and the relaxed state gains F_i = feq(rho, u + du) - feq(rho, u).
 // gamma = 2 (LBGK, omega = 2 beta) when <dh|dh> <= 1e-30 or BGK is requested;
 // otherwise gamma is held in [0, 2/beta], where (1 - beta gamma) dh, the
 // post-collision higher-order part, does not grow.
@@ -147,8 +150,13 @@ __device__ __forceinline__ f2 vgamma(f2 sh, f2 hh, float ib, bool bgk) {
 // CONSERVE: remove the FP32 rounding residue of mass and momentum from the
 // non-equilibrium part (used with FP32 storage, where it would otherwise be
 // the dominant error; with 16-bit storage the storage rounding dominates).
-template <class L, bool CONSERVE, class V>
-__device__ __forceinline__ V collide_v(V (&g)[L::Q], typename ScalarOf<V>::type beta, bool bgk) {
+// FORCED: the forced form with velocity increment (dux, duy, duz), on
+// deviations g_i = f_i - W_i ref from a reference density ref of the node
+// (the moments and the update are unchanged in that form: only rho = ref +
+// sum g_i); the unforced instantiations compile without any of its code.
+template <class L, bool CONSERVE, class V, bool FORCED = false>
+__device__ __forceinline__ V collide_v(V (&g)[L::Q], typename ScalarOf<V>::type beta, bool bgk,
+                                       V dux = V(), V duy = V(), V duz = V(), V ref = V()) {
   using SC = typename ScalarOf<V>::type;
   constexpr int Q = L::Q;
   constexpr int NR = Q / 3;  // rows of three x-neighbours (cy, cz)
@@ -185,13 +193,22 @@ __device__ __forceinline__ V collide_v(V (&g)[L::Q], typename ScalarOf<V>::type 
   const V jy = vsub(yp, ym), pyy = vadd(yp, ym);
   const V jz = vsub(zp, zm), pzz = vadd(zp, zm);
 
-  const V rho = vadd(vc<V>(1.0f), drho);
+  V rho;
+  if constexpr (FORCED) rho = vadd(ref, drho);
+  else rho = vadd(vc<V>(1.0f), drho);
   const V irho = vdivf(vc<V>(1.0f), rho);
   const V ux = vmul(jx, irho), uy = vmul(jy, irho), uz = vmul(jz, irho);
 
   const AxisEqT<V> ax = axis_eq(ux), ay = axis_eq(uy);
   AxisEqT<V> az;
   if (L::D == 3) az = axis_eq(uz);
+  // equilibrium factors at the shifted velocity u + du (forced form)
+  AxisEqT<V> sx, sy, sz;
+  if constexpr (FORCED) {
+    sx = axis_eq(vadd(ux, dux));
+    sy = axis_eq(vadd(uy, duy));
+    if (L::D == 3) sz = axis_eq(vadd(uz, duz));
+  }
 
   // ---- shear part of f - feq from the deviatoric non-equilibrium stress
   // dPi_aa = P_aa - (drho + 2 rho d_a)/3, dPi_ab = P_ab - rho u_a u_b
@@ -239,7 +256,9 @@ __device__ __forceinline__ V collide_v(V (&g)[L::Q], typename ScalarOf<V>::type 
     const int a = k2 % 3, b = k2 / 3;  // a = cx + 1, b = cy + 1
     const V exy = vfma(ay.e[b], px1[a], ax.e[a]);
     const V qxy = vadd(vc<V>(1.0f), exy);
-    const V mxy = vmul(ax.r[a], ay.r[b]);
+    V mxy;
+    if constexpr (FORCED) mxy = vmul(sx.r[a], sy.r[b]);
+    else mxy = vmul(ax.r[a], ay.r[b]);
 #pragma unroll
     for (int zc = 0; zc < (L::D == 3 ? 3 : 1); ++zc) {
       const int i = (L::D == 3 ? 9 * zc : 0) + k2;
@@ -247,7 +266,8 @@ __device__ __forceinline__ V collide_v(V (&g)[L::Q], typename ScalarOf<V>::type 
       V e = exy, m = mxy;
       if (L::D == 3) {
         e = vfma(az.e[cz + 1], qxy, e);
-        m = vmul(m, az.r[cz + 1]);
+        if constexpr (FORCED) m = vmul(m, sz.r[cz + 1]);
+        else m = vmul(m, az.r[cz + 1]);
       }
       // feq_i - W_i = W_i (drho + rho e_i);  df_i = g_i - (feq_i - W_i)
       const V d = vfma(vc<V>(-weight<L>(i)), vfma(rho, e, drho), g[i]);
@@ -303,6 +323,11 @@ __device__ __forceinline__ V collide_v(V (&g)[L::Q], typename ScalarOf<V>::type 
     const int a = k2 % 3, b = k2 / 3;
     const V exy = vfma(ay.e[b], px1[a], ax.e[a]);
     const V qxy = vadd(vc<V>(1.0f), exy);
+    V sxy = zero, sqxy = zero;  // shifted x-y factors (forced form)
+    if constexpr (FORCED) {
+      sxy = vfma(sy.e[b], vadd(vc<V>(1.0f), sx.e[a]), sx.e[a]);
+      sqxy = vadd(vc<V>(1.0f), sxy);
+    }
 #pragma unroll
     for (int zc = 0; zc < (L::D == 3 ? 3 : 1); ++zc) {
       const int i = (L::D == 3 ? 9 * zc : 0) + k2;
@@ -331,6 +356,12 @@ __device__ __forceinline__ V collide_v(V (&g)[L::Q], typename ScalarOf<V>::type 
         sds = vfma(vc<V>(-weight<L>(i)), t, sds);
       }
       g[i] = vsub(g[i], vfma(bg, d, sds));
+      if constexpr (FORCED) {
+        // F_i = feq(rho, u + du) - feq(rho, u) = W_i rho (e_i(u + du) - e_i(u))
+        V es = sxy;
+        if (L::D == 3) es = vfma(sz.e[cz + 1], sqxy, es);
+        g[i] = vfma(vc<V>(weight<L>(i)), vmul(rho, vsub(es, e)), g[i]);
+      }
     }
   }
   return rho;

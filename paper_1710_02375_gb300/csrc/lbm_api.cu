@@ -32,6 +32,8 @@ struct Layout {
   size_t sx, sv, se, seb, links, bnodes, fresh, counters, vforce, bforce, inlet[6];
   size_t sigma, orient, tvforce, tbforce;  // stress-traction output
   size_t sbox;                             // bounding box of the surface (6 floats)
+  size_t mp_rho[2], mp_pl;                 // multiphase fields (0: not reserved)
+  size_t mp_ctl, mp_partial;               // momentum-controller state, CTA partials
   int nface, bcap, inlet_n[6];
   size_t total;
 };
@@ -88,6 +90,19 @@ Layout make_layout(const lbm_config &c) {
   L.tvforce = off; off += align_up(sizeof(double) * 3 * (size_t)std::max(nv, 1));
   L.tbforce = off; off += align_up(sizeof(double) * 3 * kMaxBodies);
   L.sbox = off; off += align_up(sizeof(float) * 8);
+  L.mp_rho[0] = L.mp_rho[1] = L.mp_pl = L.mp_ctl = L.mp_partial = 0;
+  if (c.multiphase) {
+    // two density buffers (the reference of the stored state, the density
+    // of the step being computed) and (phi, lap rho) per stored node, in the
+    // compute precision
+    const size_t cb = c.storage == LBM_STORE_F64 ? 8 : 4;
+    L.mp_rho[0] = off; off += align_up(cb * (size_t)g.N);
+    L.mp_rho[1] = off; off += align_up(cb * (size_t)g.N);
+    L.mp_pl = off; off += align_up(2 * cb * (size_t)g.N);
+    L.mp_ctl = off; off += align_up(sizeof(double) * kMpControl);
+    L.mp_partial = off;
+    off += align_up(sizeof(double) * kMpPartialDoubles * (size_t)mp_grid(c.nx, c.ny, c.nz).blocks);
+  }
   for (int fc = 0; fc < 6; ++fc) {
     L.inlet_n[fc] = 0;
     L.inlet[fc] = 0;
@@ -129,6 +144,9 @@ const char *validate(const lbm_config *c) {
   if (n > (1LL << 31)) return "lattice too large";
   if (c->max_links < 0 || c->max_vertices < 0 || c->max_elements < 0) return "negative capacity";
   if (c->inlet_ramp_steps < 0) return "negative inlet ramp";
+  if (c->multiphase != 0 && c->multiphase != 1) return "multiphase must be 0 or 1";
+  if (c->multiphase && c->storage != LBM_STORE_F32 && c->storage != LBM_STORE_F64)
+    return "the multiphase model needs FP32 or FP64 storage";
   const int nz_ax = c->lattice == LBM_D2Q9 ? 2 : 3;
   const int nn[3] = {c->nx, c->ny, c->nz};
   for (int a = 0; a < nz_ax; ++a)
@@ -167,6 +185,11 @@ struct lbm_ctx {
   int shell_v0 = 0;
   mlp_ctx *mlp = nullptr;    // structural-step surrogate (Newton initial guess)
   bool traction_on = false;  // stress-traction output each step
+  bool mp_on = false;        // multiphase step (lbm_set_multiphase)
+  MpParams mp{};
+  int mp_cur = 0;            // density buffer holding the reference of the stored state
+  bool mp_have_force = false;  // a multiphase step has produced the stored state
+  int graph_cur = 0, graph_mp_cur = 0;  // buffer parities the graph was captured at
   double accept_tol = 0.0;
   // CUDA graph of graph_n steps (replayed by lbm_step_graph)
   cudaGraphExec_t gexec = nullptr;
@@ -348,9 +371,14 @@ static bool on_ctx_device(const lbm_ctx *ctx) {
   return dev == ctx->device;
 }
 
+static lbm_status mp_adopt_state(lbm_ctx *ctx);
+static const void *mp_ref(const lbm_ctx *ctx);
+static const double *mp_mean_used(const lbm_ctx *ctx);
+
 lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const double *rho, const double *u) {
   GUARD();
   if (!rho || !u) return fail(ctx, LBM_EINVAL, "lbm_init_equilibrium: NULL argument");
+  if (lbm_status st = mp_adopt_state(ctx); st != LBM_OK) return st;
   const int dim = ctx->Q == 9 ? 2 : 3;
   const long long n = (long long)ctx->g.nx * ctx->g.ny * ctx->g.nz;
   const bool dev = is_device_ptr(rho) && is_device_ptr(u);
@@ -385,6 +413,7 @@ lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const double *rho, const double *u
 lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f) {
   GUARD();
   if (!f) return fail(ctx, LBM_EINVAL, "lbm_set_populations: NULL argument");
+  if (lbm_status st = mp_adopt_state(ctx); st != LBM_OK) return st;
   const long long n = (long long)ctx->g.nx * ctx->g.ny * ctx->g.nz;
   if (is_device_ptr(f)) {
     for (int i = 0; i < ctx->Q; ++i)
@@ -410,6 +439,30 @@ lbm_status lbm_get_populations(lbm_ctx *ctx, double *f) {
   GUARD();
   if (!f) return fail(ctx, LBM_EINVAL, "lbm_get_populations: NULL argument");
   const long long n = (long long)ctx->g.nx * ctx->g.ny * ctx->g.nz;
+  if (ctx->mp_on) {
+    // populations stored relative to the local reference density
+    const void *mpl = ctx->ws + ctx->lay.mp_pl;
+    if (is_device_ptr(f)) {
+      CK(launch_mp_read(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur], mp_ref(ctx), mpl,
+                        ctx->mp, 0, mp_mean_used(ctx), 0, n, n, nullptr, nullptr, nullptr,
+                        nullptr, nullptr, f, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      return LBM_OK;
+    }
+    const long long chunk = (long long)(kStageBytes / (sizeof(double) * ctx->Q));
+    double *s = (double *)ctx->stage;
+    for (long long b = 0; b < n; b += chunk) {
+      const long long cnt = (n - b < chunk) ? n - b : chunk;
+      CK(launch_mp_read(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur], mp_ref(ctx), mpl,
+                        ctx->mp, 0, mp_mean_used(ctx), b, cnt, cnt, nullptr, nullptr, nullptr,
+                        nullptr, nullptr, s, ctx->stream));
+      for (int i = 0; i < ctx->Q; ++i)
+        CK(cudaMemcpyAsync(f + i * n + b, s + i * cnt, cnt * sizeof(double),
+                           cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return LBM_OK;
+  }
   if (is_device_ptr(f)) {
     for (int i = 0; i < ctx->Q; ++i)
       CK(launch_get_pop(ctx->Q, ctx->cfg.storage, ctx->g, i, f + i * n, 0, n, ctx->f[ctx->cur],
@@ -434,6 +487,91 @@ lbm_status lbm_get_populations(lbm_ctx *ctx, double *f) {
 static lbm_status run_geometry(lbm_ctx *ctx, int track_fresh);
 static SurfaceDev surface_dev(lbm_ctx *ctx);
 
+// A state written from outside (single-phase convention, f_i - W_i) becomes
+// the stored state of the multiphase step: reference 1 everywhere, no force
+// yet applied.
+static lbm_status mp_adopt_state(lbm_ctx *ctx) {
+  if (!ctx->mp_on) return LBM_OK;
+  CK(launch_mp_rebase(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur],
+                      ctx->ws + ctx->lay.mp_rho[ctx->mp_cur], 1.0, 0, ctx->stream));
+  CK(cudaMemsetAsync(ctx->ws + ctx->lay.mp_ctl, 0, sizeof(double) * kMpControl, ctx->stream));
+  ctx->mp_have_force = false;
+  return LBM_OK;
+}
+
+static const void *mp_ref(const lbm_ctx *ctx) { return ctx->ws + ctx->lay.mp_rho[ctx->mp_cur]; }
+static double *mp_ctl(const lbm_ctx *ctx) { return (double *)(ctx->ws + ctx->lay.mp_ctl); }
+// the controller state, which holds the correction the last step used
+static const double *mp_mean_used(const lbm_ctx *ctx) { return mp_ctl(ctx); }
+
+lbm_status lbm_set_multiphase(lbm_ctx *ctx, const lbm_multiphase_params *params) {
+  GUARD();
+  if (!params) {
+    if (ctx->mp_on)  // back to the single-phase convention f_i - W_i
+      CK(launch_mp_rebase(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur],
+                          ctx->ws + ctx->lay.mp_rho[ctx->mp_cur], 1.0, 1, ctx->stream));
+    ctx->mp_on = false;
+    ctx->graph_dirty = true;
+    return LBM_OK;
+  }
+  if (!ctx->cfg.multiphase)
+    return fail(ctx, LBM_ESTATE, "lbm_set_multiphase: context created without multiphase = 1");
+  for (int fc = 0; fc < 6; ++fc)
+    if (ctx->cfg.bc[fc] != LBM_BC_PERIODIC)
+      return fail(ctx, LBM_EINVAL, "lbm_set_multiphase: every face must be periodic");
+  if (ctx->nbodies > 0 || ctx->fem || ctx->shell)
+    return fail(ctx, LBM_EINVAL, "lbm_set_multiphase: immersed bodies are not supported");
+  if (ctx->cfg.storage != LBM_STORE_F32 && ctx->cfg.storage != LBM_STORE_F64)
+    return fail(ctx, LBM_EINVAL, "lbm_set_multiphase: FP32 or FP64 storage only");
+  if (!(params->kappa >= 0.0) || !std::isfinite(params->kappa))
+    return fail(ctx, LBM_EINVAL, "lbm_set_multiphase: kappa must be finite and >= 0");
+  if (params->eos != LBM_EOS_PAPER && params->eos != LBM_EOS_IDEAL)
+    return fail(ctx, LBM_EINVAL, "lbm_set_multiphase: unknown eos %d", params->eos);
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(params->g[a]))
+      return fail(ctx, LBM_EINVAL, "lbm_set_multiphase: non-finite acceleration");
+  ctx->mp.kappa = params->kappa;
+  ctx->mp.eos = params->eos == LBM_EOS_IDEAL ? MP_EOS_IDEAL : MP_EOS_PAPER;
+  for (int a = 0; a < 3; ++a) ctx->mp.g[a] = (a < 2 || ctx->Q == 27) ? params->g[a] : 0.0;
+  if (!ctx->mp_on) {
+    ctx->mp_on = true;
+    lbm_status st = mp_adopt_state(ctx);
+    if (st != LBM_OK) return st;
+  }
+  ctx->graph_dirty = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_get_force_field(lbm_ctx *ctx, double *F) {
+  GUARD();
+  if (!F) return fail(ctx, LBM_EINVAL, "lbm_get_force_field: NULL argument");
+  if (!ctx->mp_on) return fail(ctx, LBM_ESTATE, "lbm_get_force_field: the multiphase model is off");
+  const long long n = (long long)ctx->g.nx * ctx->g.ny * ctx->g.nz;
+  const void *mpl = ctx->ws + ctx->lay.mp_pl;
+  const int hf = ctx->mp_have_force;
+  double *mf = is_device_ptr(F) ? F : (double *)mapped_host_ptr(F);
+  if (mf) {
+    CK(launch_mp_read(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur], mp_ref(ctx), mpl, ctx->mp,
+                      hf, mp_mean_used(ctx), 0, n, n, mf, nullptr, nullptr, nullptr, nullptr,
+                      nullptr, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+  }
+  const long long chunk = (long long)(kStageBytes / (sizeof(double) * 3));
+  double *s = (double *)ctx->stage;
+  for (long long b = 0; b < n; b += chunk) {
+    const long long cnt = (n - b < chunk) ? n - b : chunk;
+    CK(launch_mp_read(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur], mp_ref(ctx), mpl, ctx->mp,
+                      hf, mp_mean_used(ctx), b, cnt, cnt, s, nullptr, nullptr, nullptr, nullptr,
+                      nullptr, ctx->stream));
+    for (int a = 0; a < 3; ++a)
+      CK(cudaMemcpyAsync(F + a * n + b, s + a * cnt, cnt * sizeof(double), cudaMemcpyDeviceToHost,
+                         ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  return LBM_OK;
+}
+
 lbm_status lbm_step(lbm_ctx *ctx, int n) {
   GUARD();
   if (n < 0) return fail(ctx, LBM_EINVAL, "lbm_step: n < 0");
@@ -457,9 +595,18 @@ lbm_status lbm_step(lbm_ctx *ctx, int n) {
                      ctx->nbodies, ctx->stream));
       if (ctx->bp.ramp_steps > 0) CK(launch_step_counter(ctx->counters + 3, ctx->stream));
     }
-    CK(launch_sweep(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur], ctx->f[1 - ctx->cur],
-                    ctx->has_solid ? ctx->flags : nullptr, beta, bgk, ctx->err, ctx->stream,
-                    ctx->sweep_variant));
+    if (ctx->mp_on) {
+      CK(launch_mp_step(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur], ctx->f[1 - ctx->cur],
+                        ctx->ws + ctx->lay.mp_rho[ctx->mp_cur],
+                        ctx->ws + ctx->lay.mp_rho[1 - ctx->mp_cur], ctx->ws + ctx->lay.mp_pl,
+                        mp_ctl(ctx), (double *)(ctx->ws + ctx->lay.mp_partial), ctx->mp, beta,
+                        bgk, ctx->err, ctx->stream));
+      ctx->mp_cur = 1 - ctx->mp_cur;
+      ctx->mp_have_force = true;
+    } else
+      CK(launch_sweep(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur], ctx->f[1 - ctx->cur],
+                      ctx->has_solid ? ctx->flags : nullptr, beta, bgk, ctx->err, ctx->stream,
+                      ctx->sweep_variant));
     if (ctx->traction_on && ctx->nbodies > 0)
       CK(launch_traction(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur],
                          (const BNode *)(ctx->ws + ctx->lay.bnodes) + ctx->nface, ctx->counters,
@@ -541,6 +688,8 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, int nbodies, const double *verts, int 
                             const int32_t *elems, int ne, const int32_t *elem_body,
                             const double *vert_vel, double band_margin) {
   GUARD();
+  if (ctx->mp_on)
+    return fail(ctx, LBM_EINVAL, "lbm_set_geometry: the multiphase model runs on periodic lattices without bodies");
   const int dim = ctx->Q == 9 ? 2 : 3;
   if (nbodies < 1 || nbodies > kMaxBodies || nv < dim || ne < 1 || !verts || !elems ||
       !elem_body || !(band_margin >= 0.0))
@@ -831,17 +980,22 @@ lbm_status lbm_step_graph(lbm_ctx *ctx, int n, int repeats) {
   GUARD();
   if (n <= 0 || (n & 1) || repeats < 0)
     return fail(ctx, LBM_EINVAL, "lbm_step_graph: n must be even and positive, repeats >= 0");
-  if (ctx->graph_dirty || ctx->graph_n != n || !ctx->gexec) {
+  if (ctx->graph_dirty || ctx->graph_n != n || !ctx->gexec || ctx->cur != ctx->graph_cur ||
+      ctx->mp_cur != ctx->graph_mp_cur) {
     if (ctx->gexec) {
       cudaGraphExecDestroy(ctx->gexec);
       ctx->gexec = nullptr;
     }
     CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed));
-    const int cur0 = ctx->cur;
+    const int cur0 = ctx->cur, mp_cur0 = ctx->mp_cur;
     lbm_status st = lbm_step(ctx, n);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
-    ctx->cur = cur0;  // an even number of steps returns to the same buffer
+    // an even number of steps returns to the same buffers
+    ctx->cur = cur0;
+    ctx->mp_cur = mp_cur0;
+    ctx->graph_cur = cur0;
+    ctx->graph_mp_cur = mp_cur0;
     if (st != LBM_OK) {
       if (graph) cudaGraphDestroy(graph);
       return st;
@@ -854,6 +1008,7 @@ lbm_status lbm_step_graph(lbm_ctx *ctx, int n, int repeats) {
     ctx->graph_dirty = false;
   }
   for (int r = 0; r < repeats; ++r) CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
+  if (repeats > 0 && ctx->mp_on) ctx->mp_have_force = true;
   return LBM_OK;
 }
 
@@ -880,6 +1035,21 @@ lbm_status lbm_check(lbm_ctx *ctx) {
   return LBM_OK;
 }
 
+// Density and velocity of the stored state for interior nodes [begin, begin
+// + count): the single-phase read-out, or in the multiphase model the
+// density R + sum g_i and the fluid velocity (j - F/2) / rho.
+static cudaError_t read_macros(lbm_ctx *ctx, const uint8_t *fl, double *rho, double *u,
+                               long long ustride, long long begin, long long count,
+                               float *rho32 = nullptr, float *u32 = nullptr) {
+  if (ctx->mp_on)
+    return launch_mp_read(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur], mp_ref(ctx),
+                          ctx->ws + ctx->lay.mp_pl, ctx->mp, ctx->mp_have_force,
+                          mp_mean_used(ctx), begin, count, ustride, nullptr, rho, u, rho32, u32,
+                          nullptr, ctx->stream);
+  return launch_macros(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur], fl, rho, u, ustride,
+                       begin, count, ctx->stream, rho32, u32);
+}
+
 lbm_status lbm_get_macros_f32(lbm_ctx *ctx, float *rho, float *u) {
   GUARD();
   if (!rho || !u) return fail(ctx, LBM_EINVAL, "lbm_get_macros_f32: NULL argument");
@@ -896,8 +1066,7 @@ lbm_status lbm_get_macros_f32(lbm_ctx *ctx, float *rho, float *u) {
   }
   if (dr && du) {
     // device or page-locked host arrays: written in place
-    CK(launch_macros(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur], fl, nullptr, nullptr, n,
-                     0, n, ctx->stream, dr, du));
+    CK(read_macros(ctx, fl, nullptr, nullptr, n, 0, n, dr, du));
     CK(cudaStreamSynchronize(ctx->stream));
     return LBM_OK;
   }
@@ -905,8 +1074,7 @@ lbm_status lbm_get_macros_f32(lbm_ctx *ctx, float *rho, float *u) {
   float *s = (float *)ctx->stage;
   for (long long b = 0; b < n; b += chunk) {
     const long long cnt = (n - b < chunk) ? n - b : chunk;
-    CK(launch_macros(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur], fl, nullptr, nullptr, cnt,
-                     b, cnt, ctx->stream, s, s + cnt));
+    CK(read_macros(ctx, fl, nullptr, nullptr, cnt, b, cnt, s, s + cnt));
     CK(cudaMemcpyAsync(rho + b, s, cnt * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
     for (int a = 0; a < dim; ++a)
       CK(cudaMemcpyAsync(u + a * n + b, s + (1 + a) * cnt, cnt * sizeof(float),
@@ -923,16 +1091,14 @@ lbm_status lbm_get_macros(lbm_ctx *ctx, double *rho, double *u) {
   const long long n = (long long)ctx->g.nx * ctx->g.ny * ctx->g.nz;
   const uint8_t *fl = ctx->has_solid ? ctx->flags : nullptr;
   if (is_device_ptr(rho) && is_device_ptr(u)) {
-    CK(launch_macros(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur], fl, rho, u, n, 0, n,
-                     ctx->stream));
+    CK(read_macros(ctx, fl, rho, u, n, 0, n));
     CK(cudaStreamSynchronize(ctx->stream));
     return LBM_OK;
   }
   double *mr = (double *)mapped_host_ptr(rho), *mu = (double *)mapped_host_ptr(u);
   if (mr && mu) {
     // page-locked host arrays: the kernel writes them in place (no staging)
-    CK(launch_macros(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur], fl, mr, mu, n, 0, n,
-                     ctx->stream));
+    CK(read_macros(ctx, fl, mr, mu, n, 0, n));
     CK(cudaStreamSynchronize(ctx->stream));
     return LBM_OK;
   }
@@ -940,8 +1106,7 @@ lbm_status lbm_get_macros(lbm_ctx *ctx, double *rho, double *u) {
   double *s = (double *)ctx->stage;
   for (long long b = 0; b < n; b += chunk) {
     const long long cnt = (n - b < chunk) ? n - b : chunk;
-    CK(launch_macros(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur], fl, s, s + cnt, cnt, b,
-                     cnt, ctx->stream));
+    CK(read_macros(ctx, fl, s, s + cnt, cnt, b, cnt));
     CK(cudaMemcpyAsync(rho + b, s, cnt * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     for (int a = 0; a < dim; ++a)
       CK(cudaMemcpyAsync(u + a * n + b, s + (1 + a) * cnt, cnt * sizeof(double),
@@ -1149,6 +1314,11 @@ lbm_status lbm_batch_create(lbm_ctx *const *ctxs, int n, void *workspace, size_t
       return LBM_EINVAL;
     }
     if (ctxs[i]->sweep_variant == SWEEP_ROWS) return LBM_EINVAL;
+    if (ctxs[i]->mp_on) {
+      snprintf(g_create_msg, sizeof(g_create_msg),
+               "lbm_batch_create: multiphase lattices are stepped one by one");
+      return LBM_EINVAL;
+    }
   }
   lbm_batch *b = new (std::nothrow) lbm_batch();
   if (!b) return LBM_ENOMEM;

@@ -62,6 +62,54 @@ cudaError_t launch_macros(int Q, int storage, const Grid &g, const void *f, cons
                           long long count, cudaStream_t s, float *rho32 = nullptr,
                           float *u32 = nullptr);
 
+// ---- multiphase model (periodic lattices; FP32 storage, or FP64 for D2Q9)
+enum { MP_EOS_PAPER = 0, MP_EOS_IDEAL = 1 };
+struct MpParams {
+  double kappa;  // capillary coefficient
+  double g[3];   // uniform acceleration (F gains rho g)
+  int eos;       // MP_EOS_*
+};
+// One multiphase step fin -> fout: density pass (rho, phi), Laplacian pass
+// (lap rho), forced sweep.  Populations are stored as f_i - W_i R(x), R the
+// node's density of the step that wrote them: fin relative to rref, fout
+// relative to the new densities rho.  rref, rho: [N] compute type; pl: [N]
+// (phi, lap) pairs.
+// ctl: momentum-controller state (kMpControl doubles, zero to start):
+// [0..2] the correcting acceleration of the next step (force rho a_c
+// subtracted per node), [3..5] the one the last step used, [6..8] the last momentum, [9] set once recorded; partial:
+// kMpPartialDoubles per CTA of mp_grid.
+constexpr int kMpControl = 10;
+constexpr int kMpPartialDoubles = 4;
+cudaError_t launch_mp_step(int Q, int storage, const Grid &g, const void *fin, void *fout,
+                           const void *rref, void *rho, void *pl, double *ctl, double *partial,
+                           const MpParams &mp, double beta, int bgk, int *err, cudaStream_t s);
+// CTA shape and count of the multiphase kernels over an nx * ny * nz lattice.
+struct MpGrid {
+  int bx, by;
+  long long blocks;
+};
+inline MpGrid mp_grid(int nx, int ny, int nz) {
+  MpGrid m;
+  m.bx = nx >= 128 ? 128 : 32;
+  m.by = nx >= 128 ? 1 : 4;
+  m.blocks = (long long)((nx + m.bx - 1) / m.bx) * ((ny + m.by - 1) / m.by) * nz;
+  return m;
+}
+// Read-out of a stored state f relative to rref for interior nodes [begin,
+// begin + count): the force of the last step F[3][stride] (when F given; zero
+// when !have_force; mean: the controller state ctl, whose correction of the
+// last step is subtracted), density and fluid velocity (j - F/2) / rho (FP64 rho_out
+// / u, or FP32 rho32 / u32), absolute populations fabs[Q][stride] (FP64).
+cudaError_t launch_mp_read(int Q, int storage, const Grid &g, const void *f, const void *rref,
+                           const void *pl, const MpParams &mp, int have_force,
+                           const double *mean, long long begin,
+                           long long count, long long stride, double *F, double *rho_out,
+                           double *u, float *rho32, float *u32, double *fabs, cudaStream_t s);
+// Change the reference of a stored state to the constant Rnew (populations
+// shifted when shift_populations, rref set to Rnew).
+cudaError_t launch_mp_rebase(int Q, int storage, const Grid &g, void *f, void *rref, double Rnew,
+                             int shift_populations, cudaStream_t s);
+
 }  // namespace kbc
 
 namespace kbc {

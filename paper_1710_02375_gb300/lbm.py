@@ -41,6 +41,7 @@ class lbm_config(ctypes.Structure):
         ("max_elements", ctypes.c_int),
         ("inlet_ramp_steps", ctypes.c_int),
         ("stream", ctypes.c_void_p),
+        ("multiphase", ctypes.c_int),
     ]
 
 
@@ -129,7 +130,7 @@ def _chk(ctx, st):
 
 def make_config(lattice, nx, ny, nz, beta, storage=LBM_STORE_F32, collision=LBM_COLLIDE_KBC,
                 bc=(0, 0, 0, 0, 0, 0), face_velocity=None, max_links=0, max_vertices=0,
-                max_elements=0, stream=None, inlet_ramp_steps=0) -> lbm_config:
+                max_elements=0, stream=None, inlet_ramp_steps=0, multiphase=False) -> lbm_config:
     c = lbm_config()
     c.lattice, c.nx, c.ny, c.nz = lattice, nx, ny, nz
     c.beta, c.storage, c.collision = beta, storage, collision
@@ -141,6 +142,7 @@ def make_config(lattice, nx, ny, nz, beta, storage=LBM_STORE_F32, collision=LBM_
     c.max_links, c.max_vertices, c.max_elements = max_links, max_vertices, max_elements
     c.inlet_ramp_steps = inlet_ramp_steps
     c.stream = stream
+    c.multiphase = int(bool(multiphase))
     return c
 
 
@@ -194,6 +196,26 @@ LBM_SWEEP_AUTO, LBM_SWEEP_DIRECT, LBM_SWEEP_ROWS, LBM_SWEEP_ASYNC, LBM_SWEEP_PAI
 
 def lbm_set_sweep_variant(ctx, variant: int):
     _chk(ctx, load().lbm_set_sweep_variant(ctx, int(variant)))
+
+
+LBM_EOS_PAPER, LBM_EOS_IDEAL = 0, 1
+
+
+def lbm_set_multiphase(ctx, kappa, eos=LBM_EOS_PAPER, g=(0.0, 0.0, 0.0)):
+    """Switch to the multiphase step (kappa None: back to single phase)."""
+    if kappa is None:
+        _chk(ctx, load().lbm_set_multiphase(ctx, None))
+        return
+    from ._abi_ext import lbm_multiphase_params
+    p = lbm_multiphase_params()
+    p.kappa, p.eos = float(kappa), int(eos)
+    for a in range(3):
+        p.g[a] = float(g[a]) if a < len(g) else 0.0
+    _chk(ctx, load().lbm_set_multiphase(ctx, ctypes.byref(p)))
+
+
+def lbm_get_force_field(ctx, F):
+    _chk(ctx, load().lbm_get_force_field(ctx, _ptr(F)))
 
 
 def lbm_set_inlet_profile(ctx, face, u):
@@ -274,7 +296,7 @@ class Lattice:
 
     def __init__(self, lattice, nx, ny, nz, beta, storage=LBM_STORE_F32, collision=LBM_COLLIDE_KBC,
                  bc=(0, 0, 0, 0, 0, 0), face_velocity=None, max_links=0, max_vertices=0,
-                 max_elements=0, stream=None, device="cuda", inlet_ramp_steps=0):
+                 max_elements=0, stream=None, device="cuda", inlet_ramp_steps=0, multiphase=False):
         import torch
 
         self.torch = torch
@@ -285,7 +307,8 @@ class Lattice:
         self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
         self.cfg = make_config(lattice, nx, ny, nz, beta, storage, collision, bc, face_velocity,
                                max_links, max_vertices, max_elements,
-                               stream=self.stream.cuda_stream, inlet_ramp_steps=inlet_ramp_steps)
+                               stream=self.stream.cuda_stream, inlet_ramp_steps=inlet_ramp_steps,
+                               multiphase=multiphase)
         nbytes = lbm_workspace_size(self.cfg)
         # 256-byte alignment: torch's caching allocator returns 512-byte aligned blocks
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
@@ -319,6 +342,15 @@ class Lattice:
         u = np.zeros((self.dim,) + self.shape)
         lbm_get_macros(self.ctx, rho, u)
         return rho, u
+
+    def set_multiphase(self, kappa, eos=LBM_EOS_PAPER, g=(0.0, 0.0, 0.0)):
+        lbm_set_multiphase(self.ctx, kappa, eos, g)
+
+    def force_field(self):
+        """Force F[3, nz, ny, nx] of the last multiphase step."""
+        F = np.zeros((3,) + self.shape)
+        lbm_get_force_field(self.ctx, F)
+        return F
 
     def set_sweep_variant(self, variant):
         lbm_set_sweep_variant(self.ctx, variant)
