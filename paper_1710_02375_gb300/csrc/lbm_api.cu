@@ -101,7 +101,7 @@ Layout make_layout(const lbm_config &c) {
     L.mp_pl = off; off += align_up(2 * cb * (size_t)g.N);
     L.mp_ctl = off; off += align_up(sizeof(double) * kMpControl);
     L.mp_partial = off;
-    off += align_up(sizeof(double) * kMpPartialDoubles * (size_t)mp_grid(c.nx, c.ny, c.nz).blocks);
+    off += align_up(mp_partial_bytes(c.nx, c.ny, c.nz));
   }
   for (int fc = 0; fc < 6; ++fc) {
     L.inlet_n[fc] = 0;
@@ -495,6 +495,8 @@ static lbm_status mp_adopt_state(lbm_ctx *ctx) {
   CK(launch_mp_rebase(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur],
                       ctx->ws + ctx->lay.mp_rho[ctx->mp_cur], 1.0, 0, ctx->stream));
   CK(cudaMemsetAsync(ctx->ws + ctx->lay.mp_ctl, 0, sizeof(double) * kMpControl, ctx->stream));
+  CK(cudaMemsetAsync(ctx->ws + ctx->lay.mp_partial, 0,
+                     mp_partial_bytes(ctx->g.nx, ctx->g.ny, ctx->g.nz), ctx->stream));
   ctx->mp_have_force = false;
   return LBM_OK;
 }

@@ -75,11 +75,14 @@ struct MpParams {
 // relative to the new densities rho.  rref, rho: [N] compute type; pl: [N]
 // (phi, lap) pairs.
 // ctl: momentum-controller state (kMpControl doubles, zero to start):
-// [0..2] the correcting acceleration of the next step (force rho a_c
-// subtracted per node), [3..5] the one the last step used, [6..8] the last momentum, [9] set once recorded; partial:
-// kMpPartialDoubles per CTA of mp_grid.
+// [0..2] the correcting acceleration a_c of the current step (force rho a_c
+// subtracted per node), [6..8] the momentum of the step before, [9] the
+// number of sweeps with partials (0, 1, 2); partial: kMpPartialDoubles per
+// CTA of mp_grid, then the same per group of kMpGroupCtas CTAs
+// (mp_partial_bytes).
 constexpr int kMpControl = 10;
 constexpr int kMpPartialDoubles = 4;
+constexpr int kMpGroupCtas = 128;
 cudaError_t launch_mp_step(int Q, int storage, const Grid &g, const void *fin, void *fout,
                            const void *rref, void *rho, void *pl, double *ctl, double *partial,
                            const MpParams &mp, double beta, int bgk, int *err, cudaStream_t s);
@@ -95,10 +98,15 @@ inline MpGrid mp_grid(int nx, int ny, int nz) {
   m.blocks = (long long)((nx + m.bx - 1) / m.bx) * ((ny + m.by - 1) / m.by) * nz;
   return m;
 }
+inline size_t mp_partial_bytes(int nx, int ny, int nz) {
+  const long long nb = mp_grid(nx, ny, nz).blocks;
+  const long long ng = (nb + kMpGroupCtas - 1) / kMpGroupCtas;
+  return sizeof(double) * kMpPartialDoubles * (size_t)(nb + ng);
+}
 // Read-out of a stored state f relative to rref for interior nodes [begin,
 // begin + count): the force of the last step F[3][stride] (when F given; zero
 // when !have_force; mean: the controller state ctl, whose correction of the
-// last step is subtracted), density and fluid velocity (j - F/2) / rho (FP64 rho_out
+// last step, ctl[0..2], is subtracted), density and fluid velocity (j - F/2) / rho (FP64 rho_out
 // / u, or FP32 rho32 / u32), absolute populations fabs[Q][stride] (FP64).
 cudaError_t launch_mp_read(int Q, int storage, const Grid &g, const void *f, const void *rref,
                            const void *pl, const MpParams &mp, int have_force,

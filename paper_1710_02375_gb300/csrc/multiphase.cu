@@ -80,132 +80,248 @@ __device__ __forceinline__ C mp_pressure(C r, int eos) {
   return p * r;
 }
 
+// Stored-space offsets of the three x columns, y rows and z planes around
+// stored node (X, Y, Z) (periodic wrap): node (X + cx, Y + cy, Z + cz) is at
+// xo[cx + 1] + yo[cy + 1] + zo[cz + 1].
+template <int D, typename IX>
+struct Nbhd {
+  IX xo[3], yo[3], zo[3];
+  __device__ __forceinline__ Nbhd(const Grid &g, int X, int Y, int Z) {
+    xo[0] = (IX)nbr(X, -1, g.NX);
+    xo[1] = (IX)X;
+    xo[2] = (IX)nbr(X, 1, g.NX);
+    yo[0] = (IX)nbr(Y, -1, g.NY) * (IX)g.pitch;
+    yo[1] = (IX)Y * (IX)g.pitch;
+    yo[2] = (IX)nbr(Y, 1, g.NY) * (IX)g.pitch;
+    const IX plane = (IX)g.NY * (IX)g.pitch;
+    zo[1] = (IX)Z * plane;
+    zo[0] = zo[2] = zo[1];
+    if (D == 3) {
+      zo[0] = (IX)nbr(Z, -1, g.NZ) * plane;
+      zo[2] = (IX)nbr(Z, 1, g.NZ) * plane;
+    }
+  }
+  __device__ __forceinline__ IX at(int cx, int cy, int cz) const {
+    return zo[cz + 1] + yo[cy + 1] + xo[cx + 1];
+  }
+};
+
+// ---------------------------------------------------------------- momentum controller
+// The sweep of step t leaves one (momentum, mass) partial per CTA; during
+// step t + 1 the first CTAs of the density pass sum them in groups of
+// kMpGroup (fixed order), and CTA 0 of the Laplacian pass sums the groups
+// and updates the controller before the sweep of step t + 1 reads it.
+// Stream order makes each stage's writes visible to the next: no atomics,
+// no fences, a deterministic result.
+// ctl: [0..2] the correcting acceleration a_c used by the current step,
+// [6..8] the momentum of the step before, [9] the number of sweeps whose
+// partials exist (0, 1, 2 = enough for an update).
+constexpr int kMpPartial = kMpPartialDoubles;  // per CTA: momentum (3), mass
+constexpr int kMpGroup = kMpGroupCtas;
+
+// Fixed-order sum of n values v[j * stride] (n <= kMpGroup) by the CTA into
+// red[q]; every thread of the CTA calls it.
+__device__ __forceinline__ void cta_sum_group(const double *__restrict__ src, long long stride,
+                                              int n, double (&red)[kMpPartial][kMpGroup],
+                                              double (&out)[kMpPartial]) {
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nthr = blockDim.x * blockDim.y;
+  for (int q = 0; q < kMpPartial; ++q)
+    for (int j = tid; j < kMpGroup; j += nthr) red[q][j] = j < n ? src[q * stride + j] : 0.0;
+  __syncthreads();
+  for (int h = kMpGroup / 2; h > 0; h >>= 1) {
+    for (int q = 0; q < kMpPartial; ++q)
+      for (int j = tid; j < h; j += nthr) red[q][j] += red[q][j + h];
+    __syncthreads();
+  }
+  for (int q = 0; q < kMpPartial; ++q) out[q] = red[q][0];
+}
+
+// Stage 1 (density pass, CTAs b < ngroups): group sums of the CTA partials.
+__device__ __forceinline__ void mp_stage1(const double *__restrict__ partial, long long nblk,
+                                          double *__restrict__ gpart, long long blk) {
+  const long long ngroups = (nblk + kMpGroup - 1) / kMpGroup;
+  if (blk >= ngroups) return;
+  __shared__ double red[kMpPartial][kMpGroup];
+  double out[kMpPartial];
+  const int n = (int)min((long long)kMpGroup, nblk - blk * kMpGroup);
+  cta_sum_group(partial + blk * kMpGroup, nblk, n, red, out);
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  if (tid < kMpPartial) gpart[tid * ngroups + blk] = out[tid];
+}
+
+// Stage 2 (Laplacian pass, CTA 0): total momentum and mass of the last
+// sweep, controller update a_c <- a_c + (P(t) - P(t-1) - M g) / M.
+__device__ __forceinline__ void mp_stage2(const double *__restrict__ gpart, long long nblk,
+                                          double gx, double gy, double gz, double *ctl,
+                                          long long blk) {
+  if (blk != 0) return;
+  const long long ngroups = (nblk + kMpGroup - 1) / kMpGroup;
+  __shared__ double red[kMpPartial][kMpGroup];
+  double tot[kMpPartial] = {0, 0, 0, 0};
+  for (long long g0 = 0; g0 < ngroups; g0 += kMpGroup) {
+    double part[kMpPartial];
+    cta_sum_group(gpart + g0, ngroups, (int)min((long long)kMpGroup, ngroups - g0), red, part);
+    for (int q = 0; q < kMpPartial; ++q) tot[q] += part[q];
+    __syncthreads();
+  }
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  if (tid == 0) {
+    const double have = ctl[9];
+    if (have >= 1.0) {
+      const double M = tot[3], gg[3] = {gx, gy, gz};
+      for (int a = 0; a < 3; ++a) {
+        if (have >= 2.0) ctl[a] += (tot[a] - ctl[6 + a] - M * gg[a]) / M;
+        ctl[6 + a] = tot[a];
+      }
+    }
+    ctl[9] = have >= 1.0 ? 2.0 : 1.0;
+  }
+}
+
 // ---------------------------------------------------------------- pass 1
-// Pulled populations of stored node (X, Y, Z) as deviations from W_i R0 (R0
-// the node's new reference; R0 = 0 gives absolute values), the sources
-// stored relative to their own references rref.
-template <int Q, int S>
+// Pulled populations of a node as deviations from W_i R0 (R0 the node's new
+// reference), the sources stored relative to their own references rref.
+template <int Q, int S, typename IX>
 __device__ __forceinline__ void mp_gather(const Grid &g, const typename Store<S>::T *__restrict__ fin,
-                                          const typename Store<S>::C *__restrict__ rref, int X,
-                                          int Y, int Z, typename Store<S>::C R0,
+                                          const typename Store<S>::C *__restrict__ rref,
+                                          const Nbhd<Lat<Q>::D, IX> &nb, typename Store<S>::C R0,
                                           typename Store<S>::C (&v)[Q]) {
   using L = Lat<Q>;
   using St = Store<S>;
   using C = typename St::C;
-  const int xs[3] = {nbr(X, 1, g.NX), X, nbr(X, -1, g.NX)};  // source x for cx = -1, 0, +1
-  const int ys[3] = {nbr(Y, 1, g.NY), Y, nbr(Y, -1, g.NY)};
-  int zs[3] = {Z, Z, Z};
-  if (L::D == 3) {
-    zs[0] = nbr(Z, 1, g.NZ);
-    zs[2] = nbr(Z, -1, g.NZ);
-  }
+  const IX N = (IX)g.N;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const long long src = ((long long)zs[L::cz(i) + 1] * g.NY + ys[L::cy(i) + 1]) * g.pitch +
-                          xs[L::cx(i) + 1];
+    const IX src = nb.at(-L::cx(i), -L::cy(i), -L::cz(i));
     const C w = (C)weight<L>(i);
-    v[i] = St::load(fin + ((long long)i * g.N + src), w) + w * (__ldg(rref + src) - R0);
+    v[i] = St::load(fin + ((IX)i * N + src), w) + w * (__ldg(rref + src) - R0);
   }
 }
 
-template <int Q, int S>
+template <int Q, int S, typename IX>
 __global__ void __launch_bounds__(128)
     k_mp_density(Grid g, const typename Store<S>::T *__restrict__ fin,
                  const typename Store<S>::C *__restrict__ rref,
                  typename Store<S>::C *__restrict__ rho,
                  typename Vec2<typename Store<S>::C>::T *__restrict__ pl, int eos,
+                 const double *__restrict__ partial, double *__restrict__ gpart, long long nblk,
                  int *__restrict__ err) {
   using C = typename Store<S>::C;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
-  if (x >= g.nx || y >= g.ny) return;
-  const int X = x + g.px, Y = y + g.py, Z = z + g.pz;
-  const long long k = sidx(g, X, Y, Z);
-  // deviations from the node's own old reference keep the sum small
-  const C R = rref[k];
-  C v[Q];
-  mp_gather<Q, S>(g, fin, rref, X, Y, Z, R, v);
-  C d = (C)0;
+  if (x < g.nx && y < g.ny) {
+    const Nbhd<Lat<Q>::D, IX> nb(g, x + g.px, y + g.py, z + g.pz);
+    const IX k = nb.at(0, 0, 0);
+    // deviations from the node's own old reference keep the sum small
+    const C R = rref[k];
+    C v[Q];
+    mp_gather<Q, S, IX>(g, fin, rref, nb, R, v);
+    C d = (C)0;
 #pragma unroll
-  for (int i = 0; i < Q; ++i) d += v[i];
-  const C r = R + d;
-  if (!(r > (C)0 && r < (C)1e30)) atomicOr(err, 1);
-  const C s = r * (C)(1.0 / 3.0) - mp_pressure(r, eos);
-  rho[k] = r;
-  pl[k].x = s > (C)0 ? sqrt(s) : (C)0;
+    for (int i = 0; i < Q; ++i) d += v[i];
+    const C r = R + d;
+    if (!(r > (C)0 && r < (C)1e30)) atomicOr(err, 1);
+    const C s = r * (C)(1.0 / 3.0) - mp_pressure(r, eos);
+    rho[k] = r;
+    pl[k].x = s > (C)0 ? sqrt(s) : (C)0;
+  }
+  mp_stage1(partial, nblk, gpart,
+            ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
 }
 
 // ---------------------------------------------------------------- pass 2
-template <int Q, class C>
+// lap rho = 6 (sum_i W_i rho(x + c_i) - rho(x)), the sum in tensor-product
+// form: rows of three x-neighbours weighted by the D1Q3 weights w(c), then
+// the rows by w(cy) w(cz).
+template <int Q, class C, typename IX>
+__device__ __forceinline__ void mp_lap_node(const Grid &g, const C *__restrict__ rho,
+                                            typename Vec2<C>::T *__restrict__ pl, int x, int y,
+                                            int z) {
+  using L = Lat<Q>;
+  const Nbhd<L::D, IX> nb(g, x + g.px, y + g.py, z + g.pz);
+  const IX k = nb.at(0, 0, 0);
+  const C r0 = rho[k];
+  C acc = (C)0;
+#pragma unroll
+  for (int cz = (L::D == 3 ? -1 : 0); cz <= (L::D == 3 ? 1 : 0); ++cz)
+#pragma unroll
+    for (int cy = -1; cy <= 1; ++cy) {
+      const IX row = nb.zo[cz + 1] + nb.yo[cy + 1];
+      const C sw = (C)(1.0 / 6.0) * (__ldg(rho + row + nb.xo[0]) + __ldg(rho + row + nb.xo[2])) +
+                   (C)(2.0 / 3.0) * __ldg(rho + row + nb.xo[1]);
+      acc += (C)((L::D == 3 ? w1d(cz) : 1.0) * w1d(cy)) * sw;
+    }
+  pl[k].y = (C)6 * (acc - r0);
+}
+
+template <int Q, class C, typename IX>
 __global__ void __launch_bounds__(128)
-    k_mp_lap(Grid g, const C *__restrict__ rho, typename Vec2<C>::T *__restrict__ pl) {
+    k_mp_lap(Grid g, const C *__restrict__ rho, typename Vec2<C>::T *__restrict__ pl,
+             const double *__restrict__ gpart, long long nblk, double gx, double gy, double gz,
+             double *__restrict__ ctl) {
   using L = Lat<Q>;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
-  if (x >= g.nx || y >= g.ny) return;
-  const int X = x + g.px, Y = y + g.py, Z = z + g.pz;
-  const int xs[3] = {nbr(X, -1, g.NX), X, nbr(X, 1, g.NX)};  // x + c for c = -1, 0, +1
-  const int ys[3] = {nbr(Y, -1, g.NY), Y, nbr(Y, 1, g.NY)};
-  int zs[3] = {Z, Z, Z};
-  if (L::D == 3) {
-    zs[0] = nbr(Z, -1, g.NZ);
-    zs[2] = nbr(Z, 1, g.NZ);
-  }
-  const long long k = sidx(g, X, Y, Z);
-  const C r0 = rho[k];
-  C acc = (C)0;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    if (L::cx(i) == 0 && L::cy(i) == 0 && L::cz(i) == 0) continue;
-    const long long kn = sidx(g, xs[L::cx(i) + 1], ys[L::cy(i) + 1], zs[L::cz(i) + 1]);
-    acc += (C)weight<L>(i) * (__ldg(rho + kn) - r0);
-  }
-  pl[k].y = (C)6 * acc;
+  if (x < g.nx && y < g.ny) mp_lap_node<Q, C, IX>(g, rho, pl, x, y, z);
+  mp_stage2(gpart, nblk, gx, gy, gz, ctl,
+            ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
 }
 
-// F at stored node (X, Y, Z) from the fields: 2 phi d(phi) + kappa rho
-// d(lap rho) + rho g.  The lattice gradient in tensor-product form:
-// d_x psi = 1/2 sum_{cy,cz} w(cy) w(cz) (psi(x+1, .) - psi(x-1, .)), w the
-// D1Q3 weights (3 W_i c_ix = c_ix w(cy) w(cz) / 2).
-template <int Q, class C>
-__device__ __forceinline__ void mp_force(const Grid &g, const C *__restrict__ rho,
-                                         const typename Vec2<C>::T *__restrict__ pl, C kappa,
-                                         C gx, C gy, C gz, int X, int Y, int Z, C &r, C (&F)[3]) {
+// F at a node from the fields: 2 phi d(phi) + kappa rho d(lap rho) + rho g.
+// The lattice gradient d_a psi = 3 sum_i W_i c_ia psi(x + c_i) in
+// tensor-product form (3 W_i c_ix = c_ix w(cy) w(cz) / 2):
+//   d_x psi = 1/2 sum_{cy,cz} w(cy) w(cz) (psi(+1, cy, cz) - psi(-1, cy, cz)),
+//   d_y psi = 1/2 sum_cz w(cz) (S(+1, cz) - S(-1, cz)),
+//   d_z psi = 1/2 sum_cy w(cy) (S(cy, +1) - S(cy, -1)),
+// S(cy, cz) = sum_cx w(cx) psi(cx, cy, cz) the weighted row sums.
+template <int Q, class C, typename IX>
+__device__ __forceinline__ void mp_force(const C *__restrict__ rho,
+                                         const typename Vec2<C>::T *__restrict__ pl,
+                                         const Nbhd<Lat<Q>::D, IX> &nb, C kappa, C gx, C gy,
+                                         C gz, C &r, C (&F)[3]) {
   using L = Lat<Q>;
-  const int xs[3] = {nbr(X, -1, g.NX), X, nbr(X, 1, g.NX)};
-  const int ys[3] = {nbr(Y, -1, g.NY), Y, nbr(Y, 1, g.NY)};
-  int zs[3] = {Z, Z, Z};
-  if (L::D == 3) {
-    zs[0] = nbr(Z, -1, g.NZ);
-    zs[2] = nbr(Z, 1, g.NZ);
-  }
-  C gp[3] = {(C)0, (C)0, (C)0}, gl[3] = {(C)0, (C)0, (C)0};
+  using C2 = typename Vec2<C>::T;
+  C dp[3] = {(C)0, (C)0, (C)0}, dl[3] = {(C)0, (C)0, (C)0};
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-    if (cx == 0 && cy == 0 && cz == 0) continue;
-    const long long kn = sidx(g, xs[cx + 1], ys[cy + 1], zs[cz + 1]);
-    const typename Vec2<C>::T q = __ldg(pl + kn);
-    const C w3 = (C)(3.0 * weight<L>(i));
-    if (cx) { gp[0] += (C)cx * w3 * q.x; gl[0] += (C)cx * w3 * q.y; }
-    if (cy) { gp[1] += (C)cy * w3 * q.x; gl[1] += (C)cy * w3 * q.y; }
-    if (cz) { gp[2] += (C)cz * w3 * q.x; gl[2] += (C)cz * w3 * q.y; }
-  }
-  const long long k = sidx(g, X, Y, Z);
+  for (int cz = (L::D == 3 ? -1 : 0); cz <= (L::D == 3 ? 1 : 0); ++cz)
+#pragma unroll
+    for (int cy = -1; cy <= 1; ++cy) {
+      const IX row = nb.zo[cz + 1] + nb.yo[cy + 1];
+      const C2 qm = __ldg(pl + row + nb.xo[0]);
+      const C2 qp = __ldg(pl + row + nb.xo[2]);
+      const C wyz = (C)(w1d(cy) * (L::D == 3 ? w1d(cz) : 1.0));
+      dp[0] += wyz * (qp.x - qm.x);
+      dl[0] += wyz * (qp.y - qm.y);
+      if (cy == 0 && cz == 0) continue;  // the centre row enters d_x only
+      const C2 q0 = __ldg(pl + row + nb.xo[1]);
+      const C spx = (C)(1.0 / 6.0) * (qm.x + qp.x) + (C)(2.0 / 3.0) * q0.x;
+      const C slx = (C)(1.0 / 6.0) * (qm.y + qp.y) + (C)(2.0 / 3.0) * q0.y;
+      if (cy != 0) {
+        const C w = (C)(cy * (L::D == 3 ? w1d(cz) : 1.0));
+        dp[1] += w * spx;
+        dl[1] += w * slx;
+      }
+      if (cz != 0) {
+        const C w = (C)(cz * w1d(cy));
+        dp[2] += w * spx;
+        dl[2] += w * slx;
+      }
+    }
+  const IX k = nb.at(0, 0, 0);
   r = rho[k];
   const C phi = pl[k].x;
   const C gg[3] = {gx, gy, gz};
 #pragma unroll
-  for (int a = 0; a < 3; ++a) F[a] = (C)2 * phi * gp[a] + kappa * r * gl[a] + r * gg[a];
+  for (int a = 0; a < 3; ++a) F[a] = phi * dp[a] + (C)0.5 * kappa * r * dl[a] + r * gg[a];
   if (L::D == 2) F[2] = (C)0;
 }
 
 // ---------------------------------------------------------------- pass 3
-// Sum of a[4] over the CTA into out[4] (FP64, fixed order).
-constexpr int kMpPartial = kMpPartialDoubles;  // per CTA: momentum (3), mass
-__device__ __forceinline__ void cta_sum4(double (&a)[kMpPartial], double *out) {
+// Sum of a[4] over the CTA into out[q * stride] (FP64, fixed order).
+__device__ __forceinline__ void cta_sum4(double (&a)[kMpPartial], double *out, long long stride) {
   __shared__ double red[kMpPartial][32];
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const int lane = tid & 31, warp = tid >> 5, nw = (blockDim.x * blockDim.y + 31) >> 5;
@@ -218,11 +334,11 @@ __device__ __forceinline__ void cta_sum4(double (&a)[kMpPartial], double *out) {
   if (tid < kMpPartial) {
     double t = 0;
     for (int w = 0; w < nw; ++w) t += red[tid][w];
-    out[tid] = t;
+    out[tid * stride] = t;
   }
 }
 
-template <int Q, int S>
+template <int Q, int S, typename IX>
 __global__ void __launch_bounds__(128, 4)
     k_mp_sweep(Grid g, const typename Store<S>::T *__restrict__ fin,
                typename Store<S>::T *__restrict__ fout, const typename Store<S>::C *__restrict__ rref,
@@ -230,7 +346,7 @@ __global__ void __launch_bounds__(128, 4)
                const typename Vec2<typename Store<S>::C>::T *__restrict__ pl,
                typename Store<S>::C beta, typename Store<S>::C kappa, typename Store<S>::C gx,
                typename Store<S>::C gy, typename Store<S>::C gz, int bgk,
-               const double *__restrict__ ctl, double *__restrict__ partial,
+               const double *__restrict__ ctl, double *__restrict__ partial, long long nblk,
                int *__restrict__ err) {
   using L = Lat<Q>;
   using C = typename Store<S>::C;
@@ -240,26 +356,33 @@ __global__ void __launch_bounds__(128, 4)
   const bool active = x < g.nx && y < g.ny;
   double part[kMpPartial] = {0, 0, 0, 0};
   if (active) {
-    const int X = x + g.px, Y = y + g.py, Z = z + g.pz;
+    const Nbhd<L::D, IX> nb(g, x + g.px, y + g.py, z + g.pz);
     C r, F[3];
-    mp_force<Q, C>(g, rho, pl, kappa, gx, gy, gz, X, Y, Z, r, F);
+    mp_force<Q, C, IX>(rho, pl, nb, kappa, gx, gy, gz, r, F);
     const C ir = (C)1 / r;
     C v[Q];
     // the new reference of the node: its density of this step
-    mp_gather<Q, S>(g, fin, rref, X, Y, Z, r, v);
+    mp_gather<Q, S, IX>(g, fin, rref, nb, r, v);
     // du = F / rho - a_c
     const C rc = collide_v<L, S == STORE_F32, C, true>(
         v, beta, bgk != 0, F[0] * ir - (C)ctl[0], F[1] * ir - (C)ctl[1],
         L::D == 3 ? F[2] * ir - (C)ctl[2] : (C)0, r);
     if (!(rc > (C)0 && rc < (C)1e30)) atomicOr(err, 1);
-    sweep_scatter<Q, S, long long>(g, fout, sidx(g, X, Y, Z), v);
-    // momentum of the stored values (the reference carries none)
+    sweep_scatter<Q, S, IX>(g, fout, nb.at(0, 0, 0), v);
+    // momentum of the stored values (the reference carries none), by rows
+    // of three x-neighbours
     C jx = (C)0, jy = (C)0, jz = (C)0;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      if (L::cx(i)) jx += (C)L::cx(i) * v[i];
-      if (L::cy(i)) jy += (C)L::cy(i) * v[i];
-      if (L::cz(i)) jz += (C)L::cz(i) * v[i];
+    for (int rw = 0; rw < Q / 3; ++rw) {
+      const int cy = L::cy(3 * rw), cz = L::cz(3 * rw);
+      jx += v[3 * rw + 2] - v[3 * rw];
+      if (cy || cz) {
+        const C sm = v[3 * rw] + v[3 * rw + 1] + v[3 * rw + 2];
+        if (cy > 0) jy += sm;
+        if (cy < 0) jy -= sm;
+        if (cz > 0) jz += sm;
+        if (cz < 0) jz -= sm;
+      }
     }
     part[0] = (double)jx;
     part[1] = (double)jy;
@@ -267,37 +390,7 @@ __global__ void __launch_bounds__(128, 4)
     part[3] = (double)r;
   }
   const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-  cta_sum4(part, partial + kMpPartial * blk);
-}
-
-// Momentum controller (one CTA, fixed order).  ctl: [0..2] the correcting
-// acceleration a_c of the next step, [3..5] the one the last step used,
-// [6..8] the momentum P of the previous step, [9] 1 once P is recorded.
-__global__ void __launch_bounds__(256) k_mp_control(const double *__restrict__ partial,
-                                                    long long nblk, double gx,
-                                                    double gy, double gz, double *__restrict__ ctl) {
-  __shared__ double red[kMpPartial][256];
-  double t[kMpPartial] = {0, 0, 0, 0};
-  for (long long b = threadIdx.x; b < nblk; b += blockDim.x)
-    for (int q = 0; q < kMpPartial; ++q) t[q] += partial[kMpPartial * b + q];
-  for (int q = 0; q < kMpPartial; ++q) red[q][threadIdx.x] = t[q];
-  __syncthreads();
-  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-    if ((int)threadIdx.x < h)
-      for (int q = 0; q < kMpPartial; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + h];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    const double M = red[3][0], gg[3] = {gx, gy, gz};
-    const bool have_prev = ctl[9] != 0.0;
-    for (int a = 0; a < 3; ++a) {
-      const double P = red[a][0];
-      ctl[3 + a] = ctl[a];
-      if (have_prev) ctl[a] += (P - ctl[6 + a] - M * gg[a]) / M;
-      ctl[6 + a] = P;
-    }
-    ctl[9] = 1.0;
-  }
+  cta_sum4(part, partial + blk, nblk);
 }
 
 // Read-out of the stored state for interior nodes [begin, begin + count),
@@ -328,9 +421,10 @@ __global__ void k_mp_read(Grid g, const typename Store<S>::T *__restrict__ f,
   const long long k = sidx(g, X, Y, Z);
   C Fv[3] = {(C)0, (C)0, (C)0}, rdummy;
   if (have_force) {
-    mp_force<Q, C>(g, rref, pl, kappa, gx, gy, gz, X, Y, Z, rdummy, Fv);
+    const Nbhd<L::D, long long> nb(g, X, Y, Z);
+    mp_force<Q, C, long long>(rref, pl, nb, kappa, gx, gy, gz, rdummy, Fv);
     // the correcting force the step used
-    for (int a = 0; a < L::D; ++a) Fv[a] -= rdummy * (C)mean[3 + a];
+    for (int a = 0; a < L::D; ++a) Fv[a] -= rdummy * (C)mean[a];
   }
   if (F)
     for (int a = 0; a < 3; ++a) F[a * stride + j] = (double)Fv[a];
@@ -391,19 +485,34 @@ template <int Q, int S>
 static cudaError_t mp_step_t(const Grid &g, const void *fin, void *fout, const void *rref,
                              void *rho, void *pl, double *ctl, double *partial,
                              const MpParams &mp, double beta, int bgk, int *err, cudaStream_t s) {
+  // partial: [4][nblk] CTA sums of the sweep, then [4][ngroups] group sums
+  double *gpart = partial + kMpPartial * mp_grid(g.nx, g.ny, g.nz).blocks;
   using T = typename Store<S>::T;
   using C = typename Store<S>::C;
   using C2 = typename Vec2<C>::T;
   const dim3 b = mp_block(g);
   const dim3 grid((g.nx + b.x - 1) / b.x, (g.ny + b.y - 1) / b.y, g.nz);
-  k_mp_density<Q, S><<<grid, b, 0, s>>>(g, (const T *)fin, (const C *)rref, (C *)rho, (C2 *)pl,
-                                        mp.eos, err);
-  k_mp_lap<Q, C><<<grid, b, 0, s>>>(g, (const C *)rho, (C2 *)pl);
-  k_mp_sweep<Q, S><<<grid, b, 0, s>>>(g, (const T *)fin, (T *)fout, (const C *)rref,
-                                      (const C *)rho, (const C2 *)pl, (C)beta, (C)mp.kappa,
-                                      (C)mp.g[0], (C)mp.g[1], (C)mp.g[2], bgk, ctl, partial, err);
   const long long nblk = (long long)grid.x * grid.y * grid.z;
-  k_mp_control<<<1, 256, 0, s>>>(partial, nblk, mp.g[0], mp.g[1], mp.g[2], ctl);
+  // 32-bit offsets when every population offset fits
+  if ((long long)Q * g.N < (1LL << 31)) {
+    k_mp_density<Q, S, int><<<grid, b, 0, s>>>(g, (const T *)fin, (const C *)rref, (C *)rho,
+                                               (C2 *)pl, mp.eos, partial, gpart, nblk, err);
+    k_mp_lap<Q, C, int><<<grid, b, 0, s>>>(g, (const C *)rho, (C2 *)pl, gpart, nblk, mp.g[0],
+                                           mp.g[1], mp.g[2], ctl);
+    k_mp_sweep<Q, S, int><<<grid, b, 0, s>>>(g, (const T *)fin, (T *)fout, (const C *)rref,
+                                             (const C *)rho, (const C2 *)pl, (C)beta, (C)mp.kappa,
+                                             (C)mp.g[0], (C)mp.g[1], (C)mp.g[2], bgk, ctl,
+                                             partial, nblk, err);
+  } else {
+    k_mp_density<Q, S, long long><<<grid, b, 0, s>>>(g, (const T *)fin, (const C *)rref,
+                                                     (C *)rho, (C2 *)pl, mp.eos, partial, gpart,
+                                                     nblk, err);
+    k_mp_lap<Q, C, long long><<<grid, b, 0, s>>>(g, (const C *)rho, (C2 *)pl, gpart, nblk,
+                                                 mp.g[0], mp.g[1], mp.g[2], ctl);
+    k_mp_sweep<Q, S, long long><<<grid, b, 0, s>>>(
+        g, (const T *)fin, (T *)fout, (const C *)rref, (const C *)rho, (const C2 *)pl, (C)beta,
+        (C)mp.kappa, (C)mp.g[0], (C)mp.g[1], (C)mp.g[2], bgk, ctl, partial, nblk, err);
+  }
   return cudaGetLastError();
 }
 
