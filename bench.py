@@ -558,13 +558,20 @@ def mp_leg(args, shape=(320, 250, 320), kappa=0.025, beta=0.6):
     del rho
     L.step(10)
     chunk, reps = 10, 10
-    L.step_graph(chunk, 1)
-    ms = _timed(stream, lambda k: L.step_graph(chunk, k), reps) / chunk
+    variants = {}
+    from paper_1710_02375_gb300.lbm import LBM_SWEEP_DIRECT, LBM_SWEEP_PAIR
+    for name, var in (("one_node", LBM_SWEEP_DIRECT), ("two_node", LBM_SWEEP_PAIR)):
+        L.set_sweep_variant(var)
+        L.step(4)
+        L.step_graph(chunk, 1)
+        variants[name] = _timed(stream, lambda k: L.step_graph(chunk, k), reps) / chunk
     L.check()
     L.close()
+    ms = min(variants.values())
     peak, peak_kind = measured_peaks()
     gbs = MP_BYTES_PER_NODE * nodes / (ms * 1e-3) / 1e9
     return {"ms_per_step": ms, "mlups": nodes / (ms * 1e-3) / 1e6, "steps": chunk * reps,
+            "sweep_forms_ms_per_step": variants,
             "algorithmic_bytes_per_node": MP_BYTES_PER_NODE, "achieved_gbs": gbs,
             "frac_of_peak": gbs / peak, "peak_kind": peak_kind,
             "config": f"D3Q27 {nx}x{ny}x{nz} periodic, droplet D=80, kappa={kappa}, beta={beta}, "

@@ -495,6 +495,8 @@ static lbm_status mp_adopt_state(lbm_ctx *ctx) {
   CK(launch_mp_rebase(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur],
                       ctx->ws + ctx->lay.mp_rho[ctx->mp_cur], 1.0, 0, ctx->stream));
   CK(cudaMemsetAsync(ctx->ws + ctx->lay.mp_ctl, 0, sizeof(double) * kMpControl, ctx->stream));
+  // lap R = 0 for the uniform reference R = 1 (the density pass reads it)
+  CK(cudaMemsetAsync(ctx->ws + ctx->lay.mp_pl, 0, ctx->lay.mp_ctl - ctx->lay.mp_pl, ctx->stream));
   CK(cudaMemsetAsync(ctx->ws + ctx->lay.mp_partial, 0,
                      mp_partial_bytes(ctx->g.nx, ctx->g.ny, ctx->g.nz), ctx->stream));
   ctx->mp_have_force = false;
@@ -598,6 +600,7 @@ lbm_status lbm_step(lbm_ctx *ctx, int n) {
       if (ctx->bp.ramp_steps > 0) CK(launch_step_counter(ctx->counters + 3, ctx->stream));
     }
     if (ctx->mp_on) {
+      ctx->mp.pair = ctx->sweep_variant != SWEEP_DIRECT;
       CK(launch_mp_step(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur], ctx->f[1 - ctx->cur],
                         ctx->ws + ctx->lay.mp_rho[ctx->mp_cur],
                         ctx->ws + ctx->lay.mp_rho[1 - ctx->mp_cur], ctx->ws + ctx->lay.mp_pl,
@@ -1018,6 +1021,13 @@ lbm_status lbm_set_sweep_variant(lbm_ctx *ctx, int variant) {
   GUARD();
   if (variant < LBM_SWEEP_AUTO || variant > LBM_SWEEP_PAIR)
     return fail(ctx, LBM_EINVAL, "lbm_set_sweep_variant: unknown variant %d", variant);
+  if (ctx->mp_on && (variant == SWEEP_DIRECT) != (ctx->sweep_variant == SWEEP_DIRECT)) {
+    // the two forms of the multiphase sweep leave per-CTA partials of
+    // different grids: restart the momentum controller
+    CK(cudaMemsetAsync(ctx->ws + ctx->lay.mp_ctl, 0, sizeof(double) * kMpControl, ctx->stream));
+    CK(cudaMemsetAsync(ctx->ws + ctx->lay.mp_partial, 0,
+                       mp_partial_bytes(ctx->g.nx, ctx->g.ny, ctx->g.nz), ctx->stream));
+  }
   ctx->sweep_variant = variant;
   ctx->graph_dirty = true;
   return LBM_OK;

@@ -68,6 +68,7 @@ struct MpParams {
   double kappa;  // capillary coefficient
   double g[3];   // uniform acceleration (F gains rho g)
   int eos;       // MP_EOS_*
+  int pair;      // FP32: the two-node form of the forced sweep
 };
 // One multiphase step fin -> fout: density pass (rho, phi), Laplacian pass
 // (lap rho), forced sweep.  Populations are stored as f_i - W_i R(x), R the
@@ -77,10 +78,11 @@ struct MpParams {
 // ctl: momentum-controller state (kMpControl doubles, zero to start):
 // [0..2] the correcting acceleration a_c of the current step (force rho a_c
 // subtracted per node), [6..8] the momentum of the step before, [9] the
-// number of sweeps with partials (0, 1, 2); partial: kMpPartialDoubles per
+// number of sweeps with partials (0, 1, 2), [10..11] a_c as three floats;
+// partial: kMpPartialDoubles per
 // CTA of mp_grid, then the same per group of kMpGroupCtas CTAs
 // (mp_partial_bytes).
-constexpr int kMpControl = 10;
+constexpr int kMpControl = 12;
 constexpr int kMpPartialDoubles = 4;
 constexpr int kMpGroupCtas = 128;
 cudaError_t launch_mp_step(int Q, int storage, const Grid &g, const void *fin, void *fout,

@@ -115,7 +115,8 @@ struct Nbhd {
 // no fences, a deterministic result.
 // ctl: [0..2] the correcting acceleration a_c used by the current step,
 // [6..8] the momentum of the step before, [9] the number of sweeps whose
-// partials exist (0, 1, 2 = enough for an update).
+// partials exist (0, 1, 2 = enough for an update), [10..11] a_c in FP32
+// (three floats).
 constexpr int kMpPartial = kMpPartialDoubles;  // per CTA: momentum (3), mass
 constexpr int kMpGroup = kMpGroupCtas;
 
@@ -176,7 +177,22 @@ __device__ __forceinline__ void mp_stage2(const double *__restrict__ gpart, long
       }
     }
     ctl[9] = have >= 1.0 ? 2.0 : 1.0;
+    float *acf = reinterpret_cast<float *>(ctl + 10);  // FP32 copy for the sweep
+    for (int a = 0; a < 3; ++a) acf[a] = (float)ctl[a];
   }
+}
+
+// The correcting acceleration of the current step in the compute type
+// (FP32 sweeps read the FP32 copy at ctl[10..11]).
+template <class C>
+__device__ __forceinline__ C mp_ac(const double *ctl, int a);
+template <>
+__device__ __forceinline__ float mp_ac<float>(const double *ctl, int a) {
+  return reinterpret_cast<const float *>(ctl + 10)[a];
+}
+template <>
+__device__ __forceinline__ double mp_ac<double>(const double *ctl, int a) {
+  return ctl[a];
 }
 
 // ---------------------------------------------------------------- pass 1
@@ -212,16 +228,22 @@ __global__ void __launch_bounds__(128)
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
   if (x < g.nx && y < g.ny) {
-    const Nbhd<Lat<Q>::D, IX> nb(g, x + g.px, y + g.py, z + g.pz);
+    using L = Lat<Q>;
+    using St = Store<S>;
+    const Nbhd<L::D, IX> nb(g, x + g.px, y + g.py, z + g.pz);
     const IX k = nb.at(0, 0, 0);
-    // deviations from the node's own old reference keep the sum small
+    // rho = sum_i g_i(x - c_i) + sum_i W_i R(x - c_i); the second sum is
+    // the weighted neighbourhood mean of the reference densities, which the
+    // Laplacian pass of the step that wrote them left at the node:
+    // sum_i W_i R(x - c_i) = R(x) + lap R(x) / 6 (W_i = W_-i)
     const C R = rref[k];
-    C v[Q];
-    mp_gather<Q, S, IX>(g, fin, rref, nb, R, v);
+    const C mean_ref = R + pl[k].y * (C)(1.0 / 6.0);
+    const IX N = (IX)g.N;
     C d = (C)0;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) d += v[i];
-    const C r = R + d;
+    for (int i = 0; i < Q; ++i)
+      d += St::load(fin + ((IX)i * N + nb.at(-L::cx(i), -L::cy(i), -L::cz(i))), (C)weight<L>(i));
+    const C r = mean_ref + d;
     if (!(r > (C)0 && r < (C)1e30)) atomicOr(err, 1);
     const C s = r * (C)(1.0 / 3.0) - mp_pressure(r, eos);
     rho[k] = r;
@@ -320,15 +342,19 @@ __device__ __forceinline__ void mp_force(const C *__restrict__ rho,
 }
 
 // ---------------------------------------------------------------- pass 3
-// Sum of a[4] over the CTA into out[q * stride] (FP64, fixed order).
-__device__ __forceinline__ void cta_sum4(double (&a)[kMpPartial], double *out, long long stride) {
+// Sum of a[4] over the CTA into out[q * stride], fixed order: within each
+// warp in the compute type A (FP64 arithmetic is scarce on this GPU; a
+// rounding that repeats from step to step cancels in the controller's
+// P(t) - P(t-1)), across the warps in FP64.
+template <class A>
+__device__ __forceinline__ void cta_sum4(A (&a)[kMpPartial], double *out, long long stride) {
   __shared__ double red[kMpPartial][32];
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const int lane = tid & 31, warp = tid >> 5, nw = (blockDim.x * blockDim.y + 31) >> 5;
 #pragma unroll
   for (int q = 0; q < kMpPartial; ++q) {
     for (int o = 16; o > 0; o >>= 1) a[q] += __shfl_down_sync(0xffffffffu, a[q], o);
-    if (lane == 0) red[q][warp] = a[q];
+    if (lane == 0) red[q][warp] = (double)a[q];
   }
   __syncthreads();
   if (tid < kMpPartial) {
@@ -338,8 +364,14 @@ __device__ __forceinline__ void cta_sum4(double (&a)[kMpPartial], double *out, l
   }
 }
 
+// Resident 128-thread CTAs per SM the one-node forced sweep's registers
+// are sized for (measured on the 320 x 250 x 320 droplet: 4 / 5 CTAs ->
+// 2.63 / 2.68 ms per step; 5 spills ~130 bytes to L1).
+#ifndef KBC_MP_CTAS
+#define KBC_MP_CTAS 4
+#endif
 template <int Q, int S, typename IX>
-__global__ void __launch_bounds__(128, 4)
+__global__ void __launch_bounds__(128, KBC_MP_CTAS)
     k_mp_sweep(Grid g, const typename Store<S>::T *__restrict__ fin,
                typename Store<S>::T *__restrict__ fout, const typename Store<S>::C *__restrict__ rref,
                const typename Store<S>::C *__restrict__ rho,
@@ -354,9 +386,10 @@ __global__ void __launch_bounds__(128, 4)
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
   const bool active = x < g.nx && y < g.ny;
-  double part[kMpPartial] = {0, 0, 0, 0};
+  C part[kMpPartial] = {(C)0, (C)0, (C)0, (C)0};
   if (active) {
     const Nbhd<L::D, IX> nb(g, x + g.px, y + g.py, z + g.pz);
+    const C ac[3] = {mp_ac<C>(ctl, 0), mp_ac<C>(ctl, 1), mp_ac<C>(ctl, 2)};
     C r, F[3];
     mp_force<Q, C, IX>(rho, pl, nb, kappa, gx, gy, gz, r, F);
     const C ir = (C)1 / r;
@@ -365,8 +398,8 @@ __global__ void __launch_bounds__(128, 4)
     mp_gather<Q, S, IX>(g, fin, rref, nb, r, v);
     // du = F / rho - a_c
     const C rc = collide_v<L, S == STORE_F32, C, true>(
-        v, beta, bgk != 0, F[0] * ir - (C)ctl[0], F[1] * ir - (C)ctl[1],
-        L::D == 3 ? F[2] * ir - (C)ctl[2] : (C)0, r);
+        v, beta, bgk != 0, F[0] * ir - ac[0], F[1] * ir - ac[1],
+        L::D == 3 ? F[2] * ir - ac[2] : (C)0, r);
     if (!(rc > (C)0 && rc < (C)1e30)) atomicOr(err, 1);
     sweep_scatter<Q, S, IX>(g, fout, nb.at(0, 0, 0), v);
     // momentum of the stored values (the reference carries none), by rows
@@ -384,10 +417,101 @@ __global__ void __launch_bounds__(128, 4)
         if (cz < 0) jz -= sm;
       }
     }
-    part[0] = (double)jx;
-    part[1] = (double)jy;
-    part[2] = (double)jz;
-    part[3] = (double)r;
+    part[0] = jx;
+    part[1] = jy;
+    part[2] = jz;
+    part[3] = r;
+  }
+  const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  cta_sum4(part, partial + blk, nblk);
+}
+
+// Two-node form of the forced sweep (FP32 storage): each thread takes the
+// columns (X, X + 1), X even, of one row and collides both nodes on the
+// paired FP32 instructions (collide_v with V = f2).  The c_x = 0 sources and
+// the references of a pair are aligned two-element loads.  When X + 1 is
+// past the row's last node the second lane repeats the first node's inputs
+// and is never stored.
+#ifndef KBC_MP_PAIR_CTAS
+#define KBC_MP_PAIR_CTAS 2
+#endif
+template <int Q, typename IX>
+__global__ void __launch_bounds__(128, KBC_MP_PAIR_CTAS)
+    k_mp_sweep2(Grid g, const float *__restrict__ fin, float *__restrict__ fout,
+                const float *__restrict__ rref, const float *__restrict__ rho,
+                const float2 *__restrict__ pl, float beta, float kappa, float gx, float gy,
+                float gz, int bgk, const double *__restrict__ ctl, double *__restrict__ partial,
+                long long nblk, int *__restrict__ err) {
+  using L = Lat<Q>;
+  using St = Store<STORE_F32>;
+  const int x = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  const bool ia = x < g.nx && y < g.ny;
+  const bool ib = ia && x + 1 < g.nx;
+  float part[kMpPartial] = {0.f, 0.f, 0.f, 0.f};
+  if (ia) {
+    const int X = x + g.px, Y = y + g.py, Z = z + g.pz;
+    const Nbhd<L::D, IX> na(g, X, Y, Z), nb(g, ib ? X + 1 : X, Y, Z);
+    float ra, rb, Fa[3], Fb[3];
+    mp_force<Q, float, IX>(rho, pl, na, kappa, gx, gy, gz, ra, Fa);
+    mp_force<Q, float, IX>(rho, pl, nb, kappa, gx, gy, gz, rb, Fb);
+    const IX N = (IX)g.N;
+    f2 v[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+      const float w = (float)weight<L>(i);
+      const IX sa = na.at(-cx, -cy, -cz);
+      float pa, pb, qa, qb;
+      if (cx == 0 && ib) {
+        // sources (X, X + 1) of the same row: one aligned pair each
+        const float2 p2 = St::load2(fin + ((IX)i * N + sa), w);
+        const float2 q2 = __ldg(reinterpret_cast<const float2 *>(rref + sa));
+        pa = p2.x; pb = p2.y; qa = q2.x; qb = q2.y;
+      } else {
+        const IX sb = nb.at(-cx, -cy, -cz);
+        pa = St::load(fin + ((IX)i * N + sa), w);
+        pb = St::load(fin + ((IX)i * N + sb), w);
+        qa = __ldg(rref + sa);
+        qb = __ldg(rref + sb);
+      }
+      v[i] = mk2(fmaf(w, qa - ra, pa), fmaf(w, qb - rb, pb));
+    }
+    const float ia_r = 1.f / ra, ib_r = 1.f / rb;
+    const float c0 = mp_ac<float>(ctl, 0), c1 = mp_ac<float>(ctl, 1), c2 = mp_ac<float>(ctl, 2);
+    const f2 dux = mk2(Fa[0] * ia_r - c0, Fb[0] * ib_r - c0);
+    const f2 duy = mk2(Fa[1] * ia_r - c1, Fb[1] * ib_r - c1);
+    const f2 duz = L::D == 3 ? mk2(Fa[2] * ia_r - c2, Fb[2] * ib_r - c2) : mk2(0.f, 0.f);
+    const f2 rc = collide_v<L, true, f2, true>(v, beta, bgk != 0, dux, duy, duz, mk2(ra, rb));
+    if (!(rc.v.x > 0.f && rc.v.x < 1e30f) || (ib && !(rc.v.y > 0.f && rc.v.y < 1e30f)))
+      atomicOr(err, 1);
+    const IX k = na.at(0, 0, 0);
+    if (ib) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) St::store2(fout + ((IX)i * N + k), v[i].v, 1.f);
+    } else {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) St::store(fout + ((IX)i * N + k), v[i].v.x, 1.f);
+    }
+    // momentum of the stored values, by rows of three x-neighbours
+    f2 jx = mk2(0.f, 0.f), jy = jx, jz = jx;
+#pragma unroll
+    for (int rw = 0; rw < Q / 3; ++rw) {
+      const int cy = L::cy(3 * rw), cz = L::cz(3 * rw);
+      jx = vadd(jx, vsub(v[3 * rw + 2], v[3 * rw]));
+      if (cy || cz) {
+        const f2 sm = vadd(vadd(v[3 * rw], v[3 * rw + 1]), v[3 * rw + 2]);
+        if (cy > 0) jy = vadd(jy, sm);
+        if (cy < 0) jy = vsub(jy, sm);
+        if (cz > 0) jz = vadd(jz, sm);
+        if (cz < 0) jz = vsub(jz, sm);
+      }
+    }
+    part[0] = jx.v.x + (ib ? jx.v.y : 0.f);
+    part[1] = jy.v.x + (ib ? jy.v.y : 0.f);
+    part[2] = jz.v.x + (ib ? jz.v.y : 0.f);
+    part[3] = ra + (ib ? rb : 0.f);
   }
   const long long blk = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   cta_sum4(part, partial + blk, nblk);
@@ -493,25 +617,44 @@ static cudaError_t mp_step_t(const Grid &g, const void *fin, void *fout, const v
   const dim3 b = mp_block(g);
   const dim3 grid((g.nx + b.x - 1) / b.x, (g.ny + b.y - 1) / b.y, g.nz);
   const long long nblk = (long long)grid.x * grid.y * grid.z;
+  // the sweep: two-node form for FP32 storage (its own CTA grid)
+  const bool pair = S == STORE_F32 && mp.pair;
+  const int npairs = (g.nx + 1) / 2;
+  const dim3 b2 = npairs >= 128 ? dim3(128, 1, 1) : dim3(32, 4, 1);
+  const dim3 grid2((npairs + b2.x - 1) / b2.x, (g.ny + b2.y - 1) / b2.y, g.nz);
+  const long long nblk_sweep = pair ? (long long)grid2.x * grid2.y * grid2.z : nblk;
   // 32-bit offsets when every population offset fits
   if ((long long)Q * g.N < (1LL << 31)) {
     k_mp_density<Q, S, int><<<grid, b, 0, s>>>(g, (const T *)fin, (const C *)rref, (C *)rho,
-                                               (C2 *)pl, mp.eos, partial, gpart, nblk, err);
-    k_mp_lap<Q, C, int><<<grid, b, 0, s>>>(g, (const C *)rho, (C2 *)pl, gpart, nblk, mp.g[0],
-                                           mp.g[1], mp.g[2], ctl);
-    k_mp_sweep<Q, S, int><<<grid, b, 0, s>>>(g, (const T *)fin, (T *)fout, (const C *)rref,
-                                             (const C *)rho, (const C2 *)pl, (C)beta, (C)mp.kappa,
-                                             (C)mp.g[0], (C)mp.g[1], (C)mp.g[2], bgk, ctl,
-                                             partial, nblk, err);
+                                               (C2 *)pl, mp.eos, partial, gpart, nblk_sweep, err);
+    k_mp_lap<Q, C, int><<<grid, b, 0, s>>>(g, (const C *)rho, (C2 *)pl, gpart, nblk_sweep,
+                                           mp.g[0], mp.g[1], mp.g[2], ctl);
+    if (pair)
+      k_mp_sweep2<Q, int><<<grid2, b2, 0, s>>>(g, (const float *)fin, (float *)fout,
+                                               (const float *)rref, (const float *)rho,
+                                               (const float2 *)pl, (float)beta, (float)mp.kappa,
+                                               (float)mp.g[0], (float)mp.g[1], (float)mp.g[2], bgk,
+                                               ctl, partial, nblk_sweep, err);
+    else
+      k_mp_sweep<Q, S, int><<<grid, b, 0, s>>>(g, (const T *)fin, (T *)fout, (const C *)rref,
+                                               (const C *)rho, (const C2 *)pl, (C)beta,
+                                               (C)mp.kappa, (C)mp.g[0], (C)mp.g[1], (C)mp.g[2],
+                                               bgk, ctl, partial, nblk_sweep, err);
   } else {
     k_mp_density<Q, S, long long><<<grid, b, 0, s>>>(g, (const T *)fin, (const C *)rref,
                                                      (C *)rho, (C2 *)pl, mp.eos, partial, gpart,
-                                                     nblk, err);
-    k_mp_lap<Q, C, long long><<<grid, b, 0, s>>>(g, (const C *)rho, (C2 *)pl, gpart, nblk,
+                                                     nblk_sweep, err);
+    k_mp_lap<Q, C, long long><<<grid, b, 0, s>>>(g, (const C *)rho, (C2 *)pl, gpart, nblk_sweep,
                                                  mp.g[0], mp.g[1], mp.g[2], ctl);
-    k_mp_sweep<Q, S, long long><<<grid, b, 0, s>>>(
-        g, (const T *)fin, (T *)fout, (const C *)rref, (const C *)rho, (const C2 *)pl, (C)beta,
-        (C)mp.kappa, (C)mp.g[0], (C)mp.g[1], (C)mp.g[2], bgk, ctl, partial, nblk, err);
+    if (pair)
+      k_mp_sweep2<Q, long long><<<grid2, b2, 0, s>>>(
+          g, (const float *)fin, (float *)fout, (const float *)rref, (const float *)rho,
+          (const float2 *)pl, (float)beta, (float)mp.kappa, (float)mp.g[0], (float)mp.g[1],
+          (float)mp.g[2], bgk, ctl, partial, nblk_sweep, err);
+    else
+      k_mp_sweep<Q, S, long long><<<grid, b, 0, s>>>(
+          g, (const T *)fin, (T *)fout, (const C *)rref, (const C *)rho, (const C2 *)pl, (C)beta,
+          (C)mp.kappa, (C)mp.g[0], (C)mp.g[1], (C)mp.g[2], bgk, ctl, partial, nblk_sweep, err);
   }
   return cudaGetLastError();
 }
