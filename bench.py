@@ -401,12 +401,12 @@ STATED_ERRORS = {
 }
 
 # Algorithmic HBM bytes per node of one multiphase step (FP32, D3Q27): the
-# density pass reads 27 populations and the node's reference density and
-# writes rho and phi (120 B); the Laplacian pass reads rho and writes lap
-# rho (8 B); the forced sweep reads 27 populations, the reference, rho and
-# the (phi, lap) pair and writes 27 populations (232 B).  Neighbour values
-# of the fields are cache hits.
-MP_BYTES_PER_NODE = 120 + 8 + 232
+# density pass reads 27 populations, the node's reference density and its
+# previous lap rho and writes rho and phi (124 B); the Laplacian pass reads
+# rho and writes lap rho (8 B); the forced sweep reads 27 populations, the
+# reference, rho and the (phi, lap) pair and writes 27 populations (232 B).
+# Neighbour values of the fields are cache hits.
+MP_BYTES_PER_NODE = 124 + 8 + 232
 
 
 def _timed(stream, fn, steps):

@@ -37,8 +37,8 @@
 // the force, of the forcing term and of the stored values repeat from step
 // to step in a quasi-steady state and add up to a net force: a liquid slab
 // at rest accelerates by ~1e-9 per step.  Each sweep therefore sums the
-// momentum of the populations it stores (per-CTA partials in FP64, one CTA
-// reducing them in a fixed order), and an acceleration a_c, whose force rho
+// momentum of the populations it stores (one partial per CTA, reduced in a
+// fixed order during the next step), and an acceleration a_c, whose force rho
 // a_c is subtracted at every node in the next step, integrates the error:
 //     a_c <- a_c + (P(t) - P(t-1) - M g) / M,
 // so the momentum error of step t + 1 is the change of the rounding between
