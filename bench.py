@@ -46,6 +46,7 @@ N_LATTICE = 128
 U0, RE = 0.05, 1600.0
 Q = 27
 SWEEP_SOURCES = ["paper_1710_02375_gb300/csrc/kbc_collide.cuh", "paper_1710_02375_gb300/csrc/kbc_sweep.cu",
+                 "paper_1710_02375_gb300/csrc/sweep_io.cuh",
                  "paper_1710_02375_gb300/csrc/kbc_common.cuh"]
 PROFILE_MD = os.path.join(ROOT, "profiles", "kbc_sweep_d3q27_f32_tgv128.md")
 
