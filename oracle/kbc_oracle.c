@@ -450,3 +450,212 @@ int or_step_multiphase(int lat, int nx, int ny, int nz, double beta, int mode, d
   free(rho); free(phi); free(lap);
   return 0;
 }
+
+/* ======================================================================
+ * Multiphase step between two planar walls (section "Extensions to
+ * fluid-structure interaction in multiphase flow": the wetting force F_s
+ * and Grad's boundary condition in the multiphase model).
+ *
+ * The walls lie half a cell outside the faces normal to axis wa (q = 1/2,
+ * at rest); the other axes are periodic.  Readings:
+ *   - Grad fill of the missing populations of a wall node, as in the
+ *     single-phase step with face walls: u_t = mean over the missing set of
+ *     q u(x_b + c_i) / (1 + q), rho_t = sum of the known pulled populations
+ *     plus the node's own stored f'_opp(i), grad u by finite differences
+ *     (central, else one-sided second order through x_b, else first
+ *     order), Pi = rho c_s^2 I + rho u u - rho c_s^2/(2 beta)(grad u +
+ *     grad u^T), f*_i of Eq. (grad).  The velocities u(x, t-1) are the
+ *     fluid velocities of the stored state, (j' - F_prev/2) / rho' (F_prev
+ *     the force of the step that produced it; zero for a state set from
+ *     outside).  The filled populations are pre-collision ones, whose
+ *     momentum under the exact difference method is rho u - F/2: the
+ *     target velocity is the interpolated fluid velocity minus
+ *     F_prev(x_b) / (2 rho_t).  (Targeting the fluid velocity itself lets
+ *     a wall-normal force at the wall node, e.g. the wetting force, inject
+ *     mass every step: the fill returns the equilibrium share of rho_t
+ *     while the outgoing populations carry the force's momentum.)
+ *   - The fields rho, phi and lap rho of the stencils take, at the nodes
+ *     beyond a wall, the value of the node across the wall (the mirror
+ *     image at a wall half a cell out).
+ *   - Wetting force F_s = kappa_w rho sum_i w_i s(x + c_i) c_i with w_i the
+ *     lattice weights W_i (the paper leaves w_i open) and s = 1 for the
+ *     nodes beyond a wall.
+ *   F = 2 phi d(phi) + kappa rho d(lap rho) + F_s + rho g.
+ * fin / fout: post-collision states [Q][n]; fprev (may be NULL): F_prev
+ * [3][n]; force (may be NULL): the F of this step [3][n].
+ * ====================================================================== */
+
+/* node index with wrap on the periodic axes and the mirror across the walls
+ * of axis wa */
+static long mp_wall_idx(int x, int y, int z, const int *n, int wa, int *beyond) {
+  int p[3] = {x, y, z};
+  *beyond = 0;
+  for (int a = 0; a < 3; ++a) {
+    if (a == wa) {
+      if (p[a] < 0) { p[a] = -1 - p[a]; *beyond = 1; }
+      if (p[a] >= n[a]) { p[a] = 2 * n[a] - 1 - p[a]; *beyond = 1; }
+    } else {
+      p[a] = wrap(p[a], n[a]);
+    }
+  }
+  return idx3(p[0], p[1], p[2], n[0], n[1]);
+}
+
+static double mp_grad_pop(const or_lattice *L, int i, double rho, const double *u,
+                          const double Pi[3][3]) {
+  const double cs2 = 1.0 / 3.0;
+  double cu = 0.0, contr = 0.0;
+  for (int a = 0; a < 3; ++a) cu += L->c[i][a] * u[a];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      contr += (Pi[a][b] - (a == b ? rho * cs2 : 0.0)) *
+               (L->c[i][a] * L->c[i][b] - (a == b ? cs2 : 0.0));
+  return L->w[i] * (rho + rho * cu / cs2 + contr / (2.0 * cs2 * cs2));
+}
+
+int or_step_multiphase_wall(int lat, int nx, int ny, int nz, double beta, int mode, double kappa,
+                            int eos, const double *g_ext, double kappa_w, int wa,
+                            const double *fin, const double *fprev, double *fout, double *force) {
+  or_lattice L;
+  if (make_lattice(lat, &L)) return -1;
+  if (L.D == 2 && nz != 1) return -1;
+  if (wa < 0 || wa >= L.D) return -1;
+  const int n3[3] = {nx, ny, nz};
+  if (n3[wa] < 3) return -1;
+  const long n = (long)nx * ny * nz;
+  const int Q = L.Q;
+  double *f = (double *)malloc(sizeof(double) * Q * n);
+  double *uo = (double *)malloc(sizeof(double) * 3 * n);
+  double *rho = (double *)malloc(sizeof(double) * n);
+  double *phi = (double *)malloc(sizeof(double) * n);
+  double *lap = (double *)malloc(sizeof(double) * n);
+  if (!f || !uo || !rho || !phi || !lap) {
+    free(f); free(uo); free(rho); free(phi); free(lap);
+    return -2;
+  }
+  /* fluid velocity of the stored state */
+  for (long k = 0; k < n; ++k) {
+    double r = 0.0, j[3] = {0, 0, 0};
+    for (int i = 0; i < Q; ++i) {
+      r += fin[i * n + k];
+      for (int a = 0; a < 3; ++a) j[a] += L.c[i][a] * fin[i * n + k];
+    }
+    for (int a = 0; a < 3; ++a) uo[a * n + k] = (j[a] - (fprev ? 0.5 * fprev[a * n + k] : 0.0)) / r;
+  }
+  /* pulled populations; Grad fill at the wall nodes */
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        const int p0[3] = {x, y, z};
+        const long k = idx3(x, y, z, nx, ny);
+        int miss[OR_MAXQ], nmiss = 0;
+        for (int i = 0; i < Q; ++i) {
+          int bey;
+          const long ks = mp_wall_idx(x - L.c[i][0], y - L.c[i][1], z - L.c[i][2], n3, wa, &bey);
+          miss[i] = bey;
+          nmiss += bey;
+          if (!bey) f[i * n + k] = fin[i * n + ks];
+        }
+        if (!nmiss) continue;
+        double rho_t = 0.0, ut[3] = {0, 0, 0};
+        for (int i = 0; i < Q; ++i) {
+          if (!miss[i]) { rho_t += f[i * n + k]; continue; }
+          rho_t += fin[(Q - 1 - i) * n + k];
+          int p[3] = {x + L.c[i][0], y + L.c[i][1], z + L.c[i][2]};
+          if (p[wa] >= 0 && p[wa] < n3[wa]) {
+            int bey;
+            const long kn = mp_wall_idx(p[0], p[1], p[2], n3, wa, &bey);
+            for (int a = 0; a < 3; ++a) ut[a] += (0.5 * uo[a * n + kn] / 1.5) / nmiss;
+          }
+        }
+        /* grad u of the stored fluid velocity */
+        double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (int b = 0; b < L.D; ++b) {
+          int pp[3] = {x, y, z};
+          double um[3], up[3], um2[3], up2[3];
+          int inm = 1, inp = 1, inm2 = 1, inp2 = 1;
+          if (b == wa) {
+            inm = p0[b] - 1 >= 0; inp = p0[b] + 1 < n3[b];
+            inm2 = p0[b] - 2 >= 0; inp2 = p0[b] + 2 < n3[b];
+          }
+          for (int s = -2; s <= 2; ++s) {
+            if (!s) continue;
+            pp[0] = x; pp[1] = y; pp[2] = z;
+            pp[b] += s;
+            if (b == wa && (pp[b] < 0 || pp[b] >= n3[b])) continue;
+            int bey;
+            const long kk = mp_wall_idx(pp[0], pp[1], pp[2], n3, wa, &bey);
+            double *dst = s == -1 ? um : s == 1 ? up : s == -2 ? um2 : up2;
+            for (int a = 0; a < 3; ++a) dst[a] = uo[a * n + kk];
+          }
+          for (int a = 0; a < 3; ++a) {
+            const double u0 = uo[a * n + k];
+            if (inm && inp) G[a][b] = 0.5 * (up[a] - um[a]);
+            else if (inp) G[a][b] = inp2 ? 0.5 * (-3.0 * u0 + 4.0 * up[a] - up2[a]) : up[a] - u0;
+            else if (inm) G[a][b] = inm2 ? 0.5 * (3.0 * u0 - 4.0 * um[a] + um2[a]) : u0 - um[a];
+          }
+        }
+        /* the filled populations are pre-collision ones, whose momentum is
+         * rho u - F/2 for the fluid velocity u (exact difference method) */
+        if (fprev)
+          for (int a = 0; a < 3; ++a) ut[a] -= 0.5 * fprev[a * n + k] / rho_t;
+        double Pi[3][3];
+        const double cs2 = 1.0 / 3.0;
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b)
+            Pi[a][b] = (a == b ? rho_t * cs2 : 0.0) + rho_t * ut[a] * ut[b] -
+                       rho_t * cs2 / (2.0 * beta) * (G[a][b] + G[b][a]);
+        for (int i = 0; i < Q; ++i)
+          if (miss[i]) f[i * n + k] = mp_grad_pop(&L, i, rho_t, ut, Pi);
+      }
+  /* fields */
+  for (long k = 0; k < n; ++k) {
+    double r = 0.0;
+    for (int i = 0; i < Q; ++i) r += f[i * n + k];
+    rho[k] = r;
+    const double s = r / 3.0 - eos_pressure(eos, r);
+    phi[k] = sqrt(s > 0.0 ? s : 0.0);
+  }
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        const long k = idx3(x, y, z, nx, ny);
+        double acc = 0.0;
+        for (int i = 0; i < Q; ++i) {
+          int bey;
+          acc += L.w[i] * (rho[mp_wall_idx(x + L.c[i][0], y + L.c[i][1], z + L.c[i][2], n3, wa,
+                                           &bey)] - rho[k]);
+        }
+        lap[k] = 6.0 * acc;
+      }
+  double fo[OR_MAXQ];
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        const long k = idx3(x, y, z, nx, ny);
+        double dphi[3] = {0, 0, 0}, dlap[3] = {0, 0, 0}, sw[3] = {0, 0, 0};
+        for (int i = 0; i < Q; ++i) {
+          int bey;
+          const long kn = mp_wall_idx(x + L.c[i][0], y + L.c[i][1], z + L.c[i][2], n3, wa, &bey);
+          for (int a = 0; a < L.D; ++a) {
+            dphi[a] += 3.0 * L.w[i] * L.c[i][a] * phi[kn];
+            dlap[a] += 3.0 * L.w[i] * L.c[i][a] * lap[kn];
+            if (bey) sw[a] += L.w[i] * L.c[i][a];
+          }
+        }
+        double F[3] = {0, 0, 0}, du[3] = {0, 0, 0};
+        for (int a = 0; a < L.D; ++a) {
+          F[a] = 2.0 * phi[k] * dphi[a] + kappa * rho[k] * dlap[a] + kappa_w * rho[k] * sw[a];
+          if (g_ext) F[a] += rho[k] * g_ext[a];
+          du[a] = F[a] / rho[k];
+        }
+        if (force)
+          for (int a = 0; a < 3; ++a) force[a * n + k] = F[a];
+        double fl[OR_MAXQ];
+        for (int i = 0; i < Q; ++i) fl[i] = f[i * n + k];
+        collide_forced(&L, beta, mode, fl, du, fo);
+        for (int i = 0; i < Q; ++i) fout[i * n + k] = fo[i];
+      }
+  free(f); free(uo); free(rho); free(phi); free(lap);
+  return 0;
+}

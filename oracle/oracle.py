@@ -81,6 +81,8 @@ def _declare(L):
     L.or_eos.argtypes = [c_int, c_int, D, D]
     L.or_step_multiphase.argtypes = [c_int, c_int, c_int, c_int, c_double, c_int, c_double, c_int, D,
                                      D, D, D]
+    L.or_step_multiphase_wall.argtypes = [c_int, c_int, c_int, c_int, c_double, c_int, c_double, c_int,
+                                          D, c_double, c_int, D, D, D, D]
 
 
 def _p(a: np.ndarray):
@@ -353,6 +355,25 @@ def step_multiphase(lat, beta, f, kappa, eos_kind=0, g_ext=None, mode=0, want_fo
                                     _p(g) if g is not None else None, _p(f), _p(fo),
                                     _p(F) if F is not None else None))
     return (fo, F) if want_force else fo
+
+
+def step_multiphase_wall(lat, beta, f, kappa, kappa_w, wall_axis, F_prev=None, eos_kind=0,
+                         g_ext=None, mode=0):
+    """One multiphase step between two planar walls normal to wall_axis (x =
+    0, y = 1, z = 2; half a cell outside the faces, at rest; the other axes
+    periodic) with the wetting force of strength kappa_w; F_prev: the force
+    of the step that produced f (None: zero).  Returns (f_new, F)."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    _, nz, ny, nx = f.shape
+    fo = np.zeros_like(f)
+    F = np.zeros((3, nz, ny, nx))
+    g = None if g_ext is None else np.ascontiguousarray(g_ext, dtype=np.float64)
+    fp = None if F_prev is None else np.ascontiguousarray(F_prev, dtype=np.float64)
+    _check(lib().or_step_multiphase_wall(lat, nx, ny, nz, float(beta), int(mode), float(kappa),
+                                         int(eos_kind), _p(g) if g is not None else None,
+                                         float(kappa_w), int(wall_axis), _p(f),
+                                         _p(fp) if fp is not None else None, _p(fo), _p(F)))
+    return fo, F
 
 
 def macros_forced(lat, f, F):
