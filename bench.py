@@ -348,6 +348,7 @@ def run_ours(args):
         forms["coupled_turek_quasi2d"] = turek_leg(args)
         forms["coupled_c3"] = c3_leg(args)
         forms["multiphase_droplet_d3q27"] = mp_leg(args)
+        forms["multiphase_droplet_on_wall_d3q27"] = mp_wall_leg(args)
         forms["surrogate"] = {
             "measured_in": "tests/test_gpu_surrogate.py, tests/test_gpu_plate_surrogate.py",
             "why_not_here": "its training pairs come from coupled FP64 oracle runs, which this "
@@ -399,6 +400,10 @@ STATED_ERRORS = {
     "multiphase_droplet_d3q27": "one step 2e-6 W (FP32 populations), force 7e-7; this workload "
                                 "sampled after 2 steps: density 9e-8, velocity 6e-8; flat interface "
                                 "2000 steps 1e-6 of rho_l (tests/test_gpu_multiphase.py)",
+    "multiphase_droplet_on_wall_d3q27": "walls on every axis, 3 steps: 3e-6 W (FP32), 1.5e-14 W "
+                                        "(FP64); D3Q27 droplet on a wall 150 steps: density 2.2e-6; "
+                                        "FP64 droplet 400 steps 5.5e-14 "
+                                        "(tests/test_gpu_multiphase_walls.py)",
 }
 
 # Algorithmic HBM bytes per node of one multiphase step (FP32, D3Q27): the
@@ -537,6 +542,36 @@ def c3_leg(args):
     for name in ("f16n", "f16"):
         out[name]["speedup_vs_f32"] = out["f32"]["ms_per_step"] / out[name]["ms_per_step"]
     return out
+
+
+def mp_wall_leg(args, shape=(320, 250, 320), kappa=0.025, beta=0.6, kappa_w=-0.145):
+    """The multiphase model with walls: the droplet-impact domain with walls on
+    the two y faces (wetting strength kappa_w), a droplet of diameter 80
+    resting on the lower wall (FP32, one-node sweep; the wall fill adds two
+    kernels over the wall rows)."""
+    import torch
+    from paper_1710_02375_gb300 import synth
+    from paper_1710_02375_gb300.lbm import Lattice
+    nz, ny, nx = shape
+    nodes = nx * ny * nz
+    stream = torch.cuda.Stream()
+    L = Lattice(27, nx, ny, nz, beta, stream=stream, bc=(0, 0, 1, 1, 0, 0), multiphase=True)
+    L.set_multiphase(kappa, kappa_w=kappa_w)
+    dev = L.device
+    radius = min(40.0, 0.3 * min(shape))
+    rho = torch.from_numpy(synth.droplet_density(shape, radius, center=(nx / 2, 0.0, nz / 2),
+                                                 rho_l=7.5, rho_v=0.08)).to(dev)
+    L.init_equilibrium(rho, torch.zeros((3,) + shape, dtype=torch.float64, device=dev))
+    del rho
+    L.step(10)
+    chunk, reps = 10, 10
+    L.step_graph(chunk, 1)
+    ms = _timed(stream, lambda k: L.step_graph(chunk, k), reps) / chunk
+    L.check()
+    L.close()
+    return {"ms_per_step": ms, "mlups": nodes / (ms * 1e-3) / 1e6, "steps": chunk * reps,
+            "config": f"D3Q27 {nx}x{ny}x{nz}, walls on the y faces (kappa_w={kappa_w}), droplet "
+                      f"D=80 on the lower wall, kappa={kappa}, beta={beta}, FP32"}
 
 
 def mp_leg(args, shape=(320, 250, 320), kappa=0.025, beta=0.6):
@@ -783,7 +818,8 @@ def main():
         import __graft_entry__
         __graft_entry__.build()
         shape = tuple(int(v) for v in args.mp_shape.split(","))
-        print(json.dumps({"workload": "multiphase", **mp_leg(args, shape=shape)}), flush=True)
+        print(json.dumps({"workload": "multiphase", **mp_leg(args, shape=shape),
+                          "walls": mp_wall_leg(args, shape=shape)}), flush=True)
     else:
         run_ours(args)
 

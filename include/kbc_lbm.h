@@ -515,15 +515,26 @@ lbm_status lbm_set_sweep_variant(lbm_ctx *ctx, int variant);
  * polynomial of Eq. (eos) (coexisting densities about 7.55 and 0.073), or
  * LBM_EOS_IDEAL, p = rho c_s^2 (phi = 0).  g: a uniform acceleration.
  *
- * Scope: every face periodic, no immersed bodies; FP32 storage (D2Q9 and
- * D3Q27) or FP64 storage (D2Q9).  The lattice must be created with
- * lbm_config.multiphase = 1 (the workspace then holds one density and one
- * (phi, lap rho) pair per node in the compute precision).
+ * Walls: the two faces of one axis may be LBM_BC_WALL at rest (the other
+ * faces periodic): the wall nodes get Grad's approximation of their missing
+ * populations (the face-wall targets at q = 1/2, with the pre-collision
+ * target velocity u - F/(2 rho) of the exact difference method and the
+ * velocities of the previous step taken as fluid velocities (j - F/2) /
+ * rho), the fields of the stencils are mirrored across the walls, and the
+ * wetting force F_s = kappa_w rho sum_i W_i s(x + c_i) c_i (s = 1 beyond a
+ * wall; the paper leaves the weights open) is added to F.  kappa_w < 0 is
+ * hydrophobic, > 0 hydrophilic.
+ *
+ * Scope: periodic faces or one pair of walls, no immersed bodies; FP32
+ * storage (D2Q9 and D3Q27) or FP64 storage (D2Q9).  The lattice must be
+ * created with lbm_config.multiphase = 1 (the workspace then holds the
+ * densities and (phi, lap rho) pairs per node in the compute precision).
  *
  * lbm_set_multiphase switches the context to the multiphase step (params
  * copied; NULL switches back to the single-phase step).  LBM_EINVAL for a
- * context outside the scope, kappa < 0 or an unknown eos; LBM_ESTATE when
- * the context was created without multiphase = 1.
+ * context outside the scope (other face kinds, moving walls), kappa < 0,
+ * non-finite values or an unknown eos; LBM_ESTATE when the context was
+ * created without multiphase = 1.
  * While the model is on, lbm_get_macros / lbm_get_macros_f32 return the
  * fluid velocity (j - F/2) / rho of the stored post-collision state, F the
  * force of the step that produced it (F = 0 before the first step and after
@@ -535,6 +546,7 @@ typedef struct {
   double kappa;   /* capillary coefficient of Eq. (Korteweg), >= 0 */
   int eos;        /* LBM_EOS_* */
   double g[3];    /* uniform acceleration (lattice units) */
+  double kappa_w; /* wetting strength of the walls (ignored without walls) */
 } lbm_multiphase_params;
 lbm_status lbm_set_multiphase(lbm_ctx *ctx, const lbm_multiphase_params *params);
 lbm_status lbm_get_force_field(lbm_ctx *ctx, double *F);

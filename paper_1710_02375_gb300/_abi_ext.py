@@ -53,6 +53,7 @@ class lbm_multiphase_params(ctypes.Structure):
         ("kappa", ctypes.c_double),
         ("eos", ctypes.c_int),
         ("g", ctypes.c_double * 3),
+        ("kappa_w", ctypes.c_double),
     ]
 
 

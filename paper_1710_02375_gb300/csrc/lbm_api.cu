@@ -34,6 +34,7 @@ struct Layout {
   size_t sbox;                             // bounding box of the surface (6 floats)
   size_t mp_rho[2], mp_pl;                 // multiphase fields (0: not reserved)
   size_t mp_ctl, mp_partial;               // momentum-controller state, CTA partials
+  size_t mp_band;                          // wall-band scratch (walls in the multiphase model)
   int nface, bcap, inlet_n[6];
   size_t total;
 };
@@ -90,7 +91,7 @@ Layout make_layout(const lbm_config &c) {
   L.tvforce = off; off += align_up(sizeof(double) * 3 * (size_t)std::max(nv, 1));
   L.tbforce = off; off += align_up(sizeof(double) * 3 * kMaxBodies);
   L.sbox = off; off += align_up(sizeof(float) * 8);
-  L.mp_rho[0] = L.mp_rho[1] = L.mp_pl = L.mp_ctl = L.mp_partial = 0;
+  L.mp_rho[0] = L.mp_rho[1] = L.mp_pl = L.mp_ctl = L.mp_partial = L.mp_band = 0;
   if (c.multiphase) {
     // two density buffers (the reference of the stored state, the density
     // of the step being computed) and (phi, lap rho) per stored node, in the
@@ -102,6 +103,8 @@ Layout make_layout(const lbm_config &c) {
     L.mp_ctl = off; off += align_up(sizeof(double) * kMpControl);
     L.mp_partial = off;
     off += align_up(mp_partial_bytes(c.nx, c.ny, c.nz));
+    L.mp_band = off;
+    off += align_up(mp_band_bytes(c.nx, c.ny, c.nz, (int)cb));
   }
   for (int fc = 0; fc < 6; ++fc) {
     L.inlet_n[fc] = 0;
@@ -520,9 +523,23 @@ lbm_status lbm_set_multiphase(lbm_ctx *ctx, const lbm_multiphase_params *params)
   }
   if (!ctx->cfg.multiphase)
     return fail(ctx, LBM_ESTATE, "lbm_set_multiphase: context created without multiphase = 1");
-  for (int fc = 0; fc < 6; ++fc)
-    if (ctx->cfg.bc[fc] != LBM_BC_PERIODIC)
-      return fail(ctx, LBM_EINVAL, "lbm_set_multiphase: every face must be periodic");
+  // fully periodic, or two walls at rest on the faces of one axis
+  int wall = -1;
+  const int naxes = ctx->Q == 9 ? 2 : 3;
+  for (int a = 0; a < naxes; ++a) {
+    const int lo = ctx->cfg.bc[2 * a], hi = ctx->cfg.bc[2 * a + 1];
+    if (lo == LBM_BC_PERIODIC && hi == LBM_BC_PERIODIC) continue;
+    if (lo != LBM_BC_WALL || hi != LBM_BC_WALL || wall >= 0)
+      return fail(ctx, LBM_EINVAL,
+                  "lbm_set_multiphase: faces must be periodic, or walls on both faces of one axis");
+    for (int fc = 2 * a; fc < 2 * a + 2; ++fc)
+      for (int b = 0; b < 3; ++b)
+        if (ctx->cfg.face_velocity[fc][b] != 0.0)
+          return fail(ctx, LBM_EINVAL, "lbm_set_multiphase: the walls must be at rest");
+    wall = a;
+  }
+  if (!std::isfinite(params->kappa_w))
+    return fail(ctx, LBM_EINVAL, "lbm_set_multiphase: non-finite kappa_w");
   if (ctx->nbodies > 0 || ctx->fem || ctx->shell)
     return fail(ctx, LBM_EINVAL, "lbm_set_multiphase: immersed bodies are not supported");
   if (ctx->cfg.storage != LBM_STORE_F32 && ctx->cfg.storage != LBM_STORE_F64)
@@ -535,6 +552,8 @@ lbm_status lbm_set_multiphase(lbm_ctx *ctx, const lbm_multiphase_params *params)
     if (!std::isfinite(params->g[a]))
       return fail(ctx, LBM_EINVAL, "lbm_set_multiphase: non-finite acceleration");
   ctx->mp.kappa = params->kappa;
+  ctx->mp.kappa_w = wall >= 0 ? params->kappa_w : 0.0;
+  ctx->mp.wall = wall;
   ctx->mp.eos = params->eos == LBM_EOS_IDEAL ? MP_EOS_IDEAL : MP_EOS_PAPER;
   for (int a = 0; a < 3; ++a) ctx->mp.g[a] = (a < 2 || ctx->Q == 27) ? params->g[a] : 0.0;
   if (!ctx->mp_on) {
@@ -581,7 +600,8 @@ lbm_status lbm_step(lbm_ctx *ctx, int n) {
   if (n < 0) return fail(ctx, LBM_EINVAL, "lbm_step: n < 0");
   const double beta = ctx->cfg.beta;
   const int bgk = ctx->cfg.collision == LBM_COLLIDE_BGK;
-  const bool bnd = ctx->nface > 0 || ctx->nbodies > 0;
+  // the multiphase step fills its wall nodes itself
+  const bool bnd = (ctx->nface > 0 || ctx->nbodies > 0) && !ctx->mp_on;
   const int cap = ctx->nface + (ctx->nbodies > 0 ? ctx->cfg.max_links : 0);
   for (int t = 0; t < n; ++t) {
     if (bnd) {
@@ -604,7 +624,8 @@ lbm_status lbm_step(lbm_ctx *ctx, int n) {
       CK(launch_mp_step(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur], ctx->f[1 - ctx->cur],
                         ctx->ws + ctx->lay.mp_rho[ctx->mp_cur],
                         ctx->ws + ctx->lay.mp_rho[1 - ctx->mp_cur], ctx->ws + ctx->lay.mp_pl,
-                        mp_ctl(ctx), (double *)(ctx->ws + ctx->lay.mp_partial), ctx->mp, beta,
+                        mp_ctl(ctx), (double *)(ctx->ws + ctx->lay.mp_partial),
+                        ctx->ws + ctx->lay.mp_band, ctx->mp_have_force ? 1 : 0, ctx->mp, beta,
                         bgk, ctx->err, ctx->stream));
       ctx->mp_cur = 1 - ctx->mp_cur;
       ctx->mp_have_force = true;

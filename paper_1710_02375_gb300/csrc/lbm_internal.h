@@ -65,11 +65,22 @@ cudaError_t launch_macros(int Q, int storage, const Grid &g, const void *f, cons
 // ---- multiphase model (periodic lattices; FP32 storage, or FP64 for D2Q9)
 enum { MP_EOS_PAPER = 0, MP_EOS_IDEAL = 1 };
 struct MpParams {
-  double kappa;  // capillary coefficient
-  double g[3];   // uniform acceleration (F gains rho g)
-  int eos;       // MP_EOS_*
-  int pair;      // FP32: the two-node form of the forced sweep
+  double kappa;    // capillary coefficient
+  double g[3];     // uniform acceleration (F gains rho g)
+  double kappa_w;  // wetting strength (walls only)
+  int eos;         // MP_EOS_*
+  int pair;        // FP32: the two-node form of the forced sweep
+  int wall;        // axis normal to the two planar walls, -1: fully periodic
 };
+// Rows of the wall-band scratch per wall side: the fluid velocity and the
+// force of the previous step on the first three interior rows.
+constexpr int kMpBandRows = 3;
+// Bytes of that scratch: 2 sides x 3 rows x 6 values x the largest plane.
+inline size_t mp_band_bytes(int nx, int ny, int nz, int cb) {
+  const long long a = (long long)nx * ny, b = (long long)ny * nz, c = (long long)nx * nz;
+  const long long m = a > b ? (a > c ? a : c) : (b > c ? b : c);
+  return (size_t)cb * 2 * kMpBandRows * 6 * (size_t)m;
+}
 // One multiphase step fin -> fout: density pass (rho, phi), Laplacian pass
 // (lap rho), forced sweep.  Populations are stored as f_i - W_i R(x), R the
 // node's density of the step that wrote them: fin relative to rref, fout
@@ -85,9 +96,13 @@ struct MpParams {
 constexpr int kMpControl = 12;
 constexpr int kMpPartialDoubles = 4;
 constexpr int kMpGroupCtas = 128;
-cudaError_t launch_mp_step(int Q, int storage, const Grid &g, const void *fin, void *fout,
+// With walls (mp.wall >= 0) the step first fills the missing populations
+// of the wall nodes into the ghost slots of fin (Grad), using band (scratch
+// of mp_band_bytes) and the force of the previous step when have_force.
+cudaError_t launch_mp_step(int Q, int storage, const Grid &g, void *fin, void *fout,
                            const void *rref, void *rho, void *pl, double *ctl, double *partial,
-                           const MpParams &mp, double beta, int bgk, int *err, cudaStream_t s);
+                           void *band, int have_force, const MpParams &mp, double beta, int bgk,
+                           int *err, cudaStream_t s);
 // CTA shape and count of the multiphase kernels over an nx * ny * nz lattice.
 struct MpGrid {
   int bx, by;

@@ -195,6 +195,37 @@ __device__ __forceinline__ double mp_ac<double>(const double *ctl, int a) {
   return ctl[a];
 }
 
+// ---------------------------------------------------------------- walls
+// Two planar walls half a cell outside the faces normal to axis wa (stored
+// rows lo and hi are the first and last interior rows; the ghost rows lo - 1
+// and hi + 1 hold, for the stencils, the fields of the row across the wall,
+// and in their population slots the Grad-filled populations of the wall
+// nodes).  kw: wetting strength.
+template <class C>
+struct MpWallT {
+  int wa, lo, hi;
+  C kw;
+};
+// -1 / +1 on the first / last interior row along the wall axis, else 0
+template <class C>
+__device__ __forceinline__ int mp_side(const MpWallT<C> &w, int X, int Y, int Z) {
+  if (w.wa < 0) return 0;
+  const int p = w.wa == 0 ? X : (w.wa == 1 ? Y : Z);
+  return p == w.lo ? -1 : (p == w.hi ? 1 : 0);
+}
+// stored-index step along the wall axis
+template <class C>
+__device__ __forceinline__ long long mp_wall_stride(const Grid &g, const MpWallT<C> &w) {
+  return w.wa == 0 ? 1LL : (w.wa == 1 ? (long long)g.pitch : (long long)g.pitch * g.NY);
+}
+// Wetting force F_s = kw rho sum_i W_i s(x + c_i) c_i: on the first row the
+// ghost neighbours (c_wa = -1) weigh 1/6 in total, so F_s = -kw rho / 6
+// along the wall normal; +kw rho / 6 on the last row.
+template <class C>
+__device__ __forceinline__ void mp_wet(const MpWallT<C> &w, int side, C r, C (&F)[3]) {
+  if (side) F[w.wa] += (C)side * w.kw * r * (C)(1.0 / 6.0);
+}
+
 // ---------------------------------------------------------------- pass 1
 // Pulled populations of a node as deviations from W_i R0 (R0 the node's new
 // reference), the sources stored relative to their own references rref.
@@ -222,7 +253,7 @@ __global__ void __launch_bounds__(128)
                  typename Store<S>::C *__restrict__ rho,
                  typename Vec2<typename Store<S>::C>::T *__restrict__ pl, int eos,
                  const double *__restrict__ partial, double *__restrict__ gpart, long long nblk,
-                 int *__restrict__ err) {
+                 MpWallT<typename Store<S>::C> wl, int *__restrict__ err) {
   using C = typename Store<S>::C;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -246,8 +277,16 @@ __global__ void __launch_bounds__(128)
     const C r = mean_ref + d;
     if (!(r > (C)0 && r < (C)1e30)) atomicOr(err, 1);
     const C s = r * (C)(1.0 / 3.0) - mp_pressure(r, eos);
+    const C ph = s > (C)0 ? sqrt(s) : (C)0;
     rho[k] = r;
-    pl[k].x = s > (C)0 ? sqrt(s) : (C)0;
+    pl[k].x = ph;
+    // the ghost row across a wall mirrors the first / last row
+    const int side = mp_side(wl, x + g.px, y + g.py, z + g.pz);
+    if (side) {
+      const long long kg = (long long)k + side * mp_wall_stride(g, wl);
+      rho[kg] = r;
+      pl[kg].x = ph;
+    }
   }
   mp_stage1(partial, nblk, gpart,
             ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
@@ -260,7 +299,7 @@ __global__ void __launch_bounds__(128)
 template <int Q, class C, typename IX>
 __device__ __forceinline__ void mp_lap_node(const Grid &g, const C *__restrict__ rho,
                                             typename Vec2<C>::T *__restrict__ pl, int x, int y,
-                                            int z) {
+                                            int z, const MpWallT<C> &wl) {
   using L = Lat<Q>;
   const Nbhd<L::D, IX> nb(g, x + g.px, y + g.py, z + g.pz);
   const IX k = nb.at(0, 0, 0);
@@ -275,21 +314,26 @@ __device__ __forceinline__ void mp_lap_node(const Grid &g, const C *__restrict__
                    (C)(2.0 / 3.0) * __ldg(rho + row + nb.xo[1]);
       acc += (C)((L::D == 3 ? w1d(cz) : 1.0) * w1d(cy)) * sw;
     }
-  pl[k].y = (C)6 * (acc - r0);
+  const C lp = (C)6 * (acc - r0);
+  pl[k].y = lp;
+  const int side = mp_side(wl, x + g.px, y + g.py, z + g.pz);
+  if (side) pl[(long long)k + side * mp_wall_stride(g, wl)].y = lp;
 }
 
 template <int Q, class C, typename IX>
 __global__ void __launch_bounds__(128)
     k_mp_lap(Grid g, const C *__restrict__ rho, typename Vec2<C>::T *__restrict__ pl,
              const double *__restrict__ gpart, long long nblk, double gx, double gy, double gz,
-             double *__restrict__ ctl) {
+             double *__restrict__ ctl, MpWallT<C> wl) {
   using L = Lat<Q>;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
-  if (x < g.nx && y < g.ny) mp_lap_node<Q, C, IX>(g, rho, pl, x, y, z);
-  mp_stage2(gpart, nblk, gx, gy, gz, ctl,
-            ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
+  if (x < g.nx && y < g.ny) mp_lap_node<Q, C, IX>(g, rho, pl, x, y, z, wl);
+  // walls take momentum: the controller runs on fully periodic lattices only
+  if (wl.wa < 0)
+    mp_stage2(gpart, nblk, gx, gy, gz, ctl,
+              ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
 }
 
 // F at a node from the fields: 2 phi d(phi) + kappa rho d(lap rho) + rho g.
@@ -379,7 +423,7 @@ __global__ void __launch_bounds__(128, KBC_MP_CTAS)
                typename Store<S>::C beta, typename Store<S>::C kappa, typename Store<S>::C gx,
                typename Store<S>::C gy, typename Store<S>::C gz, int bgk,
                const double *__restrict__ ctl, double *__restrict__ partial, long long nblk,
-               int *__restrict__ err) {
+               MpWallT<typename Store<S>::C> wl, int *__restrict__ err) {
   using L = Lat<Q>;
   using C = typename Store<S>::C;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -392,6 +436,7 @@ __global__ void __launch_bounds__(128, KBC_MP_CTAS)
     const C ac[3] = {mp_ac<C>(ctl, 0), mp_ac<C>(ctl, 1), mp_ac<C>(ctl, 2)};
     C r, F[3];
     mp_force<Q, C, IX>(rho, pl, nb, kappa, gx, gy, gz, r, F);
+    mp_wet(wl, mp_side(wl, x + g.px, y + g.py, z + g.pz), r, F);
     const C ir = (C)1 / r;
     C v[Q];
     // the new reference of the node: its density of this step
@@ -441,7 +486,7 @@ __global__ void __launch_bounds__(128, KBC_MP_PAIR_CTAS)
                 const float *__restrict__ rref, const float *__restrict__ rho,
                 const float2 *__restrict__ pl, float beta, float kappa, float gx, float gy,
                 float gz, int bgk, const double *__restrict__ ctl, double *__restrict__ partial,
-                long long nblk, int *__restrict__ err) {
+                long long nblk, MpWallT<float> wl, int *__restrict__ err) {
   using L = Lat<Q>;
   using St = Store<STORE_F32>;
   const int x = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
@@ -456,6 +501,9 @@ __global__ void __launch_bounds__(128, KBC_MP_PAIR_CTAS)
     float ra, rb, Fa[3], Fb[3];
     mp_force<Q, float, IX>(rho, pl, na, kappa, gx, gy, gz, ra, Fa);
     mp_force<Q, float, IX>(rho, pl, nb, kappa, gx, gy, gz, rb, Fb);
+    // the pair shares Y and Z, and walls normal to x are not paired
+    mp_wet(wl, mp_side(wl, X, Y, Z), ra, Fa);
+    mp_wet(wl, mp_side(wl, ib ? X + 1 : X, Y, Z), rb, Fb);
     const IX N = (IX)g.N;
     f2 v[Q];
 #pragma unroll
@@ -531,8 +579,9 @@ __global__ void k_mp_read(Grid g, const typename Store<S>::T *__restrict__ f,
                           const typename Vec2<typename Store<S>::C>::T *__restrict__ pl,
                           typename Store<S>::C kappa, typename Store<S>::C gx,
                           typename Store<S>::C gy, typename Store<S>::C gz, int have_force,
-                          const double *__restrict__ mean, long long begin, long long count,
-                          long long stride, double *F, O *rho_out, O *u, double *fabs) {
+                          const double *__restrict__ mean, MpWallT<typename Store<S>::C> wl,
+                          long long begin, long long count, long long stride, double *F,
+                          O *rho_out, O *u, double *fabs) {
   using L = Lat<Q>;
   using St = Store<S>;
   using C = typename St::C;
@@ -547,6 +596,7 @@ __global__ void k_mp_read(Grid g, const typename Store<S>::T *__restrict__ f,
   if (have_force) {
     const Nbhd<L::D, long long> nb(g, X, Y, Z);
     mp_force<Q, C, long long>(rref, pl, nb, kappa, gx, gy, gz, rdummy, Fv);
+    mp_wet(wl, mp_side(wl, X, Y, Z), rdummy, Fv);
     // the correcting force the step used
     for (int a = 0; a < L::D; ++a) Fv[a] -= rdummy * (C)mean[a];
   }
@@ -599,63 +649,256 @@ __global__ void k_mp_rebase(Grid g, typename Store<S>::T *__restrict__ f,
   rref[k] = Rnew;
 }
 
+// rref := Rnew over every stored node (ghost rows and row padding included:
+// the ghost slots of a wall are filled relative to their reference).
+template <class C>
+__global__ void k_mp_fill_ref(C *__restrict__ rref, long long N, C Rnew) {
+  const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k < N) rref[k] = Rnew;
+}
+
+// ---------------------------------------------------------------- wall fill
+// Grad's approximation for the populations that the wall nodes (first and
+// last interior rows along the wall axis) miss, written into the ghost slots
+// they pull from.  Readings (as for face walls at q = 1/2, at rest): rho_t =
+// the known pulled populations plus the node's own stored f'_opp(i); u_t =
+// mean over the missing set of u(x_b + c_i) / 3, minus F_prev(x_b) / (2
+// rho_t) (the pulled populations carry rho u - F/2); grad u of the fluid
+// velocity by central differences along the wall, one-sided second order
+// across it; Pi = rho c_s^2 I + rho u u - rho c_s^2/(2 beta)(grad u + grad
+// u^T).  u(x) = (j' - F_prev/2) / rho' of the stored state, F_prev the force
+// of the step that produced it (zero without one).
+//
+// Band scratch: band[((s * 3 + r) * 6 + q) * plane + p], side s (0: first
+// rows, 1: last rows), row r from the wall, q = 0..2 the velocity and 3..5
+// the force, p = t1 + n[a1] t2 over the two other axes a1 < a2.
+struct MpPlane {
+  int wa, a1, a2, n[3], pad[3];
+  long long plane;
+};
+__device__ __forceinline__ void mp_plane_node(const MpPlane &pl, int s, int r, long long p,
+                                              int (&X)[3]) {
+  const int t1 = (int)(p % pl.n[pl.a1]), t2 = (int)(p / pl.n[pl.a1]);
+  X[pl.a1] = t1 + pl.pad[pl.a1];
+  X[pl.a2] = t2 + pl.pad[pl.a2];
+  X[pl.wa] = pl.pad[pl.wa] + (s == 0 ? r : pl.n[pl.wa] - 1 - r);
+}
+
+template <int Q, int S, typename IX>
+__global__ void __launch_bounds__(128)
+    k_mp_wall_band(Grid g, const typename Store<S>::T *__restrict__ f,
+                   const typename Store<S>::C *__restrict__ rref,
+                   const typename Vec2<typename Store<S>::C>::T *__restrict__ fields,
+                   typename Store<S>::C kappa, typename Store<S>::C gx, typename Store<S>::C gy,
+                   typename Store<S>::C gz, MpWallT<typename Store<S>::C> wl, MpPlane mpl,
+                   int have_force, typename Store<S>::C *__restrict__ band) {
+  using L = Lat<Q>;
+  using St = Store<S>;
+  using C = typename St::C;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= 2 * kMpBandRows * mpl.plane) return;
+  const int sr = (int)(t / mpl.plane);
+  const int s = sr / kMpBandRows, r = sr % kMpBandRows;
+  const long long p = t % mpl.plane;
+  int X[3];
+  mp_plane_node(mpl, s, r, p, X);
+  const Nbhd<L::D, IX> nb(g, X[0], X[1], X[2]);
+  const IX k = nb.at(0, 0, 0);
+  C d = (C)0, j[3] = {(C)0, (C)0, (C)0};
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const C v = St::load(f + ((IX)i * (IX)g.N + k), (C)weight<L>(i));
+    d += v;
+    j[0] += (C)L::cx(i) * v;
+    j[1] += (C)L::cy(i) * v;
+    j[2] += (C)L::cz(i) * v;
+  }
+  const C rs = rref[k] + d;  // density of the stored state
+  C F[3] = {(C)0, (C)0, (C)0};
+  if (have_force) {
+    C rf;
+    mp_force<Q, C, IX>(rref, fields, nb, kappa, gx, gy, gz, rf, F);
+    mp_wet(wl, mp_side(wl, X[0], X[1], X[2]), rf, F);
+  }
+  C *out = band + (long long)sr * 6 * mpl.plane + p;
+  for (int a = 0; a < 3; ++a) {
+    out[a * mpl.plane] = (j[a] - (C)0.5 * F[a]) / rs;
+    out[(3 + a) * mpl.plane] = F[a];
+  }
+}
+
+template <int Q, int S, typename IX>
+__global__ void __launch_bounds__(128)
+    k_mp_wall_fill(Grid g, typename Store<S>::T *__restrict__ f,
+                   const typename Store<S>::C *__restrict__ rref,
+                   const typename Store<S>::C *__restrict__ band, MpPlane mpl,
+                   typename Store<S>::C beta) {
+  using L = Lat<Q>;
+  using St = Store<S>;
+  using C = typename St::C;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= 2 * mpl.plane) return;
+  const int s = (int)(t / mpl.plane);
+  const long long p = t % mpl.plane;
+  int X[3];
+  mp_plane_node(mpl, s, 0, p, X);
+  const Nbhd<L::D, IX> nb(g, X[0], X[1], X[2]);
+  const IX k = nb.at(0, 0, 0);
+  const IX N = (IX)g.N;
+  const int inward = s == 0 ? 1 : -1;  // stored-coordinate direction away from the wall
+  const int t1 = (int)(p % mpl.n[mpl.a1]), t2 = (int)(p / mpl.n[mpl.a1]);
+  // band value q of row r at tangential offsets (o1, o2), periodic along the wall
+  auto bv = [&](int r, int o1, int o2, int q) -> C {
+    int u1 = t1 + o1, u2 = t2 + o2;
+    const int n1 = mpl.n[mpl.a1], n2 = mpl.n[mpl.a2];
+    u1 = u1 < 0 ? u1 + n1 : (u1 >= n1 ? u1 - n1 : u1);
+    u2 = u2 < 0 ? u2 + n2 : (u2 >= n2 ? u2 - n2 : u2);
+    return band[((long long)(s * kMpBandRows + r) * 6 + q) * mpl.plane + u1 +
+                (long long)n1 * u2];
+  };
+  auto cax = [&](int i, int a) { return a == 0 ? L::cx(i) : (a == 1 ? L::cy(i) : L::cz(i)); };
+  const C R = rref[k];
+  C rho_t = (C)0, ut[3] = {(C)0, (C)0, (C)0};
+  int nmiss = 0;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const C w = (C)weight<L>(i);
+    if (cax(i, mpl.wa) == inward) {  // the source x_b - c_i lies beyond the wall
+      ++nmiss;
+      rho_t += St::load(f + ((IX)(Q - 1 - i) * N + k), w) + w * R;
+      for (int a = 0; a < 3; ++a)
+        ut[a] += bv(1, cax(i, mpl.a1), cax(i, mpl.a2), a) * (C)(1.0 / 3.0);
+    } else {
+      const IX src = nb.at(-L::cx(i), -L::cy(i), -L::cz(i));
+      rho_t += St::load(f + ((IX)i * N + src), w) + w * __ldg(rref + src);
+    }
+  }
+  const C im = (C)1 / (C)nmiss;
+  for (int a = 0; a < 3; ++a) ut[a] = ut[a] * im - (C)0.5 * bv(0, 0, 0, 3 + a) / rho_t;
+  // grad u, G[a][b] = d u_a / d x_b
+  C G[3][3] = {{(C)0, (C)0, (C)0}, {(C)0, (C)0, (C)0}, {(C)0, (C)0, (C)0}};
+  for (int b = 0; b < L::D; ++b)
+    for (int a = 0; a < 3; ++a) {
+      if (b == mpl.wa) {
+        const C u0 = bv(0, 0, 0, a), u1 = bv(1, 0, 0, a), u2 = bv(2, 0, 0, a);
+        G[a][b] = (C)(0.5 * inward) * ((C)-3 * u0 + (C)4 * u1 - u2);
+      } else {
+        const int o1 = b == mpl.a1 ? 1 : 0, o2 = b == mpl.a2 ? 1 : 0;
+        G[a][b] = (C)0.5 * (bv(0, o1, o2, a) - bv(0, -o1, -o2, a));
+      }
+    }
+  const C cs2 = (C)(1.0 / 3.0);
+  C Pn[3][3];  // Pi - rho c_s^2 I
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      Pn[a][b] = rho_t * ut[a] * ut[b] - rho_t * cs2 / ((C)2 * beta) * (G[a][b] + G[b][a]);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    if (cax(i, mpl.wa) != inward) continue;
+    const int c[3] = {L::cx(i), L::cy(i), L::cz(i)};
+    C cu = (C)0, contr = (C)0;
+    for (int a = 0; a < 3; ++a) cu += (C)c[a] * ut[a];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b)
+        contr += Pn[a][b] * ((C)(c[a] * c[b]) - (a == b ? cs2 : (C)0));
+    const C w = (C)weight<L>(i);
+    const C fs = w * (rho_t + rho_t * cu / cs2 + contr / ((C)2 * cs2 * cs2));
+    const IX src = nb.at(-c[0], -c[1], -c[2]);  // the ghost slot it is pulled from
+    St::store(f + ((IX)i * N + src), fs - w * __ldg(rref + src), (C)(1.0 / weight<L>(i)));
+  }
+}
+
 // ---------------------------------------------------------------- launchers
 static dim3 mp_block(const Grid &g) {
   const MpGrid m = mp_grid(g.nx, g.ny, g.nz);
   return dim3(m.bx, m.by, 1);
 }
 
-template <int Q, int S>
-static cudaError_t mp_step_t(const Grid &g, const void *fin, void *fout, const void *rref,
-                             void *rho, void *pl, double *ctl, double *partial,
-                             const MpParams &mp, double beta, int bgk, int *err, cudaStream_t s) {
-  // partial: [4][nblk] CTA sums of the sweep, then [4][ngroups] group sums
-  double *gpart = partial + kMpPartial * mp_grid(g.nx, g.ny, g.nz).blocks;
+// Wall description of a grid for the kernels (wa < 0: fully periodic).
+template <class C>
+static MpWallT<C> mp_wall_of(const Grid &g, const MpParams &mp) {
+  MpWallT<C> w;
+  w.wa = mp.wall;
+  w.kw = (C)mp.kappa_w;
+  w.lo = w.hi = -1;
+  if (mp.wall >= 0) {
+    const int n[3] = {g.nx, g.ny, g.nz}, pad[3] = {g.px, g.py, g.pz};
+    w.lo = pad[mp.wall];
+    w.hi = pad[mp.wall] + n[mp.wall] - 1;
+  }
+  return w;
+}
+static MpPlane mp_plane_of(const Grid &g, int wa) {
+  MpPlane m;
+  m.wa = wa;
+  m.a1 = wa == 0 ? 1 : 0;
+  m.a2 = wa == 2 ? 1 : 2;
+  m.n[0] = g.nx; m.n[1] = g.ny; m.n[2] = g.nz;
+  m.pad[0] = g.px; m.pad[1] = g.py; m.pad[2] = g.pz;
+  m.plane = (long long)m.n[m.a1] * m.n[m.a2];
+  return m;
+}
+
+template <int Q, int S, typename IX>
+static void mp_launch_all(const Grid &g, void *fin, void *fout, const void *rref, void *rho,
+                          void *pl, double *ctl, double *partial, double *gpart, void *band,
+                          int have_force, const MpParams &mp, double beta, int bgk, int *err,
+                          cudaStream_t s) {
   using T = typename Store<S>::T;
   using C = typename Store<S>::C;
   using C2 = typename Vec2<C>::T;
+  const MpWallT<C> wl = mp_wall_of<C>(g, mp);
   const dim3 b = mp_block(g);
   const dim3 grid((g.nx + b.x - 1) / b.x, (g.ny + b.y - 1) / b.y, g.nz);
   const long long nblk = (long long)grid.x * grid.y * grid.z;
-  // the sweep: two-node form for FP32 storage (its own CTA grid)
-  const bool pair = S == STORE_F32 && mp.pair;
+  // the sweep: two-node form for FP32 storage when x is periodic (its pairs
+  // start on even stored columns), with its own CTA grid
+  const bool pair = S == STORE_F32 && mp.pair && g.px == 0;
   const int npairs = (g.nx + 1) / 2;
   const dim3 b2 = npairs >= 128 ? dim3(128, 1, 1) : dim3(32, 4, 1);
   const dim3 grid2((npairs + b2.x - 1) / b2.x, (g.ny + b2.y - 1) / b2.y, g.nz);
   const long long nblk_sweep = pair ? (long long)grid2.x * grid2.y * grid2.z : nblk;
-  // 32-bit offsets when every population offset fits
-  if ((long long)Q * g.N < (1LL << 31)) {
-    k_mp_density<Q, S, int><<<grid, b, 0, s>>>(g, (const T *)fin, (const C *)rref, (C *)rho,
-                                               (C2 *)pl, mp.eos, partial, gpart, nblk_sweep, err);
-    k_mp_lap<Q, C, int><<<grid, b, 0, s>>>(g, (const C *)rho, (C2 *)pl, gpart, nblk_sweep,
-                                           mp.g[0], mp.g[1], mp.g[2], ctl);
-    if (pair)
-      k_mp_sweep2<Q, int><<<grid2, b2, 0, s>>>(g, (const float *)fin, (float *)fout,
-                                               (const float *)rref, (const float *)rho,
-                                               (const float2 *)pl, (float)beta, (float)mp.kappa,
-                                               (float)mp.g[0], (float)mp.g[1], (float)mp.g[2], bgk,
-                                               ctl, partial, nblk_sweep, err);
-    else
-      k_mp_sweep<Q, S, int><<<grid, b, 0, s>>>(g, (const T *)fin, (T *)fout, (const C *)rref,
-                                               (const C *)rho, (const C2 *)pl, (C)beta,
-                                               (C)mp.kappa, (C)mp.g[0], (C)mp.g[1], (C)mp.g[2],
-                                               bgk, ctl, partial, nblk_sweep, err);
-  } else {
-    k_mp_density<Q, S, long long><<<grid, b, 0, s>>>(g, (const T *)fin, (const C *)rref,
-                                                     (C *)rho, (C2 *)pl, mp.eos, partial, gpart,
-                                                     nblk_sweep, err);
-    k_mp_lap<Q, C, long long><<<grid, b, 0, s>>>(g, (const C *)rho, (C2 *)pl, gpart, nblk_sweep,
-                                                 mp.g[0], mp.g[1], mp.g[2], ctl);
-    if (pair)
-      k_mp_sweep2<Q, long long><<<grid2, b2, 0, s>>>(
+  if (mp.wall >= 0) {
+    // Grad fill of the wall nodes' missing populations (into fin's ghost slots)
+    const MpPlane mpl = mp_plane_of(g, mp.wall);
+    const long long nb_band = 2 * kMpBandRows * mpl.plane, nb_fill = 2 * mpl.plane;
+    k_mp_wall_band<Q, S, IX><<<(unsigned)((nb_band + 127) / 128), 128, 0, s>>>(
+        g, (const T *)fin, (const C *)rref, (const C2 *)pl, (C)mp.kappa, (C)mp.g[0], (C)mp.g[1],
+        (C)mp.g[2], wl, mpl, have_force, (C *)band);
+    k_mp_wall_fill<Q, S, IX><<<(unsigned)((nb_fill + 127) / 128), 128, 0, s>>>(
+        g, (T *)fin, (const C *)rref, (const C *)band, mpl, (C)beta);
+  }
+  k_mp_density<Q, S, IX><<<grid, b, 0, s>>>(g, (const T *)fin, (const C *)rref, (C *)rho,
+                                            (C2 *)pl, mp.eos, partial, gpart, nblk_sweep, wl, err);
+  k_mp_lap<Q, C, IX><<<grid, b, 0, s>>>(g, (const C *)rho, (C2 *)pl, gpart, nblk_sweep, mp.g[0],
+                                        mp.g[1], mp.g[2], ctl, wl);
+  if (pair) {
+    if constexpr (S == STORE_F32)
+      k_mp_sweep2<Q, IX><<<grid2, b2, 0, s>>>(
           g, (const float *)fin, (float *)fout, (const float *)rref, (const float *)rho,
           (const float2 *)pl, (float)beta, (float)mp.kappa, (float)mp.g[0], (float)mp.g[1],
-          (float)mp.g[2], bgk, ctl, partial, nblk_sweep, err);
-    else
-      k_mp_sweep<Q, S, long long><<<grid, b, 0, s>>>(
-          g, (const T *)fin, (T *)fout, (const C *)rref, (const C *)rho, (const C2 *)pl, (C)beta,
-          (C)mp.kappa, (C)mp.g[0], (C)mp.g[1], (C)mp.g[2], bgk, ctl, partial, nblk_sweep, err);
+          (float)mp.g[2], bgk, ctl, partial, nblk_sweep, wl, err);
+  } else {
+    k_mp_sweep<Q, S, IX><<<grid, b, 0, s>>>(g, (const T *)fin, (T *)fout, (const C *)rref,
+                                            (const C *)rho, (const C2 *)pl, (C)beta, (C)mp.kappa,
+                                            (C)mp.g[0], (C)mp.g[1], (C)mp.g[2], bgk, ctl, partial,
+                                            nblk_sweep, wl, err);
   }
+}
+
+template <int Q, int S>
+static cudaError_t mp_step_t(const Grid &g, void *fin, void *fout, const void *rref, void *rho,
+                             void *pl, double *ctl, double *partial, void *band, int have_force,
+                             const MpParams &mp, double beta, int bgk, int *err, cudaStream_t s) {
+  // partial: [4][nblk] CTA sums of the sweep, then [4][ngroups] group sums
+  double *gpart = partial + kMpPartial * mp_grid(g.nx, g.ny, g.nz).blocks;
+  // 32-bit offsets when every population offset fits
+  if ((long long)Q * g.N < (1LL << 31))
+    mp_launch_all<Q, S, int>(g, fin, fout, rref, rho, pl, ctl, partial, gpart, band, have_force,
+                             mp, beta, bgk, err, s);
+  else
+    mp_launch_all<Q, S, long long>(g, fin, fout, rref, rho, pl, ctl, partial, gpart, band,
+                                   have_force, mp, beta, bgk, err, s);
   return cudaGetLastError();
 }
 
@@ -667,11 +910,12 @@ static cudaError_t mp_step_t(const Grid &g, const void *fin, void *fout, const v
     return cudaErrorInvalidValue;                                                     \
   } while (0)
 
-cudaError_t launch_mp_step(int Q, int storage, const Grid &g, const void *fin, void *fout,
+cudaError_t launch_mp_step(int Q, int storage, const Grid &g, void *fin, void *fout,
                            const void *rref, void *rho, void *pl, double *ctl, double *partial,
-                           const MpParams &mp, double beta, int bgk, int *err, cudaStream_t s) {
-  MP_DISPATCH(Q, storage, return (mp_step_t<QQ, SS>(g, fin, fout, rref, rho, pl, ctl, partial, mp,
-                                                    beta, bgk, err, s)));
+                           void *band, int have_force, const MpParams &mp, double beta, int bgk,
+                           int *err, cudaStream_t s) {
+  MP_DISPATCH(Q, storage, return (mp_step_t<QQ, SS>(g, fin, fout, rref, rho, pl, ctl, partial,
+                                                    band, have_force, mp, beta, bgk, err, s)));
 }
 
 template <int Q, int S, class O>
@@ -687,7 +931,8 @@ static cudaError_t mp_read_t(const Grid &g, const void *f, const void *rref, con
   const int b = 256;
   k_mp_read<Q, S, O><<<(unsigned)((count + b - 1) / b), b, 0, s>>>(
       g, (const T *)f, (const C *)rref, (const C2 *)pl, (C)mp.kappa, (C)mp.g[0], (C)mp.g[1],
-      (C)mp.g[2], have_force, mean, begin, count, stride, F, rho_out, u, fabs);
+      (C)mp.g[2], have_force, mean, mp_wall_of<C>(g, mp), begin, count, stride, F, rho_out, u,
+      fabs);
   return cudaGetLastError();
 }
 
@@ -712,6 +957,7 @@ cudaError_t launch_mp_rebase(int Q, int storage, const Grid &g, void *f, void *r
     using T = typename Store<SS>::T;
     using C = typename Store<SS>::C;
     k_mp_rebase<QQ, SS><<<nb, b, 0, s>>>(g, (T *)f, (C *)rref, (C)Rnew, shift_populations);
+    k_mp_fill_ref<C><<<(unsigned)((g.N + b - 1) / b), b, 0, s>>>((C *)rref, g.N, (C)Rnew);
     return cudaGetLastError();
   });
 }

@@ -201,14 +201,14 @@ def lbm_set_sweep_variant(ctx, variant: int):
 LBM_EOS_PAPER, LBM_EOS_IDEAL = 0, 1
 
 
-def lbm_set_multiphase(ctx, kappa, eos=LBM_EOS_PAPER, g=(0.0, 0.0, 0.0)):
+def lbm_set_multiphase(ctx, kappa, eos=LBM_EOS_PAPER, g=(0.0, 0.0, 0.0), kappa_w=0.0):
     """Switch to the multiphase step (kappa None: back to single phase)."""
     if kappa is None:
         _chk(ctx, load().lbm_set_multiphase(ctx, None))
         return
     from ._abi_ext import lbm_multiphase_params
     p = lbm_multiphase_params()
-    p.kappa, p.eos = float(kappa), int(eos)
+    p.kappa, p.eos, p.kappa_w = float(kappa), int(eos), float(kappa_w)
     for a in range(3):
         p.g[a] = float(g[a]) if a < len(g) else 0.0
     _chk(ctx, load().lbm_set_multiphase(ctx, ctypes.byref(p)))
@@ -343,8 +343,8 @@ class Lattice:
         lbm_get_macros(self.ctx, rho, u)
         return rho, u
 
-    def set_multiphase(self, kappa, eos=LBM_EOS_PAPER, g=(0.0, 0.0, 0.0)):
-        lbm_set_multiphase(self.ctx, kappa, eos, g)
+    def set_multiphase(self, kappa, eos=LBM_EOS_PAPER, g=(0.0, 0.0, 0.0), kappa_w=0.0):
+        lbm_set_multiphase(self.ctx, kappa, eos, g, kappa_w)
 
     def force_field(self):
         """Force F[3, nz, ny, nx] of the last multiphase step."""

@@ -199,8 +199,8 @@ def test_multiphase_rejects_bad_set_ups():
     assert e.value.status == abi.LBM_ESTATE
     with pytest.raises(abi.LbmError):          # 16-bit storage
         Lattice(9, 8, 8, 1, 0.8, storage=1, multiphase=True)
-    Lw = Lattice(9, 8, 8, 1, 0.8, bc=(0, 0, 1, 1, 0, 0), multiphase=True)
-    with pytest.raises(abi.LbmError) as e:     # walls
+    Lw = Lattice(9, 8, 8, 1, 0.8, bc=(2, 3, 0, 0, 0, 0), multiphase=True)
+    with pytest.raises(abi.LbmError) as e:     # open faces (walls: tests/test_gpu_multiphase_walls.py)
         Lw.set_multiphase(0.02)
     assert e.value.status == abi.LBM_EINVAL
     L = Lattice(9, 8, 8, 1, 0.8, multiphase=True)
