@@ -490,8 +490,10 @@ lbm_status lbm_get_macros_f32(lbm_ctx *ctx, float *rho, float *u);
  * per-thread asynchronous copies into shared memory while it collides the
  * current one (other storage: DIRECT).  DIRECT, ROWS and ASYNC give
  * identical results; PAIR performs the same IEEE operations on the paired
- * instructions and agrees with them to the last bit or so.  LBM_EINVAL for
- * an unknown value. */
+ * instructions and agrees with them to the last bit or so.  In the
+ * multiphase model (lbm_set_multiphase) AUTO, DIRECT, ROWS and ASYNC run the
+ * one-node forced sweep and PAIR its two-node form.  LBM_EINVAL for an
+ * unknown value. */
 enum { LBM_SWEEP_AUTO = 0, LBM_SWEEP_DIRECT = 1, LBM_SWEEP_ROWS = 2, LBM_SWEEP_ASYNC = 3,
        LBM_SWEEP_PAIR = 4 };
 lbm_status lbm_set_sweep_variant(lbm_ctx *ctx, int variant);

@@ -620,7 +620,8 @@ lbm_status lbm_step(lbm_ctx *ctx, int n) {
       if (ctx->bp.ramp_steps > 0) CK(launch_step_counter(ctx->counters + 3, ctx->stream));
     }
     if (ctx->mp_on) {
-      ctx->mp.pair = ctx->sweep_variant != SWEEP_DIRECT;
+      // the one-node forced sweep is the faster form (AUTO); PAIR asks for the other
+      ctx->mp.pair = ctx->sweep_variant == SWEEP_PAIR;
       CK(launch_mp_step(ctx->Q, ctx->cfg.storage, ctx->g, ctx->f[ctx->cur], ctx->f[1 - ctx->cur],
                         ctx->ws + ctx->lay.mp_rho[ctx->mp_cur],
                         ctx->ws + ctx->lay.mp_rho[1 - ctx->mp_cur], ctx->ws + ctx->lay.mp_pl,
@@ -1042,7 +1043,7 @@ lbm_status lbm_set_sweep_variant(lbm_ctx *ctx, int variant) {
   GUARD();
   if (variant < LBM_SWEEP_AUTO || variant > LBM_SWEEP_PAIR)
     return fail(ctx, LBM_EINVAL, "lbm_set_sweep_variant: unknown variant %d", variant);
-  if (ctx->mp_on && (variant == SWEEP_DIRECT) != (ctx->sweep_variant == SWEEP_DIRECT)) {
+  if (ctx->mp_on && (variant == SWEEP_PAIR) != (ctx->sweep_variant == SWEEP_PAIR)) {
     // the two forms of the multiphase sweep leave per-CTA partials of
     // different grids: restart the momentum controller
     CK(cudaMemsetAsync(ctx->ws + ctx->lay.mp_ctl, 0, sizeof(double) * kMpControl, ctx->stream));

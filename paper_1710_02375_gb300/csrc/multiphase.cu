@@ -246,7 +246,9 @@ __device__ __forceinline__ void mp_gather(const Grid &g, const typename Store<S>
   }
 }
 
-template <int Q, int S, typename IX>
+// WALL: the wall terms (ghost-row mirrors; the periodic instantiation
+// compiles without them).
+template <int Q, int S, typename IX, bool WALL>
 __global__ void __launch_bounds__(128)
     k_mp_density(Grid g, const typename Store<S>::T *__restrict__ fin,
                  const typename Store<S>::C *__restrict__ rref,
@@ -281,11 +283,13 @@ __global__ void __launch_bounds__(128)
     rho[k] = r;
     pl[k].x = ph;
     // the ghost row across a wall mirrors the first / last row
-    const int side = mp_side(wl, x + g.px, y + g.py, z + g.pz);
-    if (side) {
-      const long long kg = (long long)k + side * mp_wall_stride(g, wl);
-      rho[kg] = r;
-      pl[kg].x = ph;
+    if constexpr (WALL) {
+      const int side = mp_side(wl, x + g.px, y + g.py, z + g.pz);
+      if (side) {
+        const long long kg = (long long)k + side * mp_wall_stride(g, wl);
+        rho[kg] = r;
+        pl[kg].x = ph;
+      }
     }
   }
   mp_stage1(partial, nblk, gpart,
@@ -296,7 +300,7 @@ __global__ void __launch_bounds__(128)
 // lap rho = 6 (sum_i W_i rho(x + c_i) - rho(x)), the sum in tensor-product
 // form: rows of three x-neighbours weighted by the D1Q3 weights w(c), then
 // the rows by w(cy) w(cz).
-template <int Q, class C, typename IX>
+template <int Q, class C, typename IX, bool WALL>
 __device__ __forceinline__ void mp_lap_node(const Grid &g, const C *__restrict__ rho,
                                             typename Vec2<C>::T *__restrict__ pl, int x, int y,
                                             int z, const MpWallT<C> &wl) {
@@ -316,11 +320,13 @@ __device__ __forceinline__ void mp_lap_node(const Grid &g, const C *__restrict__
     }
   const C lp = (C)6 * (acc - r0);
   pl[k].y = lp;
-  const int side = mp_side(wl, x + g.px, y + g.py, z + g.pz);
-  if (side) pl[(long long)k + side * mp_wall_stride(g, wl)].y = lp;
+  if constexpr (WALL) {
+    const int side = mp_side(wl, x + g.px, y + g.py, z + g.pz);
+    if (side) pl[(long long)k + side * mp_wall_stride(g, wl)].y = lp;
+  }
 }
 
-template <int Q, class C, typename IX>
+template <int Q, class C, typename IX, bool WALL>
 __global__ void __launch_bounds__(128)
     k_mp_lap(Grid g, const C *__restrict__ rho, typename Vec2<C>::T *__restrict__ pl,
              const double *__restrict__ gpart, long long nblk, double gx, double gy, double gz,
@@ -329,9 +335,9 @@ __global__ void __launch_bounds__(128)
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
-  if (x < g.nx && y < g.ny) mp_lap_node<Q, C, IX>(g, rho, pl, x, y, z, wl);
+  if (x < g.nx && y < g.ny) mp_lap_node<Q, C, IX, WALL>(g, rho, pl, x, y, z, wl);
   // walls take momentum: the controller runs on fully periodic lattices only
-  if (wl.wa < 0)
+  if constexpr (!WALL)
     mp_stage2(gpart, nblk, gx, gy, gz, ctl,
               ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
 }
@@ -414,7 +420,7 @@ __device__ __forceinline__ void cta_sum4(A (&a)[kMpPartial], double *out, long l
 #ifndef KBC_MP_CTAS
 #define KBC_MP_CTAS 4
 #endif
-template <int Q, int S, typename IX>
+template <int Q, int S, typename IX, bool WALL>
 __global__ void __launch_bounds__(128, KBC_MP_CTAS)
     k_mp_sweep(Grid g, const typename Store<S>::T *__restrict__ fin,
                typename Store<S>::T *__restrict__ fout, const typename Store<S>::C *__restrict__ rref,
@@ -436,7 +442,7 @@ __global__ void __launch_bounds__(128, KBC_MP_CTAS)
     const C ac[3] = {mp_ac<C>(ctl, 0), mp_ac<C>(ctl, 1), mp_ac<C>(ctl, 2)};
     C r, F[3];
     mp_force<Q, C, IX>(rho, pl, nb, kappa, gx, gy, gz, r, F);
-    mp_wet(wl, mp_side(wl, x + g.px, y + g.py, z + g.pz), r, F);
+    if constexpr (WALL) mp_wet(wl, mp_side(wl, x + g.px, y + g.py, z + g.pz), r, F);
     const C ir = (C)1 / r;
     C v[Q];
     // the new reference of the node: its density of this step
@@ -480,7 +486,7 @@ __global__ void __launch_bounds__(128, KBC_MP_CTAS)
 #ifndef KBC_MP_PAIR_CTAS
 #define KBC_MP_PAIR_CTAS 2
 #endif
-template <int Q, typename IX>
+template <int Q, typename IX, bool WALL>
 __global__ void __launch_bounds__(128, KBC_MP_PAIR_CTAS)
     k_mp_sweep2(Grid g, const float *__restrict__ fin, float *__restrict__ fout,
                 const float *__restrict__ rref, const float *__restrict__ rho,
@@ -502,8 +508,10 @@ __global__ void __launch_bounds__(128, KBC_MP_PAIR_CTAS)
     mp_force<Q, float, IX>(rho, pl, na, kappa, gx, gy, gz, ra, Fa);
     mp_force<Q, float, IX>(rho, pl, nb, kappa, gx, gy, gz, rb, Fb);
     // the pair shares Y and Z, and walls normal to x are not paired
-    mp_wet(wl, mp_side(wl, X, Y, Z), ra, Fa);
-    mp_wet(wl, mp_side(wl, ib ? X + 1 : X, Y, Z), rb, Fb);
+    if constexpr (WALL) {
+      mp_wet(wl, mp_side(wl, X, Y, Z), ra, Fa);
+      mp_wet(wl, mp_side(wl, ib ? X + 1 : X, Y, Z), rb, Fb);
+    }
     const IX N = (IX)g.N;
     f2 v[Q];
 #pragma unroll
@@ -839,7 +847,7 @@ static MpPlane mp_plane_of(const Grid &g, int wa) {
   return m;
 }
 
-template <int Q, int S, typename IX>
+template <int Q, int S, typename IX, bool WALL>
 static void mp_launch_all(const Grid &g, void *fin, void *fout, const void *rref, void *rho,
                           void *pl, double *ctl, double *partial, double *gpart, void *band,
                           int have_force, const MpParams &mp, double beta, int bgk, int *err,
@@ -858,7 +866,7 @@ static void mp_launch_all(const Grid &g, void *fin, void *fout, const void *rref
   const dim3 b2 = npairs >= 128 ? dim3(128, 1, 1) : dim3(32, 4, 1);
   const dim3 grid2((npairs + b2.x - 1) / b2.x, (g.ny + b2.y - 1) / b2.y, g.nz);
   const long long nblk_sweep = pair ? (long long)grid2.x * grid2.y * grid2.z : nblk;
-  if (mp.wall >= 0) {
+  if constexpr (WALL) {
     // Grad fill of the wall nodes' missing populations (into fin's ghost slots)
     const MpPlane mpl = mp_plane_of(g, mp.wall);
     const long long nb_band = 2 * kMpBandRows * mpl.plane, nb_fill = 2 * mpl.plane;
@@ -868,18 +876,18 @@ static void mp_launch_all(const Grid &g, void *fin, void *fout, const void *rref
     k_mp_wall_fill<Q, S, IX><<<(unsigned)((nb_fill + 127) / 128), 128, 0, s>>>(
         g, (T *)fin, (const C *)rref, (const C *)band, mpl, (C)beta);
   }
-  k_mp_density<Q, S, IX><<<grid, b, 0, s>>>(g, (const T *)fin, (const C *)rref, (C *)rho,
+  k_mp_density<Q, S, IX, WALL><<<grid, b, 0, s>>>(g, (const T *)fin, (const C *)rref, (C *)rho,
                                             (C2 *)pl, mp.eos, partial, gpart, nblk_sweep, wl, err);
-  k_mp_lap<Q, C, IX><<<grid, b, 0, s>>>(g, (const C *)rho, (C2 *)pl, gpart, nblk_sweep, mp.g[0],
+  k_mp_lap<Q, C, IX, WALL><<<grid, b, 0, s>>>(g, (const C *)rho, (C2 *)pl, gpart, nblk_sweep, mp.g[0],
                                         mp.g[1], mp.g[2], ctl, wl);
   if (pair) {
     if constexpr (S == STORE_F32)
-      k_mp_sweep2<Q, IX><<<grid2, b2, 0, s>>>(
+      k_mp_sweep2<Q, IX, WALL><<<grid2, b2, 0, s>>>(
           g, (const float *)fin, (float *)fout, (const float *)rref, (const float *)rho,
           (const float2 *)pl, (float)beta, (float)mp.kappa, (float)mp.g[0], (float)mp.g[1],
           (float)mp.g[2], bgk, ctl, partial, nblk_sweep, wl, err);
   } else {
-    k_mp_sweep<Q, S, IX><<<grid, b, 0, s>>>(g, (const T *)fin, (T *)fout, (const C *)rref,
+    k_mp_sweep<Q, S, IX, WALL><<<grid, b, 0, s>>>(g, (const T *)fin, (T *)fout, (const C *)rref,
                                             (const C *)rho, (const C2 *)pl, (C)beta, (C)mp.kappa,
                                             (C)mp.g[0], (C)mp.g[1], (C)mp.g[2], bgk, ctl, partial,
                                             nblk_sweep, wl, err);
@@ -893,12 +901,19 @@ static cudaError_t mp_step_t(const Grid &g, void *fin, void *fout, const void *r
   // partial: [4][nblk] CTA sums of the sweep, then [4][ngroups] group sums
   double *gpart = partial + kMpPartial * mp_grid(g.nx, g.ny, g.nz).blocks;
   // 32-bit offsets when every population offset fits
-  if ((long long)Q * g.N < (1LL << 31))
-    mp_launch_all<Q, S, int>(g, fin, fout, rref, rho, pl, ctl, partial, gpart, band, have_force,
-                             mp, beta, bgk, err, s);
-  else
-    mp_launch_all<Q, S, long long>(g, fin, fout, rref, rho, pl, ctl, partial, gpart, band,
+  const bool narrow = (long long)Q * g.N < (1LL << 31);
+  if (narrow && mp.wall < 0)
+    mp_launch_all<Q, S, int, false>(g, fin, fout, rref, rho, pl, ctl, partial, gpart, band,
+                                    have_force, mp, beta, bgk, err, s);
+  else if (narrow)
+    mp_launch_all<Q, S, int, true>(g, fin, fout, rref, rho, pl, ctl, partial, gpart, band,
                                    have_force, mp, beta, bgk, err, s);
+  else if (mp.wall < 0)
+    mp_launch_all<Q, S, long long, false>(g, fin, fout, rref, rho, pl, ctl, partial, gpart, band,
+                                          have_force, mp, beta, bgk, err, s);
+  else
+    mp_launch_all<Q, S, long long, true>(g, fin, fout, rref, rho, pl, ctl, partial, gpart, band,
+                                         have_force, mp, beta, bgk, err, s);
   return cudaGetLastError();
 }
 
