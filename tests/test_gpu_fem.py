@@ -166,3 +166,34 @@ def test_coupled_flag_graph_replay_matches_direct_stepping():
     assert Lb.boundary_info()[3] == 300  # inflow-ramp clock advanced once per step
     assert np.max(np.abs(fa - fb)) <= 1e-6 * np.max(np.abs(fa))
     assert np.max(np.abs(ua - ub)) <= 1e-9 * max(np.max(np.abs(ua)), 1e-30)
+
+
+@pytest.mark.parametrize("fac", [3.4, 3.8])
+def test_beam_large_rotation_steps_match_oracle(fac):
+    """A tip moment fac x 1.5 pi EI / L held on the C1 flag beam for 100
+    steps: the element chords turn by up to 0.28 rad in one step (the atan2
+    branch of the chord rotation, beyond the arctangent series) and, at fac
+    3.8, through +-pi (chord angles up to 4.5 rad: the wrap of atan2).  The
+    GPU beam against the oracle at every step."""
+    from paper_1710_02375_gb300.lbm import Beam
+    X, EA, EI, rhoA, fixed = synth.c1_flag_beam()
+    L = X[-1, 0] - X[0, 0]
+    gb = Beam(X, EA, EI, rhoA, fixed, thickness=2.0)
+    ob = orc.Beam(X, EA, EI, rhoA, fixed)
+    n = 3 * len(X)
+    u, v, F0 = np.zeros(n), np.zeros(n), np.zeros(n)
+    F1 = np.zeros(n)
+    F1[-1] = fac * 1.5 * np.pi * EI / L
+    worst, chord = 0.0, 0.0
+    for _ in range(100):
+        gb.step(F1)
+        u, v, it = ob.step(u, v, F0, F1)
+        F0 = F1
+        ug, _, itg = gb.state()
+        assert it >= 0 and itg >= 0
+        worst = max(worst, np.max(np.abs(ug - u)) / np.max(np.abs(u)))
+        x, y = X[:, 0] + u[0::3], X[:, 1] + u[1::3]
+        chord = max(chord, np.abs(np.unwrap(np.arctan2(np.diff(y), np.diff(x)))).max())
+    print(f"large rotations (fac {fac}): max chord angle {chord:.2f} rad, GPU vs oracle {worst:.2e}")
+    assert chord > (3.0 if fac < 3.6 else np.pi)
+    assert worst < 1e-12, worst  # measured 8.6e-15 / 8.5e-15
