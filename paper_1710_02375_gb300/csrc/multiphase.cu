@@ -342,6 +342,57 @@ __global__ void __launch_bounds__(128)
               ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
 }
 
+// D3Q27 form marching along z: a thread takes a column of up to kz nodes of
+// one (x, y) and keeps the weighted plane sums P(z) = sum_{cy} w(cy) S(cy, z)
+// of three consecutive planes in registers, so each node costs the 9 loads of
+// one new plane instead of 27 (lap rho = 6 (sum_cz w(cz) P(z + cz) - rho)).
+template <class C, typename IX, bool WALL>
+__global__ void __launch_bounds__(128)
+    k_mp_lap_z(Grid g, const C *__restrict__ rho, typename Vec2<C>::T *__restrict__ pl,
+               const double *__restrict__ gpart, long long nblk, double gx, double gy, double gz,
+               double *__restrict__ ctl, MpWallT<C> wl, int kz) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z0 = blockIdx.z * kz;
+  if (x < g.nx && y < g.ny) {
+    const int X = x + g.px, Y = y + g.py;
+    const IX xo[3] = {(IX)nbr(X, -1, g.NX), (IX)X, (IX)nbr(X, 1, g.NX)};
+    const IX yo[3] = {(IX)nbr(Y, -1, g.NY) * (IX)g.pitch, (IX)Y * (IX)g.pitch,
+                      (IX)nbr(Y, 1, g.NY) * (IX)g.pitch};
+    const IX plane = (IX)g.NY * (IX)g.pitch;
+    auto psum = [&](int Zs) -> C {
+      const IX base = (IX)Zs * plane;
+      C acc = (C)0;
+#pragma unroll
+      for (int cy = 0; cy < 3; ++cy) {
+        const IX row = base + yo[cy];
+        const C sw = (C)(1.0 / 6.0) * (__ldg(rho + row + xo[0]) + __ldg(rho + row + xo[2])) +
+                     (C)(2.0 / 3.0) * __ldg(rho + row + xo[1]);
+        acc += (C)w1d(cy - 1) * sw;
+      }
+      return acc;
+    };
+    const int zend = min(z0 + kz, g.nz);
+    C pm = psum(nbr(z0 + g.pz, -1, g.NZ)), p0 = psum(z0 + g.pz);
+    for (int z = z0; z < zend; ++z) {
+      const int Z = z + g.pz;
+      const C pp = psum(nbr(Z, 1, g.NZ));
+      const IX k = (IX)Z * plane + yo[1] + xo[1];
+      const C lp = (C)6 * ((C)(1.0 / 6.0) * (pm + pp) + (C)(2.0 / 3.0) * p0 - rho[k]);
+      pl[k].y = lp;
+      if constexpr (WALL) {
+        const int side = mp_side(wl, X, Y, Z);
+        if (side) pl[(long long)k + side * mp_wall_stride(g, wl)].y = lp;
+      }
+      pm = p0;
+      p0 = pp;
+    }
+  }
+  if constexpr (!WALL)
+    mp_stage2(gpart, nblk, gx, gy, gz, ctl,
+              ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
+}
+
 // F at a node from the fields: 2 phi d(phi) + kappa rho d(lap rho) + rho g.
 // The lattice gradient d_a psi = 3 sum_i W_i c_ia psi(x + c_i) in
 // tensor-product form (3 W_i c_ix = c_ix w(cy) w(cz) / 2):
@@ -847,6 +898,12 @@ static MpPlane mp_plane_of(const Grid &g, int wa) {
   return m;
 }
 
+// z-nodes per thread of the marching Laplacian pass
+#ifndef KBC_MP_LAP_COLUMN
+#define KBC_MP_LAP_COLUMN 16
+#endif
+constexpr int kMpLapColumn = KBC_MP_LAP_COLUMN;
+
 template <int Q, int S, typename IX, bool WALL>
 static void mp_launch_all(const Grid &g, void *fin, void *fout, const void *rref, void *rho,
                           void *pl, double *ctl, double *partial, double *gpart, void *band,
@@ -878,8 +935,14 @@ static void mp_launch_all(const Grid &g, void *fin, void *fout, const void *rref
   }
   k_mp_density<Q, S, IX, WALL><<<grid, b, 0, s>>>(g, (const T *)fin, (const C *)rref, (C *)rho,
                                             (C2 *)pl, mp.eos, partial, gpart, nblk_sweep, wl, err);
-  k_mp_lap<Q, C, IX, WALL><<<grid, b, 0, s>>>(g, (const C *)rho, (C2 *)pl, gpart, nblk_sweep, mp.g[0],
-                                        mp.g[1], mp.g[2], ctl, wl);
+  if (Q == 27 && g.nz >= 2 * kMpLapColumn) {
+    const dim3 gz(grid.x, grid.y, (g.nz + kMpLapColumn - 1) / kMpLapColumn);
+    k_mp_lap_z<C, IX, WALL><<<gz, b, 0, s>>>(g, (const C *)rho, (C2 *)pl, gpart, nblk_sweep,
+                                             mp.g[0], mp.g[1], mp.g[2], ctl, wl, kMpLapColumn);
+  } else {
+    k_mp_lap<Q, C, IX, WALL><<<grid, b, 0, s>>>(g, (const C *)rho, (C2 *)pl, gpart, nblk_sweep,
+                                                mp.g[0], mp.g[1], mp.g[2], ctl, wl);
+  }
   if (pair) {
     if constexpr (S == STORE_F32)
       k_mp_sweep2<Q, IX, WALL><<<grid2, b2, 0, s>>>(

@@ -41,7 +41,8 @@ def two_phase_state(lat, shape, seed):
 
 @pytest.mark.parametrize("lat,shape,wa", [(9, (1, 37, 53), 1), (9, (1, 37, 53), 0),
                                           (27, (13, 11, 17), 2), (27, (13, 11, 17), 1),
-                                          (27, (13, 11, 17), 0)])
+                                          (27, (13, 11, 17), 0), (27, (41, 12, 20), 2),
+                                          (27, (41, 12, 20), 1)])
 def test_three_steps_match_oracle_fp32(lat, shape, wa):
     """Three steps from a random two-phase state (the second and third fill
     the wall nodes with the force of the step before), kappa_w = -0.1, on
