@@ -237,16 +237,21 @@ def test_graph_replay_matches_direct_stepping():
     assert np.array_equal(out[0], out[1])
 
 
-def test_stress_traction_matches_oracle():
+@pytest.mark.parametrize("storage,tol", [(0, 3e-5), (3, 1e-7)])
+def test_stress_traction_matches_oracle(storage, tol):
     """Stress-path traction (lbm_set_traction_output): immersed Couette walls
     (the exact wall shear rho nu U / H) and the C1 cylinder with a rigid flag
     after 300 steps, against the oracle's boundary-node stresses and element
-    quadrature; per vertex <= 1e-3 of the largest vertex force, per body
-    <= 1e-3 of the body force (C1) or of the vertex scale (Couette)."""
+    quadrature; per vertex <= tol of the largest vertex force, per body <= tol
+    of the body force (C1) or of the vertex scale (Couette).  Measured with
+    FP32 storage: Couette 5.5e-6, C1 body 1.4e-6, C1 vertex 1.6e-7; with FP64
+    storage (D2Q9; limited by the FP32 link data of the library): 2.3e-8,
+    1.1e-9, 1.2e-10."""
     # Couette
     nx, ny, U, beta, steps = 5, 16, 0.01, 0.7, 400
     x, v, e, body = slabs(nx, ny, 2.3, 13.6, U)
-    L = lattice(9, (1, ny, nx), beta, max_links=400, max_vertices=16, max_elements=16)
+    L = lattice(9, (1, ny, nx), beta, storage=storage, max_links=400, max_vertices=16,
+                max_elements=16)
     L.set_geometry(x, e, body, vel=v)
     L.set_traction_output(True)
     rho0, u0 = np.ones((1, ny, nx)), np.zeros((2, 1, ny, nx))
@@ -264,14 +269,16 @@ def test_stress_traction_matches_oracle():
     # the slabs' totals cancel (their far faces lie outside the periodic box
     # and see the same stress), so they are compared on the vertex-force scale
     scale = np.max(np.abs(tv_o))
-    assert scale > 0 and np.max(np.abs(tb_g - tb_o)) <= 1e-3 * scale, (tb_g, tb_o)
-    assert np.max(np.abs(tv_g - tv_o)) <= 1e-3 * scale
+    e_couette = max(np.max(np.abs(tb_g - tb_o)), np.max(np.abs(tv_g - tv_o))) / scale
+    assert scale > 0 and e_couette <= tol, (tb_g, tb_o)
     # C1 geometry, rigid flag
     nx, ny, beta, prof, x, e, body = c1_setup(True)
+    if storage == 3:  # the library keeps inlet profiles in FP32: both sides take that array
+        prof = prof.astype(np.float32).astype(np.float64)
     bc = (INLET, OUTLET, WALL, WALL, 0, 0)
     steps = 300
-    L = lattice(9, (1, ny, nx), beta, bc=bc, max_links=4000, max_vertices=200, max_elements=200,
-                inlet_ramp_steps=1000)
+    L = lattice(9, (1, ny, nx), beta, storage=storage, bc=bc, max_links=4000, max_vertices=200,
+                max_elements=200, inlet_ramp_steps=1000)
     L.set_inlet_profile(0, prof)
     L.set_geometry(x, e, body)
     L.set_traction_output(True)
@@ -288,8 +295,10 @@ def test_stress_traction_matches_oracle():
         f, _, _, _, sig = orc.step_bc(9, beta, f, bc=bc, inlet={0: prof}, inlet_scale=s, surf=surf,
                                       solid=solid, want_sigma=True)
     tv_o, tb_o, _ = orc.traction(surf, sig)
-    for b in range(2):
-        assert np.linalg.norm(tb_g[b] - tb_o[b]) <= 1e-3 * np.linalg.norm(tb_o[b]), (tb_g, tb_o)
-    assert np.max(np.abs(tv_g - tv_o)) <= 1e-3 * np.max(np.abs(tv_o))
+    e_body = max(np.linalg.norm(tb_g[b] - tb_o[b]) / np.linalg.norm(tb_o[b]) for b in range(2))
+    e_vert = np.max(np.abs(tv_g - tv_o)) / np.max(np.abs(tv_o))
+    print(f"traction storage {storage}: Couette {e_couette:.2e}, C1 body {e_body:.2e}, "
+          f"C1 vertex {e_vert:.2e}")
+    assert e_body <= tol and e_vert <= tol, (e_body, e_vert)
     print("TRACTION vs momentum exchange (C1, 300 steps):", tb_g[:, :2].tolist(), mb_g[:, :2].tolist())
 
