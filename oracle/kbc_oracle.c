@@ -659,3 +659,235 @@ int or_step_multiphase_wall(int lat, int nx, int ny, int nz, double beta, int mo
   free(f); free(uo); free(rho); free(phi); free(lap);
   return 0;
 }
+
+/* ======================================================================
+ * Two-level grid refinement (the multi-domain refinement the paper uses in
+ * its validation cases; the algorithm is cited, not printed).  D2Q9.
+ * Reading:
+ *   - A periodic coarse grid (nxc x nyc cells, node at the cell centre) and
+ *     a fine patch of nfx x nfy nodes (spacing 1/2, two fine steps per
+ *     coarse step: the same lattice velocity, nu_fine = 2 nu_coarse in
+ *     lattice units) covering the coarse cells [i0, i0 + nfx/2) x
+ *     [j0, j0 + nfy/2), its node (p, q) at coarse-cell coordinates
+ *     (i0 + (p + 1/2)/2, j0 + (q + 1/2)/2).
+ *   - Coarse -> fine: a fine node whose pull reaches outside the patch gets,
+ *     for those populations only (as for a boundary node), Grad's
+ *     approximation, Eq. (grad), Pi = rho c_s^2 I + rho u u - rho c_s^2/(2
+ *     beta_f)(grad u + grad u^T), of the coarse fields rho, u (= j / rho)
+ *     and grad u (central differences, in fine units: half the coarse-unit
+ *     gradient) interpolated bilinearly to the node itself and linearly in
+ *     time to the fine time of the pull (t + 1/2, t + 1): the pre-collision
+ *     populations the node would receive.  (Grad's form evaluated at the
+ *     source node instead stands for a pre-collision state where a pulled
+ *     population is post-collision; its non-equilibrium part then has
+ *     nearly the opposite sign at beta near 1.)
+ *   - Fine -> coarse: after the two fine steps each covered coarse cell takes
+ *     Grad's approximation (beta_c) of the mean density, momentum and
+ *     velocity gradient of its 2 x 2 fine children (the gradient by central
+ *     differences of the fine velocity, the ghost ring holding the coarse
+ *     values of time t + 1, and doubled to coarse units), then the coarse
+ *     KBC collision: the stored post-collision state of that cell.
+ *   - Order per coarse step: the coarse step over all cells (the covered
+ *     ones hold the restricted state), two fine steps, the restriction.
+ * fc: coarse post-collision state [9][nyc][nxc]; ff: fine [9][nfy][nfx].
+ * ====================================================================== */
+
+static void ref_grad_pop_all(const or_lattice *L, double rho, const double *u, const double G[2][2],
+                             double beta, double *f) {
+  const double cs2 = 1.0 / 3.0;
+  double Pn[2][2];
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b)
+      Pn[a][b] = rho * u[a] * u[b] - rho * cs2 / (2.0 * beta) * (G[a][b] + G[b][a]);
+  for (int i = 0; i < L->Q; ++i) {
+    double cu = 0.0, contr = 0.0;
+    for (int a = 0; a < 2; ++a) cu += L->c[i][a] * u[a];
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b)
+        contr += Pn[a][b] * (L->c[i][a] * L->c[i][b] - (a == b ? cs2 : 0.0));
+    f[i] = L->w[i] * (rho + rho * cu / cs2 + contr / (2.0 * cs2 * cs2));
+  }
+}
+
+/* rho, u and grad u (coarse units, central differences) of a periodic coarse state */
+static void ref_coarse_fields(const or_lattice *L, const double *fc, int nx, int ny, double *rho,
+                              double *u /*[2][n]*/, double *G /*[4][n]*/) {
+  const long n = (long)nx * ny;
+  for (long k = 0; k < n; ++k) {
+    double r = 0.0, j[2] = {0, 0};
+    for (int i = 0; i < L->Q; ++i) {
+      r += fc[i * n + k];
+      j[0] += L->c[i][0] * fc[i * n + k];
+      j[1] += L->c[i][1] * fc[i * n + k];
+    }
+    rho[k] = r;
+    u[k] = j[0] / r;
+    u[n + k] = j[1] / r;
+  }
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      const long k = (long)y * nx + x;
+      const long xp = (long)y * nx + wrap(x + 1, nx), xm = (long)y * nx + wrap(x - 1, nx);
+      const long yp = (long)wrap(y + 1, ny) * nx + x, ym = (long)wrap(y - 1, ny) * nx + x;
+      for (int a = 0; a < 2; ++a) {
+        G[(2 * a + 0) * n + k] = 0.5 * (u[a * n + xp] - u[a * n + xm]);
+        G[(2 * a + 1) * n + k] = 0.5 * (u[a * n + yp] - u[a * n + ym]);
+      }
+    }
+}
+
+/* Lagrange weights of the four nodes -1, 0, 1, 2 at the offset t in [0, 1) */
+static void ref_cubic_w(double t, double *w) {
+  w[0] = -t * (t - 1.0) * (t - 2.0) / 6.0;
+  w[1] = (t + 1.0) * (t - 1.0) * (t - 2.0) / 2.0;
+  w[2] = -(t + 1.0) * t * (t - 2.0) / 2.0;
+  w[3] = (t + 1.0) * t * (t - 1.0) / 6.0;
+}
+
+/* bicubic (tensor-product Lagrange, 4 x 4 nodes) value of a periodic coarse
+ * field at coarse-cell coordinates (X, Y).  (Bilinear interpolation damps a
+ * Fourier mode by O(h^2 k^2) at every transfer; applied every coarse step
+ * that acts as an extra diffusion of the order of the grid spacing.) */
+static double ref_bilinear(const double *v, int nx, int ny, double X, double Y) {
+  const double sx = X - 0.5, sy = Y - 0.5;
+  const int ix = (int)floor(sx), iy = (int)floor(sy);
+  double wx[4], wy[4];
+  ref_cubic_w(sx - ix, wx);
+  ref_cubic_w(sy - iy, wy);
+  double acc = 0.0;
+  for (int b = 0; b < 4; ++b)
+    for (int a = 0; a < 4; ++a)
+      acc += wx[a] * wy[b] * v[(long)wrap(iy - 1 + b, ny) * nx + wrap(ix - 1 + a, nx)];
+  return acc;
+}
+
+int or_refine_step(int nxc, int nyc, double beta_c, double beta_f, int mode, int i0, int j0,
+                   int nfx, int nfy, const double *fc_in, const double *ff_in, double *fc_out,
+                   double *ff_out) {
+  or_lattice L;
+  if (make_lattice(9, &L)) return -1;
+  if (nfx < 2 || nfy < 2 || (nfx & 1) || (nfy & 1)) return -1;
+  if (nfx / 2 > nxc - 2 || nfy / 2 > nyc - 2) return -1;
+  const int Q = 9;
+  const long nc = (long)nxc * nyc, nf = (long)nfx * nfy;
+  double *rc0 = malloc(sizeof(double) * nc), *uc0 = malloc(sizeof(double) * 2 * nc);
+  double *gc0 = malloc(sizeof(double) * 4 * nc), *rc1 = malloc(sizeof(double) * nc);
+  double *uc1 = malloc(sizeof(double) * 2 * nc), *gc1 = malloc(sizeof(double) * 4 * nc);
+  double *fa = malloc(sizeof(double) * Q * nf), *fb = malloc(sizeof(double) * Q * nf);
+  if (!rc0 || !uc0 || !gc0 || !rc1 || !uc1 || !gc1 || !fa || !fb) return -2;
+  ref_coarse_fields(&L, fc_in, nxc, nyc, rc0, uc0, gc0);
+  /* coarse step over all cells */
+  if (or_step_periodic(9, nxc, nyc, 1, beta_c, mode, fc_in, fc_out, NULL)) return -1;
+  ref_coarse_fields(&L, fc_out, nxc, nyc, rc1, uc1, gc1);
+  memcpy(fa, ff_in, sizeof(double) * Q * nf);
+  double f[OR_MAXQ], fo[OR_MAXQ], g;
+  for (int k = 0; k < 2; ++k) {
+    const double w = 0.5 * (k + 1);  /* fine time of the pull, in coarse steps after t */
+    for (int q = 0; q < nfy; ++q)
+      for (int p = 0; p < nfx; ++p) {
+        const long kf = (long)q * nfx + p;
+        int nmiss = 0;
+        for (int i = 0; i < Q; ++i) {
+          const int ps = p - L.c[i][0], qs = q - L.c[i][1];
+          if (ps >= 0 && ps < nfx && qs >= 0 && qs < nfy) f[i] = fa[i * nf + (long)qs * nfx + ps];
+          else nmiss++;
+        }
+        if (nmiss) {
+          const double X = i0 + 0.5 * (p + 0.5), Y = j0 + 0.5 * (q + 0.5);
+          double r = (1 - w) * ref_bilinear(rc0, nxc, nyc, X, Y) + w * ref_bilinear(rc1, nxc, nyc, X, Y);
+          double uu[2], G[2][2], fg[OR_MAXQ];
+          for (int a = 0; a < 2; ++a)
+            uu[a] = (1 - w) * ref_bilinear(uc0 + a * nc, nxc, nyc, X, Y) +
+                    w * ref_bilinear(uc1 + a * nc, nxc, nyc, X, Y);
+          for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b)
+              G[a][b] = 0.5 * ((1 - w) * ref_bilinear(gc0 + (2 * a + b) * nc, nxc, nyc, X, Y) +
+                               w * ref_bilinear(gc1 + (2 * a + b) * nc, nxc, nyc, X, Y));
+          ref_grad_pop_all(&L, r, uu, G, beta_f, fg);
+          for (int i = 0; i < Q; ++i) {
+            const int ps = p - L.c[i][0], qs = q - L.c[i][1];
+            if (!(ps >= 0 && ps < nfx && qs >= 0 && qs < nfy)) f[i] = fg[i];
+          }
+        }
+        collide(&L, beta_f, mode, f, fo, &g, NULL, NULL, NULL);
+        for (int i = 0; i < Q; ++i) fb[i * nf + kf] = fo[i];
+      }
+    double *t = fa; fa = fb; fb = t;
+  }
+  memcpy(ff_out, fa, sizeof(double) * Q * nf);
+  /* fine fields at t + 1: rho, u on the patch; u on the ghost ring from the coarse fields */
+  const int gx = nfx + 2, gy = nfy + 2;
+  double *uf = malloc(sizeof(double) * 2 * gx * gy), *rf = malloc(sizeof(double) * gx * gy);
+  double *jf = malloc(sizeof(double) * 2 * gx * gy);
+  if (!uf || !rf || !jf) return -2;
+  for (int q = -1; q <= nfy; ++q)
+    for (int p = -1; p <= nfx; ++p) {
+      const long kg = (long)(q + 1) * gx + (p + 1);
+      if (p >= 0 && p < nfx && q >= 0 && q < nfy) {
+        const long kf = (long)q * nfx + p;
+        double r = 0.0, j[2] = {0, 0};
+        for (int i = 0; i < Q; ++i) {
+          r += fa[i * nf + kf];
+          j[0] += L.c[i][0] * fa[i * nf + kf];
+          j[1] += L.c[i][1] * fa[i * nf + kf];
+        }
+        rf[kg] = r;
+        jf[kg] = j[0];
+        jf[gx * gy + kg] = j[1];
+        uf[kg] = j[0] / r;
+        uf[gx * gy + kg] = j[1] / r;
+      } else {
+        const double X = i0 + 0.5 * (p + 0.5), Y = j0 + 0.5 * (q + 0.5);
+        const double r = ref_bilinear(rc1, nxc, nyc, X, Y);
+        rf[kg] = r;
+        for (int a = 0; a < 2; ++a) {
+          uf[a * gx * gy + kg] = ref_bilinear(uc1 + a * nc, nxc, nyc, X, Y);
+          jf[a * gx * gy + kg] = r * uf[a * gx * gy + kg];
+        }
+      }
+    }
+  /* restriction: the coarse-centre values by the cubic midpoint rule over the
+   * fine nodes 2I-1 .. 2I+2 of each axis (weights -1, 9, 9, -1 over 16; the
+   * outer ones on the ghost ring for the cells along the patch edge), the
+   * velocity gradient from the midpoint values of the neighbouring fine
+   * pairs (spacing 1/2 apart: one-sided pairs at the patch edge use the
+   * ghost ring too) */
+  static const double wm[4] = {-1.0 / 16.0, 9.0 / 16.0, 9.0 / 16.0, -1.0 / 16.0};
+  for (int J = 0; J < nfy / 2; ++J)
+    for (int I = 0; I < nfx / 2; ++I) {
+      double r = 0.0, j[2] = {0, 0}, G[2][2] = {{0, 0}, {0, 0}};
+      for (int b = 0; b < 4; ++b)
+        for (int a = 0; a < 4; ++a) {
+          const int p = 2 * I - 1 + a, q = 2 * J - 1 + b;
+          const long kg = (long)(q + 1) * gx + (p + 1);
+          const double ww = wm[a] * wm[b];
+          r += ww * rf[kg];
+          j[0] += ww * jf[kg];
+          j[1] += ww * jf[gx * gy + kg];
+        }
+      /* d/dx at the centre: fine-unit differences of the pairs (2I+1 - 2I) on
+       * the rows, midpoint-interpolated across, doubled to coarse units */
+      for (int a = 0; a < 2; ++a) {
+        double dx = 0.0, dy = 0.0;
+        for (int b = 0; b < 4; ++b) {
+          const int q = 2 * J - 1 + b;
+          const long k0 = (long)(q + 1) * gx + (2 * I + 1), k1 = k0 + 1;
+          dx += wm[b] * (uf[a * gx * gy + k1] - uf[a * gx * gy + k0]);
+          const int p = 2 * I - 1 + b;
+          const long l0 = (long)(2 * J + 1) * gx + (p + 1), l1 = l0 + gx;
+          dy += wm[b] * (uf[a * gx * gy + l1] - uf[a * gx * gy + l0]);
+        }
+        G[a][0] = 2.0 * dx;
+        G[a][1] = 2.0 * dy;
+      }
+      const double uu[2] = {j[0] / r, j[1] / r};
+      double fg[OR_MAXQ];
+      ref_grad_pop_all(&L, r, uu, G, beta_c, fg);
+      collide(&L, beta_c, mode, fg, fo, &g, NULL, NULL, NULL);
+      const long kc = (long)(j0 + J) * nxc + (i0 + I);
+      for (int i = 0; i < Q; ++i) fc_out[i * nc + kc] = fo[i];
+    }
+  free(rc0); free(uc0); free(gc0); free(rc1); free(uc1); free(gc1); free(fa); free(fb);
+  free(uf); free(rf); free(jf);
+  return 0;
+}

@@ -83,6 +83,8 @@ def _declare(L):
                                      D, D, D]
     L.or_step_multiphase_wall.argtypes = [c_int, c_int, c_int, c_int, c_double, c_int, c_double, c_int,
                                           D, c_double, c_int, D, D, D, D]
+    L.or_refine_step.argtypes = [c_int, c_int, c_double, c_double, c_int, c_int, c_int, c_int,
+                                 c_int, D, D, D, D]
 
 
 def _p(a: np.ndarray):
@@ -374,6 +376,24 @@ def step_multiphase_wall(lat, beta, f, kappa, kappa_w, wall_axis, F_prev=None, e
                                          float(kappa_w), int(wall_axis), _p(f),
                                          _p(fp) if fp is not None else None, _p(fo), _p(F)))
     return fo, F
+
+
+# ---------------------------------------------------------------- refinement
+def refine_step(beta_c, fc, ff, i0, j0, mode=0):
+    """One coarse step of the two-level refinement (D2Q9): the periodic coarse
+    state fc[9, 1, nyc, nxc] and the fine patch ff[9, 1, nfy, nfx] (spacing
+    1/2, covering the coarse cells [i0, i0 + nfx/2) x [j0, j0 + nfy/2), two
+    fine steps at nu_fine = 2 nu_coarse).  Returns (fc_new, ff_new)."""
+    fc = np.ascontiguousarray(fc, dtype=np.float64)
+    ff = np.ascontiguousarray(ff, dtype=np.float64)
+    _, _, nyc, nxc = fc.shape
+    _, _, nfy, nfx = ff.shape
+    nu_c = (1.0 / (2.0 * beta_c) - 0.5) / 3.0
+    beta_f = 1.0 / (6.0 * 2.0 * nu_c + 1.0)
+    fco, ffo = np.zeros_like(fc), np.zeros_like(ff)
+    _check(lib().or_refine_step(nxc, nyc, float(beta_c), beta_f, int(mode), int(i0), int(j0), nfx, nfy,
+                                _p(fc), _p(ff), _p(fco), _p(ffo)))
+    return fco, ffo
 
 
 def macros_forced(lat, f, F):
