@@ -6,7 +6,7 @@ the 129 MB L2, so no L2 flush is needed between steps).  A step is one pass of
 the hot path over the whole lattice: pull-stream + KBC collision, one kernel.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload tgv128|c4|c4-coupled|c1-fsi|c3-fsi] [--quick]
+                  [--workload tgv128|c4|c4-coupled|c1-fsi|c3-fsi|multiphase|refine] [--quick]
 
 The default line also carries "patterns": the same workload with IEEE half,
 bfloat16 and the narrow-range 16-bit float F16N storage, as speedups over
@@ -379,6 +379,7 @@ def run_ours(args):
         forms["coupled_c3"] = c3_leg(args)
         forms["multiphase_droplet_d3q27"] = mp_leg(args)
         forms["multiphase_droplet_on_wall_d3q27"] = mp_wall_leg(args)
+        forms["refined_d2q9_two_level"] = refine_leg(args)
         forms["surrogate"] = {
             "measured_in": "tests/test_gpu_surrogate.py, tests/test_gpu_plate_surrogate.py",
             "why_not_here": "its training pairs come from coupled FP64 oracle runs, which this "
@@ -644,6 +645,50 @@ def mp_leg(args, shape=(320, 250, 320), kappa=0.025, beta=0.6):
                       "FP32 storage relative to the local density"}
 
 
+def refine_leg(args, nxc=2048, nyc=1024, U0=0.03, nu_c=0.01):
+    """Two-level refinement (D2Q9, FP32): a periodic coarse grid 2048 x 1024
+    with a fine patch of 2048 x 1024 nodes at half the spacing over its
+    middle quarter (1024 x 512 coarse cells), a Taylor-Green flow; per coarse
+    step the coarse sweep, two fine sweeps with the Grad fill of the fine
+    boundary nodes, the field and restriction kernels.  Node updates count
+    the coarse cells once and the fine nodes twice."""
+    import torch
+    from paper_1710_02375_gb300.lbm import refined_pair
+    nfx, nfy = nxc, nyc
+    i0, j0 = nxc // 4, nyc // 4
+    beta = 1.0 / (6.0 * nu_c + 1.0)
+    C, F = refined_pair(nxc, nyc, beta, nfx, nfy, i0, j0)
+    dev = C.device
+    k = 2 * 3.141592653589793 / nxc
+
+    def fields(nx, ny, h, x0, y0):
+        y = torch.arange(ny, dtype=torch.float64, device=dev) * h + y0 + 0.5 * h
+        x = torch.arange(nx, dtype=torch.float64, device=dev) * h + x0 + 0.5 * h
+        Y, X = torch.meshgrid(y, x, indexing="ij")
+        ux = U0 * torch.sin(k * X) * torch.cos(k * Y * nxc / nyc)
+        uy = -U0 * torch.cos(k * X) * torch.sin(k * Y * nxc / nyc) * nyc / nxc
+        rho = torch.ones((1, ny, nx), dtype=torch.float64, device=dev)
+        return rho, torch.stack([ux, uy])[:, None]
+
+    C.init_equilibrium(*fields(nxc, nyc, 1.0, 0.0, 0.0))
+    F.init_equilibrium(*fields(nfx, nfy, 0.5, float(i0), float(j0)))
+    C.step(4)
+    chunk, reps = 10, 20
+    C.step_graph(chunk, 1)
+    ms = _timed(C.stream, lambda r: C.step_graph(chunk, r), reps) / chunk
+    C.check()
+    updates = nxc * nyc + 2 * nfx * nfy
+    peak, peak_kind = measured_peaks()
+    gbs = 2 * 9 * 4 * updates / (ms * 1e-3) / 1e9
+    C.close()
+    F.close()
+    return {"ms_per_step": ms, "mlups": updates / (ms * 1e-3) / 1e6, "steps": chunk * reps,
+            "achieved_gbs_sweeps": gbs, "frac_of_peak_sweeps": gbs / peak, "peak_kind": peak_kind,
+            "config": f"D2Q9 coarse {nxc}x{nyc} periodic + fine patch {nfx}x{nfy} (half spacing, "
+                      f"two fine steps per coarse step) over coarse cells [{i0},{i0 + nfx // 2})x"
+                      f"[{j0},{j0 + nfy // 2}), Taylor-Green U0={U0}, nu_c={nu_c}, FP32"}
+
+
 def run_c4(args):
     """Batched pattern: the 64-member flag ensemble (synth.c4_instances, D2Q9,
     200x40 .. 800x160 lattices, 3.78M nodes in all) stepped as one batch under
@@ -830,7 +875,7 @@ def main():
     ap.add_argument("--quick", action="store_true",
                     help="only the headline workload and its storage patterns")
     ap.add_argument("--workload", choices=["tgv128", "c4", "c4-coupled", "c1-fsi", "c3-fsi",
-                                           "multiphase"], default="tgv128")
+                                           "multiphase", "refine"], default="tgv128")
     ap.add_argument("--mp-shape", default="320,250,320",
                     help="nz,ny,nx of the multiphase droplet workload")
     args = ap.parse_args()
@@ -850,6 +895,10 @@ def main():
         shape = tuple(int(v) for v in args.mp_shape.split(","))
         print(json.dumps({"workload": "multiphase", **mp_leg(args, shape=shape),
                           "walls": mp_wall_leg(args, shape=shape)}), flush=True)
+    elif args.workload == "refine":
+        import __graft_entry__
+        __graft_entry__.build()
+        print(json.dumps({"workload": "refine", **refine_leg(args)}), flush=True)
     else:
         run_ours(args)
 

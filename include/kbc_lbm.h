@@ -16,7 +16,12 @@
  *     host memory or device memory of the context's device; the library tells
  *     them apart with cudaPointerGetAttributes.  Caller-owned arrays are only
  *     read (inputs) or written (outputs) during the call; the library keeps
- *     no reference to them.
+ *     no reference to them.  Exception: a call documented as asynchronous
+ *     (lbm_update_surface) reads device or page-locked host inputs in the
+ *     order of the context's stream, after it returns; keep them unchanged
+ *     until the stream has passed the call.  Device inputs must be complete
+ *     when the call is made: work that writes them on another stream has to
+ *     be finished or ordered before the context's stream.
  *   - Work runs in order on one CUDA stream (the caller's, given in
  *     lbm_config.stream, or one the library creates).  lbm_step returns
  *     without waiting for the GPU; every lbm_get_* call waits for the stream.
@@ -552,6 +557,57 @@ typedef struct {
 } lbm_multiphase_params;
 lbm_status lbm_set_multiphase(lbm_ctx *ctx, const lbm_multiphase_params *params);
 lbm_status lbm_get_force_field(lbm_ctx *ctx, double *F);
+
+/* ---------------------------------------------------------------------------
+ * Two-level grid refinement (the multi-domain refinement the validation
+ * cases of section "Validation" run on; the paper cites the algorithm
+ * without printing it).  D2Q9, FP32 or FP64 storage.
+ *
+ * A coupled pair: `coarse`, a periodic lattice, and `fine`, a patch at half
+ * the spacing over the coarse cells [i0, i0 + nx_f / 2) x [j0, j0 + ny_f / 2)
+ * (cell-centred: fine node (p, q) sits at coarse coordinates (i0 + (p +
+ * 1/2) / 2, j0 + (q + 1/2) / 2)), with the viscosity of the fine units,
+ * nu_f = 2 nu_c, i.e. beta_f = 1 / (2 / beta_c - 1).  lbm_step(coarse, n)
+ * then runs n coarse steps of the pair; each:
+ *   - the coarse step over every coarse cell;
+ *   - two fine steps: the populations a fine boundary node pulls from
+ *     outside the patch are Grad's approximation, Eq. (grad), with beta_f,
+ *     of the coarse rho, u and grad u (central differences, halved in fine
+ *     units) interpolated bicubically to the node and linearly in time to
+ *     the fine time level (t + 1/2, t + 1);
+ *   - each covered coarse cell is replaced by the cubic midpoint values
+ *     (weights -1, 9, 9, -1 over 16 per axis) of the fine density and
+ *     momentum and the velocity gradient of the midpoint differences of the
+ *     fine velocity (doubled to coarse units; the coarse values of t + 1
+ *     beyond the patch), through Grad's approximation with beta_c and the
+ *     coarse collision.
+ * The covered coarse cells are overwritten each step (their own coarse
+ * step only feeds the interpolation); mass is conserved to the interface
+ * truncation.
+ *
+ * Requirements (LBM_EINVAL otherwise): both D2Q9 with the same storage (FP32
+ * or FP64), collision and stream; coarse periodic on every face, fine with
+ * non-periodic x and y faces (their kinds are ignored: the coupling fills
+ * the fine ghost layer), nx_f and ny_f even and >= 4, the patch inside the
+ * coarse grid (0 <= i0, i0 + nx_f / 2 <= nx_c, nx_f / 2 <= nx_c - 2, the same
+ * for y), beta_f as
+ * above to 1e-12; no immersed bodies, beams, shells or multiphase model on
+ * either (LBM_ESTATE for a context with those, or one already coupled).
+ *
+ * lbm_refine_workspace_size: bytes of device scratch for the pair (the
+ * coarse fields at two times and the fine fields on the patch with a ring).
+ * lbm_refine_couple: workspace = device memory of at least that size
+ * (256-byte aligned, caller-owned, outliving the coupling) or NULL
+ * (cudaMalloc, freed when the pair is uncoupled or the coarse context is
+ * destroyed).  fine = NULL uncouples `coarse`.  While coupled, lbm_step and
+ * lbm_step_graph on `fine` return LBM_ESTATE (the coarse context steps it);
+ * every other call on either context works as before (the fine context's
+ * state is its interior nodes).  lbm_check(coarse) also reports a bad
+ * density met on the fine patch.  Destroying either context uncouples the
+ * pair. */
+lbm_status lbm_refine_workspace_size(lbm_ctx *coarse, lbm_ctx *fine, size_t *bytes);
+lbm_status lbm_refine_couple(lbm_ctx *coarse, lbm_ctx *fine, int i0, int j0, void *workspace,
+                             size_t workspace_bytes);
 
 /* Wait for the stream and report LBM_EUNSTABLE if any sweep since the last
  * check met a non-finite or non-positive density, LBM_ETIMEOUT if a bounded

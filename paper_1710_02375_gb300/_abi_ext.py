@@ -62,6 +62,8 @@ def declare(L):
     L.lbm_set_multiphase.argtypes = [vp, ctypes.POINTER(lbm_multiphase_params)]
     L.lbm_set_multiphase.restype = ctypes.c_int
     L.lbm_get_force_field.argtypes = [vp, vp]
+    L.lbm_refine_workspace_size.argtypes = [vp, vp, ctypes.POINTER(sz)]
+    L.lbm_refine_couple.argtypes = [vp, vp, i32, i32, vp, sz]
     L.lbm_get_force_field.restype = ctypes.c_int
     L.fem_beam_workspace_size.argtypes = [ctypes.POINTER(fem_beam_config), ctypes.POINTER(sz)]
     L.fem_beam_create.argtypes = [ctypes.POINTER(fem_beam_config), vp, sz, ctypes.POINTER(vp)]

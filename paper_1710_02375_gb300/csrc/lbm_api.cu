@@ -193,6 +193,12 @@ struct lbm_ctx {
   int mp_cur = 0;            // density buffer holding the reference of the stored state
   bool mp_have_force = false;  // a multiphase step has produced the stored state
   int graph_cur = 0, graph_mp_cur = 0;  // buffer parities the graph was captured at
+  // two-level refinement: on a coarse lattice, its fine patch; on a fine
+  // lattice, the coarse lattice that steps it
+  lbm_ctx *ref_fine = nullptr, *ref_coarse = nullptr;
+  int ref_i0 = 0, ref_j0 = 0;
+  char *ref_ws = nullptr;
+  bool ref_own_ws = false;
   double accept_tol = 0.0;
   // CUDA graph of graph_n steps (replayed by lbm_step_graph)
   cudaGraphExec_t gexec = nullptr;
@@ -345,9 +351,13 @@ const char *lbm_last_error(const lbm_ctx *ctx) { return ctx ? ctx->msg : g_creat
 
 void *lbm_stream(const lbm_ctx *ctx) { return ctx ? (void *)ctx->stream : nullptr; }
 
+static void refine_release(lbm_ctx *coarse);
+
 void lbm_destroy(lbm_ctx *ctx) {
   if (!ctx) return;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->ref_fine) refine_release(ctx);
+  if (ctx->ref_coarse) refine_release(ctx->ref_coarse);
   if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   if (ctx->own_ws) cudaFree(ctx->ws);
@@ -388,6 +398,7 @@ lbm_status lbm_init_equilibrium(lbm_ctx *ctx, const double *rho, const double *u
   if (dev) {
     CK(launch_init_eq(ctx->Q, ctx->cfg.storage, ctx->g, rho, u, n, 0, n, ctx->f[ctx->cur],
                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));  // the caller may reuse the arrays on return
     return LBM_OK;
   }
   const double *mr = (const double *)mapped_host_ptr(rho), *mu = (const double *)mapped_host_ptr(u);
@@ -422,6 +433,7 @@ lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f) {
     for (int i = 0; i < ctx->Q; ++i)
       CK(launch_set_pop(ctx->Q, ctx->cfg.storage, ctx->g, i, f + i * n, 0, n, ctx->f[ctx->cur],
                         ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));  // the caller may reuse the array on return
     return LBM_OK;
   }
   const long long chunk = (long long)(kStageBytes / sizeof(double));
@@ -595,9 +607,14 @@ lbm_status lbm_get_force_field(lbm_ctx *ctx, double *F) {
   return LBM_OK;
 }
 
+static lbm_status refine_steps(lbm_ctx *ctx, int n);
+
 lbm_status lbm_step(lbm_ctx *ctx, int n) {
   GUARD();
   if (n < 0) return fail(ctx, LBM_EINVAL, "lbm_step: n < 0");
+  if (ctx->ref_coarse)
+    return fail(ctx, LBM_ESTATE, "lbm_step: a fine patch is stepped by its coarse lattice");
+  if (ctx->ref_fine) return refine_steps(ctx, n);
   const double beta = ctx->cfg.beta;
   const int bgk = ctx->cfg.collision == LBM_COLLIDE_BGK;
   // the multiphase step fills its wall nodes itself
@@ -677,6 +694,134 @@ lbm_status lbm_step(lbm_ctx *ctx, int n) {
       lbm_status st = run_geometry(ctx, 1);
       if (st != LBM_OK) return st;
     }
+  }
+  return LBM_OK;
+}
+
+// ---- two-level refinement
+static void refine_release(lbm_ctx *coarse) {
+  lbm_ctx *fine = coarse->ref_fine;
+  if (coarse->ref_own_ws && coarse->ref_ws) {
+    cudaStreamSynchronize(coarse->stream);
+    cudaFree(coarse->ref_ws);
+  }
+  coarse->ref_ws = nullptr;
+  coarse->ref_own_ws = false;
+  coarse->ref_fine = nullptr;
+  coarse->graph_dirty = true;
+  if (fine) fine->ref_coarse = nullptr;
+}
+
+static bool refine_busy(const lbm_ctx *c) {
+  // (has_solid is also set by a ghost layer alone; solid interior nodes come with bodies)
+  return c->nbodies > 0 || c->fem || c->shell || c->mlp || c->mp_on;
+}
+
+static const char *refine_mismatch(const lbm_ctx *c, const lbm_ctx *f) {
+  if (c->Q != 9 || f->Q != 9) return "both lattices must be D2Q9";
+  if (c->cfg.storage != f->cfg.storage) return "the two lattices need the same storage";
+  if (c->cfg.storage != LBM_STORE_F32 && c->cfg.storage != LBM_STORE_F64)
+    return "refinement needs FP32 or FP64 storage";
+  if (c->cfg.collision != f->cfg.collision) return "the two lattices need the same collision";
+  if (c->stream != f->stream) return "the two lattices must share one stream";
+  if (c->device != f->device) return "the two lattices must be on one device";
+  for (int k = 0; k < 4; ++k)
+    if (c->cfg.bc[k] != LBM_BC_PERIODIC) return "the coarse lattice must be periodic";
+  for (int k = 0; k < 4; ++k)
+    if (f->cfg.bc[k] == LBM_BC_PERIODIC) return "the fine lattice needs non-periodic x and y faces";
+  if (f->cfg.nx < 4 || f->cfg.ny < 4 || (f->cfg.nx & 1) || (f->cfg.ny & 1))
+    return "the fine sizes must be even and >= 4";
+  const double bf = 1.0 / (2.0 / c->cfg.beta - 1.0);
+  if (!(std::fabs(f->cfg.beta - bf) <= 1e-12 * bf))
+    return "fine beta must be 1 / (2 / beta_c - 1) (nu_f = 2 nu_c)";
+  return nullptr;
+}
+
+lbm_status lbm_refine_workspace_size(lbm_ctx *coarse, lbm_ctx *fine, size_t *bytes) {
+  lbm_ctx *ctx = coarse;
+  GUARD();
+  if (!fine || !bytes) return fail(ctx, LBM_EINVAL, "lbm_refine_workspace_size: NULL argument");
+  if (const char *why = refine_mismatch(coarse, fine))
+    return fail(ctx, LBM_EINVAL, "lbm_refine_workspace_size: %s", why);
+  *bytes = align_up(refine_workspace_bytes(coarse->cfg.storage, coarse->cfg.nx, coarse->cfg.ny,
+                                           fine->cfg.nx, fine->cfg.ny));
+  return LBM_OK;
+}
+
+lbm_status lbm_refine_couple(lbm_ctx *coarse, lbm_ctx *fine, int i0, int j0, void *workspace,
+                             size_t workspace_bytes) {
+  lbm_ctx *ctx = coarse;
+  GUARD();
+  if (!fine) {
+    refine_release(coarse);
+    return LBM_OK;
+  }
+  if (fine == coarse) return fail(ctx, LBM_EINVAL, "lbm_refine_couple: fine == coarse");
+  if (fine->poisoned) return fail(ctx, LBM_ESTATE, "lbm_refine_couple: fine context poisoned");
+  if (coarse->ref_fine || coarse->ref_coarse || fine->ref_fine || fine->ref_coarse)
+    return fail(ctx, LBM_ESTATE, "lbm_refine_couple: a context is already part of a pair");
+  if (refine_busy(coarse) || refine_busy(fine))
+    return fail(ctx, LBM_ESTATE,
+                "lbm_refine_couple: bodies, beams, shells or the multiphase model are set");
+  if (const char *why = refine_mismatch(coarse, fine))
+    return fail(ctx, LBM_EINVAL, "lbm_refine_couple: %s", why);
+  if (i0 < 0 || j0 < 0 || i0 + fine->cfg.nx / 2 > coarse->cfg.nx ||
+      j0 + fine->cfg.ny / 2 > coarse->cfg.ny)
+    return fail(ctx, LBM_EINVAL, "lbm_refine_couple: the patch leaves the coarse grid");
+  if (fine->cfg.nx / 2 > coarse->cfg.nx - 2 || fine->cfg.ny / 2 > coarse->cfg.ny - 2)
+    return fail(ctx, LBM_EINVAL, "lbm_refine_couple: the patch must leave two coarse cells free");
+  const size_t need = align_up(refine_workspace_bytes(coarse->cfg.storage, coarse->cfg.nx,
+                                                      coarse->cfg.ny, fine->cfg.nx, fine->cfg.ny));
+  if (workspace) {
+    if (workspace_bytes < need || ((uintptr_t)workspace % kAlign) != 0)
+      return fail(ctx, LBM_ENOMEM, "lbm_refine_couple: workspace needs %zu bytes, 256-byte aligned",
+                  need);
+    if (!is_device_ptr(workspace))
+      return fail(ctx, LBM_EINVAL, "lbm_refine_couple: workspace must be device memory");
+    coarse->ref_ws = (char *)workspace;
+    coarse->ref_own_ws = false;
+  } else {
+    cudaError_t e = cudaMalloc((void **)&coarse->ref_ws, need);
+    if (e != cudaSuccess) {
+      coarse->ref_ws = nullptr;
+      return fail(ctx, LBM_ENOMEM, "lbm_refine_couple: cudaMalloc(%zu): %s", need,
+                  cudaGetErrorString(e));
+    }
+    coarse->ref_own_ws = true;
+  }
+  coarse->ref_fine = fine;
+  coarse->ref_i0 = i0;
+  coarse->ref_j0 = j0;
+  fine->ref_coarse = coarse;
+  coarse->graph_dirty = true;
+  return LBM_OK;
+}
+
+static lbm_status refine_steps(lbm_ctx *ctx, int n) {
+  lbm_ctx *fine = ctx->ref_fine;
+  if (refine_busy(ctx) || refine_busy(fine))
+    return fail(ctx, LBM_ESTATE, "lbm_step: the refined pair gained bodies or a model it lacks");
+  RefLaunch R;
+  R.gc = ctx->g;
+  R.gf = fine->g;
+  R.storage = ctx->cfg.storage;
+  R.ff[0] = fine->f[0];
+  R.ff[1] = fine->f[1];
+  R.cur_f = fine->cur;
+  R.flags_f = nullptr;
+  R.beta_c = ctx->cfg.beta;
+  R.beta_f = fine->cfg.beta;
+  R.bgk = ctx->cfg.collision == LBM_COLLIDE_BGK;
+  R.variant = ctx->sweep_variant;
+  R.i0 = ctx->ref_i0;
+  R.j0 = ctx->ref_j0;
+  R.fields = ctx->ref_ws;
+  R.err_c = R.err_f = ctx->err;
+  for (int t = 0; t < n; ++t) {
+    R.fc_in = ctx->f[ctx->cur];
+    R.fc_out = ctx->f[1 - ctx->cur];
+    CK(launch_refine_step(R, ctx->stream));
+    ctx->cur = 1 - ctx->cur;  // two fine steps leave the fine state in its own buffer
   }
   return LBM_OK;
 }
@@ -1005,6 +1150,8 @@ lbm_status lbm_get_boundary_info(lbm_ctx *ctx, int *info) {
 
 lbm_status lbm_step_graph(lbm_ctx *ctx, int n, int repeats) {
   GUARD();
+  if (ctx->ref_coarse)
+    return fail(ctx, LBM_ESTATE, "lbm_step_graph: a fine patch is stepped by its coarse lattice");
   if (n <= 0 || (n & 1) || repeats < 0)
     return fail(ctx, LBM_EINVAL, "lbm_step_graph: n must be even and positive, repeats >= 0");
   if (ctx->graph_dirty || ctx->graph_n != n || !ctx->gexec || ctx->cur != ctx->graph_cur ||
@@ -1351,6 +1498,11 @@ lbm_status lbm_batch_create(lbm_ctx *const *ctxs, int n, void *workspace, size_t
     if (ctxs[i]->mp_on) {
       snprintf(g_create_msg, sizeof(g_create_msg),
                "lbm_batch_create: multiphase lattices are stepped one by one");
+      return LBM_EINVAL;
+    }
+    if (ctxs[i]->ref_fine || ctxs[i]->ref_coarse) {
+      snprintf(g_create_msg, sizeof(g_create_msg),
+               "lbm_batch_create: a lattice of a refined pair is stepped by its pair");
       return LBM_EINVAL;
     }
   }

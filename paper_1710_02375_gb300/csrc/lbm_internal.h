@@ -135,6 +135,26 @@ cudaError_t launch_mp_read(int Q, int storage, const Grid &g, const void *f, con
 cudaError_t launch_mp_rebase(int Q, int storage, const Grid &g, void *f, void *rref, double Rnew,
                              int shift_populations, cudaStream_t s);
 
+// ---- two-level refinement (D2Q9, FP32 or FP64 storage)
+struct RefLaunch {
+  Grid gc, gf;             // coarse (periodic) and fine (with its ghost layer) grids
+  int storage;
+  const void *fc_in;       // coarse state at t (post-collision)
+  void *fc_out;            // coarse state at t + 1 (the covered cells restricted)
+  void *ff[2];             // fine ping-pong buffers
+  int cur_f;               // fine buffer holding the state at t (it holds t + 1 after two steps)
+  const uint8_t *flags_f;  // fine node flags (ghosts skipped by the sweep)
+  double beta_c, beta_f;
+  int bgk, variant;
+  int i0, j0;              // first covered coarse cell
+  void *fields;            // refine_workspace_bytes scratch
+  int *err_c, *err_f;
+};
+// One coarse step of the refined pair (coarse sweep, two fine steps with
+// the Grad fill of the fine boundary nodes, restriction).
+cudaError_t launch_refine_step(const RefLaunch &R, cudaStream_t s);
+size_t refine_workspace_bytes(int storage, int nxc, int nyc, int nfx, int nfy);
+
 }  // namespace kbc
 
 namespace kbc {

@@ -218,6 +218,18 @@ def lbm_get_force_field(ctx, F):
     _chk(ctx, load().lbm_get_force_field(ctx, _ptr(F)))
 
 
+def lbm_refine_workspace_size(coarse, fine) -> int:
+    n = ctypes.c_size_t()
+    _chk(coarse, load().lbm_refine_workspace_size(coarse, fine, ctypes.byref(n)))
+    return n.value
+
+
+def lbm_refine_couple(coarse, fine, i0, j0, workspace_ptr, workspace_bytes):
+    """Couple a fine patch to a coarse lattice (fine None: uncouple)."""
+    _chk(coarse, load().lbm_refine_couple(coarse, fine, int(i0), int(j0), workspace_ptr,
+                                          int(workspace_bytes)))
+
+
 def lbm_set_inlet_profile(ctx, face, u):
     _chk(ctx, load().lbm_set_inlet_profile(ctx, int(face), _ptr(u)))
 
@@ -319,10 +331,18 @@ class Lattice:
         nz, ny, nx = self.shape
         return nx * ny * nz
 
+    def _after_producers(self, *arrays):
+        """Order the lattice stream after torch's current stream when an input
+        is a CUDA tensor (the work that wrote it may still be queued there)."""
+        if any(isinstance(a, self.torch.Tensor) and a.is_cuda for a in arrays):
+            self.stream.wait_stream(self.torch.cuda.current_stream(self.device))
+
     def init_equilibrium(self, rho, u):
+        self._after_producers(rho, u)
         lbm_init_equilibrium(self.ctx, rho, u)
 
     def set_populations(self, f):
+        self._after_producers(f)
         lbm_set_populations(self.ctx, f)
 
     def get_populations(self, out=None):
@@ -354,6 +374,14 @@ class Lattice:
 
     def set_sweep_variant(self, variant):
         lbm_set_sweep_variant(self.ctx, variant)
+
+    def couple_fine(self, fine, i0, j0):
+        """Make `fine` (a Lattice on the same stream) the refined patch over the
+        coarse cells from (i0, j0); this lattice's step then steps both."""
+        nbytes = lbm_refine_workspace_size(self.ctx, fine.ctx)
+        ws = self.torch.empty(nbytes, dtype=self.torch.uint8, device=self.device)
+        lbm_refine_couple(self.ctx, fine.ctx, i0, j0, ws.data_ptr(), nbytes)
+        self._refine_ws, self._refine_fine = ws, fine
 
     def check(self):
         lbm_check(self.ctx)
@@ -400,12 +428,26 @@ class Lattice:
         if getattr(self, "ctx", None):
             lbm_destroy(self.ctx)
             self.ctx = None
+            self._refine_ws = self._refine_fine = None
 
     def __del__(self):
         try:
             self.close()
         except Exception:
             pass
+
+
+def refined_pair(nx, ny, beta, fine_nx, fine_ny, i0, j0, storage=LBM_STORE_F32,
+                 collision=LBM_COLLIDE_KBC, device="cuda"):
+    """A periodic D2Q9 coarse lattice nx x ny and a fine patch fine_nx x fine_ny
+    at half the spacing over the coarse cells from (i0, j0), on one stream,
+    coupled (beta_f from nu_f = 2 nu_c).  Returns (coarse, fine)."""
+    coarse = Lattice(9, nx, ny, 1, beta, storage=storage, collision=collision, device=device)
+    fine = Lattice(9, fine_nx, fine_ny, 1, 1.0 / (2.0 / beta - 1.0), storage=storage,
+                   collision=collision, bc=(LBM_BC_FREESTREAM,) * 4 + (0, 0),
+                   stream=coarse.stream, device=device)
+    coarse.couple_fine(fine, i0, j0)
+    return coarse, fine
 
 
 # ---------------------------------------------------------------- structure
