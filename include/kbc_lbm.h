@@ -595,7 +595,9 @@ lbm_status lbm_get_force_field(lbm_ctx *ctx, double *F);
  * either (LBM_ESTATE for a context with those, or one already coupled).
  *
  * lbm_refine_workspace_size: bytes of device scratch for the pair (the
- * coarse fields at two times and the fine fields on the patch with a ring).
+ * coarse fields interpolated to the ring around the patch, and a mask of
+ * the covered coarse cells deeper than three cells inside the patch edge,
+ * which skip the coarse step: the restriction replaces them).
  * lbm_refine_couple: workspace = device memory of at least that size
  * (256-byte aligned, caller-owned, outliving the coupling) or NULL
  * (cudaMalloc, freed when the pair is uncoupled or the coarse context is

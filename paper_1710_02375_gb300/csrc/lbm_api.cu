@@ -699,6 +699,8 @@ lbm_status lbm_step(lbm_ctx *ctx, int n) {
 }
 
 // ---- two-level refinement
+static RefLaunch refine_launch(const lbm_ctx *ctx);
+
 static void refine_release(lbm_ctx *coarse) {
   lbm_ctx *fine = coarse->ref_fine;
   if (coarse->ref_own_ws && coarse->ref_ws) {
@@ -743,8 +745,8 @@ lbm_status lbm_refine_workspace_size(lbm_ctx *coarse, lbm_ctx *fine, size_t *byt
   if (!fine || !bytes) return fail(ctx, LBM_EINVAL, "lbm_refine_workspace_size: NULL argument");
   if (const char *why = refine_mismatch(coarse, fine))
     return fail(ctx, LBM_EINVAL, "lbm_refine_workspace_size: %s", why);
-  *bytes = align_up(refine_workspace_bytes(coarse->cfg.storage, coarse->cfg.nx, coarse->cfg.ny,
-                                           fine->cfg.nx, fine->cfg.ny));
+  *bytes = align_up(refine_workspace_bytes(coarse->cfg.storage, coarse->g, fine->cfg.nx,
+                                           fine->cfg.ny));
   return LBM_OK;
 }
 
@@ -770,8 +772,8 @@ lbm_status lbm_refine_couple(lbm_ctx *coarse, lbm_ctx *fine, int i0, int j0, voi
     return fail(ctx, LBM_EINVAL, "lbm_refine_couple: the patch leaves the coarse grid");
   if (fine->cfg.nx / 2 > coarse->cfg.nx - 2 || fine->cfg.ny / 2 > coarse->cfg.ny - 2)
     return fail(ctx, LBM_EINVAL, "lbm_refine_couple: the patch must leave two coarse cells free");
-  const size_t need = align_up(refine_workspace_bytes(coarse->cfg.storage, coarse->cfg.nx,
-                                                      coarse->cfg.ny, fine->cfg.nx, fine->cfg.ny));
+  const size_t need = align_up(refine_workspace_bytes(coarse->cfg.storage, coarse->g,
+                                                      fine->cfg.nx, fine->cfg.ny));
   if (workspace) {
     if (workspace_bytes < need || ((uintptr_t)workspace % kAlign) != 0)
       return fail(ctx, LBM_ENOMEM, "lbm_refine_couple: workspace needs %zu bytes, 256-byte aligned",
@@ -794,6 +796,11 @@ lbm_status lbm_refine_couple(lbm_ctx *coarse, lbm_ctx *fine, int i0, int j0, voi
   coarse->ref_j0 = j0;
   fine->ref_coarse = coarse;
   coarse->graph_dirty = true;
+  const cudaError_t e = launch_refine_init(refine_launch(coarse), coarse->stream);
+  if (e != cudaSuccess) {
+    refine_release(coarse);
+    return cuda_fail(ctx, e, "launch_refine_init");
+  }
   return LBM_OK;
 }
 
@@ -801,6 +808,19 @@ static lbm_status refine_steps(lbm_ctx *ctx, int n) {
   lbm_ctx *fine = ctx->ref_fine;
   if (refine_busy(ctx) || refine_busy(fine))
     return fail(ctx, LBM_ESTATE, "lbm_step: the refined pair gained bodies or a model it lacks");
+  RefLaunch R = refine_launch(ctx);
+  for (int t = 0; t < n; ++t) {
+    R.fc_in = ctx->f[ctx->cur];
+    R.fc_out = ctx->f[1 - ctx->cur];
+    CK(launch_refine_step(R, ctx->stream));
+    ctx->cur = 1 - ctx->cur;  // two fine steps leave the fine state in its own buffer
+  }
+  return LBM_OK;
+}
+
+// Launch description of a coupled pair (coarse buffers set per step).
+static RefLaunch refine_launch(const lbm_ctx *ctx) {
+  const lbm_ctx *fine = ctx->ref_fine;
   RefLaunch R;
   R.gc = ctx->g;
   R.gf = fine->g;
@@ -817,13 +837,8 @@ static lbm_status refine_steps(lbm_ctx *ctx, int n) {
   R.j0 = ctx->ref_j0;
   R.fields = ctx->ref_ws;
   R.err_c = R.err_f = ctx->err;
-  for (int t = 0; t < n; ++t) {
-    R.fc_in = ctx->f[ctx->cur];
-    R.fc_out = ctx->f[1 - ctx->cur];
-    CK(launch_refine_step(R, ctx->stream));
-    ctx->cur = 1 - ctx->cur;  // two fine steps leave the fine state in its own buffer
-  }
-  return LBM_OK;
+  R.fc_in = R.fc_out = nullptr;
+  return R;
 }
 
 static lbm_status copy_in(lbm_ctx *ctx, void *dst, const void *src, size_t bytes) {

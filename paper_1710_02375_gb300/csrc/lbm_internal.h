@@ -147,13 +147,16 @@ struct RefLaunch {
   double beta_c, beta_f;
   int bgk, variant;
   int i0, j0;              // first covered coarse cell
-  void *fields;            // refine_workspace_bytes scratch
+  void *fields;            // refine_workspace_bytes scratch (set up by launch_refine_init)
   int *err_c, *err_f;
 };
-// One coarse step of the refined pair (coarse sweep, two fine steps with
-// the Grad fill of the fine boundary nodes, restriction).
+// One coarse step of the refined pair (coarse sweep, the sampling pass with
+// the Grad fill of the fine boundary nodes, two fine sweeps, restriction).
 cudaError_t launch_refine_step(const RefLaunch &R, cudaStream_t s);
-size_t refine_workspace_bytes(int storage, int nxc, int nyc, int nfx, int nfy);
+// The coarse-cell mask of the scratch (cells the coarse sweep skips); once
+// per coupling.
+cudaError_t launch_refine_init(const RefLaunch &R, cudaStream_t s);
+size_t refine_workspace_bytes(int storage, const Grid &gc, int nfx, int nfy);
 
 }  // namespace kbc
 

@@ -16,9 +16,11 @@
 //     fine velocity (doubled to coarse units; the ghost ring holds the
 //     coarse values of t + 1), Grad's approximation with beta_c and the
 //     coarse KBC collision: its stored post-collision state.
-// Order per coarse step: coarse fields at t, the coarse sweep over all cells,
-// coarse fields at t + 1, two fine steps (fill, sweep), the fine fields on
-// the ghost-extended patch, the restriction.
+// Order per coarse step: the coarse sweep over all cells; one sampling pass
+// (the coarse fields at t and t + 1 interpolated to the fine boundary nodes,
+// those at t + 1 to the ring around the patch); two fine steps (fill,
+// sweep); the restriction, with the fine moments of each tile staged in
+// shared memory.
 #include "kbc_collide.cuh"
 #include "lbm_internal.h"
 
@@ -33,46 +35,17 @@ __device__ __forceinline__ void ref_cubic_w(C t, C (&w)[4]) {
   w[3] = (t + (C)1) * t * (t - (C)1) / (C)6;
 }
 
+// the k-th of those weights (selected, not indexed: k varies across lanes)
+template <class C>
+__device__ __forceinline__ C ref_cubic_wk(C t, int k) {
+  C w[4];
+  ref_cubic_w(t, w);
+  return k == 0 ? w[0] : (k == 1 ? w[1] : (k == 2 ? w[2] : w[3]));
+}
+
 __device__ __forceinline__ int ref_wrap(int a, int n) {
   a %= n;
   return a < 0 ? a + n : a;
-}
-
-// Coarse fields at a position (X, Y) in coarse-cell coordinates: the density
-// deviation rho - 1, u[2], G[2][2] (coarse units), bicubic over the periodic
-// coarse grid.  The density is carried as its deviation from 1 in every
-// field and sum (the weights sum to 1), so FP32 keeps its precision.
-template <class C>
-struct RefSample {
-  C drho, u[2], G[2][2];
-};
-template <class C>
-__device__ __forceinline__ RefSample<C> ref_sample(const C *__restrict__ drho,
-                                                   const C *__restrict__ u,
-                                                   const C *__restrict__ G, int nx, int ny,
-                                                   double X, double Y) {
-  const double sx = X - 0.5, sy = Y - 0.5;
-  const int ix = (int)floor(sx), iy = (int)floor(sy);
-  C wx[4], wy[4];
-  ref_cubic_w((C)(sx - ix), wx);
-  ref_cubic_w((C)(sy - iy), wy);
-  const long long n = (long long)nx * ny;
-  RefSample<C> s;
-  s.drho = (C)0;
-  s.u[0] = s.u[1] = (C)0;
-  s.G[0][0] = s.G[0][1] = s.G[1][0] = s.G[1][1] = (C)0;
-  for (int b = 0; b < 4; ++b) {
-    const long long row = (long long)ref_wrap(iy - 1 + b, ny) * nx;
-    for (int a = 0; a < 4; ++a) {
-      const long long k = row + ref_wrap(ix - 1 + a, nx);
-      const C w = wx[a] * wy[b];
-      s.drho += w * drho[k];
-      s.u[0] += w * u[k];
-      s.u[1] += w * u[n + k];
-      for (int q = 0; q < 4; ++q) s.G[q / 2][q % 2] += w * G[q * n + k];
-    }
-  }
-  return s;
 }
 
 // Grad's approximation of direction i (D2Q9) for rho = 1 + drho, u and Pi -
@@ -98,213 +71,262 @@ __device__ __forceinline__ void ref_pn(C rho, const C (&u)[2], const C (&G)[2][2
       Pn[a][b] = rho * u[a] * u[b] - rho * cs2 / ((C)2 * beta) * (G[a][b] + G[b][a]);
 }
 
-// ---------------------------------------------------------------- coarse fields
-// The interpolation reads the coarse fields only within a few cells of the
-// patch edge: the fine boundary nodes and the ring sit within 1/4 of a cell
-// of it, their bicubic stencils reach 2 cells across it, the central
-// differences of grad u one more.  A RefBand is the frame of cells [x0, x0 +
-// w) x [y0, y0 + h) (coordinates wrapped onto the periodic grid) less the
-// inner rectangle [ix0, ix1) x [iy0, iy1), which no stencil reaches.
-struct RefBand {
-  int x0, y0, w, h;
-  int ix0, ix1, iy0, iy1;
-};
-// The band of the cells whose fields (margin 3: rho, u) or gradients (margin 2)
-// are read, for the patch of mx x my cells from (i0, j0).
-static RefBand ref_band(int nxc, int nyc, int i0, int j0, int mx, int my, int margin) {
-  RefBand b;
-  b.w = mx + 2 * margin;
-  b.h = my + 2 * margin;
-  b.x0 = i0 - margin;
-  b.y0 = j0 - margin;
-  if (b.w >= nxc) { b.w = nxc; b.x0 = 0; }
-  if (b.h >= nyc) { b.h = nyc; b.y0 = 0; }
-  b.ix0 = i0 + margin;
-  b.ix1 = i0 + mx - margin;
-  b.iy0 = j0 + margin;
-  b.iy1 = j0 + my - margin;
-  return b;
-}
-// Cell t of the band's frame, or false for the inner rectangle and the
-// threads past the frame.
-__device__ __forceinline__ bool band_cell(const RefBand &b, int nx, int ny, long long t, int &x,
-                                          int &y) {
-  if (t >= (long long)b.w * b.h) return false;
-  const int lx = (int)(t % b.w), ly = (int)(t / b.w);
-  const int ux = b.x0 + lx, uy = b.y0 + ly;  // unwrapped
-  if (ux >= b.ix0 && ux < b.ix1 && uy >= b.iy0 && uy < b.iy1) return false;
-  x = ref_wrap(ux, nx);
-  y = ref_wrap(uy, ny);
-  return true;
-}
 
-// rho - 1 and u = j / rho of the coarse state over a band (linear index k =
-// y nx + x of the coarse grid)
-template <int S>
-__global__ void k_ref_coarse_fields(Grid g, RefBand band, const typename Store<S>::T *__restrict__ f,
-                                    typename Store<S>::C *__restrict__ drho,
-                                    typename Store<S>::C *__restrict__ u) {
-  using L = Lat<9>;
-  using St = Store<S>;
-  using C = typename St::C;
-  int x, y;
-  if (!band_cell(band, g.nx, g.ny, blockIdx.x * (long long)blockDim.x + threadIdx.x, x, y)) return;
-  const long long n = (long long)g.nx * g.ny;
-  const long long k = (long long)y * g.nx + x;
-  const long long s = sidx(g, x + g.px, y + g.py, 0);
-  C d = (C)0, jx = (C)0, jy = (C)0;
-  for (int i = 0; i < 9; ++i) {
-    const C v = St::load(f + (long long)i * g.N + s, (C)weight<L>(i));
-    d += v;
-    jx += (C)L::cx(i) * v;
-    jy += (C)L::cy(i) * v;
-  }
-  const C r = (C)1 + d;
-  drho[k] = d;
-  u[k] = jx / r;
-  u[n + k] = jy / r;
-}
-
-// G[a][b] = d u_a / d x_b by central differences (periodic), coarse units,
-// over a band
-template <class C>
-__global__ void k_ref_coarse_grad(int nx, int ny, RefBand band, const C *__restrict__ u,
-                                  C *__restrict__ G) {
-  int x, y;
-  if (!band_cell(band, nx, ny, blockIdx.x * (long long)blockDim.x + threadIdx.x, x, y)) return;
-  const long long n = (long long)nx * ny;
-  const long long k = (long long)y * nx + x;
-  const long long xp = (long long)y * nx + ref_wrap(x + 1, nx), xm = (long long)y * nx + ref_wrap(x - 1, nx);
-  const long long yp = (long long)ref_wrap(y + 1, ny) * nx + x, ym = (long long)ref_wrap(y - 1, ny) * nx + x;
-  for (int a = 0; a < 2; ++a) {
-    G[(2 * a) * n + k] = (C)0.5 * (u[a * n + xp] - u[a * n + xm]);
-    G[(2 * a + 1) * n + k] = (C)0.5 * (u[a * n + yp] - u[a * n + ym]);
-  }
-}
-
-// ---------------------------------------------------------------- fine fill
-// One thread per fine boundary node (the patch perimeter, p along x, q
-// along y): Grad's approximation at the node from the coarse fields at time
-// t + w, into the ghost slots of the directions it misses.
-template <int S>
-__global__ void k_ref_fill(Grid gf, typename Store<S>::T *__restrict__ ff, int nxc, int nyc,
-                           const typename Store<S>::C *__restrict__ r0,
-                           const typename Store<S>::C *__restrict__ u0,
-                           const typename Store<S>::C *__restrict__ G0,
-                           const typename Store<S>::C *__restrict__ r1,
-                           const typename Store<S>::C *__restrict__ u1,
-                           const typename Store<S>::C *__restrict__ G1, int i0, int j0,
-                           typename Store<S>::C w, typename Store<S>::C beta_f) {
-  using L = Lat<9>;
-  using St = Store<S>;
-  using C = typename St::C;
-  const int nfx = gf.nx, nfy = gf.ny;
-  const int nper = 2 * nfx + 2 * (nfy - 2);
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nper) return;
-  int p, q;
+// ---------------------------------------------------------------- node lists
+// Fill nodes: the perimeter of the fine patch (p along x, q along y), bottom
+// row, top row, then the left and right columns without their corners.
+__host__ __device__ inline int ref_nfill(int nfx, int nfy) { return 2 * nfx + 2 * (nfy - 2); }
+__device__ __forceinline__ void ref_fill_node(int t, int nfx, int nfy, int &p, int &q) {
   if (t < nfx) { p = t; q = 0; }
   else if (t < 2 * nfx) { p = t - nfx; q = nfy - 1; }
   else if (t < 2 * nfx + nfy - 2) { p = 0; q = t - 2 * nfx + 1; }
   else { p = nfx - 1; q = t - (2 * nfx + nfy - 2) + 1; }
-  const double X = i0 + 0.5 * (p + 0.5), Y = j0 + 0.5 * (q + 0.5);
-  const RefSample<C> a = ref_sample(r0, u0, G0, nxc, nyc, X, Y);
-  const RefSample<C> b = ref_sample(r1, u1, G1, nxc, nyc, X, Y);
-  const C drho = ((C)1 - w) * a.drho + w * b.drho, rho = (C)1 + drho;
-  C u[2], G[2][2], Pn[2][2];
-  for (int c = 0; c < 2; ++c) u[c] = ((C)1 - w) * a.u[c] + w * b.u[c];
-  for (int c = 0; c < 2; ++c)
-    for (int d = 0; d < 2; ++d) G[c][d] = (C)0.5 * (((C)1 - w) * a.G[c][d] + w * b.G[c][d]);
-  ref_pn(rho, u, G, beta_f, Pn);
+}
+// Ring nodes: the perimeter of the patch extended by one node, p in [-1,
+// nfx], q in [-1, nfy]: the row q = -1, the row q = nfy, then the columns p =
+// -1 and p = nfx over q in [0, nfy).
+__host__ __device__ inline int ref_nring(int nfx, int nfy) { return 2 * (nfx + 2) + 2 * nfy; }
+__device__ __forceinline__ void ref_ring_node(int t, int nfx, int nfy, int &p, int &q) {
+  const int rw = nfx + 2;
+  if (t < rw) { p = t - 1; q = -1; }
+  else if (t < 2 * rw) { p = t - rw - 1; q = nfy; }
+  else if (t < 2 * rw + nfy) { p = -1; q = t - 2 * rw; }
+  else { p = nfx; q = t - 2 * rw - nfy; }
+}
+__device__ __forceinline__ int ref_ring_index(int p, int q, int nfx, int nfy) {
+  const int rw = nfx + 2;
+  if (q == -1) return p + 1;
+  if (q == nfy) return rw + p + 1;
+  if (p == -1) return 2 * rw + q;
+  return 2 * rw + nfy + q;
+}
+
+// Sampled values: fill node n holds (rho - 1, u_x, u_y, G_xx, G_xy, G_yx,
+// G_yy) at t, then at t + 1 (G[a][b] = d u_a / d x_b in coarse units), ring
+// node m holds (rho - 1, u_x, u_y) at t + 1; structure of arrays.
+constexpr int kRefFillVals = 14, kRefRingVals = 3;
+
+// rho - 1 and u = j / rho of coarse cell (x, y) from its stored populations
+template <int S>
+__device__ __forceinline__ void ref_cell(const Grid &g, const typename Store<S>::T *__restrict__ f,
+                                         int x, int y, typename Store<S>::C &d,
+                                         typename Store<S>::C (&u)[2]) {
+  using L = Lat<9>;
+  using St = Store<S>;
+  using C = typename St::C;
+  const long long s = sidx(g, x + g.px, y + g.py, 0);
+  C dd = (C)0, jx = (C)0, jy = (C)0;
+#pragma unroll
   for (int i = 0; i < 9; ++i) {
-    const int ps = p - L::cx(i), qs = q - L::cy(i);
-    if (ps >= 0 && ps < nfx && qs >= 0 && qs < nfy) continue;
-    // the ghost slot of direction i that the node pulls from
-    const long long s = sidx(gf, ps + gf.px, qs + gf.py, 0);
-    St::store(ff + (long long)i * gf.N + s, ref_grad_dev(i, drho, rho, u, Pn),
-              (C)(1.0 / weight<L>(i)));
+    const C v = St::load(f + (long long)i * g.N + s, (C)weight<L>(i));
+    dd += v;
+    jx += (C)L::cx(i) * v;
+    jy += (C)L::cy(i) * v;
+  }
+  d = dd;
+  u[0] = jx / ((C)1 + dd);
+  u[1] = jy / ((C)1 + dd);
+}
+
+// ---------------------------------------------------------------- fine fill
+// Grad's approximation of direction i at fill node (p, q) from the sampled
+// coarse fields v (kRefFillVals values) at time t + w, into the ghost slot
+// the node's pull reads when that direction is missing (no sweep writes
+// ghost slots).
+template <int S>
+__device__ __forceinline__ void ref_fill_dir(const Grid &gf, typename Store<S>::T *__restrict__ ff,
+                                             int p, int q, int i,
+                                             const typename Store<S>::C (&v)[kRefFillVals],
+                                             typename Store<S>::C w, typename Store<S>::C beta_f) {
+  using L = Lat<9>;
+  using St = Store<S>;
+  using C = typename St::C;
+  const int ps = p - L::cx(i), qs = q - L::cy(i);
+  if (ps >= 0 && ps < gf.nx && qs >= 0 && qs < gf.ny) return;
+  const C drho = ((C)1 - w) * v[0] + w * v[7], rho = (C)1 + drho;
+  C u[2], G[2][2], Pn[2][2];
+  for (int c = 0; c < 2; ++c) u[c] = ((C)1 - w) * v[1 + c] + w * v[8 + c];
+  for (int c = 0; c < 2; ++c)
+    for (int d = 0; d < 2; ++d)
+      G[c][d] = (C)0.5 * (((C)1 - w) * v[3 + 2 * c + d] + w * v[10 + 2 * c + d]);
+  ref_pn(rho, u, G, beta_f, Pn);
+  const long long s = sidx(gf, ps + gf.px, qs + gf.py, 0);
+  St::store(ff + (long long)i * gf.N + s, ref_grad_dev(i, drho, rho, u, Pn),
+            (C)(1.0 / weight<L>(i)));
+}
+
+// ---------------------------------------------------------------- sampling
+// One warp per sampled node.  The node at (X, Y) in coarse-cell coordinates
+// interpolates over the 4 x 4 cells floor(X - 1/2) - 1 .. + 2 per axis
+// (wrapped onto the periodic grid); their central differences reach one
+// cell further.  The 32 lanes take the 6 x 6 block around the stencil less
+// its corners (lane -> block cell (cx, cy): row cy = 0 cx = 1..4, rows 1..4
+// cx = 0..5, row 5 cx = 1..4), each forms its cell's rho - 1 and u from the
+// coarse populations at t (fc0) and t + 1 (fc1), the 16 stencil lanes take
+// grad u from their neighbours' u by shuffles, and the weighted values are
+// summed over the warp.  A fill node then writes the ghost slots of both
+// fine steps, one (time, direction) per lane: t + 1/2 into fa (read by the
+// first fine sweep), t + 1 into fb (read by the second); a ring node stores
+// its fields at t + 1 for the restriction.
+__device__ __forceinline__ void ref_block_cell(int lane, int &cx, int &cy) {
+  if (lane < 4) { cx = lane + 1; cy = 0; }
+  else if (lane < 28) { cx = (lane - 4) % 6; cy = (lane - 4) / 6 + 1; }
+  else { cx = lane - 27; cy = 5; }
+}
+__device__ __forceinline__ int ref_block_lane(int cx, int cy) {
+  return cy == 0 ? cx - 1 : (cy == 5 ? cx + 27 : 4 + (cy - 1) * 6 + cx);
+}
+
+template <int S>
+__global__ void __launch_bounds__(256)
+    k_ref_sample(Grid gc, const typename Store<S>::T *__restrict__ fc0,
+                 const typename Store<S>::T *__restrict__ fc1, Grid gf,
+                 typename Store<S>::T *__restrict__ fa, typename Store<S>::T *__restrict__ fb,
+                 int i0, int j0, typename Store<S>::C beta_f,
+                 typename Store<S>::C *__restrict__ sring) {
+  using C = typename Store<S>::C;
+  const int nfx = gf.nx, nfy = gf.ny;
+  const int node = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  const int nfill = ref_nfill(nfx, nfy), nring = ref_nring(nfx, nfy);
+  if (node >= nfill + nring) return;  // the whole warp
+  const bool fill = node < nfill;
+  int p, q;
+  if (fill) ref_fill_node(node, nfx, nfy, p, q);
+  else ref_ring_node(node - nfill, nfx, nfy, p, q);
+  // X - 1/2 = i0 + (2 p - 1) / 4 exactly: stencil origin and offset in
+  // quarter cells, in integers (floor by arithmetic shift)
+  const int nx4 = 4 * i0 + 2 * p - 1, ny4 = 4 * j0 + 2 * q - 1;
+  const int ix = nx4 >> 2, iy = ny4 >> 2;
+  const C tx = (C)0.25 * (C)(nx4 & 3), ty = (C)0.25 * (C)(ny4 & 3);
+  int cx, cy;
+  ref_block_cell(lane, cx, cy);
+  const bool inner = cx >= 1 && cx <= 4 && cy >= 1 && cy <= 4;
+  const C w = inner ? ref_cubic_wk(tx, cx - 1) * ref_cubic_wk(ty, cy - 1) : (C)0;
+  const int x = ref_wrap(ix - 2 + cx, gc.nx), y = ref_wrap(iy - 2 + cy, gc.ny);
+  // neighbour lanes of a stencil lane (own lane elsewhere: unused)
+  const int le = inner ? ref_block_lane(cx + 1, cy) : lane, lw = inner ? ref_block_lane(cx - 1, cy) : lane;
+  const int ln = inner ? ref_block_lane(cx, cy + 1) : lane, ls = inner ? ref_block_lane(cx, cy - 1) : lane;
+  // both time levels' loads first (ring nodes: t + 1 only)
+  C dt[2] = {(C)0, (C)0}, ut[2][2] = {{(C)0, (C)0}, {(C)0, (C)0}};
+  if (fill) ref_cell<S>(gc, fc0, x, y, dt[0], ut[0]);
+  ref_cell<S>(gc, fc1, x, y, dt[1], ut[1]);
+  C acc[kRefFillVals];
+#pragma unroll
+  for (int tt = 0; tt < 2; ++tt) {
+    C *o = acc + 7 * tt;
+    const C d = dt[tt], u[2] = {ut[tt][0], ut[tt][1]};
+    o[0] = w * d;
+    o[1] = w * u[0];
+    o[2] = w * u[1];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const C ue = __shfl_sync(0xffffffffu, u[c], le), uw = __shfl_sync(0xffffffffu, u[c], lw);
+      const C un = __shfl_sync(0xffffffffu, u[c], ln), us = __shfl_sync(0xffffffffu, u[c], ls);
+      o[3 + 2 * c] = w * ((C)0.5 * (ue - uw));
+      o[4 + 2 * c] = w * ((C)0.5 * (un - us));
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kRefFillVals; ++k)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
+  // every lane holds the sums: lanes 0..17 write one (time, direction) each
+  if (fill) {
+    if (lane < 18) {
+      const bool second = lane >= 9;
+      ref_fill_dir<S>(gf, second ? fb : fa, p, q, second ? lane - 9 : lane, acc,
+                      second ? (C)1 : (C)0.5, beta_f);
+    }
+  } else if (lane < kRefRingVals) {
+    const int m = node - nfill;
+    sring[(long long)lane * nring + m] = lane == 0 ? acc[7] : (lane == 1 ? acc[8] : acc[9]);
   }
 }
 
 // ---------------------------------------------------------------- restriction
-// Fine fields on the patch extended by one ring: rho - 1, j[2], u[2] at (p, q) in
-// [-1, nfx] x [-1, nfy], index (q + 1) * (nfx + 2) + (p + 1); the ring from the
-// coarse fields at t + 1.
-template <int S>
-__global__ void k_ref_fine_fields(Grid gf, const typename Store<S>::T *__restrict__ ff, int nxc,
-                                  int nyc, const typename Store<S>::C *__restrict__ r1,
-                                  const typename Store<S>::C *__restrict__ u1,
-                                  const typename Store<S>::C *__restrict__ G1, int i0, int j0,
-                                  typename Store<S>::C *__restrict__ ext) {
-  using L = Lat<9>;
-  using St = Store<S>;
-  using C = typename St::C;
-  const int ex = gf.nx + 2, ey = gf.ny + 2;
-  const long long ne = (long long)ex * ey;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= ne) return;
-  const int p = (int)(t % ex) - 1, q = (int)(t / ex) - 1;
-  C d, j[2], u[2];
-  if (p >= 0 && p < gf.nx && q >= 0 && q < gf.ny) {
-    const long long s = sidx(gf, p + gf.px, q + gf.py, 0);
-    d = (C)0;
-    j[0] = j[1] = (C)0;
-    for (int i = 0; i < 9; ++i) {
-      const C v = St::load(ff + (long long)i * gf.N + s, (C)weight<L>(i));
-      d += v;
-      j[0] += (C)L::cx(i) * v;
-      j[1] += (C)L::cy(i) * v;
-    }
-    u[0] = j[0] / ((C)1 + d);
-    u[1] = j[1] / ((C)1 + d);
-  } else {
-    const RefSample<C> c = ref_sample(r1, u1, G1, nxc, nyc, i0 + 0.5 * (p + 0.5), j0 + 0.5 * (q + 0.5));
-    d = c.drho;
-    u[0] = c.u[0];
-    u[1] = c.u[1];
-    j[0] = ((C)1 + d) * u[0];
-    j[1] = ((C)1 + d) * u[1];
-  }
-  ext[t] = d;
-  ext[ne + t] = j[0];
-  ext[2 * ne + t] = j[1];
-  ext[3 * ne + t] = u[0];
-  ext[4 * ne + t] = u[1];
-}
-
-// One thread per covered coarse cell (I, J): cubic midpoint values, Grad's
+// A CTA restricts a tile of kRefTX x kRefTY covered coarse cells.  It first
+// stages (rho - 1, j_x, j_y, u_x, u_y) of the fine nodes the tile's cubic
+// stencils reach, 2 I0 - 1 .. 2 (I0 + kRefTX) along x and the same along y
+// (ring nodes beyond the patch from the sampled coarse fields at t + 1),
+// then each thread takes one cell (I, J): the cubic midpoint values, Grad's
 // approximation with beta_c, the coarse collision, the stored state.
+constexpr int kRefTX = 32, kRefTY = 8;
+constexpr int kRefEX = 2 * kRefTX + 2, kRefEY = 2 * kRefTY + 2;
+
 template <int S>
-__global__ void k_ref_restrict(Grid gc, typename Store<S>::T *__restrict__ fc, int nfx, int nfy,
-                               const typename Store<S>::C *__restrict__ ext, int i0, int j0,
-                               typename Store<S>::C beta_c, int bgk) {
+__global__ void __launch_bounds__(kRefTX * kRefTY)
+    k_ref_restrict(Grid gc, typename Store<S>::T *__restrict__ fc, Grid gf,
+                   const typename Store<S>::T *__restrict__ ff,
+                   const typename Store<S>::C *__restrict__ sring, int i0, int j0,
+                   typename Store<S>::C beta_c, int bgk) {
   using L = Lat<9>;
   using St = Store<S>;
   using C = typename St::C;
-  const int mx = nfx / 2, my = nfy / 2;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= mx * my) return;
-  const int I = t % mx, J = t / mx;
-  const int ex = nfx + 2;
-  const long long ne = (long long)ex * (nfy + 2);
+  __shared__ C sm[5][kRefEY][kRefEX];
+  const int nfx = gf.nx, nfy = gf.ny, mx = nfx / 2, my = nfy / 2;
+  const int nring = ref_nring(nfx, nfy);
+  const int I0 = blockIdx.x * kRefTX, J0 = blockIdx.y * kRefTY;
+  const int p0 = 2 * I0 - 1, q0 = 2 * J0 - 1;  // fine node of sm[.][0][0]
+  constexpr int kPer = (kRefEX * kRefEY + kRefTX * kRefTY - 1) / (kRefTX * kRefTY);
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const int e = threadIdx.x + k * kRefTX * kRefTY;
+    if (e >= kRefEX * kRefEY) continue;
+    const int ex = e % kRefEX, ey = e / kRefEX;
+    const int p = p0 + ex, q = q0 + ey;
+    C d = (C)0, j[2] = {(C)0, (C)0}, u[2] = {(C)0, (C)0};
+    if (p >= 0 && p < nfx && q >= 0 && q < nfy) {
+      const long long s = sidx(gf, p + gf.px, q + gf.py, 0);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const C v = St::load(ff + (long long)i * gf.N + s, (C)weight<L>(i));
+        d += v;
+        j[0] += (C)L::cx(i) * v;
+        j[1] += (C)L::cy(i) * v;
+      }
+      u[0] = j[0] / ((C)1 + d);
+      u[1] = j[1] / ((C)1 + d);
+    } else if (p >= -1 && p <= nfx && q >= -1 && q <= nfy) {
+      const int m = ref_ring_index(p, q, nfx, nfy);
+      d = sring[m];
+      u[0] = sring[nring + m];
+      u[1] = sring[2 * nring + m];
+      j[0] = ((C)1 + d) * u[0];
+      j[1] = ((C)1 + d) * u[1];
+    }
+    sm[0][ey][ex] = d;
+    sm[1][ey][ex] = j[0];
+    sm[2][ey][ex] = j[1];
+    sm[3][ey][ex] = u[0];
+    sm[4][ey][ex] = u[1];
+  }
+  __syncthreads();
+  const int tx = threadIdx.x % kRefTX, ty = threadIdx.x / kRefTX;
+  const int I = I0 + tx, J = J0 + ty;
+  if (I >= mx || J >= my) return;
+  const int lx = 2 * tx, ly = 2 * ty;  // sm position of fine node (2 I - 1, 2 J - 1)
   const C wm[4] = {(C)(-1.0 / 16.0), (C)(9.0 / 16.0), (C)(9.0 / 16.0), (C)(-1.0 / 16.0)};
-  auto at = [&](int f, int p, int q) -> C { return ext[f * ne + (long long)(q + 1) * ex + (p + 1)]; };
   C d = (C)0, j[2] = {(C)0, (C)0};
+#pragma unroll
   for (int b = 0; b < 4; ++b)
+#pragma unroll
     for (int a = 0; a < 4; ++a) {
-      const int p = 2 * I - 1 + a, q = 2 * J - 1 + b;
       const C w = wm[a] * wm[b];
-      d += w * at(0, p, q);
-      j[0] += w * at(1, p, q);
-      j[1] += w * at(2, p, q);
+      d += w * sm[0][ly + b][lx + a];
+      j[0] += w * sm[1][ly + b][lx + a];
+      j[1] += w * sm[2][ly + b][lx + a];
     }
   C G[2][2];
+#pragma unroll
   for (int c = 0; c < 2; ++c) {
     C dx = (C)0, dy = (C)0;
+#pragma unroll
     for (int b = 0; b < 4; ++b) {
-      const int q = 2 * J - 1 + b, p = 2 * I - 1 + b;
-      dx += wm[b] * (at(3 + c, 2 * I + 1, q) - at(3 + c, 2 * I, q));
-      dy += wm[b] * (at(3 + c, p, 2 * J + 1) - at(3 + c, p, 2 * J));
+      // d/dx: the pairs (2I, 2I + 1) on the rows 2J - 1 .. 2J + 2; d/dy: the
+      // pairs (2J, 2J + 1) on the columns 2I - 1 .. 2I + 2
+      dx += wm[b] * (sm[3 + c][ly + b][lx + 2] - sm[3 + c][ly + b][lx + 1]);
+      dy += wm[b] * (sm[3 + c][ly + 2][lx + b] - sm[3 + c][ly + 1][lx + b]);
     }
     G[c][0] = (C)2 * dx;
     G[c][1] = (C)2 * dy;
@@ -314,54 +336,60 @@ __global__ void k_ref_restrict(Grid gc, typename Store<S>::T *__restrict__ fc, i
   C Pn[2][2];
   ref_pn(r, u, G, beta_c, Pn);
   C v[9];
+#pragma unroll
   for (int i = 0; i < 9; ++i) v[i] = ref_grad_dev(i, d, r, u, Pn);
   collide_v<L, S == STORE_F32, C>(v, beta_c, bgk != 0);
   const long long s = sidx(gc, i0 + I + gc.px, j0 + J + gc.py, 0);
+#pragma unroll
   for (int i = 0; i < 9; ++i)
     St::store(fc + (long long)i * gc.N + s, v[i], (C)(1.0 / weight<L>(i)));
 }
 
 // ---------------------------------------------------------------- launchers
+// Coarse cells that need no coarse step: those more than kRefKeep cells
+// inside the patch edge (the restriction replaces them, and no stencil of
+// the sampling reads them).
+constexpr int kRefKeep = 3;
+__global__ void k_ref_skip(Grid gc, uint8_t *__restrict__ skip, int x0, int x1, int y0, int y1) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int w = x1 - x0;
+  if (t >= (long long)w * (y1 - y0)) return;
+  const int x = x0 + (int)(t % w), y = y0 + (int)(t / w);
+  skip[sidx(gc, x + gc.px, y + gc.py, 0)] = NODE_GHOST;
+}
+
+static size_t ref_ring_bytes(int storage, int nfx, int nfy) {
+  const size_t cb = storage == STORE_F64 ? 8 : 4;
+  return (cb * kRefRingVals * (size_t)ref_nring(nfx, nfy) + 255) / 256 * 256;
+}
+
 template <int S>
 static cudaError_t ref_step_t(const RefLaunch &R, cudaStream_t s) {
   using T = typename Store<S>::T;
   using C = typename Store<S>::C;
   const Grid &gc = R.gc, &gf = R.gf;
-  const long long nc = (long long)gc.nx * gc.ny;
-  C *r0 = (C *)R.fields, *u0 = r0 + nc, *G0 = u0 + 2 * nc;
-  C *r1 = G0 + 4 * nc, *u1 = r1 + nc, *G1 = u1 + 2 * nc;
-  C *ext = G1 + 4 * nc;
-  const int b = 256;
-  const int mx = gf.nx / 2, my = gf.ny / 2;
-  const RefBand bu = ref_band(gc.nx, gc.ny, R.i0, R.j0, mx, my, 3);
-  const RefBand bg = ref_band(gc.nx, gc.ny, R.i0, R.j0, mx, my, 2);
-  const unsigned nbu = (unsigned)(((long long)bu.w * bu.h + b - 1) / b);
-  const unsigned nbg = (unsigned)(((long long)bg.w * bg.h + b - 1) / b);
-  k_ref_coarse_fields<S><<<nbu, b, 0, s>>>(gc, bu, (const T *)R.fc_in, r0, u0);
-  k_ref_coarse_grad<C><<<nbg, b, 0, s>>>(gc.nx, gc.ny, bg, u0, G0);
-  cudaError_t e = launch_sweep(9, S, gc, R.fc_in, R.fc_out, nullptr, R.beta_c, R.bgk, R.err_c, s,
+  const int nfill = ref_nfill(gf.nx, gf.ny), nring = ref_nring(gf.nx, gf.ny);
+  C *sring = (C *)R.fields;
+  const uint8_t *skip = (const uint8_t *)R.fields + ref_ring_bytes(S, gf.nx, gf.ny);
+  cudaError_t e = launch_sweep(9, S, gc, R.fc_in, R.fc_out, skip, R.beta_c, R.bgk, R.err_c, s,
                                R.variant);
   if (e != cudaSuccess) return e;
-  k_ref_coarse_fields<S><<<nbu, b, 0, s>>>(gc, bu, (const T *)R.fc_out, r1, u1);
-  k_ref_coarse_grad<C><<<nbg, b, 0, s>>>(gc.nx, gc.ny, bg, u1, G1);
-  const int nper = 2 * gf.nx + 2 * (gf.ny - 2);
   void *fa = R.ff[R.cur_f], *fb = R.ff[1 - R.cur_f];
+  const long long nthr = 32LL * (nfill + nring);
+  k_ref_sample<S><<<(unsigned)((nthr + 255) / 256), 256, 0, s>>>(
+      gc, (const T *)R.fc_in, (const T *)R.fc_out, gf, (T *)fa, (T *)fb, R.i0, R.j0, (C)R.beta_f,
+      sring);
   for (int k = 0; k < 2; ++k) {
-    k_ref_fill<S><<<(nper + 127) / 128, 128, 0, s>>>(gf, (T *)fa, gc.nx, gc.ny, r0, u0, G0, r1, u1,
-                                                     G1, R.i0, R.j0, (C)(0.5 * (k + 1)),
-                                                     (C)R.beta_f);
     e = launch_sweep(9, S, gf, fa, fb, R.flags_f, R.beta_f, R.bgk, R.err_f, s, R.variant);
     if (e != cudaSuccess) return e;
     void *tmp = fa;
     fa = fb;
     fb = tmp;
   }
-  const long long ne = (long long)(gf.nx + 2) * (gf.ny + 2);
-  k_ref_fine_fields<S><<<(unsigned)((ne + b - 1) / b), b, 0, s>>>(gf, (const T *)fa, gc.nx, gc.ny,
-                                                                  r1, u1, G1, R.i0, R.j0, ext);
-  const int ncov = (gf.nx / 2) * (gf.ny / 2);
-  k_ref_restrict<S><<<(ncov + 127) / 128, 128, 0, s>>>(gc, (T *)R.fc_out, gf.nx, gf.ny, ext, R.i0,
-                                                       R.j0, (C)R.beta_c, R.bgk);
+  const dim3 grid((unsigned)((gf.nx / 2 + kRefTX - 1) / kRefTX),
+                  (unsigned)((gf.ny / 2 + kRefTY - 1) / kRefTY));
+  k_ref_restrict<S><<<grid, kRefTX * kRefTY, 0, s>>>(gc, (T *)R.fc_out, gf, (const T *)fa, sring,
+                                                     R.i0, R.j0, (C)R.beta_c, R.bgk);
   return cudaGetLastError();
 }
 
@@ -371,10 +399,21 @@ cudaError_t launch_refine_step(const RefLaunch &R, cudaStream_t s) {
   return cudaErrorInvalidValue;
 }
 
-size_t refine_workspace_bytes(int storage, int nxc, int nyc, int nfx, int nfy) {
-  const size_t cb = storage == STORE_F64 ? 8 : 4;
-  const size_t nc = (size_t)nxc * nyc, ne = (size_t)(nfx + 2) * (nfy + 2);
-  return cb * (14 * nc + 5 * ne);
+cudaError_t launch_refine_init(const RefLaunch &R, cudaStream_t s) {
+  uint8_t *skip = (uint8_t *)R.fields + ref_ring_bytes(R.storage, R.gf.nx, R.gf.ny);
+  cudaError_t e = cudaMemsetAsync(skip, NODE_FLUID, (size_t)R.gc.N, s);
+  if (e != cudaSuccess) return e;
+  const int mx = R.gf.nx / 2, my = R.gf.ny / 2;
+  const int x0 = R.i0 + kRefKeep, x1 = R.i0 + mx - kRefKeep;
+  const int y0 = R.j0 + kRefKeep, y1 = R.j0 + my - kRefKeep;
+  if (x1 <= x0 || y1 <= y0) return cudaSuccess;
+  const long long n = (long long)(x1 - x0) * (y1 - y0);
+  k_ref_skip<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(R.gc, skip, x0, x1, y0, y1);
+  return cudaGetLastError();
+}
+
+size_t refine_workspace_bytes(int storage, const Grid &gc, int nfx, int nfy) {
+  return ref_ring_bytes(storage, nfx, nfy) + (size_t)gc.N;
 }
 
 }  // namespace kbc
