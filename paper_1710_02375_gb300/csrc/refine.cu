@@ -48,6 +48,16 @@ __device__ __forceinline__ int ref_wrap(int a, int n) {
   return a < 0 ? a + n : a;
 }
 
+// D2Q9 weight of direction i in the compute type (selects, so a runtime i
+// costs no double-precision arithmetic)
+template <class C>
+__device__ __forceinline__ C ref_weight(int i) {
+  using L = Lat<9>;
+  const C a = L::cx(i) == 0 ? (C)(2.0 / 3.0) : (C)(1.0 / 6.0);
+  const C b = L::cy(i) == 0 ? (C)(2.0 / 3.0) : (C)(1.0 / 6.0);
+  return a * b;
+}
+
 // Grad's approximation of direction i (D2Q9) for rho = 1 + drho, u and Pi -
 // rho c_s^2 I, less the weight W_i (the stored deviation).
 template <class C>
@@ -60,7 +70,7 @@ __device__ __forceinline__ C ref_grad_dev(int i, C drho, C rho, const C (&u)[2],
   for (int a = 0; a < 2; ++a) cu += (C)c[a] * u[a];
   for (int a = 0; a < 2; ++a)
     for (int b = 0; b < 2; ++b) contr += Pn[a][b] * ((C)(c[a] * c[b]) - (a == b ? cs2 : (C)0));
-  return (C)weight<L>(i) * (drho + rho * cu / cs2 + contr / ((C)2 * cs2 * cs2));
+  return ref_weight<C>(i) * (drho + rho * cu / cs2 + contr / ((C)2 * cs2 * cs2));
 }
 template <class C>
 __device__ __forceinline__ void ref_pn(C rho, const C (&u)[2], const C (&G)[2][2], C beta,
@@ -151,8 +161,8 @@ __device__ __forceinline__ void ref_fill_dir(const Grid &gf, typename Store<S>::
       G[c][d] = (C)0.5 * (((C)1 - w) * v[3 + 2 * c + d] + w * v[10 + 2 * c + d]);
   ref_pn(rho, u, G, beta_f, Pn);
   const long long s = sidx(gf, ps + gf.px, qs + gf.py, 0);
-  St::store(ff + (long long)i * gf.N + s, ref_grad_dev(i, drho, rho, u, Pn),
-            (C)(1.0 / weight<L>(i)));
+  // FP32 and FP64 storage keep f - W unscaled: the scale argument is unused
+  St::store(ff + (long long)i * gf.N + s, ref_grad_dev(i, drho, rho, u, Pn), (C)1);
 }
 
 // ---------------------------------------------------------------- sampling
@@ -365,6 +375,7 @@ static size_t ref_ring_bytes(int storage, int nfx, int nfy) {
 
 template <int S>
 static cudaError_t ref_step_t(const RefLaunch &R, cudaStream_t s) {
+  static_assert(S == STORE_F32 || S == STORE_F64, "unscaled deviations (the fill's stores)");
   using T = typename Store<S>::T;
   using C = typename Store<S>::C;
   const Grid &gc = R.gc, &gf = R.gf;
