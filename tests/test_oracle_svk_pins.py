@@ -1,0 +1,165 @@
+"""Pins of the oracle's structural model (oracle/svk_oracle.py: the
+total-Lagrangian St Venant-Kirchhoff continuum with Q2 elements of section
+"Structural modeling", the two-field theta scheme and Newton with the
+analytic Gateaux tangent), against what mechanics fixes independently of its
+formulas:
+  - patch test: an affine deformation u = (F0 - I) X on a distorted mesh gives
+    no interior nodal force and the closed-form strain energy psi(E0) V;
+  - frame invariance: a finite rigid rotation is stress free;
+  - the internal force is the gradient of a separately written strain energy,
+    and the tangent the derivative of the force (central differences);
+  - a plane-strain cantilever under a small end shear matches Timoshenko beam
+    theory;
+  - CSM3 (the paper's structural benchmark) reproduces the paper's printed
+    tip displacements and frequency (tests/golden/csm3_tip.txt)."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import svk_oracle as so
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+
+
+def _mesh(dim, distort=True):
+    if dim == 2:
+        n, L = [3, 2], [3.0, 1.0]
+    else:
+        n, L = [2, 2, 2], [2.0, 1.0, 1.5]
+
+    def dist(Y):
+        # moves interior corner nodes only (the factor vanishes on the box faces)
+        s = np.prod([np.sin(np.pi * Y[:, d] / L[d]) for d in range(dim)], axis=0)
+        return Y + 0.18 * s[:, None] * np.array([1.0, -0.7, 0.5][:dim]) * min(L)
+
+    return so.box_mesh(n, L, distort=dist if distort else None), L
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_patch_test_affine_deformation(dim):
+    (X, conn), L = _mesh(dim)
+    s = so.SVK(X, conn, 1000.0, 0.3, 1.0, np.zeros(X.size, bool))
+    assert np.abs(s.X - X).max() == 0 and np.ptp(s.detJ) > 0.05 * s.detJ.mean()  # distorted
+    F0 = np.eye(dim) + np.array([[0.1, 0.2, -0.05], [-0.15, -0.05, 0.1], [0.07, 0.12, 0.2]])[:dim, :dim]
+    u = (X @ F0.T - X).ravel()
+    R = s.internal_force(u).reshape(-1, dim)
+    onb = np.any([(np.abs(X[:, d]) < 1e-12) | (np.abs(X[:, d] - L[d]) < 1e-12) for d in range(dim)],
+                 axis=0)
+    assert np.abs(R[~onb]).max() <= 1e-11 * np.abs(R).max(), np.abs(R[~onb]).max()
+    E0 = 0.5 * (F0.T @ F0 - np.eye(dim))
+    psi = 0.5 * s.lmb * np.trace(E0) ** 2 + s.mu * np.sum(E0 * E0)
+    assert abs(s.energy(u) - psi * np.prod(L)) <= 1e-12 * psi * np.prod(L)
+    # the boundary forces are the nominal traction P0 n integrated: sum over a face
+    P0 = F0 @ (s.lmb * np.trace(E0) * np.eye(dim) + 2 * s.mu * E0)
+    right = np.abs(X[:, 0] - L[0]) < 1e-12
+    area = np.prod(L) / L[0]
+    assert np.allclose(R[right].sum(0), P0[:, 0] * area, rtol=1e-12, atol=1e-9)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_finite_rigid_rotation_is_stress_free(dim):
+    (X, conn), _ = _mesh(dim)
+    s = so.SVK(X, conn, 1000.0, 0.3, 1.0, np.zeros(X.size, bool))
+    if dim == 2:
+        t = 1.0
+        Q = np.array([[np.cos(t), -np.sin(t)], [np.sin(t), np.cos(t)]])
+    else:
+        k = np.array([1.0, 2.0, -0.5]) / np.linalg.norm([1.0, 2.0, -0.5])
+        K = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+        Q = np.eye(3) + np.sin(1.2) * K + (1 - np.cos(1.2)) * K @ K
+    u = (X @ Q.T - X + 0.3).ravel()
+    assert np.abs(s.internal_force(u)).max() <= 1e-12 * 1000.0
+    assert abs(s.energy(u)) <= 1e-20
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_force_is_energy_gradient_and_tangent_its_derivative(dim):
+    (X, conn), _ = _mesh(dim)
+    s = so.SVK(X, conn, 1000.0, 0.3, 1.0, np.zeros(X.size, bool))
+    rng = np.random.default_rng(dim)
+    u = 0.08 * rng.standard_normal(X.size)
+    du = rng.standard_normal(X.size)
+    eps = 1e-6
+    dW = (s.energy(u + eps * du) - s.energy(u - eps * du)) / (2 * eps)
+    assert abs(dW - s.internal_force(u) @ du) <= 1e-7 * abs(dW)
+    dR = (s.internal_force(u + eps * du) - s.internal_force(u - eps * du)) / (2 * eps)
+    Kdu = s.tangent_apply(u, du)
+    assert np.abs(dR - Kdu).max() <= 1e-7 * np.abs(Kdu).max()
+    # the expanded element blocks, assembled, equal the printed form
+    assert np.abs(s.tangent_matrix(u) @ du - Kdu).max() <= 1e-12 * np.abs(Kdu).max()
+    # the tangent is symmetric (the SVK law derives from an energy)
+    K = s.tangent_matrix(u).toarray()
+    assert np.abs(K - K.T).max() <= 1e-11 * np.abs(K).max()
+    # consistent mass: total rho V on every component
+    assert abs(s.M.sum() / dim - np.sum(s.wdet)) <= 1e-12 * np.sum(s.wdet)
+
+
+def test_cantilever_end_shear_matches_timoshenko():
+    """Plane strain, L / h = 10 (40 x 4 elements), clamped root, a small
+    uniform shear traction on the end face: mid-height tip deflection against
+    P L^3 / (3 E' I) + P L / (kappa G A) with E' = E / (1 - nu^2), kappa = 5/6
+    (the clamped root adds a little stiffness beam theory does not see)."""
+    E, nu, L, h, P = 1e5, 0.3, 10.0, 1.0, 1e-3
+    X, conn = so.box_mesh([40, 4], [L, h], origin=[0.0, -h / 2])
+    fixed = np.repeat(X[:, 0] < 1e-12, 2)
+    s = so.SVK(X, conn, E, nu, 1.0, fixed)
+    F = np.zeros(X.size)
+    end = np.nonzero(np.abs(X[:, 0] - L) < 1e-12)[0]
+    end = end[np.argsort(X[end, 1])]
+    he = h / 4
+    for k in range(4):  # Q2 edge: nodal weights 1/6, 4/6, 1/6 of the element edge
+        for j, wq in zip(end[2 * k:2 * k + 3], (1 / 6, 4 / 6, 1 / 6)):
+            F[2 * j + 1] += -P / h * he * wq
+    u, it = s.static(F)
+    assert it >= 0
+    mid = end[4]
+    Ep, I, G = E / (1 - nu ** 2), h ** 3 / 12, E / (2 * (1 + nu))
+    ref = P * L ** 3 / (3 * Ep * I) + P * L / (5 / 6 * G * h)
+    got = -u[2 * mid + 1]
+    print(f"cantilever tip {got:.6e}, Timoshenko {ref:.6e}, ratio {got / ref:.4f}")
+    assert abs(got / ref - 1) <= 0.02
+
+
+def _golden(name):
+    vals = {}
+    for line in open(os.path.join(ROOT, "golden", name)):
+        if line.strip() and not line.startswith("#"):
+            k, present, _ = line.split()
+            vals[k] = float(present)
+    return vals
+
+
+def test_csm3_against_the_papers_table():
+    """CSM3: the flag (0.35 x 0.02, clamped root) as 20 x 2 plane-strain Q2
+    elements under gravity from rest, theta = 1/2, dt = 10 ms for 2.5 s,
+    Newton with lambda = 0.7.  Tip mean and amplitude within 3 % and
+    frequency within 1 % of the paper's printed values (its mesh has 280
+    elements and dt = 1 ms, so the bounds state the discretisation gap)."""
+    gold = _golden("csm3_tip.txt")
+    E, nu, rho, g, L, h, dt = 1.4e6, 0.4, 1e3, 2.0, 0.35, 0.02, 0.01
+    X, conn = so.box_mesh([20, 2], [L, h], origin=[0.0, -h / 2])
+    fixed = np.repeat(X[:, 0] < 1e-12, 2)
+    s = so.SVK(X, conn, E, nu, rho, fixed, rtol=1e-8, atol=1e-14)
+    F = s.body_load([0.0, -g])
+    tip = int(np.argmin(np.abs(X[:, 0] - L) + np.abs(X[:, 1])))
+    u, v, tr = np.zeros(X.size), np.zeros(X.size), []
+    for _ in range(int(2.5 / dt)):
+        u, v, it = s.step(u, v, F, F, dt)
+        assert it >= 0
+        tr.append(u.reshape(-1, 2)[tip].copy())
+    tr = np.array(tr)
+    for c, name in ((0, "ux"), (1, "uy")):
+        mean = 0.5 * (tr[:, c].max() + tr[:, c].min())
+        amp = 0.5 * (tr[:, c].max() - tr[:, c].min())
+        print(f"{name}: mean {mean:.5f} (paper {gold[name + '_mean']}), amp {amp:.5f} "
+              f"(paper {gold[name + '_amp']})")
+        assert abs(mean - gold[name + "_mean"]) <= 0.03 * abs(gold[name + "_mean"])
+        assert abs(amp - gold[name + "_amp"]) <= 0.03 * gold[name + "_amp"]
+    y = tr[:, 1] - 0.5 * (tr[:, 1].max() + tr[:, 1].min())
+    t = dt * np.arange(1, len(y) + 1)
+    k = np.nonzero(y[:-1] * y[1:] < 0)[0]
+    tc = t[k] + dt * (-y[k]) / (y[k + 1] - y[k])
+    f = 1.0 / (2.0 * np.mean(np.diff(tc)))
+    print(f"f {f:.4f} (paper {gold['f_y']})")
+    assert abs(f - gold["f_y"]) <= 0.01 * gold["f_y"]
