@@ -306,6 +306,65 @@ lbm_status fem_shell_set_state(fem_shell_ctx *s, const double *u, const double *
 const char *fem_shell_last_error(const fem_shell_ctx *s);
 void fem_shell_destroy(fem_shell_ctx *s);
 
+/* ---------------------------------------------------------------------------
+ * The paper's structural model (section "Structural modeling"), FP64 on the
+ * GPU: total-Lagrangian St Venant-Kirchhoff continuum, S = lambda tr(E) I +
+ * 2 mu E, E = (F^T F - I) / 2, P = F S, lambda and mu from E and nu by the
+ * printed Lame relations; Q2 Lagrange elements (dim 2: 9-node
+ * quadrilaterals in plane strain; dim 3: 27-node hexahedra), the geometry
+ * mapped from each element's corner nodes by the bilinear (trilinear) map,
+ * 3 Gauss points per axis; consistent mass (rho psi, psi).
+ * Time step: the two-field theta scheme of Eq. (timeInt) for v and u.  The
+ * displacement equation is linear, so v1 is eliminated and Newton runs on
+ * u1 with the residual G(u) = M (u - u0 - dt v0) / (theta dt^2) + theta R(u)
+ * - theta F1 - (1 - theta) (F0 - R(u0)) and the tangent M / (theta dt^2) +
+ * theta A'(u) (the analytic Gateaux derivative printed after Eq.
+ * (matrixForm2)); steps relaxed by lambda, stop at |G| <= rtol |G_0| +
+ * atol (G_0 at the predictor u0 + dt v0).  Linear systems: Jacobi-
+ * preconditioned conjugate gradients on element products to cg_rtol |G|
+ * (0: 1e-3, an inexact Newton step; the residual and its stopping test stay
+ * FP64, so the converged state is that of exact solves) within max_cg
+ * iterations (0: the DOF count).  One cooperative launch per step.
+ * Element-local node a = i + 3 j (+ 9 k), i, j, k = 0, 1, 2 along the
+ * element's reference axes; nodes are dim-vectors, DOF index node * dim + d.
+ * ------------------------------------------------------------------------- */
+typedef struct fem_svk_ctx fem_svk_ctx;
+typedef struct {
+  int dim;                /* 2 or 3 */
+  int nn, ne;             /* nodes, elements */
+  const double *X;        /* [nn][dim] reference positions (host or device; copied) */
+  const int32_t *conn;    /* [ne][3^dim] element nodes (copied); corner-map Jacobians must be > 0 */
+  const int32_t *fixed;   /* [nn * dim] 1: DOF held at zero (copied) */
+  double E, nu, rho;      /* Young's modulus, Poisson ratio (0 <= nu < 0.5), density */
+  double theta, lambda, rtol, atol;
+  int max_it;
+  double dt;
+  int max_cg;
+  double cg_rtol;
+  void *stream;           /* cudaStream_t; NULL: library-owned */
+} fem_svk_config;
+lbm_status fem_svk_workspace_size(const fem_svk_config *c, size_t *bytes);
+/* workspace: device memory (256-byte aligned, caller-owned) or NULL
+ * (cudaMalloc).  LBM_EINVAL for a bad config, a node index out of range or
+ * an inverted element; LBM_ECUDA when cooperative launch is unavailable.
+ * State starts at rest with zero loads. */
+lbm_status fem_svk_create(const fem_svk_config *c, void *workspace, size_t bytes,
+                          fem_svk_ctx **out);
+/* One step with nodal loads F1[nn * dim] at the new time; the previous
+ * step's loads serve as F0.  Asynchronous. */
+lbm_status fem_svk_step(fem_svk_ctx *s, const double *F1);
+/* Consistent nodal loads of a uniform body force per unit mass b[dim]:
+ * F[nn * dim] = (rho b, psi_a) (overwritten; host or device).  Synchronises. */
+lbm_status fem_svk_body_load(fem_svk_ctx *s, const double *b, double *F);
+/* u, v [nn * dim] (either may be NULL) and iters[2]: the last step's Newton
+ * iterations (negative: not converged within max_it) and its total CG
+ * iterations.  Synchronises. */
+lbm_status fem_svk_get_state(fem_svk_ctx *s, double *u, double *v, int *iters);
+/* Replace u, v and the loads F0 of the next step (any may be NULL). */
+lbm_status fem_svk_set_state(fem_svk_ctx *s, const double *u, const double *v, const double *F0);
+const char *fem_svk_last_error(const fem_svk_ctx *s);
+void fem_svk_destroy(fem_svk_ctx *s);
+
 /* Couple a plate (fem_shell) to a D3Q27 lattice: the shell's surface
  * occupies vertices [first_vertex, first_vertex + 2 nn) of the geometry --
  * vertex first_vertex + n lies h/2 above node n along the rotated reference

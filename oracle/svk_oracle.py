@@ -78,50 +78,6 @@ def reference_tables(dim):
     return w, N, dN, L, dL, np.array(corner_local)
 
 
-def box_mesh(n, lengths, origin=None, distort=None):
-    """Q2 mesh of a box: n[d] elements along axis d; nodes on the (2 n + 1)
-    lattice, node index x fastest.  distort(X) may move the corner nodes (the
-    other nodes follow the bilinear map of their element)."""
-    dim = len(n)
-    origin = np.zeros(dim) if origin is None else np.asarray(origin, float)
-    m = [2 * k + 1 for k in n]
-    grids = np.meshgrid(*[origin[d] + np.linspace(0, lengths[d], m[d]) for d in range(dim)],
-                        indexing="ij")
-    X = np.stack([g.transpose(tuple(range(dim))[::-1]).ravel() for g in grids], 1)
-
-    def nid(idx):
-        k, s = 0, 1
-        for d in range(dim):
-            k += idx[d] * s
-            s *= m[d]
-        return k
-
-    conn = []
-    for e in itertools.product(*[range(k) for k in n[::-1]]):
-        e = e[::-1]
-        loc = [c[::-1] for c in itertools.product(range(3), repeat=dim)]
-        conn.append([nid([2 * e[d] + l[d] for d in range(dim)]) for l in loc])
-    conn = np.array(conn, np.int64)
-    if distort is not None:
-        # move the element-corner lattice nodes, then place every node by the
-        # bilinear map of its element
-        is_corner = np.all(np.stack([(np.array(np.unravel_index(np.arange(len(X)), m[::-1]))[::-1][d]
-                                      % 2 == 0) for d in range(dim)]), axis=0)
-        Xc = X.copy()
-        Xc[is_corner] = distort(X[is_corner])
-        _, _, _, _, _, cl = reference_tables(dim)
-        nodes_ref = [c[::-1] for c in itertools.product(range(3), repeat=dim)]
-        for el in conn:
-            corners = Xc[el[cl]]
-            for a, nd in enumerate(nodes_ref):
-                xi = [(-1.0, 0.0, 1.0)[nd[d]] for d in range(dim)]
-                l1 = [_q1_1d(x)[0] for x in xi]
-                cor = [c[::-1] for c in itertools.product(range(2), repeat=dim)]
-                Lw = np.array([np.prod([l1[d][cc[d]] for d in range(dim)]) for cc in cor])
-                X[el[a]] = Lw @ corners
-    return X, conn
-
-
 class SVK:
     """The continuum of nn nodes X[nn, dim] and ne Q2 elements conn[ne, 3^dim];
     E, nu: Young's modulus and Poisson ratio (the Lame relations of the

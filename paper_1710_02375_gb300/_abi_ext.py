@@ -37,6 +37,21 @@ class fem_shell_config(ctypes.Structure):
     ]
 
 
+class fem_svk_config(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("nn", ctypes.c_int), ("ne", ctypes.c_int),
+        ("X", ctypes.c_void_p), ("conn", ctypes.c_void_p), ("fixed", ctypes.c_void_p),
+        ("E", ctypes.c_double), ("nu", ctypes.c_double), ("rho", ctypes.c_double),
+        ("theta", ctypes.c_double), ("lambda_", ctypes.c_double),
+        ("rtol", ctypes.c_double), ("atol", ctypes.c_double),
+        ("max_it", ctypes.c_int),
+        ("dt", ctypes.c_double),
+        ("max_cg", ctypes.c_int),
+        ("cg_rtol", ctypes.c_double),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
 class mlp_config(ctypes.Structure):
     _fields_ = [
         ("n_layers", ctypes.c_int),
@@ -90,6 +105,19 @@ def declare(L):
     L.fem_shell_destroy.restype = None
     for name in ("fem_shell_workspace_size", "fem_shell_create", "fem_shell_step",
                  "fem_shell_get_state", "fem_shell_set_state"):
+        getattr(L, name).restype = ctypes.c_int
+    L.fem_svk_workspace_size.argtypes = [ctypes.POINTER(fem_svk_config), ctypes.POINTER(sz)]
+    L.fem_svk_create.argtypes = [ctypes.POINTER(fem_svk_config), vp, sz, ctypes.POINTER(vp)]
+    L.fem_svk_step.argtypes = [vp, vp]
+    L.fem_svk_body_load.argtypes = [vp, vp, vp]
+    L.fem_svk_get_state.argtypes = [vp, vp, vp, vp]
+    L.fem_svk_set_state.argtypes = [vp, vp, vp, vp]
+    L.fem_svk_last_error.argtypes = [vp]
+    L.fem_svk_last_error.restype = ctypes.c_char_p
+    L.fem_svk_destroy.argtypes = [vp]
+    L.fem_svk_destroy.restype = None
+    for name in ("fem_svk_workspace_size", "fem_svk_create", "fem_svk_step", "fem_svk_body_load",
+                 "fem_svk_get_state", "fem_svk_set_state"):
         getattr(L, name).restype = ctypes.c_int
     L.lbm_batch_workspace_size.argtypes = [vp, i32, ctypes.POINTER(sz)]
     L.lbm_batch_create.argtypes = [vp, i32, vp, sz, ctypes.POINTER(vp)]

@@ -617,6 +617,77 @@ class Shell:
             pass
 
 
+class SvkSolid:
+    """GPU St Venant-Kirchhoff continuum with Q2 elements (fem_svk_*): nodes
+    X[nn, dim], elements conn[ne, 3^dim] (local node i + 3 j (+ 9 k)),
+    Dirichlet mask fixed[nn * dim]; torch allocates the workspace."""
+
+    def __init__(self, X, conn, E, nu, rho, fixed, theta=0.5, lam=0.7, rtol=1e-10, atol=1e-13,
+                 max_it=500, dt=1.0, max_cg=0, cg_rtol=0.0, stream=None, device="cuda"):
+        import torch
+        from ._abi_ext import fem_svk_config
+        L = load()
+        self._X = np.ascontiguousarray(X, dtype=np.float64)
+        self.nn, self.dim = self._X.shape
+        self._conn = np.ascontiguousarray(conn, dtype=np.int32)
+        self._fixed = np.ascontiguousarray(fixed, dtype=np.int32).reshape(-1)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=torch.device(device))
+        c = fem_svk_config()
+        c.dim, c.nn, c.ne = self.dim, self.nn, self._conn.shape[0]
+        c.X, c.conn, c.fixed = self._X.ctypes.data, self._conn.ctypes.data, self._fixed.ctypes.data
+        c.E, c.nu, c.rho = E, nu, rho
+        c.theta, c.lambda_, c.rtol, c.atol, c.max_it, c.dt = theta, lam, rtol, atol, max_it, dt
+        c.max_cg, c.cg_rtol = max_cg, cg_rtol
+        c.stream = self.stream.cuda_stream
+        n = ctypes.c_size_t()
+        if L.fem_svk_workspace_size(ctypes.byref(c), ctypes.byref(n)) != LBM_OK:
+            raise LbmError(LBM_EINVAL, "fem_svk_workspace_size")
+        self.workspace = torch.empty(n.value, dtype=torch.uint8, device=torch.device(device))
+        out = ctypes.c_void_p()
+        st = L.fem_svk_create(ctypes.byref(c), self.workspace.data_ptr(), n.value, ctypes.byref(out))
+        if st != LBM_OK:
+            raise LbmError(st, L.fem_svk_last_error(None).decode())
+        self.ctx = out.value
+
+    def _chk(self, st):
+        if st != LBM_OK:
+            raise LbmError(st, load().fem_svk_last_error(self.ctx).decode(errors="replace"))
+
+    def step(self, F1):
+        F1 = np.ascontiguousarray(F1, dtype=np.float64).reshape(-1)
+        self._chk(load().fem_svk_step(self.ctx, _ptr(F1)))
+        self._F1 = F1  # the copy is asynchronous
+
+    def body_load(self, b):
+        F = np.zeros(self.nn * self.dim)
+        self._chk(load().fem_svk_body_load(self.ctx, _ptr(np.ascontiguousarray(b, dtype=np.float64)),
+                                           _ptr(F)))
+        return F
+
+    def set_state(self, u=None, v=None, F0=None):
+        arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+                for a in (u, v, F0)]
+        self._chk(load().fem_svk_set_state(self.ctx, *[_ptr(a) for a in arrs]))
+
+    def state(self):
+        u = np.zeros(self.nn * self.dim)
+        v = np.zeros(self.nn * self.dim)
+        it = np.zeros(2, dtype=np.int32)
+        self._chk(load().fem_svk_get_state(self.ctx, _ptr(u), _ptr(v), _ptr(it)))
+        return u, v, (int(it[0]), int(it[1]))
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            load().fem_svk_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Batch:
     """Many Lattice objects advanced with one launch per phase (lbm_batch_*).
 

@@ -405,3 +405,36 @@ def droplet_density(shape, radius, center=None, rho_l=RHO_L, rho_v=RHO_V, width=
     if noise:
         rho = rho * (1 + noise * np.random.default_rng(seed).uniform(-1, 1, size=rho.shape))
     return rho
+
+
+def q2_box_mesh(n, lengths, origin=None, distort=None):
+    """Mesh of a box for Q2 elements (9-node quadrilaterals for len(n) = 2,
+    27-node hexahedra for 3): n[d] elements along axis d, nodes on the (2 n +
+    1) lattice with x fastest; element-local node i + 3 j (+ 9 k).  Returns
+    (X[nn, dim], conn[ne, 3^dim]).  distort(Y) may move the element-corner
+    nodes; every other node is then placed by the multilinear map of its
+    element's corners (so the elements stay straight-sided)."""
+    import itertools
+    dim = len(n)
+    origin = np.zeros(dim) if origin is None else np.asarray(origin, float)
+    m = [2 * k + 1 for k in n]
+    axes = [origin[d] + np.linspace(0.0, lengths[d], m[d]) for d in range(dim)]
+    idx = np.stack(np.unravel_index(np.arange(int(np.prod(m))), m[::-1])[::-1], 1)  # x fastest
+    X = np.stack([axes[d][idx[:, d]] for d in range(dim)], 1)
+    stride = np.cumprod([1] + m[:-1])
+    local = np.array([l[::-1] for l in itertools.product(range(3), repeat=dim)])
+    elems = np.array([e[::-1] for e in itertools.product(*[range(k) for k in n[::-1]])])
+    conn = ((2 * elems[:, None, :] + local[None, :, :]) * stride).sum(2).astype(np.int64)
+    if distort is not None:
+        corner = np.all(idx % 2 == 0, axis=1)
+        Xc = X.copy()
+        Xc[corner] = distort(X[corner])
+        cl = np.array([sum(2 * c[d] * 3 ** d for d in range(dim))
+                       for c in (cc[::-1] for cc in itertools.product(range(2), repeat=dim))])
+        cbits = np.array([cc[::-1] for cc in itertools.product(range(2), repeat=dim)])
+        xi = local - 1.0                                   # node positions in [-1, 1]
+        wts = np.prod(np.where(cbits[None, :, :] == 1, 0.5 * (1 + xi[:, None, :]),
+                               0.5 * (1 - xi[:, None, :])), axis=2)   # [nen, ncorner]
+        for el in conn:
+            X[el] = wts @ Xc[el[cl]]
+    return X, conn

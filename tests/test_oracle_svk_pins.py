@@ -18,6 +18,7 @@ import numpy as np
 import pytest
 
 from oracle import svk_oracle as so
+from paper_1710_02375_gb300 import synth
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 
@@ -33,7 +34,7 @@ def _mesh(dim, distort=True):
         s = np.prod([np.sin(np.pi * Y[:, d] / L[d]) for d in range(dim)], axis=0)
         return Y + 0.18 * s[:, None] * np.array([1.0, -0.7, 0.5][:dim]) * min(L)
 
-    return so.box_mesh(n, L, distort=dist if distort else None), L
+    return synth.q2_box_mesh(n, L, distort=dist if distort else None), L
 
 
 @pytest.mark.parametrize("dim", [2, 3])
@@ -101,7 +102,7 @@ def test_cantilever_end_shear_matches_timoshenko():
     P L^3 / (3 E' I) + P L / (kappa G A) with E' = E / (1 - nu^2), kappa = 5/6
     (the clamped root adds a little stiffness beam theory does not see)."""
     E, nu, L, h, P = 1e5, 0.3, 10.0, 1.0, 1e-3
-    X, conn = so.box_mesh([40, 4], [L, h], origin=[0.0, -h / 2])
+    X, conn = synth.q2_box_mesh([40, 4], [L, h], origin=[0.0, -h / 2])
     fixed = np.repeat(X[:, 0] < 1e-12, 2)
     s = so.SVK(X, conn, E, nu, 1.0, fixed)
     F = np.zeros(X.size)
@@ -138,7 +139,7 @@ def test_csm3_against_the_papers_table():
     elements and dt = 1 ms, so the bounds state the discretisation gap)."""
     gold = _golden("csm3_tip.txt")
     E, nu, rho, g, L, h, dt = 1.4e6, 0.4, 1e3, 2.0, 0.35, 0.02, 0.01
-    X, conn = so.box_mesh([20, 2], [L, h], origin=[0.0, -h / 2])
+    X, conn = synth.q2_box_mesh([20, 2], [L, h], origin=[0.0, -h / 2])
     fixed = np.repeat(X[:, 0] < 1e-12, 2)
     s = so.SVK(X, conn, E, nu, rho, fixed, rtol=1e-8, atol=1e-14)
     F = s.body_load([0.0, -g])
