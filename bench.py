@@ -6,7 +6,7 @@ the 129 MB L2, so no L2 flush is needed between steps).  A step is one pass of
 the hot path over the whole lattice: pull-stream + KBC collision, one kernel.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload tgv128|c4|c4-coupled|c1-fsi|c3-fsi|multiphase|refine] [--quick]
+                  [--workload tgv128|c4|c4-coupled|c1-fsi|c3-fsi|multiphase|refine|svk] [--quick]
 
 The default line also carries "patterns": the same workload with IEEE half,
 bfloat16 and the narrow-range 16-bit float F16N storage, as speedups over
@@ -380,6 +380,7 @@ def run_ours(args):
         forms["multiphase_droplet_d3q27"] = mp_leg(args)
         forms["multiphase_droplet_on_wall_d3q27"] = mp_wall_leg(args)
         forms["refined_d2q9_two_level"] = refine_leg(args)
+        forms["svk_q2_structure"] = svk_leg(args)
         forms["surrogate"] = {
             "measured_in": "tests/test_gpu_surrogate.py, tests/test_gpu_plate_surrogate.py",
             "why_not_here": "its training pairs come from coupled FP64 oracle runs, which this "
@@ -697,6 +698,46 @@ def refine_leg(args, nxc=2048, nyc=1024, U0=0.03, nu_c=0.01):
                       f"[{j0},{j0 + nfy // 2}), Taylor-Green U0={U0}, nu_c={nu_c}, FP32"}
 
 
+def svk_leg(args):
+    """The paper's structural model (St Venant-Kirchhoff continuum, Q2
+    elements, theta = 1/2, Newton with lambda = 0.7, FP64): the CSM3 flag
+    (20 x 2 plane-strain quadrilaterals under gravity, dt = 10 ms) and the
+    plate's 140 x 20 x 2 hexahedra (172,815 DOFs, gravity, dt = 2 ms); GPU
+    time per structural step and the oracle's on the host for the flag."""
+    import torch
+    from paper_1710_02375_gb300 import synth
+    from paper_1710_02375_gb300.lbm import SvkSolid
+    out = {}
+    for name, n, L, E, nu, rho, dt, b, steps, rtol in (
+            ("csm3_flag_20x2_q2", [20, 2], [0.35, 0.02], 1.4e6, 0.4, 1e3, 0.01, [0.0, -2.0], 20, 1e-10),
+            ("plate_140x20x2_q2_hex", [140, 20, 2], [1.0, 0.5, 0.01], 1e6, 0.3, 1e3, 0.002,
+             [0.0, 0.0, -2.0], 3, 1e-8)):
+        X, conn = synth.q2_box_mesh(n, L, origin=[0.0] + [-l / 2 for l in L[1:]])
+        dim = len(n)
+        fixed = np.repeat(X[:, 0] < 1e-12, dim).astype(np.int32)
+        S = SvkSolid(X, conn, E=E, nu=nu, rho=rho, fixed=fixed, dt=dt, rtol=rtol, atol=1e-16,
+                     max_cg=20000)
+        F = S.body_load(b)
+        S.set_state(F0=F)
+        S.step(F)
+        S.state()
+        ms = _timed(S.stream, lambda k: [S.step(F) for _ in range(k)], steps)
+        _, _, (it, cgi) = S.state()
+        S.close()
+        out[name] = {"ms_per_step": ms, "dofs": int(X.size), "newton_last_step": it,
+                     "cg_last_step": cgi}
+        if name.startswith("csm3") and not args.no_cpu_baseline:
+            from oracle import svk_oracle as so
+            O = so.SVK(X, conn, E, nu, rho, fixed.astype(bool), rtol=rtol, atol=1e-16)
+            Fo = O.body_load(b)
+            u, v = np.zeros(X.size), np.zeros(X.size)
+            t0 = time.perf_counter()
+            for _ in range(5):
+                u, v, _ = O.step(u, v, Fo, Fo, dt)
+            out[name]["oracle_ms_per_step_host"] = (time.perf_counter() - t0) / 5 * 1e3
+    return out
+
+
 def run_c4(args):
     """Batched pattern: the 64-member flag ensemble (synth.c4_instances, D2Q9,
     200x40 .. 800x160 lattices, 3.78M nodes in all) stepped as one batch under
@@ -883,7 +924,7 @@ def main():
     ap.add_argument("--quick", action="store_true",
                     help="only the headline workload and its storage patterns")
     ap.add_argument("--workload", choices=["tgv128", "c4", "c4-coupled", "c1-fsi", "c3-fsi",
-                                           "multiphase", "refine"], default="tgv128")
+                                           "multiphase", "refine", "svk"], default="tgv128")
     ap.add_argument("--mp-shape", default="320,250,320",
                     help="nz,ny,nx of the multiphase droplet workload")
     args = ap.parse_args()
@@ -903,6 +944,10 @@ def main():
         shape = tuple(int(v) for v in args.mp_shape.split(","))
         print(json.dumps({"workload": "multiphase", **mp_leg(args, shape=shape),
                           "walls": mp_wall_leg(args, shape=shape)}), flush=True)
+    elif args.workload == "svk":
+        import __graft_entry__
+        __graft_entry__.build()
+        print(json.dumps({"workload": "svk", **svk_leg(args)}), flush=True)
     elif args.workload == "refine":
         import __graft_entry__
         __graft_entry__.build()
