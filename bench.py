@@ -704,7 +704,7 @@ def svk_leg(args):
     (20 x 2 plane-strain quadrilaterals under gravity, dt = 10 ms) and the
     plate's 140 x 20 x 2 hexahedra (172,815 DOFs, gravity, dt = 2 ms); GPU
     time per structural step and the oracle's on the host for the flag."""
-    import torch
+    import numpy as np
     from paper_1710_02375_gb300 import synth
     from paper_1710_02375_gb300.lbm import SvkSolid
     out = {}
