@@ -342,6 +342,8 @@ typedef struct {
   int max_cg;
   double cg_rtol;
   void *stream;           /* cudaStream_t; NULL: library-owned */
+  int solve_fp64;         /* 0: the element products inside CG in FP32 (residual, stopping
+                             test and state stay FP64); 1: in FP64 */
 } fem_svk_config;
 lbm_status fem_svk_workspace_size(const fem_svk_config *c, size_t *bytes);
 /* workspace: device memory (256-byte aligned, caller-owned) or NULL

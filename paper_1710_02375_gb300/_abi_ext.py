@@ -49,6 +49,7 @@ class fem_svk_config(ctypes.Structure):
         ("max_cg", ctypes.c_int),
         ("cg_rtol", ctypes.c_double),
         ("stream", ctypes.c_void_p),
+        ("solve_fp64", ctypes.c_int),
     ]
 
 

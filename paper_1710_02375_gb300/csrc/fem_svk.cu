@@ -31,8 +31,10 @@ namespace cg = cooperative_groups;
 
 namespace kbc {
 
+// CTA size of the cooperative grid (one warp per element).  (One CTA of 512
+// threads running the CSM3 flag alone, with block barriers, measured 254 ms
+// per step against 97 ms on the grid: latency-bound on one SM.)
 constexpr int kSvkThreads = 128;
-constexpr int kSvkWarps = kSvkThreads / 32;
 
 struct SvkParams {
   int dim, nn, ne, n;
@@ -52,6 +54,9 @@ struct SvkDev {
   double *u0, *v0, *rhs0, *f, *Mq, *diag;
   double *x, *r, *z, *p, *Ap;
   double *Fg, *Sg;       // [ne][ng][dim^2] F and S of the current iterate
+  // FP32 copies for the FP32 element products inside CG
+  const float *dNXf, *wdetf, *Ntabf;
+  float *Fgf, *Sgf;
   double *red;           // 6 reduction slots
   int *iters;            // [2] Newton iterations (negative: not converged), CG total
 };
@@ -117,11 +122,13 @@ __device__ void svk_force(const SvkParams &P, const SvkDev &V, int e, const doub
     double S[D][D];
     svk_S<D>(P, F, S);
     const double w = V.wdet[(long long)e * ng + lane];
-    double *Fo = V.Fg + ((long long)e * ng + lane) * DD, *So = V.Sg + ((long long)e * ng + lane) * DD;
+    const long long go = ((long long)e * ng + lane) * DD;
     for (int i = 0; i < D; ++i)
       for (int j = 0; j < D; ++j) {
-        Fo[i * D + j] = F[i][j];
-        So[i * D + j] = S[i][j];
+        V.Fg[go + i * D + j] = F[i][j];
+        V.Sg[go + i * D + j] = S[i][j];
+        V.Fgf[go + i * D + j] = (float)F[i][j];
+        V.Sgf[go + i * D + j] = (float)S[i][j];
         double pij = 0.0;
         for (int k = 0; k < D; ++k) pij += F[i][k] * S[k][j];
         W.gp[lane][i * D + j] = w * pij;
@@ -151,12 +158,27 @@ __device__ void svk_force(const SvkParams &P, const SvkDev &V, int e, const doub
   __syncwarp();
 }
 
+// Tables of the element products in precision T
+template <typename T>
+struct SvkTab;
+template <>
+struct SvkTab<double> {
+  const double *dN, *w, *N, *F, *S;
+  __device__ SvkTab(const SvkDev &V) : dN(V.dNX), w(V.wdet), N(V.Ntab), F(V.Fg), S(V.Sg) {}
+};
+template <>
+struct SvkTab<float> {
+  const float *dN, *w, *N, *F, *S;
+  __device__ SvkTab(const SvkDev &V) : dN(V.dNXf), w(V.wdetf), N(V.Ntabf), F(V.Fgf), S(V.Sgf) {}
+};
+
 // Element e, tangent product: y += (cM M_e + theta A'_e(u)) p with the
 // stored F, S: the printed Gateaux form (grad p S + F (mu (grad p^T F + F^T
 // grad p) + lambda tr(F^T grad p) I), grad psi).
-template <int D>
+template <int D, typename T>
 __device__ void svk_tangent(const SvkParams &P, const SvkDev &V, int e, const double *p,
                             double *y, double cM, SvkWarp<D> &W, int lane) {
+  const SvkTab<T> tb(V);
   constexpr int nen = SvkEl<D>::nen, ng = SvkEl<D>::ng, DD = SvkEl<D>::DD;
   if (lane < nen) {
     const int nd = V.conn[(long long)e * nen + lane];
@@ -165,54 +187,55 @@ __device__ void svk_tangent(const SvkParams &P, const SvkDev &V, int e, const do
   }
   __syncwarp();
   if (lane < ng) {
-    const double *dN = V.dNX + ((long long)e * ng + lane) * nen * D;
-    const double *Fi = V.Fg + ((long long)e * ng + lane) * DD, *Si = V.Sg + ((long long)e * ng + lane) * DD;
-    double dH[D][D], F[D][D], S[D][D];
+    const T *dN = tb.dN + ((long long)e * ng + lane) * nen * D;
+    const T *Fi = tb.F + ((long long)e * ng + lane) * DD, *Si = tb.S + ((long long)e * ng + lane) * DD;
+    T dH[D][D], F[D][D], S[D][D];
     for (int i = 0; i < D; ++i)
       for (int j = 0; j < D; ++j) {
-        dH[i][j] = 0.0;
+        dH[i][j] = (T)0;
         F[i][j] = Fi[i * D + j];
         S[i][j] = Si[i * D + j];
       }
     for (int a = 0; a < nen; ++a)
       for (int i = 0; i < D; ++i)
-        for (int j = 0; j < D; ++j) dH[i][j] += W.a[a][i] * dN[a * D + j];
-    double FtdH[D][D], tr = 0.0;
+        for (int j = 0; j < D; ++j) dH[i][j] += (T)W.a[a][i] * dN[a * D + j];
+    T FtdH[D][D], tr = (T)0;
     for (int i = 0; i < D; ++i)
       for (int j = 0; j < D; ++j) {
-        double s = 0.0;
+        T s = (T)0;
         for (int k = 0; k < D; ++k) s += F[k][i] * dH[k][j];
         FtdH[i][j] = s;
       }
     for (int i = 0; i < D; ++i) tr += FtdH[i][i];
-    double inner[D][D];
+    T inner[D][D];
+    const T mu = (T)P.mu, lmb = (T)P.lmb;
     for (int i = 0; i < D; ++i)
       for (int j = 0; j < D; ++j)
-        inner[i][j] = P.mu * (FtdH[j][i] + FtdH[i][j]) + (i == j ? P.lmb * tr : 0.0);
-    const double w = V.wdet[(long long)e * ng + lane];
+        inner[i][j] = mu * (FtdH[j][i] + FtdH[i][j]) + (i == j ? lmb * tr : (T)0);
+    const T w = tb.w[(long long)e * ng + lane];
     for (int i = 0; i < D; ++i)
       for (int j = 0; j < D; ++j) {
-        double q = 0.0;
+        T q = (T)0;
         for (int k = 0; k < D; ++k) q += dH[i][k] * S[k][j] + F[i][k] * inner[k][j];
-        W.gp[lane][i * D + j] = P.theta * w * q;
+        W.gp[lane][i * D + j] = (double)((T)P.theta * w * q);
       }
-    const double *N = V.Ntab + (long long)lane * nen;
+    const T *N = tb.N + (long long)lane * nen;
     for (int i = 0; i < D; ++i) {
-      double s = 0.0;
-      for (int b = 0; b < nen; ++b) s += N[b] * W.a[b][i];
-      W.gm[lane][i] = cM * P.rho * w * s;
+      T s = (T)0;
+      for (int b = 0; b < nen; ++b) s += N[b] * (T)W.a[b][i];
+      W.gm[lane][i] = (double)((T)(cM * P.rho) * w * s);
     }
   }
   __syncwarp();
   if (lane < nen) {
     for (int i = 0; i < D; ++i) {
-      double s = 0.0;
+      T s = (T)0;
       for (int g = 0; g < ng; ++g) {
-        const double *dN = V.dNX + (((long long)e * ng + g) * nen + lane) * D;
-        for (int j = 0; j < D; ++j) s += W.gp[g][i * D + j] * dN[j];
-        s += V.Ntab[(long long)g * nen + lane] * W.gm[g][i];
+        const T *dN = tb.dN + (((long long)e * ng + g) * nen + lane) * D;
+        for (int j = 0; j < D; ++j) s += (T)W.gp[g][i * D + j] * dN[j];
+        s += tb.N[(long long)g * nen + lane] * (T)W.gm[g][i];
       }
-      atomicAdd(y + (long long)W.node[lane] * D + i, s);
+      atomicAdd(y + (long long)W.node[lane] * D + i, (double)s);
     }
   }
   __syncwarp();
@@ -221,20 +244,22 @@ __device__ void svk_tangent(const SvkParams &P, const SvkDev &V, int e, const do
 // Element e, Jacobi diagonal: diag += the diagonal of cM M_e + theta A'_e(u)
 // (the Gateaux form for p = psi = e_i N_a: grad N_a . S grad N_a + mu ((F
 // grad N_a)_i^2 + (F F^T)_ii |grad N_a|^2) + lambda (F grad N_a)_i^2).
-template <int D>
+template <int D, typename T>
 __device__ void svk_diag(const SvkParams &P, const SvkDev &V, int e, double cM, int lane) {
   constexpr int nen = SvkEl<D>::nen, ng = SvkEl<D>::ng, DD = SvkEl<D>::DD;
   if (lane >= nen) return;
+  const SvkTab<T> tb(V);
+  const T th = (T)P.theta, mu = (T)P.mu, lmb = (T)P.lmb, cMr = (T)(cM * P.rho);
   const int nd = V.conn[(long long)e * nen + lane];
-  double acc[D];
-  for (int i = 0; i < D; ++i) acc[i] = 0.0;
+  T acc[D];
+  for (int i = 0; i < D; ++i) acc[i] = (T)0;
   for (int g = 0; g < ng; ++g) {
-    const double *dN = V.dNX + (((long long)e * ng + g) * nen + lane) * D;
-    const double *F = V.Fg + ((long long)e * ng + g) * DD, *S = V.Sg + ((long long)e * ng + g) * DD;
-    const double w = V.wdet[(long long)e * ng + g], Na = V.Ntab[(long long)g * nen + lane];
-    double gv[D], nSn = 0.0, nn = 0.0;
+    const T *dN = tb.dN + (((long long)e * ng + g) * nen + lane) * D;
+    const T *F = tb.F + ((long long)e * ng + g) * DD, *S = tb.S + ((long long)e * ng + g) * DD;
+    const T w = tb.w[(long long)e * ng + g], Na = tb.N[(long long)g * nen + lane];
+    T gv[D], nSn = (T)0, nn = (T)0;
     for (int i = 0; i < D; ++i) {
-      double s = 0.0, t = 0.0;
+      T s = (T)0, t = (T)0;
       for (int j = 0; j < D; ++j) {
         s += F[i * D + j] * dN[j];
         t += S[i * D + j] * dN[j];
@@ -244,21 +269,23 @@ __device__ void svk_diag(const SvkParams &P, const SvkDev &V, int e, double cM, 
       nn += dN[i] * dN[i];
     }
     for (int i = 0; i < D; ++i) {
-      double ffii = 0.0;
+      T ffii = (T)0;
       for (int k = 0; k < D; ++k) ffii += F[i * D + k] * F[i * D + k];
-      acc[i] += w * (P.theta * (nSn + P.mu * (gv[i] * gv[i] + ffii * nn) + P.lmb * gv[i] * gv[i]) +
-                     cM * P.rho * Na * Na);
+      acc[i] += w * (th * (nSn + mu * (gv[i] * gv[i] + ffii * nn) + lmb * gv[i] * gv[i]) +
+                     cMr * Na * Na);
     }
   }
-  for (int i = 0; i < D; ++i) atomicAdd(V.diag + (long long)nd * D + i, acc[i]);
+  for (int i = 0; i < D; ++i) atomicAdd(V.diag + (long long)nd * D + i, (double)acc[i]);
 }
 
 __device__ __forceinline__ void svk_sync() { cg::this_grid().sync(); }
 
 // Sums of two values over the grid: block reduction, one atomic per block
 // into slot s, barrier, read; the slot two ahead is cleared for later use.
+template <int THREADS>
 __device__ __forceinline__ void svk_sum2(double *red, int &slot, double a, double b, double &ra,
                                          double &rb) {
+  constexpr int kSvkWarps = THREADS / 32;
   __shared__ double part[2][kSvkWarps];
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_xor_sync(0xffffffffu, a, o);
@@ -295,8 +322,9 @@ __device__ __forceinline__ void svk_sum2(double *red, int &slot, double a, doubl
 // (1), the residual norm (1), the Jacobi diagonal (1), per CG iteration the
 // tangent products (1), two reductions and the new search direction (3),
 // the relaxed update (1).
-template <int D>
-__global__ void __launch_bounds__(kSvkThreads) k_svk_step(SvkParams P, SvkDev V) {
+template <int D, typename T, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_svk_step(SvkParams P, SvkDev V) {
+  constexpr int kSvkWarps = THREADS / 32;
   __shared__ SvkWarp<D> Wsh[kSvkWarps];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   SvkWarp<D> &W = Wsh[wl];
@@ -337,7 +365,7 @@ __global__ void __launch_bounds__(kSvkThreads) k_svk_step(SvkParams P, SvkDev V)
       V.x[i] = 0.0;
       gg += G * G;
     }
-    svk_sum2(V.red, slot, gg, 0.0, ra, rb);
+    svk_sum2<THREADS>(V.red, slot, gg, 0.0, ra, rb);
     const double gn = sqrt(ra);
     if (g0 < 0.0) g0 = gn;
     if (gn <= P.rtol * g0 + P.atol) {
@@ -345,7 +373,7 @@ __global__ void __launch_bounds__(kSvkThreads) k_svk_step(SvkParams P, SvkDev V)
       break;
     }
     if (it >= P.max_it) break;
-    for (int e = wg; e < P.ne; e += nwg) svk_diag<D>(P, V, e, cM, lane);
+    for (int e = wg; e < P.ne; e += nwg) svk_diag<D, T>(P, V, e, cM, lane);
     svk_sync();
     double rz = 0.0;
     for (long long i = gt; i < n; i += gs) {
@@ -355,16 +383,16 @@ __global__ void __launch_bounds__(kSvkThreads) k_svk_step(SvkParams P, SvkDev V)
       V.Ap[i] = 0.0;
       rz += V.r[i] * z;
     }
-    svk_sum2(V.red, slot, rz, 0.0, ra, rb);
+    svk_sum2<THREADS>(V.red, slot, rz, 0.0, ra, rb);
     rz = ra;
     int k = 0;
     while (k < P.max_cg) {
-      for (int e = wg; e < P.ne; e += nwg) svk_tangent<D>(P, V, e, V.p, V.Ap, cM, W, lane);
+      for (int e = wg; e < P.ne; e += nwg) svk_tangent<D, T>(P, V, e, V.p, V.Ap, cM, W, lane);
       svk_sync();
       double pAp = 0.0;
       for (long long i = gt; i < n; i += gs)
         if (!V.fixed[i]) pAp += V.p[i] * V.Ap[i];
-      svk_sum2(V.red, slot, pAp, 0.0, ra, rb);
+      svk_sum2<THREADS>(V.red, slot, pAp, 0.0, ra, rb);
       ++k;
       if (!(ra > 0.0)) break;
       const double alpha = rz / ra;
@@ -379,7 +407,7 @@ __global__ void __launch_bounds__(kSvkThreads) k_svk_step(SvkParams P, SvkDev V)
         rzn += r * z;
         rr += r * r;
       }
-      svk_sum2(V.red, slot, rzn, rr, ra, rb);
+      svk_sum2<THREADS>(V.red, slot, rzn, rr, ra, rb);
       if (sqrt(rb) <= P.cg_rtol * gn) break;
       const double beta = ra / rz;
       rz = ra;
@@ -434,6 +462,8 @@ struct fem_svk_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int grid = 0;
+  const void *fn = nullptr;  // the step kernel (dimension, precision of the CG products, CTA size)
+  int threads = 0;
   bool poisoned = false;
   char msg[256] = {0};
 };
@@ -461,6 +491,9 @@ size_t svk_layout(int dim, int nn, int ne, fem_svk_ctx *s) {
   for (int k = 0; k < 16; ++k) ovec[k] = take(sizeof(double) * n);
   const size_t oFg = take(sizeof(double) * dd * ng * ne), oSg = take(sizeof(double) * dd * ng * ne);
   const size_t ored = take(sizeof(double) * 6), oit = take(sizeof(int) * 2);
+  const size_t odNf = take(sizeof(float) * ng * nen * dim * ne), owf = take(sizeof(float) * ng * ne);
+  const size_t oNf = take(sizeof(float) * ng * nen);
+  const size_t oFgf = take(sizeof(float) * dd * ng * ne), oSgf = take(sizeof(float) * dd * ng * ne);
   if (s) {
     char *w = s->ws;
     SvkDev &d = s->d;
@@ -476,6 +509,11 @@ size_t svk_layout(int dim, int nn, int ne, fem_svk_ctx *s) {
     d.Sg = (double *)(w + oSg);
     d.red = (double *)(w + ored);
     d.iters = (int *)(w + oit);
+    d.dNXf = (const float *)(w + odNf);
+    d.wdetf = (const float *)(w + owf);
+    d.Ntabf = (const float *)(w + oNf);
+    d.Fgf = (float *)(w + oFgf);
+    d.Sgf = (float *)(w + oSgf);
   }
   return off;
 }
@@ -620,8 +658,16 @@ bool svk_geometry(int dim, int ne, const std::vector<double> &X, const std::vect
 
 static cudaError_t svk_launch(fem_svk_ctx *s) {
   void *args[] = {(void *)&s->p, (void *)&s->d};
-  const void *fn = s->p.dim == 2 ? (const void *)k_svk_step<2> : (const void *)k_svk_step<3>;
-  return cudaLaunchCooperativeKernel(fn, dim3(s->grid), dim3(kSvkThreads), args, 0, s->stream);
+  return cudaLaunchCooperativeKernel(s->fn, dim3(s->grid), dim3(s->threads), args, 0, s->stream);
+}
+
+// The step kernel for a dimension and CG-product precision.
+static const void *svk_kernel(int dim, bool fp64) {
+  if (dim == 2)
+    return fp64 ? (const void *)k_svk_step<2, double, kSvkThreads>
+                : (const void *)k_svk_step<2, float, kSvkThreads>;
+  return fp64 ? (const void *)k_svk_step<3, double, kSvkThreads>
+              : (const void *)k_svk_step<3, float, kSvkThreads>;
 }
 
 extern "C" {
@@ -705,14 +751,20 @@ lbm_status fem_svk_create(const fem_svk_config *c, void *workspace, size_t bytes
   up(s->d.wdet, wdet.data(), sizeof(double) * wdet.size());
   up(s->d.dNX, dNX.data(), sizeof(double) * dNX.size());
   up(s->d.Ntab, R.N.data(), sizeof(double) * R.N.size());
+  const std::vector<float> dNf(dNX.begin(), dNX.end()), wf(wdet.begin(), wdet.end()),
+      Nf(R.N.begin(), R.N.end());
+  up(s->d.dNXf, dNf.data(), sizeof(float) * dNf.size());
+  up(s->d.wdetf, wf.data(), sizeof(float) * wf.size());
+  up(s->d.Ntabf, Nf.data(), sizeof(float) * Nf.size());
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   int dev = 0, sms = 0, per_sm = 0, coop = 0;
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  s->fn = svk_kernel(dim, c->solve_fp64 != 0);
+  s->threads = kSvkThreads;
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, dim == 2 ? (const void *)k_svk_step<2> : (const void *)k_svk_step<3>, kSvkThreads, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, s->fn, s->threads, 0);
   if (e != cudaSuccess || !coop || per_sm < 1) {
     snprintf(g_svk_msg, sizeof(g_svk_msg), "fem_svk_create: %s",
              e != cudaSuccess ? cudaGetErrorString(e) : "cooperative launch unavailable");
@@ -721,7 +773,7 @@ lbm_status fem_svk_create(const fem_svk_config *c, void *workspace, size_t bytes
     delete s;
     return LBM_ECUDA;
   }
-  s->grid = (ne + kSvkWarps - 1) / kSvkWarps;
+  s->grid = (ne + kSvkThreads / 32 - 1) / (kSvkThreads / 32);
   if (s->grid > sms * per_sm) s->grid = sms * per_sm;
   *out = s;
   return LBM_OK;

@@ -623,7 +623,8 @@ class SvkSolid:
     Dirichlet mask fixed[nn * dim]; torch allocates the workspace."""
 
     def __init__(self, X, conn, E, nu, rho, fixed, theta=0.5, lam=0.7, rtol=1e-10, atol=1e-13,
-                 max_it=500, dt=1.0, max_cg=0, cg_rtol=0.0, stream=None, device="cuda"):
+                 max_it=500, dt=1.0, max_cg=0, cg_rtol=0.0, solve_fp64=False, stream=None,
+                 device="cuda"):
         import torch
         from ._abi_ext import fem_svk_config
         L = load()
@@ -639,6 +640,7 @@ class SvkSolid:
         c.theta, c.lambda_, c.rtol, c.atol, c.max_it, c.dt = theta, lam, rtol, atol, max_it, dt
         c.max_cg, c.cg_rtol = max_cg, cg_rtol
         c.stream = self.stream.cuda_stream
+        c.solve_fp64 = int(bool(solve_fp64))
         n = ctypes.c_size_t()
         if L.fem_svk_workspace_size(ctypes.byref(c), ctypes.byref(n)) != LBM_OK:
             raise LbmError(LBM_EINVAL, "fem_svk_workspace_size")

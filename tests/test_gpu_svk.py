@@ -1,6 +1,6 @@
 """The St Venant-Kirchhoff Q2 continuum on the GPU (csrc/fem_svk.cu: one
 cooperative launch per theta step, Newton with the Gateaux tangent, Jacobi
-CG on element products) against the oracle (oracle/svk_oracle.py), through
+CG on element products in FP32 or FP64) against the oracle (oracle/svk_oracle.py), through
 the C ABI (fem_svk_*)."""
 import numpy as np
 import pytest
@@ -38,7 +38,8 @@ def test_body_load_matches_oracle(dim):
     G.close()
 
 
-def test_csm3_steps_match_oracle():
+@pytest.mark.parametrize("solve_fp64", [False, True])
+def test_csm3_steps_match_oracle(solve_fp64):
     """CSM3 (20 x 2 plane-strain Q2 elements, gravity from rest, dt = 10 ms,
     theta = 1/2, lambda = 0.7), 40 steps: displacement and velocity.  Newton
     to |G| <= 1e-10 |G_0| (the round-off floor of this thin flag is near
@@ -47,7 +48,7 @@ def test_csm3_steps_match_oracle():
     X, conn = synth.q2_box_mesh([20, 2], [L, h], origin=[0.0, -h / 2])
     fixed = np.repeat(X[:, 0] < 1e-12, 2)
     kw = dict(rtol=1e-10, atol=1e-16)
-    G = _solid(X, conn, fixed, E=E, nu=nu, rho=rho, dt=dt, **kw)
+    G = _solid(X, conn, fixed, E=E, nu=nu, rho=rho, dt=dt, solve_fp64=solve_fp64, **kw)
     O = so.SVK(X, conn, E, nu, rho, fixed, **kw)
     F = O.body_load([0.0, -g])
     Fg = G.body_load([0.0, -g])
@@ -67,14 +68,15 @@ def test_csm3_steps_match_oracle():
     G.close()
 
 
-def test_3d_hex_cantilever_large_deflection_matches_oracle():
+@pytest.mark.parametrize("solve_fp64", [False, True])
+def test_3d_hex_cantilever_large_deflection_matches_oracle(solve_fp64):
     """Distorted 27-node hexahedra (4 x 2 x 2), clamped face, a tip load large
     enough for a finite rotation of the end, theta = 0.6, 12 steps."""
     E, nu, rho, dt = 2e3, 0.3, 1.0, 0.05
     X, conn = _distorted([4, 2, 2], [4.0, 1.0, 1.0])
     fixed = np.repeat(X[:, 0] < 1e-12, 3)
     kw = dict(theta=0.6, rtol=1e-12, atol=1e-16)
-    G = _solid(X, conn, fixed, E=E, nu=nu, rho=rho, dt=dt, **kw)
+    G = _solid(X, conn, fixed, E=E, nu=nu, rho=rho, dt=dt, solve_fp64=solve_fp64, **kw)
     O = so.SVK(X, conn, E, nu, rho, fixed, **kw)
     F = O.body_load([0.0, -0.5, 0.2])
     tip = np.abs(X[:, 0] - 4.0) < 1e-12
