@@ -76,6 +76,28 @@ struct SvkWarp {
   double a[SvkEl<D>::nen][D];             // element nodal vector
   double b[SvkEl<D>::nen][D];             // second element nodal vector
   int node[SvkEl<D>::nen];
+  // FP32 scratch of the FP32 tangent products (no conversions in the loops)
+  float gpf[SvkEl<D>::ng][SvkEl<D>::DD];
+  float gmf[SvkEl<D>::ng][D];
+  float af[SvkEl<D>::nen][D];
+};
+
+// The warp scratch in precision T
+template <int D, typename T>
+struct SvkScr;
+template <int D>
+struct SvkScr<D, double> {
+  double (*gp)[SvkEl<D>::DD];
+  double (*gm)[D];
+  double (*a)[D];
+  __device__ SvkScr(SvkWarp<D> &W) : gp(W.gp), gm(W.gm), a(W.a) {}
+};
+template <int D>
+struct SvkScr<D, float> {
+  float (*gp)[SvkEl<D>::DD];
+  float (*gm)[D];
+  float (*a)[D];
+  __device__ SvkScr(SvkWarp<D> &W) : gp(W.gpf), gm(W.gmf), a(W.af) {}
 };
 
 // S of a deformation gradient (row-major D x D)
@@ -179,11 +201,12 @@ template <int D, typename T>
 __device__ void svk_tangent(const SvkParams &P, const SvkDev &V, int e, const double *p,
                             double *y, double cM, SvkWarp<D> &W, int lane) {
   const SvkTab<T> tb(V);
+  const SvkScr<D, T> sc(W);
   constexpr int nen = SvkEl<D>::nen, ng = SvkEl<D>::ng, DD = SvkEl<D>::DD;
   if (lane < nen) {
     const int nd = V.conn[(long long)e * nen + lane];
     W.node[lane] = nd;
-    for (int d = 0; d < D; ++d) W.a[lane][d] = p[(long long)nd * D + d];
+    for (int d = 0; d < D; ++d) sc.a[lane][d] = (T)p[(long long)nd * D + d];
   }
   __syncwarp();
   if (lane < ng) {
@@ -198,7 +221,7 @@ __device__ void svk_tangent(const SvkParams &P, const SvkDev &V, int e, const do
       }
     for (int a = 0; a < nen; ++a)
       for (int i = 0; i < D; ++i)
-        for (int j = 0; j < D; ++j) dH[i][j] += (T)W.a[a][i] * dN[a * D + j];
+        for (int j = 0; j < D; ++j) dH[i][j] += sc.a[a][i] * dN[a * D + j];
     T FtdH[D][D], tr = (T)0;
     for (int i = 0; i < D; ++i)
       for (int j = 0; j < D; ++j) {
@@ -217,13 +240,13 @@ __device__ void svk_tangent(const SvkParams &P, const SvkDev &V, int e, const do
       for (int j = 0; j < D; ++j) {
         T q = (T)0;
         for (int k = 0; k < D; ++k) q += dH[i][k] * S[k][j] + F[i][k] * inner[k][j];
-        W.gp[lane][i * D + j] = (double)((T)P.theta * w * q);
+        sc.gp[lane][i * D + j] = (T)P.theta * w * q;
       }
     const T *N = tb.N + (long long)lane * nen;
     for (int i = 0; i < D; ++i) {
       T s = (T)0;
-      for (int b = 0; b < nen; ++b) s += N[b] * (T)W.a[b][i];
-      W.gm[lane][i] = (double)((T)(cM * P.rho) * w * s);
+      for (int b = 0; b < nen; ++b) s += N[b] * sc.a[b][i];
+      sc.gm[lane][i] = (T)(cM * P.rho) * w * s;
     }
   }
   __syncwarp();
@@ -232,8 +255,8 @@ __device__ void svk_tangent(const SvkParams &P, const SvkDev &V, int e, const do
       T s = (T)0;
       for (int g = 0; g < ng; ++g) {
         const T *dN = tb.dN + (((long long)e * ng + g) * nen + lane) * D;
-        for (int j = 0; j < D; ++j) s += (T)W.gp[g][i * D + j] * dN[j];
-        s += tb.N[(long long)g * nen + lane] * (T)W.gm[g][i];
+        for (int j = 0; j < D; ++j) s += sc.gp[g][i * D + j] * dN[j];
+        s += tb.N[(long long)g * nen + lane] * sc.gm[g][i];
       }
       atomicAdd(y + (long long)W.node[lane] * D + i, (double)s);
     }
