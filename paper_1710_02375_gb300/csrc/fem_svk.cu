@@ -194,19 +194,24 @@ struct SvkTab<float> {
   __device__ SvkTab(const SvkDev &V) : dN(V.dNXf), w(V.wdetf), N(V.Ntabf), F(V.Fgf), S(V.Sgf) {}
 };
 
-// Element e, tangent product: y += (cM M_e + theta A'_e(u)) p with the
+// Element e, tangent product: y += (cM M_e + theta A'_e(u)) p, p = z + beta
+// p_prev formed here (the CG search direction before it is stored), with the
 // stored F, S: the printed Gateaux form (grad p S + F (mu (grad p^T F + F^T
 // grad p) + lambda tr(F^T grad p) I), grad psi).
 template <int D, typename T>
-__device__ void svk_tangent(const SvkParams &P, const SvkDev &V, int e, const double *p,
-                            double *y, double cM, SvkWarp<D> &W, int lane) {
+__device__ void svk_tangent(const SvkParams &P, const SvkDev &V, int e, const double *z,
+                            const double *p, double beta, double *y, double cM, SvkWarp<D> &W,
+                            int lane) {
   const SvkTab<T> tb(V);
   const SvkScr<D, T> sc(W);
   constexpr int nen = SvkEl<D>::nen, ng = SvkEl<D>::ng, DD = SvkEl<D>::DD;
   if (lane < nen) {
     const int nd = V.conn[(long long)e * nen + lane];
     W.node[lane] = nd;
-    for (int d = 0; d < D; ++d) sc.a[lane][d] = (T)p[(long long)nd * D + d];
+    for (int d = 0; d < D; ++d) {
+      const long long k = (long long)nd * D + d;
+      sc.a[lane][d] = (T)__fma_rn(beta, p[k], z[k]);
+    }
   }
   __syncwarp();
   if (lane < ng) {
@@ -343,8 +348,9 @@ __device__ __forceinline__ void svk_sum2(double *red, int &slot, double a, doubl
 
 // One theta step.  Barriers per Newton iteration: element forces and mass
 // (1), the residual norm (1), the Jacobi diagonal (1), per CG iteration the
-// tangent products (1), two reductions and the new search direction (3),
-// the relaxed update (1).
+// tangent products and two reductions (3; the search direction p = z + beta
+// p_prev is formed where it is read, the same FMA at every site, and stored
+// by the update), the relaxed update (1).
 template <int D, typename T, int THREADS>
 __global__ void __launch_bounds__(THREADS) k_svk_step(SvkParams P, SvkDev V) {
   constexpr int kSvkWarps = THREADS / 32;
@@ -402,19 +408,21 @@ __global__ void __launch_bounds__(THREADS) k_svk_step(SvkParams P, SvkDev V) {
     for (long long i = gt; i < n; i += gs) {
       const double z = V.fixed[i] ? 0.0 : V.r[i] / V.diag[i];
       V.z[i] = z;
-      V.p[i] = z;
+      V.p[i] = 0.0;
       V.Ap[i] = 0.0;
       rz += V.r[i] * z;
     }
     svk_sum2<THREADS>(V.red, slot, rz, 0.0, ra, rb);
     rz = ra;
+    double beta = 0.0;
     int k = 0;
     while (k < P.max_cg) {
-      for (int e = wg; e < P.ne; e += nwg) svk_tangent<D, T>(P, V, e, V.p, V.Ap, cM, W, lane);
+      for (int e = wg; e < P.ne; e += nwg)
+        svk_tangent<D, T>(P, V, e, V.z, V.p, beta, V.Ap, cM, W, lane);
       svk_sync();
       double pAp = 0.0;
       for (long long i = gt; i < n; i += gs)
-        if (!V.fixed[i]) pAp += V.p[i] * V.Ap[i];
+        if (!V.fixed[i]) pAp += __fma_rn(beta, V.p[i], V.z[i]) * V.Ap[i];
       svk_sum2<THREADS>(V.red, slot, pAp, 0.0, ra, rb);
       ++k;
       if (!(ra > 0.0)) break;
@@ -422,9 +430,12 @@ __global__ void __launch_bounds__(THREADS) k_svk_step(SvkParams P, SvkDev V) {
       double rzn = 0.0, rr = 0.0;
       for (long long i = gt; i < n; i += gs) {
         if (V.fixed[i]) continue;
-        V.x[i] += alpha * V.p[i];
+        const double pk = __fma_rn(beta, V.p[i], V.z[i]);
+        V.p[i] = pk;
+        V.x[i] += alpha * pk;
         const double r = V.r[i] - alpha * V.Ap[i];
         const double z = r / V.diag[i];
+        V.Ap[i] = 0.0;
         V.r[i] = r;
         V.z[i] = z;
         rzn += r * z;
@@ -432,13 +443,8 @@ __global__ void __launch_bounds__(THREADS) k_svk_step(SvkParams P, SvkDev V) {
       }
       svk_sum2<THREADS>(V.red, slot, rzn, rr, ra, rb);
       if (sqrt(rb) <= P.cg_rtol * gn) break;
-      const double beta = ra / rz;
+      beta = ra / rz;
       rz = ra;
-      for (long long i = gt; i < n; i += gs) {
-        V.p[i] = V.fixed[i] ? 0.0 : V.z[i] + beta * V.p[i];
-        V.Ap[i] = 0.0;
-      }
-      svk_sync();
     }
     cg_total += k;
     for (long long i = gt; i < n; i += gs) {
