@@ -9,7 +9,8 @@ formulas:
   - the internal force is the gradient of a separately written strain energy,
     and the tangent the derivative of the force (central differences);
   - a plane-strain cantilever under a small end shear matches Timoshenko beam
-    theory;
+    theory, and a hexahedral cantilever vibrates at the Euler-Bernoulli
+    frequency;
   - CSM3 (the paper's structural benchmark) reproduces the paper's printed
     tip displacements and frequency (tests/golden/csm3_tip.txt)."""
 import os
@@ -164,3 +165,38 @@ def test_csm3_against_the_papers_table():
     f = 1.0 / (2.0 * np.mean(np.diff(tc)))
     print(f"f {f:.4f} (paper {gold['f_y']})")
     assert abs(f - gold["f_y"]) <= 0.01 * gold["f_y"]
+
+
+def test_hexahedral_cantilever_free_vibration_frequency():
+    """3-D dynamics: a cantilever of 10 x 1 x 1 27-node hexahedra (1 x 0.1 x
+    0.1, clamped face) released from its static shape under a small tip load,
+    theta = 1/2, dt = T / 40, two periods: the first bending frequency within
+    2 % below / 1 % above Euler-Bernoulli's 1.8751^2 / (2 pi) sqrt(E I / (rho A
+    L^4)) (shear and rotary inertia lower it a little), and the amplitude kept
+    (the midpoint theta rule conserves the energy of the linear vibration)."""
+    E, nu, rho, L, b = 1e4, 0.3, 1.0, 1.0, 0.1
+    X, conn = synth.q2_box_mesh([10, 1, 1], [L, b, b], origin=[0, -b / 2, -b / 2])
+    fixed = np.repeat(X[:, 0] < 1e-12, 3)
+    f_eb = 1.875104 ** 2 / (2 * np.pi) * np.sqrt(E * b ** 4 / 12 / (rho * b * b * L ** 4))
+    dt = 1 / f_eb / 40
+    s = so.SVK(X, conn, E, nu, rho, fixed, rtol=1e-6, atol=1e-16)
+    F = np.zeros(X.size)
+    tip = np.abs(X[:, 0] - L) < 1e-12
+    F.reshape(-1, 3)[tip, 1] = -1e-3 / tip.sum()
+    u, it = s.static(F)
+    assert it >= 0
+    y0 = u.reshape(-1, 3)[tip, 1].mean()
+    v, y, zero = np.zeros(X.size), [], np.zeros(X.size)
+    for _ in range(85):
+        u, v, it = s.step(u, v, zero, zero, dt)
+        assert it >= 0
+        y.append(u.reshape(-1, 3)[tip, 1].mean())
+    y = np.array(y)
+    t = dt * np.arange(1, len(y) + 1)
+    k = np.nonzero(y[:-1] * y[1:] < 0)[0]
+    tc = t[k] + dt * (-y[k]) / (y[k + 1] - y[k])
+    f = 1.0 / (2.0 * np.mean(np.diff(tc)))
+    print(f"hexahedral cantilever: f {f:.5f}, Euler-Bernoulli {f_eb:.5f}, ratio {f / f_eb:.4f}, "
+          f"amplitude {np.abs(y).max() / abs(y0):.4f}")
+    assert 0.98 <= f / f_eb <= 1.01
+    assert np.abs(y).max() >= 0.98 * abs(y0)
